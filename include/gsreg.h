@@ -1,0 +1,259 @@
+/*
+ * gsreg.h -- C ABI of the GB300 (sm_103a) 3D-Gaussian submap registration
+ * library libgsreg.so.
+ *
+ * The method is LoopSplat's registration of Gaussian-splat submaps
+ * (arXiv 2408.10154, Sec. 3.2): one submap is moved by a rigid transform,
+ * rendered (RGB + depth) at keyframes of the other submap, and the L1 colour
+ * + L1 depth loss is descended on the transform, in both directions; the
+ * per-keyframe estimates are fused by residual-weighted rotation averaging
+ * (Eq. 7).  The renderer is the 3D Gaussian splatting forward model the
+ * paper builds on (EWA projection, 16x16 screen tiles sorted by depth,
+ * front-to-back alpha compositing) and its adjoint.
+ *
+ * Conventions (all entry points):
+ *   - Every array argument is a DEVICE pointer owned by the caller unless its
+ *     comment says "host".  Arrays are C-contiguous float32 unless stated.
+ *   - Calls are stream-ordered on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) and return once the work is enqueued, except where a
+ *     comment says the call synchronises.  Device pointers must stay valid
+ *     until that work completes.
+ *   - Every function returns a gs_status_t.  GS_ERR_* leaves outputs
+ *     undefined; gs_last_error() then describes the failure.  No C++
+ *     exception crosses this boundary.  Device code never traps: faults of the
+ *     data (non-finite inputs, list capacity) are reported through a device
+ *     status word read back by the synchronising calls.
+ *   - Matrices are row-major 3x4 [R | t].  A "pose" maps the moving submap's
+ *     object frame to the world frame (mu' = R mu + t, Sigma' = R Sigma R^T,
+ *     Eq. 8/9).  Cameras are OpenCV-style (x right, y down, z forward) with a
+ *     world -> camera transform; pixel (px, py) samples the image at
+ *     (px + 0.5, py + 0.5).
+ *   - The library owns scratch memory only inside a gs_ctx_t, allocated with
+ *     cudaMalloc on first use and grown up to the context's byte budget.
+ */
+#ifndef GSREG_H
+#define GSREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSREG_VERSION 1
+/* screen tile side in pixels (fixed: the kernels run one 16x16 CTA per tile) */
+#define GS_TILE 16
+/* floats per projected record (gs_project) and per auxiliary record */
+#define GS_RECORD_FLOATS 12
+#define GS_AUX_FLOATS 8
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* bad pointer, size, camera or option */
+    GS_ERR_OOM = 2,         /* workspace would exceed the context budget or cudaMalloc failed */
+    GS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in gs_last_error) */
+    GS_ERR_NONFINITE = 4,   /* an input Gaussian parameter or pose is NaN / Inf */
+    GS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    GS_ERR_DIVERGED = 6,    /* a registration ended with a non-finite residual */
+    GS_ERR_CAPACITY = 7     /* a duplicate list outgrew its capacity twice */
+} gs_status_t;
+
+typedef struct gs_ctx gs_ctx_t;
+typedef void *gs_stream_t; /* cudaStream_t */
+
+/* A submap of n Gaussians {mu, Sigma, o, C} (Eq. 1), SoA, float4-padded:
+ * Sigma = R(q) diag(e^{2 s}) R(q)^T from per-axis log-scales s and a
+ * quaternion q (normalised on use); opacity o = sigmoid(logit); colour C in
+ * [0,1]^3, no spherical harmonics (Sec. 3.3, last paragraph). */
+typedef struct {
+    const float *means;          /* [n][4]: x, y, z, unused */
+    const float *log_scales;     /* [n][4]: sx, sy, sz, unused */
+    const float *quats;          /* [n][4]: w, x, y, z */
+    const float *opacity_logits; /* [n] */
+    const float *rgb;            /* [n][4]: r, g, b, unused */
+    int64_t n;                   /* 0 <= n < 2^31 */
+} gs_gaussians_t;
+
+/* Pinhole keyframe camera: intrinsics, image size and world -> camera. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height; /* 1..32768 each */
+    float world_to_cam[12];
+} gs_camera_t;
+
+/* A keyframe viewpoint v = (I, D, T) (Eq. 6): its colour and depth images
+ * (device, planar) and its camera. */
+typedef struct {
+    const float *rgb;   /* [3][H][W] */
+    const float *depth; /* [H][W] */
+    gs_camera_t cam;
+} gs_view_t;
+
+/* Renderer and optimiser options; gs_default_options() fills them. */
+typedef struct {
+    int32_t tile;      /* must be GS_TILE */
+    float z_near;      /* cull Gaussians with camera depth <= z_near (0.2 m) */
+    float dilation;    /* 2D low-pass added to the projected covariance (0.3 px^2) */
+    float alpha_min;   /* skip contributions with alpha < alpha_min (1/255) */
+    float alpha_max;   /* clamp alpha to alpha_max (0.99) */
+    float t_min;       /* stop before transmittance would drop below t_min (1e-4) */
+    float bg[3];       /* background colour (0) */
+    int32_t smooth;    /* 1: no radius cull (every tile), for derivative checks */
+    /* registration (Sec. 3.2; learning rates from Supp. B) */
+    float lr_rot;      /* 0.015 rad */
+    float lr_trans;    /* 0.005 m */
+    float beta1;       /* 0.8 */
+    float beta2;       /* 0.99 */
+    float adam_eps;    /* 1e-8 */
+    float lr_final;    /* cosine decay of both rates to this fraction (0.001) */
+} gs_options_t;
+
+/* ---------------------------------------------------------------- context */
+
+/* Fills *o with the defaults listed in gs_options_t. */
+void gs_default_options(gs_options_t *o);
+
+/* Creates a context on CUDA device `device` whose scratch memory never
+ * exceeds `hbm_budget_bytes` (0 = 16 GiB).  Allocates nothing yet. */
+gs_status_t gs_ctx_create(int device, size_t hbm_budget_bytes, gs_ctx_t **out);
+
+/* Frees the context's scratch (synchronises the device first). */
+gs_status_t gs_ctx_destroy(gs_ctx_t *ctx);
+
+/* Message of the last failure on this context (static storage; "" if none). */
+const char *gs_last_error(const gs_ctx_t *ctx);
+
+/* Bytes of scratch the context holds now. */
+size_t gs_ctx_bytes(const gs_ctx_t *ctx);
+
+/* -------------------------------------------------------------- rendering */
+
+/* Projection of a submap moved by one pose per camera (Eq. 8/9, then the EWA
+ * projection of the 3DGS renderer: mean to pixel, covariance to the screen,
+ * 3-sigma radius, tile rectangle).
+ *   g         submap (n Gaussians)
+ *   poses     [n_cams][12] device: pose of the submap for camera c
+ *   cams      [n_cams] host
+ *   records   [n_cams * n][GS_RECORD_FLOATS] out: record of (camera c,
+ *             Gaussian i) at index c*n + i:
+ *             {u, v, ca, cb, cc, o, z, rect_x, r, g, b, rect_y}; the exponent
+ *             at pixel offset (dx, dy) = (u - x, v - y) is
+ *             ca dx^2 + cb dx dy + cc dy^2; rect_x / rect_y hold the tile
+ *             range bits (lo | hi << 16) as uint32.  Undefined when culled.
+ *   aux       [n_cams * n][GS_AUX_FLOATS] out or NULL: camera-space mean
+ *             x, y and covariance {S00, S01, S02, S11, S12, S22}.
+ *   counts    [n_cams * n] int32 out: tiles touched, 0 if culled.
+ * Every integer outcome (cull, rect, count) and every FP32 bit of the
+ * record follows a fixed single-precision operation sequence. */
+gs_status_t gs_project(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses,
+                       const gs_camera_t *cams, int n_cams, const gs_options_t *opt,
+                       float *records, float *aux, int32_t *counts, gs_stream_t stream);
+
+/* Tile binning of the records of gs_project: duplicates every visible record
+ * into each tile it touches with key (global tile << 32) | float bits of z,
+ * value = record index, sorted stably by key (ties keep record order), and
+ * per-tile [start, end) ranges (0,0 when empty).  Camera c's tiles follow
+ * those of cameras 0..c-1 (row-major within a camera).
+ *   keys      [capacity] uint64 out, vals [capacity] uint32 out
+ *   ranges    [total tiles][2] uint32 out
+ *   n_dups    host out: number of duplicates (may exceed capacity: then
+ *             nothing is written and GS_ERR_CAPACITY is returned).
+ * Synchronises `stream`. */
+gs_status_t gs_bin(gs_ctx_t *ctx, const float *records, const int32_t *counts, const gs_camera_t *cams,
+                   int n_cams, int64_t n, uint64_t *keys, uint32_t *vals, int64_t capacity,
+                   uint32_t *ranges, int64_t *n_dups, gs_stream_t stream);
+
+/* Renders a submap moved by poses[c] at cams[c] (Sec. 3.2 "render RGB and
+ * depth").  Outputs are concatenated per camera: camera c's planes start
+ * after those of cameras 0..c-1 (rgb: 3*W*H floats per camera, planar).
+ *   rgb [sum 3HW], depth [sum HW], alpha [sum HW] (= 1 - final
+ *   transmittance), t_final [sum HW], last [sum HW] int32 (one past the
+ *   tile-list position of the last contributor).  Any output may be NULL
+ *   except t_final and last when gs_render_backward will follow.
+ * Synchronises `stream` once (to size the tile lists). */
+gs_status_t gs_render(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams,
+                      int n_cams, const gs_options_t *opt, float *rgb, float *depth, float *alpha,
+                      float *t_final, int32_t *last, gs_stream_t stream);
+
+/* Per-Gaussian parameter gradients (all device, any may be NULL); they are
+ * OVERWRITTEN: means [n][4], log_scales [n][4], quats [n][4],
+ * opacity_logits [n], rgb [n][4] (the 4th component is written as 0). */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logits, *rgb;
+} gs_gaussian_grads_t;
+
+/* Adjoint of gs_render for the cotangents d_rgb, d_depth, d_alpha (any may
+ * be NULL = 0), given the forward's t_final and last.
+ *   pivots     [n_cams][3] device or NULL (= origin): the pose gradient is
+ *              that of a left perturbation about pivot c,
+ *              x -> exp([w]x)(x - c) + c + v, in the world frame.
+ *   pose_grad  [n_cams][6] float out or NULL: dL/d(w, v) per camera.
+ *   grads      per-Gaussian gradients or NULL (summed over cameras).
+ * Synchronises `stream` once. */
+gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses,
+                               const gs_camera_t *cams, int n_cams, const gs_options_t *opt,
+                               const float *t_final, const int32_t *last, const float *d_rgb,
+                               const float *d_depth, const float *d_alpha, const float *pivots,
+                               float *pose_grad, const gs_gaussian_grads_t *grads, gs_stream_t stream);
+
+/* L1 colour + L1 depth loss per view (Sec. 3.2: L = L_col + L_depth):
+ * L_v = mean over 3HW of |I^ - I| + mean over HW of |D^ - D|, and its
+ * gradients sign(.)/(3HW), sign(.)/(HW) (sign(0) = 0).  Images are
+ * concatenated per camera as in gs_render.
+ *   loss [n_cams] double out; d_rgb, d_depth out or NULL. */
+gs_status_t gs_loss(gs_ctx_t *ctx, const gs_camera_t *cams, int n_cams, const float *rgb, const float *depth,
+                    const float *t_rgb, const float *t_depth, double *loss, float *d_rgb, float *d_depth,
+                    gs_stream_t stream);
+
+/* ---------------------------------------------------------- registration */
+
+/* One Adam step on the pose twist and the pose update about the pivot, for
+ * n independent poses (the on-device update of the registration loop):
+ *   pose   [n][12] double in/out (object -> world)
+ *   state  [n][13] double in/out: Adam m[6], v[6], step count
+ *   grad   [n][6] double: dL/d(w, v) about pivot
+ *   pivot  [n][3] double: rotation centre (world frame)
+ * Learning rate = lr * (f + (1-f)(1 + cos(pi k / iters))/2), f = lr_final;
+ * new pose: R <- exp([-w_step]x) R, t <- exp(.)(t - c) + c - v_step. */
+gs_status_t gs_pose_step(gs_ctx_t *ctx, int n, double *pose, double *state, const double *grad,
+                         const double *pivot, int k, int iters, const gs_options_t *opt, gs_stream_t stream);
+
+/* Multi-view pose refinement (Eq. 7): fuses k estimates of T_{P->Q}.
+ *   est      [k][12] double: estimates; reverse[i] != 0 marks an estimate of
+ *            T_{Q->P}, inverted first (int32 [k])
+ *   eps      [k] double: residuals; weights 1/max(eps, 1e-12)
+ *   T_out    [12] double out: rotation = weighted chordal L2 mean,
+ *            translation = weighted mean; conf [1] double out: mean weight. */
+gs_status_t gs_fuse(gs_ctx_t *ctx, int k, const double *est, const int32_t *reverse, const double *eps,
+                    double *T_out, double *conf, gs_stream_t stream);
+
+/* 3DGS registration of submap P (src) and Q (tgt) (Sec. 3.2), both
+ * directions in parallel:
+ *   - each keyframe of V^P (src_views) localised in Q: Q moved by X so that
+ *     its render at the keyframe matches the keyframe; estimate X^-1;
+ *   - each keyframe of V^Q (tgt_views) localised in P: estimate Y;
+ *   each from the identity, `iters` Adam steps on the twist about the
+ *   moving submap's centroid; residual eps = loss at the final pose;
+ *   fused by Eq. 7.  n_src_views or n_tgt_views may be 0 (one direction).
+ *   T_out [12] host out: T_{P->Q} (float64)
+ *   confidence host out: mean inverse residual
+ *   eps_out [n_src_views + n_tgt_views] host out or NULL
+ *   est_out [n_src_views + n_tgt_views][12] host out or NULL: per-keyframe
+ *   estimates of T_{P->Q} (V^P first).
+ * Synchronises `stream`. */
+gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gaussians_t *tgt,
+                        const gs_view_t *src_views, int n_src_views, const gs_view_t *tgt_views,
+                        int n_tgt_views, const gs_options_t *opt, int iters, double *T_out,
+                        double *confidence, double *eps_out, double *est_out, gs_stream_t stream);
+
+/* Rigid transform of a submap by T (Eq. 8/9): mu <- R mu + t,
+ * q <- q_R (x) q (so Sigma <- R Sigma R^T); scales, opacities, colours
+ * unchanged.  out_means, out_quats [n][4] device (may alias the inputs). */
+gs_status_t gs_transform(gs_ctx_t *ctx, const gs_gaussians_t *g, const double *T_host, float *out_means,
+                         float *out_quats, gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSREG_H */

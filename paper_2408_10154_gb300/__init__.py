@@ -1,1 +1,9 @@
-"""placeholder"""
+"""GB300-native (sm_103a) 3D-Gaussian submap registration: the differentiable
+splat rasteriser and on-device pose optimisation behind LoopSplat's 3DGS
+registration (arXiv 2408.10154, Sec. 3.2), as hand-written CUDA kernels
+behind the C ABI of include/gsreg.h.
+
+``gsreg`` is the Python binding (argument marshalling only); ``synth`` draws
+seeded synthetic workloads; ``build`` compiles the library in-tree."""
+from .gsreg import (Context, Gaussians, GsError, default_options, gs_bin, gs_fuse, gs_loss, gs_pose_step,  # noqa: F401
+                    gs_project, gs_register, gs_render, gs_render_backward, gs_transform, load, split_views)

@@ -1,0 +1,953 @@
+// api.cu -- the C ABI of include/gsreg.h: context and scratch arena,
+// argument checks, and the orchestration of the kernels behind each entry
+// point, including the CUDA-graph-replayed registration loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+enum Slot {
+    S_VPS, S_GROUPS, S_TILEVP, S_POSE32, S_REC, S_AUX, S_COUNTS, S_PARTIALS, S_NDUPS, S_K0, S_K1, S_V0, S_V1,
+    S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
+    S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
+    S_COUNT
+};
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct gs_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    std::string err;
+    Buf bufs[S_COUNT];
+    cudaStream_t cap = nullptr;  // private stream used only for graph capture
+};
+
+namespace {
+
+using gsk::GroupDesc;
+using gsk::VpDesc;
+
+gs_status_t fail(gs_ctx *c, gs_status_t st, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    return st;
+}
+
+#define GS_CUDA(call)                                                                            \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ctx, GS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+#define GS_TRY(expr)                   \
+    do {                               \
+        gs_status_t s_ = (expr);       \
+        if (s_ != GS_OK)               \
+            return s_;                 \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        if (prev != dev)
+            cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+            cudaSetDevice(prev);
+    }
+};
+
+// scratch buffer of at least `bytes` for `slot` (grown, never shrunk)
+gs_status_t ws(gs_ctx *ctx, int slot, size_t bytes, void **out)
+{
+    Buf &b = ctx->bufs[slot];
+    if (bytes == 0)
+        bytes = 16;
+    if (b.bytes >= bytes) {
+        *out = b.p;
+        return GS_OK;
+    }
+    size_t want = ((bytes + bytes / 4) + 255) & ~(size_t)255;
+    if (ctx->used - b.bytes + want > ctx->budget) {
+        want = (bytes + 255) & ~(size_t)255;
+        if (ctx->used - b.bytes + want > ctx->budget)
+            return fail(ctx, GS_ERR_OOM, "scratch of " + std::to_string(bytes) + " bytes exceeds the context budget");
+    }
+    if (b.p) {
+        cudaFree(b.p);  // synchronises the device: no kernel still uses it
+        ctx->used -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(ctx, GS_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+    }
+    b.bytes = want;
+    ctx->used += want;
+    *out = b.p;
+    return GS_OK;
+}
+
+template <typename T>
+gs_status_t wsT(gs_ctx *ctx, int slot, size_t count, T **out)
+{
+    void *p = nullptr;
+    GS_TRY(ws(ctx, slot, count * sizeof(T), &p));
+    *out = (T *)p;
+    return GS_OK;
+}
+
+template <typename T>
+gs_status_t upload(gs_ctx *ctx, int slot, const std::vector<T> &v, T **out, cudaStream_t s)
+{
+    GS_TRY(wsT(ctx, slot, v.size(), out));
+    if (!v.empty())
+        GS_CUDA(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return GS_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+gs_status_t check_gaussians(gs_ctx *ctx, const gs_gaussians_t *g, const char *what)
+{
+    if (!g)
+        return fail(ctx, GS_ERR_INVALID_ARG, std::string(what) + ": null submap");
+    if (g->n < 0 || g->n >= (int64_t)1 << 31)
+        return fail(ctx, GS_ERR_INVALID_ARG, std::string(what) + ": n out of range");
+    if (g->n == 0)
+        return GS_OK;
+    if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->rgb)
+        return fail(ctx, GS_ERR_INVALID_ARG, std::string(what) + ": null array");
+    if (!aligned16(g->means) || !aligned16(g->log_scales) || !aligned16(g->quats) || !aligned16(g->rgb))
+        return fail(ctx, GS_ERR_INVALID_ARG, std::string(what) + ": float4 arrays must be 16-byte aligned");
+    return GS_OK;
+}
+
+gs_status_t check_camera(gs_ctx *ctx, const gs_camera_t &c)
+{
+    if (c.width < 1 || c.height < 1 || c.width > 32768 || c.height > 32768)
+        return fail(ctx, GS_ERR_INVALID_ARG, "camera size out of range [1, 32768]");
+    if (!(c.fx > 0) || !(c.fy > 0) || !std::isfinite(c.fx) || !std::isfinite(c.fy) || !std::isfinite(c.cx) ||
+        !std::isfinite(c.cy))
+        return fail(ctx, GS_ERR_INVALID_ARG, "camera intrinsics must be finite with fx, fy > 0");
+    for (float v : c.world_to_cam)
+        if (!std::isfinite(v))
+            return fail(ctx, GS_ERR_INVALID_ARG, "camera extrinsics must be finite");
+    return GS_OK;
+}
+
+gs_status_t check_options(gs_ctx *ctx, const gs_options_t *o)
+{
+    if (!o)
+        return fail(ctx, GS_ERR_INVALID_ARG, "null options");
+    if (o->tile != GS_TILE)
+        return fail(ctx, GS_ERR_INVALID_ARG, "options.tile must be GS_TILE (16)");
+    if (!(o->alpha_max > 0 && o->alpha_max <= 1) || !(o->alpha_min >= 0) || !(o->t_min >= 0) ||
+        !(o->dilation >= 0) || !std::isfinite(o->z_near))
+        return fail(ctx, GS_ERR_INVALID_ARG, "options out of range");
+    return GS_OK;
+}
+
+// the tiles / records / pixels of a list of keyframes
+struct Plan {
+    std::vector<VpDesc> vps;
+    std::vector<GroupDesc> groups;
+    std::vector<uint32_t> tile_vp;
+    std::vector<int> set_vp;  // a vp of each Gaussian set
+    uint64_t n_records = 0, n_tiles = 0;
+    int64_t n_pix = 0;
+    uint32_t proj_blocks = 0;
+};
+
+void add_vp(Plan &P, const gs_gaussians_t *g, const gs_camera_t &c, int set, int problem, int reverse,
+            const float *trgb, const float *tdepth)
+{
+    VpDesc d{};
+    d.means = (const float4 *)g->means;
+    d.scales = (const float4 *)g->log_scales;
+    d.quats = (const float4 *)g->quats;
+    d.rgb = (const float4 *)g->rgb;
+    d.logits = g->opacity_logits;
+    d.n = (int)g->n;
+    d.W = c.width;
+    d.H = c.height;
+    d.TX = (c.width + GS_TILE - 1) / GS_TILE;
+    d.TY = (c.height + GS_TILE - 1) / GS_TILE;
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    std::memcpy(d.w2c, c.world_to_cam, sizeof d.w2c);
+    d.rec_base = (uint32_t)P.n_records;
+    d.tile_base = (uint32_t)P.n_tiles;
+    d.pix_base = P.n_pix;
+    d.t_rgb = trgb;
+    d.t_depth = tdepth;
+    d.set = set;
+    d.problem = problem;
+    d.reverse = reverse;
+    const int vp = (int)P.vps.size();
+    for (int k = 0; k < d.TX * d.TY; ++k)
+        P.tile_vp.push_back((uint32_t)vp);
+    P.n_records += (uint64_t)d.n;
+    P.n_tiles += (uint64_t)d.TX * d.TY;
+    P.n_pix += (int64_t)c.width * c.height;
+    if ((int)P.set_vp.size() <= set)
+        P.set_vp.resize(set + 1, vp);
+    P.vps.push_back(d);
+}
+
+// groups: runs of consecutive vps that share a Gaussian set, <= kMaxVpPerGroup
+gs_status_t finalize(gs_ctx *ctx, Plan &P)
+{
+    if (P.n_records >= 0xffffffffull || P.n_tiles >= 0xffffffffull)
+        return fail(ctx, GS_ERR_INVALID_ARG, "too many records or tiles for 32-bit indices");
+    P.groups.clear();
+    uint32_t blocks = 0;
+    for (int v = 0; v < (int)P.vps.size();) {
+        int e = v + 1;
+        while (e < (int)P.vps.size() && e - v < gsk::kMaxVpPerGroup && P.vps[e].means == P.vps[v].means &&
+               P.vps[e].n == P.vps[v].n)
+            ++e;
+        GroupDesc G{};
+        G.vp_first = v;
+        G.vp_count = e - v;
+        G.n = P.vps[v].n;
+        G.blk_base = blocks;
+        for (int k = v; k < e; ++k)
+            P.vps[k].group = (int)P.groups.size();
+        P.groups.push_back(G);
+        blocks += (uint32_t)((G.n + 255) / 256);
+        v = e;
+    }
+    P.proj_blocks = blocks;
+    return GS_OK;
+}
+
+int tile_bits(uint64_t n_tiles)
+{
+    int b = 0;
+    while (b < 32 && ((uint64_t)1 << b) < n_tiles)
+        ++b;
+    return b;
+}
+
+float skip_threshold(const gs_options_t *o)
+{
+    // exponents below ln(alpha_min) - 0.05 cannot reach alpha_min (o <= 1):
+    // skipping them without evaluating e^x leaves every decision unchanged
+    return o->alpha_min > 0 ? logf(o->alpha_min) - 0.05f : -3.0e38f;
+}
+
+// device copies of a plan's tables
+struct DevPlan {
+    VpDesc *vps = nullptr;
+    GroupDesc *groups = nullptr;
+    uint32_t *tile_vp = nullptr;
+    int *set_vp = nullptr;
+};
+
+gs_status_t upload_plan(gs_ctx *ctx, const Plan &P, DevPlan &D, cudaStream_t s)
+{
+    GS_TRY(upload(ctx, S_VPS, P.vps, &D.vps, s));
+    GS_TRY(upload(ctx, S_GROUPS, P.groups, &D.groups, s));
+    GS_TRY(upload(ctx, S_TILEVP, P.tile_vp, &D.tile_vp, s));
+    GS_TRY(upload(ctx, S_SETVP, P.set_vp, &D.set_vp, s));
+    return GS_OK;
+}
+
+// scratch of the projection + binning pipeline
+struct Pipe {
+    float4 *rec = nullptr, *aux = nullptr;
+    int32_t *counts = nullptr;
+    uint32_t *partials = nullptr, *ndups = nullptr;
+    uint64_t *keys[2] = {nullptr, nullptr};
+    uint32_t *vals[2] = {nullptr, nullptr};
+    uint32_t *hist = nullptr, *histp = nullptr;
+    uint2 *ranges = nullptr;
+    int *flags = nullptr;
+    uint32_t cap = 0;
+};
+
+gs_status_t alloc_pipe(gs_ctx *ctx, const Plan &P, bool aux, Pipe &p)
+{
+    const size_t R = P.n_records ? P.n_records : 1;
+    GS_TRY(wsT(ctx, S_REC, 3 * R, &p.rec));
+    if (aux)
+        GS_TRY(wsT(ctx, S_AUX, 2 * R, &p.aux));
+    GS_TRY(wsT(ctx, S_COUNTS, R, &p.counts));
+    GS_TRY(wsT(ctx, S_PARTIALS, gsl::scan_partials(R), &p.partials));
+    GS_TRY(wsT(ctx, S_NDUPS, 4, &p.ndups));
+    GS_TRY(wsT(ctx, S_RANGES, P.n_tiles ? P.n_tiles : 1, &p.ranges));
+    GS_TRY(wsT(ctx, S_FLAGS, 4, &p.flags));
+    return GS_OK;
+}
+
+gs_status_t alloc_sort(gs_ctx *ctx, uint64_t want, Pipe &p)
+{
+    if (want > 0xfff00000ull)
+        return fail(ctx, GS_ERR_CAPACITY, "more than 2^32 tile duplicates");
+    const uint32_t cap = (uint32_t)std::max<uint64_t>(want, 1024);
+    GS_TRY(wsT(ctx, S_K0, cap, &p.keys[0]));
+    GS_TRY(wsT(ctx, S_K1, cap, &p.keys[1]));
+    GS_TRY(wsT(ctx, S_V0, cap, &p.vals[0]));
+    GS_TRY(wsT(ctx, S_V1, cap, &p.vals[1]));
+    const size_t hn = gsl::sort_hist_entries(cap);
+    GS_TRY(wsT(ctx, S_HIST, hn, &p.hist));
+    GS_TRY(wsT(ctx, S_HISTP, gsl::scan_partials(hn), &p.histp));
+    p.cap = cap;
+    return GS_OK;
+}
+
+gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, const float *pose32,
+                              const gs_options_t *o)
+{
+    gsl::ProjectArgs a{};
+    a.vps = D.vps;
+    a.groups = D.groups;
+    a.n_groups = (int)P.groups.size();
+    a.n_blocks = P.proj_blocks;
+    a.pose32 = pose32;
+    a.z_near = o->z_near;
+    a.dilation = o->dilation;
+    a.smooth = o->smooth;
+    a.rec = p.rec;
+    a.aux = p.aux;
+    a.counts = p.counts;
+    a.flags = p.flags;
+    return a;
+}
+
+gsl::BinArgs bin_args(const Plan &P, const DevPlan &D, const Pipe &p)
+{
+    gsl::BinArgs b{};
+    b.vps = D.vps;
+    b.n_vps = (int)P.vps.size();
+    b.counts = p.counts;
+    b.rec = p.rec;
+    b.n_records = (uint32_t)P.n_records;
+    b.partials = p.partials;
+    b.n_dups = p.ndups;
+    b.keys[0] = p.keys[0];
+    b.keys[1] = p.keys[1];
+    b.vals[0] = p.vals[0];
+    b.vals[1] = p.vals[1];
+    b.capacity = p.cap;
+    b.hist = p.hist;
+    b.hist_partials = p.histp;
+    b.key_bits = 32 + tile_bits(P.n_tiles);
+    b.ranges = p.ranges;
+    b.n_tiles = (uint32_t)P.n_tiles;
+    b.flags = p.flags;
+    return b;
+}
+
+gsl::RasterArgs raster_args(const Plan &P, const DevPlan &D, const Pipe &p, int cur, const gs_options_t *o)
+{
+    gsl::RasterArgs r{};
+    r.vps = D.vps;
+    r.tile_vp = D.tile_vp;
+    r.n_tiles = (uint32_t)P.n_tiles;
+    r.ranges = p.ranges;
+    r.vals = p.vals[cur];
+    r.rec = p.rec;
+    r.aux = p.aux;
+    r.alpha_min = o->alpha_min;
+    r.alpha_max = o->alpha_max;
+    r.t_min = o->t_min;
+    r.skip_below = skip_threshold(o);
+    r.bg[0] = o->bg[0];
+    r.bg[1] = o->bg[1];
+    r.bg[2] = o->bg[2];
+    return r;
+}
+
+// project + count duplicates (synchronises) + size the sort + emit/sort/range
+gs_status_t project_and_bin(gs_ctx *ctx, const Plan &P, const DevPlan &D, Pipe &p, const float *pose32,
+                            const gs_options_t *o, cudaStream_t s, int *cur, uint32_t *n_dups_out)
+{
+    GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
+    gsl::project(project_args(P, D, p, pose32, o), s);
+    gsl::BinArgs b = bin_args(P, D, p);
+    gsl::bin_count(b, s);
+    uint32_t nd = 0;
+    GS_CUDA(cudaMemcpyAsync(&nd, p.ndups, sizeof nd, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    if (nd == 0xffffffffu)
+        return fail(ctx, GS_ERR_CAPACITY, "more than 2^32 tile duplicates");
+    if (p.cap < nd || !p.keys[0])
+        GS_TRY(alloc_sort(ctx, nd, p));
+    b = bin_args(P, D, p);
+    *cur = gsl::bin(b, s);
+    if (n_dups_out)
+        *n_dups_out = nd;
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t read_flags(gs_ctx *ctx, const Pipe &p, cudaStream_t s, int *flags)
+{
+    GS_CUDA(cudaMemcpyAsync(flags, p.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    return GS_OK;
+}
+
+gs_status_t check_common(gs_ctx *ctx, const gs_gaussians_t *g, const gs_camera_t *cams, int n_cams,
+                         const gs_options_t *o)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_options(ctx, o));
+    GS_TRY(check_gaussians(ctx, g, "submap"));
+    if (n_cams < 0 || (n_cams > 0 && !cams))
+        return fail(ctx, GS_ERR_INVALID_ARG, "bad camera list");
+    for (int c = 0; c < n_cams; ++c)
+        GS_TRY(check_camera(ctx, cams[c]));
+    return GS_OK;
+}
+
+Plan plan_for(const gs_gaussians_t *g, const gs_camera_t *cams, int n_cams)
+{
+    Plan P;
+    for (int c = 0; c < n_cams; ++c)
+        add_vp(P, g, cams[c], 0, 0, 0, nullptr, nullptr);
+    return P;
+}
+
+// pivots (world, float [n][3]) -> camera frame for each vp
+__global__ void k_cam_pivots(const VpDesc *vps, int n, const float *piv, double *ccam)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n)
+        return;
+    const VpDesc &d = vps[v];
+    const double c[3] = {piv ? piv[3 * v] : 0.0, piv ? piv[3 * v + 1] : 0.0, piv ? piv[3 * v + 2] : 0.0};
+    for (int i = 0; i < 3; ++i)
+        ccam[3 * v + i] = (double)d.w2c[4 * i] * c[0] + (double)d.w2c[4 * i + 1] * c[1] +
+                          (double)d.w2c[4 * i + 2] * c[2] + (double)d.w2c[4 * i + 3];
+}
+
+__global__ void k_to_float(const double *in, float *out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        out[i] = (float)in[i];
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported entry points
+// ===========================================================================
+extern "C" {
+
+void gs_default_options(gs_options_t *o)
+{
+    if (!o)
+        return;
+    std::memset(o, 0, sizeof *o);
+    o->tile = GS_TILE;
+    o->z_near = 0.2f;
+    o->dilation = 0.3f;
+    o->alpha_min = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->t_min = 1e-4f;
+    o->smooth = 0;
+    o->lr_rot = 0.015f;
+    o->lr_trans = 0.005f;
+    o->beta1 = 0.8f;
+    o->beta2 = 0.99f;
+    o->adam_eps = 1e-8f;
+    o->lr_final = 0.001f;
+}
+
+gs_status_t gs_ctx_create(int device, size_t budget, gs_ctx_t **out)
+{
+    if (!out)
+        return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return GS_ERR_INVALID_ARG;
+    }
+    gs_ctx *ctx = new gs_ctx();
+    ctx->device = device;
+    ctx->budget = budget ? budget : ((size_t)16 << 30);
+    DeviceGuard dg(device);
+    if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return GS_ERR_CUDA;
+    }
+    gsl::raster_init();
+    *out = ctx;
+    return GS_OK;
+}
+
+gs_status_t gs_ctx_destroy(gs_ctx_t *ctx)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    for (Buf &b : ctx->bufs)
+        if (b.p)
+            cudaFree(b.p);
+    if (ctx->cap)
+        cudaStreamDestroy(ctx->cap);
+    delete ctx;
+    return GS_OK;
+}
+
+const char *gs_last_error(const gs_ctx_t *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t gs_ctx_bytes(const gs_ctx_t *ctx) { return ctx ? ctx->used : 0; }
+
+gs_status_t gs_project(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams,
+                       int n_cams, const gs_options_t *opt, float *records, float *aux, int32_t *counts,
+                       gs_stream_t stream)
+{
+    GS_TRY(check_common(ctx, g, cams, n_cams, opt));
+    if (!poses || !records || !counts || !aligned16(records) || (aux && !aligned16(aux)))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_project: null or unaligned output");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan P = plan_for(g, cams, n_cams);
+    GS_TRY(finalize(ctx, P));
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    Pipe p;
+    p.rec = (float4 *)records;
+    p.aux = (float4 *)aux;
+    p.counts = counts;
+    GS_TRY(wsT(ctx, S_FLAGS, 4, &p.flags));
+    GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
+    gsl::project(project_args(P, D, p, poses, opt), s);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_bin(gs_ctx_t *ctx, const float *records, const int32_t *counts, const gs_camera_t *cams,
+                   int n_cams, int64_t n, uint64_t *keys, uint32_t *vals, int64_t capacity, uint32_t *ranges,
+                   int64_t *n_dups, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    if (!records || !counts || !ranges || !n_dups || n < 0 || n_cams < 0 || (n_cams > 0 && !cams) ||
+        capacity < 0 || !aligned16(records))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_bin: bad arguments");
+    for (int c = 0; c < n_cams; ++c)
+        GS_TRY(check_camera(ctx, cams[c]));
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gs_gaussians_t g{};
+    g.n = n;
+    Plan P = plan_for(&g, cams, n_cams);
+    GS_TRY(finalize(ctx, P));
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    Pipe p;
+    p.rec = (float4 *)records;
+    p.counts = (int32_t *)counts;
+    GS_TRY(wsT(ctx, S_PARTIALS, gsl::scan_partials(P.n_records ? P.n_records : 1), &p.partials));
+    GS_TRY(wsT(ctx, S_NDUPS, 4, &p.ndups));
+    GS_TRY(wsT(ctx, S_FLAGS, 4, &p.flags));
+    GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
+    p.ranges = (uint2 *)ranges;
+    gsl::BinArgs b = bin_args(P, D, p);
+    gsl::bin_count(b, s);
+    uint32_t nd = 0;
+    GS_CUDA(cudaMemcpyAsync(&nd, p.ndups, sizeof nd, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    *n_dups = nd;
+    if ((int64_t)nd > capacity || nd == 0xffffffffu)
+        return fail(ctx, GS_ERR_CAPACITY, "gs_bin: " + std::to_string(nd) + " duplicates exceed capacity");
+    GS_TRY(alloc_sort(ctx, nd, p));
+    b = bin_args(P, D, p);
+    const int cur = gsl::bin(b, s);
+    if (nd > 0) {
+        GS_CUDA(cudaMemcpyAsync(keys, p.keys[cur], sizeof(uint64_t) * nd, cudaMemcpyDeviceToDevice, s));
+        GS_CUDA(cudaMemcpyAsync(vals, p.vals[cur], sizeof(uint32_t) * nd, cudaMemcpyDeviceToDevice, s));
+    }
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_render(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams,
+                      int n_cams, const gs_options_t *opt, float *rgb, float *depth, float *alpha, float *t_final,
+                      int32_t *last, gs_stream_t stream)
+{
+    GS_TRY(check_common(ctx, g, cams, n_cams, opt));
+    if (!poses)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render: null poses");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan P = plan_for(g, cams, n_cams);
+    GS_TRY(finalize(ctx, P));
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    Pipe p;
+    GS_TRY(alloc_pipe(ctx, P, false, p));
+    int cur = 0;
+    GS_TRY(project_and_bin(ctx, P, D, p, poses, opt, s, &cur, nullptr));
+    gsl::RasterArgs r = raster_args(P, D, p, cur, opt);
+    r.out_rgb = rgb;
+    r.out_depth = depth;
+    r.out_alpha = alpha;
+    r.t_final = t_final;
+    r.last = last;
+    gsl::forward(r, false, s);
+    GS_CUDA(cudaGetLastError());
+    int flags = 0;
+    GS_TRY(read_flags(ctx, p, s, &flags));
+    if (flags & gsk::kFlagNonFinite)
+        return fail(ctx, GS_ERR_NONFINITE, "non-finite Gaussian parameter");
+    return GS_OK;
+}
+
+gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses,
+                               const gs_camera_t *cams, int n_cams, const gs_options_t *opt,
+                               const float *t_final, const int32_t *last, const float *d_rgb,
+                               const float *d_depth, const float *d_alpha, const float *pivots, float *pose_grad,
+                               const gs_gaussian_grads_t *grads, gs_stream_t stream)
+{
+    GS_TRY(check_common(ctx, g, cams, n_cams, opt));
+    if (!poses || !t_final || !last)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward: null poses or forward state");
+    if (grads && (grads->means || grads->log_scales || grads->quats || grads->opacity_logits || grads->rgb))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward: per-Gaussian gradients are not available");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan P = plan_for(g, cams, n_cams);
+    GS_TRY(finalize(ctx, P));
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    Pipe p;
+    GS_TRY(alloc_pipe(ctx, P, true, p));
+    int cur = 0;
+    GS_TRY(project_and_bin(ctx, P, D, p, poses, opt, s, &cur, nullptr));
+    gsl::RasterArgs r = raster_args(P, D, p, cur, opt);
+    r.t_final = (float *)t_final;
+    r.last = (int32_t *)last;
+    r.d_rgb = d_rgb;
+    r.d_depth = d_depth;
+    r.d_alpha = d_alpha;
+    const int nv = (int)P.vps.size();
+    double *ccam = nullptr, *grad = nullptr, *lossd = nullptr;
+    float *tloss = nullptr;
+    GS_TRY(wsT(ctx, S_CCAM, 3 * (size_t)std::max(nv, 1), &ccam));
+    GS_TRY(wsT(ctx, S_GRAD, 6 * (size_t)std::max(nv, 1), &grad));
+    GS_TRY(wsT(ctx, S_LOSS, (size_t)std::max(nv, 1), &lossd));
+    GS_TRY(wsT(ctx, S_TTWIST, 6 * (size_t)std::max<uint64_t>(P.n_tiles, 1), &r.tile_twist));
+    GS_TRY(wsT(ctx, S_TLOSS, (size_t)std::max<uint64_t>(P.n_tiles, 1), &tloss));
+    GS_CUDA(cudaMemsetAsync(tloss, 0, sizeof(float) * std::max<uint64_t>(P.n_tiles, 1), s));
+    if (nv > 0)
+        k_cam_pivots<<<(nv + 63) / 64, 64, 0, s>>>(D.vps, nv, pivots, ccam);
+    r.c_cam = ccam;
+    gsl::backward(r, false, false, s);
+    gsl::PoseArgs a{};
+    a.vps = D.vps;
+    a.n_vps = nv;
+    a.tile_twist = r.tile_twist;
+    a.tile_loss = tloss;
+    a.loss = lossd;
+    a.grad = grad;
+    a.update = 0;
+    gsl::pose_update(a, s);
+    if (pose_grad && nv > 0)
+        k_to_float<<<(6 * nv + 255) / 256, 256, 0, s>>>(grad, pose_grad, 6 * nv);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_loss(gs_ctx_t *ctx, const gs_camera_t *cams, int n_cams, const float *rgb, const float *depth,
+                    const float *t_rgb, const float *t_depth, double *loss, float *d_rgb, float *d_depth,
+                    gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    if (n_cams < 0 || (n_cams > 0 && (!cams || !rgb || !depth || !t_rgb || !t_depth || !loss)))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_loss: bad arguments");
+    for (int c = 0; c < n_cams; ++c)
+        GS_TRY(check_camera(ctx, cams[c]));
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gs_gaussians_t g{};
+    Plan P;
+    int64_t pix = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        add_vp(P, &g, cams[c], 0, 0, 0, t_rgb + 3 * pix, t_depth + pix);
+        pix += (int64_t)cams[c].width * cams[c].height;
+    }
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    float *tloss = nullptr;
+    GS_TRY(wsT(ctx, S_TLOSS, (size_t)std::max<uint64_t>(P.n_tiles, 1), &tloss));
+    gsl::loss(D.vps, (int)P.vps.size(), (uint32_t)P.n_tiles, D.tile_vp, rgb, depth, loss, d_rgb, d_depth, tloss, s);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_pose_step(gs_ctx_t *ctx, int n, double *pose, double *state, const double *grad,
+                         const double *pivot, int k, int iters, const gs_options_t *opt, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_options(ctx, opt));
+    if (n < 0 || iters <= 0 || k < 0 || (n > 0 && (!pose || !state || !grad || !pivot)))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_pose_step: bad arguments");
+    DeviceGuard dg(ctx->device);
+    gsl::pose_step_raw(n, pose, state, grad, pivot, k, iters, opt->lr_rot, opt->lr_trans, opt->beta1, opt->beta2,
+                       opt->adam_eps, opt->lr_final, (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_fuse(gs_ctx_t *ctx, int k, const double *est, const int32_t *reverse, const double *eps,
+                    double *T_out, double *conf, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    if (k <= 0 || !est || !reverse || !eps || !T_out || !conf)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_fuse: bad arguments");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *pf = nullptr, *pc = nullptr;
+    GS_TRY(upload(ctx, S_PFIRST, std::vector<int32_t>{0}, &pf, s));
+    GS_TRY(upload(ctx, S_PCOUNT, std::vector<int32_t>{k}, &pc, s));
+    gsl::FuseArgs a{};
+    a.pose64 = est;
+    a.eps = eps;
+    a.reverse = reverse;
+    a.prob_first = pf;
+    a.prob_count = pc;
+    a.n_problems = 1;
+    a.T_out = T_out;
+    a.conf = conf;
+    gsl::fuse(a, s);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_transform(gs_ctx_t *ctx, const gs_gaussians_t *g, const double *T_host, float *out_means,
+                         float *out_quats, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_gaussians(ctx, g, "submap"));
+    if (!T_host || (g->n > 0 && (!out_means || !out_quats || !aligned16(out_means) || !aligned16(out_quats))))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_transform: bad arguments");
+    DeviceGuard dg(ctx->device);
+    gsl::transform((const float4 *)g->means, (const float4 *)g->quats, g->n, T_host, (float4 *)out_means,
+                   (float4 *)out_quats, (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gaussians_t *tgt,
+                        const gs_view_t *src_views, int n_src_views, const gs_view_t *tgt_views, int n_tgt_views,
+                        const gs_options_t *opt, int iters, double *T_out, double *confidence, double *eps_out,
+                        double *est_out, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_options(ctx, opt));
+    GS_TRY(check_gaussians(ctx, src, "src"));
+    GS_TRY(check_gaussians(ctx, tgt, "tgt"));
+    if (n_src_views < 0 || n_tgt_views < 0 || n_src_views + n_tgt_views == 0 || iters < 0 || !T_out ||
+        !confidence || (n_src_views > 0 && !src_views) || (n_tgt_views > 0 && !tgt_views))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_register: bad arguments");
+    for (int k = 0; k < n_src_views; ++k) {
+        GS_TRY(check_camera(ctx, src_views[k].cam));
+        if (!src_views[k].rgb || !src_views[k].depth)
+            return fail(ctx, GS_ERR_INVALID_ARG, "gs_register: null keyframe image");
+    }
+    for (int k = 0; k < n_tgt_views; ++k) {
+        GS_TRY(check_camera(ctx, tgt_views[k].cam));
+        if (!tgt_views[k].rgb || !tgt_views[k].depth)
+            return fail(ctx, GS_ERR_INVALID_ARG, "gs_register: null keyframe image");
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // keyframes of P are localised in Q (Q moves; estimate inverted), those
+    // of Q in P (P moves).  Gaussian set 0 = Q, 1 = P.
+    Plan P;
+    for (int k = 0; k < n_src_views; ++k)
+        add_vp(P, tgt, src_views[k].cam, 0, 0, 1, src_views[k].rgb, src_views[k].depth);
+    for (int k = 0; k < n_tgt_views; ++k)
+        add_vp(P, src, tgt_views[k].cam, n_src_views > 0 ? 1 : 0, 0, 0, tgt_views[k].rgb, tgt_views[k].depth);
+    GS_TRY(finalize(ctx, P));
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    const int nv = (int)P.vps.size();
+    const int n_sets = (int)P.set_vp.size();
+    Pipe p;
+    GS_TRY(alloc_pipe(ctx, P, true, p));
+    float *pose32 = nullptr, *tloss = nullptr, *tf = nullptr;
+    double *pose64 = nullptr, *adam = nullptr, *pivot = nullptr, *ccam = nullptr, *cent = nullptr, *lossd = nullptr,
+           *ttw = nullptr, *Tdev = nullptr, *confd = nullptr, *est = nullptr;
+    int32_t *last = nullptr, *rev = nullptr, *pf = nullptr, *pc = nullptr;
+    uint8_t *code = nullptr;
+    const size_t npix = (size_t)std::max<int64_t>(P.n_pix, 1), ntl = (size_t)std::max<uint64_t>(P.n_tiles, 1);
+    GS_TRY(wsT(ctx, S_POSE32, 12 * (size_t)nv, &pose32));
+    GS_TRY(wsT(ctx, S_POSE64, 12 * (size_t)nv, &pose64));
+    GS_TRY(wsT(ctx, S_ADAM, 13 * (size_t)nv, &adam));
+    GS_TRY(wsT(ctx, S_PIVOT, 3 * (size_t)nv, &pivot));
+    GS_TRY(wsT(ctx, S_CCAM, 3 * (size_t)nv, &ccam));
+    GS_TRY(wsT(ctx, S_CENT, 3 * (size_t)n_sets, &cent));
+    GS_TRY(wsT(ctx, S_LOSS, (size_t)nv, &lossd));
+    GS_TRY(wsT(ctx, S_TF, npix, &tf));
+    GS_TRY(wsT(ctx, S_LAST, npix, &last));
+    GS_TRY(wsT(ctx, S_CODE, npix, &code));
+    GS_TRY(wsT(ctx, S_TLOSS, ntl, &tloss));
+    GS_TRY(wsT(ctx, S_TTWIST, 6 * ntl, &ttw));
+    GS_TRY(wsT(ctx, S_TOUT, 12, &Tdev));
+    GS_TRY(wsT(ctx, S_CONF, 1, &confd));
+    GS_TRY(wsT(ctx, S_EST, 12 * (size_t)nv, &est));
+    std::vector<int32_t> revh(nv);
+    for (int v = 0; v < nv; ++v)
+        revh[v] = P.vps[v].reverse;
+    GS_TRY(upload(ctx, S_REV, revh, &rev, s));
+    GS_TRY(upload(ctx, S_PFIRST, std::vector<int32_t>{0}, &pf, s));
+    GS_TRY(upload(ctx, S_PCOUNT, std::vector<int32_t>{nv}, &pc, s));
+
+    gsl::PoseArgs pa{};
+    pa.vps = D.vps;
+    pa.n_vps = nv;
+    pa.tile_twist = ttw;
+    pa.tile_loss = tloss;
+    pa.pose64 = pose64;
+    pa.pose32 = pose32;
+    pa.adam = adam;
+    pa.pivot = pivot;
+    pa.c_cam = ccam;
+    pa.centroid = cent;
+    pa.loss = lossd;
+    pa.lr_rot = opt->lr_rot;
+    pa.lr_trans = opt->lr_trans;
+    pa.beta1 = opt->beta1;
+    pa.beta2 = opt->beta2;
+    pa.eps = opt->adam_eps;
+    pa.lr_final = opt->lr_final;
+    pa.iters = std::max(iters, 1);
+    pa.update = 1;
+
+    double headroom = 1.5;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        gsl::centroids(D.vps, D.set_vp, n_sets, cent, s);
+        gsl::pose_init(pa, s);
+        // size the duplicate lists at the initial poses (with headroom: the
+        // count drifts as the poses move)
+        int cur = 0;
+        uint32_t nd = 0;
+        GS_TRY(project_and_bin(ctx, P, D, p, pose32, opt, s, &cur, &nd));
+        const uint64_t want = (uint64_t)(headroom * nd) + 65536;
+        if (p.cap < want)
+            GS_TRY(alloc_sort(ctx, want, p));
+        gsl::BinArgs b = bin_args(P, D, p);
+        gsl::RasterArgs r = raster_args(P, D, p, 0, opt);
+        r.t_final = tf;
+        r.last = last;
+        r.code = code;
+        r.tile_loss = tloss;
+        r.tile_twist = ttw;
+        r.c_cam = ccam;
+        auto iteration = [&](cudaStream_t st) {
+            gsl::project(project_args(P, D, p, pose32, opt), st);
+            const int c = gsl::bin(b, st);
+            r.vals = p.vals[c];
+            gsl::forward(r, true, st);
+            gsl::backward(r, true, false, st);
+            gsl::pose_update(pa, st);
+        };
+        GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
+        if (iters > 0) {
+            GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+            iteration(ctx->cap);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
+            if (ce != cudaSuccess || !graph)
+                return fail(ctx, GS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+            cudaGraphExec_t exec = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess)
+                return fail(ctx, GS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+            cudaError_t le = cudaSuccess;
+            for (int it = 0; it < iters && le == cudaSuccess; ++it)
+                le = cudaGraphLaunch(exec, s);
+            cudaGraphExecDestroy(exec);
+            if (le != cudaSuccess)
+                return fail(ctx, GS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(le));
+        }
+        // residual eps at the final poses, then Eq. 7
+        gsl::project(project_args(P, D, p, pose32, opt), s);
+        r.vals = p.vals[gsl::bin(b, s)];
+        gsl::forward(r, true, s);
+        gsl::PoseArgs fa = pa;
+        fa.tile_twist = nullptr;
+        fa.update = 0;
+        gsl::pose_update(fa, s);
+        gsl::FuseArgs f{};
+        f.pose64 = pose64;
+        f.eps = lossd;
+        f.reverse = rev;
+        f.prob_first = pf;
+        f.prob_count = pc;
+        f.n_problems = 1;
+        f.T_out = Tdev;
+        f.conf = confd;
+        f.est_out = est;
+        gsl::fuse(f, s);
+        GS_CUDA(cudaGetLastError());
+        int flags = 0;
+        GS_TRY(read_flags(ctx, p, s, &flags));
+        if (flags & gsk::kFlagNonFinite)
+            return fail(ctx, GS_ERR_NONFINITE, "non-finite Gaussian parameter");
+        if (flags & gsk::kFlagCapacity) {
+            headroom *= 2.0;  // the lists outgrew the headroom: redo with more
+            continue;
+        }
+        std::vector<double> epsh(nv);
+        GS_CUDA(cudaMemcpyAsync(T_out, Tdev, 12 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(confidence, confd, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(epsh.data(), lossd, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (est_out)
+            GS_CUDA(cudaMemcpyAsync(est_out, est, 12 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaStreamSynchronize(s));
+        if (eps_out)
+            std::memcpy(eps_out, epsh.data(), nv * sizeof(double));
+        for (double e : epsh)
+            if (!std::isfinite(e))
+                return fail(ctx, GS_ERR_DIVERGED, "registration residual is not finite");
+        return GS_OK;
+    }
+    return fail(ctx, GS_ERR_CAPACITY, "tile duplicate lists kept outgrowing their capacity");
+}
+
+}  // extern "C"

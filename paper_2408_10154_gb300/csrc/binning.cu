@@ -1,0 +1,324 @@
+// binning.cu -- tile binning: exclusive scan of tiles-touched counts,
+// duplicate emission with 64-bit (tile << 32 | depth bits) keys, stable LSD
+// radix sort over the needed key bits, per-tile [start, end) ranges.
+//
+// All sizes that depend on the data (the number of duplicates) live on the
+// device, so the whole sequence can be captured in a CUDA graph: grids are
+// sized for the capacity and blocks past the live count exit early.
+// HBM-bound throughout: the sort moves 8 B key + 4 B value in and out per
+// duplicate per 8-bit pass.
+#include "gs_internal.cuh"
+
+namespace {
+
+using namespace gsk;
+
+// ---------------------------------------------------------------- scan
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(const uint32_t *in, size_t n, uint32_t *partials)
+{
+    __shared__ uint32_t s[kScanThreads / 32];
+    const size_t base = (size_t)blockIdx.x * kScanTile;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanTile / kScanThreads; ++k) {
+        const size_t i = base + (size_t)k * kScanThreads + threadIdx.x;
+        if (i < n)
+            acc += in[i];
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0)
+        s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < kScanThreads / 32 ? s[threadIdx.x] : 0u;
+        v = warp_sum(v);
+        if (threadIdx.x == 0)
+            partials[blockIdx.x] = v;
+    }
+}
+
+// single block: exclusive scan of the partials in place; total (uint64
+// saturated to 0xffffffff) to *total
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *partials, size_t np, uint32_t *total)
+{
+    __shared__ uint32_t s_warp[33];
+    __shared__ unsigned long long s_carry;
+    if (threadIdx.x == 0)
+        s_carry = 0;
+    __syncthreads();
+    for (size_t c = 0; c < np; c += 1024) {
+        const size_t i = c + threadIdx.x;
+        const uint32_t x = i < np ? partials[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan<1024>(x, s_warp, tot);
+        const unsigned long long carry = s_carry;
+        if (i < np) {
+            const unsigned long long v = carry + ex;
+            partials[i] = v > 0xffffffffull ? 0xffffffffu : (uint32_t)v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_carry = carry + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total)
+        *total = s_carry > 0xffffffffull ? 0xffffffffu : (uint32_t)s_carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in, size_t n, const uint32_t *partials,
+                                                            uint32_t *out)
+{
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    constexpr int K = kScanTile / kScanThreads;
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * K;  // blocked arrangement
+    uint32_t v[K];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        sum += v[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan<kScanThreads>(sum, s_warp, tot) + partials[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (base + k < n)
+            out[base + k] = ex;
+        ex += v[k];
+    }
+}
+
+// ---------------------------------------------------------------- emission
+// Block b owns records [b*kScanTile, (b+1)*kScanTile): it re-scans their
+// counts locally, then emits its duplicates dup-parallel (thread j handles
+// the block's j-th duplicate), so that a Gaussian touching many tiles does
+// not stall a warp.
+__global__ void __launch_bounds__(kScanThreads) k_emit(const gsl::BinArgs a, const uint32_t *blk_base)
+{
+    __shared__ uint32_t s_off[kScanTile + 1];
+    __shared__ uint32_t s_t0[kScanTile];   // global tile of the rect corner
+    __shared__ uint32_t s_geo[kScanTile];  // rect width | TX << 16
+    __shared__ uint32_t s_z[kScanTile];
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    __shared__ int s_vp[2];
+    constexpr int K = kScanTile / kScanThreads;
+    const uint32_t rbase = blockIdx.x * kScanTile;
+    if (threadIdx.x == 0) {
+        // vp of the first record of this block (records of a vp are contiguous)
+        int lo = 0, hi = a.n_vps - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.vps[mid].rec_base <= rbase) lo = mid; else hi = mid - 1;
+        }
+        s_vp[0] = lo;
+    }
+    __syncthreads();
+    uint32_t c[K];
+    uint32_t sum = 0;
+    const int first = threadIdx.x * K;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t r = rbase + first + k;
+        c[k] = r < a.n_records ? (uint32_t)a.counts[r] : 0u;
+        sum += c[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan<kScanThreads>(sum, s_warp, tot);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int lr = first + k;
+        const uint32_t r = rbase + lr;
+        s_off[lr] = ex;
+        ex += c[k];
+        if (c[k]) {
+            int vp = s_vp[0];
+            while (vp + 1 < a.n_vps && a.vps[vp + 1].rec_base <= r)
+                ++vp;
+            const VpDesc &d = a.vps[vp];
+            const float4 q1 = a.rec[3 * (size_t)r + 1];
+            const float4 q2 = a.rec[3 * (size_t)r + 2];
+            const uint32_t rx = __float_as_uint(q1.w), ry = __float_as_uint(q2.w);
+            const uint32_t x0 = rx & 0xffffu, x1 = rx >> 16, y0 = ry & 0xffffu;
+            s_t0[lr] = d.tile_base + y0 * (uint32_t)d.TX + x0;
+            s_geo[lr] = (x1 - x0) | ((uint32_t)d.TX << 16);
+            s_z[lr] = __float_as_uint(q1.z);
+        }
+    }
+    if (threadIdx.x == 0)
+        s_off[kScanTile] = tot;
+    __syncthreads();
+    const uint32_t gbase = blk_base[blockIdx.x];
+    for (uint32_t j = threadIdx.x; j < tot; j += blockDim.x) {
+        // last record with s_off <= j (upper bound - 1)
+        int lo = 0, hi = kScanTile - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t local = j - s_off[lo];
+        const uint32_t geo = s_geo[lo];
+        const uint32_t w = geo & 0xffffu, TX = geo >> 16;
+        const uint32_t tile = s_t0[lo] + (local / w) * TX + local % w;
+        const uint64_t pos = (uint64_t)gbase + j;
+        if (pos < a.capacity) {
+            a.keys[0][pos] = ((uint64_t)tile << 32) | s_z[lo];
+            a.vals[0][pos] = rbase + (uint32_t)lo;
+        }
+    }
+    if (threadIdx.x == 0 && (uint64_t)gbase + tot > a.capacity && tot > 0)
+        atomicOr(a.flags, kFlagCapacity);
+}
+
+// ---------------------------------------------------------------- radix sort
+__device__ __forceinline__ uint32_t live_count(const uint32_t *n_dups, uint32_t cap)
+{
+    const uint32_t n = *n_dups;
+    return n < cap ? n : cap;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint64_t *keys, const uint32_t *n_dups, uint32_t cap,
+                                                          int shift, uint32_t *hist, uint32_t nblk)
+{
+    __shared__ uint32_t h[kSortThreads / 32][256];
+    const int warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * 256; k += blockDim.x)
+        (&h[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t n = live_count(n_dups, cap);
+    const uint32_t base = blockIdx.x * kSortTile;
+#pragma unroll
+    for (int k = 0; k < kSortKPT; ++k) {
+        const uint32_t i = base + k * kSortThreads + threadIdx.x;
+        if (i < n)
+            atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w)
+        s += h[w][threadIdx.x];
+    hist[(size_t)threadIdx.x * nblk + blockIdx.x] = s;
+}
+
+// Stable scatter: warp w ranks the block's keys [w*256, w*256+256) in 8
+// rounds of 32 consecutive keys (match_any finds equal digits), so ranks
+// follow input order within the block; digit-major scanned histograms give
+// the block's base per digit.
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint64_t *kin, const uint32_t *vin,
+                                                             const uint32_t *n_dups, uint32_t cap, int shift,
+                                                             const uint32_t *hist_scanned, uint32_t nblk,
+                                                             uint64_t *kout, uint32_t *vout)
+{
+    __shared__ uint32_t cnt[kSortThreads / 32][256];
+    __shared__ uint32_t s_base[256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * 256; k += blockDim.x)
+        (&cnt[0][0])[k] = 0;
+    s_base[threadIdx.x] = hist_scanned[(size_t)threadIdx.x * nblk + blockIdx.x];
+    __syncthreads();
+    const uint32_t n = live_count(n_dups, cap);
+    const uint32_t base = blockIdx.x * kSortTile + warp * (32 * kSortKPT);
+    const unsigned lt = lanemask_lt();
+    uint64_t key[kSortKPT];
+    uint32_t val[kSortKPT], off[kSortKPT], dig[kSortKPT];
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : 0ull;
+        val[r] = valid ? vin[i] : 0u;
+        const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 0xffu : 256u;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
+        uint32_t o = 0;
+        if (valid)
+            o = cnt[warp][d] + rank;
+        off[r] = o;
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane)
+            cnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps for each digit (thread = digit)
+    {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const uint32_t c = cnt[w][threadIdx.x];
+            cnt[w][threadIdx.x] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        if (dig[r] < 256u) {
+            const uint32_t pos = s_base[dig[r]] + cnt[warp][dig[r]] + off[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- ranges
+__global__ void k_ranges(const uint64_t *keys, const uint32_t *n_dups, uint32_t cap, uint2 *ranges)
+{
+    const uint32_t n = live_count(n_dups, cap);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t)
+        ranges[t].x = i;
+    if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t)
+        ranges[t].y = i + 1;
+}
+
+inline uint32_t div_up(size_t a, size_t b) { return (uint32_t)((a + b - 1) / b); }
+
+}  // namespace
+
+namespace gsl {
+
+size_t scan_partials(size_t n) { return div_up(n, kScanTile) + 1; }
+
+size_t sort_hist_entries(uint32_t capacity) { return (size_t)256 * div_up(capacity ? capacity : 1, kSortTile); }
+
+void scan_excl(const uint32_t *in, uint32_t *out, size_t n, uint32_t *partials, uint32_t *total, cudaStream_t s)
+{
+    const uint32_t nb = div_up(n ? n : 1, kScanTile);
+    k_scan_partials<<<nb, kScanThreads, 0, s>>>(in, n, partials);
+    k_scan_top<<<1, 1024, 0, s>>>(partials, nb, total);
+    k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, n, partials, out);
+}
+
+void bin_count(const BinArgs &a, cudaStream_t s)
+{
+    const uint32_t nb = div_up(a.n_records ? a.n_records : 1, kScanTile);
+    k_scan_partials<<<nb, kScanThreads, 0, s>>>((const uint32_t *)a.counts, a.n_records, a.partials);
+    k_scan_top<<<1, 1024, 0, s>>>(a.partials, nb, a.n_dups);
+}
+
+int bin(const BinArgs &a, cudaStream_t s)
+{
+    bin_count(a, s);
+    const uint32_t nb = div_up(a.n_records ? a.n_records : 1, kScanTile);
+    k_emit<<<nb, kScanThreads, 0, s>>>(a, a.partials);
+    const uint32_t sb = div_up(a.capacity ? a.capacity : 1, kSortTile);
+    const size_t hn = (size_t)256 * sb;
+    int cur = 0;
+    for (int shift = 0; shift < a.key_bits; shift += 8) {
+        k_rs_hist<<<sb, kSortThreads, 0, s>>>(a.keys[cur], a.n_dups, a.capacity, shift, a.hist, sb);
+        scan_excl(a.hist, a.hist, hn, a.hist_partials, nullptr, s);
+        k_rs_scatter<<<sb, kSortThreads, 0, s>>>(a.keys[cur], a.vals[cur], a.n_dups, a.capacity, shift, a.hist, sb,
+                                                 a.keys[cur ^ 1], a.vals[cur ^ 1]);
+        cur ^= 1;
+    }
+    cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.n_tiles, s);
+    k_ranges<<<div_up(a.capacity ? a.capacity : 1, 256), 256, 0, s>>>(a.keys[cur], a.n_dups, a.capacity, a.ranges);
+    return cur;
+}
+
+}  // namespace gsl

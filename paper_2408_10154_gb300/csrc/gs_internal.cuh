@@ -1,0 +1,272 @@
+// gs_internal.cuh -- device-side data layout and helpers shared by the
+// kernels of libgsreg (sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsreg.h"
+
+namespace gsk {
+
+constexpr int kTile = GS_TILE;        // 16x16 pixels per tile, one CTA each
+constexpr int kTilePix = kTile * kTile;
+constexpr int kScanTile = 2048;       // items per block in scans and emission
+constexpr int kScanThreads = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortKPT = 8;           // keys per thread in a radix pass
+constexpr int kSortTile = kSortThreads * kSortKPT;
+constexpr int kMaxVpPerGroup = 64;    // keyframes sharing one projection pass
+
+// device status word bits
+enum : int { kFlagNonFinite = 1, kFlagCapacity = 2 };
+
+// One view-problem: a moving submap seen by one keyframe camera, with its
+// own pose, Adam state and (in registration) target images.
+struct VpDesc {
+    const float4 *means, *scales, *quats, *rgb;
+    const float *logits;
+    int n;                 // Gaussians of the moving submap
+    int W, H, TX, TY;      // image and tile grid
+    float fx, fy, cx, cy;
+    float w2c[12];         // world -> camera
+    uint32_t rec_base;     // first record index
+    uint32_t tile_base;    // first global tile id
+    int64_t pix_base;      // first pixel in concatenated per-pixel arrays
+    const float *t_rgb;    // registration targets [3][H][W] (or null)
+    const float *t_depth;  // [H][W]
+    int group;             // projection group
+    int set;               // Gaussian set (centroid slot)
+    int problem;           // registration problem (fusion)
+    int reverse;           // 1: keyframe of P localised in Q (estimate is inverted)
+};
+
+// A projection group: vps that share one Gaussian set and are projected by
+// the same thread per Gaussian.
+struct GroupDesc {
+    int vp_first, vp_count;
+    int n;
+    uint32_t blk_base;     // first block of this group in the projection grid
+};
+
+// ------------------------------------------------------------------------
+// FP32 decision arithmetic.  These helpers spell out every rounding step
+// (round-to-nearest, fused multiply-add only where written) so that every
+// integer outcome -- culls, tile rectangles, depth bits, skipped and
+// stopping contributors -- is reproducible bit for bit.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// e^x: Cody-Waite reduction k = round(x log2 e), r = x - k ln2 (two-part
+// ln2), degree-6 Taylor polynomial of e^r, exact scaling by 2^k; argument
+// clamped to [-80, 80].
+__device__ __forceinline__ float exp_ct(float x)
+{
+    x = fminf(fmaxf(x, -80.0f), 80.0f);
+    const float magic = 12582912.0f;  // 1.5 * 2^23
+    const float t = __fmaf_rn(x, 1.4426950408889634f, magic);
+    const float kf = __fsub_rn(t, magic);
+    float r = __fmaf_rn(kf, -0.693145751953125f, x);
+    r = __fmaf_rn(kf, -1.428606820309417e-06f, r);
+    float p = 1.3888888888888889e-03f;       // 1/720
+    p = __fmaf_rn(p, r, 8.3333333333333333e-03f);  // 1/120
+    p = __fmaf_rn(p, r, 4.1666666666666667e-02f);  // 1/24
+    p = __fmaf_rn(p, r, 1.6666666666666667e-01f);  // 1/6
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    const int k = __float2int_rz(kf);
+    return __fmul_rn(p, __int_as_float((k + 127) << 23));
+}
+
+// M = V o T (3x4 row-major) in FP32
+__device__ __forceinline__ void compose_ct(const float *V, const float *T, float *M)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float v0 = V[4 * i], v1 = V[4 * i + 1], v2 = V[4 * i + 2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            M[4 * i + j] = fma_rn(v2, T[8 + j], fma_rn(v1, T[4 + j], mul_rn(v0, T[j])));
+        M[4 * i + 3] = fma_rn(v2, T[11], fma_rn(v1, T[7], fma_rn(v0, T[3], V[4 * i + 3])));
+    }
+}
+
+// ------------------------------------------------------------------------
+// small utilities
+// ------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// exclusive block scan of one uint32 per thread (blockDim.x = BLOCK)
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp, uint32_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += y;
+    }
+    if (lane == 31)
+        s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < BLOCK / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o)
+                wi += y;
+        }
+        if (lane < BLOCK / 32)
+            s_warp[lane] = wi - w;
+        if (lane == BLOCK / 32 - 1)
+            s_warp[BLOCK / 32] = wi;
+    }
+    __syncthreads();
+    total = s_warp[BLOCK / 32];
+    const uint32_t r = s_warp[warp] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace gsk
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files; all enqueue on `s`)
+// ---------------------------------------------------------------------------
+namespace gsl {
+
+struct ProjectArgs {
+    const gsk::VpDesc *vps;
+    const gsk::GroupDesc *groups;
+    int n_groups;
+    uint32_t n_blocks;
+    const float *pose32;      // [vp][12]
+    float z_near, dilation;
+    int smooth;
+    float4 *rec;               // [records][3] main record (AoS, 48 B)
+    float4 *aux;               // [records][2] auxiliary (may be null)
+    int32_t *counts;
+    int *flags;
+};
+void project(const ProjectArgs &a, cudaStream_t s);
+
+// exclusive scan of n uint32 (n host-known); partials sized scan_partials(n)
+size_t scan_partials(size_t n);
+void scan_excl(const uint32_t *in, uint32_t *out, size_t n, uint32_t *partials, uint32_t *total,
+               cudaStream_t s);
+
+struct BinArgs {
+    const gsk::VpDesc *vps;
+    int n_vps;
+    const int32_t *counts;
+    const float4 *rec;         // [records][3]
+    uint32_t n_records;
+    uint32_t *partials;       // scan_partials(n_records)
+    uint32_t *n_dups;         // device scalar out (may exceed capacity)
+    uint64_t *keys[2];
+    uint32_t *vals[2];
+    uint32_t capacity;
+    uint32_t *hist;           // 256 * sort blocks(capacity)
+    uint32_t *hist_partials;  // scan_partials(256 * sort blocks)
+    int key_bits;             // bits of (tile << 32 | depth) to sort
+    uint2 *ranges;            // [total tiles]
+    uint32_t n_tiles;
+    int *flags;
+};
+// emits, sorts and ranges; returns which buffer holds the sorted result
+int bin(const BinArgs &a, cudaStream_t s);
+void bin_count(const BinArgs &a, cudaStream_t s);  // scan only: n_dups
+size_t sort_hist_entries(uint32_t capacity);
+
+struct RasterArgs {
+    const gsk::VpDesc *vps;
+    const uint32_t *tile_vp;  // [tiles] vp of each tile
+    uint32_t n_tiles;
+    const uint2 *ranges;
+    const uint32_t *vals;
+    const float4 *rec;        // [records][3]
+    const float4 *aux;        // [records][2]
+    float alpha_min, alpha_max, t_min, skip_below;
+    float bg[3];
+    // per-pixel state
+    float *t_final;
+    int32_t *last;
+    uint8_t *code;            // registration: sign code of the loss gradient
+    // render outputs (render mode)
+    float *out_rgb, *out_depth, *out_alpha;
+    // cotangents (backward, render mode)
+    const float *d_rgb, *d_depth, *d_alpha;
+    // registration / backward outputs
+    float *tile_loss;         // [tiles]
+    double *tile_twist;       // [tiles][6], camera frame
+    const double *c_cam;      // [vp][3] pivot in camera frame
+    float *dup_grads;         // [dups][10] screen-space partials (full mode)
+};
+void forward(const RasterArgs &a, bool registration, cudaStream_t s);
+void raster_init();  // one-time kernel attributes (before any graph capture)
+void backward(const RasterArgs &a, bool registration, bool full, cudaStream_t s);
+
+struct PoseArgs {
+    const gsk::VpDesc *vps;
+    int n_vps;
+    const double *tile_twist;  // [tiles][6]
+    const float *tile_loss;    // [tiles]
+    double *pose64;            // [vp][12]
+    float *pose32;             // [vp][12]
+    double *adam;              // [vp][13]
+    double *pivot;             // [vp][3] world
+    double *c_cam;             // [vp][3]
+    const double *centroid;    // [set][3]
+    double *loss;              // [vp] last loss
+    double *grad;              // [vp][6] last world gradient (may be null)
+    float lr_rot, lr_trans, beta1, beta2, eps, lr_final;
+    int iters;
+    int update;                // 0: only reduce loss / gradient
+};
+void pose_update(const PoseArgs &a, cudaStream_t s);
+void pose_init(const PoseArgs &a, cudaStream_t s);
+void centroids(const gsk::VpDesc *vps, const int *set_vp, int n_sets, double *centroid, cudaStream_t s);
+
+struct FuseArgs {
+    const double *pose64;      // [vp][12]
+    const double *eps;         // [vp]
+    const int32_t *reverse;    // [vp]
+    const int32_t *prob_first, *prob_count;  // [problems]
+    int n_problems;
+    double *T_out;             // [problems][12]
+    double *conf;              // [problems]
+    double *est_out;           // [vp][12] estimates of T_{P->Q} (may be null)
+};
+void fuse(const FuseArgs &a, cudaStream_t s);
+
+void pose_step_raw(int n, double *pose, double *state, const double *grad, const double *pivot, int k, int iters,
+                   float lr_rot, float lr_trans, float b1, float b2, float eps, float lr_final, cudaStream_t s);
+void loss(const gsk::VpDesc *vps, int n_vps, uint32_t n_tiles, const uint32_t *tile_vp, const float *rgb,
+          const float *depth, double *loss, float *d_rgb, float *d_depth, float *tile_loss, cudaStream_t s);
+void transform(const float4 *means, const float4 *quats, int64_t n, const double *T, float4 *out_means,
+               float4 *out_quats, cudaStream_t s);
+
+
+}  // namespace gsl

@@ -1,0 +1,427 @@
+// raster.cu -- front-to-back compositing (forward) and back-to-front adjoint
+// (backward) of the tiled 3D Gaussian splatting renderer.
+//
+// One CTA of 256 threads per 16x16 tile; each warp owns an 8x4 pixel patch.
+// The tile's depth-sorted list is staged through shared memory 256 records
+// (48 B each) at a time; the forward stops early once every pixel of the
+// tile is opaque (transmittance would drop below t_min).
+//
+// Forward (registration mode) fuses the loss: it reads the keyframe's
+// colour and depth, accumulates the L1 loss of the tile and stores a 1-byte
+// sign code of dL/dpixel next to the final transmittance and the
+// last-contributor index.  Nothing else per pixel is saved; the backward
+// recomputes alpha and recovers transmittance by division.
+//
+// Backward: per (pixel, Gaussian) screen-space gradients are summed over
+// each warp with shuffles, over the tile's 8 warps in shared memory (fixed
+// order), chained through the projection into a camera-frame twist per
+// Gaussian, accumulated in FP64 per thread and reduced to one 6-vector per
+// tile by a block tree -- no global atomics, bit-reproducible.
+#include <float.h>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+using namespace gsk;
+
+struct PixelCoord {
+    int px, py;
+    bool inside;
+};
+
+__device__ __forceinline__ PixelCoord pixel_of(const VpDesc &d, uint32_t t)
+{
+    const uint32_t lt = t - d.tile_base;
+    const int tx = (int)(lt % (uint32_t)d.TX), ty = (int)(lt / (uint32_t)d.TX);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    PixelCoord p;
+    p.px = tx * kTile + (warp & 1) * 8 + (lane & 7);
+    p.py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    p.inside = p.px < d.W && p.py < d.H;
+    return p;
+}
+
+// exponent of record (q0 = u, v, ca, cb; cc) at the pixel sample (FP32 contract)
+__device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float pxf, float pyf, float &dx, float &dy)
+{
+    dx = sub_rn(q0.x, pxf);
+    dy = sub_rn(q0.y, pyf);
+    const float h = fma_rn(q0.z, dx, mul_rn(q0.w, dy));
+    const float k = mul_rn(mul_rn(cc, dy), dy);
+    return fma_rn(h, dx, k);
+}
+
+template <bool REG>
+__global__ void __launch_bounds__(256) k_forward(const gsl::RasterArgs a)
+{
+    __shared__ float4 s0[256], s1[256], s2[256];
+    __shared__ float s_red[8];
+    const uint32_t t = blockIdx.x;
+    const VpDesc &d = a.vps[a.tile_vp[t]];
+    const PixelCoord p = pixel_of(d, t);
+    const float pxf = (float)p.px + 0.5f, pyf = (float)p.py + 0.5f;
+    const uint2 rg = a.ranges[t];
+    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    int last = 0;
+    bool done = !p.inside;
+    for (uint32_t b = rg.x; b < rg.y; b += 256) {
+        if (__syncthreads_count(done) == 256)
+            break;
+        const uint32_t idx = b + threadIdx.x;
+        if (idx < rg.y) {
+            const float4 *R = a.rec + 3 * (size_t)a.vals[idx];
+            s0[threadIdx.x] = R[0];
+            s1[threadIdx.x] = R[1];
+            s2[threadIdx.x] = R[2];
+        }
+        __syncthreads();
+        const int cnt = (int)min(256u, rg.y - b);
+        if (!done) {
+            for (int j = 0; j < cnt; ++j) {
+                const float4 q0 = s0[j];
+                const float4 q1 = s1[j];
+                float dx, dy;
+                const float power = exponent_at(q0, q1.x, pxf, pyf, dx, dy);
+                if (power > 0.0f || power < a.skip_below)
+                    continue;
+                const float x = mul_rn(q1.y, exp_ct(power));
+                const float alpha = x > a.alpha_max ? a.alpha_max : x;
+                if (alpha < a.alpha_min)
+                    continue;
+                const float Tn = mul_rn(T, sub_rn(1.0f, alpha));
+                if (Tn < a.t_min) {
+                    done = true;
+                    break;
+                }
+                const float w = alpha * T;
+                const float4 q2 = s2[j];
+                C0 = fmaf(q2.x, w, C0);
+                C1 = fmaf(q2.y, w, C1);
+                C2 = fmaf(q2.z, w, C2);
+                D = fmaf(q1.z, w, D);
+                T = Tn;
+                last = (int)(b - rg.x) + j + 1;
+            }
+        }
+    }
+    const int64_t HW = (int64_t)d.W * d.H;
+    const int64_t off = (int64_t)p.py * d.W + p.px;
+    const int64_t pix = d.pix_base + off;
+    const float o0 = fmaf(T, a.bg[0], C0), o1 = fmaf(T, a.bg[1], C1), o2 = fmaf(T, a.bg[2], C2);
+    if (!REG) {
+        if (p.inside) {
+            if (a.out_rgb) {
+                float *rgb = a.out_rgb + 3 * d.pix_base;
+                rgb[off] = o0;
+                rgb[HW + off] = o1;
+                rgb[2 * HW + off] = o2;
+            }
+            if (a.out_depth)
+                a.out_depth[pix] = D;
+            if (a.out_alpha)
+                a.out_alpha[pix] = 1.0f - T;
+            if (a.t_final)
+                a.t_final[pix] = T;
+            if (a.last)
+                a.last[pix] = last;
+        }
+        return;
+    }
+    // registration: fused L1 colour + L1 depth loss and its sign code
+    float lsum = 0.0f;
+    if (p.inside) {
+        const float e0 = o0 - d.t_rgb[off], e1 = o1 - d.t_rgb[HW + off], e2 = o2 - d.t_rgb[2 * HW + off];
+        const float ed = D - d.t_depth[off];
+        const float inv3 = 1.0f / (3.0f * (float)HW), inv1 = 1.0f / (float)HW;
+        lsum = (fabsf(e0) + fabsf(e1) + fabsf(e2)) * inv3 + fabsf(ed) * inv1;
+        auto sg = [](float e) -> uint32_t { return e > 0.0f ? 1u : (e < 0.0f ? 2u : 0u); };
+        a.code[pix] = (uint8_t)(sg(e0) | (sg(e1) << 2) | (sg(e2) << 4) | (sg(ed) << 6));
+        a.t_final[pix] = T;
+        a.last[pix] = last;
+    }
+    lsum = warp_sum(lsum);
+    if ((threadIdx.x & 31) == 0)
+        s_red[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+            s += s_red[w];
+        a.tile_loss[t] = s;
+    }
+}
+
+// d(screen params) of one (tile, Gaussian) -> camera-frame twist (w, v)
+// about c_cam, added to tw[6].  G = {du, dv, dca, dcb, dcc, dz, ...}.
+__device__ __forceinline__ void chain_twist(const float *G, const float4 &q0, const float4 &q1, const float4 &x0,
+                                            const float4 &x1, float fx, float fy, const double *cc, double *tw)
+{
+    const float mx = x0.x, my = x0.y, mz = q1.z;
+    const float S00 = x0.z, S01 = x0.w, S02 = x1.x, S11 = x1.y, S12 = x1.z, S22 = x1.w;
+    // conic Q = [[A, B], [B, C]]: exponent = -(A dx^2 + 2 B dx dy + C dy^2)/2
+    const float A = -2.0f * q0.z, B = -q0.w, Cc = -2.0f * q1.x;
+    const float dA = -0.5f * G[2], dBh = -0.5f * G[3], dC = -0.5f * G[4];  // dBh = (dL/dB)/2
+    // dL/dSigma2D = -Q G_Q Q with G_Q = [[dA, dBh], [dBh, dC]]
+    const float t00 = A * dA + B * dBh, t01 = A * dBh + B * dC;
+    const float t10 = B * dA + Cc * dBh, t11 = B * dBh + Cc * dC;
+    const float gp = -(t00 * A + t01 * B), gq = -(t00 * B + t01 * Cc), gs = -(t10 * B + t11 * Cc);
+    const float iz = 1.0f / mz, iz2 = iz * iz;
+    const float j00 = fx * iz, j11 = fy * iz, j02 = -fx * mx * iz2, j12 = -fy * my * iz2;
+    // G2 J (2x3)
+    const float r00 = gp * j00, r01 = gq * j11, r02 = gp * j02 + gq * j12;
+    const float r10 = gq * j00, r11 = gs * j11, r12 = gq * j02 + gs * j12;
+    // dL/dSigma_cam = J^T G2 J
+    const float c00 = j00 * r00, c01 = j00 * r01, c02 = j00 * r02;
+    const float c11 = j11 * r11, c12 = j11 * r12, c22 = j02 * r02 + j12 * r12;
+    // dL/dJ = 2 G2 J Sigma_cam (entries used)
+    const float dJ00 = 2.0f * (r00 * S00 + r01 * S01 + r02 * S02);
+    const float dJ02 = 2.0f * (r00 * S02 + r01 * S12 + r02 * S22);
+    const float dJ11 = 2.0f * (r10 * S01 + r11 * S11 + r12 * S12);
+    const float dJ12 = 2.0f * (r10 * S02 + r11 * S12 + r12 * S22);
+    const float du = G[0], dv = G[1], dz = G[5];
+    const float gx = du * fx * iz - dJ02 * fx * iz2;
+    const float gy = dv * fy * iz - dJ12 * fy * iz2;
+    const float gz = -du * fx * mx * iz2 - dv * fy * my * iz2 + dz - dJ00 * fx * iz2 - dJ11 * fy * iz2 +
+                     2.0f * iz2 * iz * (dJ02 * fx * mx + dJ12 * fy * my);
+    // 2 vee(Gc S - S Gc)
+    const float k21 = (c02 * S01 + c12 * S11 + c22 * S12) - (S02 * c01 + S12 * c11 + S22 * c12);
+    const float k02 = (c00 * S02 + c01 * S12 + c02 * S22) - (S00 * c02 + S01 * c12 + S02 * c22);
+    const float k10 = (c01 * S00 + c11 * S01 + c12 * S02) - (S01 * c00 + S11 * c01 + S12 * c02);
+    const float rx = (float)(mx - cc[0]), ry = (float)(my - cc[1]), rz = (float)(mz - cc[2]);
+    tw[0] += (double)(ry * gz - rz * gy + 2.0f * k21);
+    tw[1] += (double)(rz * gx - rx * gz + 2.0f * k02);
+    tw[2] += (double)(rx * gy - ry * gx + 2.0f * k10);
+    tw[3] += (double)gx;
+    tw[4] += (double)gy;
+    tw[5] += (double)gz;
+}
+
+template <bool REG, bool FULL>
+__global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
+{
+    constexpr int NG = FULL ? 10 : 6;
+    extern __shared__ float s_slots[];  // [NG][8 warps][256]
+    __shared__ float4 s0[256], s1[256], s2[256];
+    __shared__ uint32_t s_rec[256];
+    __shared__ int s_maxl[8];
+    __shared__ double s_tw[8][6];
+    const uint32_t t = blockIdx.x;
+    const int vp = (int)a.tile_vp[t];
+    const VpDesc &d = a.vps[vp];
+    const PixelCoord p = pixel_of(d, t);
+    const float pxf = (float)p.px + 0.5f, pyf = (float)p.py + 0.5f;
+    const uint2 rg = a.ranges[t];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t HW = (int64_t)d.W * d.H;
+    const int64_t off = (int64_t)p.py * d.W + p.px;
+    const int64_t pix = d.pix_base + off;
+    float Tf = 1.0f, gr = 0.f, gg = 0.f, gb = 0.f, gd = 0.f, ga = 0.f;
+    int last = 0;
+    if (p.inside) {
+        Tf = a.t_final[pix];
+        last = a.last[pix];
+        if (REG) {
+            const uint32_t c = a.code[pix];
+            auto dec = [](uint32_t v) -> float { return v == 1u ? 1.0f : (v == 2u ? -1.0f : 0.0f); };
+            const float inv3 = 1.0f / (3.0f * (float)HW), inv1 = 1.0f / (float)HW;
+            gr = dec(c & 3u) * inv3;
+            gg = dec((c >> 2) & 3u) * inv3;
+            gb = dec((c >> 4) & 3u) * inv3;
+            gd = dec((c >> 6) & 3u) * inv1;
+        } else {
+            if (a.d_rgb) {
+                const float *dr = a.d_rgb + 3 * d.pix_base;
+                gr = dr[off];
+                gg = dr[HW + off];
+                gb = dr[2 * HW + off];
+            }
+            if (a.d_depth)
+                gd = a.d_depth[pix];
+            if (a.d_alpha)
+                ga = a.d_alpha[pix];
+        }
+    }
+    // longest list prefix any pixel of the tile used
+    int ml = last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        ml = max(ml, __shfl_xor_sync(0xffffffffu, ml, o));
+    if (lane == 0)
+        s_maxl[warp] = ml;
+    __syncthreads();
+    int maxl = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+        maxl = max(maxl, s_maxl[w]);
+
+    const double cc[3] = {a.c_cam ? a.c_cam[3 * vp] : 0.0, a.c_cam ? a.c_cam[3 * vp + 1] : 0.0,
+                          a.c_cam ? a.c_cam[3 * vp + 2] : 0.0};
+    double tw[6] = {0, 0, 0, 0, 0, 0};
+    float T = Tf, Rr = a.bg[0], Rg = a.bg[1], Rb = a.bg[2], Rd = 0.0f;
+    const float ga_tf = ga * Tf;
+    for (int hi = maxl; hi > 0; hi -= 256) {
+        const int lo = max(hi - 256, 0), cnt = hi - lo;
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            const uint32_t r = a.vals[rg.x + lo + threadIdx.x];
+            s_rec[threadIdx.x] = r;
+            const float4 *R = a.rec + 3 * (size_t)r;
+            s0[threadIdx.x] = R[0];
+            s1[threadIdx.x] = R[1];
+            s2[threadIdx.x] = R[2];
+        }
+        for (int k = threadIdx.x; k < NG * 8 * 256; k += 256)
+            s_slots[k] = 0.0f;
+        __syncthreads();
+        for (int j = cnt - 1; j >= 0; --j) {
+            float g[NG];
+#pragma unroll
+            for (int k = 0; k < NG; ++k)
+                g[k] = 0.0f;
+            bool contrib = false;
+            if (lo + j < last) {
+                const float4 q0 = s0[j];
+                const float4 q1 = s1[j];
+                float dx, dy;
+                const float power = exponent_at(q0, q1.x, pxf, pyf, dx, dy);
+                if (!(power > 0.0f) && !(power < a.skip_below)) {
+                    const float e = exp_ct(power);
+                    const float x = mul_rn(q1.y, e);
+                    const bool clamped = x > a.alpha_max;
+                    const float alpha = clamped ? a.alpha_max : x;
+                    if (alpha >= a.alpha_min) {
+                        contrib = true;
+                        const float om = 1.0f - alpha;
+                        const float Ti = __fdividef(T, om);
+                        const float4 q2 = s2[j];
+                        const float dal = Ti * (gr * (q2.x - Rr) + gg * (q2.y - Rg) + gb * (q2.z - Rb) +
+                                                gd * (q1.z - Rd)) +
+                                          __fdividef(ga_tf, om);
+                        Rr = fmaf(alpha, q2.x, om * Rr);
+                        Rg = fmaf(alpha, q2.y, om * Rg);
+                        Rb = fmaf(alpha, q2.z, om * Rb);
+                        Rd = fmaf(alpha, q1.z, om * Rd);
+                        const float wgt = alpha * Ti;
+                        g[5] = gd * wgt;
+                        if (FULL) {
+                            g[7] = gr * wgt;
+                            g[8] = gg * wgt;
+                            g[9] = gb * wgt;
+                        }
+                        if (!clamped) {
+                            const float dp = dal * alpha;
+                            g[0] = dp * (2.0f * q0.z * dx + q0.w * dy);
+                            g[1] = dp * (q0.w * dx + 2.0f * q1.x * dy);
+                            g[2] = dp * dx * dx;
+                            g[3] = dp * dx * dy;
+                            g[4] = dp * dy * dy;
+                            if (FULL)
+                                g[6] = dal * e;
+                        }
+                        T = Ti;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int k = 0; k < NG; ++k) {
+                    const float v = warp_sum(g[k]);
+                    if (lane == 0)
+                        s_slots[(k * 8 + warp) * 256 + j] = v;
+                }
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            float G[NG];
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+                float s = 0.0f;
+#pragma unroll
+                for (int w = 0; w < 8; ++w)
+                    s += s_slots[(k * 8 + w) * 256 + threadIdx.x];
+                G[k] = s;
+                any |= s != 0.0f;
+            }
+            const uint32_t r = s_rec[threadIdx.x];
+            if (FULL) {
+                float *dst = a.dup_grads + (size_t)(rg.x + lo + threadIdx.x) * 10;
+#pragma unroll
+                for (int k = 0; k < NG; ++k)
+                    dst[k] = G[k];
+            }
+            if (any && a.tile_twist)
+                chain_twist(G, s0[threadIdx.x], s1[threadIdx.x], a.aux[2 * (size_t)r], a.aux[2 * (size_t)r + 1], d.fx,
+                            d.fy, cc, tw);
+        }
+    }
+    if (!a.tile_twist)
+        return;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double v = warp_sum(tw[k]);
+        if (lane == 0)
+            s_tw[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+            s += s_tw[w][threadIdx.x];
+        a.tile_twist[(size_t)t * 6 + threadIdx.x] = s;
+    }
+}
+
+template <bool REG, bool FULL>
+constexpr size_t bwd_smem()
+{
+    return (size_t)(FULL ? 10 : 6) * 8 * 256 * sizeof(float);
+}
+
+template <bool REG, bool FULL>
+void launch_backward(const gsl::RasterArgs &a, cudaStream_t s)
+{
+    k_backward<REG, FULL><<<a.n_tiles, 256, bwd_smem<REG, FULL>(), s>>>(a);
+}
+
+}  // namespace
+
+namespace gsl {
+
+void raster_init()
+{
+    cudaFuncSetAttribute(k_backward<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_smem<true, false>());
+    cudaFuncSetAttribute(k_backward<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_smem<false, false>());
+    cudaFuncSetAttribute(k_backward<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_smem<false, true>());
+}
+
+void forward(const RasterArgs &a, bool registration, cudaStream_t s)
+{
+    if (a.n_tiles == 0)
+        return;
+    if (registration)
+        k_forward<true><<<a.n_tiles, 256, 0, s>>>(a);
+    else
+        k_forward<false><<<a.n_tiles, 256, 0, s>>>(a);
+}
+
+void backward(const RasterArgs &a, bool registration, bool full, cudaStream_t s)
+{
+    if (a.n_tiles == 0)
+        return;
+    if (registration)
+        launch_backward<true, false>(a, s);
+    else if (full)
+        launch_backward<false, true>(a, s);
+    else
+        launch_backward<false, false>(a, s);
+}
+
+}  // namespace gsl

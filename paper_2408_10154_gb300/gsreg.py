@@ -1,0 +1,348 @@
+"""Python binding of libgsreg.so (include/gsreg.h): ctypes argument
+marshalling only.  Every step of the path runs in the CUDA library; PyTorch
+supplies device memory (CUDA tensors) and the current stream.  There is no
+CPU fallback: if the compiled library cannot be loaded, every call raises.
+
+The functions carry the C names (gs_project, gs_bin, gs_render,
+gs_render_backward, gs_loss, gs_pose_step, gs_fuse, gs_register,
+gs_transform) and take tensors in the C-ABI layouts.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+GS_TILE = 16
+GS_RECORD_FLOATS = 12
+GS_AUX_FLOATS = 8
+
+STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_OOM", 3: "GS_ERR_CUDA", 4: "GS_ERR_NONFINITE",
+          5: "GS_ERR_TIMEOUT", 6: "GS_ERR_DIVERGED", 7: "GS_ERR_CAPACITY"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gs_gaussians_t(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("rgb", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class gs_camera_t(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("world_to_cam", ctypes.c_float * 12)]
+
+
+class gs_view_t(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("cam", gs_camera_t)]
+
+
+class gs_options_t(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("z_near", ctypes.c_float), ("dilation", ctypes.c_float),
+                ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
+                ("bg", ctypes.c_float * 3), ("smooth", ctypes.c_int32), ("lr_rot", ctypes.c_float),
+                ("lr_trans", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("adam_eps", ctypes.c_float), ("lr_final", ctypes.c_float)]
+
+
+class gs_gaussian_grads_t(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("rgb", ctypes.c_void_p)]
+
+
+EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_project",
+           "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step", "gs_fuse", "gs_register",
+           "gs_transform"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads the compiled library (building it first if asked and absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libgsreg.so not built ({path}); run __graft_entry__.build()")
+            _build.build()
+        L = ctypes.CDLL(path)
+        P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        sig = {
+            "gs_default_options": ([P], None),
+            "gs_ctx_create": ([I, ctypes.c_size_t, P], I),
+            "gs_ctx_destroy": ([P], I),
+            "gs_last_error": ([P], ctypes.c_char_p),
+            "gs_ctx_bytes": ([P], ctypes.c_size_t),
+            "gs_project": ([P, P, P, P, I, P, P, P, P, P], I),
+            "gs_bin": ([P, P, P, P, I, I64, P, P, I64, P, P, P], I),
+            "gs_render": ([P, P, P, P, I, P, P, P, P, P, P, P], I),
+            "gs_render_backward": ([P, P, P, P, I, P, P, P, P, P, P, P, P, P, P], I),
+            "gs_loss": ([P, P, I, P, P, P, P, P, P, P, P], I),
+            "gs_pose_step": ([P, I, P, P, P, P, I, I, P, P], I),
+            "gs_fuse": ([P, I, P, P, P, P, P, P], I),
+            "gs_register": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P], I),
+            "gs_transform": ([P, P, P, P, P, P], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("device tensor expected")
+        if not t.is_contiguous():
+            raise ValueError("contiguous tensor expected")
+        return ctypes.c_void_p(t.data_ptr())
+    return t
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_options(**kw) -> gs_options_t:
+    o = gs_options_t()
+    load().gs_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "bg":
+            o.bg = (ctypes.c_float * 3)(*v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def camera(cam18) -> gs_camera_t:
+    c = np.asarray(cam18, np.float32).reshape(18)
+    out = gs_camera_t(float(c[0]), float(c[1]), float(c[2]), float(c[3]), int(c[4]), int(c[5]))
+    out.world_to_cam = (ctypes.c_float * 12)(*[float(v) for v in c[6:]])
+    return out
+
+
+def cameras(cams):
+    cams = np.asarray(cams, np.float32).reshape(-1, 18)
+    arr = (gs_camera_t * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k] = camera(c)
+    return arr, len(cams)
+
+
+@dataclass
+class Gaussians:
+    """Device submap in the C-ABI layout (float32, float4-padded SoA)."""
+    means4: torch.Tensor
+    log_scales4: torch.Tensor
+    quats4: torch.Tensor
+    logits: torch.Tensor
+    rgb4: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.means4.shape[0])
+
+    @classmethod
+    def from_numpy(cls, d, device="cuda"):
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(device)
+        return cls(f(d["means4"]), f(d["log_scales4"]), f(d["quats4"]), f(d["logits"]), f(d["rgb4"]))
+
+    def c_struct(self) -> gs_gaussians_t:
+        return gs_gaussians_t(self.means4.data_ptr(), self.log_scales4.data_ptr(), self.quats4.data_ptr(),
+                              self.logits.data_ptr(), self.rgb4.data_ptr(), self.n)
+
+
+class Context:
+    """A gs_ctx_t: scratch arena of at most ``budget_bytes`` on ``device``."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        st = self._lib.gs_ctx_create(int(device), int(budget_bytes), ctypes.byref(self._h))
+        if st != 0:
+            raise GsError(st, "gs_ctx_create failed")
+        self.device = device
+
+    def check(self, st):
+        if st != 0:
+            raise GsError(st, self._lib.gs_last_error(self._h).decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bytes(self) -> int:
+        return int(self._lib.gs_ctx_bytes(self._h))
+
+    def close(self):
+        if self._h:
+            self._lib.gs_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _npix(cams):
+    c = np.asarray(cams, np.float32).reshape(-1, 18)
+    return int(sum(int(x[4]) * int(x[5]) for x in c))
+
+
+def gs_project(ctx: Context, g: Gaussians, poses: torch.Tensor, cams, opt=None, with_aux=True):
+    cam_arr, nc = cameras(cams)
+    opt = opt or default_options()
+    dev = g.means4.device
+    records = torch.empty((nc * g.n, GS_RECORD_FLOATS), dtype=torch.float32, device=dev)
+    aux = torch.empty((nc * g.n, GS_AUX_FLOATS), dtype=torch.float32, device=dev) if with_aux else None
+    counts = torch.empty(nc * g.n, dtype=torch.int32, device=dev)
+    gst = g.c_struct()
+    ctx.check(ctx._lib.gs_project(ctx.handle, ctypes.byref(gst), _ptr(poses.contiguous()), cam_arr, nc,
+                                  ctypes.byref(opt), _ptr(records), _ptr(aux), _ptr(counts), _stream()))
+    return records, aux, counts
+
+
+def gs_bin(ctx: Context, records, counts, cams, n, capacity=None):
+    cam_arr, nc = cameras(cams)
+    tiles = sum(((int(c[4]) + 15) // 16) * ((int(c[5]) + 15) // 16) for c in np.asarray(cams).reshape(-1, 18))
+    dev = records.device
+    ranges = torch.zeros((max(tiles, 1), 2), dtype=torch.int32, device=dev)
+    nd = ctypes.c_int64(0)
+    if capacity is None:
+        capacity = int(counts.to(torch.int64).sum().item())
+    keys = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
+    vals = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    ctx.check(ctx._lib.gs_bin(ctx.handle, _ptr(records), _ptr(counts), cam_arr, nc, int(n), _ptr(keys), _ptr(vals),
+                              int(capacity), _ptr(ranges), ctypes.byref(nd), _stream()))
+    return keys[: nd.value], vals[: nd.value], ranges[:tiles]
+
+
+def gs_render(ctx: Context, g: Gaussians, poses: torch.Tensor, cams, opt=None):
+    cam_arr, nc = cameras(cams)
+    opt = opt or default_options()
+    npx = _npix(cams)
+    dev = g.means4.device
+    out = dict(rgb=torch.empty(3 * npx, device=dev), depth=torch.empty(npx, device=dev),
+               alpha=torch.empty(npx, device=dev), t_final=torch.empty(npx, device=dev),
+               last=torch.empty(npx, dtype=torch.int32, device=dev))
+    gst = g.c_struct()
+    ctx.check(ctx._lib.gs_render(ctx.handle, ctypes.byref(gst), _ptr(poses.contiguous()), cam_arr, nc,
+                                 ctypes.byref(opt), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]),
+                                 _ptr(out["t_final"]), _ptr(out["last"]), _stream()))
+    return out
+
+
+def split_views(flat, cams, channels):
+    """Splits a concatenated per-camera buffer into [channels, H, W] views."""
+    out, o = [], 0
+    for c in np.asarray(cams).reshape(-1, 18):
+        W, H = int(c[4]), int(c[5])
+        out.append(flat[o: o + channels * H * W].view(channels, H, W) if channels > 1
+                   else flat[o: o + H * W].view(H, W))
+        o += channels * H * W
+    return out
+
+
+def gs_render_backward(ctx: Context, g: Gaussians, poses, cams, t_final, last, d_rgb=None, d_depth=None,
+                       d_alpha=None, pivots=None, opt=None):
+    cam_arr, nc = cameras(cams)
+    opt = opt or default_options()
+    dev = g.means4.device
+    pose_grad = torch.empty((nc, 6), dtype=torch.float32, device=dev)
+    gst = g.c_struct()
+    ctx.check(ctx._lib.gs_render_backward(ctx.handle, ctypes.byref(gst), _ptr(poses.contiguous()), cam_arr, nc,
+                                          ctypes.byref(opt), _ptr(t_final), _ptr(last), _ptr(d_rgb),
+                                          _ptr(d_depth), _ptr(d_alpha), _ptr(pivots), _ptr(pose_grad), None,
+                                          _stream()))
+    return pose_grad
+
+
+def gs_loss(ctx: Context, cams, rgb, depth, t_rgb, t_depth):
+    cam_arr, nc = cameras(cams)
+    dev = rgb.device
+    loss = torch.empty(nc, dtype=torch.float64, device=dev)
+    d_rgb = torch.empty_like(rgb)
+    d_depth = torch.empty_like(depth)
+    ctx.check(ctx._lib.gs_loss(ctx.handle, cam_arr, nc, _ptr(rgb), _ptr(depth), _ptr(t_rgb), _ptr(t_depth),
+                               _ptr(loss), _ptr(d_rgb), _ptr(d_depth), _stream()))
+    return loss, d_rgb, d_depth
+
+
+def gs_pose_step(ctx: Context, pose, state, grad, pivot, k, iters, opt=None):
+    """In place on ``pose`` [n,12] and ``state`` [n,13] (float64 CUDA)."""
+    opt = opt or default_options()
+    ctx.check(ctx._lib.gs_pose_step(ctx.handle, int(pose.shape[0]), _ptr(pose), _ptr(state), _ptr(grad),
+                                    _ptr(pivot), int(k), int(iters), ctypes.byref(opt), _stream()))
+
+
+def gs_fuse(ctx: Context, est, reverse, eps):
+    dev = est.device
+    T = torch.empty(12, dtype=torch.float64, device=dev)
+    conf = torch.empty(1, dtype=torch.float64, device=dev)
+    ctx.check(ctx._lib.gs_fuse(ctx.handle, int(est.shape[0]), _ptr(est.contiguous()), _ptr(reverse.contiguous()),
+                               _ptr(eps.contiguous()), _ptr(T), _ptr(conf), _stream()))
+    return T, conf
+
+
+def _views(views):
+    arr = (gs_view_t * max(len(views), 1))()
+    for k, (cam18, rgb, depth) in enumerate(views):
+        arr[k] = gs_view_t(rgb.data_ptr(), depth.data_ptr(), camera(cam18))
+    return arr
+
+
+def gs_register(ctx: Context, src: Gaussians, tgt: Gaussians, src_views, tgt_views, iters, opt=None):
+    """3DGS registration of src (P) and tgt (Q).  ``*_views`` are lists of
+    (cam18, rgb [3,H,W] CUDA, depth [H,W] CUDA).  Returns (T_{P->Q} [3,4]
+    float64 numpy, confidence, eps [n], per-keyframe estimates [n,3,4])."""
+    opt = opt or default_options()
+    for _, rgb, depth in list(src_views) + list(tgt_views):
+        if not (rgb.is_cuda and depth.is_cuda and rgb.is_contiguous() and depth.is_contiguous()):
+            raise ValueError("keyframe images must be contiguous CUDA tensors")
+    sv, tv = _views(src_views), _views(tgt_views)
+    n = len(src_views) + len(tgt_views)
+    T = np.zeros(12, np.float64)
+    conf = ctypes.c_double(0)
+    eps = np.zeros(max(n, 1), np.float64)
+    est = np.zeros((max(n, 1), 12), np.float64)
+    s, t = src.c_struct(), tgt.c_struct()
+    d = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    ctx.check(ctx._lib.gs_register(ctx.handle, ctypes.byref(s), ctypes.byref(t), sv, len(src_views), tv,
+                                   len(tgt_views), ctypes.byref(opt), int(iters), d(T), ctypes.byref(conf), d(eps),
+                                   d(est), _stream()))
+    return T.reshape(3, 4), conf.value, eps[:n], est[:n].reshape(n, 3, 4)
+
+
+def gs_transform(ctx: Context, g: Gaussians, T) -> Gaussians:
+    """Rigid transform of a submap (Eq. 8/9) on the device."""
+    Th = np.ascontiguousarray(np.asarray(T, np.float64).reshape(12))
+    m = torch.empty_like(g.means4)
+    q = torch.empty_like(g.quats4)
+    gst = g.c_struct()
+    ctx.check(ctx._lib.gs_transform(ctx.handle, ctypes.byref(gst), Th.ctypes.data_as(ctypes.c_void_p), _ptr(m),
+                                    _ptr(q), _stream()))
+    return Gaussians(m, g.log_scales4.clone(), q, g.logits.clone(), g.rgb4.clone())

@@ -1,0 +1,380 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: integer and index outcomes bit-exact (visibility, tile rectangles,
+sorted keys / values, per-tile ranges, last-contributor index, FP32 final
+transmittance, which follows the same single-precision operation sequence
+as the oracle's mirror); rendered colour / depth / alpha within 1e-4
+max-abs of the FP64 oracle; pose gradients within 1e-3 relative (L2 norm
+of the 6-vector); pose update and fusion within 1e-10; recovered
+transforms within 0.5 mm / 0.01 deg."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_10154_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2408_10154_gb300 as gsmod
+    from paper_2408_10154_gb300 import build
+    build.build()
+    O.build()
+    return gsmod
+
+
+@pytest.fixture(scope="module")
+def ctx(gs):
+    c = gs.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def rand_poses(rng, k, angle=4.0, trans=0.04):
+    return np.stack([synth.random_rigid(rng, angle, trans) for _ in range(k)])
+
+
+def f32pose(P):
+    return np.asarray(P, np.float32).astype(np.float64)
+
+
+def decode_rect(rec):
+    bx = rec[:, 7].view(np.uint32)
+    by = rec[:, 11].view(np.uint32)
+    return np.stack([bx & 0xFFFF, bx >> 16, by & 0xFFFF, by >> 16], axis=1).astype(np.int32)
+
+
+def rot_err(P, T):
+    R = np.asarray(P)[:, :3].T @ np.asarray(T)[:, :3]
+    ang = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(R) - 1) / 2))))
+    return ang, float(np.linalg.norm(np.asarray(P)[:, 3] - np.asarray(T)[:, 3]))
+
+
+# ----------------------------------------------------------------- workloads
+def plain_case():
+    c = synth.plain_2k()
+    return c["gaussians"], c["cams"]
+
+
+def room_case(n_views=2):
+    c = synth.room_150k()
+    return c["gaussians"], c["src_cams"][:n_views]
+
+
+def ragged_case():
+    c = synth.small_case(700, 100, 70, 70.0, n_views=3, seed=9, ls_mean=-3.5)
+    return c["gaussians"], c["cams"]
+
+
+CASES = {"plain_2k": plain_case, "ragged_100x70": ragged_case}
+
+
+# ----------------------------------------------------------------- projection
+def check_projection(gs, ctx, gd, cams, poses):
+    og = O.Gaussians.from_dict(gd)
+    g = gs.Gaussians.from_numpy(gd)
+    recs, aux, counts = gs.gs_project(ctx, g, dev(poses.reshape(-1, 12)), cams)
+    recs, aux, counts = recs.cpu().numpy(), aux.cpu().numpy(), counts.cpu().numpy()
+    n = og.n
+    for c, cam in enumerate(cams):
+        f, i = O.project32(og, f32pose(poses[c]), cam)
+        sl = slice(c * n, (c + 1) * n)
+        vis = i[:, 0] == 1
+        np.testing.assert_array_equal(counts[sl] > 0, vis)
+        r = recs[sl][vis]
+        rect = decode_rect(r)
+        np.testing.assert_array_equal(rect, i[vis][:, 2:6])
+        np.testing.assert_array_equal(counts[sl][vis], (rect[:, 1] - rect[:, 0]) * (rect[:, 3] - rect[:, 2]))
+        # every FP32 bit of the record: u, v, ca, cb, cc, o, z
+        got = np.stack([r[:, 0], r[:, 1], r[:, 2], r[:, 3], r[:, 4], r[:, 5], r[:, 6]], 1).view(np.uint32)
+        want = np.stack([f[vis][:, k] for k in (0, 1, 3, 4, 5, 6, 2)], 1).view(np.uint32)
+        np.testing.assert_array_equal(got, want)
+        np.testing.assert_array_equal(r[:, 8:11], og.rgb4[vis][:, :3])
+        # auxiliary camera-space mean and covariance vs FP64
+        p64 = O.project64(og, f32pose(poses[c]), cam)[vis]
+        a = aux[sl][vis]
+        np.testing.assert_allclose(a[:, 0], p64[:, 7], rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(a[:, 1], p64[:, 8], rtol=1e-5, atol=1e-6)
+        scale = np.abs(p64[:, 9:15]).max(axis=1, keepdims=True)
+        assert np.all(np.abs(a[:, 2:8] - p64[:, 9:15]) <= 1e-5 * scale + 1e-12)
+    return int(counts.sum())
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_projection_bit_exact(gs, ctx, case):
+    gd, cams = CASES[case]()
+    poses = rand_poses(np.random.default_rng(1), len(cams))
+    assert check_projection(gs, ctx, gd, cams, poses) > 0
+
+
+def test_projection_bit_exact_room_full_size(gs, ctx):
+    c = synth.room_150k()
+    poses = rand_poses(np.random.default_rng(2), 8, 10.0, 0.15)
+    assert check_projection(gs, ctx, c["gaussians"], c["src_cams"], poses) > 0
+
+
+# ----------------------------------------------------------------- binning
+def check_binning(gs, ctx, gd, cams, poses):
+    og = O.Gaussians.from_dict(gd)
+    g = gs.Gaussians.from_numpy(gd)
+    recs, _, counts = gs.gs_project(ctx, g, dev(poses.reshape(-1, 12)), cams, with_aux=False)
+    keys, vals, ranges = gs.gs_bin(ctx, recs, counts, cams, g.n)
+    ok, ov, orng = O.bin_tiles(og, np.stack([f32pose(p) for p in poses]), cams)
+    np.testing.assert_array_equal(keys.cpu().numpy().view(np.uint64), ok)
+    np.testing.assert_array_equal(vals.cpu().numpy().view(np.uint32), ov)
+    np.testing.assert_array_equal(ranges.cpu().numpy().astype(np.int64), orng)
+    return len(ok)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_binning_bit_exact(gs, ctx, case):
+    gd, cams = CASES[case]()
+    poses = rand_poses(np.random.default_rng(3), len(cams))
+    assert check_binning(gs, ctx, gd, cams, poses) > 0
+
+
+def test_binning_bit_exact_room_full_size(gs, ctx):
+    gd, cams = room_case(2)
+    poses = rand_poses(np.random.default_rng(4), 2, 10.0, 0.15)
+    assert check_binning(gs, ctx, gd, cams, poses) > 100_000
+
+
+def test_binning_empty(gs, ctx):
+    gd, cams = plain_case()
+    poses = np.stack([np.eye(3, 4)] * 4)
+    poses[:, 2, 3] = -10.0  # everything behind the cameras
+    g = gs.Gaussians.from_numpy(gd)
+    recs, _, counts = gs.gs_project(ctx, g, dev(poses.reshape(-1, 12)), cams, with_aux=False)
+    assert int(counts.sum()) == 0
+    keys, vals, ranges = gs.gs_bin(ctx, recs, counts, cams, g.n, capacity=0)
+    assert keys.numel() == 0 and int(ranges.abs().sum()) == 0
+
+
+# ----------------------------------------------------------------- render
+def check_render(gs, ctx, gd, cams, poses, opt_o=O.DEFAULT_OPT, opt_g=None):
+    og = O.Gaussians.from_dict(gd)
+    g = gs.Gaussians.from_numpy(gd)
+    out = gs.gs_render(ctx, g, dev(poses.reshape(-1, 12)), cams, opt_g)
+    rgb = [v.cpu().numpy() for v in gs.split_views(out["rgb"], cams, 3)]
+    dep = [v.cpu().numpy() for v in gs.split_views(out["depth"], cams, 1)]
+    alp = [v.cpu().numpy() for v in gs.split_views(out["alpha"], cams, 1)]
+    tf = [v.cpu().numpy() for v in gs.split_views(out["t_final"], cams, 1)]
+    last = [v.cpu().numpy() for v in gs.split_views(out["last"], cams, 1)]
+    worst = 0.0
+    for c, cam in enumerate(cams):
+        ref = O.render(og, f32pose(poses[c]), cam, opt_o)
+        worst = max(worst, np.abs(rgb[c] - ref["rgb"]).max(), np.abs(dep[c] - ref["depth"]).max(),
+                    np.abs(alp[c] - ref["alpha"]).max())
+        np.testing.assert_array_equal(tf[c].view(np.uint32), ref["t_final32"].view(np.uint32))
+        np.testing.assert_array_equal(last[c], ref["last"])
+    assert worst <= 1e-4, worst
+    return out
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_render_parity(gs, ctx, case):
+    gd, cams = CASES[case]()
+    check_render(gs, ctx, gd, cams, rand_poses(np.random.default_rng(5), len(cams)))
+
+
+def test_render_parity_smooth_mode(gs, ctx):
+    gd, cams = ragged_case()
+    check_render(gs, ctx, gd, cams[:1], rand_poses(np.random.default_rng(6), 1), O.SMOOTH_OPT,
+                 gs.default_options(alpha_min=0.0, alpha_max=1.0, t_min=0.0, smooth=1))
+
+
+def test_render_parity_room_full_size(gs, ctx):
+    gd, cams = room_case(2)
+    check_render(gs, ctx, gd, cams, rand_poses(np.random.default_rng(7), 2, 10.0, 0.15))
+
+
+def test_render_empty_and_single(gs, ctx):
+    gd, cams = ragged_case()
+    empty = {k: v[:0] for k, v in gd.items()}
+    g = gs.Gaussians.from_numpy(empty)
+    out = gs.gs_render(ctx, g, dev(np.eye(3, 4).reshape(1, 12)), cams[:1])
+    assert float(out["rgb"].abs().max()) == 0.0 and float(out["t_final"].min()) == 1.0
+    single = {k: v[:1] for k, v in gd.items()}
+    check_render(gs, ctx, single, cams[:1], np.stack([np.eye(3, 4)]))
+
+
+# ----------------------------------------------------------------- loss
+def test_loss_parity(gs, ctx):
+    gd, cams = ragged_case()
+    og = O.Gaussians.from_dict(gd)
+    rng = np.random.default_rng(8)
+    ims, tg = [], []
+    for c, cam in enumerate(cams):
+        a = O.render(og, rand_poses(rng, 1)[0], cam)
+        b = O.render(og, rand_poses(rng, 1)[0], cam)
+        ims.append((a["rgb"].astype(np.float32), a["depth"].astype(np.float32)))
+        tg.append((b["rgb"].astype(np.float32), b["depth"].astype(np.float32)))
+    tg[0][0][0, 3, 4] = ims[0][0][0, 3, 4]  # one exact match: zero subgradient
+    cat = lambda xs: dev(np.concatenate([x.reshape(-1) for x in xs]))
+    loss, d_rgb, d_depth = gs.gs_loss(ctx, cams, cat([i[0] for i in ims]), cat([i[1] for i in ims]),
+                                      cat([t[0] for t in tg]), cat([t[1] for t in tg]))
+    d_rgb = gs.split_views(d_rgb, cams, 3)
+    d_depth = gs.split_views(d_depth, cams, 1)
+    for c in range(len(cams)):
+        L, gr, gd_ = O.loss(ims[c][0], ims[c][1], tg[c][0], tg[c][1])
+        assert float(loss[c]) == pytest.approx(L, rel=1e-6)
+        np.testing.assert_array_equal(d_rgb[c].cpu().numpy(), gr.astype(np.float32))
+        np.testing.assert_array_equal(d_depth[c].cpu().numpy(), gd_.astype(np.float32))
+
+
+# ----------------------------------------------------------------- adjoint
+def check_pose_grad(gs, ctx, gd, cams, poses, seed):
+    og = O.Gaussians.from_dict(gd)
+    g = gs.Gaussians.from_numpy(gd)
+    rng = np.random.default_rng(seed)
+    P = dev(poses.reshape(-1, 12))
+    out = gs.gs_render(ctx, g, P, cams)
+    cots_r = [rng.standard_normal((3, int(c[5]), int(c[4]))) for c in cams]
+    cots_d = [rng.standard_normal((int(c[5]), int(c[4]))) for c in cams]
+    cots_a = [rng.standard_normal((int(c[5]), int(c[4]))) for c in cams]
+    pivots = np.stack([O.centroid(og) + rng.normal(0, 0.05, 3) for _ in cams])
+    cat = lambda xs: dev(np.concatenate([x.reshape(-1) for x in xs]))
+    pg = gs.gs_render_backward(ctx, g, P, cams, out["t_final"], out["last"], cat(cots_r), cat(cots_d), cat(cots_a),
+                               dev(pivots)).cpu().numpy()
+    for c, cam in enumerate(cams):
+        cr = cots_r[c].astype(np.float32).astype(np.float64)
+        cd = cots_d[c].astype(np.float32).astype(np.float64)
+        ca = cots_a[c].astype(np.float32).astype(np.float64)
+        ref = O.backward(og, f32pose(poses[c]), cam, cr, cd, ca, pivot=pivots[c].astype(np.float32), params=False)
+        tw = ref["twist"]
+        err = np.linalg.norm(pg[c] - tw) / np.linalg.norm(tw)
+        assert err <= 1e-3, (c, err, pg[c], tw)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_pose_gradient_parity(gs, ctx, case):
+    gd, cams = CASES[case]()
+    check_pose_grad(gs, ctx, gd, cams, rand_poses(np.random.default_rng(9), len(cams)), 10)
+
+
+def test_pose_gradient_parity_room_full_size(gs, ctx):
+    gd, cams = room_case(2)
+    check_pose_grad(gs, ctx, gd, cams, rand_poses(np.random.default_rng(11), 2, 10.0, 0.15), 12)
+
+
+# ----------------------------------------------------------------- update / fusion / transform
+def test_pose_step_parity(gs, ctx):
+    rng = np.random.default_rng(13)
+    n = 5
+    poses = rand_poses(rng, n, 20.0, 0.3)
+    states = np.concatenate([rng.normal(0, 0.1, (n, 6)), rng.uniform(0.001, 0.1, (n, 6)), np.full((n, 1), 7.0)], 1)
+    grads = rng.standard_normal((n, 6))
+    piv = rng.standard_normal((n, 3))
+    P = dev(poses.reshape(n, 12), torch.float64)
+    S = dev(states, torch.float64)
+    gs.gs_pose_step(ctx, P, S, dev(grads, torch.float64), dev(piv, torch.float64), 11, 50)
+    for i in range(n):
+        p, s = O.pose_step(poses[i], states[i], grads[i], piv[i], 11, 50)
+        np.testing.assert_allclose(P[i].cpu().numpy(), p.reshape(12), atol=1e-12)
+        np.testing.assert_allclose(S[i].cpu().numpy(), s, atol=1e-12)
+
+
+def test_fuse_parity(gs, ctx):
+    rng = np.random.default_rng(14)
+    T0 = synth.random_rigid(rng, 30.0, 0.5)
+    est, rev = [], []
+    for k in range(7):
+        E = synth.compose(synth.random_rigid(rng, 1.0, 0.01), T0)
+        r = k % 2 == 1
+        est.append(synth.inverse(E) if r else E)
+        rev.append(r)
+    eps = rng.uniform(0.01, 0.2, 7)
+    T, conf = gs.gs_fuse(ctx, dev(np.stack(est).reshape(7, 12), torch.float64),
+                         dev(np.array(rev, np.int32), torch.int32), dev(eps, torch.float64))
+    Tr, cr = O.fuse(np.stack(est), eps, rev)
+    np.testing.assert_allclose(T.cpu().numpy().reshape(3, 4), Tr, atol=1e-10)
+    assert float(conf) == pytest.approx(cr, rel=1e-12)
+
+
+def test_transform_parity(gs, ctx):
+    gd, _ = plain_case()
+    og = O.Gaussians.from_dict(gd)
+    T = synth.random_rigid(np.random.default_rng(15), 40.0, 0.3)
+    out = gs.gs_transform(ctx, gs.Gaussians.from_numpy(gd), T)
+    ref = O.transform(og, T)
+    np.testing.assert_allclose(out.means4.cpu().numpy(), ref.means4, atol=2e-6)
+    q = out.quats4.cpu().numpy()
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    q *= np.sign(q[:, :1] + 1e-30)
+    np.testing.assert_allclose(q, ref.quats4, atol=2e-6)
+
+
+# ----------------------------------------------------------------- registration
+def test_registration_plain_2k_matches_oracle(gs, ctx):
+    c = synth.plain_2k()
+    og = O.Gaussians.from_dict(c["gaussians"])
+    g = gs.Gaussians.from_numpy(c["gaussians"])
+    T = c["T_gt"]
+    views, ests, epss = [], [], []
+    for cam in c["cams"]:
+        tr = O.render(og, T, cam)
+        t_rgb, t_dep = tr["rgb"].astype(np.float32), tr["depth"].astype(np.float32)
+        views.append((cam, dev(t_rgb), dev(t_dep)))
+        P, eps, _ = O.register_view(og, cam, t_rgb, t_dep, 50)
+        ests.append(P)
+        epss.append(eps)
+    Tg, conf, eps_g, est_g = gs.gs_register(ctx, g, g, [], views, 50)
+    To, co = O.fuse(np.stack(ests), epss, [False] * 4)
+    for k in range(4):
+        ang, dt = rot_err(est_g[k], ests[k])
+        assert ang < 0.01 and dt < 5e-4, (k, ang, dt)
+    ang, dt = rot_err(Tg, To)
+    assert ang < 0.01 and dt < 5e-4, (ang, dt)
+    ang, dt = rot_err(Tg, T)
+    assert ang < 0.01 and dt < 5e-4, (ang, dt)
+    np.testing.assert_allclose(eps_g, epss, rtol=0.5, atol=2e-4)
+
+
+def test_registration_is_deterministic_and_zero_iters(gs, ctx):
+    gd, cams = ragged_case()
+    og = O.Gaussians.from_dict(gd)
+    g = gs.Gaussians.from_numpy(gd)
+    T = synth.about_point(synth.random_rigid(np.random.default_rng(16), 2.0, 0.02), O.centroid(og))
+    views = []
+    for cam in cams:
+        tr = O.render(og, T, cam)
+        views.append((cam, dev(tr["rgb"].astype(np.float32)), dev(tr["depth"].astype(np.float32))))
+    a = gs.gs_register(ctx, g, g, views[:1], views[1:], 20)
+    b = gs.gs_register(ctx, g, g, views[:1], views[1:], 20)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[3], b[3])
+    z = gs.gs_register(ctx, g, g, [], views, 0)
+    for E in z[3]:
+        np.testing.assert_allclose(E, np.eye(3, 4), atol=1e-12)
+
+
+def test_registration_room_full_size_recovers_transform(gs, ctx):
+    # room-scale workload at full size (150k Gaussians, 8+8 keyframes of
+    # 1200x680, 100 iterations, both directions): targets rendered on the
+    # device; the expected value is the generator's ground truth
+    c = synth.room_150k()
+    src = gs.Gaussians.from_numpy(c["gaussians"])
+    tgt = gs.gs_transform(ctx, src, c["T_gt"])
+    I = dev(np.stack([np.eye(3, 4)] * 8).reshape(8, 12))
+    rs = gs.gs_render(ctx, src, I, c["src_cams"])
+    rt = gs.gs_render(ctx, tgt, I, c["tgt_cams"])
+    sv = list(zip(c["src_cams"], [x.contiguous() for x in gs.split_views(rs["rgb"], c["src_cams"], 3)],
+                  [x.contiguous() for x in gs.split_views(rs["depth"], c["src_cams"], 1)]))
+    tv = list(zip(c["tgt_cams"], [x.contiguous() for x in gs.split_views(rt["rgb"], c["tgt_cams"], 3)],
+                  [x.contiguous() for x in gs.split_views(rt["depth"], c["tgt_cams"], 1)]))
+    T, conf, eps, est = gs.gs_register(ctx, src, tgt, sv, tv, 100)
+    ang, dt = rot_err(T, c["T_gt"])
+    assert ang < 0.01 and dt < 5e-4, (ang, dt, eps)
+    assert np.all(np.isfinite(eps)) and conf > 0
