@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of 3DGS loop-edge registration on GB300.
+
+Workload (one bench step = one loop edge): the room-scale registration of
+LoopSplat's Sec. 3.2 at full size -- a 150,000-Gaussian room submap P and
+its copy Q moved by a 10 deg / 15 cm rigid map, 8 keyframes of 1200x680 per
+submap, 100 iterations of forward + backward + on-device pose update in both
+directions (16 keyframe problems, 13.06 Mpx per iteration), the residual
+pass and the Eq. 7 fusion.  Inputs are seeded and synthetic (no dataset).
+
+Metric: registration steps/s (one step = one iteration over all 16
+keyframes, forward + backward + update), whole job over N GPUs; plus Mpx/s
+and the p50/p99 latency of a loop edge.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "registration steps/s"
+UNIT = "steps/s"
+ITERS = 100
+WORKLOAD = ("room_150k: 150,000-Gaussian room submap pair (10 deg / 15 cm), 8+8 keyframes 1200x680, "
+            "100 iterations fwd+bwd+update in both directions, residual + Eq. 7 fusion")
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# FP32 operations of the dominant kernels per unit of work
+BWD_FLOPS_PER_PAIR = 80.0
+FWD_FLOPS_PER_PAIR = 45.0
+SMS = 152
+FP32_LANES = 128
+PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAK_FILE))
+    except (OSError, ValueError):
+        return {}
+
+
+def make_workload(gs, ctx, torch, seed=1001):
+    from paper_2408_10154_gb300 import synth
+    c = synth.room_150k(seed=seed)
+    src = gs.Gaussians.from_numpy(c["gaussians"])
+    tgt = gs.gs_transform(ctx, src, c["T_gt"])  # Q = T_gt P (Eq. 8/9), on the device
+    I8 = torch.tensor(np.stack([np.eye(3, 4)] * 8).reshape(8, 12), dtype=torch.float32, device="cuda")
+    rs = gs.gs_render(ctx, src, I8, c["src_cams"])
+    rt = gs.gs_render(ctx, tgt, I8, c["tgt_cams"])
+    sv = list(zip(c["src_cams"], [x.contiguous() for x in gs.split_views(rs["rgb"], c["src_cams"], 3)],
+                  [x.contiguous() for x in gs.split_views(rs["depth"], c["src_cams"], 1)]))
+    tv = list(zip(c["tgt_cams"], [x.contiguous() for x in gs.split_views(rt["rgb"], c["tgt_cams"], 3)],
+                  [x.contiguous() for x in gs.split_views(rt["depth"], c["tgt_cams"], 1)]))
+    px = sum(int(cam[4]) * int(cam[5]) for cam in list(c["src_cams"]) + list(c["tgt_cams"]))
+    return c, src, tgt, sv, tv, px
+
+
+def rot_err(P, T):
+    R = np.asarray(P)[:, :3].T @ np.asarray(T)[:, :3]
+    return math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(R) - 1) / 2)))), float(
+        np.linalg.norm(np.asarray(P)[:, 3] - np.asarray(T)[:, 3]))
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2408_10154_gb300 import synth
+    O.build()
+    c = synth.room_150k()
+    g_src = O.Gaussians.from_dict(c["gaussians"])
+    g_tgt = O.transform(g_src, c["T_gt"])
+    cam = c["src_cams"][0]
+    tr = O.render(g_src, np.eye(3, 4), cam)
+    t_rgb, t_dep = tr["rgb"].astype(np.float32), tr["depth"].astype(np.float32)
+    piv = O.centroid(g_tgt)
+
+    def one_keyframe_iteration():
+        pose = np.eye(3, 4)
+        r = O.render(g_tgt, pose, cam)
+        L, gr, gd = O.loss(r["rgb"], r["depth"], t_rgb, t_dep)
+        b = O.backward(g_tgt, pose, cam, gr, gd, pivot=piv, params=False)
+        O.pose_step(pose, np.zeros(13), b["twist"], piv, 0, ITERS)
+
+    for _ in range(args.warmup):
+        one_keyframe_iteration()
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        one_keyframe_iteration()
+        times.append(time.perf_counter() - t)
+    per_kf = float(np.mean(times))
+    value = 1.0 / (16.0 * per_kf)  # a registration step covers 16 keyframes
+    sample = "one keyframe iteration (1200x680 render + L1 loss + adjoint + pose step) of the room workload per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_kf * 16 * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "iters_per_edge": ITERS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    device = torch.cuda.current_device()
+    import paper_2408_10154_gb300 as gs
+    ctx = gs.Context(device)
+    c, src, tgt, sv, tv, px = make_workload(gs, ctx, torch)
+    opt = gs.default_options(profile=1)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stats_cls = gs.gsreg.gs_stats_t
+    import ctypes
+
+    def stats():
+        st = stats_cls()
+        ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st)))
+        return st
+
+    for _ in range(max(args.warmup, 0)):
+        gs.gs_register(ctx, src, tgt, sv, tv, ITERS, opt)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(device)
+    sampler.start()
+    times, phases, launches, pairs, dups, results = [], np.zeros(5), 0, 0, 0, []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()  # evict L2 between timed calls (outside the timed region)
+        ev0.record()
+        res = gs.gs_register(ctx, src, tgt, sv, tv, ITERS, opt)
+        ev1.record()
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        st = stats()
+        phases += np.array(list(st.phase_ms))
+        launches += st.kernel_launches
+        pairs += st.pairs
+        dups = st.n_dups
+        results.append(res)
+    torch.cuda.synchronize()
+    sampler.stop()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    steps_total = world * args.steps * ITERS
+    value = steps_total / (total_ms / 1000.0)
+    # end to end: inputs from pinned host memory each step, result read back
+    host = {k: getattr(src, k).cpu().pin_memory() for k in ("means4", "log_scales4", "quats4", "logits", "rgb4")}
+    host_t = {k: getattr(tgt, k).cpu().pin_memory() for k in ("means4", "log_scales4", "quats4", "logits", "rgb4")}
+    host_v = [(cam, r.cpu().pin_memory(), d.cpu().pin_memory()) for cam, r, d in list(sv) + list(tv)]
+    dsrc = gs.Gaussians(*[torch.empty_like(getattr(src, k)) for k in ("means4", "log_scales4", "quats4", "logits",
+                                                                         "rgb4")])
+    dtgt = gs.Gaussians(*[torch.empty_like(getattr(tgt, k)) for k in ("means4", "log_scales4", "quats4", "logits",
+                                                                         "rgb4")])
+    dviews = [(cam, torch.empty_like(r, device="cuda"), torch.empty_like(d, device="cuda")) for cam, r, d in host_v]
+    h2d = sum(v.numel() * v.element_size() for v in list(host.values()) + list(host_t.values()))
+    h2d += sum(r.numel() * r.element_size() + d.numel() * d.element_size() for _, r, d in host_v)
+    d2h = 12 * 8 + 8 + 16 * 8 + 16 * 12 * 8
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in host:
+            getattr(dsrc, k).copy_(host[k], non_blocking=True)
+            getattr(dtgt, k).copy_(host_t[k], non_blocking=True)
+        for (cam, r, d), (_, hr, hd) in zip(dviews, host_v):
+            r.copy_(hr, non_blocking=True)
+            d.copy_(hd, non_blocking=True)
+        gs.gs_register(ctx, dsrc, dtgt, dviews[:8], dviews[8:], ITERS, opt)  # returns T on the host
+        e2e_times.append((time.perf_counter() - t0) * 1000.0)
+    e2e_value = world * ITERS / (np.mean(e2e_times) / 1000.0)
+
+    pk = peaks()
+    clocks = sampler.summary()
+    # roofline of the dominant kernel, from the CUDA-event phase times of the timed calls
+    names = ["project", "bin", "forward", "backward", "update"]
+    calls = args.steps
+    per_launch_ms = phases / (calls * ITERS)
+    dom = int(np.argmax(per_launch_ms))
+    pairs_per_launch = pairs / (calls * ITERS)
+    peak_fp32 = SMS * FP32_LANES * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+    if names[dom] in ("backward", "forward"):
+        fl = BWD_FLOPS_PER_PAIR if names[dom] == "backward" else FWD_FLOPS_PER_PAIR
+        achieved = pairs_per_launch * fl / (per_launch_ms[dom] / 1000.0) / 1e12
+        roof = {"kernel": f"k_{names[dom]}", "bound": "alu", "achieved": achieved, "peak": peak_fp32,
+                "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (of derived)"}
+    else:
+        hbm = pk.get("hbm_gbs", 6800.0)
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None}
+    lat = sorted(times)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "iters_per_edge": ITERS, "pixels_per_iteration": px,
+                   "l2": "flushed between timed calls (256 MB write); per-iteration working set > 129 MB L2",
+                   "bench_step": "one loop edge = 100 registration steps + residual + fusion"},
+        "mpx_per_s": value * px / 1e6,
+        "edge_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "phase_ms_per_iteration": {n: float(v) for n, v in zip(names, per_launch_ms)},
+        "pairs_per_iteration": pairs_per_launch, "dups": int(dups),
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    T = results[-1][0]
+    ang, dt = rot_err(T, c["T_gt"])
+    out["accuracy"] = {"rot_err_deg": ang, "trans_err_mm": dt * 1000.0,
+                       "keyframes_converged": int(np.sum(np.asarray(results[-1][2]) < 0.01))}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(c)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def cpu_baseline(c):
+    """Times the FP64 oracle, as it stands, on host cores: one keyframe
+    iteration (render + loss + adjoint + pose step) at full size from each
+    direction, scaled to registration steps/s (16 keyframes per step)."""
+    import oracle as O
+    O.build()
+    g_src = O.Gaussians.from_dict(c["gaussians"])
+    g_tgt = O.transform(g_src, c["T_gt"])
+    jobs = [(g_tgt, g_src, c["src_cams"][0]), (g_src, g_tgt, c["tgt_cams"][0])]
+    per = []
+    for moving, fixed, cam in jobs:
+        tr = O.render(fixed, np.eye(3, 4), cam)
+        t_rgb, t_dep = tr["rgb"].astype(np.float32), tr["depth"].astype(np.float32)
+        piv = O.centroid(moving)
+        t = time.perf_counter()
+        pose = np.eye(3, 4)
+        r = O.render(moving, pose, cam)
+        L, gr, gd = O.loss(r["rgb"], r["depth"], t_rgb, t_dep)
+        b = O.backward(moving, pose, cam, gr, gd, pivot=piv, params=False)
+        O.pose_step(pose, np.zeros(13), b["twist"], piv, 0, ITERS)
+        per.append(time.perf_counter() - t)
+    per_kf = float(np.mean(per))
+    return {"value": 1.0 / (16.0 * per_kf), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "2 keyframe iterations at full size (one per direction), scaled x8 to a 16-keyframe step",
+            "seconds": float(sum(per))}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

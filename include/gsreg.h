@@ -107,7 +107,22 @@ typedef struct {
     float beta2;       /* 0.99 */
     float adam_eps;    /* 1e-8 */
     float lr_final;    /* cosine decay of both rates to this fraction (0.001) */
+    int32_t profile;   /* 1: gs_register times each phase with CUDA events (gs_ctx_stats) */
 } gs_options_t;
+
+/* Statistics of the last gs_register / gs_render call on a context. */
+typedef struct {
+    int64_t kernel_launches; /* kernels of this library launched by the call */
+    int64_t n_dups;          /* tile duplicates at the last binning */
+    int64_t n_pixels;        /* pixels of one render pass over all keyframes */
+    int64_t pairs;           /* sum over iterations and pixels of the list prefix the adjoint re-walks */
+    int32_t iterations;      /* optimisation iterations run */
+    int32_t reserved;
+    /* profile != 0: summed CUDA-event time (ms) of each phase over the
+     * iterations: project, bin (scan+emit+sort+ranges), forward+loss,
+     * backward, pose update */
+    double phase_ms[5];
+} gs_stats_t;
 
 /* ---------------------------------------------------------------- context */
 
@@ -126,6 +141,14 @@ const char *gs_last_error(const gs_ctx_t *ctx);
 
 /* Bytes of scratch the context holds now. */
 size_t gs_ctx_bytes(const gs_ctx_t *ctx);
+
+/* Copies the statistics of the last gs_register / gs_render call. */
+gs_status_t gs_ctx_stats(const gs_ctx_t *ctx, gs_stats_t *out);
+
+/* sizeof of the ABI structs, for binding checks (no device needed):
+ * out[0..5] = gs_gaussians_t, gs_camera_t, gs_view_t, gs_options_t,
+ * gs_stats_t, gs_gaussian_grads_t; returns the number written (<= n). */
+int gs_abi_sizes(size_t *out, int n);
 
 /* -------------------------------------------------------------- rendering */
 

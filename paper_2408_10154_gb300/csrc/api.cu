@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -18,7 +19,7 @@ enum Slot {
     S_VPS, S_GROUPS, S_TILEVP, S_POSE32, S_REC, S_AUX, S_COUNTS, S_PARTIALS, S_NDUPS, S_K0, S_K1, S_V0, S_V1,
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
-    S_COUNT
+    S_PAIRS, S_COUNT
 };
 
 struct Buf {
@@ -26,7 +27,13 @@ struct Buf {
     size_t bytes = 0;
 };
 
+constexpr int kPhases = 5;  // project, bin, forward, backward, update
+
 }  // namespace
+
+namespace gsl {
+long long g_launches = 0;
+}
 
 struct gs_ctx {
     int device = 0;
@@ -35,6 +42,9 @@ struct gs_ctx {
     std::string err;
     Buf bufs[S_COUNT];
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    gs_stats_t stats{};
+    cudaEvent_t tev[kPhases + 1] = {};  // phase boundaries recorded in the captured iteration
+    std::vector<cudaEvent_t> pool;      // per-iteration copies of the boundaries
 };
 
 namespace {
@@ -518,6 +528,11 @@ gs_status_t gs_ctx_destroy(gs_ctx_t *ctx)
     for (Buf &b : ctx->bufs)
         if (b.p)
             cudaFree(b.p);
+    for (cudaEvent_t e : ctx->tev)
+        if (e)
+            cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->pool)
+        cudaEventDestroy(e);
     if (ctx->cap)
         cudaStreamDestroy(ctx->cap);
     delete ctx;
@@ -527,6 +542,24 @@ gs_status_t gs_ctx_destroy(gs_ctx_t *ctx)
 const char *gs_last_error(const gs_ctx_t *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 size_t gs_ctx_bytes(const gs_ctx_t *ctx) { return ctx ? ctx->used : 0; }
+
+gs_status_t gs_ctx_stats(const gs_ctx_t *ctx, gs_stats_t *out)
+{
+    if (!ctx || !out)
+        return GS_ERR_INVALID_ARG;
+    *out = ctx->stats;
+    return GS_OK;
+}
+
+int gs_abi_sizes(size_t *out, int n)
+{
+    const size_t s[6] = {sizeof(gs_gaussians_t), sizeof(gs_camera_t), sizeof(gs_view_t), sizeof(gs_options_t),
+                         sizeof(gs_stats_t), sizeof(gs_gaussian_grads_t)};
+    int k = 0;
+    for (; out && k < n && k < 6; ++k)
+        out[k] = s[k];
+    return k;
+}
 
 gs_status_t gs_project(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams,
                        int n_cams, const gs_options_t *opt, float *records, float *aux, int32_t *counts,
@@ -614,7 +647,9 @@ gs_status_t gs_render(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses
     Pipe p;
     GS_TRY(alloc_pipe(ctx, P, false, p));
     int cur = 0;
-    GS_TRY(project_and_bin(ctx, P, D, p, poses, opt, s, &cur, nullptr));
+    uint32_t nd = 0;
+    const long long l0 = gsl::g_launches;
+    GS_TRY(project_and_bin(ctx, P, D, p, poses, opt, s, &cur, &nd));
     gsl::RasterArgs r = raster_args(P, D, p, cur, opt);
     r.out_rgb = rgb;
     r.out_depth = depth;
@@ -623,6 +658,10 @@ gs_status_t gs_render(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses
     r.last = last;
     gsl::forward(r, false, s);
     GS_CUDA(cudaGetLastError());
+    ctx->stats = gs_stats_t{};
+    ctx->stats.kernel_launches = gsl::g_launches - l0;
+    ctx->stats.n_dups = nd;
+    ctx->stats.n_pixels = P.n_pix;
     int flags = 0;
     GS_TRY(read_flags(ctx, p, s, &flags));
     if (flags & gsk::kFlagNonFinite)
@@ -666,8 +705,10 @@ gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const flo
     GS_TRY(wsT(ctx, S_TTWIST, 6 * (size_t)std::max<uint64_t>(P.n_tiles, 1), &r.tile_twist));
     GS_TRY(wsT(ctx, S_TLOSS, (size_t)std::max<uint64_t>(P.n_tiles, 1), &tloss));
     GS_CUDA(cudaMemsetAsync(tloss, 0, sizeof(float) * std::max<uint64_t>(P.n_tiles, 1), s));
-    if (nv > 0)
+    if (nv > 0) {
         k_cam_pivots<<<(nv + 63) / 64, 64, 0, s>>>(D.vps, nv, pivots, ccam);
+        ++gsl::g_launches;
+    }
     r.c_cam = ccam;
     gsl::backward(r, false, false, s);
     gsl::PoseArgs a{};
@@ -679,8 +720,10 @@ gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const flo
     a.grad = grad;
     a.update = 0;
     gsl::pose_update(a, s);
-    if (pose_grad && nv > 0)
+    if (pose_grad && nv > 0) {
         k_to_float<<<(6 * nv + 255) / 256, 256, 0, s>>>(grad, pose_grad, 6 * nv);
+        ++gsl::g_launches;
+    }
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -857,8 +900,25 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
     pa.iters = std::max(iters, 1);
     pa.update = 1;
 
+    unsigned long long *pairs = nullptr;
+    GS_TRY(wsT(ctx, S_PAIRS, ntl, &pairs));
+    const bool prof = opt->profile != 0 && iters > 0;
+    if (prof) {
+        for (cudaEvent_t &e : ctx->tev)
+            if (!e)
+                GS_CUDA(cudaEventCreate(&e));
+        while ((int)ctx->pool.size() < iters * (kPhases + 1)) {
+            cudaEvent_t e;
+            GS_CUDA(cudaEventCreate(&e));
+            ctx->pool.push_back(e);
+        }
+    }
+
     double headroom = 1.5;
     for (int attempt = 0; attempt < 3; ++attempt) {
+        const long long l0 = gsl::g_launches;
+        long long captured = 0, graph_kernels = 0;
+        ctx->stats = gs_stats_t{};
         gsl::centroids(D.vps, D.set_vp, n_sets, cent, s);
         gsl::pose_init(pa, s);
         // size the duplicate lists at the initial poses (with headroom: the
@@ -877,35 +937,84 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
         r.tile_loss = tloss;
         r.tile_twist = ttw;
         r.c_cam = ccam;
+        r.tile_pairs = pairs;
+        cudaError_t mark_err = cudaSuccess;
+        auto mark = [&](int k, cudaStream_t st) {
+            // an event record node of the captured graph (re-targeted per replay)
+            if (prof && mark_err == cudaSuccess)
+                mark_err = cudaEventRecordWithFlags(ctx->tev[k], st, cudaEventRecordExternal);
+        };
         auto iteration = [&](cudaStream_t st) {
+            mark(0, st);
             gsl::project(project_args(P, D, p, pose32, opt), st);
+            mark(1, st);
             const int c = gsl::bin(b, st);
+            mark(2, st);
             r.vals = p.vals[c];
             gsl::forward(r, true, st);
+            mark(3, st);
             gsl::backward(r, true, false, st);
+            mark(4, st);
             gsl::pose_update(pa, st);
+            mark(5, st);
         };
         GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
+        GS_CUDA(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * ntl, s));
         if (iters > 0) {
             GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+            const long long c0 = gsl::g_launches;
             iteration(ctx->cap);
+            captured = gsl::g_launches - c0;
             cudaGraph_t graph = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
             if (ce != cudaSuccess || !graph)
                 return fail(ctx, GS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+            if (mark_err != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return fail(ctx, GS_ERR_CUDA, std::string("profile events: ") + cudaGetErrorString(mark_err));
+            }
+            // kernel nodes and the phase-boundary event nodes of the graph
+            size_t nn = 0;
+            cudaGraphGetNodes(graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            cudaGraphGetNodes(graph, nodes.data(), &nn);
+            cudaGraphNode_t evnode[kPhases + 1] = {};
+            for (cudaGraphNode_t nd_ : nodes) {
+                cudaGraphNodeType t;
+                cudaGraphNodeGetType(nd_, &t);
+                if (t == cudaGraphNodeTypeKernel)
+                    ++graph_kernels;
+                if (t == cudaGraphNodeTypeEventRecord) {
+                    cudaEvent_t e;
+                    cudaGraphEventRecordNodeGetEvent(nd_, &e);
+                    for (int k = 0; k <= kPhases; ++k)
+                        if (e == ctx->tev[k])
+                            evnode[k] = nd_;
+                }
+            }
             cudaGraphExec_t exec = nullptr;
             const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ie != cudaSuccess)
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(graph);
                 return fail(ctx, GS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+            }
             cudaError_t le = cudaSuccess;
-            for (int it = 0; it < iters && le == cudaSuccess; ++it)
-                le = cudaGraphLaunch(exec, s);
+            for (int it = 0; it < iters && le == cudaSuccess; ++it) {
+                if (prof)
+                    for (int k = 0; k <= kPhases && le == cudaSuccess; ++k)
+                        if (evnode[k])
+                            le = cudaGraphExecEventRecordNodeSetEvent(exec, evnode[k],
+                                                                     ctx->pool[(size_t)it * (kPhases + 1) + k]);
+                if (le == cudaSuccess)
+                    le = cudaGraphLaunch(exec, s);
+            }
             cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
             if (le != cudaSuccess)
                 return fail(ctx, GS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(le));
         }
         // residual eps at the final poses, then Eq. 7
+        r.tile_pairs = nullptr;
         gsl::project(project_args(P, D, p, pose32, opt), s);
         r.vals = p.vals[gsl::bin(b, s)];
         gsl::forward(r, true, s);
@@ -934,12 +1043,29 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
             continue;
         }
         std::vector<double> epsh(nv);
+        std::vector<unsigned long long> pairs_h(ntl);
         GS_CUDA(cudaMemcpyAsync(T_out, Tdev, 12 * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(confidence, confd, sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(epsh.data(), lossd, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(pairs_h.data(), pairs, ntl * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         if (est_out)
             GS_CUDA(cudaMemcpyAsync(est_out, est, 12 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaStreamSynchronize(s));
+        gs_stats_t &st = ctx->stats;
+        st.kernel_launches = (gsl::g_launches - l0) - captured + graph_kernels * iters;
+        st.n_dups = nd;
+        st.n_pixels = P.n_pix;
+        st.iterations = iters;
+        for (unsigned long long v : pairs_h)
+            st.pairs += (int64_t)v;
+        if (prof)
+            for (int it = 0; it < iters; ++it)
+                for (int k = 0; k < kPhases; ++k) {
+                    float ms = 0.0f;
+                    if (cudaEventElapsedTime(&ms, ctx->pool[(size_t)it * (kPhases + 1) + k],
+                                             ctx->pool[(size_t)it * (kPhases + 1) + k + 1]) == cudaSuccess)
+                        st.phase_ms[k] += ms;
+                }
         if (eps_out)
             std::memcpy(eps_out, epsh.data(), nv * sizeof(double));
         for (double e : epsh)

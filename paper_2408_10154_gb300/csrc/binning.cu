@@ -292,6 +292,7 @@ void scan_excl(const uint32_t *in, uint32_t *out, size_t n, uint32_t *partials, 
     k_scan_partials<<<nb, kScanThreads, 0, s>>>(in, n, partials);
     k_scan_top<<<1, 1024, 0, s>>>(partials, nb, total);
     k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, n, partials, out);
+    g_launches += 3;
 }
 
 void bin_count(const BinArgs &a, cudaStream_t s)
@@ -299,6 +300,7 @@ void bin_count(const BinArgs &a, cudaStream_t s)
     const uint32_t nb = div_up(a.n_records ? a.n_records : 1, kScanTile);
     k_scan_partials<<<nb, kScanThreads, 0, s>>>((const uint32_t *)a.counts, a.n_records, a.partials);
     k_scan_top<<<1, 1024, 0, s>>>(a.partials, nb, a.n_dups);
+    g_launches += 2;
 }
 
 int bin(const BinArgs &a, cudaStream_t s)
@@ -306,6 +308,7 @@ int bin(const BinArgs &a, cudaStream_t s)
     bin_count(a, s);
     const uint32_t nb = div_up(a.n_records ? a.n_records : 1, kScanTile);
     k_emit<<<nb, kScanThreads, 0, s>>>(a, a.partials);
+    ++g_launches;
     const uint32_t sb = div_up(a.capacity ? a.capacity : 1, kSortTile);
     const size_t hn = (size_t)256 * sb;
     int cur = 0;
@@ -314,10 +317,12 @@ int bin(const BinArgs &a, cudaStream_t s)
         scan_excl(a.hist, a.hist, hn, a.hist_partials, nullptr, s);
         k_rs_scatter<<<sb, kSortThreads, 0, s>>>(a.keys[cur], a.vals[cur], a.n_dups, a.capacity, shift, a.hist, sb,
                                                  a.keys[cur ^ 1], a.vals[cur ^ 1]);
+        g_launches += 2;
         cur ^= 1;
     }
     cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.n_tiles, s);
     k_ranges<<<div_up(a.capacity ? a.capacity : 1, 256), 256, 0, s>>>(a.keys[cur], a.n_dups, a.capacity, a.ranges);
+    ++g_launches;
     return cur;
 }
 

@@ -157,6 +157,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp
 // ---------------------------------------------------------------------------
 namespace gsl {
 
+// kernels launched (or captured) by this library since load; each launch
+// site adds one
+extern long long g_launches;
+
 struct ProjectArgs {
     const gsk::VpDesc *vps;
     const gsk::GroupDesc *groups;
@@ -220,6 +224,7 @@ struct RasterArgs {
     const float *d_rgb, *d_depth, *d_alpha;
     // registration / backward outputs
     float *tile_loss;         // [tiles]
+    unsigned long long *tile_pairs;  // [tiles] += sum of `last` (registration statistics, may be null)
     double *tile_twist;       // [tiles][6], camera frame
     const double *c_cam;      // [vp][3] pivot in camera frame
     float *dup_grads;         // [dups][10] screen-space partials (full mode)

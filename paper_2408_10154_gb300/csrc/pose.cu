@@ -370,34 +370,44 @@ namespace gsl {
 
 void centroids(const VpDesc *vps, const int *set_vp, int n_sets, double *centroid, cudaStream_t s)
 {
-    if (n_sets > 0)
+    if (n_sets > 0) {
         k_centroid<<<n_sets, 256, 0, s>>>(vps, set_vp, centroid);
+        ++g_launches;
+    }
 }
 
 void pose_init(const PoseArgs &a, cudaStream_t s)
 {
-    if (a.n_vps > 0)
+    if (a.n_vps > 0) {
         k_pose_init<<<(a.n_vps + 127) / 128, 128, 0, s>>>(a);
+        ++g_launches;
+    }
 }
 
 void pose_update(const PoseArgs &a, cudaStream_t s)
 {
-    if (a.n_vps > 0)
+    if (a.n_vps > 0) {
         k_pose_update<<<a.n_vps, 256, 0, s>>>(a);
+        ++g_launches;
+    }
 }
 
 void pose_step_raw(int n, double *pose, double *state, const double *grad, const double *pivot, int k, int iters,
                    float lr_rot, float lr_trans, float b1, float b2, float eps, float lr_final, cudaStream_t s)
 {
-    if (n > 0)
+    if (n > 0) {
         k_pose_step<<<(n + 127) / 128, 128, 0, s>>>(n, pose, state, grad, pivot, k, iters, lr_rot, lr_trans, b1, b2,
                                                     eps, lr_final);
+        ++g_launches;
+    }
 }
 
 void fuse(const FuseArgs &a, cudaStream_t s)
 {
-    if (a.n_problems > 0)
+    if (a.n_problems > 0) {
         k_fuse<<<(a.n_problems + 63) / 64, 64, 0, s>>>(a);
+        ++g_launches;
+    }
 }
 
 void loss(const VpDesc *vps, int n_vps, uint32_t n_tiles, const uint32_t *tile_vp, const float *rgb,
@@ -412,6 +422,7 @@ void loss(const VpDesc *vps, int n_vps, uint32_t n_tiles, const uint32_t *tile_v
     a.tile_loss = tile_loss;
     a.loss = loss_out;
     k_pose_update<<<n_vps, 256, 0, s>>>(a);
+    g_launches += 2;
 }
 
 void transform(const float4 *means, const float4 *quats, int64_t n, const double *T, float4 *out_means,
@@ -423,6 +434,7 @@ void transform(const float4 *means, const float4 *quats, int64_t n, const double
     for (int k = 0; k < 12; ++k)
         r.T[k] = T[k];
     k_transform<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(means, quats, n, r, out_means, out_quats);
+    ++g_launches;
 }
 
 }  // namespace gsl

@@ -179,6 +179,7 @@ void project(const ProjectArgs &a, cudaStream_t s)
     if (a.n_blocks == 0)
         return;
     k_project<<<a.n_blocks, 256, 0, s>>>(a);
+    ++g_launches;
 }
 
 }  // namespace gsl

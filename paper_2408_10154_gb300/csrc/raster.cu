@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(256) k_forward(const gsl::RasterArgs a)
         return;
     }
     // registration: fused L1 colour + L1 depth loss and its sign code
+    __shared__ int s_pairs[8];
     float lsum = 0.0f;
     if (p.inside) {
         const float e0 = o0 - d.t_rgb[off], e1 = o1 - d.t_rgb[HW + off], e2 = o2 - d.t_rgb[2 * HW + off];
@@ -141,58 +142,66 @@ __global__ void __launch_bounds__(256) k_forward(const gsl::RasterArgs a)
         a.last[pix] = last;
     }
     lsum = warp_sum(lsum);
-    if ((threadIdx.x & 31) == 0)
+    const int wl = warp_sum(last);
+    if ((threadIdx.x & 31) == 0) {
         s_red[threadIdx.x >> 5] = lsum;
+        s_pairs[threadIdx.x >> 5] = wl;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         float s = 0.0f;
+        unsigned long long np = 0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w)
+        for (int w = 0; w < 8; ++w) {
             s += s_red[w];
+            np += (unsigned long long)s_pairs[w];
+        }
         a.tile_loss[t] = s;
+        if (a.tile_pairs)
+            a.tile_pairs[t] += np;
     }
 }
 
 // d(screen params) of one (tile, Gaussian) -> camera-frame twist (w, v)
-// about c_cam, added to tw[6].  G = {du, dv, dca, dcb, dcc, dz, ...}.
+// about c_cam, added to tw[6].  G = {dL/du, dL/dv, 2 dL/dSigma2D_00,
+// 2 dL/dSigma2D_01, 2 dL/dSigma2D_11, dL/dz, ...} (the 2D covariance is the
+// dilated one; dilation is constant).  S = scalar type of the arithmetic.
+template <typename S>
 __device__ __forceinline__ void chain_twist(const float *G, const float4 &q0, const float4 &q1, const float4 &x0,
-                                            const float4 &x1, float fx, float fy, const double *cc, double *tw)
+                                            const float4 &x1, float fxf, float fyf, const double *cc, double *tw)
 {
-    const float mx = x0.x, my = x0.y, mz = q1.z;
-    const float S00 = x0.z, S01 = x0.w, S02 = x1.x, S11 = x1.y, S12 = x1.z, S22 = x1.w;
-    // conic Q = [[A, B], [B, C]]: exponent = -(A dx^2 + 2 B dx dy + C dy^2)/2
-    const float A = -2.0f * q0.z, B = -q0.w, Cc = -2.0f * q1.x;
-    const float dA = -0.5f * G[2], dBh = -0.5f * G[3], dC = -0.5f * G[4];  // dBh = (dL/dB)/2
-    // dL/dSigma2D = -Q G_Q Q with G_Q = [[dA, dBh], [dBh, dC]]
-    const float t00 = A * dA + B * dBh, t01 = A * dBh + B * dC;
-    const float t10 = B * dA + Cc * dBh, t11 = B * dBh + Cc * dC;
-    const float gp = -(t00 * A + t01 * B), gq = -(t00 * B + t01 * Cc), gs = -(t10 * B + t11 * Cc);
-    const float iz = 1.0f / mz, iz2 = iz * iz;
-    const float j00 = fx * iz, j11 = fy * iz, j02 = -fx * mx * iz2, j12 = -fy * my * iz2;
+    (void)q0;
+    const S fx = fxf, fy = fyf;
+    const S mx = x0.x, my = x0.y, mz = q1.z;
+    const S S00 = x0.z, S01 = x0.w, S02 = x1.x, S11 = x1.y, S12 = x1.z, S22 = x1.w;
+    // dL/dSigma2D = [[gp, gq], [gq, gs]]
+    const S gp = S(0.5) * S(G[2]), gq = S(0.5) * S(G[3]), gs = S(0.5) * S(G[4]);
+    const S iz = S(1) / mz, iz2 = iz * iz;
+    const S j00 = fx * iz, j11 = fy * iz, j02 = -fx * mx * iz2, j12 = -fy * my * iz2;
     // G2 J (2x3)
-    const float r00 = gp * j00, r01 = gq * j11, r02 = gp * j02 + gq * j12;
-    const float r10 = gq * j00, r11 = gs * j11, r12 = gq * j02 + gs * j12;
+    const S r00 = gp * j00, r01 = gq * j11, r02 = gp * j02 + gq * j12;
+    const S r10 = gq * j00, r11 = gs * j11, r12 = gq * j02 + gs * j12;
     // dL/dSigma_cam = J^T G2 J
-    const float c00 = j00 * r00, c01 = j00 * r01, c02 = j00 * r02;
-    const float c11 = j11 * r11, c12 = j11 * r12, c22 = j02 * r02 + j12 * r12;
+    const S c00 = j00 * r00, c01 = j00 * r01, c02 = j00 * r02;
+    const S c11 = j11 * r11, c12 = j11 * r12, c22 = j02 * r02 + j12 * r12;
     // dL/dJ = 2 G2 J Sigma_cam (entries used)
-    const float dJ00 = 2.0f * (r00 * S00 + r01 * S01 + r02 * S02);
-    const float dJ02 = 2.0f * (r00 * S02 + r01 * S12 + r02 * S22);
-    const float dJ11 = 2.0f * (r10 * S01 + r11 * S11 + r12 * S12);
-    const float dJ12 = 2.0f * (r10 * S02 + r11 * S12 + r12 * S22);
-    const float du = G[0], dv = G[1], dz = G[5];
-    const float gx = du * fx * iz - dJ02 * fx * iz2;
-    const float gy = dv * fy * iz - dJ12 * fy * iz2;
-    const float gz = -du * fx * mx * iz2 - dv * fy * my * iz2 + dz - dJ00 * fx * iz2 - dJ11 * fy * iz2 +
-                     2.0f * iz2 * iz * (dJ02 * fx * mx + dJ12 * fy * my);
+    const S dJ00 = S(2) * (r00 * S00 + r01 * S01 + r02 * S02);
+    const S dJ02 = S(2) * (r00 * S02 + r01 * S12 + r02 * S22);
+    const S dJ11 = S(2) * (r10 * S01 + r11 * S11 + r12 * S12);
+    const S dJ12 = S(2) * (r10 * S02 + r11 * S12 + r12 * S22);
+    const S du = G[0], dv = G[1], dz = G[5];
+    const S gx = du * fx * iz - dJ02 * fx * iz2;
+    const S gy = dv * fy * iz - dJ12 * fy * iz2;
+    const S gz = -du * fx * mx * iz2 - dv * fy * my * iz2 + dz - dJ00 * fx * iz2 - dJ11 * fy * iz2 +
+                 S(2) * iz2 * iz * (dJ02 * fx * mx + dJ12 * fy * my);
     // 2 vee(Gc S - S Gc)
-    const float k21 = (c02 * S01 + c12 * S11 + c22 * S12) - (S02 * c01 + S12 * c11 + S22 * c12);
-    const float k02 = (c00 * S02 + c01 * S12 + c02 * S22) - (S00 * c02 + S01 * c12 + S02 * c22);
-    const float k10 = (c01 * S00 + c11 * S01 + c12 * S02) - (S01 * c00 + S11 * c01 + S12 * c02);
-    const float rx = (float)(mx - cc[0]), ry = (float)(my - cc[1]), rz = (float)(mz - cc[2]);
-    tw[0] += (double)(ry * gz - rz * gy + 2.0f * k21);
-    tw[1] += (double)(rz * gx - rx * gz + 2.0f * k02);
-    tw[2] += (double)(rx * gy - ry * gx + 2.0f * k10);
+    const S k21 = (c02 * S01 + c12 * S11 + c22 * S12) - (S02 * c01 + S12 * c11 + S22 * c12);
+    const S k02 = (c00 * S02 + c01 * S12 + c02 * S22) - (S00 * c02 + S01 * c12 + S02 * c22);
+    const S k10 = (c01 * S00 + c11 * S01 + c12 * S02) - (S01 * c00 + S11 * c01 + S12 * c02);
+    const S rx = (S)(mx - cc[0]), ry = (S)(my - cc[1]), rz = (S)(mz - cc[2]);
+    tw[0] += (double)(ry * gz - rz * gy + S(2) * k21);
+    tw[1] += (double)(rz * gx - rx * gz + S(2) * k02);
+    tw[2] += (double)(rx * gy - ry * gx + S(2) * k10);
     tw[3] += (double)gx;
     tw[4] += (double)gy;
     tw[5] += (double)gz;
@@ -311,12 +320,17 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
                             g[9] = gb * wgt;
                         }
                         if (!clamped) {
+                            // d(exponent)/d(u, v) = (gu, gv) = -Q d; the
+                            // exponent's gradient w.r.t. the 2D covariance is
+                            // (Q d)(Q d)^T / 2, accumulated here as twice that
                             const float dp = dal * alpha;
-                            g[0] = dp * (2.0f * q0.z * dx + q0.w * dy);
-                            g[1] = dp * (q0.w * dx + 2.0f * q1.x * dy);
-                            g[2] = dp * dx * dx;
-                            g[3] = dp * dx * dy;
-                            g[4] = dp * dy * dy;
+                            const float gu = fmaf(2.0f * q0.z, dx, q0.w * dy);
+                            const float gv = fmaf(q0.w, dx, 2.0f * q1.x * dy);
+                            g[0] = dp * gu;
+                            g[1] = dp * gv;
+                            g[2] = g[0] * gu;
+                            g[3] = g[0] * gv;
+                            g[4] = g[1] * gv;
                             if (FULL)
                                 g[6] = dal * e;
                         }
@@ -354,8 +368,8 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
                     dst[k] = G[k];
             }
             if (any && a.tile_twist)
-                chain_twist(G, s0[threadIdx.x], s1[threadIdx.x], a.aux[2 * (size_t)r], a.aux[2 * (size_t)r + 1], d.fx,
-                            d.fy, cc, tw);
+                chain_twist<float>(G, s0[threadIdx.x], s1[threadIdx.x], a.aux[2 * (size_t)r],
+                                   a.aux[2 * (size_t)r + 1], d.fx, d.fy, cc, tw);
         }
     }
     if (!a.tile_twist)
@@ -386,6 +400,7 @@ template <bool REG, bool FULL>
 void launch_backward(const gsl::RasterArgs &a, cudaStream_t s)
 {
     k_backward<REG, FULL><<<a.n_tiles, 256, bwd_smem<REG, FULL>(), s>>>(a);
+    ++gsl::g_launches;
 }
 
 }  // namespace
@@ -410,6 +425,7 @@ void forward(const RasterArgs &a, bool registration, cudaStream_t s)
         k_forward<true><<<a.n_tiles, 256, 0, s>>>(a);
     else
         k_forward<false><<<a.n_tiles, 256, 0, s>>>(a);
+    ++g_launches;
 }
 
 void backward(const RasterArgs &a, bool registration, bool full, cudaStream_t s)

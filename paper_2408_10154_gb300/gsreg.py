@@ -52,7 +52,13 @@ class gs_options_t(ctypes.Structure):
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("smooth", ctypes.c_int32), ("lr_rot", ctypes.c_float),
                 ("lr_trans", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("adam_eps", ctypes.c_float), ("lr_final", ctypes.c_float)]
+                ("adam_eps", ctypes.c_float), ("lr_final", ctypes.c_float), ("profile", ctypes.c_int32)]
+
+
+class gs_stats_t(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("n_dups", ctypes.c_int64), ("n_pixels", ctypes.c_int64),
+                ("pairs", ctypes.c_int64), ("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("phase_ms", ctypes.c_double * 5)]
 
 
 class gs_gaussian_grads_t(ctypes.Structure):
@@ -60,9 +66,10 @@ class gs_gaussian_grads_t(ctypes.Structure):
                 ("opacity_logits", ctypes.c_void_p), ("rgb", ctypes.c_void_p)]
 
 
-EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_project",
-           "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step", "gs_fuse", "gs_register",
-           "gs_transform"]
+EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
+           "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
+           "gs_fuse", "gs_register", "gs_transform"]
+ABI_STRUCTS = [gs_gaussians_t, gs_camera_t, gs_view_t, gs_options_t, gs_stats_t, gs_gaussian_grads_t]
 
 _lock = threading.Lock()
 _lib = None
@@ -91,6 +98,8 @@ def load(build_if_missing: bool = False):
             "gs_ctx_destroy": ([P], I),
             "gs_last_error": ([P], ctypes.c_char_p),
             "gs_ctx_bytes": ([P], ctypes.c_size_t),
+            "gs_ctx_stats": ([P, P], I),
+            "gs_abi_sizes": ([P, I], I),
             "gs_project": ([P, P, P, P, I, P, P, P, P, P], I),
             "gs_bin": ([P, P, P, P, I, I64, P, P, I64, P, P, P], I),
             "gs_render": ([P, P, P, P, I, P, P, P, P, P, P, P], I),
@@ -105,6 +114,12 @@ def load(build_if_missing: bool = False):
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
+        # the binding's struct layouts must be the library's
+        sizes = (ctypes.c_size_t * len(ABI_STRUCTS))()
+        L.gs_abi_sizes(sizes, len(ABI_STRUCTS))
+        for st, sz in zip(ABI_STRUCTS, sizes):
+            if ctypes.sizeof(st) != sz:
+                raise RuntimeError(f"{st.__name__}: binding has {ctypes.sizeof(st)} bytes, library {sz}")
         _lib = L
         return L
 

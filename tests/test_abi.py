@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "gsreg.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:gs_status_t|void|const char \*|size_t)\s*\*?\s*(gs_\w+)\s*\(", text,
+    return sorted(set(re.findall(r"^\s*(?:gs_status_t|void|const char \*|size_t|int)\s*\*?\s*(gs_\w+)\s*\(", text,
                                  flags=re.M)))
 
 
@@ -54,13 +54,13 @@ def test_default_options_match_the_oracle(lib):
                                rtol=1e-6)
 
 
-def test_structs_match_the_header(lib):
+def test_structs_match_the_library(lib):
     from paper_2408_10154_gb300 import gsreg
-    # sizes of the C structs as laid out by the header (LP64)
-    assert ctypes.sizeof(gsreg.gs_camera_t) == 72
-    assert ctypes.sizeof(gsreg.gs_gaussians_t) == 48
-    assert ctypes.sizeof(gsreg.gs_view_t) == 88
-    assert ctypes.sizeof(gsreg.gs_options_t) == 4 * 16
+    sizes = (ctypes.c_size_t * 6)()
+    assert lib.gs_abi_sizes(sizes, 6) == 6
+    for st, sz in zip(gsreg.ABI_STRUCTS, sizes):
+        assert ctypes.sizeof(st) == sz, st.__name__
+    assert ctypes.sizeof(gsreg.gs_camera_t) == 72 and ctypes.sizeof(gsreg.gs_options_t) == 4 * 17
 
 
 def test_context_without_device_is_rejected(lib):
