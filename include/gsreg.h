@@ -270,6 +270,42 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
                         int n_tgt_views, const gs_options_t *opt, int iters, double *T_out,
                         double *confidence, double *eps_out, double *est_out, gs_stream_t stream);
 
+/* -------------------------------------------------- no-allocation render */
+
+/* Bytes of the fixed device scratch behind gs_render_noalloc. */
+#define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* gs_render for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this is a deployment convenience.
+ *
+ * Some callers are not allowed to call cudaMalloc / cudaFree at all: code
+ * running inside a host program whose allocator owns every byte of device
+ * memory (an engine plugin, a robotics or game runtime with a fixed memory
+ * plan), and latency-bound loops where an allocation or a free would
+ * synchronise the whole device.  This entry point takes no context and
+ * allocates nothing: its scratch is one fixed array of
+ * GS_NOALLOC_SCRATCH_BYTES in device memory that every GPU which loads the
+ * library holds until the process exits.  It runs on the caller's current
+ * CUDA device.
+ *
+ * Arguments and outputs are those of gs_render (all outputs may be NULL).
+ * The work must fit the fixed scratch: about 52 B per (camera, Gaussian)
+ * record, 25 B per tile duplicate, 12 B per tile, 200 B per camera; larger
+ * requests are rejected with GS_ERR_CAPACITY before any output is written
+ * (the record part is checked before any GPU work, the duplicate part after
+ * counting them).  The call synchronises `stream` (to count duplicates) and
+ * returns GS_ERR_NONFINITE for non-finite Gaussian parameters.
+ *
+ * The first call on a device looks up the scratch's device address (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  Every call on a device reuses the same scratch and leaves
+ * its contents behind; the call clears what must start at zero.  Two calls
+ * that overlap on the GPU (different streams or threads at the same time)
+ * race on the scratch and produce undefined results: serialise them. */
+gs_status_t gs_render_noalloc(const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams, int n_cams,
+                              const gs_options_t *opt, float *rgb, float *depth, float *alpha, float *t_final,
+                              int32_t *last, gs_stream_t stream);
+
 /* Rigid transform of a submap by T (Eq. 8/9): mu <- R mu + t,
  * q <- q_R (x) q (so Sigma <- R Sigma R^T); scales, opacities, colours
  * unchanged.  out_means, out_quats [n][4] device (may alias the inputs). */

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1077,3 +1078,142 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// gs_render_noalloc: gs_render on a fixed device array instead of a context
+// arena, for callers that may not allocate device memory
+// ===========================================================================
+namespace {
+
+// the fixed scratch; every GPU that loads the library holds it until exit
+__device__ __align__(256) unsigned char g_noalloc_scratch[GS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+gs_status_t noalloc_scratch(void **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return GS_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return GS_OK;
+}
+
+// bump allocator over the fixed scratch (256-byte aligned pieces)
+struct FixedCarve {
+    char *base;
+    size_t off, cap;
+    template <typename T>
+    T *take(size_t count)
+    {
+        const size_t bytes = ((count ? count : 1) * sizeof(T) + 255) & ~(size_t)255;
+        if (off + bytes > cap)
+            return nullptr;
+        T *p = (T *)(base + off);
+        off += bytes;
+        return p;
+    }
+};
+
+}  // namespace
+
+extern "C" gs_status_t gs_render_noalloc(const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams,
+                                         int n_cams, const gs_options_t *opt, float *rgb, float *depth, float *alpha,
+                                         float *t_final, int32_t *last, gs_stream_t stream)
+{
+    gs_ctx *ctx = nullptr;  // no context: failures are reported by status only
+    GS_TRY(check_options(ctx, opt));
+    GS_TRY(check_gaussians(ctx, g, "submap"));
+    if (!poses || n_cams < 0 || (n_cams > 0 && !cams))
+        return GS_ERR_INVALID_ARG;
+    for (int c = 0; c < n_cams; ++c)
+        GS_TRY(check_camera(ctx, cams[c]));
+    cudaStream_t s = (cudaStream_t)stream;
+    void *base = nullptr;
+    GS_TRY(noalloc_scratch(&base));
+    Plan P = plan_for(g, cams, n_cams);
+    GS_TRY(finalize(ctx, P));
+    FixedCarve cv{(char *)base, 0, GS_NOALLOC_SCRATCH_BYTES};
+    const size_t R = P.n_records ? P.n_records : 1;
+    VpDesc *vps = cv.take<VpDesc>(P.vps.size());
+    GroupDesc *groups = cv.take<GroupDesc>(P.groups.size());
+    uint32_t *tile_vp = cv.take<uint32_t>(P.tile_vp.size());
+    Pipe p;
+    p.rec = cv.take<float4>(3 * R);
+    p.counts = cv.take<int32_t>(R);
+    p.partials = cv.take<uint32_t>(gsl::scan_partials(R));
+    p.ndups = cv.take<uint32_t>(4);
+    p.flags = cv.take<int>(4);
+    p.ranges = cv.take<uint2>(P.n_tiles ? P.n_tiles : 1);
+    if (!vps || !groups || !tile_vp || !p.rec || !p.counts || !p.partials || !p.ndups || !p.flags || !p.ranges)
+        return GS_ERR_CAPACITY;
+    if (!P.vps.empty() && cudaMemcpyAsync(vps, P.vps.data(), P.vps.size() * sizeof(VpDesc), cudaMemcpyHostToDevice,
+                                          s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    if (!P.groups.empty() && cudaMemcpyAsync(groups, P.groups.data(), P.groups.size() * sizeof(GroupDesc),
+                                             cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    if (!P.tile_vp.empty() && cudaMemcpyAsync(tile_vp, P.tile_vp.data(), P.tile_vp.size() * sizeof(uint32_t),
+                                              cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    DevPlan D;
+    D.vps = vps;
+    D.groups = groups;
+    D.tile_vp = tile_vp;
+    // the scratch keeps the previous call's contents: clear the status word
+    if (cudaMemsetAsync(p.flags, 0, sizeof(int), s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    gsl::project(project_args(P, D, p, poses, opt), s);
+    gsl::BinArgs b = bin_args(P, D, p);
+    gsl::bin_count(b, s);
+    uint32_t nd = 0;
+    if (cudaMemcpyAsync(&nd, p.ndups, sizeof nd, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    if (nd == 0xffffffffu)
+        return GS_ERR_CAPACITY;
+    const uint32_t cap = std::max<uint32_t>(nd, 1);
+    p.keys[0] = cv.take<uint64_t>(cap);
+    p.keys[1] = cv.take<uint64_t>(cap);
+    p.vals[0] = cv.take<uint32_t>(cap);
+    p.vals[1] = cv.take<uint32_t>(cap);
+    const size_t hn = gsl::sort_hist_entries(cap);
+    p.hist = cv.take<uint32_t>(hn);
+    p.histp = cv.take<uint32_t>(gsl::scan_partials(hn));
+    if (!p.keys[0] || !p.keys[1] || !p.vals[0] || !p.vals[1] || !p.hist || !p.histp)
+        return GS_ERR_CAPACITY;
+    p.cap = cap;
+    b = bin_args(P, D, p);
+    const int cur = gsl::bin(b, s);  // clears the tile ranges itself
+    gsl::RasterArgs r = raster_args(P, D, p, cur, opt);
+    r.out_rgb = rgb;
+    r.out_depth = depth;
+    r.out_alpha = alpha;
+    r.t_final = t_final;
+    r.last = last;
+    gsl::forward(r, false, s);
+    if (cudaGetLastError() != cudaSuccess)
+        return GS_ERR_CUDA;
+    int flags = 0;
+    if (cudaMemcpyAsync(&flags, p.flags, sizeof flags, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    return (flags & gsk::kFlagNonFinite) ? GS_ERR_NONFINITE : GS_OK;
+}

@@ -68,7 +68,7 @@ class gs_gaussian_grads_t(ctypes.Structure):
 
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
-           "gs_fuse", "gs_register", "gs_transform"]
+           "gs_fuse", "gs_register", "gs_transform", "gs_render_noalloc"]
 ABI_STRUCTS = [gs_gaussians_t, gs_camera_t, gs_view_t, gs_options_t, gs_stats_t, gs_gaussian_grads_t]
 
 _lock = threading.Lock()
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = False):
             "gs_fuse": ([P, I, P, P, P, P, P, P], I),
             "gs_register": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P], I),
             "gs_transform": ([P, P, P, P, P, P], I),
+            "gs_render_noalloc": ([P, P, P, I, P, P, P, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -361,3 +362,27 @@ def gs_transform(ctx: Context, g: Gaussians, T) -> Gaussians:
     ctx.check(ctx._lib.gs_transform(ctx.handle, ctypes.byref(gst), Th.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                     _ptr(q), _stream()))
     return Gaussians(m, g.log_scales4.clone(), q, g.logits.clone(), g.rgb4.clone())
+
+
+def gs_render_noalloc(g: Gaussians, poses: torch.Tensor, cams, opt=None, out=None):
+    """gs_render without a context and without any device allocation by the
+    library: its scratch is a fixed device array (see include/gsreg.h), for
+    callers whose host program forbids cudaMalloc / cudaFree at run time.
+    ``out`` may hold caller-allocated output tensors (rgb, depth, alpha,
+    t_final, last); missing ones are created here with torch.  Returns the
+    status code (0 = GS_OK) and the outputs."""
+    cam_arr, nc = cameras(cams)
+    opt = opt or default_options()
+    npx = _npix(cams)
+    dev = g.means4.device
+    out = dict(out or {})
+    out.setdefault("rgb", torch.empty(3 * npx, device=dev))
+    out.setdefault("depth", torch.empty(npx, device=dev))
+    out.setdefault("alpha", torch.empty(npx, device=dev))
+    out.setdefault("t_final", torch.empty(npx, device=dev))
+    out.setdefault("last", torch.empty(npx, dtype=torch.int32, device=dev))
+    gst = g.c_struct()
+    st = load().gs_render_noalloc(ctypes.byref(gst), _ptr(poses.contiguous()), cam_arr, nc, ctypes.byref(opt),
+                                  _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]), _ptr(out["t_final"]),
+                                  _ptr(out["last"]), _stream())
+    return st, out
