@@ -334,7 +334,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--iters", type=int, default=ITERS,
+                    help="iterations per loop edge (100 for the benchmark; fewer only for profiling captures)")
     args = ap.parse_args()
+    globals()["ITERS"] = args.iters
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

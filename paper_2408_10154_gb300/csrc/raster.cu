@@ -162,6 +162,33 @@ __global__ void __launch_bounds__(256) k_forward(const gsl::RasterArgs a)
     }
 }
 
+// Warp sums of N (8 or 16) values per lane.  Each exchange over a lane bit
+// halves the values a lane carries (it keeps the half its partner sends
+// away), so log2(N) halving steps plus log2(32/N) plain butterflies need
+// N - 1 + log2(32/N) shuffles instead of 5 N.  On return lane l holds the
+// full sum of value index l / (32 / N).
+template <int N>
+__device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int lane)
+{
+    int bit = 16;
+#pragma unroll
+    for (int h = N / 2; h >= 1; h /= 2) {
+        const bool up = (lane & bit) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+        bit >>= 1;
+    }
+    float s = v[0];
+#pragma unroll
+    for (int o = 32 / N / 2; o >= 1; o >>= 1)
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // d(screen params) of one (tile, Gaussian) -> camera-frame twist (w, v)
 // about c_cam, added to tw[6].  G = {dL/du, dL/dv, 2 dL/dSigma2D_00,
 // 2 dL/dSigma2D_01, 2 dL/dSigma2D_11, dL/dz, ...} (the 2D covariance is the
@@ -339,12 +366,16 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
+                constexpr int NP = NG <= 8 ? 8 : 16;
+                float v[NP];
 #pragma unroll
-                for (int k = 0; k < NG; ++k) {
-                    const float v = warp_sum(g[k]);
-                    if (lane == 0)
-                        s_slots[(k * 8 + warp) * 256 + j] = v;
-                }
+                for (int k = 0; k < NP; ++k)
+                    v[k] = k < NG ? g[k] : 0.0f;
+                const float sum = warp_sum_transpose<NP>(v, lane);
+                constexpr int L = 32 / NP;
+                const int k = lane / L;
+                if ((lane % L) == 0 && k < NG)
+                    s_slots[(k * 8 + warp) * 256 + j] = sum;
             }
         }
         __syncthreads();
