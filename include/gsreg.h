@@ -146,8 +146,9 @@ size_t gs_ctx_bytes(const gs_ctx_t *ctx);
 gs_status_t gs_ctx_stats(const gs_ctx_t *ctx, gs_stats_t *out);
 
 /* sizeof of the ABI structs, for binding checks (no device needed):
- * out[0..5] = gs_gaussians_t, gs_camera_t, gs_view_t, gs_options_t,
- * gs_stats_t, gs_gaussian_grads_t; returns the number written (<= n). */
+ * out[0..6] = gs_gaussians_t, gs_camera_t, gs_view_t, gs_options_t,
+ * gs_stats_t, gs_gaussian_grads_t, gs_problem_t; returns the number
+ * written (<= n). */
 int gs_abi_sizes(size_t *out, int n);
 
 /* -------------------------------------------------------------- rendering */
@@ -305,6 +306,29 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
 gs_status_t gs_render_noalloc(const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams, int n_cams,
                               const gs_options_t *opt, float *rgb, float *depth, float *alpha, float *t_final,
                               int32_t *last, gs_stream_t stream);
+
+/* One registration problem of a batch: submaps P (src) and Q (tgt) and
+ * their keyframes V^P, V^Q (Eq. 6); either keyframe list may be empty. */
+typedef struct {
+    gs_gaussians_t src, tgt;
+    const gs_view_t *src_views; /* host array of n_src_views */
+    int32_t n_src_views;
+    const gs_view_t *tgt_views; /* host array of n_tgt_views */
+    int32_t n_tgt_views;
+} gs_problem_t;
+
+/* Batched 3DGS registration (Sec. 3.2 for each problem): all keyframe
+ * problems of all n problems -- uneven submap sizes, keyframe counts and
+ * image sizes -- advance together, each iteration one projection pass per
+ * moving submap, one sort and one compositing launch over every tile of
+ * every keyframe, replayed from one CUDA graph; Eq. 7 fuses each problem.
+ *   T_out [n][12] host out; conf_out [n] host out;
+ *   eps_out [sum of keyframes] host out or NULL (problem-major, V^P first).
+ * Results equal n separate gs_register calls up to the order of floating
+ * point reductions (every reduction is per keyframe, so in practice bit-equal).
+ * Synchronises `stream`. */
+gs_status_t gs_register_batch(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt, int iters,
+                              double *T_out, double *conf_out, double *eps_out, gs_stream_t stream);
 
 /* Rigid transform of a submap by T (Eq. 8/9): mu <- R mu + t,
  * q <- q_R (x) q (so Sigma <- R Sigma R^T); scales, opacities, colours

@@ -470,6 +470,50 @@ __global__ void k_to_float(const double *in, float *out, int n)
         out[i] = (float)in[i];
 }
 
+// The keyframe problems of one registration problem (Sec. 3.2): keyframes
+// of P are localised in Q (Q moves; the estimate is inverted), keyframes of
+// Q in P (P moves).  Each moving submap is one Gaussian set.
+void add_problem(Plan &P, const gs_gaussians_t *src, const gs_gaussians_t *tgt, const gs_view_t *sv, int ns,
+                 const gs_view_t *tv, int nt, int problem, int &sets)
+{
+    if (ns > 0) {
+        const int set = sets++;
+        for (int k = 0; k < ns; ++k)
+            add_vp(P, tgt, sv[k].cam, set, problem, 1, sv[k].rgb, sv[k].depth);
+    }
+    if (nt > 0) {
+        const int set = sets++;
+        for (int k = 0; k < nt; ++k)
+            add_vp(P, src, tv[k].cam, set, problem, 0, tv[k].rgb, tv[k].depth);
+    }
+}
+
+gs_status_t check_views(gs_ctx *ctx, const gs_view_t *v, int n)
+{
+    if (n < 0 || (n > 0 && !v))
+        return fail(ctx, GS_ERR_INVALID_ARG, "bad keyframe list");
+    for (int k = 0; k < n; ++k) {
+        GS_TRY(check_camera(ctx, v[k].cam));
+        if (!v[k].rgb || !v[k].depth)
+            return fail(ctx, GS_ERR_INVALID_ARG, "null keyframe image");
+    }
+    return GS_OK;
+}
+
+gs_status_t check_problem(gs_ctx *ctx, const gs_problem_t &q)
+{
+    GS_TRY(check_gaussians(ctx, &q.src, "src"));
+    GS_TRY(check_gaussians(ctx, &q.tgt, "tgt"));
+    if (q.n_src_views + q.n_tgt_views <= 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "a problem without keyframes");
+    GS_TRY(check_views(ctx, q.src_views, q.n_src_views));
+    GS_TRY(check_views(ctx, q.tgt_views, q.n_tgt_views));
+    return GS_OK;
+}
+
+gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_options_t *opt, int iters,
+                             cudaStream_t s, double *T_out, double *conf_out, double *eps_out, double *est_out);
+
 }  // namespace
 
 // ===========================================================================
@@ -554,10 +598,10 @@ gs_status_t gs_ctx_stats(const gs_ctx_t *ctx, gs_stats_t *out)
 
 int gs_abi_sizes(size_t *out, int n)
 {
-    const size_t s[6] = {sizeof(gs_gaussians_t), sizeof(gs_camera_t), sizeof(gs_view_t), sizeof(gs_options_t),
-                         sizeof(gs_stats_t), sizeof(gs_gaussian_grads_t)};
+    const size_t s[7] = {sizeof(gs_gaussians_t), sizeof(gs_camera_t),  sizeof(gs_view_t),           sizeof(gs_options_t),
+                         sizeof(gs_stats_t),     sizeof(gs_gaussian_grads_t), sizeof(gs_problem_t)};
     int k = 0;
-    for (; out && k < n && k < 6; ++k)
+    for (; out && k < n && k < 7; ++k)
         out[k] = s[k];
     return k;
 }
@@ -837,14 +881,42 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
             return fail(ctx, GS_ERR_INVALID_ARG, "gs_register: null keyframe image");
     }
     DeviceGuard dg(ctx->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    // keyframes of P are localised in Q (Q moves; estimate inverted), those
-    // of Q in P (P moves).  Gaussian set 0 = Q, 1 = P.
     Plan P;
-    for (int k = 0; k < n_src_views; ++k)
-        add_vp(P, tgt, src_views[k].cam, 0, 0, 1, src_views[k].rgb, src_views[k].depth);
-    for (int k = 0; k < n_tgt_views; ++k)
-        add_vp(P, src, tgt_views[k].cam, n_src_views > 0 ? 1 : 0, 0, 0, tgt_views[k].rgb, tgt_views[k].depth);
+    int sets = 0;
+    add_problem(P, src, tgt, src_views, n_src_views, tgt_views, n_tgt_views, 0, sets);
+    return run_registration(ctx, P, 1, opt, iters, (cudaStream_t)stream, T_out, confidence, eps_out, est_out);
+}
+
+gs_status_t gs_register_batch(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt, int iters,
+                              double *T_out, double *conf_out, double *eps_out, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_options(ctx, opt));
+    if (n <= 0 || !problems || iters < 0 || !T_out || !conf_out)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_register_batch: bad arguments");
+    for (int i = 0; i < n; ++i)
+        GS_TRY(check_problem(ctx, problems[i]));
+    DeviceGuard dg(ctx->device);
+    Plan P;
+    int sets = 0;
+    for (int i = 0; i < n; ++i) {
+        const gs_problem_t &q = problems[i];
+        add_problem(P, &q.src, &q.tgt, q.src_views, q.n_src_views, q.tgt_views, q.n_tgt_views, i, sets);
+    }
+    return run_registration(ctx, P, n, opt, iters, (cudaStream_t)stream, T_out, conf_out, eps_out, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The registration engine behind gs_register and gs_register_batch: every
+// keyframe problem of the plan (any mix of submaps, keyframe counts and
+// image sizes) advances together, one CUDA graph per iteration.
+gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_options_t *opt, int iters,
+                             cudaStream_t s, double *T_out, double *conf_out, double *eps_out, double *est_out)
+{
     GS_TRY(finalize(ctx, P));
     DevPlan D;
     GS_TRY(upload_plan(ctx, P, D, s));
@@ -870,15 +942,19 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
     GS_TRY(wsT(ctx, S_CODE, npix, &code));
     GS_TRY(wsT(ctx, S_TLOSS, ntl, &tloss));
     GS_TRY(wsT(ctx, S_TTWIST, 6 * ntl, &ttw));
-    GS_TRY(wsT(ctx, S_TOUT, 12, &Tdev));
-    GS_TRY(wsT(ctx, S_CONF, 1, &confd));
+    GS_TRY(wsT(ctx, S_TOUT, 12 * (size_t)n_problems, &Tdev));
+    GS_TRY(wsT(ctx, S_CONF, (size_t)n_problems, &confd));
     GS_TRY(wsT(ctx, S_EST, 12 * (size_t)nv, &est));
-    std::vector<int32_t> revh(nv);
-    for (int v = 0; v < nv; ++v)
+    std::vector<int32_t> revh(nv), pfh(n_problems, 0), pch(n_problems, 0);
+    for (int v = 0; v < nv; ++v) {
         revh[v] = P.vps[v].reverse;
+        const int q = P.vps[v].problem;
+        if (pch[q]++ == 0)
+            pfh[q] = v;
+    }
     GS_TRY(upload(ctx, S_REV, revh, &rev, s));
-    GS_TRY(upload(ctx, S_PFIRST, std::vector<int32_t>{0}, &pf, s));
-    GS_TRY(upload(ctx, S_PCOUNT, std::vector<int32_t>{nv}, &pc, s));
+    GS_TRY(upload(ctx, S_PFIRST, pfh, &pf, s));
+    GS_TRY(upload(ctx, S_PCOUNT, pch, &pc, s));
 
     gsl::PoseArgs pa{};
     pa.vps = D.vps;
@@ -1029,7 +1105,7 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
         f.reverse = rev;
         f.prob_first = pf;
         f.prob_count = pc;
-        f.n_problems = 1;
+        f.n_problems = n_problems;
         f.T_out = Tdev;
         f.conf = confd;
         f.est_out = est;
@@ -1045,8 +1121,8 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
         }
         std::vector<double> epsh(nv);
         std::vector<unsigned long long> pairs_h(ntl);
-        GS_CUDA(cudaMemcpyAsync(T_out, Tdev, 12 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        GS_CUDA(cudaMemcpyAsync(confidence, confd, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(T_out, Tdev, 12 * sizeof(double) * n_problems, cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(conf_out, confd, sizeof(double) * n_problems, cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(epsh.data(), lossd, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(pairs_h.data(), pairs, ntl * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         if (est_out)
@@ -1077,7 +1153,7 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
     return fail(ctx, GS_ERR_CAPACITY, "tile duplicate lists kept outgrowing their capacity");
 }
 
-}  // extern "C"
+}  // namespace
 
 // ===========================================================================
 // gs_render_noalloc: gs_render on a fixed device array instead of a context

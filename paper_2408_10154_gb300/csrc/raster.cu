@@ -15,8 +15,9 @@
 // Backward: per (pixel, Gaussian) screen-space gradients are summed over
 // each warp with shuffles, over the tile's 8 warps in shared memory (fixed
 // order), chained through the projection into a camera-frame twist per
-// Gaussian, accumulated in FP64 per thread and reduced to one 6-vector per
-// tile by a block tree -- no global atomics, bit-reproducible.
+// Gaussian, accumulated per thread in FP32 with Kahan compensation and
+// reduced to one FP64 6-vector per tile by a block tree -- no global
+// atomics, bit-reproducible.
 #include <float.h>
 
 #include "gs_internal.cuh"
@@ -189,16 +190,33 @@ __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int lane)
     return s;
 }
 
+// Six running FP32 sums with Kahan compensation (the lost low-order part is
+// carried in c); the true sum is s - c.
+struct Twist6 {
+    float s[6], c[6];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            s[k] = c[k] = 0.0f;
+    }
+    __device__ __forceinline__ void add(int k, float v)
+    {
+        const float y = v - c[k];
+        const float t = s[k] + y;
+        c[k] = (t - s[k]) - y;
+        s[k] = t;
+    }
+};
+
 // d(screen params) of one (tile, Gaussian) -> camera-frame twist (w, v)
-// about c_cam, added to tw[6].  G = {dL/du, dL/dv, 2 dL/dSigma2D_00,
-// 2 dL/dSigma2D_01, 2 dL/dSigma2D_11, dL/dz, ...} (the 2D covariance is the
-// dilated one; dilation is constant).  S = scalar type of the arithmetic.
-template <typename S>
-__device__ __forceinline__ void chain_twist(const float *G, const float4 &q0, const float4 &q1, const float4 &x0,
-                                            const float4 &x1, float fxf, float fyf, const double *cc, double *tw)
+// about cc (camera frame), added to tw.  G = {dL/du, dL/dv,
+// 2 dL/dSigma2D_00, 2 dL/dSigma2D_01, 2 dL/dSigma2D_11, dL/dz, ...} (the 2D
+// covariance is the dilated one; dilation is constant).
+__device__ __forceinline__ void chain_twist(const float *G, const float4 &q1, const float4 &x0, const float4 &x1,
+                                            float fx, float fy, const float *cc, Twist6 &tw)
 {
-    (void)q0;
-    const S fx = fxf, fy = fyf;
+    using S = float;
     const S mx = x0.x, my = x0.y, mz = q1.z;
     const S S00 = x0.z, S01 = x0.w, S02 = x1.x, S11 = x1.y, S12 = x1.z, S22 = x1.w;
     // dL/dSigma2D = [[gp, gq], [gq, gs]]
@@ -225,22 +243,30 @@ __device__ __forceinline__ void chain_twist(const float *G, const float4 &q0, co
     const S k21 = (c02 * S01 + c12 * S11 + c22 * S12) - (S02 * c01 + S12 * c11 + S22 * c12);
     const S k02 = (c00 * S02 + c01 * S12 + c02 * S22) - (S00 * c02 + S01 * c12 + S02 * c22);
     const S k10 = (c01 * S00 + c11 * S01 + c12 * S02) - (S01 * c00 + S11 * c01 + S12 * c02);
-    const S rx = (S)(mx - cc[0]), ry = (S)(my - cc[1]), rz = (S)(mz - cc[2]);
-    tw[0] += (double)(ry * gz - rz * gy + S(2) * k21);
-    tw[1] += (double)(rz * gx - rx * gz + S(2) * k02);
-    tw[2] += (double)(rx * gy - ry * gx + S(2) * k10);
-    tw[3] += (double)gx;
-    tw[4] += (double)gy;
-    tw[5] += (double)gz;
+    const S rx = mx - cc[0], ry = my - cc[1], rz = mz - cc[2];
+    tw.add(0, ry * gz - rz * gy + S(2) * k21);
+    tw.add(1, rz * gx - rx * gz + S(2) * k02);
+    tw.add(2, rx * gy - ry * gx + S(2) * k10);
+    tw.add(3, gx);
+    tw.add(4, gy);
+    tw.add(5, gz);
 }
 
+// records staged per chunk of the adjoint (shared memory: 48 B + 4 B per
+// record, NG x 8 warps x 4 B per record for the per-warp gradient slots);
+// 128 records and 4 CTAs per SM (<= 64 registers) measured fastest on the
+// room workload among 256/3, 192/4, 128/4
+constexpr int kBwdChunk = 128;
+constexpr int kBwdMinBlocks = 4;
+static_assert(kBwdChunk <= 256, "one thread stages one record");
+
 template <bool REG, bool FULL>
-__global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
+__global__ void __launch_bounds__(256, kBwdMinBlocks) k_backward(const gsl::RasterArgs a)
 {
     constexpr int NG = FULL ? 10 : 6;
     extern __shared__ float s_slots[];  // [NG][8 warps][256]
-    __shared__ float4 s0[256], s1[256], s2[256];
-    __shared__ uint32_t s_rec[256];
+    __shared__ float4 s0[kBwdChunk], s1[kBwdChunk], s2[kBwdChunk];
+    __shared__ uint32_t s_rec[kBwdChunk];
     __shared__ int s_maxl[8];
     __shared__ double s_tw[8][6];
     const uint32_t t = blockIdx.x;
@@ -292,13 +318,14 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
     for (int w = 0; w < 8; ++w)
         maxl = max(maxl, s_maxl[w]);
 
-    const double cc[3] = {a.c_cam ? a.c_cam[3 * vp] : 0.0, a.c_cam ? a.c_cam[3 * vp + 1] : 0.0,
-                          a.c_cam ? a.c_cam[3 * vp + 2] : 0.0};
-    double tw[6] = {0, 0, 0, 0, 0, 0};
+    const float cc[3] = {a.c_cam ? (float)a.c_cam[3 * vp] : 0.0f, a.c_cam ? (float)a.c_cam[3 * vp + 1] : 0.0f,
+                         a.c_cam ? (float)a.c_cam[3 * vp + 2] : 0.0f};
+    Twist6 tw;
+    tw.zero();
     float T = Tf, Rr = a.bg[0], Rg = a.bg[1], Rb = a.bg[2], Rd = 0.0f;
     const float ga_tf = ga * Tf;
-    for (int hi = maxl; hi > 0; hi -= 256) {
-        const int lo = max(hi - 256, 0), cnt = hi - lo;
+    for (int hi = maxl; hi > 0; hi -= kBwdChunk) {
+        const int lo = max(hi - kBwdChunk, 0), cnt = hi - lo;
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
             const uint32_t r = a.vals[rg.x + lo + threadIdx.x];
@@ -308,7 +335,7 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
             s1[threadIdx.x] = R[1];
             s2[threadIdx.x] = R[2];
         }
-        for (int k = threadIdx.x; k < NG * 8 * 256; k += 256)
+        for (int k = threadIdx.x; k < NG * 8 * kBwdChunk; k += 256)
             s_slots[k] = 0.0f;
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
@@ -375,7 +402,7 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
                 constexpr int L = 32 / NP;
                 const int k = lane / L;
                 if ((lane % L) == 0 && k < NG)
-                    s_slots[(k * 8 + warp) * 256 + j] = sum;
+                    s_slots[(k * 8 + warp) * kBwdChunk + j] = sum;
             }
         }
         __syncthreads();
@@ -387,7 +414,7 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
                 float s = 0.0f;
 #pragma unroll
                 for (int w = 0; w < 8; ++w)
-                    s += s_slots[(k * 8 + w) * 256 + threadIdx.x];
+                    s += s_slots[(k * 8 + w) * kBwdChunk + threadIdx.x];
                 G[k] = s;
                 any |= s != 0.0f;
             }
@@ -399,15 +426,14 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
                     dst[k] = G[k];
             }
             if (any && a.tile_twist)
-                chain_twist<float>(G, s0[threadIdx.x], s1[threadIdx.x], a.aux[2 * (size_t)r],
-                                   a.aux[2 * (size_t)r + 1], d.fx, d.fy, cc, tw);
+                chain_twist(G, s1[threadIdx.x], a.aux[2 * (size_t)r], a.aux[2 * (size_t)r + 1], d.fx, d.fy, cc, tw);
         }
     }
     if (!a.tile_twist)
         return;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const double v = warp_sum(tw[k]);
+        const double v = warp_sum((double)tw.s[k] - (double)tw.c[k]);
         if (lane == 0)
             s_tw[warp][k] = v;
     }
@@ -424,7 +450,7 @@ __global__ void __launch_bounds__(256) k_backward(const gsl::RasterArgs a)
 template <bool REG, bool FULL>
 constexpr size_t bwd_smem()
 {
-    return (size_t)(FULL ? 10 : 6) * 8 * 256 * sizeof(float);
+    return (size_t)(FULL ? 10 : 6) * 8 * kBwdChunk * sizeof(float);
 }
 
 template <bool REG, bool FULL>

@@ -68,8 +68,7 @@ class gs_gaussian_grads_t(ctypes.Structure):
 
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
-           "gs_fuse", "gs_register", "gs_transform", "gs_render_noalloc"]
-ABI_STRUCTS = [gs_gaussians_t, gs_camera_t, gs_view_t, gs_options_t, gs_stats_t, gs_gaussian_grads_t]
+           "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc"]
 
 _lock = threading.Lock()
 _lib = None
@@ -110,12 +109,14 @@ def load(build_if_missing: bool = False):
             "gs_register": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P], I),
             "gs_transform": ([P, P, P, P, P, P], I),
             "gs_render_noalloc": ([P, P, P, I, P, P, P, P, P, P, P], I),
+            "gs_register_batch": ([P, P, I, P, I, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
         # the binding's struct layouts must be the library's
+        ABI_STRUCTS = abi_structs()
         sizes = (ctypes.c_size_t * len(ABI_STRUCTS))()
         L.gs_abi_sizes(sizes, len(ABI_STRUCTS))
         for st, sz in zip(ABI_STRUCTS, sizes):
@@ -386,3 +387,37 @@ def gs_render_noalloc(g: Gaussians, poses: torch.Tensor, cams, opt=None, out=Non
                                   _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]), _ptr(out["t_final"]),
                                   _ptr(out["last"]), _stream())
     return st, out
+
+
+class gs_problem_t(ctypes.Structure):
+    _fields_ = [("src", gs_gaussians_t), ("tgt", gs_gaussians_t), ("src_views", ctypes.c_void_p),
+                ("n_src_views", ctypes.c_int32), ("tgt_views", ctypes.c_void_p), ("n_tgt_views", ctypes.c_int32)]
+
+
+def gs_register_batch(ctx: Context, problems, iters, opt=None):
+    """Batched registration.  ``problems``: list of (src Gaussians, tgt
+    Gaussians, src_views, tgt_views) with views as in gs_register.  Returns
+    (T [n,3,4] float64, confidence [n], eps [sum of keyframes])."""
+    opt = opt or default_options()
+    n = len(problems)
+    arr = (gs_problem_t * n)()
+    keep = []
+    total = 0
+    for i, (s, t, sv, tv) in enumerate(problems):
+        sva, tva = _views(sv), _views(tv)
+        keep += [sva, tva]
+        arr[i] = gs_problem_t(s.c_struct(), t.c_struct(), ctypes.cast(sva, ctypes.c_void_p), len(sv),
+                              ctypes.cast(tva, ctypes.c_void_p), len(tv))
+        total += len(sv) + len(tv)
+    T = np.zeros((n, 12), np.float64)
+    conf = np.zeros(n, np.float64)
+    eps = np.zeros(max(total, 1), np.float64)
+    d = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    ctx.check(ctx._lib.gs_register_batch(ctx.handle, arr, n, ctypes.byref(opt), int(iters), d(T), d(conf), d(eps),
+                                         _stream()))
+    return T.reshape(n, 3, 4), conf, eps[:total]
+
+
+def abi_structs():
+    """The ABI structs in the order gs_abi_sizes reports them."""
+    return [gs_gaussians_t, gs_camera_t, gs_view_t, gs_options_t, gs_stats_t, gs_gaussian_grads_t, gs_problem_t]

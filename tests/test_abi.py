@@ -56,9 +56,10 @@ def test_default_options_match_the_oracle(lib):
 
 def test_structs_match_the_library(lib):
     from paper_2408_10154_gb300 import gsreg
-    sizes = (ctypes.c_size_t * 6)()
-    assert lib.gs_abi_sizes(sizes, 6) == 6
-    for st, sz in zip(gsreg.ABI_STRUCTS, sizes):
+    structs = gsreg.abi_structs()
+    sizes = (ctypes.c_size_t * len(structs))()
+    assert lib.gs_abi_sizes(sizes, len(structs)) == len(structs)
+    for st, sz in zip(structs, sizes):
         assert ctypes.sizeof(st) == sz, st.__name__
     assert ctypes.sizeof(gsreg.gs_camera_t) == 72 and ctypes.sizeof(gsreg.gs_options_t) == 4 * 17
 

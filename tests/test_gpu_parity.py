@@ -362,6 +362,36 @@ def test_registration_is_deterministic_and_zero_iters(gs, ctx):
         np.testing.assert_allclose(E, np.eye(3, 4), atol=1e-12)
 
 
+def _problem(gs, n, W, H, f, n_src, n_tgt, seed):
+    c = synth.small_case(n, W, H, f, n_views=max(n_src + n_tgt, 2), seed=seed, ls_mean=-3.3)
+    og = O.Gaussians.from_dict(c["gaussians"])
+    oq = O.transform(og, c["T_gt"])
+    cams_p = c["cams"][:n_src]
+    cams_q = synth.moved_cameras(c["cams"][n_src:n_src + n_tgt], c["T_gt"]) if n_tgt else []
+    sv = [(cam, dev(O.render(og, np.eye(3, 4), cam)["rgb"].astype(np.float32)),
+           dev(O.render(og, np.eye(3, 4), cam)["depth"].astype(np.float32))) for cam in cams_p]
+    tv = [(cam, dev(O.render(oq, np.eye(3, 4), cam)["rgb"].astype(np.float32)),
+           dev(O.render(oq, np.eye(3, 4), cam)["depth"].astype(np.float32))) for cam in cams_q]
+    src = gs.Gaussians.from_numpy(c["gaussians"])
+    tgt = gs.Gaussians(*[dev(a) for a in (oq.means4, oq.log_scales4, oq.quats4, oq.logits, oq.rgb4)])
+    return src, tgt, sv, tv
+
+
+def test_batched_registration_equals_separate_calls(gs, ctx):
+    # uneven problems: submap sizes, keyframe counts per direction, image
+    # sizes (ragged tiles) all differ; one batch vs one call per problem
+    probs = [_problem(gs, 900, 96, 64, 80.0, 1, 2, 31), _problem(gs, 300, 64, 40, 50.0, 2, 0, 32),
+             _problem(gs, 1500, 120, 90, 100.0, 2, 1, 33)]
+    T, conf, eps = gs.gs_register_batch(ctx, probs, 15)
+    off = 0
+    for i, (src, tgt, sv, tv) in enumerate(probs):
+        Ti, ci, ei, _ = gs.gs_register(ctx, src, tgt, sv, tv, 15)
+        np.testing.assert_array_equal(T[i], Ti)
+        assert conf[i] == ci
+        np.testing.assert_array_equal(eps[off:off + len(ei)], ei)
+        off += len(ei)
+
+
 def test_registration_profile_and_stats(gs, ctx):
     import ctypes
     gd, cams = ragged_case()
