@@ -447,16 +447,262 @@ __global__ void __launch_bounds__(256, kBwdMinBlocks) k_backward(const gsl::Rast
     }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint with two pixels per thread: 128 threads per 16x16 tile, warp w
+// owns rows 4w..4w+3 (lane -> column lane & 15, rows (lane >> 4) and +2).
+// Each staged record is evaluated for both pixels (two independent chains)
+// and their gradients are added before the warp reduction, which therefore
+// covers 64 pixels.
+// ---------------------------------------------------------------------------
+struct PixAdj {
+    float pxf, pyf, T, Tf, Rr, Rg, Rb, Rd, gr, gg, gb, gd, ga_tf;
+    int last;
+};
+
+template <bool REG>
+__device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const gsl::RasterArgs &a, int px, int py,
+                                             const float bg[3])
+{
+    P.pxf = (float)px + 0.5f;
+    P.pyf = (float)py + 0.5f;
+    P.Tf = 1.0f;
+    P.gr = P.gg = P.gb = P.gd = 0.0f;
+    float ga = 0.0f;
+    P.last = 0;
+    if (px < d.W && py < d.H) {
+        const int64_t HW = (int64_t)d.W * d.H;
+        const int64_t off = (int64_t)py * d.W + px;
+        const int64_t pix = d.pix_base + off;
+        P.Tf = a.t_final[pix];
+        P.last = a.last[pix];
+        if (REG) {
+            const uint32_t c = a.code[pix];
+            auto dec = [](uint32_t v) -> float { return v == 1u ? 1.0f : (v == 2u ? -1.0f : 0.0f); };
+            const float inv3 = 1.0f / (3.0f * (float)HW), inv1 = 1.0f / (float)HW;
+            P.gr = dec(c & 3u) * inv3;
+            P.gg = dec((c >> 2) & 3u) * inv3;
+            P.gb = dec((c >> 4) & 3u) * inv3;
+            P.gd = dec((c >> 6) & 3u) * inv1;
+        } else {
+            if (a.d_rgb) {
+                const float *dr = a.d_rgb + 3 * d.pix_base;
+                P.gr = dr[off];
+                P.gg = dr[HW + off];
+                P.gb = dr[2 * HW + off];
+            }
+            if (a.d_depth)
+                P.gd = a.d_depth[pix];
+            if (a.d_alpha)
+                ga = a.d_alpha[pix];
+        }
+    }
+    P.T = P.Tf;
+    P.Rr = bg[0];
+    P.Rg = bg[1];
+    P.Rb = bg[2];
+    P.Rd = 0.0f;
+    P.ga_tf = ga * P.Tf;
+}
+
+// One (pixel, Gaussian) pair of the back-to-front walk: the contract's
+// decisions, the transmittance recovery, the colour-behind update and the
+// screen-space gradient added to g.  Returns whether the pair contributed.
+template <bool FULL>
+__device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0, const float4 &q1,
+                                             const float4 *q2p, const gsl::RasterArgs &a, float *g)
+{
+    if (jj >= P.last)
+        return false;
+    float dx, dy;
+    const float power = exponent_at(q0, q1.x, P.pxf, P.pyf, dx, dy);
+    if (power > 0.0f || power < a.skip_below)
+        return false;
+    const float e = exp_ct(power);
+    const float x = mul_rn(q1.y, e);
+    const bool clamped = x > a.alpha_max;
+    const float alpha = clamped ? a.alpha_max : x;
+    if (alpha < a.alpha_min)
+        return false;
+    const float om = 1.0f - alpha;
+    const float Ti = __fdividef(P.T, om);
+    const float4 q2 = *q2p;
+    const float dal = Ti * (P.gr * (q2.x - P.Rr) + P.gg * (q2.y - P.Rg) + P.gb * (q2.z - P.Rb) + P.gd * (q1.z - P.Rd)) +
+                      __fdividef(P.ga_tf, om);
+    P.Rr = fmaf(alpha, q2.x, om * P.Rr);
+    P.Rg = fmaf(alpha, q2.y, om * P.Rg);
+    P.Rb = fmaf(alpha, q2.z, om * P.Rb);
+    P.Rd = fmaf(alpha, q1.z, om * P.Rd);
+    const float wgt = alpha * Ti;
+    g[5] = fmaf(P.gd, wgt, g[5]);
+    if (FULL) {
+        g[7] = fmaf(P.gr, wgt, g[7]);
+        g[8] = fmaf(P.gg, wgt, g[8]);
+        g[9] = fmaf(P.gb, wgt, g[9]);
+    }
+    if (!clamped) {
+        // d(exponent)/d(u, v) = (gu, gv) = -Q d; the exponent's gradient
+        // w.r.t. the 2D covariance is (Q d)(Q d)^T / 2, accumulated as twice that
+        const float dp = dal * alpha;
+        const float gu = fmaf(2.0f * q0.z, dx, q0.w * dy);
+        const float gv = fmaf(q0.w, dx, 2.0f * q1.x * dy);
+        const float g0 = dp * gu, g1 = dp * gv;
+        g[0] += g0;
+        g[1] += g1;
+        g[2] = fmaf(g0, gu, g[2]);
+        g[3] = fmaf(g0, gv, g[3]);
+        g[4] = fmaf(g1, gv, g[4]);
+        if (FULL)
+            g[6] = fmaf(dal, e, g[6]);
+    }
+    P.T = Ti;
+    return true;
+}
+
+constexpr int kBwd2Threads = 128;
+constexpr int kBwd2Warps = kBwd2Threads / 32;
+constexpr int kBwd2Chunk = 128;
+constexpr int kBwd2MinBlocks = 7;
+static_assert(kBwd2Chunk <= kBwd2Threads, "one thread stages one record");
+
+template <bool REG, bool FULL>
+__global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(const gsl::RasterArgs a)
+{
+    constexpr int NG = FULL ? 10 : 6;
+    extern __shared__ float s_slots[];  // [NG][warps][chunk]
+    __shared__ float4 s0[kBwd2Chunk], s1[kBwd2Chunk], s2[kBwd2Chunk];
+    __shared__ uint32_t s_rec[kBwd2Chunk];
+    __shared__ int s_maxl[kBwd2Warps];
+    __shared__ double s_tw[kBwd2Warps][6];
+    const uint32_t t = blockIdx.x;
+    const int vp = (int)a.tile_vp[t];
+    const VpDesc &d = a.vps[vp];
+    const uint32_t lt = t - d.tile_base;
+    const int tx = (int)(lt % (uint32_t)d.TX), ty = (int)(lt / (uint32_t)d.TX);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = tx * kTile + (lane & 15);
+    const int py0 = ty * kTile + warp * 4 + (lane >> 4);
+    const uint2 rg = a.ranges[t];
+    PixAdj P0, P1;
+    pix_adj_init<REG>(P0, d, a, px, py0, a.bg);
+    pix_adj_init<REG>(P1, d, a, px, py0 + 2, a.bg);
+    int ml = max(P0.last, P1.last);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        ml = max(ml, __shfl_xor_sync(0xffffffffu, ml, o));
+    if (lane == 0)
+        s_maxl[warp] = ml;
+    __syncthreads();
+    int maxl = 0;
+#pragma unroll
+    for (int w = 0; w < kBwd2Warps; ++w)
+        maxl = max(maxl, s_maxl[w]);
+
+    const float cc[3] = {a.c_cam ? (float)a.c_cam[3 * vp] : 0.0f, a.c_cam ? (float)a.c_cam[3 * vp + 1] : 0.0f,
+                         a.c_cam ? (float)a.c_cam[3 * vp + 2] : 0.0f};
+    Twist6 tw;
+    tw.zero();
+    for (int hi = maxl; hi > 0; hi -= kBwd2Chunk) {
+        const int lo = max(hi - kBwd2Chunk, 0), cnt = hi - lo;
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            const uint32_t r = a.vals[rg.x + lo + threadIdx.x];
+            s_rec[threadIdx.x] = r;
+            const float4 *R = a.rec + 3 * (size_t)r;
+            s0[threadIdx.x] = R[0];
+            s1[threadIdx.x] = R[1];
+            s2[threadIdx.x] = R[2];
+        }
+        for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwd2Chunk; k += kBwd2Threads)
+            s_slots[k] = 0.0f;
+        __syncthreads();
+        // this warp's pixels never reach past wl: skip the list tail
+        const int wl = min(s_maxl[warp] - lo, cnt);
+        for (int j = wl - 1; j >= 0; --j) {
+            float g[NG];
+#pragma unroll
+            for (int k = 0; k < NG; ++k)
+                g[k] = 0.0f;
+            const float4 q0 = s0[j];
+            const float4 q1 = s1[j];
+            const bool c0 = pix_adj_pair<FULL>(P0, lo + j, q0, q1, &s2[j], a, g);
+            const bool c1 = pix_adj_pair<FULL>(P1, lo + j, q0, q1, &s2[j], a, g);
+            if (__any_sync(0xffffffffu, c0 || c1)) {
+                constexpr int NP = NG <= 8 ? 8 : 16;
+                float v[NP];
+#pragma unroll
+                for (int k = 0; k < NP; ++k)
+                    v[k] = k < NG ? g[k] : 0.0f;
+                const float sum = warp_sum_transpose<NP>(v, lane);
+                constexpr int L = 32 / NP;
+                const int k = lane / L;
+                if ((lane % L) == 0 && k < NG)
+                    s_slots[(k * kBwd2Warps + warp) * kBwd2Chunk + j] = sum;
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            float G[NG];
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+                float s = 0.0f;
+#pragma unroll
+                for (int w = 0; w < kBwd2Warps; ++w)
+                    s += s_slots[(k * kBwd2Warps + w) * kBwd2Chunk + threadIdx.x];
+                G[k] = s;
+                any |= s != 0.0f;
+            }
+            const uint32_t r = s_rec[threadIdx.x];
+            if (FULL) {
+                float *dst = a.dup_grads + (size_t)(rg.x + lo + threadIdx.x) * 10;
+#pragma unroll
+                for (int k = 0; k < NG; ++k)
+                    dst[k] = G[k];
+            }
+            if (any && a.tile_twist)
+                chain_twist(G, s1[threadIdx.x], a.aux[2 * (size_t)r], a.aux[2 * (size_t)r + 1], d.fx, d.fy, cc, tw);
+        }
+    }
+    if (!a.tile_twist)
+        return;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double v = warp_sum((double)tw.s[k] - (double)tw.c[k]);
+        if (lane == 0)
+            s_tw[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kBwd2Warps; ++w)
+            s += s_tw[w][threadIdx.x];
+        a.tile_twist[(size_t)t * 6 + threadIdx.x] = s;
+    }
+}
+
+template <bool REG, bool FULL>
+constexpr size_t bwd2_smem()
+{
+    return (size_t)(FULL ? 10 : 6) * kBwd2Warps * kBwd2Chunk * sizeof(float);
+}
+
 template <bool REG, bool FULL>
 constexpr size_t bwd_smem()
 {
     return (size_t)(FULL ? 10 : 6) * 8 * kBwdChunk * sizeof(float);
 }
 
+// adjoint variant: 2 = two pixels per thread (k_backward2), 1 = one (k_backward)
+constexpr int kBwdPixelsPerThread = 2;
+
 template <bool REG, bool FULL>
 void launch_backward(const gsl::RasterArgs &a, cudaStream_t s)
 {
-    k_backward<REG, FULL><<<a.n_tiles, 256, bwd_smem<REG, FULL>(), s>>>(a);
+    if (kBwdPixelsPerThread == 2)
+        k_backward2<REG, FULL><<<a.n_tiles, kBwd2Threads, bwd2_smem<REG, FULL>(), s>>>(a);
+    else
+        k_backward<REG, FULL><<<a.n_tiles, 256, bwd_smem<REG, FULL>(), s>>>(a);
     ++gsl::g_launches;
 }
 
@@ -478,6 +724,8 @@ void forward(const RasterArgs &a, bool registration, cudaStream_t s)
 {
     if (a.n_tiles == 0)
         return;
+    // (a two-pixels-per-thread forward measured slower: 0.82 vs 0.76 ms on
+    // the room workload; the early stop favours one pixel per thread)
     if (registration)
         k_forward<true><<<a.n_tiles, 256, 0, s>>>(a);
     else
