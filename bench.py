@@ -327,6 +327,83 @@ def cpu_baseline(c):
             "seconds": float(sum(per))}
 
 
+def run_batched(args):
+    """Batched uneven registration: the 32 submap pairs of the batched
+    workload (20k-400k Gaussians, 4-12 keyframes per submap at 640x480 or
+    1200x680, offsets up to 15 deg / 25 cm), each pair in both directions,
+    registered (a) one pair per call ("plain", gs_register) and (b) all
+    pairs in one batch (gs_register_batch).  Prints one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2408_10154_gb300 as gs
+    from paper_2408_10154_gb300 import synth
+    ctx = gs.Context(0, 96 << 30)
+    wl = synth.batched_pairs()
+    problems, px = [], 0
+    for pr in wl["pairs"]:
+        src = gs.Gaussians.from_numpy(pr["gaussians"])
+        tgt = gs.gs_transform(ctx, src, pr["T_gt"])
+        k = len(pr["src_cams"])
+        I = torch.tensor(np.stack([np.eye(3, 4)] * k).reshape(k, 12), dtype=torch.float32, device="cuda")
+        rs = gs.gs_render(ctx, src, I, pr["src_cams"])
+        rt = gs.gs_render(ctx, tgt, I, pr["tgt_cams"])
+        sv = list(zip(pr["src_cams"], [x.contiguous() for x in gs.split_views(rs["rgb"], pr["src_cams"], 3)],
+                      [x.contiguous() for x in gs.split_views(rs["depth"], pr["src_cams"], 1)]))
+        tv = list(zip(pr["tgt_cams"], [x.contiguous() for x in gs.split_views(rt["rgb"], pr["tgt_cams"], 3)],
+                      [x.contiguous() for x in gs.split_views(rt["depth"], pr["tgt_cams"], 1)]))
+        problems.append((src, tgt, sv, tv))
+        px += sum(int(c[4]) * int(c[5]) for c in list(pr["src_cams"]) + list(pr["tgt_cams"]))
+    iters = ITERS
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev0.record()
+        out = fn()
+        ev1.record()
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1), out
+
+    def plain():
+        lat = []
+        for p in problems:
+            t, _ = timed(lambda: gs.gs_register(ctx, *p, iters))
+            lat.append(t)
+        return lat
+
+    def batched():
+        return gs.gs_register_batch(ctx, problems, iters)
+
+    for _ in range(max(args.warmup, 1)):
+        batched()
+        plain()
+    plain_runs, batch_runs = [], []
+    for _ in range(args.steps):
+        lat = plain()
+        plain_runs.append(lat)
+        t, res = timed(batched)
+        batch_runs.append(t)
+    plain_ms = float(np.mean([sum(l) for l in plain_runs]))
+    batch_ms = float(np.mean(batch_runs))
+    lat_all = sorted(x for l in plain_runs for x in l)
+    out = {"metric": METRIC, "value": len(problems) * iters / (batch_ms / 1000.0), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batched_32: 32 uneven submap pairs (20k-400k Gaussians, 4-12 keyframes per "
+                                  "submap at 640x480 / 1200x680), both directions, %d iterations" % iters,
+                      "pixels_per_iteration": px, "step": "all 32 loop edges, one registration iteration"},
+           "batched": {"ms_per_batch": batch_ms, "edges_per_s": len(problems) / (batch_ms / 1000.0),
+                       "mpx_per_s": px * iters / (batch_ms / 1000.0) / 1e6},
+           "plain": {"ms_per_batch": plain_ms, "edges_per_s": len(problems) / (plain_ms / 1000.0),
+                     "mpx_per_s": px * iters / (plain_ms / 1000.0) / 1e6,
+                     "edge_latency_ms": {"p50": float(np.percentile(lat_all, 50)),
+                                         "p99": float(np.percentile(lat_all, 99))}},
+           "batched_over_plain": plain_ms / batch_ms}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,12 +411,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="room_150k", choices=["room_150k", "batched_32"],
+                    help="room_150k: the benchmark line; batched_32: batched vs one-pair-per-call")
     ap.add_argument("--iters", type=int, default=ITERS,
                     help="iterations per loop edge (100 for the benchmark; fewer only for profiling captures)")
     args = ap.parse_args()
     globals()["ITERS"] = args.iters
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched_32":
+        return run_batched(args)
     return run_ours(args)
 
 

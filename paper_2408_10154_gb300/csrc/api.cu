@@ -20,7 +20,7 @@ enum Slot {
     S_VPS, S_GROUPS, S_TILEVP, S_POSE32, S_REC, S_AUX, S_COUNTS, S_PARTIALS, S_NDUPS, S_K0, S_K1, S_V0, S_V1,
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
-    S_PAIRS, S_COUNT
+    S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_COUNT
 };
 
 struct Buf {
@@ -303,7 +303,19 @@ struct Pipe {
     uint2 *ranges = nullptr;
     int *flags = nullptr;
     uint32_t cap = 0;
+    // two-stage binning
+    uint32_t *dkeys[2] = {nullptr, nullptr}, *dvals[2] = {nullptr, nullptr};
+    uint32_t *tkeys[2] = {nullptr, nullptr};
+    uint32_t *n_vis = nullptr;
+    uint64_t n_records = 0;
 };
+
+// Binning route of the context-based entry points: the two-stage route
+// (depth sort of the visible records, then a tile sort of 32-bit keys)
+// moves about a quarter of the bytes of one sort of 64-bit (tile, depth)
+// keys and yields the same lists.  gs_render_noalloc keeps the one-stage
+// route, so the two are cross-checked by its test.
+constexpr bool kTwoStageBinning = true;
 
 gs_status_t alloc_pipe(gs_ctx *ctx, const Plan &P, bool aux, Pipe &p)
 {
@@ -316,6 +328,14 @@ gs_status_t alloc_pipe(gs_ctx *ctx, const Plan &P, bool aux, Pipe &p)
     GS_TRY(wsT(ctx, S_NDUPS, 4, &p.ndups));
     GS_TRY(wsT(ctx, S_RANGES, P.n_tiles ? P.n_tiles : 1, &p.ranges));
     GS_TRY(wsT(ctx, S_FLAGS, 4, &p.flags));
+    if (kTwoStageBinning) {
+        GS_TRY(wsT(ctx, S_DK0, R, &p.dkeys[0]));
+        GS_TRY(wsT(ctx, S_DK1, R, &p.dkeys[1]));
+        GS_TRY(wsT(ctx, S_DV0, R, &p.dvals[0]));
+        GS_TRY(wsT(ctx, S_DV1, R, &p.dvals[1]));
+        GS_TRY(wsT(ctx, S_NVIS, 4, &p.n_vis));
+    }
+    p.n_records = R;
     return GS_OK;
 }
 
@@ -324,15 +344,25 @@ gs_status_t alloc_sort(gs_ctx *ctx, uint64_t want, Pipe &p)
     if (want > 0xfff00000ull)
         return fail(ctx, GS_ERR_CAPACITY, "more than 2^32 tile duplicates");
     const uint32_t cap = (uint32_t)std::max<uint64_t>(want, 1024);
-    GS_TRY(wsT(ctx, S_K0, cap, &p.keys[0]));
-    GS_TRY(wsT(ctx, S_K1, cap, &p.keys[1]));
+    if (kTwoStageBinning) {
+        GS_TRY(wsT(ctx, S_K0, cap, &p.tkeys[0]));
+        GS_TRY(wsT(ctx, S_K1, cap, &p.tkeys[1]));
+    } else {
+        GS_TRY(wsT(ctx, S_K0, cap, &p.keys[0]));
+        GS_TRY(wsT(ctx, S_K1, cap, &p.keys[1]));
+    }
     GS_TRY(wsT(ctx, S_V0, cap, &p.vals[0]));
     GS_TRY(wsT(ctx, S_V1, cap, &p.vals[1]));
-    const size_t hn = gsl::sort_hist_entries(cap);
+    const size_t hn = gsl::sort_hist_entries((uint32_t)std::max<uint64_t>(cap, p.n_records));
     GS_TRY(wsT(ctx, S_HIST, hn, &p.hist));
     GS_TRY(wsT(ctx, S_HISTP, gsl::scan_partials(hn), &p.histp));
     p.cap = cap;
     return GS_OK;
+}
+
+int run_bin(const gsl::BinArgs &b, cudaStream_t s)
+{
+    return kTwoStageBinning ? gsl::bin2(b, s) : gsl::bin(b, s);
 }
 
 gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, const float *pose32,
@@ -375,6 +405,12 @@ gsl::BinArgs bin_args(const Plan &P, const DevPlan &D, const Pipe &p)
     b.ranges = p.ranges;
     b.n_tiles = (uint32_t)P.n_tiles;
     b.flags = p.flags;
+    for (int k = 0; k < 2; ++k) {
+        b.dkeys[k] = p.dkeys[k];
+        b.dvals[k] = p.dvals[k];
+        b.tkeys[k] = p.tkeys[k];
+    }
+    b.n_vis = p.n_vis;
     return b;
 }
 
@@ -414,7 +450,7 @@ gs_status_t project_and_bin(gs_ctx *ctx, const Plan &P, const DevPlan &D, Pipe &
     if (p.cap < nd || !p.keys[0])
         GS_TRY(alloc_sort(ctx, nd, p));
     b = bin_args(P, D, p);
-    *cur = gsl::bin(b, s);
+    *cur = run_bin(b, s);
     if (n_dups_out)
         *n_dups_out = nd;
     GS_CUDA(cudaGetLastError());
@@ -657,6 +693,15 @@ gs_status_t gs_bin(gs_ctx_t *ctx, const float *records, const int32_t *counts, c
     GS_TRY(wsT(ctx, S_FLAGS, 4, &p.flags));
     GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
     p.ranges = (uint2 *)ranges;
+    const size_t R = P.n_records ? P.n_records : 1;
+    p.n_records = R;
+    if (kTwoStageBinning) {
+        GS_TRY(wsT(ctx, S_DK0, R, &p.dkeys[0]));
+        GS_TRY(wsT(ctx, S_DK1, R, &p.dkeys[1]));
+        GS_TRY(wsT(ctx, S_DV0, R, &p.dvals[0]));
+        GS_TRY(wsT(ctx, S_DV1, R, &p.dvals[1]));
+        GS_TRY(wsT(ctx, S_NVIS, 4, &p.n_vis));
+    }
     gsl::BinArgs b = bin_args(P, D, p);
     gsl::bin_count(b, s);
     uint32_t nd = 0;
@@ -667,9 +712,12 @@ gs_status_t gs_bin(gs_ctx_t *ctx, const float *records, const int32_t *counts, c
         return fail(ctx, GS_ERR_CAPACITY, "gs_bin: " + std::to_string(nd) + " duplicates exceed capacity");
     GS_TRY(alloc_sort(ctx, nd, p));
     b = bin_args(P, D, p);
-    const int cur = gsl::bin(b, s);
+    const int cur = run_bin(b, s);
     if (nd > 0) {
-        GS_CUDA(cudaMemcpyAsync(keys, p.keys[cur], sizeof(uint64_t) * nd, cudaMemcpyDeviceToDevice, s));
+        if (kTwoStageBinning)
+            gsl::keys64(b, cur, keys, s);
+        else
+            GS_CUDA(cudaMemcpyAsync(keys, p.keys[cur], sizeof(uint64_t) * nd, cudaMemcpyDeviceToDevice, s));
         GS_CUDA(cudaMemcpyAsync(vals, p.vals[cur], sizeof(uint32_t) * nd, cudaMemcpyDeviceToDevice, s));
     }
     GS_CUDA(cudaGetLastError());
@@ -723,8 +771,11 @@ gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const flo
     GS_TRY(check_common(ctx, g, cams, n_cams, opt));
     if (!poses || !t_final || !last)
         return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward: null poses or forward state");
-    if (grads && (grads->means || grads->log_scales || grads->quats || grads->opacity_logits || grads->rgb))
-        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward: per-Gaussian gradients are not available");
+    const bool full = grads && (grads->means || grads->log_scales || grads->quats || grads->opacity_logits ||
+                                grads->rgb);
+    if (full && ((grads->means && !aligned16(grads->means)) || (grads->log_scales && !aligned16(grads->log_scales)) ||
+                 (grads->quats && !aligned16(grads->quats)) || (grads->rgb && !aligned16(grads->rgb))))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward: gradient float4 arrays must be 16-byte aligned");
     DeviceGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     Plan P = plan_for(g, cams, n_cams);
@@ -755,7 +806,37 @@ gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const flo
         ++gsl::g_launches;
     }
     r.c_cam = ccam;
-    gsl::backward(r, false, false, s);
+    if (full)
+        GS_TRY(wsT(ctx, S_DUPG, 10 * (size_t)p.cap, &r.dup_grads));
+    gsl::backward(r, false, full, s);
+    if (full) {
+        // group the duplicates by record, then chain per Gaussian
+        uint32_t *rk[2] = {nullptr, nullptr}, *rp[2] = {nullptr, nullptr};
+        uint2 *rr = nullptr;
+        GS_TRY(wsT(ctx, S_RK0, p.cap, &rk[0]));
+        GS_TRY(wsT(ctx, S_RK1, p.cap, &rk[1]));
+        GS_TRY(wsT(ctx, S_RP0, p.cap, &rp[0]));
+        GS_TRY(wsT(ctx, S_RP1, p.cap, &rp[1]));
+        GS_TRY(wsT(ctx, S_RRANGES, (size_t)p.n_records, &rr));
+        gsl::ParamArgs pa{};
+        pa.vps = D.vps;
+        pa.n_vps = nv;
+        pa.n = (int)g->n;
+        pa.rec = p.rec;
+        pa.aux = p.aux;
+        pa.pose32 = poses;
+        pa.dup_grads = r.dup_grads;
+        pa.quats = (const float4 *)g->quats;
+        pa.scales = (const float4 *)g->log_scales;
+        pa.logits = g->opacity_logits;
+        pa.g_means = grads->means;
+        pa.g_scales = grads->log_scales;
+        pa.g_quats = grads->quats;
+        pa.g_logits = grads->opacity_logits;
+        pa.g_rgb = grads->rgb;
+        gsl::param_grads(pa, p.vals[cur], p.ndups, p.cap, rk, rp, tile_bits(P.n_records), p.hist, p.histp, rr,
+                         (uint32_t)P.n_records, s);
+    }
     gsl::PoseArgs a{};
     a.vps = D.vps;
     a.n_vps = nv;
@@ -1025,7 +1106,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             mark(0, st);
             gsl::project(project_args(P, D, p, pose32, opt), st);
             mark(1, st);
-            const int c = gsl::bin(b, st);
+            const int c = run_bin(b, st);
             mark(2, st);
             r.vals = p.vals[c];
             gsl::forward(r, true, st);
@@ -1093,7 +1174,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         // residual eps at the final poses, then Eq. 7
         r.tile_pairs = nullptr;
         gsl::project(project_args(P, D, p, pose32, opt), s);
-        r.vals = p.vals[gsl::bin(b, s)];
+        r.vals = p.vals[run_bin(b, s)];
         gsl::forward(r, true, s);
         gsl::PoseArgs fa = pa;
         fa.tile_twist = nullptr;

@@ -176,7 +176,8 @@ __device__ __forceinline__ uint32_t live_count(const uint32_t *n_dups, uint32_t 
     return n < cap ? n : cap;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint64_t *keys, const uint32_t *n_dups, uint32_t cap,
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const K *keys, const uint32_t *n_dups, uint32_t cap,
                                                           int shift, uint32_t *hist, uint32_t nblk)
 {
     __shared__ uint32_t h[kSortThreads / 32][256];
@@ -189,8 +190,10 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint64_t *keys, 
 #pragma unroll
     for (int k = 0; k < kSortKPT; ++k) {
         const uint32_t i = base + k * kSortThreads + threadIdx.x;
-        if (i < n)
-            atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 0xffu], 1u);
+        const uint32_t d = i < n ? (uint32_t)(keys[i] >> shift) & 0xffu : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && (uint32_t)(__ffs(peers) - 1) == (threadIdx.x & 31u))
+            atomicAdd(&h[warp][d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     uint32_t s = 0;
@@ -204,10 +207,11 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint64_t *keys, 
 // rounds of 32 consecutive keys (match_any finds equal digits), so ranks
 // follow input order within the block; digit-major scanned histograms give
 // the block's base per digit.
-__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint64_t *kin, const uint32_t *vin,
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const K *kin, const uint32_t *vin,
                                                              const uint32_t *n_dups, uint32_t cap, int shift,
                                                              const uint32_t *hist_scanned, uint32_t nblk,
-                                                             uint64_t *kout, uint32_t *vout)
+                                                             K *kout, uint32_t *vout)
 {
     __shared__ uint32_t cnt[kSortThreads / 32][256];
     __shared__ uint32_t s_base[256];
@@ -219,13 +223,13 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint64_t *kin
     const uint32_t n = live_count(n_dups, cap);
     const uint32_t base = blockIdx.x * kSortTile + warp * (32 * kSortKPT);
     const unsigned lt = lanemask_lt();
-    uint64_t key[kSortKPT];
+    K key[kSortKPT];
     uint32_t val[kSortKPT], off[kSortKPT], dig[kSortKPT];
 #pragma unroll
     for (int r = 0; r < kSortKPT; ++r) {
         const uint32_t i = base + r * 32 + lane;
         const bool valid = i < n;
-        key[r] = valid ? kin[i] : 0ull;
+        key[r] = valid ? kin[i] : K(0);
         val[r] = valid ? vin[i] : 0u;
         const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 0xffu : 256u;
         dig[r] = d;
@@ -263,20 +267,209 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint64_t *kin
 }
 
 // ---------------------------------------------------------------- ranges
-__global__ void k_ranges(const uint64_t *keys, const uint32_t *n_dups, uint32_t cap, uint2 *ranges)
+// tile of a key: the high word of a 64-bit (tile << 32 | depth) key, or a
+// 32-bit tile key itself
+__device__ __forceinline__ uint32_t tile_of(uint64_t k) { return (uint32_t)(k >> 32); }
+__device__ __forceinline__ uint32_t tile_of(uint32_t k) { return k; }
+
+template <typename K>
+__global__ void k_ranges(const K *keys, const uint32_t *n_dups, uint32_t cap, uint2 *ranges)
 {
     const uint32_t n = live_count(n_dups, cap);
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t)
+    const uint32_t t = tile_of(keys[i]);
+    if (i == 0 || tile_of(keys[i - 1]) != t)
         ranges[t].x = i;
-    if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t)
+    if (i == n - 1 || tile_of(keys[i + 1]) != t)
         ranges[t].y = i + 1;
 }
 
+// ---------------------------------------------------------------- two-stage binning
+// Stage 1 sorts the visible records by depth (stable, ties by record
+// index); stage 2 emits their duplicates in that order with 32-bit tile
+// keys and sorts them stably by tile.  The per-tile order is (depth bits,
+// record index), the same as a stable sort of (tile << 32 | depth) keys
+// emitted in record order, with 4-byte keys and 2 tile passes instead of 6
+// passes over 8-byte keys.
+
+// visible records per block of kScanTile records
+__global__ void __launch_bounds__(kScanThreads) k_vis_partials(const int32_t *counts, uint32_t n, uint32_t *partials)
+{
+    __shared__ uint32_t s[kScanThreads / 32];
+    const uint32_t base = blockIdx.x * kScanTile;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanTile / kScanThreads; ++k) {
+        const uint32_t i = base + k * kScanThreads + threadIdx.x;
+        acc += (i < n && counts[i] > 0) ? 1u : 0u;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0)
+        s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < kScanThreads / 32 ? s[threadIdx.x] : 0u;
+        v = warp_sum(v);
+        if (threadIdx.x == 0)
+            partials[blockIdx.x] = v;
+    }
+}
+
+// compacts the visible records (record order) with their depth bits
+__global__ void __launch_bounds__(kScanThreads) k_vis_compact(const int32_t *counts, const float4 *rec, uint32_t n,
+                                                             const uint32_t *blk_base, uint32_t *dkeys, uint32_t *dvals)
+{
+    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
+    constexpr int K = kScanTile / kScanThreads;
+    const uint32_t first = blockIdx.x * kScanTile + threadIdx.x * K;
+    uint32_t f[K], sum = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        f[k] = (first + k < n && counts[first + k] > 0) ? 1u : 0u;
+        sum += f[k];
+    }
+    uint32_t tot;
+    uint32_t pos = block_excl_scan<kScanThreads>(sum, s_warp, tot) + blk_base[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (f[k]) {
+            const uint32_t r = first + k;
+            dkeys[pos] = __float_as_uint(rec[3 * (size_t)r + 1].z);
+            dvals[pos] = r;
+            ++pos;
+        }
+    }
+}
+
+// tile count of each depth-sorted visible record (0 past the live count)
+__global__ void k_sorted_counts(const int32_t *counts, const uint32_t *dvals, const uint32_t *n_vis, uint32_t n,
+                                uint32_t *out)
+{
+    const uint32_t nv = live_count(n_vis, n);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        out[i] = i < nv ? (uint32_t)counts[dvals[i]] : 0u;
+}
+
+// largest i in [0, n) with a[i] <= t, for non-decreasing a with a[0] <= t:
+// a 32-ary search by one warp (each round narrows the range 32-fold)
+__device__ __forceinline__ uint32_t warp_last_le(const uint32_t *a, uint32_t n, uint32_t t)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t p = lo + lane * step;
+        const unsigned m = __ballot_sync(0xffffffffu, p < hi && a[p] <= t) | 1u;
+        const uint32_t nlo = lo + (uint32_t)(31 - __clz(m)) * step;
+        hi = min(nlo + step, hi);
+        lo = nlo;
+    }
+    const uint32_t p = lo + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, p < hi && a[p] <= t) | 1u;
+    return lo + (uint32_t)(31 - __clz(m));
+}
+
+// Emits the duplicates [b*kScanTile, (b+1)*kScanTile) of the depth-sorted
+// visible records (offsets = exclusive scan of their tile counts) with
+// 32-bit tile keys.  Work is split by duplicates, not by records, so the
+// few near-camera splats covering thousands of tiles (all at the front of
+// the depth order) do not serialise one block.  A block touches at most
+// kScanTile records because every visible record has at least one tile.
+__global__ void __launch_bounds__(kScanThreads) k_emit_balanced(const gsl::BinArgs a, const uint32_t *dvals,
+                                                               const uint32_t *offs, uint32_t *tkeys, uint32_t *vals)
+{
+    __shared__ uint32_t s_off[kScanTile];
+    __shared__ uint32_t s_t0[kScanTile];
+    __shared__ uint32_t s_geo[kScanTile];
+    __shared__ uint32_t s_rec[kScanTile];
+    __shared__ uint32_t s_r[2];
+    const uint32_t total = *a.n_dups;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && total > a.capacity)
+        atomicOr(a.flags, kFlagCapacity);
+    const uint32_t nd = total < a.capacity ? total : a.capacity;
+    const uint32_t b0 = blockIdx.x * kScanTile;
+    if (b0 >= nd)
+        return;
+    const uint32_t b1 = min(b0 + (uint32_t)kScanTile, nd);
+    const uint32_t nv = live_count(a.n_vis, a.n_records);
+    if (nv == 0)
+        return;
+    if (threadIdx.x < 64) {
+        const uint32_t r = warp_last_le(offs, nv, threadIdx.x < 32 ? b0 : b1 - 1);
+        if ((threadIdx.x & 31) == 0)
+            s_r[threadIdx.x >> 5] = r;
+    }
+    __syncthreads();
+    const uint32_t r0 = s_r[0];
+    if (s_r[1] < r0 || s_r[1] - r0 >= (uint32_t)kScanTile)
+        return;  // offsets not monotone (a saturated count): nothing sound to emit
+    const uint32_t nr = s_r[1] - r0 + 1;
+    for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x) {
+        const uint32_t r = dvals[r0 + k];
+        // keyframe of record r: the last vp whose records start at or before r
+        int lo = 0, hi = a.n_vps - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.vps[mid].rec_base <= r) lo = mid; else hi = mid - 1;
+        }
+        const gsk::VpDesc &d = a.vps[lo];
+        const uint32_t rx = __float_as_uint(a.rec[3 * (size_t)r + 1].w);
+        const uint32_t ry = __float_as_uint(a.rec[3 * (size_t)r + 2].w);
+        const uint32_t x0 = rx & 0xffffu, x1 = rx >> 16, y0 = ry & 0xffffu;
+        s_off[k] = offs[r0 + k];
+        s_t0[k] = d.tile_base + y0 * (uint32_t)d.TX + x0;
+        s_geo[k] = (x1 - x0) | ((uint32_t)d.TX << 16);
+        s_rec[k] = r;
+    }
+    __syncthreads();
+    for (uint32_t j = b0 + threadIdx.x; j < b1; j += blockDim.x) {
+        uint32_t lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t local = j - s_off[lo];
+        const uint32_t geo = s_geo[lo];
+        const uint32_t w = geo & 0xffffu, TX = geo >> 16;
+        tkeys[j] = s_t0[lo] + (local / w) * TX + local % w;
+        vals[j] = s_rec[lo];
+    }
+}
+
+// 64-bit (tile << 32 | depth bits) keys of a tile-sorted list (for gs_bin)
+__global__ void k_keys64(const uint32_t *tkeys, const uint32_t *vals, const float4 *rec, const uint32_t *n_dups,
+                         uint32_t cap, uint64_t *keys)
+{
+    const uint32_t n = live_count(n_dups, cap);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        keys[i] = ((uint64_t)tkeys[i] << 32) | __float_as_uint(rec[3 * (size_t)vals[i] + 1].z);
+}
+
 inline uint32_t div_up(size_t a, size_t b) { return (uint32_t)((a + b - 1) / b); }
+
+// stable LSD radix sort of (key, value) over `bits` low key bits, 8 per pass;
+// returns the buffer index holding the result
+template <typename K>
+int radix_sort(K *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits, uint32_t *hist,
+               uint32_t *hist_partials, cudaStream_t s)
+{
+    const uint32_t sb = div_up(cap ? cap : 1, kSortTile);
+    const size_t hn = (size_t)256 * sb;
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_rs_hist<K><<<sb, kSortThreads, 0, s>>>(keys[cur], n_dev, cap, shift, hist, sb);
+        gsl::scan_excl(hist, hist, hn, hist_partials, nullptr, s);
+        k_rs_scatter<K><<<sb, kSortThreads, 0, s>>>(keys[cur], vals[cur], n_dev, cap, shift, hist, sb, keys[cur ^ 1],
+                                                    vals[cur ^ 1]);
+        gsl::g_launches += 2;
+        cur ^= 1;
+    }
+    return cur;
+}
 
 }  // namespace
 
@@ -301,6 +494,47 @@ void bin_count(const BinArgs &a, cudaStream_t s)
     k_scan_partials<<<nb, kScanThreads, 0, s>>>((const uint32_t *)a.counts, a.n_records, a.partials);
     k_scan_top<<<1, 1024, 0, s>>>(a.partials, nb, a.n_dups);
     g_launches += 2;
+}
+
+int sort_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits, uint32_t *hist,
+             uint32_t *hist_partials, cudaStream_t s)
+{
+    return radix_sort<uint32_t>(keys, vals, n_dev, cap, bits, hist, hist_partials, s);
+}
+
+int bin2(const BinArgs &a, cudaStream_t s)
+{
+    const uint32_t R = a.n_records;
+    const uint32_t nb = div_up(R ? R : 1, kScanTile);
+    k_vis_partials<<<nb, kScanThreads, 0, s>>>(a.counts, R, a.partials);
+    k_scan_top<<<1, 1024, 0, s>>>(a.partials, nb, a.n_vis);
+    k_vis_compact<<<nb, kScanThreads, 0, s>>>(a.counts, a.rec, R, a.partials, a.dkeys[0], a.dvals[0]);
+    g_launches += 3;
+    uint32_t *dk[2] = {a.dkeys[0], a.dkeys[1]}, *dv[2] = {a.dvals[0], a.dvals[1]};
+    const int dc = radix_sort<uint32_t>(dk, dv, a.n_vis, R, 32, a.hist, a.hist_partials, s);
+    // tile counts in depth order and their exclusive scan (total = n_dups),
+    // in the depth-key buffers the sort no longer needs
+    uint32_t *cnt = dk[dc], *offs = dk[dc ^ 1];
+    k_sorted_counts<<<div_up(R ? R : 1, 256), 256, 0, s>>>(a.counts, dv[dc], a.n_vis, R, cnt);
+    ++g_launches;
+    scan_excl(cnt, offs, R, a.partials, a.n_dups, s);
+    k_emit_balanced<<<div_up(a.capacity ? a.capacity : 1, kScanTile), kScanThreads, 0, s>>>(a, dv[dc], offs,
+                                                                                          a.tkeys[0], a.vals[0]);
+    ++g_launches;
+    uint32_t *tk[2] = {a.tkeys[0], a.tkeys[1]}, *tv[2] = {a.vals[0], a.vals[1]};
+    const int tc = radix_sort<uint32_t>(tk, tv, a.n_dups, a.capacity, a.key_bits - 32, a.hist, a.hist_partials, s);
+    cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.n_tiles, s);
+    k_ranges<uint32_t><<<div_up(a.capacity ? a.capacity : 1, 256), 256, 0, s>>>(tk[tc], a.n_dups, a.capacity,
+                                                                                a.ranges);
+    ++g_launches;
+    return tc;
+}
+
+void keys64(const BinArgs &a, int cur, uint64_t *out, cudaStream_t s)
+{
+    k_keys64<<<div_up(a.capacity ? a.capacity : 1, 256), 256, 0, s>>>(a.tkeys[cur], a.vals[cur], a.rec, a.n_dups,
+                                                                      a.capacity, out);
+    ++g_launches;
 }
 
 int bin(const BinArgs &a, cudaStream_t s)

@@ -198,9 +198,20 @@ struct BinArgs {
     uint2 *ranges;            // [total tiles]
     uint32_t n_tiles;
     int *flags;
+    // two-stage binning (bin2): depth sort of the visible records, then a
+    // tile sort of 32-bit tile keys
+    uint32_t *dkeys[2], *dvals[2];  // [n_records]
+    uint32_t *tkeys[2];             // [capacity]
+    uint32_t *n_vis;                // device scalar
 };
 // emits, sorts and ranges; returns which buffer holds the sorted result
 int bin(const BinArgs &a, cudaStream_t s);
+// the same result by the two-stage route (depth sort of visible records,
+// tile sort of duplicates); the sorted values are in vals[return], the tile
+// keys in tkeys[return]
+int bin2(const BinArgs &a, cudaStream_t s);
+// 64-bit keys (tile << 32 | depth bits) of a bin2 result
+void keys64(const BinArgs &a, int cur, uint64_t *out, cudaStream_t s);
 void bin_count(const BinArgs &a, cudaStream_t s);  // scan only: n_dups
 size_t sort_hist_entries(uint32_t capacity);
 
@@ -272,6 +283,29 @@ void loss(const gsk::VpDesc *vps, int n_vps, uint32_t n_tiles, const uint32_t *t
           const float *depth, double *loss, float *d_rgb, float *d_depth, float *tile_loss, cudaStream_t s);
 void transform(const float4 *means, const float4 *quats, int64_t n, const double *T, float4 *out_means,
                float4 *out_quats, cudaStream_t s);
+
+// stable LSD radix sort of 32-bit keys with 32-bit values over `bits` low
+// bits (device-side count); returns the buffer index of the result
+int sort_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits, uint32_t *hist,
+             uint32_t *hist_partials, cudaStream_t s);
+
+// adjoint to every Gaussian parameter of one submap seen by n_vps cameras
+struct ParamArgs {
+    const gsk::VpDesc *vps;
+    int n_vps;
+    int n;                    // Gaussians
+    const float4 *rec, *aux;  // records of the forward
+    const float *pose32;      // [vp][12]
+    const float *dup_grads;   // [dups][10] screen gradients, tile-sorted order
+    const uint32_t *rpos;     // dup positions grouped by record (filled by param_grads)
+    const uint2 *rec_ranges;  // [records] (filled by param_grads)
+    const float4 *quats, *scales;
+    const float *logits;
+    float *g_means, *g_scales, *g_quats, *g_logits, *g_rgb;  // outputs (any may be null)
+};
+void param_grads(const ParamArgs &a, const uint32_t *sorted_recs, const uint32_t *n_dups, uint32_t cap,
+                 uint32_t *rkeys[2], uint32_t *rpos[2], int rec_bits, uint32_t *hist, uint32_t *hist_partials,
+                 uint2 *rec_ranges, uint32_t n_records, cudaStream_t s);
 
 
 }  // namespace gsl

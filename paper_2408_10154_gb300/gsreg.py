@@ -285,17 +285,27 @@ def split_views(flat, cams, channels):
 
 
 def gs_render_backward(ctx: Context, g: Gaussians, poses, cams, t_final, last, d_rgb=None, d_depth=None,
-                       d_alpha=None, pivots=None, opt=None):
+                       d_alpha=None, pivots=None, opt=None, params=False):
+    """Pose twist gradient [n_cams, 6]; with ``params`` also the per-Gaussian
+    gradients as a dict in the submap layout (means4, log_scales4, quats4,
+    logits, rgb4)."""
     cam_arr, nc = cameras(cams)
     opt = opt or default_options()
     dev = g.means4.device
     pose_grad = torch.empty((nc, 6), dtype=torch.float32, device=dev)
     gst = g.c_struct()
+    out, grads = None, None
+    if params:
+        out = dict(means4=torch.empty_like(g.means4), log_scales4=torch.empty_like(g.log_scales4),
+                   quats4=torch.empty_like(g.quats4), logits=torch.empty_like(g.logits), rgb4=torch.empty_like(g.rgb4))
+        grads = ctypes.byref(gs_gaussian_grads_t(out["means4"].data_ptr(), out["log_scales4"].data_ptr(),
+                                                 out["quats4"].data_ptr(), out["logits"].data_ptr(),
+                                                 out["rgb4"].data_ptr()))
     ctx.check(ctx._lib.gs_render_backward(ctx.handle, ctypes.byref(gst), _ptr(poses.contiguous()), cam_arr, nc,
                                           ctypes.byref(opt), _ptr(t_final), _ptr(last), _ptr(d_rgb),
-                                          _ptr(d_depth), _ptr(d_alpha), _ptr(pivots), _ptr(pose_grad), None,
+                                          _ptr(d_depth), _ptr(d_alpha), _ptr(pivots), _ptr(pose_grad), grads,
                                           _stream()))
-    return pose_grad
+    return (pose_grad, out) if params else pose_grad
 
 
 def gs_loss(ctx: Context, cams, rgb, depth, t_rgb, t_depth):
