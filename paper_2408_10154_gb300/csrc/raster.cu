@@ -53,15 +53,50 @@ __device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float p
     return fma_rn(h, dx, k);
 }
 
+// Warp-level cull of a staged record against the warp's pixel patch.  The
+// record can only pass the alpha test (alpha >= alpha_min) where its exact
+// exponent is at least tau = ln(alpha_min / o); that region is the ellipse
+// d^T Q d <= -2 tau (Q the conic), inside the axis-aligned box of half-sizes
+// sqrt(-2 tau Sigma00), sqrt(-2 tau Sigma11) about (u, v).  The record is
+// dropped for the warp only when every pixel sample of the patch
+// [xa, xb] x [ya, yb] lies outside that box, with margins that cover the
+// FP32 evaluation of the exponent (tau lowered by 0.06, the box widened by
+// 0.1 % + 0.01 px; conics with |B| > 0.999 sqrt(AC), where the FP32
+// exponent loses that accuracy, are never dropped).  A dropped pair would
+// have been skipped by the alpha test, so every result is unchanged; the
+// cull only removes iterations (most of a tile's list misses a given 8x4
+// patch).  NaN anywhere keeps the record.
+__device__ __forceinline__ bool patch_may_hit(const float4 &q0, float cc, float o, float xa, float xb, float ya,
+                                              float yb, float cut)
+{
+    const float A = -2.0f * q0.z, B = -q0.w, C = -2.0f * cc;
+    const float AC = A * C, BB = B * B;
+    const float tau = cut - __logf(o);  // cut = ln(alpha_min) - 0.06
+    if (tau >= 0.0f)
+        return false;  // o < alpha_min e^-0.06: no pixel can reach alpha_min
+    const float det = AC - BB;
+    if (!(det > 0.0f) || !(BB <= 0.998f * AC))
+        return true;
+    const float s = (-2.0f * tau) / det;
+    const float ex = fmaf(sqrtf(s * C), 1.001f, 0.01f), ey = fmaf(sqrtf(s * A), 1.001f, 0.01f);
+    const bool out = (q0.x + ex < xa) || (q0.x - ex > xb) || (q0.y + ey < ya) || (q0.y - ey > yb);
+    return !out;
+}
+
 template <bool REG>
-__global__ void __launch_bounds__(256) k_forward(const gsl::RasterArgs a)
+__global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
 {
     __shared__ float4 s0[256], s1[256], s2[256];
+    __shared__ uint8_t s_sel[8][256];  // per warp: batch positions that may hit its patch
     __shared__ float s_red[8];
     const uint32_t t = blockIdx.x;
     const VpDesc &d = a.vps[a.tile_vp[t]];
     const PixelCoord p = pixel_of(d, t);
     const float pxf = (float)p.px + 0.5f, pyf = (float)p.py + 0.5f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float xa = pxf - (float)(lane & 7), xb = xa + 7.0f, ya = pyf - (float)(lane >> 3), yb = ya + 3.0f;
+    const bool cull = a.alpha_min > 0.0f;
+    const float cut = a.skip_below - 0.01f;
     const uint2 rg = a.ranges[t];
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     int last = 0;
@@ -78,8 +113,21 @@ __global__ void __launch_bounds__(256) k_forward(const gsl::RasterArgs a)
         }
         __syncthreads();
         const int cnt = (int)min(256u, rg.y - b);
+        int nsel = 0;
+        if (!__all_sync(0xffffffffu, done)) {
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                const int j = j0 + lane;
+                const bool keep = j < cnt && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].y, xa, xb, ya, yb, cut));
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep)
+                    s_sel[warp][nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
+                nsel += __popc(m);
+            }
+            __syncwarp();
+        }
         if (!done) {
-            for (int j = 0; j < cnt; ++j) {
+            for (int k = 0; k < nsel; ++k) {
+                const int j = s_sel[warp][k];
                 const float4 q0 = s0[j];
                 const float4 q1 = s1[j];
                 float dx, dy;
@@ -571,6 +619,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     extern __shared__ float s_slots[];  // [NG][warps][chunk]
     __shared__ float4 s0[kBwd2Chunk], s1[kBwd2Chunk], s2[kBwd2Chunk];
     __shared__ uint32_t s_rec[kBwd2Chunk];
+    __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
     __shared__ int s_maxl[kBwd2Warps];
     __shared__ double s_tw[kBwd2Warps][6];
     const uint32_t t = blockIdx.x;
@@ -581,6 +630,11 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = tx * kTile + (lane & 15);
     const int py0 = ty * kTile + warp * 4 + (lane >> 4);
+    // the warp's pixel samples: a 16x4 patch
+    const float xa = (float)(tx * kTile) + 0.5f, xb = xa + 15.0f;
+    const float ya = (float)(ty * kTile + warp * 4) + 0.5f, yb = ya + 3.0f;
+    const bool cull = a.alpha_min > 0.0f;
+    const float cut = a.skip_below - 0.01f;
     const uint2 rg = a.ranges[t];
     PixAdj P0, P1;
     pix_adj_init<REG>(P0, d, a, px, py0, a.bg);
@@ -617,7 +671,18 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
         __syncthreads();
         // this warp's pixels never reach past wl: skip the list tail
         const int wl = min(s_maxl[warp] - lo, cnt);
-        for (int j = wl - 1; j >= 0; --j) {
+        int nsel = 0;
+        for (int j0 = 0; j0 < wl; j0 += 32) {
+            const int j = j0 + lane;
+            const bool keep = j < wl && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].y, xa, xb, ya, yb, cut));
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep)
+                s_sel[warp][nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
+            nsel += __popc(m);
+        }
+        __syncwarp();
+        for (int k = nsel - 1; k >= 0; --k) {
+            const int j = s_sel[warp][k];
             float g[NG];
 #pragma unroll
             for (int k = 0; k < NG; ++k)

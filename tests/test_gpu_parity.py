@@ -78,7 +78,21 @@ def ragged_case():
     return c["gaussians"], c["cams"]
 
 
-CASES = {"plain_2k": plain_case, "ragged_100x70": ragged_case}
+def needle_case():
+    # needle-shaped splats (one axis x4.5, one x0.08) in all orientations,
+    # half of them with opacities at the alpha_min threshold: the regime
+    # where the compositing kernels' per-warp cull is closest to its margins
+    c = synth.small_case(1500, 300, 200, 200.0, n_views=2, seed=21, ls_mean=-3.2, ls_std=0.3)
+    g = {k: np.array(v, copy=True) for k, v in c["gaussians"].items()}
+    rng = np.random.default_rng(21)
+    g["log_scales4"][:, 0] += 1.5
+    g["log_scales4"][:, 1] -= 2.5
+    near = rng.random(len(g["logits"])) < 0.5
+    g["logits"][near] = rng.normal(-5.55, 0.15, int(near.sum()))
+    return g, c["cams"]
+
+
+CASES = {"plain_2k": plain_case, "ragged_100x70": ragged_case, "needles_300x200": needle_case}
 
 
 # ----------------------------------------------------------------- projection
