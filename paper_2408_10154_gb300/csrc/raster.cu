@@ -257,6 +257,57 @@ struct Twist6 {
     }
 };
 
+// hi + lo += bhi + blo without losing the rounding error of the high parts
+// (Knuth's TwoSum: e is exactly the error of hi + bhi); FP32 only -- the
+// FP64 pipe of this part is a small fraction of its FP32 rate.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float bhi, float blo)
+{
+    const float s = hi + bhi;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (bhi - bp);
+    hi = s;
+    lo = lo + blo + e;
+}
+
+// The tile's twist: each warp reduces its lanes' compensated sums with
+// TwoSum butterflies, lane 0 leaves hi + lo in FP64, and threads 0..5 add
+// the warps in FP64 in a fixed order.
+template <int WARPS>
+__device__ __forceinline__ void store_tile_twist(const Twist6 &tw, double (*s_tw)[6], double *out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float hi = tw.s[k], lo = -tw.c[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
+            two_sum_add(hi, lo, bh, bl);
+        }
+        if (lane == 0)
+            s_tw[warp][k] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w)
+            s += s_tw[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// camera-frame pivot of keyframe vp as floats, converted once per CTA
+__device__ __forceinline__ void load_pivot(const double *c_cam, int vp, float *s_cc, float *cc)
+{
+    if (threadIdx.x < 3)
+        s_cc[threadIdx.x] = c_cam ? (float)c_cam[3 * vp + threadIdx.x] : 0.0f;
+    __syncthreads();
+    cc[0] = s_cc[0];
+    cc[1] = s_cc[1];
+    cc[2] = s_cc[2];
+}
+
 // d(screen params) of one (tile, Gaussian) -> camera-frame twist (w, v)
 // about cc (camera frame), added to tw.  G = {dL/du, dL/dv,
 // 2 dL/dSigma2D_00, 2 dL/dSigma2D_01, 2 dL/dSigma2D_11, dL/dz, ...} (the 2D
@@ -366,8 +417,9 @@ __global__ void __launch_bounds__(256, kBwdMinBlocks) k_backward(const gsl::Rast
     for (int w = 0; w < 8; ++w)
         maxl = max(maxl, s_maxl[w]);
 
-    const float cc[3] = {a.c_cam ? (float)a.c_cam[3 * vp] : 0.0f, a.c_cam ? (float)a.c_cam[3 * vp + 1] : 0.0f,
-                         a.c_cam ? (float)a.c_cam[3 * vp + 2] : 0.0f};
+    __shared__ float s_cc[3];
+    float cc[3];
+    load_pivot(a.c_cam, vp, s_cc, cc);
     Twist6 tw;
     tw.zero();
     float T = Tf, Rr = a.bg[0], Rg = a.bg[1], Rb = a.bg[2], Rd = 0.0f;
@@ -479,20 +531,7 @@ __global__ void __launch_bounds__(256, kBwdMinBlocks) k_backward(const gsl::Rast
     }
     if (!a.tile_twist)
         return;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const double v = warp_sum((double)tw.s[k] - (double)tw.c[k]);
-        if (lane == 0)
-            s_tw[warp][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w)
-            s += s_tw[w][threadIdx.x];
-        a.tile_twist[(size_t)t * 6 + threadIdx.x] = s;
-    }
+    store_tile_twist<8>(tw, s_tw, a.tile_twist + (size_t)t * 6);
 }
 
 // ---------------------------------------------------------------------------
@@ -651,8 +690,9 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     for (int w = 0; w < kBwd2Warps; ++w)
         maxl = max(maxl, s_maxl[w]);
 
-    const float cc[3] = {a.c_cam ? (float)a.c_cam[3 * vp] : 0.0f, a.c_cam ? (float)a.c_cam[3 * vp + 1] : 0.0f,
-                         a.c_cam ? (float)a.c_cam[3 * vp + 2] : 0.0f};
+    __shared__ float s_cc[3];
+    float cc[3];
+    load_pivot(a.c_cam, vp, s_cc, cc);
     Twist6 tw;
     tw.zero();
     for (int hi = maxl; hi > 0; hi -= kBwd2Chunk) {
@@ -730,20 +770,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     }
     if (!a.tile_twist)
         return;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const double v = warp_sum((double)tw.s[k] - (double)tw.c[k]);
-        if (lane == 0)
-            s_tw[warp][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kBwd2Warps; ++w)
-            s += s_tw[w][threadIdx.x];
-        a.tile_twist[(size_t)t * 6 + threadIdx.x] = s;
-    }
+    store_tile_twist<kBwd2Warps>(tw, s_tw, a.tile_twist + (size_t)t * 6);
 }
 
 template <bool REG, bool FULL>
