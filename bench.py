@@ -38,8 +38,17 @@ WORKLOAD = ("room_150k: 150,000-Gaussian room submap pair (10 deg / 15 cm), 8+8 
             "100 iterations fwd+bwd+update in both directions, residual + Eq. 7 fusion")
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # FP32 operations of the dominant kernels per unit of work
-BWD_FLOPS_PER_PAIR = 80.0
-FWD_FLOPS_PER_PAIR = 45.0
+# (FMA = 2).  Every (pixel, Gaussian) pair the compositing walks costs the
+# exponent (9); a pair that passes the alpha test costs 34 more in the
+# forward (exp32, alpha, transmittance, 4 blends) and 73 more in the adjoint
+# (exp32, alpha, T by division, dL/dalpha, colour-behind recursion, screen
+# and 2D-covariance gradients).
+FLOPS_WALKED = 9.0
+FWD_FLOPS_CONTRIB = 34.0
+BWD_FLOPS_CONTRIB = 73.0
+# DRAM bytes per adjoint launch of the room workload from one ncu capture of
+# the current kernel (profiles/k_backward2_room_150k.md); None if stale
+BWD_TRAFFIC_BYTES = None
 SMS = 152
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -198,7 +207,7 @@ def run_ours(args):
         torch.distributed.barrier()
     sampler = ClockSampler(device)
     sampler.start()
-    times, phases, launches, pairs, dups, results = [], np.zeros(5), 0, 0, 0, []
+    times, phases, launches, pairs, contrib, dups, results = [], np.zeros(5), 0, 0, 0, 0, []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.zero_()  # evict L2 between timed calls (outside the timed region)
@@ -211,6 +220,7 @@ def run_ours(args):
         phases += np.array(list(st.phase_ms))
         launches += st.kernel_launches
         pairs += st.pairs
+        contrib += st.contributing
         dups = st.n_dups
         results.append(res)
     torch.cuda.synchronize()
@@ -258,13 +268,17 @@ def run_ours(args):
     per_launch_ms = phases / (calls * ITERS)
     dom = int(np.argmax(per_launch_ms))
     pairs_per_launch = pairs / (calls * ITERS)
+    contrib_per_launch = contrib / (calls * ITERS)
     peak_fp32 = SMS * FP32_LANES * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
     if names[dom] in ("backward", "forward"):
-        fl = BWD_FLOPS_PER_PAIR if names[dom] == "backward" else FWD_FLOPS_PER_PAIR
-        achieved = pairs_per_launch * fl / (per_launch_ms[dom] / 1000.0) / 1e12
-        roof = {"kernel": f"k_{names[dom]}", "bound": "alu", "achieved": achieved, "peak": peak_fp32,
-                "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (of derived)"}
+        fc = BWD_FLOPS_CONTRIB if names[dom] == "backward" else FWD_FLOPS_CONTRIB
+        flops = FLOPS_WALKED * pairs_per_launch + fc * contrib_per_launch
+        achieved = flops / (per_launch_ms[dom] / 1000.0) / 1e12
+        roof = {"kernel": "k_backward2" if names[dom] == "backward" else "k_forward", "bound": "alu",
+                "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+                "traffic": BWD_TRAFFIC_BYTES if names[dom] == "backward" else None,
+                "flops_per_launch": flops,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock (derived; no measured FP32 peak)"}
     else:
         hbm = pk.get("hbm_gbs", 6800.0)
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
@@ -280,7 +294,8 @@ def run_ours(args):
         "mpx_per_s": value * px / 1e6,
         "edge_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "phase_ms_per_iteration": {n: float(v) for n, v in zip(names, per_launch_ms)},
-        "pairs_per_iteration": pairs_per_launch, "dups": int(dups),
+        "pairs_per_iteration": pairs_per_launch, "contributing_pairs_per_iteration": contrib_per_launch,
+        "dups": int(dups),
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,

@@ -122,6 +122,8 @@ typedef struct {
      * iterations: project, bin (scan+emit+sort+ranges), forward+loss,
      * backward, pose update */
     double phase_ms[5];
+    int64_t contributing;    /* sum over iterations of the (pixel, Gaussian) pairs that pass the
+                                alpha test before the early stop (the pairs that carry gradient) */
 } gs_stats_t;
 
 /* ---------------------------------------------------------------- context */

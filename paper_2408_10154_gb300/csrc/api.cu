@@ -1059,7 +1059,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
     pa.update = 1;
 
     unsigned long long *pairs = nullptr;
-    GS_TRY(wsT(ctx, S_PAIRS, ntl, &pairs));
+    GS_TRY(wsT(ctx, S_PAIRS, 2 * ntl, &pairs));  // per tile: walked, contributing
     const bool prof = opt->profile != 0 && iters > 0;
     if (prof) {
         for (cudaEvent_t &e : ctx->tev)
@@ -1117,7 +1117,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             mark(5, st);
         };
         GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
-        GS_CUDA(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * ntl, s));
+        GS_CUDA(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * 2 * ntl, s));
         if (iters > 0) {
             GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
             const long long c0 = gsl::g_launches;
@@ -1201,11 +1201,12 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             continue;
         }
         std::vector<double> epsh(nv);
-        std::vector<unsigned long long> pairs_h(ntl);
+        std::vector<unsigned long long> pairs_h(2 * ntl);
         GS_CUDA(cudaMemcpyAsync(T_out, Tdev, 12 * sizeof(double) * n_problems, cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(conf_out, confd, sizeof(double) * n_problems, cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(epsh.data(), lossd, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
-        GS_CUDA(cudaMemcpyAsync(pairs_h.data(), pairs, ntl * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(pairs_h.data(), pairs, 2 * ntl * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                s));
         if (est_out)
             GS_CUDA(cudaMemcpyAsync(est_out, est, 12 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaStreamSynchronize(s));
@@ -1214,8 +1215,10 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         st.n_dups = nd;
         st.n_pixels = P.n_pix;
         st.iterations = iters;
-        for (unsigned long long v : pairs_h)
-            st.pairs += (int64_t)v;
+        for (size_t k = 0; k < ntl; ++k) {
+            st.pairs += (int64_t)pairs_h[k];
+            st.contributing += (int64_t)pairs_h[ntl + k];
+        }
         if (prof)
             for (int it = 0; it < iters; ++it)
                 for (int k = 0; k < kPhases; ++k) {

@@ -235,7 +235,7 @@ struct RasterArgs {
     const float *d_rgb, *d_depth, *d_alpha;
     // registration / backward outputs
     float *tile_loss;         // [tiles]
-    unsigned long long *tile_pairs;  // [tiles] += sum of `last` (registration statistics, may be null)
+    unsigned long long *tile_pairs;  // [2][tiles] += sum of `last`, contributing pairs (statistics, may be null)
     double *tile_twist;       // [tiles][6], camera frame
     const double *c_cam;      // [vp][3] pivot in camera frame
     float *dup_grads;         // [dups][10] screen-space partials (full mode)

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
     const float cut = a.skip_below - 0.01f;
     const uint2 rg = a.ranges[t];
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    int last = 0;
+    int last = 0, n_contrib = 0;
     bool done = !p.inside;
     for (uint32_t b = rg.x; b < rg.y; b += 256) {
         if (__syncthreads_count(done) == 256)
@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
                 D = fmaf(q1.z, w, D);
                 T = Tn;
                 last = (int)(b - rg.x) + j + 1;
+                ++n_contrib;
             }
         }
     }
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
         return;
     }
     // registration: fused L1 colour + L1 depth loss and its sign code
-    __shared__ int s_pairs[8];
+    __shared__ int s_pairs[8], s_contrib[8];
     float lsum = 0.0f;
     if (p.inside) {
         const float e0 = o0 - d.t_rgb[off], e1 = o1 - d.t_rgb[HW + off], e2 = o2 - d.t_rgb[2 * HW + off];
@@ -191,23 +192,27 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
         a.last[pix] = last;
     }
     lsum = warp_sum(lsum);
-    const int wl = warp_sum(last);
+    const int wl = warp_sum(last), wc = warp_sum(n_contrib);
     if ((threadIdx.x & 31) == 0) {
         s_red[threadIdx.x >> 5] = lsum;
         s_pairs[threadIdx.x >> 5] = wl;
+        s_contrib[threadIdx.x >> 5] = wc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         float s = 0.0f;
-        unsigned long long np = 0;
+        unsigned long long np = 0, nc = 0;
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
             s += s_red[w];
             np += (unsigned long long)s_pairs[w];
+            nc += (unsigned long long)s_contrib[w];
         }
         a.tile_loss[t] = s;
-        if (a.tile_pairs)
+        if (a.tile_pairs) {
             a.tile_pairs[t] += np;
+            a.tile_pairs[a.n_tiles + t] += nc;
+        }
     }
 }
 

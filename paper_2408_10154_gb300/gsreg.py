@@ -58,7 +58,7 @@ class gs_options_t(ctypes.Structure):
 class gs_stats_t(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("n_dups", ctypes.c_int64), ("n_pixels", ctypes.c_int64),
                 ("pairs", ctypes.c_int64), ("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("phase_ms", ctypes.c_double * 5)]
+                ("phase_ms", ctypes.c_double * 5), ("contributing", ctypes.c_int64)]
 
 
 class gs_gaussian_grads_t(ctypes.Structure):

@@ -430,6 +430,7 @@ def test_registration_profile_and_stats(gs, ctx):
     st = gs.gsreg.gs_stats_t()
     ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st)))
     assert st.iterations == 7 and st.pairs > 0 and st.n_dups > 0 and st.kernel_launches > 7 * 5
+    assert 0 < st.contributing <= st.pairs
     assert st.n_pixels == sum(int(c[4]) * int(c[5]) for c in cams)
     assert all(v > 0 for v in st.phase_ms)
 
