@@ -342,6 +342,131 @@ def cpu_baseline(c):
             "seconds": float(sum(per))}
 
 
+def edge_problems(gs, ctx, torch, pairs):
+    """Device problems (src, tgt = T_gt src, src keyframes, tgt keyframes,
+    targets rendered on the device) of batched-workload pairs, and their
+    pixels per iteration."""
+    problems, px = [], 0
+    for pr in pairs:
+        src = gs.Gaussians.from_numpy(pr["gaussians"])
+        tgt = gs.gs_transform(ctx, src, pr["T_gt"])
+        k = len(pr["src_cams"])
+        I = torch.tensor(np.stack([np.eye(3, 4)] * k).reshape(k, 12), dtype=torch.float32, device="cuda")
+        rs = gs.gs_render(ctx, src, I, pr["src_cams"])
+        rt = gs.gs_render(ctx, tgt, I, pr["tgt_cams"])
+        sv = list(zip(pr["src_cams"], [x.contiguous() for x in gs.split_views(rs["rgb"], pr["src_cams"], 3)],
+                      [x.contiguous() for x in gs.split_views(rs["depth"], pr["src_cams"], 1)]))
+        tv = list(zip(pr["tgt_cams"], [x.contiguous() for x in gs.split_views(rt["rgb"], pr["tgt_cams"], 3)],
+                      [x.contiguous() for x in gs.split_views(rt["depth"], pr["tgt_cams"], 1)]))
+        problems.append((src, tgt, sv, tv))
+        px += sum(int(c[4]) * int(c[5]) for c in list(pr["src_cams"]) + list(pr["tgt_cams"]))
+    return problems, px
+
+
+def run_serve(args):
+    """Serving stream (Poisson arrivals, 70 % frame-to-model tracking of a
+    resident submap, 30 % loop edges; 40 / 100 iterations) through the
+    continuous-batching server in real time, and the plain form: the same
+    stream served one request at a time in arrival order (each request's
+    gs_register time measured, FIFO queueing computed from the arrivals).
+    Prints one JSON line with p50/p99 latencies and throughput of both."""
+    import time
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2408_10154_gb300 as gs
+    from paper_2408_10154_gb300 import synth
+    ctx = gs.Context(0, 64 << 30)
+    st = synth.serving_stream(rate=args.rate, seconds=args.seconds, n_submaps=args.pool)
+    edges, _ = edge_problems(gs, ctx, torch, synth.batched_pairs()["pairs"])
+    tracks = []
+    for sm in st["submaps"]:
+        g = gs.Gaussians.from_numpy(sm["gaussians"])
+        k = len(sm["cams"])
+        I = torch.tensor(np.stack([np.eye(3, 4)] * k).reshape(k, 12), dtype=torch.float32, device="cuda")
+        r = gs.gs_render(ctx, g, I, sm["cams"])
+        rgb, dep = gs.split_views(r["rgb"], sm["cams"], 3), gs.split_views(r["depth"], sm["cams"], 1)
+        tracks.append((g, [(sm["guesses"][f], rgb[f].contiguous(), dep[f].contiguous()) for f in range(k)]))
+    arrivals = st["arrivals"]
+    n = len(arrivals)
+
+    def request(a):
+        _, kind, idx, fr = a
+        if kind == "track":
+            g, fv = tracks[idx]
+            return (g, g, [], [fv[fr]]), st["track_iters"], 640 * 480
+        src, tgt, sv, tv = edges[idx]
+        return edges[idx], st["edge_iters"], sum(int(c[4]) * int(c[5]) for c, _, _ in list(sv) + list(tv))
+
+    # warm-up: one request of each kind through both forms
+    for a in (next(x for x in arrivals if x[1] == "track"), next(x for x in arrivals if x[1] == "edge")):
+        prob, iters, _ = request(a)
+        gs.gs_register(ctx, *prob, iters)
+        w = gs.Server(0, max_keyframes=args.max_kf, max_round_iters=args.round_iters)
+        w.submit(*prob, iters)
+        while w.counts()[1] or w.counts()[0]:
+            w.step()
+        w.close()
+    torch.cuda.synchronize()
+    # served: submit each request at its arrival time, one round per step
+    srv = gs.Server(0, budget_bytes=160 << 30, max_keyframes=args.max_kf, max_round_iters=args.round_iters)
+    done_at, rid_of, i = {}, {}, 0
+    t0 = time.perf_counter()
+    while len(done_at) < n:
+        now = time.perf_counter() - t0
+        while i < n and arrivals[i][0] <= now:
+            prob, iters, _ = request(arrivals[i])
+            rid_of[srv.submit(*prob, iters)] = i
+            i += 1
+        waiting, inflight = srv.counts()[:2]
+        if waiting == 0 and inflight == 0:
+            time.sleep(max(0.0, arrivals[i][0] - (time.perf_counter() - t0)))
+            continue
+        for rid in srv.step():
+            done_at[rid_of[rid]] = time.perf_counter() - t0
+    served_T = {rid_of[r]: srv.poll(r)["T"] for r in rid_of}
+    _, _, _, rounds, replans = srv.counts()
+    srv.close()
+    # plain: each request alone, FIFO in arrival order
+    service, plain_T = [], {}
+    for k, a in enumerate(arrivals):
+        prob, iters, _ = request(a)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        plain_T[k] = gs.gs_register(ctx, *prob, iters)[0]
+        service.append(time.perf_counter() - t)
+    finish, tcur = [], 0.0
+    for k, a in enumerate(arrivals):
+        tcur = max(a[0], tcur) + service[k]
+        finish.append(tcur)
+    work = sum(request(a)[1] * request(a)[2] for a in arrivals)
+
+    def summary(done):
+        lat = {kind: [1000.0 * (done[k] - arrivals[k][0]) for k in range(n) if arrivals[k][1] == kind]
+               for kind in ("track", "edge")}
+        span = max(done[k] for k in range(n))
+        out = {"makespan_s": span, "requests_per_s": n / span, "mpx_iter_per_s": work / span / 1e6}
+        for kind, l in lat.items():
+            if l:
+                out[kind + "_latency_ms"] = {"p50": float(np.percentile(l, 50)), "p99": float(np.percentile(l, 99))}
+        return out
+
+    served = summary(done_at)
+    plain = summary({k: finish[k] for k in range(n)})
+    same = sum(int(np.array_equal(served_T[k], plain_T[k])) for k in range(n))
+    out = {"metric": "serving requests/s", "value": served["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
+           "steps": n, "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "serving: Poisson %.0f/s for %.0f s (%d requests; 70 %% tracking 640x480, 40 it, "
+                                  "%d resident submaps of 50k-300k; 30 %% loop edges of the batched pool, 100 it)"
+                                  % (args.rate, args.seconds, n, args.pool),
+                      "max_keyframes": args.max_kf, "round_iters": args.round_iters},
+           "served": served, "plain": plain, "served_rounds": rounds, "served_replans": replans,
+           "results_identical": same, "n_requests": n}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_batched(args):
     """Batched uneven registration: the 32 submap pairs of the batched
     workload (20k-400k Gaussians, 4-12 keyframes per submap at 640x480 or
@@ -364,20 +489,7 @@ def run_batched(args):
     costs = [shard.edge_cost(len(pr["gaussians"]["means4"]), len(pr["gaussians"]["means4"]), pr["src_cams"],
                              pr["tgt_cams"]) for pr in wl["pairs"]]
     mine = shard.lpt_partition(costs, world)[rank]
-    problems, px = [], 0
-    for pr in [wl["pairs"][i] for i in mine]:
-        src = gs.Gaussians.from_numpy(pr["gaussians"])
-        tgt = gs.gs_transform(ctx, src, pr["T_gt"])
-        k = len(pr["src_cams"])
-        I = torch.tensor(np.stack([np.eye(3, 4)] * k).reshape(k, 12), dtype=torch.float32, device="cuda")
-        rs = gs.gs_render(ctx, src, I, pr["src_cams"])
-        rt = gs.gs_render(ctx, tgt, I, pr["tgt_cams"])
-        sv = list(zip(pr["src_cams"], [x.contiguous() for x in gs.split_views(rs["rgb"], pr["src_cams"], 3)],
-                      [x.contiguous() for x in gs.split_views(rs["depth"], pr["src_cams"], 1)]))
-        tv = list(zip(pr["tgt_cams"], [x.contiguous() for x in gs.split_views(rt["rgb"], pr["tgt_cams"], 3)],
-                      [x.contiguous() for x in gs.split_views(rt["depth"], pr["tgt_cams"], 1)]))
-        problems.append((src, tgt, sv, tv))
-        px += sum(int(c[4]) * int(c[5]) for c in list(pr["src_cams"]) + list(pr["tgt_cams"]))
+    problems, px = edge_problems(gs, ctx, torch, [wl["pairs"][i] for i in mine])
     iters = ITERS
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -460,8 +572,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="room_150k", choices=["room_150k", "batched_32"],
-                    help="room_150k: the benchmark line; batched_32: batched vs one-pair-per-call")
+    ap.add_argument("--workload", default="room_150k", choices=["room_150k", "batched_32", "serve"],
+                    help="room_150k: the benchmark line; batched_32: batched vs one-pair-per-call; "
+                         "serve: continuous-batching server vs one request at a time")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
+    ap.add_argument("--seconds", type=float, default=10.0, help="serve: length of the arrival stream")
+    ap.add_argument("--pool", type=int, default=64, help="serve: resident tracking submaps")
+    ap.add_argument("--max-kf", type=int, default=128, help="serve: keyframe problems in flight")
+    ap.add_argument("--round-iters", type=int, default=10, help="serve: iterations per round")
     ap.add_argument("--iters", type=int, default=ITERS,
                     help="iterations per loop edge (100 for the benchmark; fewer only for profiling captures)")
     args = ap.parse_args()
@@ -470,6 +588,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched_32":
         return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

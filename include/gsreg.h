@@ -332,6 +332,62 @@ typedef struct {
 gs_status_t gs_register_batch(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt, int iters,
                               double *T_out, double *conf_out, double *eps_out, gs_stream_t stream);
 
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous-batching registration server.  A request is one registration
+ * problem (Sec. 3.2, as in gs_register; a frame-to-model tracking request is
+ * a problem with one target keyframe -- the frame, its camera at the initial
+ * guess -- and no source keyframes, whose estimate T maps the submap so that
+ * it renders the frame, i.e. the tracked camera is world_to_cam o T) with its
+ * own iteration count.  The submaps and keyframe images stay resident in
+ * caller-owned device memory until the request is done.
+ *
+ * gs_server_step runs one round on `stream`:
+ *   1. admits waiting requests in submission order while the in-flight
+ *      keyframe problems stay <= max_keyframes and the estimated scratch of
+ *      the in-flight requests stays <= hbm_budget_bytes (the first waiting
+ *      request is always admitted into an empty server);
+ *   2. when the in-flight set changed, re-plans it: one projection pass per
+ *      moving submap, one sort and one compositing launch over every tile of
+ *      every in-flight keyframe per iteration, captured into a CUDA graph,
+ *      each request's pose and optimiser state carried over;
+ *   3. replays the graph for min(max_round_iters, the fewest iterations any
+ *      in-flight request has left) iterations;
+ *   4. retires the requests whose iterations are done (plus one iteration at
+ *      the frozen final pose that measures the residual of Eq. 7) and fuses
+ *      their estimates by Eq. 7.
+ * Every iteration of a request depends only on its own problem, so its
+ * result equals gs_register's for the same problem and iteration count,
+ * whatever else is in flight.  Synchronises `stream` once per round. */
+typedef struct gs_server gs_server_t;
+
+gs_status_t gs_server_create(int device, size_t hbm_budget_bytes, int max_keyframes, int max_round_iters,
+                             const gs_options_t *opt, gs_server_t **out);
+gs_status_t gs_server_destroy(gs_server_t *srv);
+const char *gs_server_last_error(const gs_server_t *srv);
+
+/* Queues a request; the problem's arrays must stay valid until it is done.
+ * iters >= 0.  *id_out = the request id (ids start at 0 and increase).
+ * GS_ERR_OOM if the request's estimated scratch alone exceeds the budget
+ * (hbm_budget_bytes, 0 = 16 GiB; the scratch arena may exceed it by a
+ * quarter, at least 256 MiB, to absorb the estimate's error). */
+gs_status_t gs_server_submit(gs_server_t *srv, const gs_problem_t *problem, int iters, int64_t *id_out);
+
+/* One round (see above).  done_ids [max_done] host out (may be NULL): ids of
+ * the requests retired in this round; *n_done = their number. */
+gs_status_t gs_server_step(gs_server_t *srv, gs_stream_t stream, int64_t *done_ids, int max_done, int *n_done);
+
+/* Result of request `id`: *state = 0 waiting, 1 in flight, 2 done.  When
+ * done: T_out [12] host (row-major [R|t] of T_{P->Q}), *confidence,
+ * eps_out [its keyframes] host or NULL (residuals, V^P first).  *t_submit,
+ * *t_done: seconds on the server's clock (steady, from creation); any
+ * output pointer may be NULL. */
+gs_status_t gs_server_poll(gs_server_t *srv, int64_t id, int *state, double *T_out, double *confidence,
+                           double *eps_out, double *t_submit, double *t_done);
+
+/* Counts: requests waiting, in flight, done; rounds and re-plans run. */
+gs_status_t gs_server_counts(const gs_server_t *srv, int64_t out[5]);
+
 /* Rigid transform of a submap by T (Eq. 8/9): mu <- R mu + t,
  * q <- q_R (x) q (so Sigma <- R Sigma R^T); scales, opacities, colours
  * unchanged.  out_means, out_quats [n][4] device (may alias the inputs). */

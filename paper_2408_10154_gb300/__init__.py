@@ -5,6 +5,6 @@ behind the C ABI of include/gsreg.h.
 
 ``gsreg`` is the Python binding (argument marshalling only); ``synth`` draws
 seeded synthetic workloads; ``build`` compiles the library in-tree."""
-from .gsreg import (Context, Gaussians, GsError, default_options, gs_bin, gs_fuse, gs_loss, gs_pose_step,  # noqa: F401
+from .gsreg import (Context, Gaussians, GsError, Server, default_options, gs_bin, gs_fuse, gs_loss, gs_pose_step,  # noqa: F401
                     gs_project, gs_register, gs_register_batch, gs_render, gs_render_backward, gs_render_noalloc,
                     gs_transform, load, split_views)

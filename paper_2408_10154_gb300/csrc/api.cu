@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1377,3 +1378,464 @@ extern "C" gs_status_t gs_render_noalloc(const gs_gaussians_t *g, const float *p
         return GS_ERR_CUDA;
     return (flags & gsk::kFlagNonFinite) ? GS_ERR_NONFINITE : GS_OK;
 }
+
+// ===========================================================================
+// Serving: continuous batching of registration requests (gs_server_*)
+// ===========================================================================
+namespace {
+
+// per keyframe problem: pose64 [12], Adam state [13], pivot [3], camera-frame pivot [3]
+constexpr int kVpState = 31;
+// tile duplicates per record assumed by admission (the room workload has ~1.2)
+constexpr double kAdmitDupsPerRecord = 3.0;
+
+struct ServerReq {
+    gs_gaussians_t src{}, tgt{};
+    std::vector<gs_view_t> sv, tv;
+    int iters = 0;
+    int state = 0;       // 0 waiting, 1 in flight, 2 done
+    int ran = 0;         // graph iterations run: iters pose updates + 1 at the frozen pose
+    bool fresh = true;   // optimiser state not created yet
+    int vp_first = 0;    // first keyframe problem in the current plan
+    std::vector<double> st;  // [vps][kVpState]
+    double T[12] = {}, conf = 0;
+    std::vector<double> eps;
+    double t_submit = 0, t_done = 0;
+    size_t est_bytes = 0;
+    int n_vps() const { return (int)(sv.size() + tv.size()); }
+};
+
+}  // namespace
+
+struct gs_server {
+    gs_ctx *ctx = nullptr;
+    gs_options_t opt{};
+    int max_kf = 0, max_round = 0;
+    size_t budget = 0;
+    std::vector<ServerReq> reqs;  // indexed by id
+    std::vector<int64_t> waiting;  // FIFO (front = index `wait_head`)
+    size_t wait_head = 0;
+    std::vector<int64_t> active;
+    bool dirty = true;
+    double headroom = 1.5;
+    int64_t rounds = 0, replans = 0, n_done = 0;
+    std::chrono::steady_clock::time_point t0;
+    // the current plan and its device state
+    Plan P;
+    DevPlan D;
+    Pipe p;
+    int n_vps = 0, n_problems = 0;
+    float *pose32 = nullptr, *tloss = nullptr, *tf = nullptr;
+    double *pose64 = nullptr, *adam = nullptr, *pivot = nullptr, *ccam = nullptr, *cent = nullptr,
+           *lossd = nullptr, *ttw = nullptr, *Tdev = nullptr, *confd = nullptr;
+    int32_t *last = nullptr, *rev = nullptr, *pf = nullptr, *pc = nullptr;
+    uint8_t *code = nullptr;
+    gsl::PoseArgs pa{};
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+double srv_now(const gs_server *srv)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - srv->t0).count();
+}
+
+size_t estimate_bytes(const ServerReq &r)
+{
+    double b = 0;
+    auto add = [&](const gs_gaussians_t &g, const gs_view_t &v) {
+        const double n = (double)g.n, px = (double)v.cam.width * v.cam.height;
+        const double tiles = (double)((v.cam.width + GS_TILE - 1) / GS_TILE) * ((v.cam.height + GS_TILE - 1) / GS_TILE);
+        // records + aux + counts + depth keys; duplicates (keys + values, double-buffered, headroom);
+        // per pixel T_final, last, code; per tile ranges, loss, twist, counters
+        b += n * (48 + 32 + 4 + 16) + kAdmitDupsPerRecord * n * 16 * 1.5 + px * 9 + tiles * (8 + 4 + 48 + 16);
+    };
+    for (const gs_view_t &v : r.sv)
+        add(r.tgt, v);
+    for (const gs_view_t &v : r.tv)
+        add(r.src, v);
+    return (size_t)b + 4096;
+}
+
+// admits waiting requests (FIFO) within the keyframe and memory limits
+void srv_admit(gs_server *srv)
+{
+    int kf = 0;
+    size_t bytes = 0;
+    for (int64_t id : srv->active) {
+        kf += srv->reqs[id].n_vps();
+        bytes += srv->reqs[id].est_bytes;
+    }
+    while (srv->wait_head < srv->waiting.size()) {
+        ServerReq &r = srv->reqs[srv->waiting[srv->wait_head]];
+        const bool empty = srv->active.empty();
+        if (!empty && (kf + r.n_vps() > srv->max_kf || bytes + r.est_bytes > srv->budget))
+            break;
+        kf += r.n_vps();
+        bytes += r.est_bytes;
+        r.state = 1;
+        srv->active.push_back(srv->waiting[srv->wait_head++]);
+        srv->dirty = true;
+    }
+    if (srv->wait_head > 4096 && srv->wait_head * 2 > srv->waiting.size()) {
+        srv->waiting.erase(srv->waiting.begin(), srv->waiting.begin() + (ptrdiff_t)srv->wait_head);
+        srv->wait_head = 0;
+    }
+}
+
+// builds the plan of the in-flight requests, restores their state and
+// captures one iteration into a graph
+gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
+{
+    gs_ctx *ctx = srv->ctx;
+    if (srv->exec) {
+        cudaGraphExecDestroy(srv->exec);
+        srv->exec = nullptr;
+    }
+    Plan &P = srv->P;
+    P = Plan{};
+    int sets = 0;
+    for (size_t i = 0; i < srv->active.size(); ++i) {
+        ServerReq &r = srv->reqs[srv->active[i]];
+        r.vp_first = (int)P.vps.size();
+        add_problem(P, &r.src, &r.tgt, r.sv.data(), (int)r.sv.size(), r.tv.data(), (int)r.tv.size(), (int)i, sets);
+        for (int v = r.vp_first; v < (int)P.vps.size(); ++v)
+            P.vps[v].iters = r.iters;
+    }
+    GS_TRY(finalize(ctx, P));
+    DevPlan &D = srv->D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    const int nv = (int)P.vps.size(), n_sets = (int)P.set_vp.size(), np = (int)srv->active.size();
+    srv->n_vps = nv;
+    srv->n_problems = np;
+    Pipe &p = srv->p;
+    p = Pipe{};
+    GS_TRY(alloc_pipe(ctx, P, true, p));
+    const size_t npix = (size_t)std::max<int64_t>(P.n_pix, 1), ntl = (size_t)std::max<uint64_t>(P.n_tiles, 1);
+    GS_TRY(wsT(ctx, S_POSE32, 12 * (size_t)nv, &srv->pose32));
+    GS_TRY(wsT(ctx, S_POSE64, 12 * (size_t)nv, &srv->pose64));
+    GS_TRY(wsT(ctx, S_ADAM, 13 * (size_t)nv, &srv->adam));
+    GS_TRY(wsT(ctx, S_PIVOT, 3 * (size_t)nv, &srv->pivot));
+    GS_TRY(wsT(ctx, S_CCAM, 3 * (size_t)nv, &srv->ccam));
+    GS_TRY(wsT(ctx, S_CENT, 3 * (size_t)std::max(n_sets, 1), &srv->cent));
+    GS_TRY(wsT(ctx, S_LOSS, (size_t)nv, &srv->lossd));
+    GS_TRY(wsT(ctx, S_TF, npix, &srv->tf));
+    GS_TRY(wsT(ctx, S_LAST, npix, &srv->last));
+    GS_TRY(wsT(ctx, S_CODE, npix, &srv->code));
+    GS_TRY(wsT(ctx, S_TLOSS, ntl, &srv->tloss));
+    GS_TRY(wsT(ctx, S_TTWIST, 6 * ntl, &srv->ttw));
+    GS_TRY(wsT(ctx, S_TOUT, 12 * (size_t)np, &srv->Tdev));
+    GS_TRY(wsT(ctx, S_CONF, (size_t)np, &srv->confd));
+    std::vector<int32_t> revh(nv), pfh(np, 0), pch(np, 0);
+    for (int v = 0; v < nv; ++v) {
+        revh[v] = P.vps[v].reverse;
+        const int q = P.vps[v].problem;
+        if (pch[q]++ == 0)
+            pfh[q] = v;
+    }
+    GS_TRY(upload(ctx, S_REV, revh, &srv->rev, s));
+    GS_TRY(upload(ctx, S_PFIRST, pfh, &srv->pf, s));
+    GS_TRY(upload(ctx, S_PCOUNT, pch, &srv->pc, s));
+
+    gsl::PoseArgs &pa = srv->pa;
+    pa = gsl::PoseArgs{};
+    pa.vps = D.vps;
+    pa.n_vps = nv;
+    pa.tile_twist = srv->ttw;
+    pa.tile_loss = srv->tloss;
+    pa.pose64 = srv->pose64;
+    pa.pose32 = srv->pose32;
+    pa.adam = srv->adam;
+    pa.pivot = srv->pivot;
+    pa.c_cam = srv->ccam;
+    pa.centroid = srv->cent;
+    pa.loss = srv->lossd;
+    pa.lr_rot = srv->opt.lr_rot;
+    pa.lr_trans = srv->opt.lr_trans;
+    pa.beta1 = srv->opt.beta1;
+    pa.beta2 = srv->opt.beta2;
+    pa.eps = srv->opt.adam_eps;
+    pa.lr_final = srv->opt.lr_final;
+    pa.iters = 0;  // every keyframe carries its request's count
+    pa.update = 1;
+
+    // fresh requests start at the identity; the others resume their state
+    gsl::centroids(D.vps, D.set_vp, n_sets, srv->cent, s);
+    gsl::pose_init(pa, s);
+    for (int64_t id : srv->active) {
+        const ServerReq &r = srv->reqs[id];
+        if (r.fresh)
+            continue;
+        for (int k = 0; k < r.n_vps(); ++k) {
+            const double *st = r.st.data() + (size_t)k * kVpState;
+            const size_t v = (size_t)r.vp_first + k;
+            GS_CUDA(cudaMemcpyAsync(srv->pose64 + 12 * v, st, 12 * sizeof(double), cudaMemcpyHostToDevice, s));
+            GS_CUDA(cudaMemcpyAsync(srv->adam + 13 * v, st + 12, 13 * sizeof(double), cudaMemcpyHostToDevice, s));
+            GS_CUDA(cudaMemcpyAsync(srv->pivot + 3 * v, st + 25, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+            GS_CUDA(cudaMemcpyAsync(srv->ccam + 3 * v, st + 28, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+        }
+    }
+    k_to_float<<<(12 * nv + 255) / 256, 256, 0, s>>>(srv->pose64, srv->pose32, 12 * nv);
+    ++gsl::g_launches;
+    // size the duplicate lists at the current poses
+    int cur = 0;
+    uint32_t nd = 0;
+    GS_TRY(project_and_bin(ctx, P, D, p, srv->pose32, &srv->opt, s, &cur, &nd));
+    const uint64_t want = (uint64_t)(srv->headroom * nd) + 65536;
+    if (p.cap < want)
+        GS_TRY(alloc_sort(ctx, want, p));
+    const gsl::BinArgs b = bin_args(P, D, p);
+    gsl::RasterArgs r = raster_args(P, D, p, 0, &srv->opt);
+    r.t_final = srv->tf;
+    r.last = srv->last;
+    r.code = srv->code;
+    r.tile_loss = srv->tloss;
+    r.tile_twist = srv->ttw;
+    r.c_cam = srv->ccam;
+    r.tile_pairs = nullptr;
+    GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    gsl::project(project_args(P, D, p, srv->pose32, &srv->opt), ctx->cap);
+    r.vals = p.vals[run_bin(b, ctx->cap)];
+    gsl::forward(r, true, ctx->cap);
+    gsl::backward(r, true, false, ctx->cap);
+    gsl::pose_update(pa, ctx->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
+    if (ce != cudaSuccess || !graph)
+        return fail(ctx, GS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&srv->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        srv->exec = nullptr;
+        return fail(ctx, GS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    srv->dirty = false;
+    ++srv->replans;
+    return GS_OK;
+}
+
+gs_status_t srv_round(gs_server *srv, cudaStream_t s, int64_t *done_ids, int max_done, int *n_done)
+{
+    gs_ctx *ctx = srv->ctx;
+    *n_done = 0;
+    srv_admit(srv);
+    if (srv->active.empty())
+        return GS_OK;
+    for (int attempt = 0;; ++attempt) {
+        if (srv->dirty)
+            GS_TRY(srv_replan(srv, s));
+        int S = std::max(srv->max_round, 1);
+        for (int64_t id : srv->active) {
+            const ServerReq &r = srv->reqs[id];
+            S = std::min(S, r.iters + 1 - r.ran);
+        }
+        S = std::max(S, 1);
+        GS_CUDA(cudaMemsetAsync(srv->p.flags, 0, sizeof(int), s));
+        for (int it = 0; it < S; ++it)
+            GS_CUDA(cudaGraphLaunch(srv->exec, s));
+        const int nv = srv->n_vps;
+        std::vector<double> pose(12 * (size_t)nv), adam(13 * (size_t)nv), piv(3 * (size_t)nv), cc(3 * (size_t)nv),
+            loss(nv);
+        int flags = 0;
+        GS_CUDA(cudaMemcpyAsync(&flags, srv->p.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(pose.data(), srv->pose64, pose.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(adam.data(), srv->adam, adam.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(piv.data(), srv->pivot, piv.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(cc.data(), srv->ccam, cc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(loss.data(), srv->lossd, loss.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaStreamSynchronize(s));
+        if (flags & gsk::kFlagNonFinite)
+            return fail(ctx, GS_ERR_NONFINITE, "non-finite Gaussian parameter in an in-flight request");
+        if (flags & gsk::kFlagCapacity) {
+            // the lists outgrew their headroom: redo the round from the saved states
+            if (attempt >= 3)
+                return fail(ctx, GS_ERR_CAPACITY, "tile duplicate lists kept outgrowing their capacity");
+            srv->headroom *= 2.0;
+            srv->dirty = true;
+            continue;
+        }
+        ++srv->rounds;
+        std::vector<int64_t> retiring;
+        for (int64_t id : srv->active) {
+            ServerReq &r = srv->reqs[id];
+            r.st.resize((size_t)r.n_vps() * kVpState);
+            for (int k = 0; k < r.n_vps(); ++k) {
+                const size_t v = (size_t)r.vp_first + k;
+                double *st = r.st.data() + (size_t)k * kVpState;
+                std::memcpy(st, &pose[12 * v], 12 * sizeof(double));
+                std::memcpy(st + 12, &adam[13 * v], 13 * sizeof(double));
+                std::memcpy(st + 25, &piv[3 * v], 3 * sizeof(double));
+                std::memcpy(st + 28, &cc[3 * v], 3 * sizeof(double));
+            }
+            r.fresh = false;
+            r.ran += S;
+            if (r.ran >= r.iters + 1)
+                retiring.push_back(id);
+        }
+        if (retiring.empty())
+            return GS_OK;
+        // Eq. 7 over the in-flight problems (losses measured at the frozen poses)
+        gsl::FuseArgs f{};
+        f.pose64 = srv->pose64;
+        f.eps = srv->lossd;
+        f.reverse = srv->rev;
+        f.prob_first = srv->pf;
+        f.prob_count = srv->pc;
+        f.n_problems = srv->n_problems;
+        f.T_out = srv->Tdev;
+        f.conf = srv->confd;
+        f.est_out = nullptr;
+        gsl::fuse(f, s);
+        std::vector<double> T(12 * (size_t)srv->n_problems), conf(srv->n_problems);
+        GS_CUDA(cudaMemcpyAsync(T.data(), srv->Tdev, T.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(conf.data(), srv->confd, conf.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaStreamSynchronize(s));
+        const double now = srv_now(srv);
+        std::vector<int64_t> keep;
+        for (size_t i = 0; i < srv->active.size(); ++i) {
+            const int64_t id = srv->active[i];
+            ServerReq &r = srv->reqs[id];
+            if (r.ran < r.iters + 1) {
+                keep.push_back(id);
+                continue;
+            }
+            std::memcpy(r.T, &T[12 * i], 12 * sizeof(double));
+            r.conf = conf[i];
+            r.eps.assign(loss.begin() + r.vp_first, loss.begin() + r.vp_first + r.n_vps());
+            r.state = 2;
+            r.t_done = now;
+            r.st.clear();
+            r.st.shrink_to_fit();
+            ++srv->n_done;
+            if (done_ids && *n_done < max_done)
+                done_ids[*n_done] = id;
+            ++*n_done;
+        }
+        srv->active.swap(keep);
+        srv->dirty = true;
+        return GS_OK;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status_t gs_server_create(int device, size_t budget, int max_keyframes, int max_round_iters,
+                             const gs_options_t *opt, gs_server_t **out)
+{
+    if (!out || !opt || max_keyframes < 1 || max_round_iters < 1)
+        return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    // admission keeps the estimated scratch within `budget`; the arena gets
+    // slack above it for the estimate's error
+    const size_t adm = budget ? budget : ((size_t)16 << 30);
+    gs_ctx_t *ctx = nullptr;
+    GS_TRY(gs_ctx_create(device, adm + std::max(adm / 4, (size_t)256 << 20), &ctx));
+    const gs_status_t st = check_options(ctx, opt);
+    if (st != GS_OK) {
+        gs_ctx_destroy(ctx);
+        return st;
+    }
+    gs_server *srv = new gs_server();
+    srv->ctx = ctx;
+    srv->opt = *opt;
+    srv->max_kf = max_keyframes;
+    srv->max_round = max_round_iters;
+    srv->budget = adm;
+    srv->t0 = std::chrono::steady_clock::now();
+    *out = srv;
+    return GS_OK;
+}
+
+gs_status_t gs_server_destroy(gs_server_t *srv)
+{
+    if (!srv)
+        return GS_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(srv->ctx->device);
+        if (srv->exec)
+            cudaGraphExecDestroy(srv->exec);
+    }
+    gs_ctx_destroy(srv->ctx);
+    delete srv;
+    return GS_OK;
+}
+
+const char *gs_server_last_error(const gs_server_t *srv) { return srv ? srv->ctx->err.c_str() : "null server"; }
+
+gs_status_t gs_server_submit(gs_server_t *srv, const gs_problem_t *q, int iters, int64_t *id_out)
+{
+    if (!srv || !q || !id_out)
+        return GS_ERR_INVALID_ARG;
+    gs_ctx *ctx = srv->ctx;
+    if (iters < 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "iters must be >= 0");
+    GS_TRY(check_problem(ctx, *q));
+    if (q->n_src_views + q->n_tgt_views > srv->max_kf)
+        return fail(ctx, GS_ERR_INVALID_ARG, "request has more keyframes than the server's max_keyframes");
+    ServerReq r;
+    r.src = q->src;
+    r.tgt = q->tgt;
+    r.sv.assign(q->src_views, q->src_views + q->n_src_views);
+    r.tv.assign(q->tgt_views, q->tgt_views + q->n_tgt_views);
+    r.iters = iters;
+    r.est_bytes = estimate_bytes(r);
+    if (r.est_bytes > srv->budget)
+        return fail(ctx, GS_ERR_OOM, "the request's scratch (" + std::to_string(r.est_bytes) +
+                                         " bytes estimated) exceeds the server's budget");
+    r.t_submit = srv_now(srv);
+    *id_out = (int64_t)srv->reqs.size();
+    srv->waiting.push_back(*id_out);
+    srv->reqs.push_back(std::move(r));
+    return GS_OK;
+}
+
+gs_status_t gs_server_step(gs_server_t *srv, gs_stream_t stream, int64_t *done_ids, int max_done, int *n_done)
+{
+    if (!srv || !n_done || max_done < 0)
+        return GS_ERR_INVALID_ARG;
+    DeviceGuard g(srv->ctx->device);
+    const gs_status_t st = srv_round(srv, (cudaStream_t)stream, done_ids, max_done, n_done);
+    if (st != GS_OK)
+        srv->dirty = true;
+    return st;
+}
+
+gs_status_t gs_server_poll(gs_server_t *srv, int64_t id, int *state, double *T_out, double *confidence,
+                           double *eps_out, double *t_submit, double *t_done)
+{
+    if (!srv || id < 0 || id >= (int64_t)srv->reqs.size())
+        return GS_ERR_INVALID_ARG;
+    const ServerReq &r = srv->reqs[id];
+    if (state)
+        *state = r.state;
+    if (t_submit)
+        *t_submit = r.t_submit;
+    if (r.state != 2)
+        return GS_OK;
+    if (T_out)
+        std::memcpy(T_out, r.T, sizeof r.T);
+    if (confidence)
+        *confidence = r.conf;
+    if (eps_out)
+        std::memcpy(eps_out, r.eps.data(), r.eps.size() * sizeof(double));
+    if (t_done)
+        *t_done = r.t_done;
+    return GS_OK;
+}
+
+gs_status_t gs_server_counts(const gs_server_t *srv, int64_t out[5])
+{
+    if (!srv || !out)
+        return GS_ERR_INVALID_ARG;
+    out[0] = (int64_t)(srv->waiting.size() - srv->wait_head);
+    out[1] = (int64_t)srv->active.size();
+    out[2] = srv->n_done;
+    out[3] = srv->rounds;
+    out[4] = srv->replans;
+    return GS_OK;
+}
+
+}  // extern "C"

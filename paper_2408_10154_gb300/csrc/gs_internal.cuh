@@ -39,6 +39,8 @@ struct VpDesc {
     int set;               // Gaussian set (centroid slot)
     int problem;           // registration problem (fusion)
     int reverse;           // 1: keyframe of P localised in Q (estimate is inverted)
+    int iters;             // pose updates of this keyframe's problem (0: the call's count); once
+                           // taken, the pose is frozen and later iterations only re-measure the loss
 };
 
 // A projection group: vps that share one Gaussian set and are projected by

@@ -161,10 +161,14 @@ __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
         for (int i = 0; i < 6; ++i)
             a.grad[6 * vp + i] = g[i];
     if (!a.update)
+        return;  // (pose and optimiser state may be absent: gradient-only callers)
+    const int iters = d.iters > 0 ? d.iters : a.iters;
+    const int k = (int)a.adam[13 * vp + 12];
+    if (k >= iters)
         return;
     double *P = a.pose64 + 12 * vp;
-    adam_exp_update(P, a.adam + 13 * vp, g, a.pivot + 3 * vp, (int)a.adam[13 * vp + 12], a.iters, a.lr_rot,
-                    a.lr_trans, a.beta1, a.beta2, a.eps, a.lr_final);
+    adam_exp_update(P, a.adam + 13 * vp, g, a.pivot + 3 * vp, k, iters, a.lr_rot, a.lr_trans, a.beta1, a.beta2,
+                    a.eps, a.lr_final);
     for (int k = 0; k < 12; ++k)
         a.pose32[12 * vp + k] = (float)P[k];
     pivots_of(d, P, a.centroid + 3 * d.set, a.pivot + 3 * vp, a.c_cam + 3 * vp);

@@ -68,7 +68,9 @@ class gs_gaussian_grads_t(ctypes.Structure):
 
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
-           "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc"]
+           "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc", "gs_server_create",
+           "gs_server_destroy", "gs_server_last_error", "gs_server_submit", "gs_server_step", "gs_server_poll",
+           "gs_server_counts"]
 
 _lock = threading.Lock()
 _lib = None
@@ -110,6 +112,13 @@ def load(build_if_missing: bool = False):
             "gs_transform": ([P, P, P, P, P, P], I),
             "gs_render_noalloc": ([P, P, P, I, P, P, P, P, P, P, P], I),
             "gs_register_batch": ([P, P, I, P, I, P, P, P, P], I),
+            "gs_server_create": ([I, ctypes.c_size_t, I, I, P, P], I),
+            "gs_server_destroy": ([P], I),
+            "gs_server_last_error": ([P], ctypes.c_char_p),
+            "gs_server_submit": ([P, P, I, P], I),
+            "gs_server_step": ([P, P, P, I, P], I),
+            "gs_server_poll": ([P, I64, P, P, P, P, P, P], I),
+            "gs_server_counts": ([P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -426,6 +435,81 @@ def gs_register_batch(ctx: Context, problems, iters, opt=None):
     ctx.check(ctx._lib.gs_register_batch(ctx.handle, arr, n, ctypes.byref(opt), int(iters), d(T), d(conf), d(eps),
                                          _stream()))
     return T.reshape(n, 3, 4), conf, eps[:total]
+
+
+class Server:
+    """Continuous-batching registration server (gs_server_*).  Requests are
+    registration problems as in gs_register_batch -- (src, tgt, src_views,
+    tgt_views) -- with their own iteration count; a tracking request is
+    (submap, submap, [], [frame view]).  The caller keeps every array of a
+    request alive until it is done (this object keeps references)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, max_keyframes: int = 256, max_round_iters: int = 10,
+                 opt=None):
+        self._lib = load()
+        self.opt = opt or default_options()
+        h = ctypes.c_void_p()
+        st = self._lib.gs_server_create(int(device), int(budget_bytes), int(max_keyframes), int(max_round_iters),
+                                        ctypes.byref(self.opt), ctypes.byref(h))
+        if st != 0:
+            raise GsError(st, "gs_server_create failed")
+        self.handle = h
+        self._keep = {}
+        self._nvps = {}
+
+    def check(self, st):
+        if st != 0:
+            raise GsError(st, self._lib.gs_server_last_error(self.handle).decode())
+
+    def submit(self, src: Gaussians, tgt: Gaussians, src_views, tgt_views, iters: int) -> int:
+        sva, tva = _views(src_views), _views(tgt_views)
+        q = gs_problem_t(src.c_struct(), tgt.c_struct(), ctypes.cast(sva, ctypes.c_void_p), len(src_views),
+                         ctypes.cast(tva, ctypes.c_void_p), len(tgt_views))
+        rid = ctypes.c_int64()
+        self.check(self._lib.gs_server_submit(self.handle, ctypes.byref(q), int(iters), ctypes.byref(rid)))
+        self._keep[rid.value] = (src, tgt, src_views, tgt_views, sva, tva)
+        self._nvps[rid.value] = len(src_views) + len(tgt_views)
+        return rid.value
+
+    def step(self, max_done: int = 4096):
+        """One round; returns the ids retired in it."""
+        ids = (ctypes.c_int64 * max_done)()
+        n = ctypes.c_int()
+        self.check(self._lib.gs_server_step(self.handle, _stream(), ids, max_done, ctypes.byref(n)))
+        done = [ids[k] for k in range(min(n.value, max_done))]
+        for i in done:
+            self._keep.pop(i, None)
+        return done
+
+    def poll(self, rid: int):
+        """dict(state, T [3,4], confidence, eps, t_submit, t_done)."""
+        state = ctypes.c_int()
+        T = np.zeros(12, np.float64)
+        conf = ctypes.c_double()
+        eps = np.zeros(max(self._nvps.get(rid, 1), 1), np.float64)
+        ts, td = ctypes.c_double(), ctypes.c_double()
+        self.check(self._lib.gs_server_poll(self.handle, int(rid), ctypes.byref(state), T.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(conf), eps.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(ts), ctypes.byref(td)))
+        return dict(state=state.value, T=T.reshape(3, 4), confidence=conf.value, eps=eps, t_submit=ts.value,
+                    t_done=td.value)
+
+    def counts(self):
+        """(waiting, in flight, done, rounds, re-plans)."""
+        out = (ctypes.c_int64 * 5)()
+        self.check(self._lib.gs_server_counts(self.handle, out))
+        return tuple(out)
+
+    def close(self):
+        if self.handle:
+            self._lib.gs_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def abi_structs():

@@ -230,6 +230,41 @@ def batched_pairs(seed=1002, n_pairs=32, n_min=20_000, n_max=400_000):
     return dict(name="batched_32", pairs=pairs, iters=100)
 
 
+def serving_stream(seed=1004, rate=200.0, seconds=60.0, n_submaps=64, frames=4, n_edges=32, track_frac=0.7):
+    """Serving stream: Poisson arrivals at ``rate`` per second for
+    ``seconds``; a fraction ``track_frac`` are frame-to-model tracking
+    requests (one 640x480 RGB-D frame of a resident submap of U[50k, 300k]
+    room Gaussians, the request's camera the frame's true camera perturbed by
+    0.69 deg and 1.34 cm, 40 iterations), the rest loop edges drawn from a
+    pool of ``n_edges`` batched-workload pairs (100 iterations, both
+    directions).  Returns dict(submaps=[dict(gaussians, cams, guesses)],
+    arrivals=[(t, kind, index, frame)]) with kind "track" or "edge"."""
+    rng = np.random.default_rng(seed)
+    submaps = []
+    for _ in range(n_submaps):
+        n = int(rng.integers(50_000, 300_001))
+        scale = (n / 150_000) ** (1.0 / 3.0)
+        g = gaussians_room(n, rng, scale=scale)
+        cams = room_cameras(frames, rng, 640, 480, 320.0, scale=scale, shrink=0.75 * scale)
+        guesses = []
+        for c in cams:
+            c2 = np.array(c, np.float32).copy()
+            # the camera moved by a small rigid motion in its own frame
+            c2[6:] = compose(random_rigid(rng, 0.69, 0.0134), np.asarray(c[6:], np.float64).reshape(3, 4)).reshape(12)
+            guesses.append(c2)
+        submaps.append(dict(gaussians=g, cams=cams, guesses=np.stack(guesses)))
+    arrivals, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= seconds:
+            break
+        if rng.uniform() < track_frac:
+            arrivals.append((t, "track", int(rng.integers(n_submaps)), int(rng.integers(frames))))
+        else:
+            arrivals.append((t, "edge", int(rng.integers(n_edges)), 0))
+    return dict(name="serving", submaps=submaps, arrivals=arrivals, track_iters=40, edge_iters=100)
+
+
 def diff_check_300k(seed=1003):
     """Differentiation check: 300,000 room Gaussians, 4 keyframes of
     1200x680; plus the exhaustive small case (500 Gaussians, 64x48,
