@@ -75,12 +75,14 @@ def _load():
         lib.or_project32.argtypes = [I, P, P, P, P, P, P, P, P, P]
         lib.or_project64.argtypes = [I, P, P, P, P, P, P, P, P]
         lib.or_bin.argtypes = [I, P, P, P, P, I, P, P, P, P, P, L, P, P]
-        lib.or_render.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.or_render.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.or_loss.argtypes = [I, I, P, P, P, P, P, P]
         lib.or_loss.restype = ctypes.c_double
         lib.or_backward.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.or_pose_step.argtypes = [P, P, P, P, P, I, I]
-        lib.or_register_view.argtypes = [I, P, P, P, P, P, P, P, P, P, P, I, P, P, P]
+        lib.or_register_view.argtypes = [I, P, P, P, P, P, P, P, P, P, P, I, P, P, P, P]
+        lib.or_track_loss.argtypes = [I, I, P, P, P, P, P, P, ctypes.c_double, P, P, P, P]
+        lib.or_track_loss.restype = ctypes.c_double
         lib.or_transform.argtypes = [I, P, P, P, P, P]
         for f in ("or_project32", "or_project64", "or_bin", "or_render", "or_backward",
                   "or_pose_step", "or_register_view", "or_transform"):
@@ -183,7 +185,7 @@ def bin_tiles(g: Gaussians, poses, cams, opt=DEFAULT_OPT):
 
 def render(g: Gaussians, pose, cam, opt=DEFAULT_OPT):
     """FP64 render at one camera.  Returns dict(rgb [3,H,W], depth, alpha,
-    t_final (FP64), t_final32 (mirror FP32), last (int32))."""
+    t_final (FP64), t_final32 and depth32 (the FP32 mirror), last (int32))."""
     lib = _load()
     W, H = int(cam[4]), int(cam[5])
     rgb = np.zeros((3, H, W), np.float64)
@@ -192,9 +194,33 @@ def render(g: Gaussians, pose, cam, opt=DEFAULT_OPT):
     tf = np.zeros((H, W), np.float64)
     tf32 = np.zeros((H, W), np.float32)
     last = np.zeros((H, W), np.int32)
+    d32 = np.zeros((H, W), np.float32)
     _check(lib.or_render(*g.args(), _p(g.rgb4), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_f32(opt)), _p(rgb),
-                         _p(depth), _p(alpha), _p(tf), _p(tf32), _p(last)), "render")
-    return dict(rgb=rgb, depth=depth, alpha=alpha, t_final=tf, t_final32=tf32, last=last)
+                         _p(depth), _p(alpha), _p(tf), _p(tf32), _p(last), _p(d32)), "render")
+    return dict(rgb=rgb, depth=depth, alpha=alpha, t_final=tf, t_final32=tf32, last=last, depth32=d32)
+
+
+# lambda_c of the tracking loss (Supp. A, per-dataset hyperparameters: 0.6 on
+# TUM-RGBD and ScanNet)
+TRACK_LAMBDA_C = 0.6
+
+
+def track_loss(r, t_rgb, t_depth, lambda_c=TRACK_LAMBDA_C):
+    """Frame-to-model tracking loss (Eq. 2 with the alpha^3 and inlier masks
+    of Supp. A) of a render ``r`` (a dict of ``render``) against FP32 targets.
+    Returns dict(loss, g_rgb, g_depth, inlier (bool [H,W]), median)."""
+    lib = _load()
+    H, W = r["depth"].shape
+    g_rgb = np.zeros((3, H, W), np.float64)
+    g_depth = np.zeros((H, W), np.float64)
+    inl = np.zeros((H, W), np.int8)
+    med = ctypes.c_float(0.0)
+    L = lib.or_track_loss(H, W, _p(_f64(r["rgb"])), _p(_f64(r["depth"])), _p(_f64(r["t_final"])),
+                          _p(_f32(r["depth32"])), _p(_f32(t_rgb)), _p(_f32(t_depth)), float(lambda_c), _p(g_rgb),
+                          _p(g_depth), _p(inl), ctypes.byref(med))
+    if L != L:
+        raise RuntimeError("oracle track_loss: out of memory")
+    return dict(loss=float(L), g_rgb=g_rgb, g_depth=g_depth, inlier=inl.astype(bool), median=float(med.value))
 
 
 def loss(rgb, depth, t_rgb, t_depth):
@@ -248,16 +274,18 @@ def pose_step(pose, state, grad, pivot, k, iters, hyper=DEFAULT_HYPER):
 
 
 def register_view(g: Gaussians, cam, t_rgb, t_depth, iters, pose0=None, opt=DEFAULT_OPT,
-                  hyper=DEFAULT_HYPER, history=False):
+                  hyper=DEFAULT_HYPER, history=False, track_lambda_c=None):
     """Keyframe localisation of one view (Sec. 3.2).  Returns (pose [3,4],
-    eps, loss history or None)."""
+    eps, loss history or None).  track_lambda_c: None = the registration
+    loss, else the tracking loss of Eq. 2 with that lambda_c."""
     lib = _load()
     pose = np.eye(3, 4, dtype=np.float64).reshape(12).copy() if pose0 is None else _f64(pose0, (12,)).copy()
     eps = ctypes.c_double(0.0)
     hist = np.zeros(max(iters, 1), np.float64) if history else None
+    trk = None if track_lambda_c is None else np.array([track_lambda_c], np.float64)
     _check(lib.or_register_view(*g.args(), _p(g.rgb4), _p(_f32(cam)), _p(_f32(opt)), _p(_f32(t_rgb)),
                                 _p(_f32(t_depth)), _p(_f64(hyper, (6,))), int(iters), _p(pose),
-                                ctypes.byref(eps), _p(hist)), "register_view")
+                                ctypes.byref(eps), _p(hist), _p(trk)), "register_view")
     return pose.reshape(3, 4), eps.value, (hist[:iters] if history else None)
 
 

@@ -483,14 +483,17 @@ typedef struct {
 
 /* Walks the tile list of pixel (px,py); fills the contributor list (if cl is
  * not NULL) and returns their number.  *Tf64, *Tf32: final transmittance;
- * *last: one past the list position of the last contributor. */
+ * *D32: the FP32 mirror of the depth (sum of z * (alpha * T) by fused
+ * multiply-adds in list order, alpha and T the mirror's); *last: one past
+ * the list position of the last contributor. */
 static int walk_pixel(const prep_t *p, const opts_t *op, int px, int py, contrib_t *cl,
-                      double *rgb, double *depth, const float *rgb4, double *Tf64, float *Tf32, long *last)
+                      double *rgb, double *depth, const float *rgb4, double *Tf64, float *Tf32, float *D32,
+                      long *last)
 {
     int tx = px / op->tile, ty = py / op->tile;
     long t = (long)ty * p->TX + tx;
     double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
-    float T32 = 1.0f;
+    float T32 = 1.0f, Dm = 0.0f;
     long lst = 0;
     int k = 0;
     double pxc = px + 0.5, pyc = py + 0.5;
@@ -522,6 +525,7 @@ static int walk_pixel(const prep_t *p, const opts_t *op, int px, int py, contrib
             cl[k].clamped = clamped;
         }
         ++k;
+        Dm = fmaf(p->g32[gi].z, a32 * T32, Dm);
         T = T * (1.0 - a);
         T32 = Tn32;
         lst = j - p->rstart[t] + 1;
@@ -531,6 +535,8 @@ static int walk_pixel(const prep_t *p, const opts_t *op, int px, int py, contrib
     *depth = D;
     *Tf64 = T;
     *Tf32 = T32;
+    if (D32)
+        *D32 = Dm;
     *last = lst;
     return k;
 }
@@ -546,16 +552,17 @@ static long max_list(const prep_t *p)
 
 static void composite(const prep_t *p, const opts_t *op, const float *rgb4, double *out_rgb,
                       double *out_depth, double *out_alpha, double *out_tf, float *out_tf32,
-                      int32_t *out_last)
+                      int32_t *out_last, float *out_depth32)
 {
     const long HW = (long)p->W * p->H;
     for (int py = 0; py < p->H; ++py)
         for (int px = 0; px < p->W; ++px) {
             double c[3], d, Tf;
-            float Tf32;
+            float Tf32, D32;
             long last;
-            walk_pixel(p, op, px, py, NULL, c, &d, rgb4, &Tf, &Tf32, &last);
+            walk_pixel(p, op, px, py, NULL, c, &d, rgb4, &Tf, &Tf32, &D32, &last);
             long pix = (long)py * p->W + px;
+            if (out_depth32) out_depth32[pix] = D32;
             for (int ch = 0; ch < 3; ++ch)
                 if (out_rgb)
                     out_rgb[ch * HW + pix] = c[ch];
@@ -599,7 +606,7 @@ static int adjoint_screen(const prep_t *p, const opts_t *op, const float *rgb4, 
             double c[3], d, Tf;
             float Tf32;
             long last;
-            int K = walk_pixel(p, op, px, py, cl, c, &d, rgb4, &Tf, &Tf32, &last);
+            int K = walk_pixel(p, op, px, py, cl, c, &d, rgb4, &Tf, &Tf32, NULL, &last);
             /* suffix sums S_i = sum_{j>i} c_j alpha_j T_j (+ T_f bg for colour) */
             double s[4] = {Tf * op->bg[0], Tf * op->bg[1], Tf * op->bg[2], 0.0};
             for (int i = K - 1; i >= 0; --i) {
@@ -884,12 +891,13 @@ int or_bin(int n, const float *means4, const float *scales4, const float *quats4
 }
 
 /* Renders n Gaussians transformed by pose at one camera.  Colour is planar
- * [3][H][W]; any output may be NULL.  tf32 is the mirror's FP32 final
- * transmittance, last is one past the tile-list position of the last
- * contributor (0 if none). */
+ * [3][H][W]; any output may be NULL.  tf32 and depth32 are the mirror's FP32
+ * final transmittance and depth, last is one past the tile-list position of
+ * the last contributor (0 if none). */
 int or_render(int n, const float *means4, const float *scales4, const float *quats4, const float *logits,
               const float *rgb4, const double *pose, const float *cam, const float *opt, double *out_rgb,
-              double *out_depth, double *out_alpha, double *out_tf, float *out_tf32, int32_t *out_last)
+              double *out_depth, double *out_alpha, double *out_tf, float *out_tf32, int32_t *out_last,
+              float *out_depth32)
 {
     opts_t op;
     read_opts(opt, &op);
@@ -898,7 +906,7 @@ int or_render(int n, const float *means4, const float *scales4, const float *qua
     prep_t p;
     int st = prep_camera(n, means4, scales4, quats4, logits, pose, cam, &op, &p);
     if (st == OR_OK)
-        composite(&p, &op, rgb4, out_rgb, out_depth, out_alpha, out_tf, out_tf32, out_last);
+        composite(&p, &op, rgb4, out_rgb, out_depth, out_alpha, out_tf, out_tf32, out_last, out_depth32);
     prep_free(&p);
     return st;
 }
@@ -925,6 +933,71 @@ double or_loss(int H, int W, const double *rgb, const double *depth, const doubl
             g_depth[k] = (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / (double)HW;
     }
     return lc / (3.0 * (double)HW) + ld / (double)HW;
+}
+
+static int cmp_float(const void *a, const void *b)
+{
+    const float x = *(const float *)a, y = *(const float *)b;
+    return (x > y) - (x < y);
+}
+
+/* Frame-to-model tracking loss of one view (Eq. 2, masks of Supp. A):
+ *   L = sum over pixels of M_in * M_a * (lambda_c |I^ - I|_1 + (1 - lambda_c) |D^ - D|)
+ * with |.|_1 over the three colour channels, M_a = alpha^3 (alpha = 1 - final
+ * transmittance; a weight, not differentiated), and the inlier mask M_in:
+ * pixels with a valid input depth (D > 0) whose depth error e = |D^ - D| is at
+ * most 50 times the median depth error over the valid pixels.  The median is
+ * the lower one (rank floor((m - 1) / 2) of the m valid errors); e and the
+ * threshold are taken in FP32 from the FP32 mirror of the rendered depth
+ * (depth32), as the kernels take them, so that the inlier decisions are
+ * exact.  Writes g_rgb = dL/dI^ and g_depth = dL/dD^ (mask held fixed;
+ * sign(0) = 0), inlier[HW] (1/0) and *median when the pointers are not NULL.
+ * Returns L, or NaN when out of memory. */
+double or_track_loss(int H, int W, const double *rgb, const double *depth, const double *tf,
+                     const float *depth32, const float *t_rgb, const float *t_depth, double lambda_c,
+                     double *g_rgb, double *g_depth, int8_t *inlier, float *median)
+{
+    const long HW = (long)H * W;
+    float *e = malloc((size_t)(HW > 0 ? HW : 1) * sizeof(float));
+    float *sorted = malloc((size_t)(HW > 0 ? HW : 1) * sizeof(float));
+    if (!e || !sorted) {
+        free(e);
+        free(sorted);
+        return NAN;
+    }
+    long m = 0;
+    for (long k = 0; k < HW; ++k) {
+        e[k] = fabsf(depth32[k] - t_depth[k]);
+        if (t_depth[k] > 0.0f)
+            sorted[m++] = e[k];
+    }
+    qsort(sorted, (size_t)m, sizeof(float), cmp_float);
+    const float med = m > 0 ? sorted[(m - 1) / 2] : 0.0f;
+    const float thr = 50.0f * med;
+    if (median)
+        *median = med;
+    double L = 0.0;
+    for (long k = 0; k < HW; ++k) {
+        const int in = m > 0 && t_depth[k] > 0.0f && e[k] <= thr;
+        if (inlier)
+            inlier[k] = (int8_t)in;
+        const double a = 1.0 - tf[k];
+        const double w = in ? a * a * a : 0.0;
+        double lc = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            const double d = rgb[ch * HW + k] - (double)t_rgb[ch * HW + k];
+            lc += fabs(d);
+            if (g_rgb)
+                g_rgb[ch * HW + k] = w * lambda_c * (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0));
+        }
+        const double dd = depth[k] - (double)t_depth[k];
+        if (g_depth)
+            g_depth[k] = w * (1.0 - lambda_c) * (dd > 0 ? 1.0 : (dd < 0 ? -1.0 : 0.0));
+        L += w * (lambda_c * lc + (1.0 - lambda_c) * fabs(dd));
+    }
+    free(e);
+    free(sorted);
+    return L;
 }
 
 /* Adjoint of or_render for given cotangents (any may be NULL).  twist[6]
@@ -1040,11 +1113,13 @@ int or_pose_step(double *pose, double *state, const double *grad, const double *
  * applied to the moving submap so that its render at the keyframe camera
  * matches the keyframe's colour and depth.  pose (in/out) starts at the
  * given value; eps_out = loss at the final pose; loss_hist[iters] (may be
- * NULL) records the loss at each iteration before its update. */
+ * NULL) records the loss at each iteration before its update.  track NULL:
+ * the registration loss (or_loss); otherwise the tracking loss of Eq. 2
+ * (or_track_loss) with lambda_c = track[0]. */
 int or_register_view(int n, const float *means4, const float *scales4, const float *quats4,
                      const float *logits, const float *rgb4, const float *cam, const float *opt,
                      const float *t_rgb, const float *t_depth, const double *hyper, int iters,
-                     double *pose, double *eps_out, double *loss_hist)
+                     double *pose, double *eps_out, double *loss_hist, const double *track)
 {
     opts_t op;
     read_opts(opt, &op);
@@ -1059,7 +1134,9 @@ int or_register_view(int n, const float *means4, const float *scales4, const flo
     double *acc = calloc((size_t)(n > 0 ? n : 1) * G_N, sizeof(double));
     double *trgb = malloc((size_t)HW * 3 * sizeof(double));
     double *tdep = malloc((size_t)HW * sizeof(double));
-    int st = (rgb && dep && grgb && gdep && acc && trgb && tdep) ? OR_OK : OR_ERR_OOM;
+    double *tf = malloc((size_t)HW * sizeof(double));
+    float *dep32 = malloc((size_t)HW * sizeof(float));
+    int st = (rgb && dep && grgb && gdep && acc && trgb && tdep && tf && dep32) ? OR_OK : OR_ERR_OOM;
     for (long k = 0; st == OR_OK && k < 3 * HW; ++k)
         trgb[k] = t_rgb[k];
     for (long k = 0; st == OR_OK && k < HW; ++k)
@@ -1070,8 +1147,12 @@ int or_register_view(int n, const float *means4, const float *scales4, const flo
         prep_t p;
         st = prep_camera(n, means4, scales4, quats4, logits, pose, cam, &op, &p);
         if (st == OR_OK) {
-            composite(&p, &op, rgb4, rgb, dep, NULL, NULL, NULL, NULL);
-            double L = or_loss(H, W, rgb, dep, trgb, tdep, grgb, gdep);
+            composite(&p, &op, rgb4, rgb, dep, NULL, tf, NULL, NULL, dep32);
+            double L = track ? or_track_loss(H, W, rgb, dep, tf, dep32, t_rgb, t_depth, track[0], grgb, gdep, NULL,
+                                             NULL)
+                             : or_loss(H, W, rgb, dep, trgb, tdep, grgb, gdep);
+            if (L != L)
+                st = OR_ERR_OOM;
             if (k == iters) {
                 *eps_out = L;
             } else {
@@ -1098,6 +1179,8 @@ int or_register_view(int n, const float *means4, const float *scales4, const flo
     free(acc);
     free(trgb);
     free(tdep);
+    free(tf);
+    free(dep32);
     return st;
 }
 

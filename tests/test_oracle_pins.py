@@ -498,3 +498,89 @@ def test_default_learning_rates_follow_the_paper():
     # real-data column (TUM-RGBD / ScanNet / ScanNet++) is the default
     assert O.DEFAULT_HYPER[0] == hp["lr_rotation"]["ScanNet"]
     assert O.DEFAULT_HYPER[1] == hp["lr_translation"]["ScanNet"]
+
+
+# ----------------------------------------------------------------- tracking loss (Eq. 2, Supp. A)
+def _fake_render(depth, tf, rgb=None):
+    depth = np.asarray(depth, np.float64)
+    H, W = depth.shape
+    return dict(rgb=np.zeros((3, H, W)) if rgb is None else np.asarray(rgb, np.float64), depth=depth,
+                t_final=np.asarray(tf, np.float64), depth32=depth.astype(np.float32))
+
+
+def test_track_loss_median_inliers_and_depth_weight():
+    # 2x3 image, alpha = 1 everywhere (T_final = 0), colours exact; depth
+    # errors 0.25, 0.5, 0.75, 1.0, 50 and one pixel without input depth.
+    # Valid errors sorted: 0.25 0.5 0.75 1 50 -> lower median 0.75, threshold
+    # 37.5: the 50 error is an outlier.  Loss = (1 - 0.6) * (0.25 + 0.5 + 0.75 + 1) = 1.
+    t_depth = np.array([[2.0, 2.0, 2.0], [2.0, 2.0, 0.0]], np.float32)
+    depth = np.array([[2.25, 1.5, 2.75], [3.0, 52.0, 7.0]])
+    r = _fake_render(depth, np.zeros((2, 3)))
+    out = O.track_loss(r, np.zeros((3, 2, 3), np.float32), t_depth, 0.6)
+    assert out["median"] == 0.75
+    np.testing.assert_array_equal(out["inlier"], [[True, True, True], [True, False, False]])
+    assert abs(out["loss"] - 1.0) < 1e-12
+    np.testing.assert_allclose(out["g_depth"], [[0.4, -0.4, 0.4], [0.4, 0.0, 0.0]], atol=1e-12)
+    assert not out["g_rgb"].any()  # colour errors are zero: sign(0) = 0
+
+
+def test_track_loss_alpha_cube_and_colour_weight():
+    # one pixel, alpha = 0.5 (weight 1/8), colour errors (0.5, -1, 0), depth exact:
+    # loss = 1/8 * 0.6 * 1.5 = 0.1125; dL/dI = 1/8 * 0.6 * sign = (0.075, -0.075, 0)
+    r = _fake_render([[2.0]], [[0.5]], rgb=np.array([0.5, 0.0, 0.25]).reshape(3, 1, 1))
+    t_rgb = np.array([0.0, 1.0, 0.25], np.float32).reshape(3, 1, 1)
+    out = O.track_loss(r, t_rgb, np.array([[2.0]], np.float32), 0.6)
+    assert out["median"] == 0.0 and out["inlier"][0, 0]
+    assert abs(out["loss"] - 0.1125) < 1e-12
+    np.testing.assert_allclose(out["g_rgb"].reshape(3), [0.075, -0.075, 0.0], atol=1e-15)
+    assert out["g_depth"][0, 0] == 0.0
+
+
+def test_track_loss_even_count_zero_median_and_no_valid_depth():
+    # even count: errors 1 2 3 4 -> lower median 2 (rank 1), all inliers
+    t = np.full((1, 4), 1.0, np.float32)
+    r = _fake_render([[2.0, 3.0, 4.0, 5.0]], np.zeros((1, 4)))
+    out = O.track_loss(r, np.zeros((3, 1, 4), np.float32), t, 0.5)
+    assert out["median"] == 2.0 and out["inlier"].all() and abs(out["loss"] - 0.5 * 10) < 1e-12
+    # zero median: only exact pixels are inliers (threshold 50 * 0 = 0)
+    r = _fake_render([[1.0, 1.0, 1.0, 6.0]], np.zeros((1, 4)))
+    out = O.track_loss(r, np.zeros((3, 1, 4), np.float32), t, 0.5)
+    np.testing.assert_array_equal(out["inlier"], [[True, True, True, False]])
+    assert out["loss"] == 0.0
+    # no valid input depth: nothing is an inlier
+    out = O.track_loss(r, np.ones((3, 1, 4), np.float32), np.zeros((1, 4), np.float32), 0.5)
+    assert not out["inlier"].any() and out["loss"] == 0.0 and not out["g_rgb"].any()
+
+
+def test_depth_mirror_tracks_fp64_depth():
+    c = synth.small_case(600, 64, 48, 56.0, seed=5)
+    g = O.Gaussians.from_dict(c["gaussians"])
+    r = O.render(g, np.eye(3, 4), c["cams"][0])
+    assert r["depth"].max() > 0.5
+    np.testing.assert_allclose(r["depth32"], r["depth"], rtol=2e-5, atol=2e-6)
+
+
+def test_tracking_hyperparameters_follow_the_paper():
+    hp = json.load(open(os.path.join(GOLDEN, "tracking_hyperparams.json")))
+    assert O.TRACK_LAMBDA_C == hp["lambda_c"]["ScanNet"]
+    assert hp["inlier_factor"] == 50 and hp["alpha_mask_power"] == 3
+
+
+def test_tracking_recovers_a_small_camera_motion():
+    # one plain-2k keyframe seen from a camera moved by 0.69 deg / 1.34 cm
+    # (the mean ScanNet frame motion): 40 iterations of the tracking loss at
+    # the paper's tracking learning rates recover it
+    hp = json.load(open(os.path.join(GOLDEN, "tracking_hyperparams.json")))
+    c = synth.plain_2k()
+    g = O.Gaussians.from_dict(c["gaussians"])
+    T = synth.about_point(synth.random_rigid(np.random.default_rng(77), 0.69, 0.0134),
+                          synth.centroid(c["gaussians"]))
+    cam = c["cams"][1]
+    tr = O.render(g, T, cam)
+    hyper = [hp["lr_rotation"]["ScanNet"], hp["lr_translation"]["ScanNet"]] + list(O.DEFAULT_HYPER[2:])
+    ang0, dt0 = _rot_err(np.eye(3, 4), T)
+    P, eps, hist = O.register_view(g, cam, tr["rgb"].astype(np.float32), tr["depth32"], 40, hyper=hyper,
+                                   history=True, track_lambda_c=O.TRACK_LAMBDA_C)
+    ang, dt = _rot_err(P, T)
+    assert ang < 0.2 * ang0 and dt < 0.2 * dt0, (ang, dt, ang0, dt0)
+    assert eps < 0.1 * hist[0]
