@@ -108,6 +108,11 @@ typedef struct {
     float adam_eps;    /* 1e-8 */
     float lr_final;    /* cosine decay of both rates to this fraction (0.001) */
     int32_t profile;   /* 1: gs_register times each phase with CUDA events (gs_ctx_stats) */
+    /* loss of the registration calls: 0 = the registration loss of Sec. 3.2
+     * (L1 colour + L1 depth means); 1 = the frame-to-model tracking loss of
+     * Eq. 2 with the masks of Supp. A (see gs_track_loss) */
+    int32_t tracking_loss;
+    float lambda_c;    /* colour weight of the tracking loss (0.6: TUM-RGBD / ScanNet, Supp. A) */
 } gs_options_t;
 
 /* Statistics of the last gs_register / gs_render call on a context. */
@@ -232,6 +237,23 @@ gs_status_t gs_loss(gs_ctx_t *ctx, const gs_camera_t *cams, int n_cams, const fl
                     const float *t_rgb, const float *t_depth, double *loss, float *d_rgb, float *d_depth,
                     gs_stream_t stream);
 
+/* Frame-to-model tracking loss per view (Eq. 2 with the masks of Supp. A):
+ *   L_v = sum over pixels of M_in * M_a * (lambda_c |I^ - I|_1 + (1 - lambda_c) |D^ - D|),
+ * |.|_1 over the colour channels, M_a = alpha^3 (alpha = 1 - t_final; a
+ * weight, not differentiated), M_in = 1 where the input depth D > 0 and the
+ * depth error e = |D^ - D| (FP32) is at most 50 times the view's median
+ * error (the lower median over pixels with D > 0; FP32 product 50 * median).
+ * Gradients (mask held fixed): dL/dI^ = M lambda_c sign(I^ - I),
+ * dL/dD^ = M (1 - lambda_c) sign(D^ - D), sign(0) = 0.  Images concatenated
+ * per camera as in gs_render (depth must be gs_render's FP32 depth for the
+ * inlier decisions to be reproducible).
+ *   loss [n_cams] double device out; d_rgb, d_depth, inlier (uint8 [pixels])
+ *   and median [n_cams] float device out or NULL. */
+gs_status_t gs_track_loss(gs_ctx_t *ctx, const gs_camera_t *cams, int n_cams, const float *rgb, const float *depth,
+                          const float *t_final, const float *t_rgb, const float *t_depth, float lambda_c,
+                          double *loss, float *d_rgb, float *d_depth, uint8_t *inlier, float *median,
+                          gs_stream_t stream);
+
 /* ---------------------------------------------------------- registration */
 
 /* One Adam step on the pose twist and the pose update about the pivot, for
@@ -317,6 +339,10 @@ typedef struct {
     int32_t n_src_views;
     const gs_view_t *tgt_views; /* host array of n_tgt_views */
     int32_t n_tgt_views;
+    /* this problem's learning rates and loss (lr_rot, lr_trans,
+     * tracking_loss, lambda_c; the other fields are the call's), or NULL =
+     * the call's options */
+    const gs_options_t *opt;
 } gs_problem_t;
 
 /* Batched 3DGS registration (Sec. 3.2 for each problem): all keyframe

@@ -21,7 +21,8 @@ enum Slot {
     S_VPS, S_GROUPS, S_TILEVP, S_POSE32, S_REC, S_AUX, S_COUNTS, S_PARTIALS, S_NDUPS, S_K0, S_K1, S_V0, S_V1,
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
-    S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_COUNT
+    S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
+    S_TMED, S_TNV, S_TVPS, S_COUNT
 };
 
 struct Buf {
@@ -182,6 +183,8 @@ gs_status_t check_options(gs_ctx *ctx, const gs_options_t *o)
     if (!(o->alpha_max > 0 && o->alpha_max <= 1) || !(o->alpha_min >= 0) || !(o->t_min >= 0) ||
         !(o->dilation >= 0) || !std::isfinite(o->z_near))
         return fail(ctx, GS_ERR_INVALID_ARG, "options out of range");
+    if ((o->tracking_loss != 0 && o->tracking_loss != 1) || !(o->lambda_c >= 0 && o->lambda_c <= 1))
+        return fail(ctx, GS_ERR_INVALID_ARG, "tracking_loss must be 0 or 1 and lambda_c in [0, 1]");
     return GS_OK;
 }
 
@@ -511,8 +514,9 @@ __global__ void k_to_float(const double *in, float *out, int n)
 // of P are localised in Q (Q moves; the estimate is inverted), keyframes of
 // Q in P (P moves).  Each moving submap is one Gaussian set.
 void add_problem(Plan &P, const gs_gaussians_t *src, const gs_gaussians_t *tgt, const gs_view_t *sv, int ns,
-                 const gs_view_t *tv, int nt, int problem, int &sets)
+                 const gs_view_t *tv, int nt, int problem, int &sets, const gs_options_t *o)
 {
+    const size_t v0 = P.vps.size();
     if (ns > 0) {
         const int set = sets++;
         for (int k = 0; k < ns; ++k)
@@ -523,6 +527,47 @@ void add_problem(Plan &P, const gs_gaussians_t *src, const gs_gaussians_t *tgt, 
         for (int k = 0; k < nt; ++k)
             add_vp(P, src, tv[k].cam, set, problem, 0, tv[k].rgb, tv[k].depth);
     }
+    for (size_t v = v0; v < P.vps.size(); ++v) {
+        P.vps[v].lr_rot = o->lr_rot;
+        P.vps[v].lr_trans = o->lr_trans;
+        P.vps[v].loss_kind = o->tracking_loss ? 1 : 0;
+        P.vps[v].lambda_c = o->lambda_c;
+    }
+}
+
+// per-pixel and per-keyframe scratch of the tracking loss, if the plan has
+// tracking keyframes (else ta.n_track = 0 and nothing is allocated)
+gs_status_t alloc_track(gs_ctx *ctx, const Plan &P, const DevPlan &D, gsl::RasterArgs &r, gsl::TrackArgs &ta,
+                        float *tloss, cudaStream_t s)
+{
+    ta = gsl::TrackArgs{};
+    std::vector<int> tv;
+    for (int v = 0; v < (int)P.vps.size(); ++v)
+        if (P.vps[v].loss_kind == 1)
+            tv.push_back(v);
+    if (tv.empty())
+        return GS_OK;
+    const size_t npix = (size_t)std::max<int64_t>(P.n_pix, 1), nv = P.vps.size();
+    int *tvd = nullptr;
+    GS_TRY(wsT(ctx, S_TERR, npix, &r.trk_err));
+    GS_TRY(wsT(ctx, S_TCOL, npix, &r.trk_col));
+    float *w = nullptr;
+    GS_TRY(wsT(ctx, S_TW, npix, &w));
+    r.trk_w = w;
+    GS_TRY(wsT(ctx, S_TMED, nv, &ta.med));
+    GS_TRY(wsT(ctx, S_TNV, nv, &ta.n_valid));
+    GS_TRY(upload(ctx, S_TVPS, tv, &tvd, s));
+    ta.vps = D.vps;
+    ta.tile_vp = D.tile_vp;
+    ta.n_tiles = (uint32_t)P.n_tiles;
+    ta.track_vps = tvd;
+    ta.n_track = (int)tv.size();
+    ta.t_final = r.t_final;
+    ta.err = r.trk_err;
+    ta.col = r.trk_col;
+    ta.w = w;
+    ta.tile_loss = tloss;
+    return GS_OK;
 }
 
 gs_status_t check_views(gs_ctx *ctx, const gs_view_t *v, int n)
@@ -575,6 +620,8 @@ void gs_default_options(gs_options_t *o)
     o->beta1 = 0.8f;
     o->beta2 = 0.99f;
     o->adam_eps = 1e-8f;
+    o->tracking_loss = 0;
+    o->lambda_c = 0.6f;
     o->lr_final = 0.001f;
 }
 
@@ -883,6 +930,53 @@ gs_status_t gs_loss(gs_ctx_t *ctx, const gs_camera_t *cams, int n_cams, const fl
     return GS_OK;
 }
 
+gs_status_t gs_track_loss(gs_ctx_t *ctx, const gs_camera_t *cams, int n_cams, const float *rgb, const float *depth,
+                          const float *t_final, const float *t_rgb, const float *t_depth, float lambda_c,
+                          double *loss, float *d_rgb, float *d_depth, uint8_t *inlier, float *median,
+                          gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    if (n_cams < 0 || (n_cams > 0 && (!cams || !rgb || !depth || !t_final || !t_rgb || !t_depth || !loss)) ||
+        !(lambda_c >= 0.0f && lambda_c <= 1.0f))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_track_loss: bad arguments");
+    for (int c = 0; c < n_cams; ++c)
+        GS_TRY(check_camera(ctx, cams[c]));
+    if (n_cams == 0)
+        return GS_OK;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gs_gaussians_t g{};
+    Plan P;
+    int64_t pix = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        add_vp(P, &g, cams[c], 0, 0, 0, t_rgb + 3 * pix, t_depth + pix);
+        P.vps.back().loss_kind = 1;
+        P.vps.back().lambda_c = lambda_c;
+        pix += (int64_t)cams[c].width * cams[c].height;
+    }
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    float *tloss = nullptr;
+    GS_TRY(wsT(ctx, S_TLOSS, (size_t)std::max<uint64_t>(P.n_tiles, 1), &tloss));
+    gsl::RasterArgs r{};
+    r.t_final = const_cast<float *>(t_final);
+    gsl::TrackArgs ta;
+    GS_TRY(alloc_track(ctx, P, D, r, ta, tloss, s));
+    ta.rgb = rgb;
+    ta.depth = depth;
+    ta.d_rgb = d_rgb;
+    ta.d_depth = d_depth;
+    ta.inlier = inlier;
+    gsl::track_prep(ta, rgb, depth, r.trk_err, r.trk_col, s);
+    gsl::track_loss(ta, s);
+    gsl::loss_reduce(D.vps, (int)P.vps.size(), tloss, loss, s);
+    if (median)
+        GS_CUDA(cudaMemcpyAsync(median, ta.med, sizeof(float) * (size_t)n_cams, cudaMemcpyDeviceToDevice, s));
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
 gs_status_t gs_pose_step(gs_ctx_t *ctx, int n, double *pose, double *state, const double *grad,
                          const double *pivot, int k, int iters, const gs_options_t *opt, gs_stream_t stream)
 {
@@ -965,7 +1059,7 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
     DeviceGuard dg(ctx->device);
     Plan P;
     int sets = 0;
-    add_problem(P, src, tgt, src_views, n_src_views, tgt_views, n_tgt_views, 0, sets);
+    add_problem(P, src, tgt, src_views, n_src_views, tgt_views, n_tgt_views, 0, sets, opt);
     return run_registration(ctx, P, 1, opt, iters, (cudaStream_t)stream, T_out, confidence, eps_out, est_out);
 }
 
@@ -977,14 +1071,18 @@ gs_status_t gs_register_batch(gs_ctx_t *ctx, const gs_problem_t *problems, int n
     GS_TRY(check_options(ctx, opt));
     if (n <= 0 || !problems || iters < 0 || !T_out || !conf_out)
         return fail(ctx, GS_ERR_INVALID_ARG, "gs_register_batch: bad arguments");
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
         GS_TRY(check_problem(ctx, problems[i]));
+        if (problems[i].opt)
+            GS_TRY(check_options(ctx, problems[i].opt));
+    }
     DeviceGuard dg(ctx->device);
     Plan P;
     int sets = 0;
     for (int i = 0; i < n; ++i) {
         const gs_problem_t &q = problems[i];
-        add_problem(P, &q.src, &q.tgt, q.src_views, q.n_src_views, q.tgt_views, q.n_tgt_views, i, sets);
+        add_problem(P, &q.src, &q.tgt, q.src_views, q.n_src_views, q.tgt_views, q.n_tgt_views, i, sets,
+                    q.opt ? q.opt : opt);
     }
     return run_registration(ctx, P, n, opt, iters, (cudaStream_t)stream, T_out, conf_out, eps_out, nullptr);
 }
@@ -1097,6 +1195,8 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         r.tile_twist = ttw;
         r.c_cam = ccam;
         r.tile_pairs = pairs;
+        gsl::TrackArgs ta;
+        GS_TRY(alloc_track(ctx, P, D, r, ta, tloss, s));
         cudaError_t mark_err = cudaSuccess;
         auto mark = [&](int k, cudaStream_t st) {
             // an event record node of the captured graph (re-targeted per replay)
@@ -1111,6 +1211,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             mark(2, st);
             r.vals = p.vals[c];
             gsl::forward(r, true, st);
+            gsl::track_loss(ta, st);
             mark(3, st);
             gsl::backward(r, true, false, st);
             mark(4, st);
@@ -1177,6 +1278,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         gsl::project(project_args(P, D, p, pose32, opt), s);
         r.vals = p.vals[run_bin(b, s)];
         gsl::forward(r, true, s);
+        gsl::track_loss(ta, s);
         gsl::PoseArgs fa = pa;
         fa.tile_twist = nullptr;
         fa.update = 0;
@@ -1391,6 +1493,7 @@ constexpr double kAdmitDupsPerRecord = 3.0;
 
 struct ServerReq {
     gs_gaussians_t src{}, tgt{};
+    gs_options_t opt{};  // learning rates and loss of this request
     std::vector<gs_view_t> sv, tv;
     int iters = 0;
     int state = 0;       // 0 waiting, 1 in flight, 2 done
@@ -1499,7 +1602,8 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     for (size_t i = 0; i < srv->active.size(); ++i) {
         ServerReq &r = srv->reqs[srv->active[i]];
         r.vp_first = (int)P.vps.size();
-        add_problem(P, &r.src, &r.tgt, r.sv.data(), (int)r.sv.size(), r.tv.data(), (int)r.tv.size(), (int)i, sets);
+        add_problem(P, &r.src, &r.tgt, r.sv.data(), (int)r.sv.size(), r.tv.data(), (int)r.tv.size(), (int)i, sets,
+                    &r.opt);
         for (int v = r.vp_first; v < (int)P.vps.size(); ++v)
             P.vps[v].iters = r.iters;
     }
@@ -1594,10 +1698,13 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     r.tile_twist = srv->ttw;
     r.c_cam = srv->ccam;
     r.tile_pairs = nullptr;
+    gsl::TrackArgs ta;
+    GS_TRY(alloc_track(ctx, P, D, r, ta, srv->tloss, s));
     GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     gsl::project(project_args(P, D, p, srv->pose32, &srv->opt), ctx->cap);
     r.vals = p.vals[run_bin(b, ctx->cap)];
     gsl::forward(r, true, ctx->cap);
+    gsl::track_loss(ta, ctx->cap);
     gsl::backward(r, true, false, ctx->cap);
     gsl::pose_update(pa, ctx->cap);
     cudaGraph_t graph = nullptr;
@@ -1773,9 +1880,12 @@ gs_status_t gs_server_submit(gs_server_t *srv, const gs_problem_t *q, int iters,
     if (iters < 0)
         return fail(ctx, GS_ERR_INVALID_ARG, "iters must be >= 0");
     GS_TRY(check_problem(ctx, *q));
+    if (q->opt)
+        GS_TRY(check_options(ctx, q->opt));
     if (q->n_src_views + q->n_tgt_views > srv->max_kf)
         return fail(ctx, GS_ERR_INVALID_ARG, "request has more keyframes than the server's max_keyframes");
     ServerReq r;
+    r.opt = q->opt ? *q->opt : srv->opt;
     r.src = q->src;
     r.tgt = q->tgt;
     r.sv.assign(q->src_views, q->src_views + q->n_src_views);

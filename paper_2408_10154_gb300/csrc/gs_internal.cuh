@@ -41,6 +41,9 @@ struct VpDesc {
     int reverse;           // 1: keyframe of P localised in Q (estimate is inverted)
     int iters;             // pose updates of this keyframe's problem (0: the call's count); once
                            // taken, the pose is frozen and later iterations only re-measure the loss
+    float lr_rot, lr_trans;  // Adam learning rates of this keyframe's problem
+    int loss_kind;         // 0: registration L1 means; 1: tracking loss (Eq. 2, masks of Supp. A)
+    float lambda_c;        // tracking loss colour weight
 };
 
 // A projection group: vps that share one Gaussian set and are projected by
@@ -241,10 +244,40 @@ struct RasterArgs {
     double *tile_twist;       // [tiles][6], camera frame
     const double *c_cam;      // [vp][3] pivot in camera frame
     float *dup_grads;         // [dups][10] screen-space partials (full mode)
+    // tracking-loss keyframes (loss_kind 1): the forward writes the FP32
+    // depth error (+inf without input depth) and the colour L1 per pixel;
+    // the backward scales the loss signs by the per-pixel mask weight
+    float *trk_err, *trk_col;
+    const float *trk_w;
 };
 void forward(const RasterArgs &a, bool registration, cudaStream_t s);
 void raster_init();  // one-time kernel attributes (before any graph capture)
 void backward(const RasterArgs &a, bool registration, bool full, cudaStream_t s);
+
+// Tracking loss (Eq. 2, masks of Supp. A) of the tracking keyframes of a
+// plan: per keyframe the lower median of the valid depth errors (radix
+// select), then per pixel the mask weight M_in * alpha^3 and per tile the
+// loss (overwriting the tile's registration loss).
+struct TrackArgs {
+    const gsk::VpDesc *vps;
+    const uint32_t *tile_vp;
+    uint32_t n_tiles;
+    const int *track_vps;     // [n_track] vp indices with loss_kind 1
+    int n_track;
+    const float *t_final;     // [pix]
+    const float *err, *col;   // [pix] from the forward (or k_track_prep)
+    float *med;               // [vp] median depth error
+    int *n_valid;             // [vp] pixels with input depth
+    float *w;                 // [pix] out: M_in * alpha^3
+    float *tile_loss;         // [tiles] out
+    // standalone gs_track_loss: cotangents and the inlier mask (may be null)
+    const float *rgb, *depth;
+    float *d_rgb, *d_depth;
+    uint8_t *inlier;
+};
+void track_loss(const TrackArgs &a, cudaStream_t s);
+// err / col of rendered images (standalone gs_track_loss)
+void track_prep(const TrackArgs &a, const float *rgb, const float *depth, float *err, float *col, cudaStream_t s);
 
 struct PoseArgs {
     const gsk::VpDesc *vps;
@@ -264,6 +297,8 @@ struct PoseArgs {
     int update;                // 0: only reduce loss / gradient
 };
 void pose_update(const PoseArgs &a, cudaStream_t s);
+// per-keyframe sum of the tile losses (FP64, fixed order)
+void loss_reduce(const gsk::VpDesc *vps, int n_vps, const float *tile_loss, double *loss_out, cudaStream_t s);
 void pose_init(const PoseArgs &a, cudaStream_t s);
 void centroids(const gsk::VpDesc *vps, const int *set_vp, int n_sets, double *centroid, cudaStream_t s);
 

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
     if (k >= iters)
         return;
     double *P = a.pose64 + 12 * vp;
-    adam_exp_update(P, a.adam + 13 * vp, g, a.pivot + 3 * vp, k, iters, a.lr_rot, a.lr_trans, a.beta1, a.beta2,
+    adam_exp_update(P, a.adam + 13 * vp, g, a.pivot + 3 * vp, k, iters, d.lr_rot, d.lr_trans, a.beta1, a.beta2,
                     a.eps, a.lr_final);
     for (int k = 0; k < 12; ++k)
         a.pose32[12 * vp + k] = (float)P[k];
@@ -427,6 +427,19 @@ void loss(const VpDesc *vps, int n_vps, uint32_t n_tiles, const uint32_t *tile_v
     a.loss = loss_out;
     k_pose_update<<<n_vps, 256, 0, s>>>(a);
     g_launches += 2;
+}
+
+void loss_reduce(const VpDesc *vps, int n_vps, const float *tile_loss, double *loss_out, cudaStream_t s)
+{
+    if (n_vps <= 0)
+        return;
+    PoseArgs a{};
+    a.vps = vps;
+    a.n_vps = n_vps;
+    a.tile_loss = tile_loss;
+    a.loss = loss_out;
+    k_pose_update<<<n_vps, 256, 0, s>>>(a);
+    ++g_launches;
 }
 
 void transform(const float4 *means, const float4 *quats, int64_t n, const double *T, float4 *out_means,

@@ -190,6 +190,11 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
         a.code[pix] = (uint8_t)(sg(e0) | (sg(e1) << 2) | (sg(e2) << 4) | (sg(ed) << 6));
         a.t_final[pix] = T;
         a.last[pix] = last;
+        if (d.loss_kind == 1) {
+            // tracking loss: depth error (+inf without input depth) and colour L1 for its masks
+            a.trk_err[pix] = d.t_depth[off] > 0.0f ? fabsf(ed) : __uint_as_float(0x7f800000u);
+            a.trk_col[pix] = fabsf(e0) + fabsf(e1) + fabsf(e2);
+        }
     }
     lsum = warp_sum(lsum);
     const int wl = warp_sum(last), wc = warp_sum(n_contrib);
@@ -570,7 +575,13 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
         if (REG) {
             const uint32_t c = a.code[pix];
             auto dec = [](uint32_t v) -> float { return v == 1u ? 1.0f : (v == 2u ? -1.0f : 0.0f); };
-            const float inv3 = 1.0f / (3.0f * (float)HW), inv1 = 1.0f / (float)HW;
+            // registration: means over 3HW and HW; tracking: mask weight x lambda_c, x (1 - lambda_c)
+            float inv3 = 1.0f / (3.0f * (float)HW), inv1 = 1.0f / (float)HW;
+            if (d.loss_kind == 1) {
+                const float w = a.trk_w[pix];
+                inv3 = w * d.lambda_c;
+                inv1 = w * (1.0f - d.lambda_c);
+            }
             P.gr = dec(c & 3u) * inv3;
             P.gg = dec((c >> 2) & 3u) * inv3;
             P.gb = dec((c >> 4) & 3u) * inv3;

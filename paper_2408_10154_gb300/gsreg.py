@@ -52,7 +52,8 @@ class gs_options_t(ctypes.Structure):
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("smooth", ctypes.c_int32), ("lr_rot", ctypes.c_float),
                 ("lr_trans", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("adam_eps", ctypes.c_float), ("lr_final", ctypes.c_float), ("profile", ctypes.c_int32)]
+                ("adam_eps", ctypes.c_float), ("lr_final", ctypes.c_float), ("profile", ctypes.c_int32),
+                ("tracking_loss", ctypes.c_int32), ("lambda_c", ctypes.c_float)]
 
 
 class gs_stats_t(ctypes.Structure):
@@ -68,7 +69,8 @@ class gs_gaussian_grads_t(ctypes.Structure):
 
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
-           "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc", "gs_server_create",
+           "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc", "gs_track_loss",
+           "gs_server_create",
            "gs_server_destroy", "gs_server_last_error", "gs_server_submit", "gs_server_step", "gs_server_poll",
            "gs_server_counts"]
 
@@ -106,6 +108,7 @@ def load(build_if_missing: bool = False):
             "gs_render": ([P, P, P, P, I, P, P, P, P, P, P, P], I),
             "gs_render_backward": ([P, P, P, P, I, P, P, P, P, P, P, P, P, P, P], I),
             "gs_loss": ([P, P, I, P, P, P, P, P, P, P, P], I),
+            "gs_track_loss": ([P, P, I, P, P, P, P, P, ctypes.c_float, P, P, P, P, P, P], I),
             "gs_pose_step": ([P, I, P, P, P, P, I, I, P, P], I),
             "gs_fuse": ([P, I, P, P, P, P, P, P], I),
             "gs_register": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P], I),
@@ -328,6 +331,23 @@ def gs_loss(ctx: Context, cams, rgb, depth, t_rgb, t_depth):
     return loss, d_rgb, d_depth
 
 
+def gs_track_loss(ctx: Context, cams, rgb, depth, t_final, t_rgb, t_depth, lambda_c=0.6):
+    """Tracking loss (Eq. 2 with the masks of Supp. A) of rendered images.
+    Returns (loss [n] float64, d_rgb, d_depth, inlier (uint8 per pixel),
+    median [n] float32)."""
+    cam_arr, nc = cameras(cams)
+    dev = rgb.device
+    loss = torch.empty(nc, dtype=torch.float64, device=dev)
+    d_rgb = torch.empty_like(rgb)
+    d_depth = torch.empty_like(depth)
+    inl = torch.empty(depth.shape, dtype=torch.uint8, device=dev)
+    med = torch.empty(nc, dtype=torch.float32, device=dev)
+    ctx.check(ctx._lib.gs_track_loss(ctx.handle, cam_arr, nc, _ptr(rgb), _ptr(depth), _ptr(t_final), _ptr(t_rgb),
+                                     _ptr(t_depth), float(lambda_c), _ptr(loss), _ptr(d_rgb), _ptr(d_depth),
+                                     _ptr(inl), _ptr(med), _stream()))
+    return loss, d_rgb, d_depth, inl, med
+
+
 def gs_pose_step(ctx: Context, pose, state, grad, pivot, k, iters, opt=None):
     """In place on ``pose`` [n,12] and ``state`` [n,13] (float64 CUDA)."""
     opt = opt or default_options()
@@ -410,24 +430,35 @@ def gs_render_noalloc(g: Gaussians, poses: torch.Tensor, cams, opt=None, out=Non
 
 class gs_problem_t(ctypes.Structure):
     _fields_ = [("src", gs_gaussians_t), ("tgt", gs_gaussians_t), ("src_views", ctypes.c_void_p),
-                ("n_src_views", ctypes.c_int32), ("tgt_views", ctypes.c_void_p), ("n_tgt_views", ctypes.c_int32)]
+                ("n_src_views", ctypes.c_int32), ("tgt_views", ctypes.c_void_p), ("n_tgt_views", ctypes.c_int32),
+                ("opt", ctypes.c_void_p)]
+
+
+def _problem(p, keep):
+    """gs_problem_t of (src, tgt, src_views, tgt_views[, options]); the ctypes
+    arrays it points to are appended to ``keep``."""
+    s, t, sv, tv = p[:4]
+    o = p[4] if len(p) > 4 else None
+    sva, tva = _views(sv), _views(tv)
+    keep += [sva, tva, o]
+    return gs_problem_t(s.c_struct(), t.c_struct(), ctypes.cast(sva, ctypes.c_void_p), len(sv),
+                        ctypes.cast(tva, ctypes.c_void_p), len(tv),
+                        ctypes.cast(ctypes.pointer(o), ctypes.c_void_p) if o is not None else None)
 
 
 def gs_register_batch(ctx: Context, problems, iters, opt=None):
     """Batched registration.  ``problems``: list of (src Gaussians, tgt
-    Gaussians, src_views, tgt_views) with views as in gs_register.  Returns
-    (T [n,3,4] float64, confidence [n], eps [sum of keyframes])."""
+    Gaussians, src_views, tgt_views[, gs_options_t of this problem]) with
+    views as in gs_register.  Returns (T [n,3,4] float64, confidence [n],
+    eps [sum of keyframes])."""
     opt = opt or default_options()
     n = len(problems)
     arr = (gs_problem_t * n)()
     keep = []
     total = 0
-    for i, (s, t, sv, tv) in enumerate(problems):
-        sva, tva = _views(sv), _views(tv)
-        keep += [sva, tva]
-        arr[i] = gs_problem_t(s.c_struct(), t.c_struct(), ctypes.cast(sva, ctypes.c_void_p), len(sv),
-                              ctypes.cast(tva, ctypes.c_void_p), len(tv))
-        total += len(sv) + len(tv)
+    for i, p in enumerate(problems):
+        arr[i] = _problem(p, keep)
+        total += len(p[2]) + len(p[3])
     T = np.zeros((n, 12), np.float64)
     conf = np.zeros(n, np.float64)
     eps = np.zeros(max(total, 1), np.float64)
@@ -461,13 +492,14 @@ class Server:
         if st != 0:
             raise GsError(st, self._lib.gs_server_last_error(self.handle).decode())
 
-    def submit(self, src: Gaussians, tgt: Gaussians, src_views, tgt_views, iters: int) -> int:
-        sva, tva = _views(src_views), _views(tgt_views)
-        q = gs_problem_t(src.c_struct(), tgt.c_struct(), ctypes.cast(sva, ctypes.c_void_p), len(src_views),
-                         ctypes.cast(tva, ctypes.c_void_p), len(tgt_views))
+    def submit(self, src: Gaussians, tgt: Gaussians, src_views, tgt_views, iters: int, opt=None) -> int:
+        """Queues a request; ``opt`` (gs_options_t or None = the server's)
+        sets its learning rates and loss."""
+        keep = []
+        q = _problem((src, tgt, src_views, tgt_views, opt), keep)
         rid = ctypes.c_int64()
         self.check(self._lib.gs_server_submit(self.handle, ctypes.byref(q), int(iters), ctypes.byref(rid)))
-        self._keep[rid.value] = (src, tgt, src_views, tgt_views, sva, tva)
+        self._keep[rid.value] = (src, tgt, src_views, tgt_views, keep)
         self._nvps[rid.value] = len(src_views) + len(tgt_views)
         return rid.value
 
