@@ -80,7 +80,9 @@ def _load():
         lib.or_loss.restype = ctypes.c_double
         lib.or_backward.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.or_pose_step.argtypes = [P, P, P, P, P, I, I]
-        lib.or_register_view.argtypes = [I, P, P, P, P, P, P, P, P, P, P, I, P, P, P, P]
+        lib.or_register_view.argtypes = [I, P, P, P, P, P, P, P, P, P, P, I, P, P, P, P, P, P]
+        lib.or_exposure_loss.argtypes = [I, I, P, P, P, P, P, P, P, P]
+        lib.or_exposure_loss.restype = ctypes.c_double
         lib.or_track_loss.argtypes = [I, I, P, P, P, P, P, P, ctypes.c_double, P, P, P, P]
         lib.or_track_loss.restype = ctypes.c_double
         lib.or_transform.argtypes = [I, P, P, P, P, P]
@@ -274,19 +276,40 @@ def pose_step(pose, state, grad, pivot, k, iters, hyper=DEFAULT_HYPER):
 
 
 def register_view(g: Gaussians, cam, t_rgb, t_depth, iters, pose0=None, opt=DEFAULT_OPT,
-                  hyper=DEFAULT_HYPER, history=False, track_lambda_c=None):
+                  hyper=DEFAULT_HYPER, history=False, track_lambda_c=None, lr_exposure=None):
     """Keyframe localisation of one view (Sec. 3.2).  Returns (pose [3,4],
-    eps, loss history or None).  track_lambda_c: None = the registration
-    loss, else the tracking loss of Eq. 2 with that lambda_c."""
+    eps, loss history or None), plus the exposure (a, b) when
+    ``lr_exposure`` is given.  track_lambda_c: None = the registration loss,
+    else the tracking loss of Eq. 2 with that lambda_c."""
     lib = _load()
     pose = np.eye(3, 4, dtype=np.float64).reshape(12).copy() if pose0 is None else _f64(pose0, (12,)).copy()
     eps = ctypes.c_double(0.0)
     hist = np.zeros(max(iters, 1), np.float64) if history else None
     trk = None if track_lambda_c is None else np.array([track_lambda_c], np.float64)
+    ex = None if lr_exposure is None else np.array([lr_exposure], np.float64)
+    ab = np.zeros(2, np.float64)
     _check(lib.or_register_view(*g.args(), _p(g.rgb4), _p(_f32(cam)), _p(_f32(opt)), _p(_f32(t_rgb)),
                                 _p(_f32(t_depth)), _p(_f64(hyper, (6,))), int(iters), _p(pose),
-                                ctypes.byref(eps), _p(hist), _p(trk)), "register_view")
-    return pose.reshape(3, 4), eps.value, (hist[:iters] if history else None)
+                                ctypes.byref(eps), _p(hist), _p(trk), _p(ex), _p(ab)), "register_view")
+    out = (pose.reshape(3, 4), eps.value, (hist[:iters] if history else None))
+    return out + (ab,) if lr_exposure is not None else out
+
+
+def exposure_loss(rgb, depth, t_rgb, t_depth, ab):
+    """Registration loss of the exposure-compensated colour e^a I^ + b
+    (Supp. B).  Returns (L, dL/dI^ of the raw render, dL/dD^, (dL/da, dL/db))."""
+    lib = _load()
+    rgb = _f64(rgb)
+    depth = _f64(depth)
+    H, W = depth.shape
+    g_rgb = np.zeros_like(rgb)
+    g_depth = np.zeros_like(depth)
+    g_ab = np.zeros(2, np.float64)
+    L = lib.or_exposure_loss(H, W, _p(rgb), _p(depth), _p(_f64(t_rgb)), _p(_f64(t_depth)), _p(_f64(ab, (2,))),
+                             _p(g_rgb), _p(g_depth), _p(g_ab))
+    if L != L:
+        raise RuntimeError("oracle exposure_loss: out of memory")
+    return float(L), g_rgb, g_depth, g_ab
 
 
 def transform(g: Gaussians, T):

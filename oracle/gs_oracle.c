@@ -935,6 +935,62 @@ double or_loss(int H, int W, const double *rgb, const double *depth, const doubl
     return lc / (3.0 * (double)HW) + ld / (double)HW;
 }
 
+/* Registration loss with exposure compensation (Supp. B: the exposure of
+ * each keyframe is optimised with its pose).  The compensated colour is
+ * e^a I^ + b (one gain and one offset per keyframe, shared by the three
+ * channels); returns or_loss of the compensated colour, and writes
+ * g_rgb = dL/dI^ (the raw render's cotangent, e^a times the compensated
+ * one), g_depth, and g_ab = (dL/da, dL/db). */
+double or_exposure_loss(int H, int W, const double *rgb, const double *depth, const double *t_rgb,
+                        const double *t_depth, const double *ab, double *g_rgb, double *g_depth, double *g_ab)
+{
+    const long HW = (long)H * W;
+    double *x = malloc((size_t)(3 * HW > 0 ? 3 * HW : 1) * sizeof(double));
+    double *gx = malloc((size_t)(3 * HW > 0 ? 3 * HW : 1) * sizeof(double));
+    if (!x || !gx) {
+        free(x);
+        free(gx);
+        return NAN;
+    }
+    const double ea = exp(ab[0]);
+    for (long k = 0; k < 3 * HW; ++k)
+        x[k] = ea * rgb[k] + ab[1];
+    const double L = or_loss(H, W, x, depth, t_rgb, t_depth, gx, g_depth);
+    double ga = 0.0, gb = 0.0;
+    for (long k = 0; k < 3 * HW; ++k) {
+        ga += gx[k] * ea * rgb[k];
+        gb += gx[k];
+        if (g_rgb)
+            g_rgb[k] = ea * gx[k];
+    }
+    if (g_ab) {
+        g_ab[0] = ga;
+        g_ab[1] = gb;
+    }
+    free(x);
+    free(gx);
+    return L;
+}
+
+/* One Adam step on the exposure (a, b): the pose's moments and cosine
+ * schedule (hyper as in or_pose_step) with learning rate lr_exposure;
+ * state[5] = m_a, m_b, v_a, v_b, steps taken. */
+static void exposure_step(double *ab, double *state, const double *g, const double *hyper, double lr_exposure, int k,
+                          int iters)
+{
+    const double b1 = hyper[2], b2 = hyper[3], eps = hyper[4], f = hyper[5];
+    const double t = state[4] + 1.0;
+    state[4] = t;
+    const double sched = f + (1.0 - f) * 0.5 * (1.0 + cos(M_PI * (double)k / (double)iters));
+    for (int i = 0; i < 2; ++i) {
+        state[i] = b1 * state[i] + (1.0 - b1) * g[i];
+        state[2 + i] = b2 * state[2 + i] + (1.0 - b2) * g[i] * g[i];
+        const double mh = state[i] / (1.0 - pow(b1, t));
+        const double vh = state[2 + i] / (1.0 - pow(b2, t));
+        ab[i] -= lr_exposure * sched * mh / (sqrt(vh) + eps);
+    }
+}
+
 static int cmp_float(const void *a, const void *b)
 {
     const float x = *(const float *)a, y = *(const float *)b;
@@ -1115,16 +1171,21 @@ int or_pose_step(double *pose, double *state, const double *grad, const double *
  * given value; eps_out = loss at the final pose; loss_hist[iters] (may be
  * NULL) records the loss at each iteration before its update.  track NULL:
  * the registration loss (or_loss); otherwise the tracking loss of Eq. 2
- * (or_track_loss) with lambda_c = track[0]. */
+ * (or_track_loss) with lambda_c = track[0].  expo NULL: no exposure
+ * compensation; otherwise the keyframe's exposure (a, b), starting at 0, is
+ * optimised with the pose at learning rate expo[0] (or_exposure_loss;
+ * registration loss only) and returned in ab_out[2] (may be NULL). */
 int or_register_view(int n, const float *means4, const float *scales4, const float *quats4,
                      const float *logits, const float *rgb4, const float *cam, const float *opt,
                      const float *t_rgb, const float *t_depth, const double *hyper, int iters,
-                     double *pose, double *eps_out, double *loss_hist, const double *track)
+                     double *pose, double *eps_out, double *loss_hist, const double *track, const double *expo,
+                     double *ab_out)
 {
     opts_t op;
     read_opts(opt, &op);
-    if (n < 0 || iters < 0 || !check_cam(cam, &op))
+    if (n < 0 || iters < 0 || !check_cam(cam, &op) || (track && expo))
         return OR_ERR_ARG;
+    double ab[2] = {0.0, 0.0}, ab_state[5] = {0, 0, 0, 0, 0}, gab[2] = {0.0, 0.0};
     const int W = (int)cam[4], H = (int)cam[5];
     const long HW = (long)W * H;
     double *rgb = malloc((size_t)HW * 3 * sizeof(double));
@@ -1148,9 +1209,10 @@ int or_register_view(int n, const float *means4, const float *scales4, const flo
         st = prep_camera(n, means4, scales4, quats4, logits, pose, cam, &op, &p);
         if (st == OR_OK) {
             composite(&p, &op, rgb4, rgb, dep, NULL, tf, NULL, NULL, dep32);
-            double L = track ? or_track_loss(H, W, rgb, dep, tf, dep32, t_rgb, t_depth, track[0], grgb, gdep, NULL,
-                                             NULL)
-                             : or_loss(H, W, rgb, dep, trgb, tdep, grgb, gdep);
+            double L = track  ? or_track_loss(H, W, rgb, dep, tf, dep32, t_rgb, t_depth, track[0], grgb, gdep, NULL,
+                                              NULL)
+                       : expo ? or_exposure_loss(H, W, rgb, dep, trgb, tdep, ab, grgb, gdep, gab)
+                              : or_loss(H, W, rgb, dep, trgb, tdep, grgb, gdep);
             if (L != L)
                 st = OR_ERR_OOM;
             if (k == iters) {
@@ -1167,6 +1229,8 @@ int or_register_view(int n, const float *means4, const float *scales4, const flo
                         c[i] = R[i][0] * mbar[0] + R[i][1] * mbar[1] + R[i][2] * mbar[2] + t[i];
                     chain(&p, pose, cam, acc, c, logits, tw, NULL, NULL, NULL, NULL, NULL);
                     or_pose_step(pose, state, tw, c, hyper, k, iters);
+                    if (expo)
+                        exposure_step(ab, ab_state, gab, hyper, expo[0], k, iters);
                 }
             }
         }
@@ -1181,6 +1245,10 @@ int or_register_view(int n, const float *means4, const float *scales4, const flo
     free(tdep);
     free(tf);
     free(dep32);
+    if (ab_out) {
+        ab_out[0] = ab[0];
+        ab_out[1] = ab[1];
+    }
     return st;
 }
 

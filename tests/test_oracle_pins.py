@@ -584,3 +584,53 @@ def test_tracking_recovers_a_small_camera_motion():
     ang, dt = _rot_err(P, T)
     assert ang < 0.2 * ang0 and dt < 0.2 * dt0, (ang, dt, ang0, dt0)
     assert eps < 0.1 * hist[0]
+
+
+# ----------------------------------------------------------------- exposure compensation (Supp. B)
+def test_exposure_loss_reduces_to_l1_and_matches_finite_differences():
+    rng = np.random.default_rng(12)
+    rgb, depth = rng.uniform(0, 1, (3, 6, 5)), rng.uniform(1, 3, (6, 5))
+    t_rgb, t_depth = rng.uniform(0, 1, (3, 6, 5)), rng.uniform(1, 3, (6, 5))
+    # zero exposure: exactly the registration loss
+    L0, g0, gd0, _ = O.exposure_loss(rgb, depth, t_rgb, t_depth, [0.0, 0.0])
+    L1, g1, gd1 = O.loss(rgb, depth, t_rgb, t_depth)
+    assert L0 == L1
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(gd0, gd1)
+    # gain / offset gradient and the raw render's cotangent by central differences
+    ab = np.array([0.2, -0.05])
+    L, g, gd, gab = O.exposure_loss(rgb, depth, t_rgb, t_depth, ab)
+    h = 1e-7
+    for i in range(2):
+        e = np.zeros(2)
+        e[i] = h
+        fd = (O.exposure_loss(rgb, depth, t_rgb, t_depth, ab + e)[0] -
+              O.exposure_loss(rgb, depth, t_rgb, t_depth, ab - e)[0]) / (2 * h)
+        assert abs(fd - gab[i]) <= 1e-6 * max(1.0, abs(gab[i])), (i, fd, gab[i])
+    for idx in [(0, 1, 2), (2, 5, 4)]:
+        r2 = rgb.copy()
+        r2[idx] += h
+        r3 = rgb.copy()
+        r3[idx] -= h
+        fd = (O.exposure_loss(r2, depth, t_rgb, t_depth, ab)[0] - O.exposure_loss(r3, depth, t_rgb, t_depth, ab)[0]) / (
+            2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * abs(g[idx]), (idx, fd, g[idx])
+
+
+def test_exposure_compensation_recovers_gain_offset_and_pose():
+    # a keyframe of the 2k workload whose colours were taken with another
+    # exposure (gain e^0.15, offset -0.03): registering pose and exposure
+    # together (Supp. B rate 0.1) recovers both; pose alone cannot fit it
+    hp = json.load(open(os.path.join(GOLDEN, "loop_closure_hyperparams.json")))
+    c = synth.plain_2k()
+    g = O.Gaussians.from_dict(c["gaussians"])
+    T = c["T_gt"]
+    cam = c["cams"][0]
+    tr = O.render(g, T, cam)
+    t_rgb = (math.exp(0.15) * tr["rgb"] - 0.03).astype(np.float32)
+    P, eps, _, ab = O.register_view(g, cam, t_rgb, tr["depth"], 50, lr_exposure=hp["lr_exposure"]["ScanNet"])
+    ang, dt = _rot_err(P, T)
+    assert ang < 0.05 and dt < 2e-3, (ang, dt)
+    assert abs(ab[0] - 0.15) < 0.01 and abs(ab[1] + 0.03) < 0.005, ab
+    P2, eps2, _ = O.register_view(g, cam, t_rgb, tr["depth"], 50)
+    assert eps2 > 5 * eps
