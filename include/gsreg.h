@@ -107,12 +107,20 @@ typedef struct {
     float beta2;       /* 0.99 */
     float adam_eps;    /* 1e-8 */
     float lr_final;    /* cosine decay of both rates to this fraction (0.001) */
-    int32_t profile;   /* 1: gs_register times each phase with CUDA events (gs_ctx_stats) */
+    int32_t profile;   /* 1: gs_register times each phase with CUDA events (gs_ctx_stats);
+                          2: also counts the pairs that pass the alpha test (a slower forward
+                          variant: use a separate call for the count, 1 for timing) */
     /* loss of the registration calls: 0 = the registration loss of Sec. 3.2
      * (L1 colour + L1 depth means); 1 = the frame-to-model tracking loss of
      * Eq. 2 with the masks of Supp. A (see gs_track_loss) */
     int32_t tracking_loss;
     float lambda_c;    /* colour weight of the tracking loss (0.6: TUM-RGBD / ScanNet, Supp. A) */
+    /* exposure compensation of the registration loss (Supp. B): each keyframe
+     * problem fits a gain e^a and an offset b of the rendered colour
+     * (e^a I^ + b, shared by the channels; a = b = 0 at the start) with its
+     * pose; not combinable with tracking_loss */
+    int32_t exposure;
+    float lr_exposure; /* 0.1 (Supp. B) */
 } gs_options_t;
 
 /* Statistics of the last gs_register / gs_render call on a context. */
@@ -127,8 +135,8 @@ typedef struct {
      * iterations: project, bin (scan+emit+sort+ranges), forward+loss,
      * backward, pose update */
     double phase_ms[5];
-    int64_t contributing;    /* sum over iterations of the (pixel, Gaussian) pairs that pass the
-                                alpha test before the early stop (the pairs that carry gradient) */
+    int64_t contributing;    /* profile = 2 only (else 0): sum over iterations of the (pixel,
+                                Gaussian) pairs that pass the alpha test before the early stop */
 } gs_stats_t;
 
 /* ---------------------------------------------------------------- context */

@@ -22,7 +22,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_COUNT
 };
 
 struct Buf {
@@ -185,6 +185,10 @@ gs_status_t check_options(gs_ctx *ctx, const gs_options_t *o)
         return fail(ctx, GS_ERR_INVALID_ARG, "options out of range");
     if ((o->tracking_loss != 0 && o->tracking_loss != 1) || !(o->lambda_c >= 0 && o->lambda_c <= 1))
         return fail(ctx, GS_ERR_INVALID_ARG, "tracking_loss must be 0 or 1 and lambda_c in [0, 1]");
+    if ((o->exposure != 0 && o->exposure != 1) || !(o->lr_exposure >= 0) || !std::isfinite(o->lr_exposure) ||
+        (o->exposure && o->tracking_loss))
+        return fail(ctx, GS_ERR_INVALID_ARG,
+                    "exposure must be 0 or 1 with a finite lr_exposure >= 0, and applies to the registration loss only");
     return GS_OK;
 }
 
@@ -532,7 +536,33 @@ void add_problem(Plan &P, const gs_gaussians_t *src, const gs_gaussians_t *tgt, 
         P.vps[v].lr_trans = o->lr_trans;
         P.vps[v].loss_kind = o->tracking_loss ? 1 : 0;
         P.vps[v].lambda_c = o->lambda_c;
+        P.vps[v].exposure = o->exposure ? 1 : 0;
+        P.vps[v].lr_exposure = o->lr_exposure;
     }
+}
+
+bool any_exposure(const Plan &P)
+{
+    for (const VpDesc &d : P.vps)
+        if (d.exposure)
+            return true;
+    return false;
+}
+
+// exposure state [vp][7] (FP64), gains / offsets [vp][2] and the forward's
+// per-tile partial gradients [tiles][2]
+gs_status_t alloc_exposure(gs_ctx *ctx, const Plan &P, gsl::PoseArgs &pa, gsl::RasterArgs &r)
+{
+    const size_t nv = std::max<size_t>(P.vps.size(), 1), ntl = (size_t)std::max<uint64_t>(P.n_tiles, 1);
+    float *e32 = nullptr, *te = nullptr;
+    GS_TRY(wsT(ctx, S_EXPO, 7 * nv, &pa.expo));
+    GS_TRY(wsT(ctx, S_EXPO32, 2 * nv, &e32));
+    GS_TRY(wsT(ctx, S_TEXPO, 2 * ntl, &te));
+    pa.expo32 = e32;
+    pa.tile_expo = te;
+    r.expo32 = e32;
+    r.tile_expo = te;
+    return GS_OK;
 }
 
 // per-pixel and per-keyframe scratch of the tracking loss, if the plan has
@@ -622,6 +652,8 @@ void gs_default_options(gs_options_t *o)
     o->adam_eps = 1e-8f;
     o->tracking_loss = 0;
     o->lambda_c = 0.6f;
+    o->exposure = 0;
+    o->lr_exposure = 0.1f;
     o->lr_final = 0.001f;
 }
 
@@ -1171,6 +1203,8 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         }
     }
 
+    gsl::RasterArgs expo_r{};
+    GS_TRY(alloc_exposure(ctx, P, pa, expo_r));
     double headroom = 1.5;
     for (int attempt = 0; attempt < 3; ++attempt) {
         const long long l0 = gsl::g_launches;
@@ -1195,6 +1229,10 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         r.tile_twist = ttw;
         r.c_cam = ccam;
         r.tile_pairs = pairs;
+        r.expo32 = expo_r.expo32;
+        r.tile_expo = expo_r.tile_expo;
+        r.exposure = any_exposure(P);
+        r.count_contrib = opt->profile >= 2;
         gsl::TrackArgs ta;
         GS_TRY(alloc_track(ctx, P, D, r, ta, tloss, s));
         cudaError_t mark_err = cudaSuccess;
@@ -1486,8 +1524,9 @@ extern "C" gs_status_t gs_render_noalloc(const gs_gaussians_t *g, const float *p
 // ===========================================================================
 namespace {
 
-// per keyframe problem: pose64 [12], Adam state [13], pivot [3], camera-frame pivot [3]
-constexpr int kVpState = 31;
+// per keyframe problem: pose64 [12], Adam state [13], pivot [3], camera-frame
+// pivot [3], exposure state [7]
+constexpr int kVpState = 38;
 // tile duplicates per record assumed by admission (the room workload has ~1.2)
 constexpr double kAdmitDupsPerRecord = 3.0;
 
@@ -1663,6 +1702,8 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     pa.lr_final = srv->opt.lr_final;
     pa.iters = 0;  // every keyframe carries its request's count
     pa.update = 1;
+    gsl::RasterArgs expo_r{};
+    GS_TRY(alloc_exposure(ctx, P, pa, expo_r));
 
     // fresh requests start at the identity; the others resume their state
     gsl::centroids(D.vps, D.set_vp, n_sets, srv->cent, s);
@@ -1678,10 +1719,12 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
             GS_CUDA(cudaMemcpyAsync(srv->adam + 13 * v, st + 12, 13 * sizeof(double), cudaMemcpyHostToDevice, s));
             GS_CUDA(cudaMemcpyAsync(srv->pivot + 3 * v, st + 25, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
             GS_CUDA(cudaMemcpyAsync(srv->ccam + 3 * v, st + 28, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+            GS_CUDA(cudaMemcpyAsync(pa.expo + 7 * v, st + 31, 7 * sizeof(double), cudaMemcpyHostToDevice, s));
         }
     }
     k_to_float<<<(12 * nv + 255) / 256, 256, 0, s>>>(srv->pose64, srv->pose32, 12 * nv);
     ++gsl::g_launches;
+    gsl::exposure_floats(pa.expo, pa.expo32, nv, s);
     // size the duplicate lists at the current poses
     int cur = 0;
     uint32_t nd = 0;
@@ -1698,6 +1741,9 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     r.tile_twist = srv->ttw;
     r.c_cam = srv->ccam;
     r.tile_pairs = nullptr;
+    r.expo32 = expo_r.expo32;
+    r.tile_expo = expo_r.tile_expo;
+    r.exposure = any_exposure(P);
     gsl::TrackArgs ta;
     GS_TRY(alloc_track(ctx, P, D, r, ta, srv->tloss, s));
     GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
@@ -1743,7 +1789,7 @@ gs_status_t srv_round(gs_server *srv, cudaStream_t s, int64_t *done_ids, int max
             GS_CUDA(cudaGraphLaunch(srv->exec, s));
         const int nv = srv->n_vps;
         std::vector<double> pose(12 * (size_t)nv), adam(13 * (size_t)nv), piv(3 * (size_t)nv), cc(3 * (size_t)nv),
-            loss(nv);
+            loss(nv), expo(7 * (size_t)nv);
         int flags = 0;
         GS_CUDA(cudaMemcpyAsync(&flags, srv->p.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(pose.data(), srv->pose64, pose.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1751,6 +1797,7 @@ gs_status_t srv_round(gs_server *srv, cudaStream_t s, int64_t *done_ids, int max
         GS_CUDA(cudaMemcpyAsync(piv.data(), srv->pivot, piv.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(cc.data(), srv->ccam, cc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaMemcpyAsync(loss.data(), srv->lossd, loss.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaMemcpyAsync(expo.data(), srv->pa.expo, expo.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaStreamSynchronize(s));
         if (flags & gsk::kFlagNonFinite)
             return fail(ctx, GS_ERR_NONFINITE, "non-finite Gaussian parameter in an in-flight request");
@@ -1774,6 +1821,7 @@ gs_status_t srv_round(gs_server *srv, cudaStream_t s, int64_t *done_ids, int max
                 std::memcpy(st + 12, &adam[13 * v], 13 * sizeof(double));
                 std::memcpy(st + 25, &piv[3 * v], 3 * sizeof(double));
                 std::memcpy(st + 28, &cc[3 * v], 3 * sizeof(double));
+                std::memcpy(st + 31, &expo[7 * v], 7 * sizeof(double));
             }
             r.fresh = false;
             r.ran += S;

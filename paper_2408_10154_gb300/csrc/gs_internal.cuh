@@ -44,6 +44,8 @@ struct VpDesc {
     float lr_rot, lr_trans;  // Adam learning rates of this keyframe's problem
     int loss_kind;         // 0: registration L1 means; 1: tracking loss (Eq. 2, masks of Supp. A)
     float lambda_c;        // tracking loss colour weight
+    int exposure;          // 1: the registration loss compares e^a I^ + b (Supp. B) and fits (a, b)
+    float lr_exposure;
 };
 
 // A projection group: vps that share one Gaussian set and are projected by
@@ -240,7 +242,10 @@ struct RasterArgs {
     const float *d_rgb, *d_depth, *d_alpha;
     // registration / backward outputs
     float *tile_loss;         // [tiles]
-    unsigned long long *tile_pairs;  // [2][tiles] += sum of `last`, contributing pairs (statistics, may be null)
+    unsigned long long *tile_pairs;  // [2][tiles] += sum of `last`, pairs passing the alpha test
+                                     // (count_contrib only); statistics, may be null
+    int exposure;                    // some keyframe compensates exposure (forward variant)
+    int count_contrib;               // count the pairs that pass the alpha test (forward variant)
     double *tile_twist;       // [tiles][6], camera frame
     const double *c_cam;      // [vp][3] pivot in camera frame
     float *dup_grads;         // [dups][10] screen-space partials (full mode)
@@ -249,6 +254,10 @@ struct RasterArgs {
     // the backward scales the loss signs by the per-pixel mask weight
     float *trk_err, *trk_col;
     const float *trk_w;
+    // exposure compensation: [vp][2] gain e^a and offset b; [tiles][2]
+    // partial dL/da, dL/db written by the forward
+    const float *expo32;
+    float *tile_expo;
 };
 void forward(const RasterArgs &a, bool registration, cudaStream_t s);
 void raster_init();  // one-time kernel attributes (before any graph capture)
@@ -292,11 +301,16 @@ struct PoseArgs {
     const double *centroid;    // [set][3]
     double *loss;              // [vp] last loss
     double *grad;              // [vp][6] last world gradient (may be null)
+    double *expo;              // [vp][7] exposure a, b and Adam state (m_a, m_b, v_a, v_b, steps)
+    float *expo32;             // [vp][2] gain e^a, offset b for the forward
+    const float *tile_expo;    // [tiles][2]
     float lr_rot, lr_trans, beta1, beta2, eps, lr_final;
     int iters;
     int update;                // 0: only reduce loss / gradient
 };
 void pose_update(const PoseArgs &a, cudaStream_t s);
+// gain e^a and offset b (floats) from the FP64 exposure state [vp][7]
+void exposure_floats(const double *expo, float *expo32, int n_vps, cudaStream_t s);
 // per-keyframe sum of the tile losses (FP64, fixed order)
 void loss_reduce(const gsk::VpDesc *vps, int n_vps, const float *tile_loss, double *loss_out, cudaStream_t s);
 void pose_init(const PoseArgs &a, cudaStream_t s);

@@ -116,25 +116,55 @@ __global__ void k_pose_init(const gsl::PoseArgs a)
     for (int k = 0; k < 13; ++k)
         a.adam[13 * vp + k] = 0.0;
     pivots_of(d, P, a.centroid + 3 * d.set, a.pivot + 3 * vp, a.c_cam + 3 * vp);
+    if (a.expo) {
+        for (int k = 0; k < 7; ++k)
+            a.expo[7 * vp + k] = 0.0;
+        a.expo32[2 * vp] = 1.0f;
+        a.expo32[2 * vp + 1] = 0.0f;
+    }
+}
+
+// Adam step on the exposure (a, b) with the pose's moments and schedule
+// (iteration k of iters); e = a, b, m_a, m_b, v_a, v_b, steps taken
+__device__ void exposure_step(double *e, const double *g, int k, int iters, float lr, float b1f, float b2f, float epsf,
+                              float lr_final)
+{
+    const double kPi = 3.14159265358979323846;
+    const double b1 = b1f, b2 = b2f, eps = epsf, f = lr_final;
+    const double t = e[6] + 1.0;
+    e[6] = t;
+    const double sched = f + (1.0 - f) * 0.5 * (1.0 + cos(kPi * (double)k / (double)iters));
+    for (int i = 0; i < 2; ++i) {
+        e[2 + i] = b1 * e[2 + i] + (1.0 - b1) * g[i];
+        e[4 + i] = b2 * e[4 + i] + (1.0 - b2) * g[i] * g[i];
+        const double mh = e[2 + i] / (1.0 - pow(b1, t));
+        const double vh = e[4 + i] / (1.0 - pow(b2, t));
+        e[i] -= (double)lr * sched * mh / (sqrt(vh) + eps);
+    }
 }
 
 // one block per keyframe: reduce the tile twists and losses in a fixed
 // order, rotate the twist to the world frame, then (update) take the step
 __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
 {
-    __shared__ double s[8][7];
+    __shared__ double s[8][9];
     const int vp = blockIdx.x;
     const VpDesc &d = a.vps[vp];
     const uint32_t nt = (uint32_t)d.TX * d.TY;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const bool expo = d.exposure && a.tile_expo && a.expo;
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (uint32_t k = threadIdx.x; k < nt; k += blockDim.x) {
         const size_t t = d.tile_base + k;
         if (a.tile_twist)
             for (int i = 0; i < 6; ++i)
                 acc[i] += a.tile_twist[t * 6 + i];
         acc[6] += (double)a.tile_loss[t];
+        if (expo) {
+            acc[7] += (double)a.tile_expo[2 * t];
+            acc[8] += (double)a.tile_expo[2 * t + 1];
+        }
     }
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < 9; ++i) {
         const double v = warp_sum(acc[i]);
         if ((threadIdx.x & 31) == 0)
             s[threadIdx.x >> 5][i] = v;
@@ -142,8 +172,8 @@ __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
     __syncthreads();
     if (threadIdx.x != 0)
         return;
-    double tot[7];
-    for (int i = 0; i < 7; ++i) {
+    double tot[9];
+    for (int i = 0; i < 9; ++i) {
         tot[i] = 0;
         for (int w = 0; w < 8; ++w)
             tot[i] += s[w][i];
@@ -169,9 +199,24 @@ __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
     double *P = a.pose64 + 12 * vp;
     adam_exp_update(P, a.adam + 13 * vp, g, a.pivot + 3 * vp, k, iters, d.lr_rot, d.lr_trans, a.beta1, a.beta2,
                     a.eps, a.lr_final);
+    if (expo) {
+        double *e = a.expo + 7 * vp;
+        exposure_step(e, tot + 7, k, iters, d.lr_exposure, a.beta1, a.beta2, a.eps, a.lr_final);
+        a.expo32[2 * vp] = (float)exp(e[0]);
+        a.expo32[2 * vp + 1] = (float)e[1];
+    }
     for (int k = 0; k < 12; ++k)
         a.pose32[12 * vp + k] = (float)P[k];
     pivots_of(d, P, a.centroid + 3 * d.set, a.pivot + 3 * vp, a.c_cam + 3 * vp);
+}
+
+__global__ void k_expo32(const double *expo, float *expo32, int n)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) {
+        expo32[2 * v] = (float)exp(expo[7 * v]);
+        expo32[2 * v + 1] = (float)expo[7 * v + 1];
+    }
 }
 
 __global__ void k_pose_step(int n, double *pose, double *state, const double *grad, const double *pivot, int k,
@@ -427,6 +472,14 @@ void loss(const VpDesc *vps, int n_vps, uint32_t n_tiles, const uint32_t *tile_v
     a.loss = loss_out;
     k_pose_update<<<n_vps, 256, 0, s>>>(a);
     g_launches += 2;
+}
+
+void exposure_floats(const double *expo, float *expo32, int n_vps, cudaStream_t s)
+{
+    if (n_vps <= 0)
+        return;
+    k_expo32<<<(n_vps + 127) / 128, 128, 0, s>>>(expo, expo32, n_vps);
+    ++g_launches;
 }
 
 void loss_reduce(const VpDesc *vps, int n_vps, const float *tile_loss, double *loss_out, cudaStream_t s)

@@ -430,7 +430,12 @@ def test_registration_profile_and_stats(gs, ctx):
     st = gs.gsreg.gs_stats_t()
     ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st)))
     assert st.iterations == 7 and st.pairs > 0 and st.n_dups > 0 and st.kernel_launches > 7 * 5
-    assert 0 < st.contributing <= st.pairs
+    assert st.contributing == 0
+    counted = gs.gs_register(ctx, g, g, [], views, 7, gs.default_options(profile=2))
+    np.testing.assert_array_equal(counted[3], plain[3])  # the counting variant changes no result
+    st2 = gs.gsreg.gs_stats_t()
+    ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st2)))
+    assert 0 < st2.contributing <= st2.pairs and st2.pairs == st.pairs
     assert st.n_pixels == sum(int(c[4]) * int(c[5]) for c in cams)
     assert all(v > 0 for v in st.phase_ms)
 

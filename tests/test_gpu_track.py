@@ -163,3 +163,33 @@ def test_served_tracking_equals_gs_register(gs, ctx):
     Tb, _, eb = gs.gs_register_batch(ctx, [(g, g, [], view, topt), (g, g, [], view)], 12)
     np.testing.assert_array_equal(Tb[0], ref_t[0])
     np.testing.assert_array_equal(Tb[1], gs.gs_register(ctx, g, g, [], view, 12)[0])
+
+
+def test_exposure_registration_matches_oracle(gs, ctx):
+    # a keyframe whose colours carry another exposure (gain e^0.15, offset
+    # -0.03): pose and exposure registered together (Supp. B) on the GPU and
+    # in the oracle follow the same trajectory
+    c = synth.plain_2k()
+    og = O.Gaussians.from_dict(c["gaussians"])
+    g = gs.Gaussians.from_numpy(c["gaussians"])
+    cam = c["cams"][0]
+    tr = O.render(og, c["T_gt"], cam)
+    t_rgb = (math.exp(0.15) * tr["rgb"] - 0.03).astype(np.float32)
+    t_dep = tr["depth"].astype(np.float32)
+    opt = gs.default_options(exposure=1)
+    iters = 20
+    Tg, conf, eps, _ = gs.gs_register(ctx, g, g, [], [(cam, dev(t_rgb), dev(t_dep))], iters, opt)
+    hyper = [float(np.float32(v)) for v in (opt.lr_rot, opt.lr_trans, opt.beta1, opt.beta2, opt.adam_eps,
+                                            opt.lr_final)]
+    Po, eps_o, _, ab = O.register_view(og, cam, t_rgb, t_dep, iters, hyper=hyper,
+                                       lr_exposure=float(np.float32(opt.lr_exposure)))
+    ang, dt = _rot_err(Tg, Po)
+    assert ang < 0.01 and dt < 5e-4, (ang, dt)
+    assert abs(eps[0] - eps_o) <= 2e-3 * eps_o + 1e-6, (eps[0], eps_o)
+    # without compensation the residual stays higher
+    _, _, eps_plain, _ = gs.gs_register(ctx, g, g, [], [(cam, dev(t_rgb), dev(t_dep))], iters)
+    assert eps_plain[0] > 1.2 * eps[0]
+    # exposure with the tracking loss is refused
+    with pytest.raises(gs.GsError):
+        gs.gs_register(ctx, g, g, [], [(cam, dev(t_rgb), dev(t_dep))], 2,
+                       gs.default_options(exposure=1, tracking_loss=1))
