@@ -82,6 +82,10 @@ def _load():
         lib.or_pose_step.argtypes = [P, P, P, P, P, I, I]
         lib.or_register_view.argtypes = [I, P, P, P, P, P, P, P, P, P, P, I, P, P, P, P, P, P]
         lib.or_exposure_loss.argtypes = [I, I, P, P, P, P, P, P, P, P]
+        lib.or_overlap_ratio.argtypes = [I, P, I, P, P, ctypes.c_float, P, P, P]
+        lib.or_overlap_ratio.restype = ctypes.c_double
+        lib.or_nearest_subset.argtypes = [I, P, I, P, P, I, P, P]
+        lib.or_nearest_subset.restype = I
         lib.or_exposure_loss.restype = ctypes.c_double
         lib.or_track_loss.argtypes = [I, I, P, P, P, P, P, P, ctypes.c_double, P, P, P, P]
         lib.or_track_loss.restype = ctypes.c_double
@@ -345,3 +349,32 @@ def fuse(estimates, eps, reverse):
     R = U @ D @ Vt
     t = (w[:, None] * Ts[:, :, 3]).sum(0) / w.sum()
     return np.concatenate([R, t[:, None]], axis=1), float(w.mean())
+
+
+# overlap threshold tau_1 of the loop filter (Supp.: 0.2 m on TUM-RGBD,
+# ScanNet, ScanNet++; 0.1 m on Replica)
+OVERLAP_TAU = 0.2
+
+
+def overlap_ratio(p: Gaussians, q: Gaussians, T, tau=OVERLAP_TAU):
+    """Overlap ratio of P and Q under T_{P->Q} (reciprocal closest points,
+    FP32 distances).  Returns (OR, |K|, nn_pq [np], nn_qp [nq])."""
+    lib = _load()
+    nn_pq = np.zeros(max(p.n, 1), np.int32)
+    nn_qp = np.zeros(max(q.n, 1), np.int32)
+    k = ctypes.c_long(0)
+    r = lib.or_overlap_ratio(p.n, _p(p.means4), q.n, _p(q.means4), _p(_f64(T, (12,))), float(tau), _p(nn_pq),
+                             _p(nn_qp), ctypes.byref(k))
+    if r < 0:
+        raise RuntimeError("oracle overlap_ratio: out of memory")
+    return float(r), int(k.value), nn_pq[:p.n], nn_qp[:q.n]
+
+
+def nearest_subset(p: Gaussians, q: Gaussians, T, idx):
+    """Nearest neighbours in Q of the moved means of P[idx]."""
+    lib = _load()
+    idx = np.ascontiguousarray(idx, np.int32)
+    nn = np.zeros(max(len(idx), 1), np.int32)
+    _check(lib.or_nearest_subset(p.n, _p(p.means4), q.n, _p(q.means4), _p(_f64(T, (12,))), len(idx), _p(idx), _p(nn)),
+           "nearest_subset")
+    return nn[:len(idx)]

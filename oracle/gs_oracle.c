@@ -1309,3 +1309,114 @@ int or_transform(int n, const float *means4, const float *quats4, const double *
     }
     return OR_OK;
 }
+
+/* ======================================================================== */
+/* overlap ratio (loop filter, Supp.: reciprocal closest-point matching)     */
+/* ======================================================================== */
+
+/* p' = R p + t in FP32, fused multiply-adds translation first (the
+ * projection's convention); T is [R|t] rounded to FP32 */
+static void rigid32(const float T[12], const float *p, float *out)
+{
+    for (int i = 0; i < 3; ++i)
+        out[i] = fmaf(T[4 * i + 2], p[2], fmaf(T[4 * i + 1], p[1], fmaf(T[4 * i], p[0], T[4 * i + 3])));
+}
+
+/* squared distance in FP32: dx = b - a per axis, fma(dz, dz, fma(dy, dy, dx*dx)) */
+static float dist2_32(const float *a, const float *b)
+{
+    const float dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+/* nearest neighbour of each of the na points a (xyz, stride 4) among the nb
+ * points b: the smallest FP32 squared distance, ties to the smaller index;
+ * -1 if nb = 0 */
+static void nearest(const float *a, int na, const float *b, int nb, int32_t *nn, float *d2)
+{
+    for (int i = 0; i < na; ++i) {
+        float best = INFINITY;
+        int32_t bi = -1;
+        for (int j = 0; j < nb; ++j) {
+            const float d = dist2_32(a + 4 * (size_t)i, b + 4 * (size_t)j);
+            if (d < best) {
+                best = d;
+                bi = j;
+            }
+        }
+        nn[i] = bi;
+        if (d2)
+            d2[i] = best;
+    }
+}
+
+/* Overlap ratio of submaps P and Q under T = T_{P->Q} (the loop filter of
+ * the supplement): the means of P are moved by T (FP32, rigid32), K is the
+ * set of reciprocal nearest-neighbour pairs (p, q) -- q the nearest of T p
+ * in Q and T p the nearest of q in T P -- and OR is the fraction of K with
+ * |T p - q| < tau, decided as d2 < tau * tau in FP32.  Writes nn_pq[np],
+ * nn_qp[nq] (may be NULL) and *n_corr = |K|; returns OR (0 when K is
+ * empty), or -1 when out of memory. */
+double or_overlap_ratio(int np, const float *p_means4, int nq, const float *q_means4, const double *T, float tau,
+                        int32_t *nn_pq_out, int32_t *nn_qp_out, long *n_corr)
+{
+    float T32[12];
+    for (int k = 0; k < 12; ++k)
+        T32[k] = (float)T[k];
+    float *pt = malloc((size_t)(np > 0 ? np : 1) * 4 * sizeof(float));
+    int32_t *pq = malloc((size_t)(np > 0 ? np : 1) * sizeof(int32_t));
+    int32_t *qp = malloc((size_t)(nq > 0 ? nq : 1) * sizeof(int32_t));
+    float *d2 = malloc((size_t)(np > 0 ? np : 1) * sizeof(float));
+    if (!pt || !pq || !qp || !d2) {
+        free(pt);
+        free(pq);
+        free(qp);
+        free(d2);
+        return -1.0;
+    }
+    for (int i = 0; i < np; ++i) {
+        rigid32(T32, p_means4 + 4 * (size_t)i, pt + 4 * (size_t)i);
+        pt[4 * (size_t)i + 3] = 0.0f;
+    }
+    nearest(pt, np, q_means4, nq, pq, d2);
+    nearest(q_means4, nq, pt, np, qp, NULL);
+    const float tau2 = tau * tau;
+    long k = 0, in = 0;
+    for (int i = 0; i < np; ++i) {
+        const int32_t j = pq[i];
+        if (j >= 0 && qp[j] == i) {
+            ++k;
+            if (d2[i] < tau2)
+                ++in;
+        }
+    }
+    if (nn_pq_out)
+        memcpy(nn_pq_out, pq, (size_t)np * sizeof(int32_t));
+    if (nn_qp_out)
+        memcpy(nn_qp_out, qp, (size_t)nq * sizeof(int32_t));
+    if (n_corr)
+        *n_corr = k;
+    free(pt);
+    free(pq);
+    free(qp);
+    free(d2);
+    return k > 0 ? (double)in / (double)k : 0.0;
+}
+
+/* nearest neighbours in Q of a subset of P's moved means (for parity checks
+ * at full size): idx[m] indices into P; writes nn[m] */
+int or_nearest_subset(int np, const float *p_means4, int nq, const float *q_means4, const double *T, int m,
+                      const int32_t *idx, int32_t *nn)
+{
+    float T32[12], pt[4];
+    for (int k = 0; k < 12; ++k)
+        T32[k] = (float)T[k];
+    for (int s = 0; s < m; ++s) {
+        if (idx[s] < 0 || idx[s] >= np)
+            return OR_ERR_ARG;
+        rigid32(T32, p_means4 + 4 * (size_t)idx[s], pt);
+        pt[3] = 0.0f;
+        nearest(pt, 1, q_means4, nq, nn + s, NULL);
+    }
+    return OR_OK;
+}

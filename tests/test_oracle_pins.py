@@ -634,3 +634,53 @@ def test_exposure_compensation_recovers_gain_offset_and_pose():
     assert abs(ab[0] - 0.15) < 0.01 and abs(ab[1] + 0.03) < 0.005, ab
     P2, eps2, _ = O.register_view(g, cam, t_rgb, tr["depth"], 50)
     assert eps2 > 5 * eps
+
+
+# ----------------------------------------------------------------- overlap ratio (loop filter, Supp.)
+def _pts(x):
+    x = np.asarray(x, np.float32)
+    return O.Gaussians(np.concatenate([x, np.zeros((len(x), 1), np.float32)], 1), np.zeros((len(x), 4)),
+                       np.tile([1.0, 0, 0, 0], (len(x), 1)), np.zeros(len(x)), np.zeros((len(x), 4)))
+
+
+def test_overlap_identical_and_disjoint_sets():
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, (500, 3))
+    r, k, nn, _ = O.overlap_ratio(_pts(x), _pts(x), np.eye(3, 4))
+    assert (r, k) == (1.0, 500) and (nn == np.arange(500)).all()
+    # far-away outliers added to Q match nothing of P reciprocally
+    y = np.concatenate([x, rng.uniform(99, 101, (50, 3))])
+    r, k, _, _ = O.overlap_ratio(_pts(x), _pts(y), np.eye(3, 4))
+    assert (r, k) == (1.0, 500)
+    # Q 10 m away: reciprocal pairs exist (the closest pair always is one) but none is within tau
+    r, k, _, _ = O.overlap_ratio(_pts(x), _pts(x + [10.0, 0, 0]), np.eye(3, 4))
+    assert r == 0.0 and k >= 1
+
+
+def test_overlap_nearest_neighbours_match_a_kd_tree():
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(4)
+    a, b = rng.uniform(-2, 2, (1500, 3)), rng.uniform(-2, 2, (1200, 3))
+    T = synth.random_rigid(rng, 20.0, 0.3)
+    _, _, nn_pq, nn_qp = O.overlap_ratio(_pts(a), _pts(b), T)
+    at = (np.asarray(T, np.float32)[:, :3].astype(np.float64) @ np.float32(a).T).T + np.float32(T)[:, 3]
+    np.testing.assert_array_equal(nn_pq, cKDTree(np.float32(b)).query(at)[1])
+    np.testing.assert_array_equal(nn_qp, cKDTree(at).query(np.float32(b))[1])
+    np.testing.assert_array_equal(O.nearest_subset(_pts(a), _pts(b), T, [0, 7, 1499]), nn_pq[[0, 7, 1499]])
+
+
+def test_overlap_of_a_rigidly_moved_submap_is_one():
+    # Q = T P (Eq. 8 on the means): under T_{P->Q} = T every mean meets its image
+    c = synth.plain_2k()
+    g = O.Gaussians.from_dict(c["gaussians"])
+    q = O.transform(g, c["T_gt"])
+    r, k, nn, _ = O.overlap_ratio(g, q, c["T_gt"], tau=0.01)
+    assert r == 1.0 and k == g.n and (nn == np.arange(g.n)).all()
+    # under the identity the 5 cm / 5 deg offset pushes many pairs past 1 cm
+    r0, _, _, _ = O.overlap_ratio(g, q, np.eye(3, 4), tau=0.01)
+    assert r0 < 0.5
+
+
+def test_overlap_threshold_follows_the_paper():
+    hp = json.load(open(os.path.join(GOLDEN, "loop_closure_hyperparams.json")))
+    assert O.OVERLAP_TAU == hp["overlap_tau"]["ScanNet"]
