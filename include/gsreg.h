@@ -366,6 +366,24 @@ typedef struct {
 gs_status_t gs_register_batch(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt, int iters,
                               double *T_out, double *conf_out, double *eps_out, gs_stream_t stream);
 
+/* ----------------------------------------------------------- loop filter */
+
+/* Overlap ratio of submaps P and Q under T = T_{P->Q} (the loop filter of
+ * the supplement, after Predator): P's means are moved by T (FP32, fused
+ * multiply-adds translation first), each moved mean and each mean of Q find
+ * their exact nearest neighbour on the other side (FP32 squared distance
+ * fma(dz, dz, fma(dy, dy, dx * dx)), dx = b - a; ties to the smaller index),
+ * the reciprocal pairs form K, and
+ *   OR = |{(p, q) in K : |T p - q|^2 < tau^2 (FP32)}| / |K|  (0 if K is empty).
+ *   T_host [12] host (row-major [R|t]); tau in metres (0.2 on TUM-RGBD /
+ *   ScanNet / ScanNet++, 0.1 on Replica);
+ *   ratio, n_corr (= |K|) host out; nn_pq [P.n], nn_qp [Q.n] device out or
+ *   NULL (nearest neighbour indices, -1 when the other side is empty).
+ * Synchronises `stream`. */
+gs_status_t gs_overlap_ratio(gs_ctx_t *ctx, const gs_gaussians_t *p, const gs_gaussians_t *q, const double *T_host,
+                             float tau, double *ratio, int64_t *n_corr, int32_t *nn_pq, int32_t *nn_qp,
+                             gs_stream_t stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Continuous-batching registration server.  A request is one registration

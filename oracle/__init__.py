@@ -86,6 +86,8 @@ def _load():
         lib.or_overlap_ratio.restype = ctypes.c_double
         lib.or_nearest_subset.argtypes = [I, P, I, P, P, I, P, P]
         lib.or_nearest_subset.restype = I
+        lib.or_moved_means.argtypes = [I, P, P, P]
+        lib.or_moved_means.restype = I
         lib.or_exposure_loss.restype = ctypes.c_double
         lib.or_track_loss.argtypes = [I, I, P, P, P, P, P, P, ctypes.c_double, P, P, P, P]
         lib.or_track_loss.restype = ctypes.c_double
@@ -378,3 +380,11 @@ def nearest_subset(p: Gaussians, q: Gaussians, T, idx):
     _check(lib.or_nearest_subset(p.n, _p(p.means4), q.n, _p(q.means4), _p(_f64(T, (12,))), len(idx), _p(idx), _p(nn)),
            "nearest_subset")
     return nn[:len(idx)]
+
+
+def moved_means(g: Gaussians, T):
+    """The overlap ratio's FP32 moved means T mu, [n, 4] (w = 0)."""
+    lib = _load()
+    out = np.zeros((max(g.n, 1), 4), np.float32)
+    _check(lib.or_moved_means(g.n, _p(g.means4), _p(_f64(T, (12,))), _p(out)), "moved_means")
+    return out[:g.n]

@@ -1420,3 +1420,16 @@ int or_nearest_subset(int np, const float *p_means4, int nq, const float *q_mean
     }
     return OR_OK;
 }
+
+/* the FP32 moved means of the overlap ratio (rigid32), [n][4] with w = 0 */
+int or_moved_means(int n, const float *means4, const double *T, float *out4)
+{
+    float T32[12];
+    for (int k = 0; k < 12; ++k)
+        T32[k] = (float)T[k];
+    for (int i = 0; i < n; ++i) {
+        rigid32(T32, means4 + 4 * (size_t)i, out4 + 4 * (size_t)i);
+        out4[4 * (size_t)i + 3] = 0.0f;
+    }
+    return OR_OK;
+}

@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgsreg.so")
-SOURCES = ["api.cu", "project.cu", "binning.cu", "raster.cu", "pose.cu", "params.cu", "track.cu"]
+SOURCES = ["api.cu", "project.cu", "binning.cu", "raster.cu", "pose.cu", "params.cu", "track.cu", "overlap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -22,7 +22,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_COUNT
 };
 
 struct Buf {
@@ -1006,6 +1006,55 @@ gs_status_t gs_track_loss(gs_ctx_t *ctx, const gs_camera_t *cams, int n_cams, co
     if (median)
         GS_CUDA(cudaMemcpyAsync(median, ta.med, sizeof(float) * (size_t)n_cams, cudaMemcpyDeviceToDevice, s));
     GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_overlap_ratio(gs_ctx_t *ctx, const gs_gaussians_t *p, const gs_gaussians_t *q, const double *T_host,
+                             float tau, double *ratio, int64_t *n_corr, int32_t *nn_pq, int32_t *nn_qp,
+                             gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_gaussians(ctx, p, "P"));
+    GS_TRY(check_gaussians(ctx, q, "Q"));
+    if (!T_host || !ratio || !(tau >= 0.0f) || !std::isfinite(tau))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_overlap_ratio: bad arguments");
+    for (int k = 0; k < 12; ++k)
+        if (!std::isfinite(T_host[k]))
+            return fail(ctx, GS_ERR_INVALID_ARG, "gs_overlap_ratio: non-finite transform");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t np = (size_t)p->n, nq = (size_t)q->n;
+    gsl::OverlapArgs a{};
+    a.p = (const float4 *)p->means;
+    a.q = (const float4 *)q->means;
+    a.np = (int)np;
+    a.nq = (int)nq;
+    std::vector<float> T32(12);
+    for (int k = 0; k < 12; ++k)
+        T32[k] = (float)T_host[k];
+    float *Td = nullptr;
+    GS_TRY(upload(ctx, S_OT, T32, &Td, s));
+    a.T32 = Td;
+    GS_TRY(wsT(ctx, S_OPT, std::max<size_t>(np, 1), &a.pt));
+    if (nn_pq)
+        a.nn_pq = nn_pq;
+    else
+        GS_TRY(wsT(ctx, S_ONN1, std::max<size_t>(np, 1), &a.nn_pq));
+    if (nn_qp)
+        a.nn_qp = nn_qp;
+    else
+        GS_TRY(wsT(ctx, S_ONN2, std::max<size_t>(nq, 1), &a.nn_qp));
+    GS_TRY(wsT(ctx, S_OD2, std::max<size_t>(np, 1), &a.d2));
+    GS_TRY(wsT(ctx, S_OCNT, 2, &a.counts));
+    a.tau2 = tau * tau;
+    gsl::overlap(a, s);
+    unsigned long long c[2] = {0, 0};
+    GS_CUDA(cudaMemcpyAsync(c, a.counts, sizeof c, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    *ratio = c[0] ? (double)c[1] / (double)c[0] : 0.0;
+    if (n_corr)
+        *n_corr = (int64_t)c[0];
     return GS_OK;
 }
 

@@ -288,6 +288,20 @@ void track_loss(const TrackArgs &a, cudaStream_t s);
 // err / col of rendered images (standalone gs_track_loss)
 void track_prep(const TrackArgs &a, const float *rgb, const float *depth, float *err, float *col, cudaStream_t s);
 
+// Overlap ratio of two submaps (loop filter): moved means of P, exact
+// nearest neighbours both ways, reciprocal pairs and those within tau.
+struct OverlapArgs {
+    const float4 *p, *q;      // means [np], [nq]
+    int np, nq;
+    const float *T32;         // [12] device, T_{P->Q} rounded to FP32
+    float4 *pt;               // [np] scratch: T p
+    int32_t *nn_pq, *nn_qp;   // [np], [nq] out
+    float *d2;                // [np] out: squared distance to the nearest of Q
+    float tau2;               // tau * tau (FP32)
+    unsigned long long *counts;  // [2] out: |K|, pairs of K within tau
+};
+void overlap(const OverlapArgs &a, cudaStream_t s);
+
 struct PoseArgs {
     const gsk::VpDesc *vps;
     int n_vps;

@@ -71,6 +71,7 @@ class gs_gaussian_grads_t(ctypes.Structure):
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
            "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc", "gs_track_loss",
+           "gs_overlap_ratio",
            "gs_server_create",
            "gs_server_destroy", "gs_server_last_error", "gs_server_submit", "gs_server_step", "gs_server_poll",
            "gs_server_counts"]
@@ -110,6 +111,7 @@ def load(build_if_missing: bool = False):
             "gs_render_backward": ([P, P, P, P, I, P, P, P, P, P, P, P, P, P, P], I),
             "gs_loss": ([P, P, I, P, P, P, P, P, P, P, P], I),
             "gs_track_loss": ([P, P, I, P, P, P, P, P, ctypes.c_float, P, P, P, P, P, P], I),
+            "gs_overlap_ratio": ([P, P, P, P, ctypes.c_float, P, P, P, P, P], I),
             "gs_pose_step": ([P, I, P, P, P, P, I, I, P, P], I),
             "gs_fuse": ([P, I, P, P, P, P, P, P], I),
             "gs_register": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P], I),
@@ -347,6 +349,22 @@ def gs_track_loss(ctx: Context, cams, rgb, depth, t_final, t_rgb, t_depth, lambd
                                      _ptr(t_depth), float(lambda_c), _ptr(loss), _ptr(d_rgb), _ptr(d_depth),
                                      _ptr(inl), _ptr(med), _stream()))
     return loss, d_rgb, d_depth, inl, med
+
+
+def gs_overlap_ratio(ctx: Context, p: Gaussians, q: Gaussians, T, tau=0.2, with_nn=False):
+    """Overlap ratio of P and Q under T_{P->Q} (loop filter).  Returns
+    (OR, |K|) or, with ``with_nn``, (OR, |K|, nn_pq, nn_qp) device int32."""
+    Th = np.ascontiguousarray(np.asarray(T, np.float64).reshape(12))
+    ratio, k = ctypes.c_double(), ctypes.c_int64()
+    nn_pq = torch.empty(max(p.n, 1), dtype=torch.int32, device=p.means4.device) if with_nn else None
+    nn_qp = torch.empty(max(q.n, 1), dtype=torch.int32, device=p.means4.device) if with_nn else None
+    pst, qst = p.c_struct(), q.c_struct()
+    ctx.check(ctx._lib.gs_overlap_ratio(ctx.handle, ctypes.byref(pst), ctypes.byref(qst),
+                                        Th.ctypes.data_as(ctypes.c_void_p), float(tau), ctypes.byref(ratio),
+                                        ctypes.byref(k), _ptr(nn_pq), _ptr(nn_qp), _stream()))
+    if with_nn:
+        return ratio.value, k.value, nn_pq[:p.n], nn_qp[:q.n]
+    return ratio.value, k.value
 
 
 def gs_pose_step(ctx: Context, pose, state, grad, pivot, k, iters, opt=None):
