@@ -446,6 +446,15 @@ gs_status_t gs_server_counts(const gs_server_t *srv, int64_t out[5]);
 gs_status_t gs_transform(gs_ctx_t *ctx, const gs_gaussians_t *g, const double *T_host, float *out_means,
                          float *out_quats, gs_stream_t stream);
 
+/* Map adjustment after pose-graph optimisation (Eq. 8/9 on every submap):
+ * gs_transform of n_maps submaps, each by its own T, in one launch.
+ *   T_host [n_maps][12] host; out_means, out_quats: host arrays of n_maps
+ *   device pointers ([n][4] each, may alias the inputs).  Results equal
+ *   gs_transform's bit for bit.  Keyframe poses of a corrected submap follow
+ *   on the host: world_to_cam <- world_to_cam o T^-1 (a 3x4 product each). */
+gs_status_t gs_transform_batch(gs_ctx_t *ctx, const gs_gaussians_t *maps, int n_maps, const double *T_host,
+                               float *const *out_means, float *const *out_quats, gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_COUNT
 };
 
 struct Buf {
@@ -1110,6 +1110,46 @@ gs_status_t gs_transform(gs_ctx_t *ctx, const gs_gaussians_t *g, const double *T
     DeviceGuard dg(ctx->device);
     gsl::transform((const float4 *)g->means, (const float4 *)g->quats, g->n, T_host, (float4 *)out_means,
                    (float4 *)out_quats, (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status_t gs_transform_batch(gs_ctx_t *ctx, const gs_gaussians_t *maps, int n_maps, const double *T_host,
+                               float *const *out_means, float *const *out_quats, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    if (n_maps < 0 || (n_maps > 0 && (!maps || !T_host || !out_means || !out_quats)))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_transform_batch: bad arguments");
+    std::vector<gsl::MapDesc> md;
+    unsigned blocks = 0;
+    for (int k = 0; k < n_maps; ++k) {
+        GS_TRY(check_gaussians(ctx, &maps[k], "submap"));
+        if (maps[k].n > 0 && (!out_means[k] || !out_quats[k] || !aligned16(out_means[k]) || !aligned16(out_quats[k])))
+            return fail(ctx, GS_ERR_INVALID_ARG, "gs_transform_batch: bad output arrays");
+        for (int j = 0; j < 12; ++j)
+            if (!std::isfinite(T_host[12 * k + j]))
+                return fail(ctx, GS_ERR_INVALID_ARG, "gs_transform_batch: non-finite transform");
+        if (maps[k].n == 0)
+            continue;
+        gsl::MapDesc m{};
+        m.means = (const float4 *)maps[k].means;
+        m.quats = (const float4 *)maps[k].quats;
+        m.out_means = (float4 *)out_means[k];
+        m.out_quats = (float4 *)out_quats[k];
+        m.n = maps[k].n;
+        m.blk_base = blocks;
+        std::memcpy(m.T, T_host + 12 * k, sizeof m.T);
+        md.push_back(m);
+        blocks += (unsigned)((m.n + 255) / 256);
+    }
+    if (md.empty())
+        return GS_OK;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gsl::MapDesc *dmd = nullptr;
+    GS_TRY(upload(ctx, S_MAPS, md, &dmd, s));
+    gsl::transform_batch(dmd, (int)md.size(), blocks, s);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

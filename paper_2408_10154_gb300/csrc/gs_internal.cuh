@@ -288,6 +288,17 @@ void track_loss(const TrackArgs &a, cudaStream_t s);
 // err / col of rendered images (standalone gs_track_loss)
 void track_prep(const TrackArgs &a, const float *rgb, const float *depth, float *err, float *col, cudaStream_t s);
 
+// One submap of a batched rigid update (map adjustment after pose-graph
+// optimisation, Eq. 8/9): blocks [blk_base, blk_base + ceil(n / 256)).
+struct MapDesc {
+    const float4 *means, *quats;
+    float4 *out_means, *out_quats;
+    int64_t n;
+    unsigned blk_base;
+    double T[12];
+};
+void transform_batch(const MapDesc *maps, int n_maps, unsigned blocks, cudaStream_t s);
+
 // Overlap ratio of two submaps (loop filter): moved means of P, exact
 // nearest neighbours both ways, reciprocal pairs and those within tau.
 struct OverlapArgs {

@@ -374,13 +374,9 @@ struct Rigid {
     double T[12];
 };
 
-__global__ void k_transform(const float4 *means, const float4 *quats, int64_t n, const Rigid rt, float4 *om,
-                            float4 *oq)
+// mu <- R mu + t and q <- q_R (x) q of one Gaussian (FP64 arithmetic)
+__device__ __forceinline__ void rigid_apply(const double *T, const float4 m, const float4 q, float4 &om, float4 &oq)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
-        return;
-    const double *T = rt.T;
     // quaternion of R (largest-pivot branch), w >= 0
     const double tr = T[0] + T[5] + T[10];
     double qw, qx, qy, qz;
@@ -397,7 +393,6 @@ __global__ void k_transform(const float4 *means, const float4 *quats, int64_t n,
         const double s = sqrt(1.0 + T[10] - T[0] - T[5]) * 2;
         qw = (T[4] - T[1]) / s; qx = (T[2] + T[8]) / s; qy = (T[6] + T[9]) / s; qz = 0.25 * s;
     }
-    const float4 m = means[i], q = quats[i];
     float4 r;
     r.x = (float)(T[0] * m.x + T[1] * m.y + T[2] * m.z + T[3]);
     r.y = (float)(T[4] * m.x + T[5] * m.y + T[6] * m.z + T[7]);
@@ -409,8 +404,38 @@ __global__ void k_transform(const float4 *means, const float4 *quats, int64_t n,
     p.y = (float)(qw * q.y + qx * q.x + qy * q.w - qz * q.z);
     p.z = (float)(qw * q.z - qx * q.w + qy * q.x + qz * q.y);
     p.w = (float)(qw * q.w + qx * q.z - qy * q.y + qz * q.x);
-    om[i] = r;
-    oq[i] = p;
+    om = r;
+    oq = p;
+}
+
+__global__ void k_transform(const float4 *means, const float4 *quats, int64_t n, const Rigid rt, float4 *om,
+                            float4 *oq)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    float4 a, b;
+    rigid_apply(rt.T, means[i], quats[i], a, b);
+    om[i] = a;
+    oq[i] = b;
+}
+
+// many submaps, each with its own T: blocks [blk_base, next blk_base) of map k
+__global__ void k_transform_batch(const gsl::MapDesc *maps, int n_maps)
+{
+    int lo = 0, hi = n_maps - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (maps[mid].blk_base <= blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const gsl::MapDesc &m = maps[lo];
+    const int64_t i = (int64_t)(blockIdx.x - m.blk_base) * blockDim.x + threadIdx.x;
+    if (i >= m.n)
+        return;
+    float4 a, b;
+    rigid_apply(m.T, m.means[i], m.quats[i], a, b);
+    m.out_means[i] = a;
+    m.out_quats[i] = b;
 }
 
 }  // namespace
@@ -504,6 +529,14 @@ void transform(const float4 *means, const float4 *quats, int64_t n, const double
     for (int k = 0; k < 12; ++k)
         r.T[k] = T[k];
     k_transform<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(means, quats, n, r, out_means, out_quats);
+    ++g_launches;
+}
+
+void transform_batch(const MapDesc *maps, int n_maps, unsigned blocks, cudaStream_t s)
+{
+    if (n_maps <= 0 || blocks == 0)
+        return;
+    k_transform_batch<<<blocks, 256, 0, s>>>(maps, n_maps);
     ++g_launches;
 }
 

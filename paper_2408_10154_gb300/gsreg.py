@@ -71,7 +71,7 @@ class gs_gaussian_grads_t(ctypes.Structure):
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
            "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc", "gs_track_loss",
-           "gs_overlap_ratio",
+           "gs_overlap_ratio", "gs_transform_batch",
            "gs_server_create",
            "gs_server_destroy", "gs_server_last_error", "gs_server_submit", "gs_server_step", "gs_server_poll",
            "gs_server_counts"]
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = False):
             "gs_loss": ([P, P, I, P, P, P, P, P, P, P, P], I),
             "gs_track_loss": ([P, P, I, P, P, P, P, P, ctypes.c_float, P, P, P, P, P, P], I),
             "gs_overlap_ratio": ([P, P, P, P, ctypes.c_float, P, P, P, P, P], I),
+            "gs_transform_batch": ([P, P, I, P, P, P, P], I),
             "gs_pose_step": ([P, I, P, P, P, P, I, I, P, P], I),
             "gs_fuse": ([P, I, P, P, P, P, P, P], I),
             "gs_register": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P], I),
@@ -421,6 +422,19 @@ def gs_transform(ctx: Context, g: Gaussians, T) -> Gaussians:
     ctx.check(ctx._lib.gs_transform(ctx.handle, ctypes.byref(gst), Th.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                     _ptr(q), _stream()))
     return Gaussians(m, g.log_scales4.clone(), q, g.logits.clone(), g.rgb4.clone())
+
+
+def gs_transform_batch(ctx: Context, maps, Ts):
+    """Map adjustment: every submap of ``maps`` moved by its own T (Eq. 8/9)
+    in one launch.  Returns new Gaussians per map."""
+    n = len(maps)
+    arr = (gs_gaussians_t * max(n, 1))(*[g.c_struct() for g in maps])
+    Th = np.ascontiguousarray(np.asarray(Ts, np.float64).reshape(n, 12))
+    outs = [(torch.empty_like(g.means4), torch.empty_like(g.quats4)) for g in maps]
+    om = (ctypes.c_void_p * max(n, 1))(*[m.data_ptr() for m, _ in outs])
+    oq = (ctypes.c_void_p * max(n, 1))(*[q.data_ptr() for _, q in outs])
+    ctx.check(ctx._lib.gs_transform_batch(ctx.handle, arr, n, Th.ctypes.data_as(ctypes.c_void_p), om, oq, _stream()))
+    return [Gaussians(m, g.log_scales4, q, g.logits, g.rgb4) for g, (m, q) in zip(maps, outs)]
 
 
 def gs_render_noalloc(g: Gaussians, poses: torch.Tensor, cams, opt=None, out=None):

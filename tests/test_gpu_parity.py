@@ -488,3 +488,20 @@ def test_registration_room_full_size_converged_keyframes(gs, ctx):
         assert ang < 0.01 and dt < 5e-4, (k, ang, dt, eps[k])
     ang, dt = rot_err(T, c["T_gt"])
     assert ang < 0.5 and dt < 0.01, (ang, dt)
+
+
+def test_transform_batch_equals_single_transforms(gs, ctx):
+    # map adjustment: three submaps (one empty) corrected in one launch,
+    # bit-equal to one gs_transform each and within 2e-6 of the oracle
+    rng = np.random.default_rng(16)
+    cases = [synth.small_case(n, 32, 32, 30.0, seed=s)["gaussians"] for n, s in ((700, 1), (0, 2), (2500, 3))]
+    maps = [gs.Gaussians.from_numpy(d) for d in cases]
+    Ts = [synth.random_rigid(rng, 25.0, 0.4) for _ in cases]
+    outs = gs.gs_transform_batch(ctx, maps, Ts)
+    for d, g, T, o in zip(cases, maps, Ts, outs):
+        one = gs.gs_transform(ctx, g, T)
+        np.testing.assert_array_equal(o.means4.cpu().numpy(), one.means4.cpu().numpy())
+        np.testing.assert_array_equal(o.quats4.cpu().numpy(), one.quats4.cpu().numpy())
+        if len(d["means4"]):
+            ref = O.transform(O.Gaussians.from_dict(d), T)
+            np.testing.assert_allclose(o.means4.cpu().numpy(), ref.means4, atol=2e-6)
