@@ -47,8 +47,9 @@ FLOPS_WALKED = 9.0
 FWD_FLOPS_CONTRIB = 34.0
 BWD_FLOPS_CONTRIB = 73.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
-# the current kernel (profiles/k_backward2_room_150k.md); None if stale
-BWD_TRAFFIC_BYTES = None
+# the current kernel (profiles/k_backward2_room_150k.md: 184.7 MB read +
+# 5.5 MB written); None once the kernel changes
+BWD_TRAFFIC_BYTES = 190.2e6
 SMS = 152
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -474,6 +475,44 @@ def run_serve(args):
     return 0
 
 
+def run_overlap(args):
+    """Overlap ratio (loop filter) of the room submap pair under its ground
+    truth: exact nearest neighbours both ways over 150k x 150k means.  Prints
+    one JSON line (ms per call, pairs evaluated, FP32 issue roofline)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2408_10154_gb300 as gs
+    from paper_2408_10154_gb300 import synth
+    ctx = gs.Context(0)
+    c = synth.room_150k()
+    src = gs.Gaussians.from_numpy(c["gaussians"])
+    tgt = gs.gs_transform(ctx, src, c["T_gt"])
+    for _ in range(max(args.warmup, 1)):
+        gs.gs_overlap_ratio(ctx, src, tgt, c["T_gt"])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        r, k = gs.gs_overlap_ratio(ctx, src, tgt, c["T_gt"])
+    ev1.record()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    pairs = 2.0 * src.n * tgt.n
+    pk = peaks()
+    peak = SMS * FP32_LANES * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+    flops = 8.0 * pairs  # 3 differences, 1 multiply, 2 fused multiply-adds (2 flops each)
+    out = {"metric": "overlap ratio calls/s", "value": 1000.0 / ms, "unit": "calls/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "overlap ratio of the room_150k pair (150,000 x 150,000 means, both directions)"},
+           "overlap": r, "correspondences": k, "pairs_per_call": pairs,
+           "roofline": {"kernel": "k_nn", "bound": "alu", "achieved": flops / (ms / 1000.0) / 1e12, "peak": peak,
+                        "unit": "TFLOP/s", "frac": flops / (ms / 1000.0) / 1e12 / peak, "traffic": None}}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_batched(args):
     """Batched uneven registration: the 32 submap pairs of the batched
     workload (20k-400k Gaussians, 4-12 keyframes per submap at 640x480 or
@@ -579,7 +618,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="room_150k", choices=["room_150k", "batched_32", "serve"],
+    ap.add_argument("--workload", default="room_150k", choices=["room_150k", "batched_32", "serve", "overlap"],
                     help="room_150k: the benchmark line; batched_32: batched vs one-pair-per-call; "
                          "serve: continuous-batching server vs one request at a time")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
@@ -597,6 +636,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "overlap":
+        return run_overlap(args)
     return run_ours(args)
 
 
