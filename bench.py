@@ -47,9 +47,9 @@ FLOPS_WALKED = 9.0
 FWD_FLOPS_CONTRIB = 34.0
 BWD_FLOPS_CONTRIB = 73.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
-# the current kernel (profiles/k_backward2_room_150k.md: 184.7 MB read +
-# 5.5 MB written); None once the kernel changes
-BWD_TRAFFIC_BYTES = 190.2e6
+# the current kernel (profiles/k_backward2_room_150k.md); None while the
+# kernel has changed since the capture
+BWD_TRAFFIC_BYTES = None
 SMS = 152
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")

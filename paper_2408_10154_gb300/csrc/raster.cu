@@ -65,13 +65,14 @@ __device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float p
 // exponent loses that accuracy, are never dropped).  A dropped pair would
 // have been skipped by the alpha test, so every result is unchanged; the
 // cull only removes iterations (most of a tile's list misses a given 8x4
-// patch).  NaN anywhere keeps the record.
-__device__ __forceinline__ bool patch_may_hit(const float4 &q0, float cc, float o, float xa, float xb, float ya,
-                                              float yb, float cut)
+// patch).  NaN anywhere keeps the record.  pcut = ln(alpha_min / o) - 0.05,
+// the record's exponent cutoff (see stage_cutoff).
+__device__ __forceinline__ bool patch_may_hit(const float4 &q0, float cc, float pcut, float xa, float xb, float ya,
+                                              float yb)
 {
     const float A = -2.0f * q0.z, B = -q0.w, C = -2.0f * cc;
     const float AC = A * C, BB = B * B;
-    const float tau = cut - __logf(o);  // cut = ln(alpha_min) - 0.06
+    const float tau = pcut - 0.01f;
     if (tau >= 0.0f)
         return false;  // o < alpha_min e^-0.06: no pixel can reach alpha_min
     const float det = AC - BB;
@@ -81,6 +82,20 @@ __device__ __forceinline__ bool patch_may_hit(const float4 &q0, float cc, float 
     const float ex = fmaf(sqrtf(s * C), 1.001f, 0.01f), ey = fmaf(sqrtf(s * A), 1.001f, 0.01f);
     const bool out = (q0.x + ex < xa) || (q0.x - ex > xb) || (q0.y + ey < ya) || (q0.y - ey > yb);
     return !out;
+}
+
+// The second float4 of a staged record, {cc, o, z, cutoff}: the tile
+// rectangle it carries in HBM is not needed once the lists are built, and
+// its slot takes the record's exponent cutoff ln(alpha_min / o) - 0.05
+// (ln(alpha_min) - 0.05 - ln o; __logf's error is far inside the 0.05
+// margin).  A pair whose exponent is below it has alpha = o e^x <
+// alpha_min e^-0.05 and fails the alpha test, so skipping it before e^x
+// changes no decision.  Without an alpha test (smooth mode) the cutoff is
+// the plain skip_below (-3e38), which skips nothing.
+__device__ __forceinline__ float4 stage_cutoff(float4 q1, const gsl::RasterArgs &a)
+{
+    q1.w = a.alpha_min > 0.0f ? a.skip_below - __logf(q1.y) : a.skip_below;
+    return q1;
 }
 
 // forward variants (registration mode): exposure compensation, and the
@@ -101,7 +116,6 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float xa = pxf - (float)(lane & 7), xb = xa + 7.0f, ya = pyf - (float)(lane >> 3), yb = ya + 3.0f;
     const bool cull = a.alpha_min > 0.0f;
-    const float cut = a.skip_below - 0.01f;
     const uint2 rg = a.ranges[t];
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     int last = 0, n_contrib = 0;
@@ -113,7 +127,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
         if (idx < rg.y) {
             const float4 *R = a.rec + 3 * (size_t)a.vals[idx];
             s0[threadIdx.x] = R[0];
-            s1[threadIdx.x] = R[1];
+            s1[threadIdx.x] = stage_cutoff(R[1], a);
             s2[threadIdx.x] = R[2];
         }
         __syncthreads();
@@ -122,7 +136,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
         if (!__all_sync(0xffffffffu, done)) {
             for (int j0 = 0; j0 < cnt; j0 += 32) {
                 const int j = j0 + lane;
-                const bool keep = j < cnt && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].y, xa, xb, ya, yb, cut));
+                const bool keep = j < cnt && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].w, xa, xb, ya, yb));
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (keep)
                     s_sel[warp][nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
@@ -137,7 +151,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
                 const float4 q1 = s1[j];
                 float dx, dy;
                 const float power = exponent_at(q0, q1.x, pxf, pyf, dx, dy);
-                if (power > 0.0f || power < a.skip_below)
+                if (power > 0.0f || power < q1.w)
                     continue;
                 const float x = mul_rn(q1.y, exp_ct(power));
                 const float alpha = x > a.alpha_max ? a.alpha_max : x;
@@ -479,7 +493,7 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
         return false;
     float dx, dy;
     const float power = exponent_at(q0, q1.x, P.pxf, P.pyf, dx, dy);
-    if (power > 0.0f || power < a.skip_below)
+    if (power > 0.0f || power < q1.w)
         return false;
     const float e = exp_ct(power);
     const float x = mul_rn(q1.y, e);
@@ -550,7 +564,6 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     const float xa = (float)(tx * kTile) + 0.5f, xb = xa + 15.0f;
     const float ya = (float)(ty * kTile + warp * 4) + 0.5f, yb = ya + 3.0f;
     const bool cull = a.alpha_min > 0.0f;
-    const float cut = a.skip_below - 0.01f;
     const uint2 rg = a.ranges[t];
     PixAdj P0, P1;
     const float gain = (REG && d.exposure) ? a.expo32[2 * vp] : 1.0f;
@@ -581,7 +594,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
             s_rec[threadIdx.x] = r;
             const float4 *R = a.rec + 3 * (size_t)r;
             s0[threadIdx.x] = R[0];
-            s1[threadIdx.x] = R[1];
+            s1[threadIdx.x] = stage_cutoff(R[1], a);
             s2[threadIdx.x] = R[2];
         }
         for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwd2Chunk; k += kBwd2Threads)
@@ -592,7 +605,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
         int nsel = 0;
         for (int j0 = 0; j0 < wl; j0 += 32) {
             const int j = j0 + lane;
-            const bool keep = j < wl && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].y, xa, xb, ya, yb, cut));
+            const bool keep = j < wl && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].w, xa, xb, ya, yb));
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (keep)
                 s_sel[warp][nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
