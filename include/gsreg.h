@@ -229,7 +229,8 @@ typedef struct {
  *              x -> exp([w]x)(x - c) + c + v, in the world frame.
  *   pose_grad  [n_cams][6] float out or NULL: dL/d(w, v) per camera.
  *   grads      per-Gaussian gradients or NULL (summed over cameras).
- * Synchronises `stream` once. */
+ * Synchronises `stream` (to size the lists, and at the end to read the
+ * device status word). */
 gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses,
                                const gs_camera_t *cams, int n_cams, const gs_options_t *opt,
                                const float *t_final, const int32_t *last, const float *d_rgb,

@@ -22,7 +22,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_COUNT
 };
 
 struct Buf {
@@ -316,6 +316,7 @@ struct Pipe {
     uint32_t *tkeys[2] = {nullptr, nullptr};
     uint32_t *n_vis = nullptr;
     uint64_t n_records = 0;
+    uint8_t *os = nullptr;  // one-sweep sort state
 };
 
 // Binning route of the context-based entry points: the two-stage route
@@ -364,6 +365,9 @@ gs_status_t alloc_sort(gs_ctx *ctx, uint64_t want, Pipe &p)
     const size_t hn = gsl::sort_hist_entries((uint32_t)std::max<uint64_t>(cap, p.n_records));
     GS_TRY(wsT(ctx, S_HIST, hn, &p.hist));
     GS_TRY(wsT(ctx, S_HISTP, gsl::scan_partials(hn), &p.histp));
+    if (kTwoStageBinning)
+        GS_TRY(wsT(ctx, S_OS, gsl::onesweep_scratch_bytes((uint32_t)std::max<uint64_t>(cap, p.n_records), 32),
+                   &p.os));
     p.cap = cap;
     return GS_OK;
 }
@@ -419,6 +423,7 @@ gsl::BinArgs bin_args(const Plan &P, const DevPlan &D, const Pipe &p)
         b.tkeys[k] = p.tkeys[k];
     }
     b.n_vis = p.n_vis;
+    b.os_scratch = p.os;
     return b;
 }
 
@@ -801,6 +806,10 @@ gs_status_t gs_bin(gs_ctx_t *ctx, const float *records, const int32_t *counts, c
         GS_CUDA(cudaMemcpyAsync(vals, p.vals[cur], sizeof(uint32_t) * nd, cudaMemcpyDeviceToDevice, s));
     }
     GS_CUDA(cudaGetLastError());
+    int flags = 0;
+    GS_TRY(read_flags(ctx, p, s, &flags));
+    if (flags & gsk::kFlagTimeout)
+        return fail(ctx, GS_ERR_TIMEOUT, "a sort pass gave up waiting for an earlier tile");
     return GS_OK;
 }
 
@@ -839,6 +848,8 @@ gs_status_t gs_render(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses
     GS_TRY(read_flags(ctx, p, s, &flags));
     if (flags & gsk::kFlagNonFinite)
         return fail(ctx, GS_ERR_NONFINITE, "non-finite Gaussian parameter");
+    if (flags & gsk::kFlagTimeout)
+        return fail(ctx, GS_ERR_TIMEOUT, "a sort pass gave up waiting for an earlier tile");
     return GS_OK;
 }
 
@@ -931,6 +942,10 @@ gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const flo
         ++gsl::g_launches;
     }
     GS_CUDA(cudaGetLastError());
+    int flags = 0;
+    GS_TRY(read_flags(ctx, p, s, &flags));
+    if (flags & gsk::kFlagTimeout)
+        return fail(ctx, GS_ERR_TIMEOUT, "a sort pass gave up waiting for an earlier tile");
     return GS_OK;
 }
 
@@ -1426,6 +1441,8 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         GS_TRY(read_flags(ctx, p, s, &flags));
         if (flags & gsk::kFlagNonFinite)
             return fail(ctx, GS_ERR_NONFINITE, "non-finite Gaussian parameter");
+        if (flags & gsk::kFlagTimeout)
+            return fail(ctx, GS_ERR_TIMEOUT, "a sort pass gave up waiting for an earlier tile");
         if (flags & gsk::kFlagCapacity) {
             headroom *= 2.0;  // the lists outgrew the headroom: redo with more
             continue;
@@ -1890,6 +1907,8 @@ gs_status_t srv_round(gs_server *srv, cudaStream_t s, int64_t *done_ids, int max
         GS_CUDA(cudaStreamSynchronize(s));
         if (flags & gsk::kFlagNonFinite)
             return fail(ctx, GS_ERR_NONFINITE, "non-finite Gaussian parameter in an in-flight request");
+        if (flags & gsk::kFlagTimeout)
+            return fail(ctx, GS_ERR_TIMEOUT, "a sort pass gave up waiting for an earlier tile");
         if (flags & gsk::kFlagCapacity) {
             // the lists outgrew their headroom: redo the round from the saved states
             if (attempt >= 3)

@@ -170,6 +170,8 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const gsl::BinArgs a, con
 }
 
 // ---------------------------------------------------------------- radix sort
+__device__ __forceinline__ uint32_t div_up_d(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
+
 __device__ __forceinline__ uint32_t live_count(const uint32_t *n_dups, uint32_t cap)
 {
     const uint32_t n = *n_dups;
@@ -451,6 +453,185 @@ __global__ void k_keys64(const uint32_t *tkeys, const uint32_t *vals, const floa
 
 inline uint32_t div_up(size_t a, size_t b) { return (uint32_t)((a + b - 1) / b); }
 
+// ------------------------------------------------------------ one-sweep sort
+// status word of (tile, digit): 2 flag bits (1 = aggregate of this tile
+// only, 2 = inclusive prefix over tiles 0..t) and a 62-bit count
+constexpr unsigned long long kOsAgg = 1ull << 62, kOsPrefix = 2ull << 62, kOsCount = (1ull << 62) - 1;
+constexpr int kOsMaxPasses = 4;
+constexpr long kOsSpinLimit = 1l << 20;  // well under a second of L2 round trips, then give up
+constexpr int kOsWindow = 16;            // predecessor status words read per look-back step
+
+struct OsLayout {
+    uint32_t *counters;             // [passes] dynamic tile ids
+    uint32_t *ghist;                // [passes][256] global digit counts
+    uint32_t *gbase;                // [passes][256] their exclusive scan
+    unsigned long long *status;     // [passes][tiles][256]
+    size_t zero_bytes;              // bytes from counters through status to clear
+};
+
+OsLayout os_layout(uint8_t *base, uint32_t tiles)
+{
+    OsLayout L;
+    L.counters = (uint32_t *)base;                                   // 64 B
+    L.ghist = (uint32_t *)(base + 64);                               // 4 KB
+    L.gbase = L.ghist + kOsMaxPasses * 256;                          // 4 KB
+    L.status = (unsigned long long *)(base + 64 + 2 * 4 * kOsMaxPasses * 256);
+    L.zero_bytes = 64 + 2 * 4 * kOsMaxPasses * 256 + sizeof(unsigned long long) * kOsMaxPasses * 256 * (size_t)tiles;
+    return L;
+}
+
+// per-digit counts of every pass, over all live keys (grid-stride, warp-
+// aggregated shared atomics, one global atomic per block and digit)
+__global__ void __launch_bounds__(kSortThreads) k_os_hist(const uint32_t *keys, const uint32_t *n_dev, uint32_t cap,
+                                                          int passes, uint32_t *ghist)
+{
+    __shared__ uint32_t h[kOsMaxPasses][256];
+    for (int k = threadIdx.x; k < kOsMaxPasses * 256; k += blockDim.x)
+        (&h[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t n = live_count(n_dev, cap);
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t key = valid ? keys[i] : 0u;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = valid ? (key >> (8 * p)) & 0xffu : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256u && (uint32_t)(__ffs(peers) - 1) == lane)
+                atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < passes * 256; k += blockDim.x) {
+        const uint32_t v = (&h[0][0])[k];
+        if (v)
+            atomicAdd(&ghist[k], v);
+    }
+}
+
+// exclusive scan of each pass's 256 digit counts (one CTA of 256 threads)
+__global__ void __launch_bounds__(256) k_os_scan(const uint32_t *ghist, int passes, uint32_t *gbase)
+{
+    __shared__ uint32_t s_warp[256 / 32 + 1];
+    for (int p = 0; p < passes; ++p) {
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan<256>(ghist[p * 256 + threadIdx.x], s_warp, tot);
+        gbase[p * 256 + threadIdx.x] = ex;
+    }
+}
+
+__device__ __forceinline__ unsigned long long os_load(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+
+// One pass: rank the tile's keys stably (as k_rs_scatter), publish the
+// tile's digit counts, look back for the prefix of the earlier tiles, and
+// scatter to the digit's global base + that prefix + the local rank.
+__global__ void __launch_bounds__(kSortThreads) k_os_pass(const uint32_t *kin, const uint32_t *vin,
+                                                          const uint32_t *n_dev, uint32_t cap, int shift,
+                                                          const uint32_t *gbase, unsigned long long *status,
+                                                          uint32_t *counter, uint32_t *kout, uint32_t *vout,
+                                                          int *flags)
+{
+    __shared__ uint32_t cnt[kSortThreads / 32][256];
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0)
+        s_tile = atomicAdd(counter, 1u);
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * 256; k += blockDim.x)
+        (&cnt[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t n = live_count(n_dev, cap);
+    const uint32_t tile = s_tile;
+    if (tile >= div_up_d(n, kSortTile))
+        return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = tile * kSortTile + warp * (32 * kSortKPT);
+    const unsigned lt = lanemask_lt();
+    uint32_t key[kSortKPT], val[kSortKPT], off[kSortKPT], dig[kSortKPT];
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : 0u;
+        val[r] = valid ? vin[i] : 0u;
+        const uint32_t d = valid ? (key[r] >> shift) & 0xffu : 256u;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
+        uint32_t o = 0;
+        if (valid)
+            o = cnt[warp][d] + rank;
+        off[r] = o;
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane)
+            cnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread = digit: prefix over warps, the tile's total, then the look-back
+    {
+        const uint32_t d = threadIdx.x;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const uint32_t c = cnt[w][d];
+            cnt[w][d] = tot;
+            tot += c;
+        }
+        unsigned long long *mine = status + (size_t)tile * 256 + d;
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            atomicExch(mine, kOsPrefix | (unsigned long long)tot);
+        } else {
+            atomicExch(mine, kOsAgg | (unsigned long long)tot);
+            // walk back kOsWindow tiles per step (independent loads in
+            // flight): add aggregates up to the first inclusive prefix; stop
+            // at a tile that has not published yet and re-read from there
+            long spins = 0;
+            long j = (long)tile - 1;
+            bool found = false;
+            while (!found && j >= 0) {
+                unsigned long long v[kOsWindow];
+#pragma unroll
+                for (int w = 0; w < kOsWindow; ++w)
+                    v[w] = (j - w >= 0) ? os_load(status + (size_t)(j - w) * 256 + d) : kOsPrefix;
+                int w = 0;
+                for (; w < kOsWindow; ++w) {
+                    const unsigned long long f = v[w] & ~kOsCount;
+                    if (f == 0)
+                        break;  // not published yet
+                    excl += v[w] & kOsCount;
+                    if (f == kOsPrefix) {
+                        found = true;
+                        break;
+                    }
+                }
+                if (found)
+                    break;
+                j -= w;
+                if (w == 0 && ++spins > kOsSpinLimit) {  // an earlier tile never published: give up
+                    atomicOr(flags, kFlagTimeout);
+                    break;
+                }
+            }
+            atomicExch(mine, kOsPrefix | (excl + tot));
+        }
+        s_base[d] = gbase[d] + (uint32_t)excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortKPT; ++r) {
+        if (dig[r] < 256u) {
+            const uint32_t pos = s_base[dig[r]] + cnt[warp][dig[r]] + off[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
 // stable LSD radix sort of (key, value) over `bits` low key bits, 8 per pass;
 // returns the buffer index holding the result
 template <typename K>
@@ -496,6 +677,38 @@ void bin_count(const BinArgs &a, cudaStream_t s)
     g_launches += 2;
 }
 
+size_t onesweep_scratch_bytes(uint32_t cap, int bits)
+{
+    (void)bits;
+    return os_layout(nullptr, div_up(cap ? cap : 1, kSortTile)).zero_bytes;
+}
+
+int onesweep_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits,
+                 uint8_t *scratch, int *flags, cudaStream_t s)
+{
+    const int passes = (bits + 7) / 8;
+    if (passes <= 0)
+        return 0;
+    const uint32_t tiles = div_up(cap ? cap : 1, kSortTile);
+    const OsLayout L = os_layout(scratch, tiles);
+    // clear the ids, histograms and the status words of the passes used
+    cudaMemsetAsync(scratch, 0, (size_t)((uint8_t *)L.status - scratch) + sizeof(unsigned long long) * 256 *
+                                    (size_t)tiles * passes, s);
+    const uint32_t hb = std::min<uint32_t>(tiles, 4 * 152);
+    k_os_hist<<<hb, kSortThreads, 0, s>>>(keys[0], n_dev, cap, passes, L.ghist);
+    k_os_scan<<<1, 256, 0, s>>>(L.ghist, passes, L.gbase);
+    g_launches += 2;
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        k_os_pass<<<tiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], n_dev, cap, 8 * p, L.gbase + 256 * p,
+                                                 L.status + (size_t)p * tiles * 256, L.counters + p,
+                                                 keys[cur ^ 1], vals[cur ^ 1], flags);
+        ++g_launches;
+        cur ^= 1;
+    }
+    return cur;
+}
+
 int sort_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits, uint32_t *hist,
              uint32_t *hist_partials, cudaStream_t s)
 {
@@ -511,7 +724,8 @@ int bin2(const BinArgs &a, cudaStream_t s)
     k_vis_compact<<<nb, kScanThreads, 0, s>>>(a.counts, a.rec, R, a.partials, a.dkeys[0], a.dvals[0]);
     g_launches += 3;
     uint32_t *dk[2] = {a.dkeys[0], a.dkeys[1]}, *dv[2] = {a.dvals[0], a.dvals[1]};
-    const int dc = radix_sort<uint32_t>(dk, dv, a.n_vis, R, 32, a.hist, a.hist_partials, s);
+    const int dc = a.os_scratch ? onesweep_u32(dk, dv, a.n_vis, R, 32, a.os_scratch, a.flags, s)
+                                : radix_sort<uint32_t>(dk, dv, a.n_vis, R, 32, a.hist, a.hist_partials, s);
     // tile counts in depth order and their exclusive scan (total = n_dups),
     // in the depth-key buffers the sort no longer needs
     uint32_t *cnt = dk[dc], *offs = dk[dc ^ 1];
@@ -522,7 +736,10 @@ int bin2(const BinArgs &a, cudaStream_t s)
                                                                                           a.tkeys[0], a.vals[0]);
     ++g_launches;
     uint32_t *tk[2] = {a.tkeys[0], a.tkeys[1]}, *tv[2] = {a.vals[0], a.vals[1]};
-    const int tc = radix_sort<uint32_t>(tk, tv, a.n_dups, a.capacity, a.key_bits - 32, a.hist, a.hist_partials, s);
+    const int tc = a.os_scratch
+                       ? onesweep_u32(tk, tv, a.n_dups, a.capacity, a.key_bits - 32, a.os_scratch, a.flags, s)
+                       : radix_sort<uint32_t>(tk, tv, a.n_dups, a.capacity, a.key_bits - 32, a.hist, a.hist_partials,
+                                              s);
     cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.n_tiles, s);
     k_ranges<uint32_t><<<div_up(a.capacity ? a.capacity : 1, 256), 256, 0, s>>>(tk[tc], a.n_dups, a.capacity,
                                                                                 a.ranges);

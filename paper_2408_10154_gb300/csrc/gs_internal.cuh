@@ -19,7 +19,7 @@ constexpr int kSortTile = kSortThreads * kSortKPT;
 constexpr int kMaxVpPerGroup = 64;    // keyframes sharing one projection pass
 
 // device status word bits
-enum : int { kFlagNonFinite = 1, kFlagCapacity = 2 };
+enum : int { kFlagNonFinite = 1, kFlagCapacity = 2, kFlagTimeout = 4 };
 
 // One view-problem: a moving submap seen by one keyframe camera, with its
 // own pose, Adam state and (in registration) target images.
@@ -210,6 +210,7 @@ struct BinArgs {
     uint32_t *dkeys[2], *dvals[2];  // [n_records]
     uint32_t *tkeys[2];             // [capacity]
     uint32_t *n_vis;                // device scalar
+    uint8_t *os_scratch;            // one-sweep sort state (onesweep_scratch_bytes), or null = classic passes
 };
 // emits, sorts and ranges; returns which buffer holds the sorted result
 int bin(const BinArgs &a, cudaStream_t s);
@@ -217,6 +218,14 @@ int bin(const BinArgs &a, cudaStream_t s);
 // tile sort of duplicates); the sorted values are in vals[return], the tile
 // keys in tkeys[return]
 int bin2(const BinArgs &a, cudaStream_t s);
+// One-sweep LSD radix sort of 32-bit keys (8-bit digits): one histogram
+// kernel for every digit, one scan of the digit counts, one scatter per
+// pass whose CTAs find their digit offsets by decoupled look-back (dynamic
+// tile ids; every wait bounded, a timeout sets kFlagTimeout).  Same stable
+// order as radix_sort.  Returns the buffer index holding the result.
+size_t onesweep_scratch_bytes(uint32_t cap, int bits);
+int onesweep_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits,
+                 uint8_t *scratch, int *flags, cudaStream_t s);
 // 64-bit keys (tile << 32 | depth bits) of a bin2 result
 void keys64(const BinArgs &a, int cur, uint64_t *out, cudaStream_t s);
 void bin_count(const BinArgs &a, cudaStream_t s);  // scan only: n_dups
