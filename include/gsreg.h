@@ -121,6 +121,12 @@ typedef struct {
      * pose; not combinable with tracking_loss */
     int32_t exposure;
     float lr_exposure; /* 0.1 (Supp. B) */
+    /* CTA schedule of the compositing kernels in gs_register* (results are
+     * identical either way): 0 = picked by the autotuner (the first
+     * registration of a plan shape on a context times both on trial
+     * iterations from the initial poses and keeps the faster), 1 = natural
+     * tile order, 2 = longest tile lists first */
+    int32_t tile_schedule;
 } gs_options_t;
 
 /* Statistics of the last gs_register / gs_render call on a context. */

@@ -9,7 +9,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -22,7 +24,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_COUNT
 };
 
 struct Buf {
@@ -48,6 +50,9 @@ struct gs_ctx {
     gs_stats_t stats{};
     cudaEvent_t tev[kPhases + 1] = {};  // phase boundaries recorded in the captured iteration
     std::vector<cudaEvent_t> pool;      // per-iteration copies of the boundaries
+    // autotuner: tile schedule chosen per plan shape (tiles, keyframes, records)
+    std::map<std::tuple<uint64_t, size_t, uint64_t>, int> schedule;
+    int64_t tuned = 0;  // trial runs made
 };
 
 namespace {
@@ -185,6 +190,8 @@ gs_status_t check_options(gs_ctx *ctx, const gs_options_t *o)
         return fail(ctx, GS_ERR_INVALID_ARG, "options out of range");
     if ((o->tracking_loss != 0 && o->tracking_loss != 1) || !(o->lambda_c >= 0 && o->lambda_c <= 1))
         return fail(ctx, GS_ERR_INVALID_ARG, "tracking_loss must be 0 or 1 and lambda_c in [0, 1]");
+    if (o->tile_schedule < 0 || o->tile_schedule > 2)
+        return fail(ctx, GS_ERR_INVALID_ARG, "tile_schedule must be 0 (autotune), 1 or 2");
     if ((o->exposure != 0 && o->exposure != 1) || !(o->lr_exposure >= 0) || !std::isfinite(o->lr_exposure) ||
         (o->exposure && o->tracking_loss))
         return fail(ctx, GS_ERR_INVALID_ARG,
@@ -659,6 +666,7 @@ void gs_default_options(gs_options_t *o)
     o->lambda_c = 0.6f;
     o->exposure = 0;
     o->lr_exposure = 0.1f;
+    o->tile_schedule = 0;
     o->lr_final = 0.001f;
 }
 
@@ -1312,7 +1320,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
     double headroom = 1.5;
     for (int attempt = 0; attempt < 3; ++attempt) {
         const long long l0 = gsl::g_launches;
-        long long captured = 0, graph_kernels = 0;
+        long long captured = 0, graph_kernels = 0, trial_kernels = 0;
         ctx->stats = gs_stats_t{};
         gsl::centroids(D.vps, D.set_vp, n_sets, cent, s);
         gsl::pose_init(pa, s);
@@ -1339,10 +1347,14 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         r.count_contrib = opt->profile >= 2;
         gsl::TrackArgs ta;
         GS_TRY(alloc_track(ctx, P, D, r, ta, tloss, s));
+        uint32_t *order = nullptr, *order_cnt = nullptr;
+        GS_TRY(wsT(ctx, S_ORDER, ntl, &order));
+        GS_TRY(wsT(ctx, S_ORDC, 128, &order_cnt));
+        bool ordered = false, marking = prof;
         cudaError_t mark_err = cudaSuccess;
         auto mark = [&](int k, cudaStream_t st) {
             // an event record node of the captured graph (re-targeted per replay)
-            if (prof && mark_err == cudaSuccess)
+            if (marking && mark_err == cudaSuccess)
                 mark_err = cudaEventRecordWithFlags(ctx->tev[k], st, cudaEventRecordExternal);
         };
         auto iteration = [&](cudaStream_t st) {
@@ -1350,8 +1362,11 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             gsl::project(project_args(P, D, p, pose32, opt), st);
             mark(1, st);
             const int c = run_bin(b, st);
+            if (ordered)
+                gsl::tile_order(p.ranges, (uint32_t)P.n_tiles, order, order_cnt, st);
             mark(2, st);
             r.vals = p.vals[c];
+            r.tile_order = ordered ? order : nullptr;
             gsl::forward(r, true, st);
             gsl::track_loss(ta, st);
             mark(3, st);
@@ -1360,18 +1375,86 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             gsl::pose_update(pa, st);
             mark(5, st);
         };
-        GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
-        GS_CUDA(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * 2 * ntl, s));
-        if (iters > 0) {
+        // one iteration captured into an executable graph
+        auto capture = [&](cudaGraphExec_t *exec, cudaGraph_t *graph_out) -> gs_status_t {
             GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-            const long long c0 = gsl::g_launches;
             iteration(ctx->cap);
-            captured = gsl::g_launches - c0;
             cudaGraph_t graph = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
             if (ce != cudaSuccess || !graph)
                 return fail(ctx, GS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+            const cudaError_t ie = cudaGraphInstantiate(exec, graph, 0);
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return fail(ctx, GS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+            }
+            if (graph_out)
+                *graph_out = graph;
+            else
+                cudaGraphDestroy(graph);
+            return GS_OK;
+        };
+        // Autotuner: the CTA schedule of the compositing kernels (natural
+        // tile order or longest lists first) for this plan shape, timed on
+        // trial iterations A B B A from the initial poses, then the poses
+        // start over.  Either schedule gives the same results.
+        int sched = opt->tile_schedule;
+        const auto key = std::make_tuple((uint64_t)P.n_tiles, P.vps.size(), (uint64_t)P.n_records);
+        if (sched == 0) {
+            const auto it = ctx->schedule.find(key);
+            if (it != ctx->schedule.end()) {
+                sched = it->second;
+            } else if (iters >= 8 && P.n_tiles >= 2048) {
+                marking = false;
+                cudaGraphExec_t ga = nullptr, gb = nullptr;
+                const long long t0 = gsl::g_launches;
+                ordered = false;
+                GS_TRY(capture(&ga, nullptr));
+                ordered = true;
+                gs_status_t st = capture(&gb, nullptr);
+                trial_kernels = gsl::g_launches - t0;  // each graph runs twice: count them once more
+                cudaEvent_t e[5] = {};
+                for (cudaEvent_t &x : e)
+                    if (st == GS_OK && cudaEventCreate(&x) != cudaSuccess)
+                        st = fail(ctx, GS_ERR_CUDA, "autotuner events");
+                const cudaGraphExec_t seq[4] = {ga, gb, gb, ga};
+                if (st == GS_OK && cudaEventRecord(e[0], s) != cudaSuccess)
+                    st = fail(ctx, GS_ERR_CUDA, "autotuner events");
+                for (int k = 0; k < 4 && st == GS_OK; ++k)
+                    if (cudaGraphLaunch(seq[k], s) != cudaSuccess || cudaEventRecord(e[k + 1], s) != cudaSuccess)
+                        st = fail(ctx, GS_ERR_CUDA, "autotuner trial launch");
+                float ms[4] = {0, 0, 0, 0};
+                if (st == GS_OK && cudaEventSynchronize(e[4]) == cudaSuccess)
+                    for (int k = 0; k < 4; ++k)
+                        cudaEventElapsedTime(&ms[k], e[k], e[k + 1]);
+                for (cudaEvent_t x : e)
+                    if (x)
+                        cudaEventDestroy(x);
+                if (ga)
+                    cudaGraphExecDestroy(ga);
+                if (gb)
+                    cudaGraphExecDestroy(gb);
+                GS_TRY(st);
+                sched = (ms[1] + ms[2] < ms[0] + ms[3]) ? 2 : 1;
+                ctx->schedule[key] = sched;
+                ++ctx->tuned;
+                gsl::pose_init(pa, s);  // back to the initial poses
+                marking = prof;
+            } else {
+                sched = 1;
+            }
+        }
+        ordered = sched == 2;
+        GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
+        GS_CUDA(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * 2 * ntl, s));
+        if (iters > 0) {
+            const long long c0 = gsl::g_launches;
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            GS_TRY(capture(&exec, &graph));
+            captured = gsl::g_launches - c0;
             if (mark_err != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
                 cudaGraphDestroy(graph);
                 return fail(ctx, GS_ERR_CUDA, std::string("profile events: ") + cudaGetErrorString(mark_err));
             }
@@ -1394,12 +1477,6 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
                             evnode[k] = nd_;
                 }
             }
-            cudaGraphExec_t exec = nullptr;
-            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-            if (ie != cudaSuccess) {
-                cudaGraphDestroy(graph);
-                return fail(ctx, GS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
-            }
             cudaError_t le = cudaSuccess;
             for (int it = 0; it < iters && le == cudaSuccess; ++it) {
                 if (prof)
@@ -1417,6 +1494,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         }
         // residual eps at the final poses, then Eq. 7
         r.tile_pairs = nullptr;
+        r.tile_order = nullptr;
         gsl::project(project_args(P, D, p, pose32, opt), s);
         r.vals = p.vals[run_bin(b, s)];
         gsl::forward(r, true, s);
@@ -1458,7 +1536,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             GS_CUDA(cudaMemcpyAsync(est_out, est, 12 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaStreamSynchronize(s));
         gs_stats_t &st = ctx->stats;
-        st.kernel_launches = (gsl::g_launches - l0) - captured + graph_kernels * iters;
+        st.kernel_launches = (gsl::g_launches - l0) - captured + graph_kernels * iters + trial_kernels;
         st.n_dups = nd;
         st.n_pixels = P.n_pix;
         st.iterations = iters;

@@ -632,6 +632,43 @@ __global__ void __launch_bounds__(kSortThreads) k_os_pass(const uint32_t *kin, c
     }
 }
 
+// ------------------------------------------------------------ tile schedule
+// bucket of a list length: 0 holds the longest (top bit 31), 32 the empty
+__device__ __forceinline__ uint32_t len_bucket(const uint2 r) { return (uint32_t)__clz((int)(r.y - r.x)); }
+
+__global__ void k_order_hist(const uint2 *ranges, uint32_t n, uint32_t *counts)
+{
+    __shared__ uint32_t h[33];
+    if (threadIdx.x < 33)
+        h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n)
+        atomicAdd(&h[len_bucket(ranges[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x < 33 && h[threadIdx.x])
+        atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+}
+
+// exclusive scan of the 33 bucket counts into the cursors (one warp)
+__global__ void k_order_scan(const uint32_t *counts, uint32_t *cursors)
+{
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int b = 0; b < 33; ++b) {
+            cursors[b] = s;
+            s += counts[b];
+        }
+    }
+}
+
+__global__ void k_order_scatter(const uint2 *ranges, uint32_t n, uint32_t *cursors, uint32_t *order)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n)
+        order[atomicAdd(&cursors[len_bucket(ranges[t])], 1u)] = t;
+}
+
 // stable LSD radix sort of (key, value) over `bits` low key bits, 8 per pass;
 // returns the buffer index holding the result
 template <typename K>
@@ -675,6 +712,17 @@ void bin_count(const BinArgs &a, cudaStream_t s)
     k_scan_partials<<<nb, kScanThreads, 0, s>>>((const uint32_t *)a.counts, a.n_records, a.partials);
     k_scan_top<<<1, 1024, 0, s>>>(a.partials, nb, a.n_dups);
     g_launches += 2;
+}
+
+void tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *counters, cudaStream_t s)
+{
+    if (n_tiles == 0)
+        return;
+    cudaMemsetAsync(counters, 0, 64 * sizeof(uint32_t), s);
+    k_order_hist<<<div_up(n_tiles, 256), 256, 0, s>>>(ranges, n_tiles, counters);
+    k_order_scan<<<1, 32, 0, s>>>(counters, counters + 64);
+    k_order_scatter<<<div_up(n_tiles, 256), 256, 0, s>>>(ranges, n_tiles, counters + 64, order);
+    g_launches += 3;
 }
 
 size_t onesweep_scratch_bytes(uint32_t cap, int bits)

@@ -218,6 +218,12 @@ int bin(const BinArgs &a, cudaStream_t s);
 // tile sort of duplicates); the sorted values are in vals[return], the tile
 // keys in tkeys[return]
 int bin2(const BinArgs &a, cudaStream_t s);
+// Tile schedule for the compositing kernels: tiles ordered by decreasing
+// list length (bucketed by the position of the length's top bit; order
+// within a bucket arbitrary), so the longest tiles start first and do not
+// form the tail of a launch.  counters: 128 uint32 of scratch.
+void tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *counters, cudaStream_t s);
+
 // One-sweep LSD radix sort of 32-bit keys (8-bit digits): one histogram
 // kernel for every digit, one scan of the digit counts, one scatter per
 // pass whose CTAs find their digit offsets by decoupled look-back (dynamic
@@ -253,6 +259,7 @@ struct RasterArgs {
     float *tile_loss;         // [tiles]
     unsigned long long *tile_pairs;  // [2][tiles] += sum of `last`, pairs passing the alpha test
                                      // (count_contrib only); statistics, may be null
+    const uint32_t *tile_order;      // CTA -> tile schedule (longest lists first), or null = natural
     int exposure;                    // some keyframe compensates exposure (forward variant)
     int count_contrib;               // count the pairs that pass the alpha test (forward variant)
     double *tile_twist;       // [tiles][6], camera frame

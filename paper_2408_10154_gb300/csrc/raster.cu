@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
     __shared__ float4 s0[256], s1[256], s2[256];
     __shared__ uint8_t s_sel[8][256];  // per warp: batch positions that may hit its patch
     __shared__ float s_red[8];
-    const uint32_t t = blockIdx.x;
+    const uint32_t t = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
     const VpDesc &d = a.vps[a.tile_vp[t]];
     const PixelCoord p = pixel_of(d, t);
     const float pxf = (float)p.px + 0.5f, pyf = (float)p.py + 0.5f;
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
     __shared__ int s_maxl[kBwd2Warps];
     __shared__ double s_tw[kBwd2Warps][6];
-    const uint32_t t = blockIdx.x;
+    const uint32_t t = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
     const int vp = (int)a.tile_vp[t];
     const VpDesc &d = a.vps[vp];
     const uint32_t lt = t - d.tile_base;

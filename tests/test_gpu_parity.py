@@ -505,3 +505,19 @@ def test_transform_batch_equals_single_transforms(gs, ctx):
         if len(d["means4"]):
             ref = O.transform(O.Gaussians.from_dict(d), T)
             np.testing.assert_allclose(o.means4.cpu().numpy(), ref.means4, atol=2e-6)
+
+
+def test_tile_schedules_give_identical_registrations(gs, ctx):
+    # two full-size room keyframes (3225 tiles each): natural tile order,
+    # longest lists first, and the autotuner's pick give the same result
+    c = synth.room_150k()
+    og = O.Gaussians.from_dict(c["gaussians"])
+    g = gs.Gaussians.from_numpy(c["gaussians"])
+    views = []
+    for cam in c["src_cams"][:2]:
+        tr = O.render(og, c["T_gt"], cam)
+        views.append((cam, dev(tr["rgb"].astype(np.float32)), dev(tr["depth"].astype(np.float32))))
+    out = [gs.gs_register(ctx, g, g, [], views, 10, gs.default_options(tile_schedule=k)) for k in (1, 2, 0, 0)]
+    for o in out[1:]:
+        np.testing.assert_array_equal(o[0], out[0][0])
+        np.testing.assert_array_equal(o[2], out[0][2])
