@@ -127,6 +127,11 @@ typedef struct {
      * iterations from the initial poses and keeps the faster), 1 = natural
      * tile order, 2 = longest tile lists first */
     int32_t tile_schedule;
+    /* tile lists of gs_register* (results are identical either way): 1 =
+     * each Gaussian listed only on the tiles where some pixel can reach
+     * alpha_min (its alpha-threshold ellipse's box, with margins; about a
+     * third fewer duplicates), 0 = the 3-sigma rectangles of gs_bin */
+    int32_t tight_lists;
 } gs_options_t;
 
 /* Statistics of the last gs_register / gs_render call on a context. */

@@ -192,6 +192,8 @@ gs_status_t check_options(gs_ctx *ctx, const gs_options_t *o)
         return fail(ctx, GS_ERR_INVALID_ARG, "tracking_loss must be 0 or 1 and lambda_c in [0, 1]");
     if (o->tile_schedule < 0 || o->tile_schedule > 2)
         return fail(ctx, GS_ERR_INVALID_ARG, "tile_schedule must be 0 (autotune), 1 or 2");
+    if (o->tight_lists != 0 && o->tight_lists != 1)
+        return fail(ctx, GS_ERR_INVALID_ARG, "tight_lists must be 0 or 1");
     if ((o->exposure != 0 && o->exposure != 1) || !(o->lr_exposure >= 0) || !std::isfinite(o->lr_exposure) ||
         (o->exposure && o->tracking_loss))
         return fail(ctx, GS_ERR_INVALID_ARG,
@@ -385,7 +387,7 @@ int run_bin(const gsl::BinArgs &b, cudaStream_t s)
 }
 
 gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, const float *pose32,
-                              const gs_options_t *o)
+                              const gs_options_t *o, bool tight = false)
 {
     gsl::ProjectArgs a{};
     a.vps = D.vps;
@@ -400,6 +402,8 @@ gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, co
     a.aux = p.aux;
     a.counts = p.counts;
     a.flags = p.flags;
+    a.tight = tight && o->alpha_min > 0 && !o->smooth;
+    a.skip_below = skip_threshold(o);
     return a;
 }
 
@@ -456,10 +460,10 @@ gsl::RasterArgs raster_args(const Plan &P, const DevPlan &D, const Pipe &p, int 
 
 // project + count duplicates (synchronises) + size the sort + emit/sort/range
 gs_status_t project_and_bin(gs_ctx *ctx, const Plan &P, const DevPlan &D, Pipe &p, const float *pose32,
-                            const gs_options_t *o, cudaStream_t s, int *cur, uint32_t *n_dups_out)
+                            const gs_options_t *o, cudaStream_t s, int *cur, uint32_t *n_dups_out, bool tight = false)
 {
     GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
-    gsl::project(project_args(P, D, p, pose32, o), s);
+    gsl::project(project_args(P, D, p, pose32, o, tight), s);
     gsl::BinArgs b = bin_args(P, D, p);
     gsl::bin_count(b, s);
     uint32_t nd = 0;
@@ -667,6 +671,7 @@ void gs_default_options(gs_options_t *o)
     o->exposure = 0;
     o->lr_exposure = 0.1f;
     o->tile_schedule = 0;
+    o->tight_lists = 1;
     o->lr_final = 0.001f;
 }
 
@@ -1328,7 +1333,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         // count drifts as the poses move)
         int cur = 0;
         uint32_t nd = 0;
-        GS_TRY(project_and_bin(ctx, P, D, p, pose32, opt, s, &cur, &nd));
+        GS_TRY(project_and_bin(ctx, P, D, p, pose32, opt, s, &cur, &nd, opt->tight_lists != 0));
         const uint64_t want = (uint64_t)(headroom * nd) + 65536;
         if (p.cap < want)
             GS_TRY(alloc_sort(ctx, want, p));
@@ -1359,7 +1364,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         };
         auto iteration = [&](cudaStream_t st) {
             mark(0, st);
-            gsl::project(project_args(P, D, p, pose32, opt), st);
+            gsl::project(project_args(P, D, p, pose32, opt, opt->tight_lists != 0), st);
             mark(1, st);
             const int c = run_bin(b, st);
             if (ordered)
@@ -1495,7 +1500,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         // residual eps at the final poses, then Eq. 7
         r.tile_pairs = nullptr;
         r.tile_order = nullptr;
-        gsl::project(project_args(P, D, p, pose32, opt), s);
+        gsl::project(project_args(P, D, p, pose32, opt, opt->tight_lists != 0), s);
         r.vals = p.vals[run_bin(b, s)];
         gsl::forward(r, true, s);
         gsl::track_loss(ta, s);
@@ -1912,7 +1917,7 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     // size the duplicate lists at the current poses
     int cur = 0;
     uint32_t nd = 0;
-    GS_TRY(project_and_bin(ctx, P, D, p, srv->pose32, &srv->opt, s, &cur, &nd));
+    GS_TRY(project_and_bin(ctx, P, D, p, srv->pose32, &srv->opt, s, &cur, &nd, srv->opt.tight_lists != 0));
     const uint64_t want = (uint64_t)(srv->headroom * nd) + 65536;
     if (p.cap < want)
         GS_TRY(alloc_sort(ctx, want, p));
@@ -1931,7 +1936,7 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     gsl::TrackArgs ta;
     GS_TRY(alloc_track(ctx, P, D, r, ta, srv->tloss, s));
     GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    gsl::project(project_args(P, D, p, srv->pose32, &srv->opt), ctx->cap);
+    gsl::project(project_args(P, D, p, srv->pose32, &srv->opt, srv->opt.tight_lists != 0), ctx->cap);
     r.vals = p.vals[run_bin(b, ctx->cap)];
     gsl::forward(r, true, ctx->cap);
     gsl::track_loss(ta, ctx->cap);

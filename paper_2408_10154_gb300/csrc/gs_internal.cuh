@@ -180,6 +180,14 @@ struct ProjectArgs {
     float4 *aux;               // [records][2] auxiliary (may be null)
     int32_t *counts;
     int *flags;
+    // registration lists: shrink each rectangle to the tiles that meet the
+    // axis-aligned box of the record's alpha-threshold ellipse (exponent >=
+    // ln(alpha_min / o) - 0.06, box widened by 0.1 % + 0.01 px; nearly
+    // singular conics keep the 3-sigma rectangle).  The dropped (tile,
+    // record) pairs fail the alpha test at every pixel of the tile, so the
+    // compositing is unchanged; the lists are no longer those of gs_bin.
+    int tight;
+    float skip_below;         // ln(alpha_min) - 0.05
 };
 void project(const ProjectArgs &a, cudaStream_t s);
 

@@ -20,6 +20,40 @@ namespace {
 
 using namespace gsk;
 
+// The tiles of [x0, x1) x [y0, y1) whose pixel centres can reach the
+// record's alpha threshold (see ProjectArgs::tight): the ellipse
+// d^T Q d <= -2 tau, tau = ln(alpha_min / o) - 0.06, lies in the box of
+// half-sizes sqrt(-2 tau Sigma00), sqrt(-2 tau Sigma11) about (u, v); tile t
+// meets it when its centres [16 t + 0.5, 16 t + 15.5] meet the box.  An
+// opacity below alpha_min e^-0.06 empties the rectangle.
+__device__ __forceinline__ void tighten(float ca, float cb, float cc, float o, float u, float v, float skip_below,
+                                        int TX, int TY, int &x0, int &x1, int &y0, int &y1)
+{
+    const float A = -2.0f * ca, B = -cb, C = -2.0f * cc;
+    const float AC = A * C, BB = B * B;
+    const float tau = skip_below - 0.01f - __logf(o);
+    if (tau >= 0.0f) {
+        x1 = x0;
+        return;
+    }
+    const float det = AC - BB;
+    if (!(det > 0.0f) || !(BB <= 0.998f * AC))
+        return;
+    const float s = (-2.0f * tau) / det;
+    const float ex = fmaf(sqrtf(s * C), 1.001f, 0.01f), ey = fmaf(sqrtf(s * A), 1.001f, 0.01f);
+    if (!(ex >= 0.0f) || !(ey >= 0.0f))
+        return;
+    const float B16 = (float)kTile;
+    const float tx0 = fminf(fmaxf(ceilf((u - ex - 15.5f) / B16), 0.0f), (float)TX);
+    const float tx1 = fminf(fmaxf(floorf((u + ex - 0.5f) / B16) + 1.0f, 0.0f), (float)TX);
+    const float ty0 = fminf(fmaxf(ceilf((v - ey - 15.5f) / B16), 0.0f), (float)TY);
+    const float ty1 = fminf(fmaxf(floorf((v + ey - 0.5f) / B16) + 1.0f, 0.0f), (float)TY);
+    x0 = max(x0, (int)tx0);
+    x1 = min(x1, (int)tx1);
+    y0 = max(y0, (int)ty0);
+    y1 = min(y1, (int)ty1);
+}
+
 __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
 {
     // locate the group of this block (groups are few; linear scan)
@@ -151,6 +185,8 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
                         x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)TX);
                         y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)TY);
                         y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)TY);
+                        if (a.tight)
+                            tighten(ca, cb, cc, opa, u, vv, a.skip_below, TX, TY, x0, x1, y0, y1);
                     }
                     if (x0 < x1 && y0 < y1) {
                         count = (x1 - x0) * (y1 - y0);

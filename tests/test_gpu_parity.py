@@ -509,7 +509,8 @@ def test_transform_batch_equals_single_transforms(gs, ctx):
 
 def test_tile_schedules_give_identical_registrations(gs, ctx):
     # two full-size room keyframes (3225 tiles each): natural tile order,
-    # longest lists first, and the autotuner's pick give the same result
+    # longest lists first, the autotuner's pick, tight or 3-sigma tile lists
+    # give the same result
     c = synth.room_150k()
     og = O.Gaussians.from_dict(c["gaussians"])
     g = gs.Gaussians.from_numpy(c["gaussians"])
@@ -521,3 +522,15 @@ def test_tile_schedules_give_identical_registrations(gs, ctx):
     for o in out[1:]:
         np.testing.assert_array_equal(o[0], out[0][0])
         np.testing.assert_array_equal(o[2], out[0][2])
+    # the 3-sigma rectangles of gs_bin instead of the tight lists: the same
+    # contributors in the same order; only the adjoint's per-thread
+    # accumulation groups (records per chunk) differ, at the FP32 rounding level
+    import ctypes
+    st = gs.gsreg.gs_stats_t()
+    ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st)))
+    tight_dups = st.n_dups
+    loose = gs.gs_register(ctx, g, g, [], views, 10, gs.default_options(tile_schedule=1, tight_lists=0))
+    ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st)))
+    assert tight_dups < 0.9 * st.n_dups
+    np.testing.assert_allclose(loose[0], out[0][0], atol=1e-5)
+    np.testing.assert_allclose(loose[2], out[0][2], rtol=1e-5)
