@@ -85,7 +85,10 @@ __device__ __forceinline__ float exp_ct(float x)
     p = __fmaf_rn(p, r, 0.5f);
     p = __fmaf_rn(p, r, 1.0f);
     p = __fmaf_rn(p, r, 1.0f);
-    const int k = __float2int_rz(kf);
+    // k = kf exactly: t = 1.5 * 2^23 + k holds k in its low mantissa bits
+    // (|k| <= 116 here), so an integer difference of the bit patterns gives
+    // it without a float-to-int conversion
+    const int k = __float_as_int(t) - 0x4B400000;
     return __fmul_rn(p, __int_as_float((k + 127) << 23));
 }
 
