@@ -396,6 +396,23 @@ gs_status_t gs_overlap_ratio(gs_ctx_t *ctx, const gs_gaussians_t *p, const gs_ga
                              float tau, double *ratio, int64_t *n_corr, int32_t *nn_pq, int32_t *nn_qp,
                              gs_stream_t stream);
 
+/* --------------------------------------------------------------- utility */
+
+/* Stable sort of n (key, value) pairs by the low `bits` bits of the keys
+ * (device arrays, sorted in place): the one-sweep LSD radix sort of the
+ * tile lists (8-bit digits; one histogram pass, one look-back scatter per
+ * digit).  GS_ERR_TIMEOUT if a pass's bounded wait gave up (the device
+ * keeps answering; the arrays' contents are then unspecified).
+ * Synchronises `stream`. */
+gs_status_t gs_sort_u32(gs_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int bits, gs_stream_t stream);
+
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * sort pass over (keys, vals) whose first tile of 2048 keys is withheld, so
+ * that every later tile's look-back runs out of its spin limit (well under
+ * a second), sets the status word and returns.  Returns GS_ERR_TIMEOUT when
+ * the waits behave; the context stays usable. */
+gs_status_t gs_selftest_bounded_wait(gs_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, gs_stream_t stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Continuous-batching registration server.  A request is one registration

@@ -24,7 +24,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_COUNT
 };
 
 struct Buf {
@@ -1140,6 +1140,51 @@ gs_status_t gs_transform(gs_ctx_t *ctx, const gs_gaussians_t *g, const double *T
                    (float4 *)out_quats, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
+}
+
+gs_status_t sort_u32_impl(gs_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int bits, bool withhold,
+                          cudaStream_t s)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    if (n < 0 || n > 0xfff00000ll || bits < 0 || bits > 32 || (n > 0 && (!keys || !vals)))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_sort_u32: bad arguments");
+    if (n == 0 || bits == 0)
+        return GS_OK;
+    DeviceGuard dg(ctx->device);
+    const uint32_t cap = (uint32_t)n;
+    uint32_t *k2 = nullptr, *v2 = nullptr, *nd = nullptr;
+    uint8_t *os = nullptr;
+    int *flags = nullptr;
+    GS_TRY(wsT(ctx, S_SK, cap, &k2));
+    GS_TRY(wsT(ctx, S_SV, cap, &v2));
+    GS_TRY(wsT(ctx, S_SN, 2, &nd));
+    GS_TRY(wsT(ctx, S_OS, gsl::onesweep_scratch_bytes(cap, bits), &os));
+    GS_TRY(wsT(ctx, S_FLAGS, 4, &flags));
+    GS_CUDA(cudaMemcpyAsync(nd, &cap, sizeof cap, cudaMemcpyHostToDevice, s));
+    GS_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));
+    uint32_t *kk[2] = {keys, k2}, *vv[2] = {vals, v2};
+    const int cur = gsl::onesweep_u32(kk, vv, nd, cap, bits, os, flags, s, withhold);
+    if (cur != 0) {
+        GS_CUDA(cudaMemcpyAsync(keys, k2, sizeof(uint32_t) * cap, cudaMemcpyDeviceToDevice, s));
+        GS_CUDA(cudaMemcpyAsync(vals, v2, sizeof(uint32_t) * cap, cudaMemcpyDeviceToDevice, s));
+    }
+    int fl = 0;
+    GS_CUDA(cudaMemcpyAsync(&fl, flags, sizeof fl, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    if (fl & gsk::kFlagTimeout)
+        return fail(ctx, GS_ERR_TIMEOUT, "a sort pass gave up waiting for an earlier tile");
+    return GS_OK;
+}
+
+gs_status_t gs_sort_u32(gs_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int bits, gs_stream_t stream)
+{
+    return sort_u32_impl(ctx, keys, vals, n, bits, false, (cudaStream_t)stream);
+}
+
+gs_status_t gs_selftest_bounded_wait(gs_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, gs_stream_t stream)
+{
+    return sort_u32_impl(ctx, keys, vals, n, 8, true, (cudaStream_t)stream);
 }
 
 gs_status_t gs_transform_batch(gs_ctx_t *ctx, const gs_gaussians_t *maps, int n_maps, const double *T_host,

@@ -482,8 +482,15 @@ OsLayout os_layout(uint8_t *base, uint32_t tiles)
 
 // per-digit counts of every pass, over all live keys (grid-stride, warp-
 // aggregated shared atomics, one global atomic per block and digit)
+// digit mask of pass p over the low `bits` key bits (the last pass may be narrower)
+__host__ __device__ __forceinline__ uint32_t os_digit_mask(int bits, int p)
+{
+    const int left = bits - 8 * p;
+    return left >= 8 ? 0xffu : (1u << left) - 1u;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_os_hist(const uint32_t *keys, const uint32_t *n_dev, uint32_t cap,
-                                                          int passes, uint32_t *ghist)
+                                                          int passes, int bits, uint32_t *ghist)
 {
     __shared__ uint32_t h[kOsMaxPasses][256];
     for (int k = threadIdx.x; k < kOsMaxPasses * 256; k += blockDim.x)
@@ -496,7 +503,7 @@ __global__ void __launch_bounds__(kSortThreads) k_os_hist(const uint32_t *keys, 
         const bool valid = i < n;
         const uint32_t key = valid ? keys[i] : 0u;
         for (int p = 0; p < passes; ++p) {
-            const uint32_t d = valid ? (key >> (8 * p)) & 0xffu : 256u;
+            const uint32_t d = valid ? (key >> (8 * p)) & os_digit_mask(bits, p) : 256u;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             if (d < 256u && (uint32_t)(__ffs(peers) - 1) == lane)
                 atomicAdd(&h[p][d], (uint32_t)__popc(peers));
@@ -531,7 +538,8 @@ __device__ __forceinline__ unsigned long long os_load(const unsigned long long *
 // scatter to the digit's global base + that prefix + the local rank.
 __global__ void __launch_bounds__(kSortThreads) k_os_pass(const uint32_t *kin, const uint32_t *vin,
                                                           const uint32_t *n_dev, uint32_t cap, int shift,
-                                                          const uint32_t *gbase, unsigned long long *status,
+                                                          uint32_t dmask, const uint32_t *gbase,
+                                                          unsigned long long *status,
                                                           uint32_t *counter, uint32_t *kout, uint32_t *vout,
                                                           int *flags)
 {
@@ -557,7 +565,7 @@ __global__ void __launch_bounds__(kSortThreads) k_os_pass(const uint32_t *kin, c
         const bool valid = i < n;
         key[r] = valid ? kin[i] : 0u;
         val[r] = valid ? vin[i] : 0u;
-        const uint32_t d = valid ? (key[r] >> shift) & 0xffu : 256u;
+        const uint32_t d = valid ? (key[r] >> shift) & dmask : 256u;
         dig[r] = d;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t rank = __popc(peers & lt);
@@ -732,7 +740,7 @@ size_t onesweep_scratch_bytes(uint32_t cap, int bits)
 }
 
 int onesweep_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits,
-                 uint8_t *scratch, int *flags, cudaStream_t s)
+                 uint8_t *scratch, int *flags, cudaStream_t s, bool withhold_first_tile)
 {
     const int passes = (bits + 7) / 8;
     if (passes <= 0)
@@ -742,13 +750,20 @@ int onesweep_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, ui
     // clear the ids, histograms and the status words of the passes used
     cudaMemsetAsync(scratch, 0, (size_t)((uint8_t *)L.status - scratch) + sizeof(unsigned long long) * 256 *
                                     (size_t)tiles * passes, s);
+    if (withhold_first_tile) {
+        // self-test of the bounded wait: tile ids of the first pass start at
+        // 1, so tile 0 never publishes and every later tile gives up
+        static const uint32_t one = 1;
+        cudaMemcpyAsync(L.counters, &one, sizeof one, cudaMemcpyHostToDevice, s);
+    }
     const uint32_t hb = std::min<uint32_t>(tiles, 4 * 152);
-    k_os_hist<<<hb, kSortThreads, 0, s>>>(keys[0], n_dev, cap, passes, L.ghist);
+    k_os_hist<<<hb, kSortThreads, 0, s>>>(keys[0], n_dev, cap, passes, bits, L.ghist);
     k_os_scan<<<1, 256, 0, s>>>(L.ghist, passes, L.gbase);
     g_launches += 2;
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
-        k_os_pass<<<tiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], n_dev, cap, 8 * p, L.gbase + 256 * p,
+        k_os_pass<<<tiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], n_dev, cap, 8 * p, os_digit_mask(bits, p),
+                                                 L.gbase + 256 * p,
                                                  L.status + (size_t)p * tiles * 256, L.counters + p,
                                                  keys[cur ^ 1], vals[cur ^ 1], flags);
         ++g_launches;

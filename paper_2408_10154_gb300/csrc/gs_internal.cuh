@@ -242,7 +242,7 @@ void tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t
 // order as radix_sort.  Returns the buffer index holding the result.
 size_t onesweep_scratch_bytes(uint32_t cap, int bits);
 int onesweep_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits,
-                 uint8_t *scratch, int *flags, cudaStream_t s);
+                 uint8_t *scratch, int *flags, cudaStream_t s, bool withhold_first_tile = false);
 // 64-bit keys (tile << 32 | depth bits) of a bin2 result
 void keys64(const BinArgs &a, int cur, uint64_t *out, cudaStream_t s);
 void bin_count(const BinArgs &a, cudaStream_t s);  // scan only: n_dups

@@ -72,7 +72,7 @@ class gs_gaussian_grads_t(ctypes.Structure):
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
            "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc", "gs_track_loss",
-           "gs_overlap_ratio", "gs_transform_batch",
+           "gs_overlap_ratio", "gs_transform_batch", "gs_sort_u32", "gs_selftest_bounded_wait",
            "gs_server_create",
            "gs_server_destroy", "gs_server_last_error", "gs_server_submit", "gs_server_step", "gs_server_poll",
            "gs_server_counts"]
@@ -114,6 +114,8 @@ def load(build_if_missing: bool = False):
             "gs_track_loss": ([P, P, I, P, P, P, P, P, ctypes.c_float, P, P, P, P, P, P], I),
             "gs_overlap_ratio": ([P, P, P, P, ctypes.c_float, P, P, P, P, P], I),
             "gs_transform_batch": ([P, P, I, P, P, P, P], I),
+            "gs_sort_u32": ([P, P, P, I64, I, P], I),
+            "gs_selftest_bounded_wait": ([P, P, P, I64, P], I),
             "gs_pose_step": ([P, I, P, P, P, P, I, I, P, P], I),
             "gs_fuse": ([P, I, P, P, P, P, P, P], I),
             "gs_register": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P], I),
@@ -423,6 +425,13 @@ def gs_transform(ctx: Context, g: Gaussians, T) -> Gaussians:
     ctx.check(ctx._lib.gs_transform(ctx.handle, ctypes.byref(gst), Th.ctypes.data_as(ctypes.c_void_p), _ptr(m),
                                     _ptr(q), _stream()))
     return Gaussians(m, g.log_scales4.clone(), q, g.logits.clone(), g.rgb4.clone())
+
+
+def gs_sort_u32(ctx: Context, keys, vals, bits=32):
+    """Stable device sort of (keys, vals) (32-bit CUDA tensors, in place) by
+    the low ``bits`` key bits."""
+    ctx.check(ctx._lib.gs_sort_u32(ctx.handle, _ptr(keys), _ptr(vals), int(keys.numel()), int(bits), _stream()))
+    return keys, vals
 
 
 def gs_transform_batch(ctx: Context, maps, Ts):
