@@ -24,7 +24,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_COUNT
 };
 
 struct Buf {
@@ -1076,7 +1076,78 @@ gs_status_t gs_overlap_ratio(gs_ctx_t *ctx, const gs_gaussians_t *p, const gs_ga
     GS_TRY(wsT(ctx, S_OD2, std::max<size_t>(np, 1), &a.d2));
     GS_TRY(wsT(ctx, S_OCNT, 2, &a.counts));
     a.tau2 = tau * tau;
-    gsl::overlap(a, s);
+    if (np < 64 || nq < 64) {
+        gsl::overlap(a, s);  // brute force
+    } else {
+        // uniform grid over the box of both point sets (read back once)
+        uint32_t *bbox = nullptr;
+        GS_TRY(wsT(ctx, S_OBOX, 6, &bbox));
+        gsl::overlap_moved_bbox(a, bbox, s);
+        uint32_t mm[6];
+        GS_CUDA(cudaMemcpyAsync(mm, bbox, sizeof mm, cudaMemcpyDeviceToHost, s));
+        GS_CUDA(cudaStreamSynchronize(s));
+        auto o2f = [](uint32_t u) {
+            const uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+            float f;
+            std::memcpy(&f, &b, sizeof f);
+            return (double)f;
+        };
+        double lo[3], ext[3], emax = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = o2f(mm[k]);
+            ext[k] = o2f(mm[3 + k]) - lo[k];
+            if (!std::isfinite(lo[k]) || !std::isfinite(ext[k]))
+                return fail(ctx, GS_ERR_NONFINITE, "gs_overlap_ratio: non-finite mean");
+            emax = std::max(emax, ext[k]);
+        }
+        const double pad = 1e-3 * emax + 1e-6;
+        double vol = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            lo[k] -= pad;
+            ext[k] = std::max(ext[k] + 2.0 * pad, 1e-3 * emax + 1e-6);
+            vol *= ext[k];
+        }
+        // about two cells per target, at most 2^22 cells and 2048 per axis
+        double cell = std::cbrt(vol / (2.0 * (double)std::max(np, nq)));
+        cell = std::max(cell, (emax + 2.0 * pad) / 2048.0);
+        int dims[3];
+        for (;;) {
+            size_t cells = 1;
+            for (int k = 0; k < 3; ++k) {
+                dims[k] = std::max(1, (int)std::ceil(ext[k] / cell));
+                cells *= (size_t)dims[k];
+            }
+            if (cells <= ((size_t)1 << 22))
+                break;
+            cell *= 1.26;
+        }
+        gsl::NNGrid g{};
+        g.ox = (float)lo[0];
+        g.oy = (float)lo[1];
+        g.oz = (float)lo[2];
+        g.s = (float)cell;
+        g.inv_s = 1.0f / g.s;
+        g.nx = dims[0];
+        g.ny = dims[1];
+        g.nz = dims[2];
+        double amax = 0.0;  // largest coordinate magnitude in the box
+        for (int k = 0; k < 3; ++k)
+            amax = std::max(amax, std::max(std::fabs(lo[k]), std::fabs(lo[k] + ext[k])));
+        g.margin = (float)(4e-6 * (emax + amax) + 1e-7);
+        const size_t cells = (size_t)dims[0] * dims[1] * dims[2], nmax = std::max(np, nq);
+        gsl::NNScratch sc{};
+        GS_TRY(wsT(ctx, S_GCELL, nmax, &sc.cell));
+        GS_TRY(wsT(ctx, S_GSTART, cells + 1, &sc.start));
+        GS_TRY(wsT(ctx, S_GCUR, cells, &sc.cursor));
+        GS_TRY(wsT(ctx, S_GPART, gsl::scan_partials(cells + 1), &sc.partials));
+        GS_TRY(wsT(ctx, S_GPTS, nmax, &sc.spts));
+        GS_TRY(wsT(ctx, S_GIDX, nmax, &sc.sidx));
+        GS_TRY(wsT(ctx, S_GLIST, nmax, &sc.list));
+        GS_TRY(wsT(ctx, S_GNL, 1, &sc.n_list));
+        gsl::nn_grid(a.pt, (int)np, a.q, (int)nq, g, sc, a.nn_pq, a.d2, s);
+        gsl::nn_grid(a.q, (int)nq, a.pt, (int)np, g, sc, a.nn_qp, nullptr, s);
+        gsl::overlap_count(a, s);
+    }
     unsigned long long c[2] = {0, 0};
     GS_CUDA(cudaMemcpyAsync(c, a.counts, sizeof c, cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));

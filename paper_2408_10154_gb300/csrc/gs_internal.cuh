@@ -340,6 +340,35 @@ struct OverlapArgs {
 };
 void overlap(const OverlapArgs &a, cudaStream_t s);
 
+// Uniform grid for exact nearest-neighbour search: cell of x is
+// floor((x - o) * inv_s) per axis (FP32, clamped to the grid), cells
+// numbered x-fastest.  margin bounds how far a cell boundary computed this
+// way can sit from o + k s (FP32 rounding of coordinates within the box).
+struct NNGrid {
+    float ox, oy, oz, s, inv_s, margin;
+    int nx, ny, nz;
+};
+// Scratch of one grid search (targets nt, queries na):
+//   cell [nt], start [cells + 1], cursor [cells], spts [nt], sidx [nt],
+//   list [na], n_list [1]
+struct NNScratch {
+    uint32_t *cell, *start, *cursor, *partials;
+    float4 *spts;
+    int32_t *sidx, *list;
+    uint32_t *n_list;
+};
+// moved means pt = T p and the bounding box of pt and q as ordered-int
+// min x, y, z, max x, y, z in bbox[6]
+void overlap_moved_bbox(const OverlapArgs &a, uint32_t *bbox, cudaStream_t s);
+// exact nearest neighbour in targets B of every query in A (FP32 squared
+// distance, ties to the smaller index): a grid search that stops once no
+// unsearched cell can hold a nearer target, and the brute-force sweep for
+// the queries whose search would run past kNNMaxRing rings
+void nn_grid(const float4 *A, int na, const float4 *B, int nb, const NNGrid &g, const NNScratch &sc, int32_t *nn,
+             float *d2, cudaStream_t s);
+// |K| and the pairs within tau from the nearest neighbours both ways
+void overlap_count(const OverlapArgs &a, cudaStream_t s);
+
 struct PoseArgs {
     const gsk::VpDesc *vps;
     int n_vps;

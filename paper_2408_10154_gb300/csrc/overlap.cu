@@ -9,9 +9,22 @@
 // k_nn is a brute-force sweep: targets staged through shared memory 2048 at
 // a time (one broadcast load per target per warp), four queries per thread;
 // FP32-ALU bound at ~9 operations per (query, target) pair.
+//
+// k_nn_grid searches a uniform grid over the targets instead: each query
+// scans the shells of cells at Chebyshev distance r = 0, 1, 2, ... around
+// its cell and stops after shell r once its best squared distance is below
+// (r s - margin)^2 (1 - 1e-6): a target outside the searched block lies at
+// least r s - margin away (cell boundaries are computed in FP32 within the
+// box), and its FP32 squared distance exceeds the best, so the result is
+// the brute-force argmin.  Queries that would need more than kNNMaxRing
+// shells go to the brute-force sweep.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace {
+
+constexpr int kNNMaxRing = 6;
 
 constexpr int kNNThreads = 256;
 constexpr int kNNQ = 4;        // queries per thread
@@ -77,6 +90,180 @@ __global__ void __launch_bounds__(kNNThreads) k_nn(const float4 *A, int na, cons
     }
 }
 
+// brute-force nearest neighbours of the queries listed in list[0 .. *n_list)
+__global__ void __launch_bounds__(kNNThreads) k_nn_list(const float4 *A, const int32_t *list,
+                                                        const uint32_t *n_list, const float4 *B, int nb, int32_t *nn,
+                                                        float *d2)
+{
+    __shared__ float4 sb[kNNChunk];
+    const uint32_t nl = *n_list;
+    const uint32_t base = blockIdx.x * kNNThreads * kNNQ;
+    if (base >= nl)
+        return;
+    float ax[kNNQ], ay[kNNQ], az[kNNQ], best[kNNQ];
+    int bi[kNNQ];
+#pragma unroll
+    for (int q = 0; q < kNNQ; ++q) {
+        const uint32_t i = base + q * kNNThreads + threadIdx.x;
+        const float4 a = i < nl ? A[list[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ax[q] = a.x;
+        ay[q] = a.y;
+        az[q] = a.z;
+        best[q] = __int_as_float(0x7f800000);
+        bi[q] = -1;
+    }
+    for (int c0 = 0; c0 < nb; c0 += kNNChunk) {
+        const int cnt = min(kNNChunk, nb - c0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNNThreads)
+            sb[k] = B[c0 + k];
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const float4 b = sb[j];
+#pragma unroll
+            for (int q = 0; q < kNNQ; ++q) {
+                const float dx = __fsub_rn(b.x, ax[q]), dy = __fsub_rn(b.y, ay[q]), dz = __fsub_rn(b.z, az[q]);
+                const float d = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                if (d < best[q]) {
+                    best[q] = d;
+                    bi[q] = c0 + j;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kNNQ; ++q) {
+        const uint32_t i = base + q * kNNThreads + threadIdx.x;
+        if (i < nl) {
+            nn[list[i]] = bi[q];
+            if (d2)
+                d2[list[i]] = best[q];
+        }
+    }
+}
+
+// float <-> order-preserving uint (for atomic min / max of floats)
+__device__ __forceinline__ uint32_t f2o(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__global__ void k_bbox(const float4 *a, int na, const float4 *b, int nb, uint32_t *mm)
+{
+    uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += gridDim.x * blockDim.x) {
+        const float4 v = i < na ? a[i] : b[i - na];
+        const uint32_t c[3] = {f2o(v.x), f2o(v.y), f2o(v.z)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = min(lo[k], c[k]);
+            hi[k] = max(hi[k], c[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
+        hi[k] = __reduce_max_sync(0xffffffffu, hi[k]);
+    }
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&mm[k], lo[k]);
+            atomicMax(&mm[3 + k], hi[k]);
+        }
+}
+
+__device__ __forceinline__ int cell_axis(float x, float o, float inv_s, int n)
+{
+    const float t = floorf(__fmul_rn(__fsub_rn(x, o), inv_s));
+    return (int)fminf(fmaxf(t, 0.0f), (float)(n - 1));
+}
+
+__global__ void k_cell_count(const float4 *pts, int n, const gsl::NNGrid g, uint32_t *cell, uint32_t *cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const float4 p = pts[i];
+    const uint32_t c = (uint32_t)cell_axis(p.x, g.ox, g.inv_s, g.nx) +
+                       (uint32_t)g.nx * ((uint32_t)cell_axis(p.y, g.oy, g.inv_s, g.ny) +
+                                         (uint32_t)g.ny * (uint32_t)cell_axis(p.z, g.oz, g.inv_s, g.nz));
+    cell[i] = c;
+    atomicAdd(&cnt[c], 1u);
+}
+
+// targets bucketed by cell (order within a cell arbitrary: ties are broken by index)
+__global__ void k_cell_scatter(const float4 *pts, int n, const uint32_t *cell, uint32_t *cursor, float4 *spts,
+                               int32_t *sidx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const uint32_t pos = atomicAdd(&cursor[cell[i]], 1u);
+    spts[pos] = pts[i];
+    sidx[pos] = i;
+}
+
+__global__ void __launch_bounds__(256) k_nn_grid(const float4 *A, int na, const gsl::NNGrid g, const uint32_t *start,
+                                                 const float4 *spts, const int32_t *sidx, int32_t *nn, float *d2,
+                                                 int32_t *list, uint32_t *n_list)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na)
+        return;
+    const float4 a = A[i];
+    const int cx = cell_axis(a.x, g.ox, g.inv_s, g.nx), cy = cell_axis(a.y, g.oy, g.inv_s, g.ny),
+              cz = cell_axis(a.z, g.oz, g.inv_s, g.nz);
+    float best = __int_as_float(0x7f800000);
+    int bi = -1;
+    auto scan_cell = [&](int x, int y, int z) {
+        const uint32_t c = (uint32_t)x + (uint32_t)g.nx * ((uint32_t)y + (uint32_t)g.ny * (uint32_t)z);
+        for (uint32_t j = start[c]; j < start[c + 1]; ++j) {
+            const float4 b = spts[j];
+            const float dx = __fsub_rn(b.x, a.x), dy = __fsub_rn(b.y, a.y), dz = __fsub_rn(b.z, a.z);
+            const float d = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+            const int idx = sidx[j];
+            if (d < best || (d == best && idx < bi)) {
+                best = d;
+                bi = idx;
+            }
+        }
+    };
+    for (int r = 0;; ++r) {
+        // the shell of cells at Chebyshev distance r (clipped to the grid)
+        for (int dz = -r; dz <= r; ++dz) {
+            const int z = cz + dz;
+            if (z < 0 || z >= g.nz)
+                continue;
+            const bool zface = (dz == -r || dz == r);
+            for (int dy = -r; dy <= r; ++dy) {
+                const int y = cy + dy;
+                if (y < 0 || y >= g.ny)
+                    continue;
+                const bool face = zface || dy == -r || dy == r;
+                const int step = face ? 1 : 2 * r;  // inside the shell only dx = -r and +r
+                for (int dx = -r; dx <= r; dx += (step > 0 ? step : 1)) {
+                    const int x = cx + dx;
+                    if (x >= 0 && x < g.nx)
+                        scan_cell(x, y, z);
+                }
+            }
+        }
+        const bool covered = cx - r <= 0 && cx + r >= g.nx - 1 && cy - r <= 0 && cy + r >= g.ny - 1 &&
+                             cz - r <= 0 && cz + r >= g.nz - 1;
+        const float lb = (float)r * g.s - g.margin;
+        if (covered || (lb > 0.0f && best < lb * lb * (1.0f - 1e-6f)))
+            break;
+        if (r >= kNNMaxRing) {
+            list[atomicAdd(n_list, 1u)] = i;  // far from every target: the brute-force sweep
+            return;
+        }
+    }
+    nn[i] = bi;
+    if (d2)
+        d2[i] = best;
+}
+
 // |K| and the pairs of K within tau (counts[0], counts[1])
 __global__ void k_reciprocal(const int32_t *nn_pq, const float *d2, int np, const int32_t *nn_qp, float tau2,
                              unsigned long long *counts)
@@ -116,6 +303,52 @@ inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1)
 }  // namespace
 
 namespace gsl {
+
+void overlap_moved_bbox(const OverlapArgs &a, uint32_t *bbox, cudaStream_t s)
+{
+    static const uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+    cudaMemcpyAsync(bbox, init, sizeof init, cudaMemcpyHostToDevice, s);
+    if (a.np > 0) {
+        k_rigid32<<<div_up(a.np, 256), 256, 0, s>>>(a.p, a.np, a.T32, a.pt);
+        ++g_launches;
+    }
+    if (a.np + a.nq > 0) {
+        k_bbox<<<std::min<unsigned>(div_up(a.np + a.nq, 256), 1216), 256, 0, s>>>(a.pt, a.np, a.q, a.nq, bbox);
+        ++g_launches;
+    }
+}
+
+void nn_grid(const float4 *A, int na, const float4 *B, int nb, const NNGrid &g, const NNScratch &sc, int32_t *nn,
+             float *d2, cudaStream_t s)
+{
+    if (na <= 0)
+        return;
+    const size_t cells = (size_t)g.nx * g.ny * g.nz;
+    cudaMemsetAsync(sc.start, 0, sizeof(uint32_t) * (cells + 1), s);
+    cudaMemsetAsync(sc.n_list, 0, sizeof(uint32_t), s);
+    if (nb > 0) {
+        k_cell_count<<<div_up(nb, 256), 256, 0, s>>>(B, nb, g, sc.cell, sc.start);
+        ++g_launches;
+    }
+    scan_excl(sc.start, sc.start, cells + 1, sc.partials, nullptr, s);
+    cudaMemcpyAsync(sc.cursor, sc.start, sizeof(uint32_t) * cells, cudaMemcpyDeviceToDevice, s);
+    if (nb > 0) {
+        k_cell_scatter<<<div_up(nb, 256), 256, 0, s>>>(B, nb, sc.cell, sc.cursor, sc.spts, sc.sidx);
+        ++g_launches;
+    }
+    k_nn_grid<<<div_up(na, 256), 256, 0, s>>>(A, na, g, sc.start, sc.spts, sc.sidx, nn, d2, sc.list, sc.n_list);
+    k_nn_list<<<div_up(na, kNNThreads * kNNQ), kNNThreads, 0, s>>>(A, sc.list, sc.n_list, B, nb, nn, d2);
+    g_launches += 2;
+}
+
+void overlap_count(const OverlapArgs &a, cudaStream_t s)
+{
+    cudaMemsetAsync(a.counts, 0, 2 * sizeof(unsigned long long), s);
+    if (a.np > 0) {
+        k_reciprocal<<<div_up(a.np, 256), 256, 0, s>>>(a.nn_pq, a.d2, a.np, a.nn_qp, a.tau2, a.counts);
+        ++g_launches;
+    }
+}
 
 void overlap(const OverlapArgs &a, cudaStream_t s)
 {

@@ -94,3 +94,20 @@ def test_overlap_room_full_size_sampled(gs, ctx):
     recip = gqp[gpq] == np.arange(g.n)
     assert k == int(recip.sum())
     assert 0.5 < r <= 1.0
+
+
+def test_overlap_grid_with_far_outliers(gs, ctx):
+    # a dense cluster plus a few points tens of metres away: the grid's cells
+    # grow with the box, the cluster's queries stop after a shell or two and
+    # the far ones run past the shell limit into the brute-force sweep
+    rng = np.random.default_rng(12)
+
+    def pts(a):
+        a = np.asarray(a, np.float32)
+        return O.Gaussians(np.concatenate([a, np.zeros((len(a), 1), np.float32)], 1), np.zeros((len(a), 4)),
+                           np.tile([1.0, 0, 0, 0], (len(a), 1)), np.zeros(len(a)), np.zeros((len(a), 4)))
+
+    x = np.concatenate([rng.uniform(-0.5, 0.5, (3000, 3)), rng.uniform(40, 80, (20, 3))])
+    y = np.concatenate([rng.uniform(-0.5, 0.5, (2500, 3)), rng.uniform(-80, -40, (10, 3))])
+    r, k = check(gs, ctx, pts(x), pts(y), synth.random_rigid(rng, 5.0, 0.05), tau=0.05)
+    assert 0.0 < r < 1.0 and k > 100
