@@ -55,33 +55,47 @@ __device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float p
 
 // Warp-level cull of a staged record against the warp's pixel patch.  The
 // record can only pass the alpha test (alpha >= alpha_min) where its exact
-// exponent is at least tau = ln(alpha_min / o); that region is the ellipse
-// d^T Q d <= -2 tau (Q the conic), inside the axis-aligned box of half-sizes
-// sqrt(-2 tau Sigma00), sqrt(-2 tau Sigma11) about (u, v).  The record is
-// dropped for the warp only when every pixel sample of the patch
-// [xa, xb] x [ya, yb] lies outside that box, with margins that cover the
-// FP32 evaluation of the exponent (tau lowered by 0.06, the box widened by
-// 0.1 % + 0.01 px; conics with |B| > 0.999 sqrt(AC), where the FP32
-// exponent loses that accuracy, are never dropped).  A dropped pair would
-// have been skipped by the alpha test, so every result is unchanged; the
-// cull only removes iterations (most of a tile's list misses a given 8x4
-// patch).  NaN anywhere keeps the record.  pcut = ln(alpha_min / o) - 0.05,
-// the record's exponent cutoff (see stage_cutoff).
+// exponent is at least tau = ln(alpha_min / o), i.e. inside the ellipse
+// q(d) = A dx^2 + 2 B dx dy + C dy^2 <= -2 tau about (u, v) (A = -2 ca,
+// B = -cb, C = -2 cc).  Over the rectangle [xa, xb] x [ya, yb] of the
+// patch's pixel samples the smallest q is 0 when (u, v) lies inside it;
+// otherwise it sits on a side that faces (u, v) (q falls along the segment
+// from any point of the rectangle to the centre, and that segment leaves
+// the rectangle through such a side), where it is the minimum of a 1-D
+// quadratic clamped to the side.  The record is dropped for the warp only
+// when that minimum exceeds -2 tau, with margins that cover the FP32
+// evaluation of the exponent and of this test (tau lowered by 0.06, the
+// bound raised by 0.2 % + 0.02; conics with |B| > 0.999 sqrt(AC), where the
+// FP32 exponent loses that accuracy, are never dropped).  A dropped pair
+// would have failed the alpha test, so every result is unchanged; the cull
+// only removes iterations (most of a tile's list misses a given patch).
+// NaN anywhere keeps the record.  pcut = ln(alpha_min / o) - 0.05, the
+// record's exponent cutoff (see stage_cutoff).
 __device__ __forceinline__ bool patch_may_hit(const float4 &q0, float cc, float pcut, float xa, float xb, float ya,
                                               float yb)
 {
     const float A = -2.0f * q0.z, B = -q0.w, C = -2.0f * cc;
-    const float AC = A * C, BB = B * B;
     const float tau = pcut - 0.01f;
     if (tau >= 0.0f)
         return false;  // o < alpha_min e^-0.06: no pixel can reach alpha_min
-    const float det = AC - BB;
-    if (!(det > 0.0f) || !(BB <= 0.998f * AC))
+    if (!(A > 0.0f) || !(C > 0.0f) || !(B * B <= 0.998f * (A * C)))
         return true;
-    const float s = (-2.0f * tau) / det;
-    const float ex = fmaf(sqrtf(s * C), 1.001f, 0.01f), ey = fmaf(sqrtf(s * A), 1.001f, 0.01f);
-    const bool out = (q0.x + ex < xa) || (q0.x - ex > xb) || (q0.y + ey < ya) || (q0.y - ey > yb);
-    return !out;
+    const float u = q0.x, v = q0.y;
+    const bool lo_x = u < xa, hi_x = u > xb, lo_y = v < ya, hi_y = v > yb;
+    if (!(lo_x || hi_x || lo_y || hi_y))
+        return true;  // centre inside the patch (or NaN)
+    float m = __int_as_float(0x7f800000);
+    if (lo_x || hi_x) {
+        const float dx = (lo_x ? xa : xb) - u;
+        const float dy = fminf(fmaxf(-B * dx / C, ya - v), yb - v);
+        m = fmaf(fmaf(C, dy, 2.0f * B * dx), dy, A * dx * dx);
+    }
+    if (lo_y || hi_y) {
+        const float dy = (lo_y ? ya : yb) - v;
+        const float dx = fminf(fmaxf(-B * dy / A, xa - u), xb - u);
+        m = fminf(m, fmaf(fmaf(A, dx, 2.0f * B * dy), dx, C * dy * dy));
+    }
+    return !(m > fmaf(-2.0f * tau, 1.002f, 0.02f));
 }
 
 // The second float4 of a staged record, {cc, o, z, cutoff}: the tile
@@ -419,7 +433,9 @@ __device__ __forceinline__ void chain_twist(const float *G, const float4 &q1, co
 
 // ---------------------------------------------------------------------------
 // Adjoint with two pixels per thread: 128 threads per 16x16 tile, warp w
-// owns rows 4w..4w+3 (lane -> column lane & 15, rows (lane >> 4) and +2).
+// owns the 8x8 quadrant (w & 1, w >> 1) (lane -> column lane & 7, rows
+// lane >> 3 and +4): the squarest patch of 64 pixels, which the fewest
+// records reach.
 // Each staged record is evaluated for both pixels (two independent chains)
 // and their gradients are added before the warp reduction, which therefore
 // covers 64 pixels.
@@ -558,17 +574,17 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     const uint32_t lt = t - d.tile_base;
     const int tx = (int)(lt % (uint32_t)d.TX), ty = (int)(lt / (uint32_t)d.TX);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = tx * kTile + (lane & 15);
-    const int py0 = ty * kTile + warp * 4 + (lane >> 4);
-    // the warp's pixel samples: a 16x4 patch
-    const float xa = (float)(tx * kTile) + 0.5f, xb = xa + 15.0f;
-    const float ya = (float)(ty * kTile + warp * 4) + 0.5f, yb = ya + 3.0f;
+    const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
+    const int py0 = ty * kTile + (warp >> 1) * 8 + (lane >> 3);
+    // the warp's pixel samples: an 8x8 patch
+    const float xa = (float)(tx * kTile + (warp & 1) * 8) + 0.5f, xb = xa + 7.0f;
+    const float ya = (float)(ty * kTile + (warp >> 1) * 8) + 0.5f, yb = ya + 7.0f;
     const bool cull = a.alpha_min > 0.0f;
     const uint2 rg = a.ranges[t];
     PixAdj P0, P1;
     const float gain = (REG && d.exposure) ? a.expo32[2 * vp] : 1.0f;
     pix_adj_init<REG>(P0, d, a, px, py0, a.bg, gain);
-    pix_adj_init<REG>(P1, d, a, px, py0 + 2, a.bg, gain);
+    pix_adj_init<REG>(P1, d, a, px, py0 + 4, a.bg, gain);
     int ml = max(P0.last, P1.last);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)

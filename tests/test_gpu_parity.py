@@ -523,14 +523,21 @@ def test_tile_schedules_give_identical_registrations(gs, ctx):
         np.testing.assert_array_equal(o[0], out[0][0])
         np.testing.assert_array_equal(o[2], out[0][2])
     # the 3-sigma rectangles of gs_bin instead of the tight lists: the same
-    # contributors in the same order; only the adjoint's per-thread
-    # accumulation groups (records per chunk) differ, at the FP32 rounding level
+    # contributors in the same order, so the compositing (the residuals at
+    # the initial pose) is bit-equal.  The adjoint's accumulation groups
+    # (records per staged chunk) differ at the FP32 rounding level, and
+    # Adam's normalised steps carry that into the poses where a twist
+    # component's gradient is small against its history: after 10 iterations
+    # the poses agree to 1e-4 (0.006 deg, 0.1 mm)
     import ctypes
     st = gs.gsreg.gs_stats_t()
     ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st)))
     tight_dups = st.n_dups
+    e_tight = gs.gs_register(ctx, g, g, [], views, 0, gs.default_options(tile_schedule=1))[2]
+    e_loose = gs.gs_register(ctx, g, g, [], views, 0, gs.default_options(tile_schedule=1, tight_lists=0))[2]
+    np.testing.assert_array_equal(e_loose, e_tight)
     loose = gs.gs_register(ctx, g, g, [], views, 10, gs.default_options(tile_schedule=1, tight_lists=0))
     ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st)))
     assert tight_dups < 0.9 * st.n_dups
-    np.testing.assert_allclose(loose[0], out[0][0], atol=1e-5)
-    np.testing.assert_allclose(loose[2], out[0][2], rtol=1e-5)
+    np.testing.assert_allclose(loose[0], out[0][0], atol=1e-4)
+    np.testing.assert_allclose(loose[2], out[0][2], rtol=1e-4)
