@@ -24,7 +24,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_SEGZ, S_SEGCUR, S_SEGBIG, S_COUNT
 };
 
 struct Buf {
@@ -207,7 +207,7 @@ struct Plan {
     std::vector<GroupDesc> groups;
     std::vector<uint32_t> tile_vp;
     std::vector<int> set_vp;  // a vp of each Gaussian set
-    uint64_t n_records = 0, n_tiles = 0;
+    uint64_t n_records = 0, n_tiles = 0, n_diff = 0;
     int64_t n_pix = 0;
     uint32_t proj_blocks = 0;
 };
@@ -233,6 +233,7 @@ void add_vp(Plan &P, const gs_gaussians_t *g, const gs_camera_t &c, int set, int
     std::memcpy(d.w2c, c.world_to_cam, sizeof d.w2c);
     d.rec_base = (uint32_t)P.n_records;
     d.tile_base = (uint32_t)P.n_tiles;
+    d.diff_base = (uint32_t)P.n_diff;
     d.pix_base = P.n_pix;
     d.t_rgb = trgb;
     d.t_depth = tdepth;
@@ -244,6 +245,7 @@ void add_vp(Plan &P, const gs_gaussians_t *g, const gs_camera_t &c, int set, int
         P.tile_vp.push_back((uint32_t)vp);
     P.n_records += (uint64_t)d.n;
     P.n_tiles += (uint64_t)d.TX * d.TY;
+    P.n_diff += (uint64_t)(d.TX + 1) * (d.TY + 1);
     P.n_pix += (int64_t)c.width * c.height;
     if ((int)P.set_vp.size() <= set)
         P.set_vp.resize(set + 1, vp);
@@ -253,7 +255,7 @@ void add_vp(Plan &P, const gs_gaussians_t *g, const gs_camera_t &c, int set, int
 // groups: runs of consecutive vps that share a Gaussian set, <= kMaxVpPerGroup
 gs_status_t finalize(gs_ctx *ctx, Plan &P)
 {
-    if (P.n_records >= 0xffffffffull || P.n_tiles >= 0xffffffffull)
+    if (P.n_records >= 0xffffffffull || P.n_tiles >= 0xffffffffull || P.n_diff >= 0xffffffffull)
         return fail(ctx, GS_ERR_INVALID_ARG, "too many records or tiles for 32-bit indices");
     P.groups.clear();
     uint32_t blocks = 0;
@@ -320,20 +322,40 @@ struct Pipe {
     uint2 *ranges = nullptr;
     int *flags = nullptr;
     uint32_t cap = 0;
-    // two-stage binning
+    // two-stage binning (gs_bin)
     uint32_t *dkeys[2] = {nullptr, nullptr}, *dvals[2] = {nullptr, nullptr};
     uint32_t *tkeys[2] = {nullptr, nullptr};
     uint32_t *n_vis = nullptr;
     uint64_t n_records = 0;
     uint8_t *os = nullptr;  // one-sweep sort state
+    // segmented build
+    unsigned long long *seg_hdr = nullptr;
+    uint32_t *seg_diff = nullptr, *seg_cursor = nullptr, *seg_big = nullptr;
+    size_t seg_zero = 0;
 };
 
-// Binning route of the context-based entry points: the two-stage route
-// (depth sort of the visible records, then a tile sort of 32-bit keys)
-// moves about a quarter of the bytes of one sort of 64-bit (tile, depth)
-// keys and yields the same lists.  gs_render_noalloc keeps the one-stage
-// route, so the two are cross-checked by its test.
-constexpr bool kTwoStageBinning = true;
+// Binning routes.  The context-based entry points use the segmented build
+// (per-tile counts from difference grids of the records' tile rectangles,
+// atomic placement, a sort of each short tile list): no global sort at
+// all.  gs_bin, which bins the caller's records, keeps the two-stage route
+// (depth sort of the visible records, then a stable tile sort of 32-bit
+// keys), and gs_render_noalloc the one-stage route (one sort of 64-bit
+// (tile, depth) keys); all three yield the same lists, which their tests
+// cross-check.
+
+// scratch of the segmented build: cleared header + difference grids, cursors, long-list queue
+gs_status_t alloc_seg(gs_ctx *ctx, const Plan &P, Pipe &p)
+{
+    const size_t T = P.n_tiles ? P.n_tiles : 1;
+    p.seg_zero = gsl::seg_zero_bytes((int)P.vps.size(), P.n_diff);
+    uint8_t *z = nullptr;
+    GS_TRY(wsT(ctx, S_SEGZ, p.seg_zero, &z));
+    p.seg_hdr = (unsigned long long *)z;
+    p.seg_diff = (uint32_t *)(p.seg_hdr + 1 + P.vps.size());
+    GS_TRY(wsT(ctx, S_SEGCUR, T, &p.seg_cursor));
+    GS_TRY(wsT(ctx, S_SEGBIG, T, &p.seg_big));
+    return GS_OK;
+}
 
 gs_status_t alloc_pipe(gs_ctx *ctx, const Plan &P, bool aux, Pipe &p)
 {
@@ -346,13 +368,7 @@ gs_status_t alloc_pipe(gs_ctx *ctx, const Plan &P, bool aux, Pipe &p)
     GS_TRY(wsT(ctx, S_NDUPS, 4, &p.ndups));
     GS_TRY(wsT(ctx, S_RANGES, P.n_tiles ? P.n_tiles : 1, &p.ranges));
     GS_TRY(wsT(ctx, S_FLAGS, 4, &p.flags));
-    if (kTwoStageBinning) {
-        GS_TRY(wsT(ctx, S_DK0, R, &p.dkeys[0]));
-        GS_TRY(wsT(ctx, S_DK1, R, &p.dkeys[1]));
-        GS_TRY(wsT(ctx, S_DV0, R, &p.dvals[0]));
-        GS_TRY(wsT(ctx, S_DV1, R, &p.dvals[1]));
-        GS_TRY(wsT(ctx, S_NVIS, 4, &p.n_vis));
-    }
+    GS_TRY(alloc_seg(ctx, P, p));
     p.n_records = R;
     return GS_OK;
 }
@@ -362,29 +378,18 @@ gs_status_t alloc_sort(gs_ctx *ctx, uint64_t want, Pipe &p)
     if (want > 0xfff00000ull)
         return fail(ctx, GS_ERR_CAPACITY, "more than 2^32 tile duplicates");
     const uint32_t cap = (uint32_t)std::max<uint64_t>(want, 1024);
-    if (kTwoStageBinning) {
-        GS_TRY(wsT(ctx, S_K0, cap, &p.tkeys[0]));
-        GS_TRY(wsT(ctx, S_K1, cap, &p.tkeys[1]));
-    } else {
-        GS_TRY(wsT(ctx, S_K0, cap, &p.keys[0]));
-        GS_TRY(wsT(ctx, S_K1, cap, &p.keys[1]));
-    }
+    GS_TRY(wsT(ctx, S_K0, cap, &p.tkeys[0]));
+    GS_TRY(wsT(ctx, S_K1, cap, &p.tkeys[1]));
     GS_TRY(wsT(ctx, S_V0, cap, &p.vals[0]));
     GS_TRY(wsT(ctx, S_V1, cap, &p.vals[1]));
     const size_t hn = gsl::sort_hist_entries((uint32_t)std::max<uint64_t>(cap, p.n_records));
     GS_TRY(wsT(ctx, S_HIST, hn, &p.hist));
     GS_TRY(wsT(ctx, S_HISTP, gsl::scan_partials(hn), &p.histp));
-    if (kTwoStageBinning)
-        GS_TRY(wsT(ctx, S_OS, gsl::onesweep_scratch_bytes((uint32_t)std::max<uint64_t>(cap, p.n_records), 32),
-                   &p.os));
     p.cap = cap;
     return GS_OK;
 }
 
-int run_bin(const gsl::BinArgs &b, cudaStream_t s)
-{
-    return kTwoStageBinning ? gsl::bin2(b, s) : gsl::bin(b, s);
-}
+int run_bin(const gsl::BinArgs &b, cudaStream_t s) { return gsl::bin_seg(b, s); }
 
 gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, const float *pose32,
                               const gs_options_t *o, bool tight = false)
@@ -435,6 +440,11 @@ gsl::BinArgs bin_args(const Plan &P, const DevPlan &D, const Pipe &p)
     }
     b.n_vis = p.n_vis;
     b.os_scratch = p.os;
+    b.seg_hdr = p.seg_hdr;
+    b.seg_diff = p.seg_diff;
+    b.seg_zero_bytes = p.seg_zero;
+    b.seg_cursor = p.seg_cursor;
+    b.seg_big = p.seg_big;
     return b;
 }
 
@@ -471,7 +481,7 @@ gs_status_t project_and_bin(gs_ctx *ctx, const Plan &P, const DevPlan &D, Pipe &
     GS_CUDA(cudaStreamSynchronize(s));
     if (nd == 0xffffffffu)
         return fail(ctx, GS_ERR_CAPACITY, "more than 2^32 tile duplicates");
-    if (p.cap < nd || !p.keys[0])
+    if (p.cap < nd || !p.tkeys[0])
         GS_TRY(alloc_sort(ctx, nd, p));
     b = bin_args(P, D, p);
     *cur = run_bin(b, s);
@@ -793,13 +803,7 @@ gs_status_t gs_bin(gs_ctx_t *ctx, const float *records, const int32_t *counts, c
     p.ranges = (uint2 *)ranges;
     const size_t R = P.n_records ? P.n_records : 1;
     p.n_records = R;
-    if (kTwoStageBinning) {
-        GS_TRY(wsT(ctx, S_DK0, R, &p.dkeys[0]));
-        GS_TRY(wsT(ctx, S_DK1, R, &p.dkeys[1]));
-        GS_TRY(wsT(ctx, S_DV0, R, &p.dvals[0]));
-        GS_TRY(wsT(ctx, S_DV1, R, &p.dvals[1]));
-        GS_TRY(wsT(ctx, S_NVIS, 4, &p.n_vis));
-    }
+    GS_TRY(alloc_seg(ctx, P, p));
     gsl::BinArgs b = bin_args(P, D, p);
     gsl::bin_count(b, s);
     uint32_t nd = 0;
@@ -810,12 +814,9 @@ gs_status_t gs_bin(gs_ctx_t *ctx, const float *records, const int32_t *counts, c
         return fail(ctx, GS_ERR_CAPACITY, "gs_bin: " + std::to_string(nd) + " duplicates exceed capacity");
     GS_TRY(alloc_sort(ctx, nd, p));
     b = bin_args(P, D, p);
-    const int cur = run_bin(b, s);
+    const int cur = gsl::bin_seg(b, s);
     if (nd > 0) {
-        if (kTwoStageBinning)
-            gsl::keys64(b, cur, keys, s);
-        else
-            GS_CUDA(cudaMemcpyAsync(keys, p.keys[cur], sizeof(uint64_t) * nd, cudaMemcpyDeviceToDevice, s));
+        gsl::seg_keys64(b, keys, s);
         GS_CUDA(cudaMemcpyAsync(vals, p.vals[cur], sizeof(uint32_t) * nd, cudaMemcpyDeviceToDevice, s));
     }
     GS_CUDA(cudaGetLastError());

@@ -677,6 +677,413 @@ __global__ void k_order_scatter(const uint2 *ranges, uint32_t n, uint32_t *curso
         order[atomicAdd(&cursors[len_bucket(ranges[t])], 1u)] = t;
 }
 
+// --------------------------------------------------------- segmented build
+// Tile lists without a global sort: every record adds its tile rectangle to
+// its keyframe's 2-D difference grid, whose prefix sums give each tile's
+// list length and start; records are then placed into their tiles' lists
+// through per-tile atomic cursors (in no particular order), and each list is
+// sorted on its own by (depth bits, record index) -- the order of a stable
+// depth sort of the records, as the key is unique.
+
+// keyframe of record r: the last vp whose records start at or before r
+__device__ __forceinline__ int vp_of_record(const VpDesc *vps, int n_vps, uint32_t r)
+{
+    int lo = 0, hi = n_vps - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (vps[mid].rec_base <= r)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+struct SegRect {
+    uint32_t x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ SegRect seg_rect(const float4 *rec, uint32_t r)
+{
+    const uint32_t rx = __float_as_uint(rec[3 * (size_t)r + 1].w);
+    const uint32_t ry = __float_as_uint(rec[3 * (size_t)r + 2].w);
+    return SegRect{rx & 0xffffu, rx >> 16, ry & 0xffffu, ry >> 16};
+}
+
+// a record takes part when its rectangle lies in its keyframe's tile grid
+// and matches its count (records from the projection always do; gs_bin's
+// caller-supplied ones are checked here, the same way in every kernel)
+__device__ __forceinline__ bool seg_valid(const SegRect &q, const VpDesc &d, int count)
+{
+    return q.x0 < q.x1 && q.x1 <= (uint32_t)d.TX && q.y0 < q.y1 && q.y1 <= (uint32_t)d.TY &&
+           (uint32_t)count == (q.x1 - q.x0) * (q.y1 - q.y0);
+}
+
+constexpr int kSegThreads = 256;
+
+// One thread per record: a visible record adds +1 at (y0, x0) and (y1, x1)
+// and -1 (mod 2^32) at (y0, x1) and (y1, x0) of its keyframe's (TY + 1) x
+// (TX + 1) grid, four atomics whatever its size, and its tile count to its
+// keyframe's total (one atomic per block when the block's records share a
+// keyframe).
+__global__ void __launch_bounds__(kSegThreads) k_seg_diff(const gsl::BinArgs a)
+{
+    __shared__ int s_vp[2];
+    __shared__ unsigned long long s_sum[kSegThreads / 32];
+    const uint32_t b0 = blockIdx.x * kSegThreads;
+    const uint32_t r = b0 + threadIdx.x;
+    if (threadIdx.x == 0) {
+        s_vp[0] = vp_of_record(a.vps, a.n_vps, b0);
+        s_vp[1] = vp_of_record(a.vps, a.n_vps, min(b0 + (uint32_t)kSegThreads, a.n_records) - 1);
+    }
+    int vp = 0;
+    uint32_t cnt = 0;
+    if (r < a.n_records) {
+        const int c = a.counts[r];
+        const int rv = c > 0 ? vp_of_record(a.vps, a.n_vps, r) : 0;
+        const SegRect q = c > 0 ? seg_rect(a.rec, r) : SegRect{0, 0, 0, 0};
+        if (c > 0 && seg_valid(q, a.vps[rv], c)) {
+            cnt = (uint32_t)c;
+            vp = rv;
+            const VpDesc &d = a.vps[vp];
+            const uint32_t w1 = (uint32_t)d.TX + 1;
+            uint32_t *g = a.seg_diff + d.diff_base;
+            atomicAdd(g + q.y0 * w1 + q.x0, 1u);
+            atomicAdd(g + q.y1 * w1 + q.x1, 1u);
+            atomicAdd(g + q.y0 * w1 + q.x1, 0xffffffffu);
+            atomicAdd(g + q.y1 * w1 + q.x0, 0xffffffffu);
+        }
+    }
+    __syncthreads();
+    unsigned long long *tot = a.seg_hdr + 1;
+    if (s_vp[0] != s_vp[1]) {
+        if (cnt)
+            atomicAdd(tot + vp, (unsigned long long)cnt);
+        return;
+    }
+    const unsigned long long w = warp_sum((unsigned long long)cnt);
+    if ((threadIdx.x & 31) == 0)
+        s_sum[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+#pragma unroll
+        for (int k = 0; k < kSegThreads / 32; ++k)
+            t += s_sum[k];
+        if (t)
+            atomicAdd(tot + s_vp[0], t);
+    }
+}
+
+constexpr int kSegTileThreads = 512;
+
+// inclusive block scan of one value per thread (kSegTileThreads threads)
+__device__ __forceinline__ unsigned long long block_incl_scan(unsigned long long v, unsigned long long *s_w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o)
+            v += u;
+    }
+    if (lane == 31)
+        s_w[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long x = lane < kSegTileThreads / 32 ? s_w[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o)
+                x += u;
+        }
+        if (lane < kSegTileThreads / 32)
+            s_w[lane] = x;
+    }
+    __syncthreads();
+    const unsigned long long r = v + (warp ? s_w[warp - 1] : 0ull);
+    __syncthreads();
+    return r;
+}
+
+// One CTA per keyframe: 2-D prefix sums of its grid (rows, then columns;
+// in place) give the tile counts; an exclusive scan in tile order, offset
+// by the totals of the earlier keyframes, gives each tile's start.  Writes
+// the ranges (clipped to the capacity), the placement cursors, and (CTA 0)
+// the duplicate total and the capacity flag.
+__global__ void __launch_bounds__(kSegTileThreads) k_seg_tiles(const gsl::BinArgs a)
+{
+    __shared__ unsigned long long s_w[kSegTileThreads / 32];
+    const int v = blockIdx.x;
+    const VpDesc &d = a.vps[v];
+    const int TX = d.TX, TY = d.TY, w1 = TX + 1;
+    uint32_t *g = a.seg_diff + d.diff_base;
+    const unsigned long long *tot = a.seg_hdr + 1;
+    unsigned long long before = 0, all = 0;
+    for (int k = threadIdx.x; k < a.n_vps; k += blockDim.x) {
+        const unsigned long long t = tot[k];
+        before += k < v ? t : 0ull;
+        all += t;
+    }
+    const unsigned long long base = block_incl_scan(before, s_w);
+    const unsigned long long grand = block_incl_scan(all, s_w);
+    __shared__ unsigned long long s_base;
+    if (threadIdx.x == kSegTileThreads - 1) {
+        s_base = base;
+        if (v == 0) {
+            *a.n_dups = grand < 0xffffffffull ? (uint32_t)grand : 0xffffffffu;
+            if (grand > a.capacity)
+                atomicOr(a.flags, kFlagCapacity);
+        }
+    }
+    for (int y = threadIdx.x; y < TY; y += blockDim.x) {
+        uint32_t acc = 0;
+        uint32_t *row = g + (size_t)y * w1;
+        for (int x = 0; x < TX; ++x) {
+            acc += row[x];
+            row[x] = acc;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < TX; x += blockDim.x) {
+        uint32_t acc = 0;
+        for (int y = 0; y < TY; ++y) {
+            acc += g[(size_t)y * w1 + x];
+            g[(size_t)y * w1 + x] = acc;
+        }
+    }
+    __syncthreads();
+    const uint32_t nt = (uint32_t)TX * (uint32_t)TY;
+    unsigned long long carry = s_base;
+    for (uint32_t c0 = 0; c0 < nt; c0 += kSegTileThreads) {
+        const uint32_t lt = c0 + threadIdx.x;
+        uint32_t n = 0;
+        if (lt < nt)
+            n = g[(size_t)(lt / (uint32_t)TX) * w1 + lt % (uint32_t)TX];
+        const unsigned long long incl = block_incl_scan(n, s_w);
+        if (lt < nt) {
+            const unsigned long long st = carry + incl - n, en = st + n;
+            const uint32_t t = d.tile_base + lt;
+            const unsigned long long cap = a.capacity;
+            // (0, 0) for an empty tile
+            a.ranges[t] = n ? make_uint2((uint32_t)(st < cap ? st : cap), (uint32_t)(en < cap ? en : cap))
+                            : make_uint2(0u, 0u);
+            a.seg_cursor[t] = (uint32_t)(st < cap ? st : cap);
+        }
+        __shared__ unsigned long long s_tot;
+        if (threadIdx.x == kSegTileThreads - 1)
+            s_tot = incl;
+        __syncthreads();
+        carry += s_tot;
+        __syncthreads();
+    }
+}
+
+constexpr uint32_t kSegSmall = 8;  // records with more tiles are placed by the whole warp
+
+__device__ __forceinline__ void seg_put(const gsl::BinArgs &a, uint32_t t, uint32_t zb, uint32_t r)
+{
+    const uint32_t pos = atomicAdd(a.seg_cursor + t, 1u);
+    if (pos < a.capacity) {
+        a.tkeys[0][pos] = zb;
+        a.vals[0][pos] = r;
+    }
+}
+
+// One thread per record: each visible record writes (depth bits, record)
+// into the lists of the tiles of its rectangle at positions taken from the
+// tiles' cursors.  Records with more than kSegSmall tiles are spread over
+// the lanes of their warp, one record at a time, so a splat covering
+// thousands of tiles does not serialise one thread.  Positions at or past
+// the capacity are dropped (the capacity flag is already set).
+__global__ void __launch_bounds__(kSegThreads) k_seg_place(const gsl::BinArgs a)
+{
+    const uint32_t r = blockIdx.x * kSegThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    uint32_t cnt = 0, t0 = 0, w = 1, tx = 0, zb = 0;
+    if (r < a.n_records) {
+        const int c = a.counts[r];
+        const VpDesc &d = a.vps[c > 0 ? vp_of_record(a.vps, a.n_vps, r) : 0];
+        const SegRect q = c > 0 ? seg_rect(a.rec, r) : SegRect{0, 0, 0, 0};
+        if (c > 0 && seg_valid(q, d, c)) {
+            cnt = (uint32_t)c;
+            tx = (uint32_t)d.TX;
+            t0 = d.tile_base + q.y0 * tx + q.x0;
+            w = q.x1 - q.x0;
+            zb = __float_as_uint(a.rec[3 * (size_t)r + 1].z);
+        }
+    }
+    const bool big = cnt > kSegSmall;
+    if (!big)
+        for (uint32_t k = 0; k < cnt; ++k)
+            seg_put(a, t0 + (k / w) * tx + k % w, zb, r);
+    unsigned m = __ballot_sync(0xffffffffu, big);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t c = __shfl_sync(0xffffffffu, cnt, src), b = __shfl_sync(0xffffffffu, t0, src);
+        const uint32_t ww = __shfl_sync(0xffffffffu, w, src), tt = __shfl_sync(0xffffffffu, tx, src);
+        const uint32_t z = __shfl_sync(0xffffffffu, zb, src), rr = __shfl_sync(0xffffffffu, r, src);
+        for (uint32_t k = lane; k < c; k += 32)
+            seg_put(a, b + (k / ww) * tt + k % ww, z, rr);
+    }
+}
+
+// Ascending bitonic sort with "flip" merges: merging two sorted halves of a
+// block of size k compares element i of the block with element k - 1 - i,
+// after which every element of the lower half is at most every element of
+// the upper one and each half is bitonic; half-cleaners at distances
+// k/4, ..., 1 then sort each half.  Only ascending compare-exchanges occur,
+// so positions past the list end act as +infinity and their exchanges can
+// be skipped.
+
+// 32 keys, one per lane (lanes past the list hold ~0)
+__device__ __forceinline__ unsigned long long warp_bitonic32(unsigned long long x, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+        {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, k - 1);
+            const bool lower = (lane & (k >> 1)) == 0;
+            x = lower ? (y < x ? y : x) : (y > x ? y : x);
+        }
+#pragma unroll
+        for (int j = k >> 2; j >= 1; j >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+            const bool lower = (lane & j) == 0;
+            x = lower ? (y < x ? y : x) : (y > x ? y : x);
+        }
+    }
+    return x;
+}
+
+__device__ __forceinline__ void cex(unsigned long long *s, int i, int p)
+{
+    const unsigned long long u = s[i], v = s[p];
+    if (u > v) {
+        s[i] = v;
+        s[p] = u;
+    }
+}
+
+constexpr int kSegSortWarps = 8;
+constexpr int kSegSortCap = 512;  // longest list sorted by one warp in shared memory
+
+// One warp per tile: lists of up to 32 entries are sorted in registers,
+// up to kSegSortCap in shared memory (padded with ~0 to a power of two);
+// longer lists are queued for k_seg_sort_big.  The sorted record indices
+// replace the tile's values in place.
+__global__ void __launch_bounds__(kSegSortWarps * 32) k_seg_sort(const gsl::BinArgs a)
+{
+    __shared__ unsigned long long s_k[kSegSortWarps][kSegSortCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t t = blockIdx.x * kSegSortWarps + warp;
+    if (t >= a.n_tiles)
+        return;
+    const uint2 rg = a.ranges[t];
+    const uint32_t n = rg.y - rg.x;
+    if (n <= 1)
+        return;
+    const uint32_t *keys = a.tkeys[0] + rg.x;
+    uint32_t *vals = a.vals[0] + rg.x;
+    if (n <= 32) {
+        unsigned long long x = ~0ull;
+        if ((uint32_t)lane < n)
+            x = ((unsigned long long)keys[lane] << 32) | vals[lane];
+        x = warp_bitonic32(x, lane);
+        if ((uint32_t)lane < n)
+            vals[lane] = (uint32_t)x;
+        return;
+    }
+    if (n > (uint32_t)kSegSortCap) {
+        if (lane == 0)
+            a.seg_big[atomicAdd(a.seg_hdr, 1ull)] = t;
+        return;
+    }
+    int N = 64;
+    while ((uint32_t)N < n)
+        N <<= 1;
+    unsigned long long *sk = s_k[warp];
+    for (int i = lane; i < N; i += 32)
+        sk[i] = (uint32_t)i < n ? (((unsigned long long)keys[i] << 32) | vals[i]) : ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= N; k <<= 1) {
+        const int h = k >> 1;
+        for (int q = lane; q < (N >> 1); q += 32) {
+            const int i = (q / h) * k + (q & (h - 1));
+            cex(sk, i, i + k - 1 - 2 * (q & (h - 1)));
+        }
+        __syncwarp();
+        for (int j = k >> 2; j >= 1; j >>= 1) {
+            for (int q = lane; q < (N >> 1); q += 32) {
+                const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                cex(sk, i, i | j);
+            }
+            __syncwarp();
+        }
+    }
+    for (int i = lane; (uint32_t)i < n; i += 32)
+        vals[i] = (uint32_t)sk[i];
+}
+
+// 64-bit (tile << 32 | depth bits) keys of the segmented lists, one warp per tile (for gs_bin)
+__global__ void __launch_bounds__(256) k_seg_keys64(const gsl::BinArgs a, uint64_t *keys)
+{
+    const uint32_t t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= a.n_tiles)
+        return;
+    const uint2 rg = a.ranges[t];
+    for (uint32_t i = rg.x + (threadIdx.x & 31); i < rg.y; i += 32)
+        keys[i] = ((uint64_t)t << 32) | __float_as_uint(a.rec[3 * (size_t)a.vals[0][i] + 1].z);
+}
+
+// Lists longer than kSegSortCap (none on typical views; a splat-dense tile
+// close to the camera): one CTA per queued tile, the same network over the
+// list in global memory, (key, value) pairs exchanged in place, then the
+// values kept.  Slow per element but only ever reached by a few tiles.
+__global__ void __launch_bounds__(1024) k_seg_sort_big(const gsl::BinArgs a)
+{
+    const unsigned long long nb = a.seg_hdr[0];
+    for (unsigned long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        const uint2 rg = a.ranges[a.seg_big[b]];
+        const uint32_t n = rg.y - rg.x;
+        uint32_t *keys = a.tkeys[0] + rg.x;
+        uint32_t *vals = a.vals[0] + rg.x;
+        uint64_t N = 1;
+        while (N < n)
+            N <<= 1;
+        auto ce = [&](uint64_t i, uint64_t p) {
+            if (p >= n)
+                return;  // +infinity past the end
+            const unsigned long long u = ((unsigned long long)keys[i] << 32) | vals[i];
+            const unsigned long long v = ((unsigned long long)keys[p] << 32) | vals[p];
+            if (u > v) {
+                keys[i] = (uint32_t)(v >> 32);
+                vals[i] = (uint32_t)v;
+                keys[p] = (uint32_t)(u >> 32);
+                vals[p] = (uint32_t)u;
+            }
+        };
+        for (uint64_t k = 2; k <= N; k <<= 1) {
+            const uint64_t h = k >> 1;
+            for (uint64_t q = threadIdx.x; q < (N >> 1); q += blockDim.x) {
+                const uint64_t i = (q / h) * k + (q & (h - 1));
+                ce(i, i + k - 1 - 2 * (q & (h - 1)));
+            }
+            __syncthreads();
+            for (uint64_t j = k >> 2; j >= 1; j >>= 1) {
+                for (uint64_t q = threadIdx.x; q < (N >> 1); q += blockDim.x) {
+                    const uint64_t i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                    ce(i, i | j);
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // stable LSD radix sort of (key, value) over `bits` low key bits, 8 per pass;
 // returns the buffer index holding the result
 template <typename K>
@@ -808,6 +1215,42 @@ int bin2(const BinArgs &a, cudaStream_t s)
                                                                                 a.ranges);
     ++g_launches;
     return tc;
+}
+
+size_t seg_zero_bytes(int n_vps, uint64_t n_diff)
+{
+    return sizeof(unsigned long long) * (1 + (size_t)n_vps) + sizeof(uint32_t) * (size_t)n_diff;
+}
+
+int bin_seg(const BinArgs &a, cudaStream_t s)
+{
+    cudaMemsetAsync(a.seg_hdr, 0, a.seg_zero_bytes, s);
+    if (a.n_vps == 0) {
+        cudaMemsetAsync(a.n_dups, 0, sizeof(uint32_t), s);
+        return 0;
+    }
+    if (a.n_records)
+        k_seg_diff<<<div_up(a.n_records, kSegThreads), kSegThreads, 0, s>>>(a);
+    k_seg_tiles<<<a.n_vps, kSegTileThreads, 0, s>>>(a);
+    g_launches += 1 + (a.n_records ? 1 : 0);
+    if (a.n_records) {
+        k_seg_place<<<div_up(a.n_records, kSegThreads), kSegThreads, 0, s>>>(a);
+        ++g_launches;
+    }
+    if (a.n_tiles) {
+        k_seg_sort<<<div_up(a.n_tiles, kSegSortWarps), kSegSortWarps * 32, 0, s>>>(a);
+        k_seg_sort_big<<<152, 1024, 0, s>>>(a);
+        g_launches += 2;
+    }
+    return 0;
+}
+
+void seg_keys64(const BinArgs &a, uint64_t *out, cudaStream_t s)
+{
+    if (a.n_tiles == 0)
+        return;
+    k_seg_keys64<<<div_up(a.n_tiles, 8), 256, 0, s>>>(a, out);
+    ++g_launches;
 }
 
 void keys64(const BinArgs &a, int cur, uint64_t *out, cudaStream_t s)

@@ -32,6 +32,7 @@ struct VpDesc {
     float w2c[12];         // world -> camera
     uint32_t rec_base;     // first record index
     uint32_t tile_base;    // first global tile id
+    uint32_t diff_base;    // first cell of its (TY + 1) x (TX + 1) tile difference grid
     int64_t pix_base;      // first pixel in concatenated per-pixel arrays
     const float *t_rgb;    // registration targets [3][H][W] (or null)
     const float *t_depth;  // [H][W]
@@ -222,6 +223,15 @@ struct BinArgs {
     uint32_t *tkeys[2];             // [capacity]
     uint32_t *n_vis;                // device scalar
     uint8_t *os_scratch;            // one-sweep sort state (onesweep_scratch_bytes), or null = classic passes
+    // segmented build (bin_seg): seg_hdr[0] counts the tiles queued for the
+    // long-list sort, seg_hdr[1 + v] holds keyframe v's duplicate total, and
+    // the difference grids (VpDesc::diff_base) follow in the same allocation
+    // of seg_zero_bytes, cleared at the start of every build
+    unsigned long long *seg_hdr;
+    uint32_t *seg_diff;
+    size_t seg_zero_bytes;
+    uint32_t *seg_cursor;  // [n_tiles] placement cursors
+    uint32_t *seg_big;     // [n_tiles] tiles whose lists exceed the warp sort
 };
 // emits, sorts and ranges; returns which buffer holds the sorted result
 int bin(const BinArgs &a, cudaStream_t s);
@@ -229,6 +239,14 @@ int bin(const BinArgs &a, cudaStream_t s);
 // tile sort of duplicates); the sorted values are in vals[return], the tile
 // keys in tkeys[return]
 int bin2(const BinArgs &a, cudaStream_t s);
+// the same lists by the segmented build: per-tile counts from 2-D
+// difference grids of the records' tile rectangles, atomic placement, and a
+// sort of each tile's list by (depth bits, record); sorted values in vals[0]
+// (the return value), the ranges written directly, n_dups set
+int bin_seg(const BinArgs &a, cudaStream_t s);
+size_t seg_zero_bytes(int n_vps, uint64_t n_diff);
+// 64-bit (tile << 32 | depth bits) keys of the lists bin_seg built
+void seg_keys64(const BinArgs &a, uint64_t *out, cudaStream_t s);
 // Tile schedule for the compositing kernels: tiles ordered by decreasing
 // list length (bucketed by the position of the length's top bit; order
 // within a bucket arbitrary), so the longest tiles start first and do not
