@@ -445,6 +445,8 @@ gsl::BinArgs bin_args(const Plan &P, const DevPlan &D, const Pipe &p)
     b.seg_zero_bytes = p.seg_zero;
     b.seg_cursor = p.seg_cursor;
     b.seg_big = p.seg_big;
+    for (const VpDesc &d : P.vps)
+        b.seg_max_cells = std::max(b.seg_max_cells, (uint32_t)(d.TX * d.TY));
     return b;
 }
 

@@ -807,14 +807,20 @@ __device__ __forceinline__ unsigned long long block_incl_scan(unsigned long long
     return r;
 }
 
-// One CTA per keyframe: 2-D prefix sums of its grid (rows, then columns;
-// in place) give the tile counts; an exclusive scan in tile order, offset
-// by the totals of the earlier keyframes, gives each tile's start.  Writes
-// the ranges (clipped to the capacity), the placement cursors, and (CTA 0)
-// the duplicate total and the capacity flag.
+// One CTA per keyframe: 2-D prefix sums of its grid (rows, then columns)
+// give the tile counts; an exclusive scan in tile order, offset by the
+// totals of the earlier keyframes, gives each tile's start.  Writes the
+// ranges ((0, 0) when empty; clipped to the capacity), the placement
+// cursors, and (CTA 0) the duplicate total and the capacity flag.  SMEM:
+// the grid's TY x TX counting cells are copied to shared memory (dynamic,
+// a.seg_max_cells words); otherwise the prefix sums run in place in global
+// memory.
+template <bool SMEM>
 __global__ void __launch_bounds__(kSegTileThreads) k_seg_tiles(const gsl::BinArgs a)
 {
+    extern __shared__ uint32_t s_grid[];
     __shared__ unsigned long long s_w[kSegTileThreads / 32];
+    __shared__ unsigned long long s_base;
     const int v = blockIdx.x;
     const VpDesc &d = a.vps[v];
     const int TX = d.TX, TY = d.TY, w1 = TX + 1;
@@ -828,7 +834,6 @@ __global__ void __launch_bounds__(kSegTileThreads) k_seg_tiles(const gsl::BinArg
     }
     const unsigned long long base = block_incl_scan(before, s_w);
     const unsigned long long grand = block_incl_scan(all, s_w);
-    __shared__ unsigned long long s_base;
     if (threadIdx.x == kSegTileThreads - 1) {
         s_base = base;
         if (v == 0) {
@@ -837,9 +842,18 @@ __global__ void __launch_bounds__(kSegTileThreads) k_seg_tiles(const gsl::BinArg
                 atomicOr(a.flags, kFlagCapacity);
         }
     }
+    const uint32_t nt = (uint32_t)TX * (uint32_t)TY;
+    // cell (y, x) of the counting grid: compact TY x TX in shared memory, or the pitched grid itself
+    uint32_t *c = SMEM ? s_grid : g;
+    const int pitch = SMEM ? TX : w1;
+    if (SMEM) {
+        for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x)
+            s_grid[i] = g[(size_t)(i / (uint32_t)TX) * w1 + i % (uint32_t)TX];
+        __syncthreads();
+    }
     for (int y = threadIdx.x; y < TY; y += blockDim.x) {
         uint32_t acc = 0;
-        uint32_t *row = g + (size_t)y * w1;
+        uint32_t *row = c + (size_t)y * pitch;
         for (int x = 0; x < TX; ++x) {
             acc += row[x];
             row[x] = acc;
@@ -849,34 +863,29 @@ __global__ void __launch_bounds__(kSegTileThreads) k_seg_tiles(const gsl::BinArg
     for (int x = threadIdx.x; x < TX; x += blockDim.x) {
         uint32_t acc = 0;
         for (int y = 0; y < TY; ++y) {
-            acc += g[(size_t)y * w1 + x];
-            g[(size_t)y * w1 + x] = acc;
+            acc += c[(size_t)y * pitch + x];
+            c[(size_t)y * pitch + x] = acc;
         }
     }
     __syncthreads();
-    const uint32_t nt = (uint32_t)TX * (uint32_t)TY;
-    unsigned long long carry = s_base;
-    for (uint32_t c0 = 0; c0 < nt; c0 += kSegTileThreads) {
-        const uint32_t lt = c0 + threadIdx.x;
-        uint32_t n = 0;
-        if (lt < nt)
-            n = g[(size_t)(lt / (uint32_t)TX) * w1 + lt % (uint32_t)TX];
-        const unsigned long long incl = block_incl_scan(n, s_w);
-        if (lt < nt) {
-            const unsigned long long st = carry + incl - n, en = st + n;
-            const uint32_t t = d.tile_base + lt;
-            const unsigned long long cap = a.capacity;
-            // (0, 0) for an empty tile
-            a.ranges[t] = n ? make_uint2((uint32_t)(st < cap ? st : cap), (uint32_t)(en < cap ? en : cap))
-                            : make_uint2(0u, 0u);
-            a.seg_cursor[t] = (uint32_t)(st < cap ? st : cap);
-        }
-        __shared__ unsigned long long s_tot;
-        if (threadIdx.x == kSegTileThreads - 1)
-            s_tot = incl;
-        __syncthreads();
-        carry += s_tot;
-        __syncthreads();
+    // each thread scans a contiguous run of tiles; one block scan joins the runs
+    const uint32_t per = (nt + kSegTileThreads - 1) / kSegTileThreads;
+    const uint32_t l0 = min(threadIdx.x * per, nt), l1 = min(l0 + per, nt);
+    auto cell = [&](uint32_t lt) { return c[(size_t)(lt / (uint32_t)TX) * pitch + lt % (uint32_t)TX]; };
+    unsigned long long run = 0;
+    for (uint32_t lt = l0; lt < l1; ++lt)
+        run += cell(lt);
+    unsigned long long st = s_base + block_incl_scan(run, s_w) - run;
+    const unsigned long long cap = a.capacity;
+    for (uint32_t lt = l0; lt < l1; ++lt) {
+        const uint32_t n = cell(lt);
+        const unsigned long long en = st + n;
+        const uint32_t t = d.tile_base + lt;
+        // (0, 0) for an empty tile
+        a.ranges[t] = n ? make_uint2((uint32_t)(st < cap ? st : cap), (uint32_t)(en < cap ? en : cap))
+                        : make_uint2(0u, 0u);
+        a.seg_cursor[t] = (uint32_t)(st < cap ? st : cap);
+        st = en;
     }
 }
 
@@ -915,9 +924,28 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_place(const gsl::BinArgs a)
         }
     }
     const bool big = cnt > kSegSmall;
-    if (!big)
-        for (uint32_t k = 0; k < cnt; ++k)
-            seg_put(a, t0 + (k / w) * tx + k % w, zb, r);
+    if (!big) {
+        // all cursor atomics first (independent, so in flight together), then the stores
+        uint32_t pos[kSegSmall];
+        uint32_t col = 0, row = t0;
+#pragma unroll
+        for (uint32_t k = 0; k < kSegSmall; ++k) {
+            if (k < cnt) {
+                pos[k] = atomicAdd(a.seg_cursor + row + col, 1u);
+                if (++col == w) {
+                    col = 0;
+                    row += tx;
+                }
+            }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < kSegSmall; ++k) {
+            if (k < cnt && pos[k] < a.capacity) {
+                a.tkeys[0][pos[k]] = zb;
+                a.vals[0][pos[k]] = r;
+            }
+        }
+    }
     unsigned m = __ballot_sync(0xffffffffu, big);
     while (m) {
         const int src = __ffs(m) - 1;
@@ -1231,7 +1259,10 @@ int bin_seg(const BinArgs &a, cudaStream_t s)
     }
     if (a.n_records)
         k_seg_diff<<<div_up(a.n_records, kSegThreads), kSegThreads, 0, s>>>(a);
-    k_seg_tiles<<<a.n_vps, kSegTileThreads, 0, s>>>(a);
+    if (a.seg_max_cells * sizeof(uint32_t) <= 40 * 1024)
+        k_seg_tiles<true><<<a.n_vps, kSegTileThreads, a.seg_max_cells * sizeof(uint32_t), s>>>(a);
+    else
+        k_seg_tiles<false><<<a.n_vps, kSegTileThreads, 0, s>>>(a);
     g_launches += 1 + (a.n_records ? 1 : 0);
     if (a.n_records) {
         k_seg_place<<<div_up(a.n_records, kSegThreads), kSegThreads, 0, s>>>(a);

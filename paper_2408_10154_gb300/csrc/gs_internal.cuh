@@ -232,6 +232,7 @@ struct BinArgs {
     size_t seg_zero_bytes;
     uint32_t *seg_cursor;  // [n_tiles] placement cursors
     uint32_t *seg_big;     // [n_tiles] tiles whose lists exceed the warp sort
+    uint32_t seg_max_cells;  // largest TX * TY over the keyframes
 };
 // emits, sorts and ranges; returns which buffer holds the sorted result
 int bin(const BinArgs &a, cudaStream_t s);
