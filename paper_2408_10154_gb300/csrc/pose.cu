@@ -30,27 +30,28 @@ __device__ void so3_exp(const double *w, double R[3][3])
         }
 }
 
-// Adam step on the twist g (about pivot c) and the pose update
-// R <- exp(-s_w) R, t <- exp(-s_w)(t - c) + c - s_v.
-// k = iteration index in [0, iters) of the learning-rate schedule; st[12]
-// counts the steps taken (bias correction).
-__device__ void adam_exp_update(double *pose, double *st, const double *g, const double *c, int k, int iters,
-                                float lr_rot, float lr_trans, float b1f, float b2f, float epsf, float lr_final)
+// Adam step of twist component i (0..2 rotation, 3..5 translation) with
+// gradient gi: updates its moments st[i], st[6 + i] and returns the step
+// xi_i.  k = iteration index in [0, iters) of the learning-rate schedule;
+// t = steps taken including this one (bias correction).
+__device__ double adam_component(double *st, int i, double gi, double t, int k, int iters, float lr_rot,
+                                 float lr_trans, float b1f, float b2f, float epsf, float lr_final)
 {
     const double kPi = 3.14159265358979323846;
     const double b1 = b1f, b2 = b2f, eps = epsf, f = lr_final;
-    const double t = st[12] + 1.0;
-    st[12] = t;
     const double sched = f + (1.0 - f) * 0.5 * (1.0 + cos(kPi * (double)k / (double)iters));
-    double xi[6];
-    for (int i = 0; i < 6; ++i) {
-        st[i] = b1 * st[i] + (1.0 - b1) * g[i];
-        st[6 + i] = b2 * st[6 + i] + (1.0 - b2) * g[i] * g[i];
-        const double mh = st[i] / (1.0 - pow(b1, t));
-        const double vh = st[6 + i] / (1.0 - pow(b2, t));
-        const double lr = (i < 3 ? (double)lr_rot : (double)lr_trans) * sched;
-        xi[i] = -lr * mh / (sqrt(vh) + eps);
-    }
+    st[i] = b1 * st[i] + (1.0 - b1) * gi;
+    st[6 + i] = b2 * st[6 + i] + (1.0 - b2) * gi * gi;
+    const double mh = st[i] / (1.0 - pow(b1, t));
+    const double vh = st[6 + i] / (1.0 - pow(b2, t));
+    const double lr = (i < 3 ? (double)lr_rot : (double)lr_trans) * sched;
+    return -lr * mh / (sqrt(vh) + eps);
+}
+
+// Pose update by the step xi about pivot c:
+// R <- exp(-s_w) R, t <- exp(-s_w)(t - c) + c - s_v (xi carries the signs).
+__device__ void exp_update(double *pose, const double *xi, const double *c)
+{
     double dR[3][3];
     so3_exp(xi, dR);
     double R[3][3], tt[3];
@@ -65,6 +66,19 @@ __device__ void adam_exp_update(double *pose, double *st, const double *g, const
             pose[4 * i + j] = dR[i][0] * R[0][j] + dR[i][1] * R[1][j] + dR[i][2] * R[2][j];
         pose[4 * i + 3] = dR[i][0] * rel[0] + dR[i][1] * rel[1] + dR[i][2] * rel[2] + c[i] + xi[3 + i];
     }
+}
+
+// Adam step on the twist g (about pivot c) and the pose update, serially;
+// st[12] counts the steps taken
+__device__ void adam_exp_update(double *pose, double *st, const double *g, const double *c, int k, int iters,
+                                float lr_rot, float lr_trans, float b1f, float b2f, float epsf, float lr_final)
+{
+    const double t = st[12] + 1.0;
+    double xi[6];
+    for (int i = 0; i < 6; ++i)
+        xi[i] = adam_component(st, i, g[i], t, k, iters, lr_rot, lr_trans, b1f, b2f, epsf, lr_final);
+    st[12] = t;
+    exp_update(pose, xi, c);
 }
 
 // pivot = R mu_bar + t (world) and its camera-frame image for keyframe d
@@ -144,10 +158,15 @@ __device__ void exposure_step(double *e, const double *g, int k, int iters, floa
 }
 
 // one block per keyframe: reduce the tile twists and losses in a fixed
-// order, rotate the twist to the world frame, then (update) take the step
+// order, rotate the twist to the world frame, then (update) take the step.
+// The step's FP64 work runs on warp 0: Adam on the six twist components in
+// parallel (one lane each -- serially, their pow/sqrt chains dominated the
+// update, the FP64 pipe being a small fraction of the FP32 one), then the
+// exponential-map update, the exposure step and the pivots on lane 0.
 __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
 {
     __shared__ double s[8][9];
+    __shared__ double s_g[6], s_xi[6];
     const int vp = blockIdx.x;
     const VpDesc &d = a.vps[vp];
     const uint32_t nt = (uint32_t)d.TX * d.TY;
@@ -170,43 +189,53 @@ __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
             s[threadIdx.x >> 5][i] = v;
     }
     __syncthreads();
-    if (threadIdx.x != 0)
+    if (threadIdx.x >= 32)
         return;
+    const int lane = threadIdx.x;
     double tot[9];
     for (int i = 0; i < 9; ++i) {
         tot[i] = 0;
         for (int w = 0; w < 8; ++w)
             tot[i] += s[w][i];
     }
-    a.loss[vp] = tot[6];
+    if (lane == 0)
+        a.loss[vp] = tot[6];
     if (!a.tile_twist)
         return;
     // camera frame -> world frame: w = Rv^T w_c, v = Rv^T v_c
-    double g[6];
-    for (int i = 0; i < 3; ++i) {
-        g[i] = (double)d.w2c[i] * tot[0] + (double)d.w2c[4 + i] * tot[1] + (double)d.w2c[8 + i] * tot[2];
-        g[3 + i] = (double)d.w2c[i] * tot[3] + (double)d.w2c[4 + i] * tot[4] + (double)d.w2c[8 + i] * tot[5];
+    if (lane < 6) {
+        const int r = lane % 3, o = lane < 3 ? 0 : 3;
+        const double gi =
+            (double)d.w2c[r] * tot[o] + (double)d.w2c[4 + r] * tot[o + 1] + (double)d.w2c[8 + r] * tot[o + 2];
+        s_g[lane] = gi;
+        if (a.grad)
+            a.grad[6 * vp + lane] = gi;
     }
-    if (a.grad)
-        for (int i = 0; i < 6; ++i)
-            a.grad[6 * vp + i] = g[i];
     if (!a.update)
         return;  // (pose and optimiser state may be absent: gradient-only callers)
     const int iters = d.iters > 0 ? d.iters : a.iters;
-    const int k = (int)a.adam[13 * vp + 12];
+    double *st = a.adam + 13 * vp;
+    const int k = (int)st[12];
     if (k >= iters)
         return;
+    const double t = st[12] + 1.0;
+    if (lane < 6)
+        s_xi[lane] = adam_component(st, lane, s_g[lane], t, k, iters, d.lr_rot, d.lr_trans, a.beta1, a.beta2,
+                                    a.eps, a.lr_final);
+    __syncwarp();
+    if (lane != 0)
+        return;
+    st[12] = t;
     double *P = a.pose64 + 12 * vp;
-    adam_exp_update(P, a.adam + 13 * vp, g, a.pivot + 3 * vp, k, iters, d.lr_rot, d.lr_trans, a.beta1, a.beta2,
-                    a.eps, a.lr_final);
+    exp_update(P, s_xi, a.pivot + 3 * vp);
     if (expo) {
         double *e = a.expo + 7 * vp;
         exposure_step(e, tot + 7, k, iters, d.lr_exposure, a.beta1, a.beta2, a.eps, a.lr_final);
         a.expo32[2 * vp] = (float)exp(e[0]);
         a.expo32[2 * vp + 1] = (float)e[1];
     }
-    for (int k = 0; k < 12; ++k)
-        a.pose32[12 * vp + k] = (float)P[k];
+    for (int q = 0; q < 12; ++q)
+        a.pose32[12 * vp + q] = (float)P[q];
     pivots_of(d, P, a.centroid + 3 * d.set, a.pivot + 3 * vp, a.c_cam + 3 * vp);
 }
 
