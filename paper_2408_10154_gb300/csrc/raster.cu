@@ -501,7 +501,9 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
 // One (pixel, Gaussian) pair of the back-to-front walk: the contract's
 // decisions, the transmittance recovery, the colour-behind update and the
 // screen-space gradient added to g.  Returns whether the pair contributed.
-template <bool FULL>
+// ALPHA: the alpha image has a cotangent (render mode; the registration
+// loss has none).
+template <bool FULL, bool ALPHA>
 __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0, const float4 &q1,
                                              const float4 *q2p, const gsl::RasterArgs &a, float *g)
 {
@@ -520,8 +522,9 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     const float om = 1.0f - alpha;
     const float Ti = __fdividef(P.T, om);
     const float4 q2 = *q2p;
-    const float dal = Ti * (P.gr * (q2.x - P.Rr) + P.gg * (q2.y - P.Rg) + P.gb * (q2.z - P.Rb) + P.gd * (q1.z - P.Rd)) +
-                      __fdividef(P.ga_tf, om);
+    float dal = Ti * (P.gr * (q2.x - P.Rr) + P.gg * (q2.y - P.Rg) + P.gb * (q2.z - P.Rb) + P.gd * (q1.z - P.Rd));
+    if (ALPHA)
+        dal += __fdividef(P.ga_tf, om);
     P.Rr = fmaf(alpha, q2.x, om * P.Rr);
     P.Rg = fmaf(alpha, q2.y, om * P.Rg);
     P.Rb = fmaf(alpha, q2.z, om * P.Rb);
@@ -636,8 +639,8 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
                 g[k] = 0.0f;
             const float4 q0 = s0[j];
             const float4 q1 = s1[j];
-            const bool c0 = pix_adj_pair<FULL>(P0, lo + j, q0, q1, &s2[j], a, g);
-            const bool c1 = pix_adj_pair<FULL>(P1, lo + j, q0, q1, &s2[j], a, g);
+            const bool c0 = pix_adj_pair<FULL, !REG>(P0, lo + j, q0, q1, &s2[j], a, g);
+            const bool c1 = pix_adj_pair<FULL, !REG>(P1, lo + j, q0, q1, &s2[j], a, g);
             if (__any_sync(0xffffffffu, c0 || c1)) {
                 constexpr int NP = NG <= 8 ? 8 : 16;
                 float v[NP];
