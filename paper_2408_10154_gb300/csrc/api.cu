@@ -24,7 +24,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_SEGZ, S_SEGCUR, S_SEGBIG, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_SEGZ, S_SEGCUR, S_SEGBIG, S_SEGLIST, S_COUNT
 };
 
 struct Buf {
@@ -331,6 +331,7 @@ struct Pipe {
     // segmented build
     unsigned long long *seg_hdr = nullptr;
     uint32_t *seg_diff = nullptr, *seg_cursor = nullptr, *seg_big = nullptr;
+    uint4 *seg_list = nullptr;
     size_t seg_zero = 0;
 };
 
@@ -343,15 +344,17 @@ struct Pipe {
 // (tile, depth) keys); all three yield the same lists, which their tests
 // cross-check.
 
-// scratch of the segmented build: cleared header + difference grids, cursors, long-list queue
+// scratch of the segmented build: cleared header + difference grids,
+// visible-record list, cursors, long-list queue
 gs_status_t alloc_seg(gs_ctx *ctx, const Plan &P, Pipe &p)
 {
-    const size_t T = P.n_tiles ? P.n_tiles : 1;
+    const size_t T = P.n_tiles ? P.n_tiles : 1, R = P.n_records ? P.n_records : 1;
     p.seg_zero = gsl::seg_zero_bytes((int)P.vps.size(), P.n_diff);
     uint8_t *z = nullptr;
     GS_TRY(wsT(ctx, S_SEGZ, p.seg_zero, &z));
     p.seg_hdr = (unsigned long long *)z;
     p.seg_diff = (uint32_t *)(p.seg_hdr + 1 + P.vps.size());
+    GS_TRY(wsT(ctx, S_SEGLIST, R, &p.seg_list));
     GS_TRY(wsT(ctx, S_SEGCUR, T, &p.seg_cursor));
     GS_TRY(wsT(ctx, S_SEGBIG, T, &p.seg_big));
     return GS_OK;
@@ -409,6 +412,11 @@ gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, co
     a.flags = p.flags;
     a.tight = tight && o->alpha_min > 0 && !o->smooth;
     a.skip_below = skip_threshold(o);
+    // the projection counts and lists for the segmented build (run_bin follows every projection here)
+    a.seg_hdr = p.seg_hdr;
+    a.seg_diff = p.seg_diff;
+    a.seg_zero_bytes = p.seg_zero;
+    a.seg_list = p.seg_list;
     return a;
 }
 
@@ -445,6 +453,8 @@ gsl::BinArgs bin_args(const Plan &P, const DevPlan &D, const Pipe &p)
     b.seg_zero_bytes = p.seg_zero;
     b.seg_cursor = p.seg_cursor;
     b.seg_big = p.seg_big;
+    b.seg_list = p.seg_list;
+    b.seg_counted = 1;
     for (const VpDesc &d : P.vps)
         b.seg_max_cells = std::max(b.seg_max_cells, (uint32_t)(d.TX * d.TY));
     return b;
@@ -816,6 +826,7 @@ gs_status_t gs_bin(gs_ctx_t *ctx, const float *records, const int32_t *counts, c
         return fail(ctx, GS_ERR_CAPACITY, "gs_bin: " + std::to_string(nd) + " duplicates exceed capacity");
     GS_TRY(alloc_sort(ctx, nd, p));
     b = bin_args(P, D, p);
+    b.seg_counted = 0;  // the caller's records: collect them here
     const int cur = gsl::bin_seg(b, s);
     if (nd > 0) {
         gsl::seg_keys64(b, keys, s);

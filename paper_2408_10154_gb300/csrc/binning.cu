@@ -721,58 +721,32 @@ __device__ __forceinline__ bool seg_valid(const SegRect &q, const VpDesc &d, int
 
 constexpr int kSegThreads = 256;
 
-// One thread per record: a visible record adds +1 at (y0, x0) and (y1, x1)
-// and -1 (mod 2^32) at (y0, x1) and (y1, x0) of its keyframe's (TY + 1) x
-// (TX + 1) grid, four atomics whatever its size, and its tile count to its
-// keyframe's total (one atomic per block when the block's records share a
-// keyframe).
-__global__ void __launch_bounds__(kSegThreads) k_seg_diff(const gsl::BinArgs a)
+// One thread per record (gs_bin: records supplied by the caller; the
+// context paths do this inside the projection): a valid visible record adds
+// its rectangle to its keyframe's difference grid (+1 at (y0, x0) and
+// (y1, x1), -1 mod 2^32 at (y0, x1) and (y1, x0));
+// every record writes its entry (size 0 when not taking part).
+__global__ void __launch_bounds__(kSegThreads) k_seg_collect(const gsl::BinArgs a)
 {
-    __shared__ int s_vp[2];
-    __shared__ unsigned long long s_sum[kSegThreads / 32];
-    const uint32_t b0 = blockIdx.x * kSegThreads;
-    const uint32_t r = b0 + threadIdx.x;
-    if (threadIdx.x == 0) {
-        s_vp[0] = vp_of_record(a.vps, a.n_vps, b0);
-        s_vp[1] = vp_of_record(a.vps, a.n_vps, min(b0 + (uint32_t)kSegThreads, a.n_records) - 1);
-    }
-    int vp = 0;
-    uint32_t cnt = 0;
-    if (r < a.n_records) {
-        const int c = a.counts[r];
-        const int rv = c > 0 ? vp_of_record(a.vps, a.n_vps, r) : 0;
-        const SegRect q = c > 0 ? seg_rect(a.rec, r) : SegRect{0, 0, 0, 0};
-        if (c > 0 && seg_valid(q, a.vps[rv], c)) {
-            cnt = (uint32_t)c;
-            vp = rv;
-            const VpDesc &d = a.vps[vp];
-            const uint32_t w1 = (uint32_t)d.TX + 1;
-            uint32_t *g = a.seg_diff + d.diff_base;
-            atomicAdd(g + q.y0 * w1 + q.x0, 1u);
-            atomicAdd(g + q.y1 * w1 + q.x1, 1u);
-            atomicAdd(g + q.y0 * w1 + q.x1, 0xffffffffu);
-            atomicAdd(g + q.y1 * w1 + q.x0, 0xffffffffu);
-        }
-    }
-    __syncthreads();
-    unsigned long long *tot = a.seg_hdr + 1;
-    if (s_vp[0] != s_vp[1]) {
-        if (cnt)
-            atomicAdd(tot + vp, (unsigned long long)cnt);
+    const uint32_t r = blockIdx.x * kSegThreads + threadIdx.x;
+    if (r >= a.n_records)
         return;
+    const int c = a.counts[r];
+    const int vp = c > 0 ? vp_of_record(a.vps, a.n_vps, r) : 0;
+    const VpDesc &d = a.vps[vp];
+    const SegRect q = c > 0 ? seg_rect(a.rec, r) : SegRect{0, 0, 0, 0};
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (c > 0 && seg_valid(q, d, c)) {
+        const uint32_t w1 = (uint32_t)d.TX + 1;
+        uint32_t *g = a.seg_diff + d.diff_base;
+        atomicAdd(g + q.y0 * w1 + q.x0, 1u);
+        atomicAdd(g + q.y1 * w1 + q.x1, 1u);
+        atomicAdd(g + q.y0 * w1 + q.x1, 0xffffffffu);
+        atomicAdd(g + q.y1 * w1 + q.x0, 0xffffffffu);
+        e = make_uint4(__float_as_uint(a.rec[3 * (size_t)r + 1].z), d.tile_base + q.y0 * (uint32_t)d.TX + q.x0,
+                       (q.x1 - q.x0) | ((q.y1 - q.y0) << 16), (uint32_t)d.TX);
     }
-    const unsigned long long w = warp_sum((unsigned long long)cnt);
-    if ((threadIdx.x & 31) == 0)
-        s_sum[threadIdx.x >> 5] = w;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-#pragma unroll
-        for (int k = 0; k < kSegThreads / 32; ++k)
-            t += s_sum[k];
-        if (t)
-            atomicAdd(tot + s_vp[0], t);
-    }
+    a.seg_list[r] = e;
 }
 
 constexpr int kSegTileThreads = 512;
@@ -807,43 +781,21 @@ __device__ __forceinline__ unsigned long long block_incl_scan(unsigned long long
     return r;
 }
 
-// One CTA per keyframe: 2-D prefix sums of its grid (rows, then columns)
-// give the tile counts; an exclusive scan in tile order, offset by the
-// totals of the earlier keyframes, gives each tile's start.  Writes the
-// ranges ((0, 0) when empty; clipped to the capacity), the placement
-// cursors, and (CTA 0) the duplicate total and the capacity flag.  SMEM:
-// the grid's TY x TX counting cells are copied to shared memory (dynamic,
-// a.seg_max_cells words); otherwise the prefix sums run in place in global
-// memory.
+// One CTA per keyframe: 2-D prefix sums of its difference grid (rows, then
+// columns) turn it into the tile counts, written back in place, and the
+// keyframe's duplicate total goes to seg_hdr[1 + v].  SMEM: the TY x TX
+// counting cells are summed in shared memory (dynamic, a.seg_max_cells
+// words); otherwise in place in global memory.
 template <bool SMEM>
-__global__ void __launch_bounds__(kSegTileThreads) k_seg_tiles(const gsl::BinArgs a)
+__global__ void __launch_bounds__(kSegTileThreads) k_seg_count(const gsl::BinArgs a)
 {
     extern __shared__ uint32_t s_grid[];
     __shared__ unsigned long long s_w[kSegTileThreads / 32];
-    __shared__ unsigned long long s_base;
     const int v = blockIdx.x;
     const VpDesc &d = a.vps[v];
     const int TX = d.TX, TY = d.TY, w1 = TX + 1;
     uint32_t *g = a.seg_diff + d.diff_base;
-    const unsigned long long *tot = a.seg_hdr + 1;
-    unsigned long long before = 0, all = 0;
-    for (int k = threadIdx.x; k < a.n_vps; k += blockDim.x) {
-        const unsigned long long t = tot[k];
-        before += k < v ? t : 0ull;
-        all += t;
-    }
-    const unsigned long long base = block_incl_scan(before, s_w);
-    const unsigned long long grand = block_incl_scan(all, s_w);
-    if (threadIdx.x == kSegTileThreads - 1) {
-        s_base = base;
-        if (v == 0) {
-            *a.n_dups = grand < 0xffffffffull ? (uint32_t)grand : 0xffffffffu;
-            if (grand > a.capacity)
-                atomicOr(a.flags, kFlagCapacity);
-        }
-    }
     const uint32_t nt = (uint32_t)TX * (uint32_t)TY;
-    // cell (y, x) of the counting grid: compact TY x TX in shared memory, or the pitched grid itself
     uint32_t *c = SMEM ? s_grid : g;
     const int pitch = SMEM ? TX : w1;
     if (SMEM) {
@@ -868,10 +820,54 @@ __global__ void __launch_bounds__(kSegTileThreads) k_seg_tiles(const gsl::BinArg
         }
     }
     __syncthreads();
+    unsigned long long sum = 0;
+    for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x) {
+        const uint32_t y = i / (uint32_t)TX, x = i % (uint32_t)TX;
+        const uint32_t n = c[(size_t)y * pitch + x];
+        if (SMEM)
+            g[(size_t)y * w1 + x] = n;
+        sum += n;
+    }
+    const unsigned long long tot = block_incl_scan(sum, s_w);
+    if (threadIdx.x == kSegTileThreads - 1)
+        a.seg_hdr[1 + v] = tot;
+}
+
+// One CTA per keyframe: an exclusive scan of its tile counts in tile order,
+// offset by the totals of the earlier keyframes, gives each tile's start.
+// Writes the ranges ((0, 0) when empty; clipped to the capacity), the
+// placement cursors, and (CTA 0) the duplicate total and the capacity flag.
+__global__ void __launch_bounds__(kSegTileThreads) k_seg_ranges(const gsl::BinArgs a)
+{
+    __shared__ unsigned long long s_w[kSegTileThreads / 32];
+    __shared__ unsigned long long s_base;
+    const int v = blockIdx.x;
+    const VpDesc &d = a.vps[v];
+    const int TX = d.TX, w1 = TX + 1;
+    const uint32_t *g = a.seg_diff + d.diff_base;
+    const unsigned long long *tot = a.seg_hdr + 1;
+    unsigned long long before = 0, all = 0;
+    for (int k = threadIdx.x; k < a.n_vps; k += blockDim.x) {
+        const unsigned long long t = tot[k];
+        before += k < v ? t : 0ull;
+        all += t;
+    }
+    const unsigned long long base = block_incl_scan(before, s_w);
+    const unsigned long long grand = block_incl_scan(all, s_w);
+    if (threadIdx.x == kSegTileThreads - 1) {
+        s_base = base;
+        if (v == 0) {
+            *a.n_dups = grand < 0xffffffffull ? (uint32_t)grand : 0xffffffffu;
+            if (grand > a.capacity)
+                atomicOr(a.flags, kFlagCapacity);
+        }
+    }
+    __syncthreads();
     // each thread scans a contiguous run of tiles; one block scan joins the runs
+    const uint32_t nt = (uint32_t)TX * (uint32_t)d.TY;
     const uint32_t per = (nt + kSegTileThreads - 1) / kSegTileThreads;
     const uint32_t l0 = min(threadIdx.x * per, nt), l1 = min(l0 + per, nt);
-    auto cell = [&](uint32_t lt) { return c[(size_t)(lt / (uint32_t)TX) * pitch + lt % (uint32_t)TX]; };
+    auto cell = [&](uint32_t lt) { return g[(size_t)(lt / (uint32_t)TX) * w1 + lt % (uint32_t)TX]; };
     unsigned long long run = 0;
     for (uint32_t lt = l0; lt < l1; ++lt)
         run += cell(lt);
@@ -900,32 +896,31 @@ __device__ __forceinline__ void seg_put(const gsl::BinArgs &a, uint32_t t, uint3
     }
 }
 
-// One thread per record: each visible record writes (depth bits, record)
-// into the lists of the tiles of its rectangle at positions taken from the
-// tiles' cursors.  Records with more than kSegSmall tiles are spread over
-// the lanes of their warp, one record at a time, so a splat covering
-// thousands of tiles does not serialise one thread.  Positions at or past
-// the capacity are dropped (the capacity flag is already set).
+// One thread per record: a visible one writes (depth bits, record) into the
+// lists of the tiles of its rectangle (from its seg_list entry) at positions
+// taken from the tiles' cursors, all cursor atomics in flight before the
+// stores.
+// Entries with more than kSegSmall tiles are spread over the lanes of their
+// warp, one entry at a time, so a splat covering thousands of tiles does not
+// serialise one thread.  Positions at or past the capacity are dropped (the
+// capacity flag is already set).
 __global__ void __launch_bounds__(kSegThreads) k_seg_place(const gsl::BinArgs a)
 {
     const uint32_t r = blockIdx.x * kSegThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
     uint32_t cnt = 0, t0 = 0, w = 1, tx = 0, zb = 0;
     if (r < a.n_records) {
-        const int c = a.counts[r];
-        const VpDesc &d = a.vps[c > 0 ? vp_of_record(a.vps, a.n_vps, r) : 0];
-        const SegRect q = c > 0 ? seg_rect(a.rec, r) : SegRect{0, 0, 0, 0};
-        if (c > 0 && seg_valid(q, d, c)) {
-            cnt = (uint32_t)c;
-            tx = (uint32_t)d.TX;
-            t0 = d.tile_base + q.y0 * tx + q.x0;
-            w = q.x1 - q.x0;
-            zb = __float_as_uint(a.rec[3 * (size_t)r + 1].z);
+        const uint4 e = a.seg_list[r];
+        if (e.z) {
+            zb = e.x;
+            t0 = e.y;
+            w = e.z & 0xffffu;
+            cnt = w * (e.z >> 16);
+            tx = e.w;
         }
     }
     const bool big = cnt > kSegSmall;
     if (!big) {
-        // all cursor atomics first (independent, so in flight together), then the stores
         uint32_t pos[kSegSmall];
         uint32_t col = 0, row = t0;
 #pragma unroll
@@ -1252,18 +1247,22 @@ size_t seg_zero_bytes(int n_vps, uint64_t n_diff)
 
 int bin_seg(const BinArgs &a, cudaStream_t s)
 {
-    cudaMemsetAsync(a.seg_hdr, 0, a.seg_zero_bytes, s);
+    if (!a.seg_counted)
+        cudaMemsetAsync(a.seg_hdr, 0, a.seg_zero_bytes, s);
     if (a.n_vps == 0) {
         cudaMemsetAsync(a.n_dups, 0, sizeof(uint32_t), s);
         return 0;
     }
-    if (a.n_records)
-        k_seg_diff<<<div_up(a.n_records, kSegThreads), kSegThreads, 0, s>>>(a);
+    if (a.n_records && !a.seg_counted) {
+        k_seg_collect<<<div_up(a.n_records, kSegThreads), kSegThreads, 0, s>>>(a);
+        ++g_launches;
+    }
     if (a.seg_max_cells * sizeof(uint32_t) <= 40 * 1024)
-        k_seg_tiles<true><<<a.n_vps, kSegTileThreads, a.seg_max_cells * sizeof(uint32_t), s>>>(a);
+        k_seg_count<true><<<a.n_vps, kSegTileThreads, a.seg_max_cells * sizeof(uint32_t), s>>>(a);
     else
-        k_seg_tiles<false><<<a.n_vps, kSegTileThreads, 0, s>>>(a);
-    g_launches += 1 + (a.n_records ? 1 : 0);
+        k_seg_count<false><<<a.n_vps, kSegTileThreads, 0, s>>>(a);
+    k_seg_ranges<<<a.n_vps, kSegTileThreads, 0, s>>>(a);
+    g_launches += 2;
     if (a.n_records) {
         k_seg_place<<<div_up(a.n_records, kSegThreads), kSegThreads, 0, s>>>(a);
         ++g_launches;

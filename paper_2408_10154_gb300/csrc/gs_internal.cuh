@@ -192,6 +192,14 @@ struct ProjectArgs {
     // compositing is unchanged; the lists are no longer those of gs_bin.
     int tight;
     float skip_below;         // ln(alpha_min) - 0.05
+    // segmented tile lists (null: not built here): clears seg_hdr/seg_diff
+    // (seg_zero_bytes), then every visible record adds its rectangle to its
+    // keyframe's difference grid, and every record writes its seg_list
+    // entry (see BinArgs)
+    unsigned long long *seg_hdr;
+    uint32_t *seg_diff;
+    size_t seg_zero_bytes;
+    uint4 *seg_list;
 };
 void project(const ProjectArgs &a, cudaStream_t s);
 
@@ -226,10 +234,16 @@ struct BinArgs {
     // segmented build (bin_seg): seg_hdr[0] counts the tiles queued for the
     // long-list sort, seg_hdr[1 + v] holds keyframe v's duplicate total, and
     // the difference grids (VpDesc::diff_base) follow in the same allocation
-    // of seg_zero_bytes, cleared at the start of every build
+    // of seg_zero_bytes, cleared at the start of every build.  seg_list: per
+    // record {depth bits, first tile, width | height << 16, tiles per row}
+    // (size 0: not visible).  seg_counted: the projection has already
+    // cleared, counted and written the entries (ProjectArgs::seg_*);
+    // otherwise bin_seg does it from rec / counts.
     unsigned long long *seg_hdr;
     uint32_t *seg_diff;
     size_t seg_zero_bytes;
+    uint4 *seg_list;     // [n_records]
+    int seg_counted;
     uint32_t *seg_cursor;  // [n_tiles] placement cursors
     uint32_t *seg_big;     // [n_tiles] tiles whose lists exceed the warp sort
     uint32_t seg_max_cells;  // largest TX * TY over the keyframes

@@ -54,6 +54,30 @@ __device__ __forceinline__ void tighten(float ca, float cb, float cc, float o, f
     y1 = min(y1, (int)ty1);
 }
 
+// Segmented lists: a visible record (count > 0) adds +1 at (y0, x0) and
+// (y1, x1) and -1 (mod 2^32) at (y0, x1) and (y1, x0) of its keyframe's
+// (TY + 1) x (TX + 1) difference grid, whose 2-D prefix sum is the tile
+// count; every record writes its entry {depth bits, first tile, width |
+// height << 16, tiles per row} (size 0 when not visible).
+__device__ __forceinline__ void seg_note(const gsl::ProjectArgs &a, const int *geo, uint32_t rec, float z, int count,
+                                         int x0, int x1, int y0, int y1)
+{
+    const bool vis = count > 0;
+    const int TX = geo[0];
+    if (vis) {
+        const uint32_t w1 = (uint32_t)TX + 1;
+        uint32_t *g = a.seg_diff + (uint32_t)geo[4];
+        atomicAdd(g + (uint32_t)y0 * w1 + (uint32_t)x0, 1u);
+        atomicAdd(g + (uint32_t)y1 * w1 + (uint32_t)x1, 1u);
+        atomicAdd(g + (uint32_t)y0 * w1 + (uint32_t)x1, 0xffffffffu);
+        atomicAdd(g + (uint32_t)y1 * w1 + (uint32_t)x0, 0xffffffffu);
+    }
+    a.seg_list[rec] = vis ? make_uint4(__float_as_uint(z),
+                                           (uint32_t)geo[3] + (uint32_t)y0 * (uint32_t)TX + (uint32_t)x0,
+                                           (uint32_t)(x1 - x0) | ((uint32_t)(y1 - y0) << 16), (uint32_t)TX)
+                              : make_uint4(0u, 0u, 0u, 0u);
+}
+
 __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
 {
     // locate the group of this block (groups are few; linear scan)
@@ -63,7 +87,7 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
     const GroupDesc G = a.groups[gi];
     __shared__ float sM[kMaxVpPerGroup][12];
     __shared__ float sCam[kMaxVpPerGroup][4];  // fx, fy, cx, cy
-    __shared__ int sGeo[kMaxVpPerGroup][4];    // TX, TY, rec_base, unused
+    __shared__ int sGeo[kMaxVpPerGroup][6];    // TX, TY, rec_base, tile_base, diff_base, unused
     for (int v = threadIdx.x; v < G.vp_count; v += blockDim.x) {
         const int vp = G.vp_first + v;
         const VpDesc &d = a.vps[vp];
@@ -84,6 +108,8 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
         sGeo[v][0] = d.TX;
         sGeo[v][1] = d.TY;
         sGeo[v][2] = (int)d.rec_base;
+        sGeo[v][3] = (int)d.tile_base;
+        sGeo[v][4] = (int)d.diff_base;
     }
     __syncthreads();
     const int i = (int)(blockIdx.x - G.blk_base) * blockDim.x + threadIdx.x;
@@ -130,6 +156,7 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
         const float y = fma_rn(M[6], mu.z, fma_rn(M[5], mu.y, fma_rn(M[4], mu.x, M[7])));
         const float z = fma_rn(M[10], mu.z, fma_rn(M[9], mu.y, fma_rn(M[8], mu.x, M[11])));
         int count = 0;
+        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
         if (z > a.z_near && qok) {
             float A[3][3];
 #pragma unroll
@@ -172,7 +199,6 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
                 const float vv = fma_rn(fy, ty, cy);
                 if (rf < 1.0e7f && fabsf(u) < 1.0e7f && fabsf(vv) < 1.0e7f) {
                     const int TX = sGeo[v][0], TY = sGeo[v][1];
-                    int x0, x1, y0, y1;
                     if (a.smooth) {
                         x0 = 0; x1 = TX; y0 = 0; y1 = TY;
                     } else {
@@ -203,6 +229,8 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
             }
         }
         a.counts[rec] = count;
+        if (a.seg_hdr)
+            seg_note(a, sGeo[v], rec, z, count, x0, x1, y0, y1);
     }
 }
 
@@ -212,6 +240,8 @@ namespace gsl {
 
 void project(const ProjectArgs &a, cudaStream_t s)
 {
+    if (a.seg_hdr)
+        cudaMemsetAsync(a.seg_hdr, 0, a.seg_zero_bytes, s);
     if (a.n_blocks == 0)
         return;
     k_project<<<a.n_blocks, 256, 0, s>>>(a);
