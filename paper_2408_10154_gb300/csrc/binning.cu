@@ -981,6 +981,70 @@ __device__ __forceinline__ unsigned long long warp_bitonic32(unsigned long long 
     return x;
 }
 
+// 32 K keys in registers, element k * 32 + lane in slot k of its lane
+// (positions past the list hold ~0): the same network, with exchanges at
+// distances below 32 done by shuffles and at 32 and above inside a lane.
+template <int K>
+__device__ __forceinline__ void warp_bitonic_reg(unsigned long long (&x)[K], int lane)
+{
+    auto pick = [](unsigned long long u, unsigned long long v, bool lower) {
+        return lower ? (v < u ? v : u) : (v > u ? v : u);
+    };
+#pragma unroll
+    for (int size = 2; size <= 32 * K; size <<= 1) {
+        if (size <= 32) {
+            const bool lower = (lane & (size >> 1)) == 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                x[k] = pick(x[k], __shfl_xor_sync(0xffffffffu, x[k], size - 1), lower);
+        } else {
+            // partner of k * 32 + lane: slot k ^ (size / 32 - 1) of lane ^ 31
+            unsigned long long y[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                y[k] = __shfl_xor_sync(0xffffffffu, x[k ^ (size / 32 - 1)], 31);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                x[k] = pick(x[k], y[k], (k & (size / 64)) == 0);
+        }
+#pragma unroll
+        for (int j = size >> 2; j >= 1; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if ((k & (j / 32)) == 0) {
+                        const unsigned long long u = x[k], v = x[k | (j / 32)];
+                        x[k] = v < u ? v : u;
+                        x[k | (j / 32)] = v < u ? u : v;
+                    }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    x[k] = pick(x[k], __shfl_xor_sync(0xffffffffu, x[k], j), lower);
+            }
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void sort_list_reg(const uint32_t *keys, uint32_t *vals, uint32_t n, int lane)
+{
+    unsigned long long x[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t e = (uint32_t)(k * 32 + lane);
+        x[k] = e < n ? (((unsigned long long)keys[e] << 32) | vals[e]) : ~0ull;
+    }
+    warp_bitonic_reg<K>(x, lane);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t e = (uint32_t)(k * 32 + lane);
+        if (e < n)
+            vals[e] = (uint32_t)x[k];
+    }
+}
+
 __device__ __forceinline__ void cex(unsigned long long *s, int i, int p)
 {
     const unsigned long long u = s[i], v = s[p];
@@ -993,8 +1057,9 @@ __device__ __forceinline__ void cex(unsigned long long *s, int i, int p)
 constexpr int kSegSortWarps = 8;
 constexpr int kSegSortCap = 512;  // longest list sorted by one warp in shared memory
 
-// One warp per tile: lists of up to 32 entries are sorted in registers,
-// up to kSegSortCap in shared memory (padded with ~0 to a power of two);
+// One warp per tile: lists of up to 256 entries are sorted in registers (up
+// to 8 per lane), up to kSegSortCap in shared memory (padded with ~0 to a
+// power of two);
 // longer lists are queued for k_seg_sort_big.  The sorted record indices
 // replace the tile's values in place.
 __global__ void __launch_bounds__(kSegSortWarps * 32) k_seg_sort(const gsl::BinArgs a)
@@ -1019,12 +1084,24 @@ __global__ void __launch_bounds__(kSegSortWarps * 32) k_seg_sort(const gsl::BinA
             vals[lane] = (uint32_t)x;
         return;
     }
+    if (n <= 64) {
+        sort_list_reg<2>(keys, vals, n, lane);
+        return;
+    }
+    if (n <= 128) {
+        sort_list_reg<4>(keys, vals, n, lane);
+        return;
+    }
+    if (n <= 256) {
+        sort_list_reg<8>(keys, vals, n, lane);
+        return;
+    }
     if (n > (uint32_t)kSegSortCap) {
         if (lane == 0)
             a.seg_big[atomicAdd(a.seg_hdr, 1ull)] = t;
         return;
     }
-    int N = 64;
+    int N = 512;
     while ((uint32_t)N < n)
         N <<= 1;
     unsigned long long *sk = s_k[warp];

@@ -165,6 +165,25 @@ def test_binning_bit_exact_room_full_size(gs, ctx):
     assert check_binning(gs, ctx, gd, cams, poses) > 100_000
 
 
+def dense_case(n):
+    # n Gaussians of ~5 px in a 10 cm cube 2 m in front of a 64 x 48 image:
+    # every one of the 12 tiles lists most of them (n = 400: lists of a few
+    # hundred entries; n = 3000: thousands, past the per-warp sorts)
+    c = synth.small_case(n, 64, 48, 200.0, n_views=2, seed=31, ls_mean=-3.0, ls_std=0.2, half=0.05)
+    return c["gaussians"], c["cams"]
+
+
+@pytest.mark.parametrize("n", [400, 3000])
+def test_binning_long_tile_lists(gs, ctx, n):
+    gd, cams = dense_case(n)
+    poses = rand_poses(np.random.default_rng(5), len(cams), 1.0, 0.005)
+    assert check_binning(gs, ctx, gd, cams, poses) > 0
+    _, _, ranges = O.bin_tiles(O.Gaussians.from_dict(gd), np.stack([f32pose(p) for p in poses]), cams)
+    longest = int((ranges[:, 1] - ranges[:, 0]).max())
+    assert longest > (256 if n == 400 else 512), longest
+    check_render(gs, ctx, gd, cams, poses)
+
+
 def test_binning_empty(gs, ctx):
     gd, cams = plain_case()
     poses = np.stack([np.eye(3, 4)] * 4)
