@@ -20,10 +20,10 @@
 namespace {
 
 enum Slot {
-    S_VPS, S_GROUPS, S_TILEVP, S_POSE32, S_REC, S_AUX, S_COUNTS, S_PARTIALS, S_NDUPS, S_K0, S_K1, S_V0, S_V1,
+    S_VPS, S_GROUPS, S_TILEVP, S_POSE32, S_REC, S_AUX, S_COUNTS, S_PARTIALS, S_NDUPS, S_K0, S_V0, S_V1,
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
-    S_PAIRS, S_DK0, S_DK1, S_DV0, S_DV1, S_NVIS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
+    S_PAIRS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
     S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_SEGZ, S_SEGCUR, S_SEGBIG, S_SEGLIST, S_COUNT
 };
 
@@ -322,12 +322,8 @@ struct Pipe {
     uint2 *ranges = nullptr;
     int *flags = nullptr;
     uint32_t cap = 0;
-    // two-stage binning (gs_bin)
-    uint32_t *dkeys[2] = {nullptr, nullptr}, *dvals[2] = {nullptr, nullptr};
     uint32_t *tkeys[2] = {nullptr, nullptr};
-    uint32_t *n_vis = nullptr;
     uint64_t n_records = 0;
-    uint8_t *os = nullptr;  // one-sweep sort state
     // segmented build
     unsigned long long *seg_hdr = nullptr;
     uint32_t *seg_diff = nullptr, *seg_cursor = nullptr, *seg_big = nullptr;
@@ -335,14 +331,12 @@ struct Pipe {
     size_t seg_zero = 0;
 };
 
-// Binning routes.  The context-based entry points use the segmented build
-// (per-tile counts from difference grids of the records' tile rectangles,
-// atomic placement, a sort of each short tile list): no global sort at
-// all.  gs_bin, which bins the caller's records, keeps the two-stage route
-// (depth sort of the visible records, then a stable tile sort of 32-bit
-// keys), and gs_render_noalloc the one-stage route (one sort of 64-bit
-// (tile, depth) keys); all three yield the same lists, which their tests
-// cross-check.
+// Binning routes.  The context-based entry points and gs_bin use the
+// segmented build (per-tile counts from difference grids of the records'
+// tile rectangles, atomic placement, a sort of each short tile list): no
+// global sort at all.  gs_render_noalloc keeps the one-stage route (one
+// radix sort of 64-bit (tile, depth) keys), which needs less scratch; both
+// yield the same lists, which the tests cross-check.
 
 // scratch of the segmented build: cleared header + difference grids,
 // visible-record list, cursors, long-list queue
@@ -382,7 +376,6 @@ gs_status_t alloc_sort(gs_ctx *ctx, uint64_t want, Pipe &p)
         return fail(ctx, GS_ERR_CAPACITY, "more than 2^32 tile duplicates");
     const uint32_t cap = (uint32_t)std::max<uint64_t>(want, 1024);
     GS_TRY(wsT(ctx, S_K0, cap, &p.tkeys[0]));
-    GS_TRY(wsT(ctx, S_K1, cap, &p.tkeys[1]));
     GS_TRY(wsT(ctx, S_V0, cap, &p.vals[0]));
     GS_TRY(wsT(ctx, S_V1, cap, &p.vals[1]));
     const size_t hn = gsl::sort_hist_entries((uint32_t)std::max<uint64_t>(cap, p.n_records));
@@ -441,13 +434,7 @@ gsl::BinArgs bin_args(const Plan &P, const DevPlan &D, const Pipe &p)
     b.ranges = p.ranges;
     b.n_tiles = (uint32_t)P.n_tiles;
     b.flags = p.flags;
-    for (int k = 0; k < 2; ++k) {
-        b.dkeys[k] = p.dkeys[k];
-        b.dvals[k] = p.dvals[k];
-        b.tkeys[k] = p.tkeys[k];
-    }
-    b.n_vis = p.n_vis;
-    b.os_scratch = p.os;
+    b.tkeys[0] = p.tkeys[0];
     b.seg_hdr = p.seg_hdr;
     b.seg_diff = p.seg_diff;
     b.seg_zero_bytes = p.seg_zero;

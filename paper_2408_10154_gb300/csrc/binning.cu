@@ -1,12 +1,19 @@
-// binning.cu -- tile binning: exclusive scan of tiles-touched counts,
-// duplicate emission with 64-bit (tile << 32 | depth bits) keys, stable LSD
-// radix sort over the needed key bits, per-tile [start, end) ranges.
+// binning.cu -- tile lists: for every tile, the records whose tile
+// rectangle covers it, ordered by (depth bits, record index).
 //
-// All sizes that depend on the data (the number of duplicates) live on the
-// device, so the whole sequence can be captured in a CUDA graph: grids are
-// sized for the capacity and blocks past the live count exit early.
-// HBM-bound throughout: the sort moves 8 B key + 4 B value in and out per
-// duplicate per 8-bit pass.
+// Segmented build (the context paths and gs_bin): per-keyframe 2-D
+// difference grids of the records' rectangles give every tile's list length
+// and start without sorting the duplicates; records are placed into their
+// tiles through per-tile atomic cursors and each short list is then sorted
+// on its own (registers, shared memory, or global memory for the rare long
+// list).  One-stage route (gs_render_noalloc): exclusive scan of the
+// tiles-touched counts, emission of 64-bit (tile << 32 | depth bits) keys,
+// stable LSD radix sort, per-tile ranges.  Also the one-sweep LSD radix sort
+// of 32-bit keys (gs_sort_u32) and the longest-first tile schedule.
+//
+// All sizes that depend on the data live on the device, so every sequence
+// can be captured in a CUDA graph: grids are sized for the capacity and
+// blocks past the live count exit early.
 #include "gs_internal.cuh"
 
 namespace {
@@ -295,161 +302,6 @@ __global__ void k_ranges(const K *keys, const uint32_t *n_dups, uint32_t cap, ui
 // record index), the same as a stable sort of (tile << 32 | depth) keys
 // emitted in record order, with 4-byte keys and 2 tile passes instead of 6
 // passes over 8-byte keys.
-
-// visible records per block of kScanTile records
-__global__ void __launch_bounds__(kScanThreads) k_vis_partials(const int32_t *counts, uint32_t n, uint32_t *partials)
-{
-    __shared__ uint32_t s[kScanThreads / 32];
-    const uint32_t base = blockIdx.x * kScanTile;
-    uint32_t acc = 0;
-#pragma unroll
-    for (int k = 0; k < kScanTile / kScanThreads; ++k) {
-        const uint32_t i = base + k * kScanThreads + threadIdx.x;
-        acc += (i < n && counts[i] > 0) ? 1u : 0u;
-    }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0)
-        s[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t v = threadIdx.x < kScanThreads / 32 ? s[threadIdx.x] : 0u;
-        v = warp_sum(v);
-        if (threadIdx.x == 0)
-            partials[blockIdx.x] = v;
-    }
-}
-
-// compacts the visible records (record order) with their depth bits
-__global__ void __launch_bounds__(kScanThreads) k_vis_compact(const int32_t *counts, const float4 *rec, uint32_t n,
-                                                             const uint32_t *blk_base, uint32_t *dkeys, uint32_t *dvals)
-{
-    __shared__ uint32_t s_warp[kScanThreads / 32 + 1];
-    constexpr int K = kScanTile / kScanThreads;
-    const uint32_t first = blockIdx.x * kScanTile + threadIdx.x * K;
-    uint32_t f[K], sum = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        f[k] = (first + k < n && counts[first + k] > 0) ? 1u : 0u;
-        sum += f[k];
-    }
-    uint32_t tot;
-    uint32_t pos = block_excl_scan<kScanThreads>(sum, s_warp, tot) + blk_base[blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        if (f[k]) {
-            const uint32_t r = first + k;
-            dkeys[pos] = __float_as_uint(rec[3 * (size_t)r + 1].z);
-            dvals[pos] = r;
-            ++pos;
-        }
-    }
-}
-
-// tile count of each depth-sorted visible record (0 past the live count)
-__global__ void k_sorted_counts(const int32_t *counts, const uint32_t *dvals, const uint32_t *n_vis, uint32_t n,
-                                uint32_t *out)
-{
-    const uint32_t nv = live_count(n_vis, n);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n)
-        out[i] = i < nv ? (uint32_t)counts[dvals[i]] : 0u;
-}
-
-// largest i in [0, n) with a[i] <= t, for non-decreasing a with a[0] <= t:
-// a 32-ary search by one warp (each round narrows the range 32-fold)
-__device__ __forceinline__ uint32_t warp_last_le(const uint32_t *a, uint32_t n, uint32_t t)
-{
-    const uint32_t lane = threadIdx.x & 31;
-    uint32_t lo = 0, hi = n;
-    while (hi - lo > 32) {
-        const uint32_t step = (hi - lo + 31) / 32;
-        const uint32_t p = lo + lane * step;
-        const unsigned m = __ballot_sync(0xffffffffu, p < hi && a[p] <= t) | 1u;
-        const uint32_t nlo = lo + (uint32_t)(31 - __clz(m)) * step;
-        hi = min(nlo + step, hi);
-        lo = nlo;
-    }
-    const uint32_t p = lo + lane;
-    const unsigned m = __ballot_sync(0xffffffffu, p < hi && a[p] <= t) | 1u;
-    return lo + (uint32_t)(31 - __clz(m));
-}
-
-// Emits the duplicates [b*kScanTile, (b+1)*kScanTile) of the depth-sorted
-// visible records (offsets = exclusive scan of their tile counts) with
-// 32-bit tile keys.  Work is split by duplicates, not by records, so the
-// few near-camera splats covering thousands of tiles (all at the front of
-// the depth order) do not serialise one block.  A block touches at most
-// kScanTile records because every visible record has at least one tile.
-__global__ void __launch_bounds__(kScanThreads) k_emit_balanced(const gsl::BinArgs a, const uint32_t *dvals,
-                                                               const uint32_t *offs, uint32_t *tkeys, uint32_t *vals)
-{
-    __shared__ uint32_t s_off[kScanTile];
-    __shared__ uint32_t s_t0[kScanTile];
-    __shared__ uint32_t s_geo[kScanTile];
-    __shared__ uint32_t s_rec[kScanTile];
-    __shared__ uint32_t s_r[2];
-    const uint32_t total = *a.n_dups;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && total > a.capacity)
-        atomicOr(a.flags, kFlagCapacity);
-    const uint32_t nd = total < a.capacity ? total : a.capacity;
-    const uint32_t b0 = blockIdx.x * kScanTile;
-    if (b0 >= nd)
-        return;
-    const uint32_t b1 = min(b0 + (uint32_t)kScanTile, nd);
-    const uint32_t nv = live_count(a.n_vis, a.n_records);
-    if (nv == 0)
-        return;
-    if (threadIdx.x < 64) {
-        const uint32_t r = warp_last_le(offs, nv, threadIdx.x < 32 ? b0 : b1 - 1);
-        if ((threadIdx.x & 31) == 0)
-            s_r[threadIdx.x >> 5] = r;
-    }
-    __syncthreads();
-    const uint32_t r0 = s_r[0];
-    if (s_r[1] < r0 || s_r[1] - r0 >= (uint32_t)kScanTile)
-        return;  // offsets not monotone (a saturated count): nothing sound to emit
-    const uint32_t nr = s_r[1] - r0 + 1;
-    for (uint32_t k = threadIdx.x; k < nr; k += blockDim.x) {
-        const uint32_t r = dvals[r0 + k];
-        // keyframe of record r: the last vp whose records start at or before r
-        int lo = 0, hi = a.n_vps - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.vps[mid].rec_base <= r) lo = mid; else hi = mid - 1;
-        }
-        const gsk::VpDesc &d = a.vps[lo];
-        const uint32_t rx = __float_as_uint(a.rec[3 * (size_t)r + 1].w);
-        const uint32_t ry = __float_as_uint(a.rec[3 * (size_t)r + 2].w);
-        const uint32_t x0 = rx & 0xffffu, x1 = rx >> 16, y0 = ry & 0xffffu;
-        s_off[k] = offs[r0 + k];
-        s_t0[k] = d.tile_base + y0 * (uint32_t)d.TX + x0;
-        s_geo[k] = (x1 - x0) | ((uint32_t)d.TX << 16);
-        s_rec[k] = r;
-    }
-    __syncthreads();
-    for (uint32_t j = b0 + threadIdx.x; j < b1; j += blockDim.x) {
-        uint32_t lo = 0, hi = nr - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t local = j - s_off[lo];
-        const uint32_t geo = s_geo[lo];
-        const uint32_t w = geo & 0xffffu, TX = geo >> 16;
-        tkeys[j] = s_t0[lo] + (local / w) * TX + local % w;
-        vals[j] = s_rec[lo];
-    }
-}
-
-// 64-bit (tile << 32 | depth bits) keys of a tile-sorted list (for gs_bin)
-__global__ void k_keys64(const uint32_t *tkeys, const uint32_t *vals, const float4 *rec, const uint32_t *n_dups,
-                         uint32_t cap, uint64_t *keys)
-{
-    const uint32_t n = live_count(n_dups, cap);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n)
-        keys[i] = ((uint64_t)tkeys[i] << 32) | __float_as_uint(rec[3 * (size_t)vals[i] + 1].z);
-}
 
 inline uint32_t div_up(size_t a, size_t b) { return (uint32_t)((a + b - 1) / b); }
 
@@ -1285,38 +1137,6 @@ int sort_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32
     return radix_sort<uint32_t>(keys, vals, n_dev, cap, bits, hist, hist_partials, s);
 }
 
-int bin2(const BinArgs &a, cudaStream_t s)
-{
-    const uint32_t R = a.n_records;
-    const uint32_t nb = div_up(R ? R : 1, kScanTile);
-    k_vis_partials<<<nb, kScanThreads, 0, s>>>(a.counts, R, a.partials);
-    k_scan_top<<<1, 1024, 0, s>>>(a.partials, nb, a.n_vis);
-    k_vis_compact<<<nb, kScanThreads, 0, s>>>(a.counts, a.rec, R, a.partials, a.dkeys[0], a.dvals[0]);
-    g_launches += 3;
-    uint32_t *dk[2] = {a.dkeys[0], a.dkeys[1]}, *dv[2] = {a.dvals[0], a.dvals[1]};
-    const int dc = a.os_scratch ? onesweep_u32(dk, dv, a.n_vis, R, 32, a.os_scratch, a.flags, s)
-                                : radix_sort<uint32_t>(dk, dv, a.n_vis, R, 32, a.hist, a.hist_partials, s);
-    // tile counts in depth order and their exclusive scan (total = n_dups),
-    // in the depth-key buffers the sort no longer needs
-    uint32_t *cnt = dk[dc], *offs = dk[dc ^ 1];
-    k_sorted_counts<<<div_up(R ? R : 1, 256), 256, 0, s>>>(a.counts, dv[dc], a.n_vis, R, cnt);
-    ++g_launches;
-    scan_excl(cnt, offs, R, a.partials, a.n_dups, s);
-    k_emit_balanced<<<div_up(a.capacity ? a.capacity : 1, kScanTile), kScanThreads, 0, s>>>(a, dv[dc], offs,
-                                                                                          a.tkeys[0], a.vals[0]);
-    ++g_launches;
-    uint32_t *tk[2] = {a.tkeys[0], a.tkeys[1]}, *tv[2] = {a.vals[0], a.vals[1]};
-    const int tc = a.os_scratch
-                       ? onesweep_u32(tk, tv, a.n_dups, a.capacity, a.key_bits - 32, a.os_scratch, a.flags, s)
-                       : radix_sort<uint32_t>(tk, tv, a.n_dups, a.capacity, a.key_bits - 32, a.hist, a.hist_partials,
-                                              s);
-    cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.n_tiles, s);
-    k_ranges<uint32_t><<<div_up(a.capacity ? a.capacity : 1, 256), 256, 0, s>>>(tk[tc], a.n_dups, a.capacity,
-                                                                                a.ranges);
-    ++g_launches;
-    return tc;
-}
-
 size_t seg_zero_bytes(int n_vps, uint64_t n_diff)
 {
     return sizeof(unsigned long long) * (1 + (size_t)n_vps) + sizeof(uint32_t) * (size_t)n_diff;
@@ -1357,13 +1177,6 @@ void seg_keys64(const BinArgs &a, uint64_t *out, cudaStream_t s)
     if (a.n_tiles == 0)
         return;
     k_seg_keys64<<<div_up(a.n_tiles, 8), 256, 0, s>>>(a, out);
-    ++g_launches;
-}
-
-void keys64(const BinArgs &a, int cur, uint64_t *out, cudaStream_t s)
-{
-    k_keys64<<<div_up(a.capacity ? a.capacity : 1, 256), 256, 0, s>>>(a.tkeys[cur], a.vals[cur], a.rec, a.n_dups,
-                                                                      a.capacity, out);
     ++g_launches;
 }
 

@@ -225,12 +225,7 @@ struct BinArgs {
     uint2 *ranges;            // [total tiles]
     uint32_t n_tiles;
     int *flags;
-    // two-stage binning (bin2): depth sort of the visible records, then a
-    // tile sort of 32-bit tile keys
-    uint32_t *dkeys[2], *dvals[2];  // [n_records]
-    uint32_t *tkeys[2];             // [capacity]
-    uint32_t *n_vis;                // device scalar
-    uint8_t *os_scratch;            // one-sweep sort state (onesweep_scratch_bytes), or null = classic passes
+    uint32_t *tkeys[2];             // [capacity] segmented build: depth bits of the placed entries (tkeys[0])
     // segmented build (bin_seg): seg_hdr[0] counts the tiles queued for the
     // long-list sort, seg_hdr[1 + v] holds keyframe v's duplicate total, and
     // the difference grids (VpDesc::diff_base) follow in the same allocation
@@ -250,10 +245,6 @@ struct BinArgs {
 };
 // emits, sorts and ranges; returns which buffer holds the sorted result
 int bin(const BinArgs &a, cudaStream_t s);
-// the same result by the two-stage route (depth sort of visible records,
-// tile sort of duplicates); the sorted values are in vals[return], the tile
-// keys in tkeys[return]
-int bin2(const BinArgs &a, cudaStream_t s);
 // the same lists by the segmented build: per-tile counts from 2-D
 // difference grids of the records' tile rectangles, atomic placement, and a
 // sort of each tile's list by (depth bits, record); sorted values in vals[0]
@@ -276,8 +267,6 @@ void tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t
 size_t onesweep_scratch_bytes(uint32_t cap, int bits);
 int onesweep_u32(uint32_t *keys[2], uint32_t *vals[2], const uint32_t *n_dev, uint32_t cap, int bits,
                  uint8_t *scratch, int *flags, cudaStream_t s, bool withhold_first_tile = false);
-// 64-bit keys (tile << 32 | depth bits) of a bin2 result
-void keys64(const BinArgs &a, int cur, uint64_t *out, cudaStream_t s);
 void bin_count(const BinArgs &a, cudaStream_t s);  // scan only: n_dups
 size_t sort_hist_entries(uint32_t capacity);
 
