@@ -349,10 +349,12 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float bhi, flo
 }
 
 // The tile's twist: each warp reduces its lanes' compensated sums with
-// TwoSum butterflies, lane 0 leaves hi + lo in FP64, and threads 0..5 add
-// the warps in FP64 in a fixed order.
+// TwoSum butterflies, threads 0..5 join the warps' (hi, lo) pairs the same
+// way in a fixed order, and each leaves hi + lo in FP64 (one conversion per
+// component and tile: the FP64 pipe is a small fraction of the FP32 one,
+// and FP64 work in every warp kept it busy and lengthened every CTA's tail).
 template <int WARPS>
-__device__ __forceinline__ void store_tile_twist(const Twist6 &tw, double (*s_tw)[6], double *out)
+__device__ __forceinline__ void store_tile_twist(const Twist6 &tw, float (*s_tw)[6][2], double *out)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -363,16 +365,18 @@ __device__ __forceinline__ void store_tile_twist(const Twist6 &tw, double (*s_tw
             const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
             two_sum_add(hi, lo, bh, bl);
         }
-        if (lane == 0)
-            s_tw[warp][k] = (double)hi + (double)lo;
+        if (lane == 0) {
+            s_tw[warp][k][0] = hi;
+            s_tw[warp][k][1] = lo;
+        }
     }
     __syncthreads();
     if (threadIdx.x < 6) {
-        double s = 0.0;
+        float hi = s_tw[0][threadIdx.x][0], lo = s_tw[0][threadIdx.x][1];
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w)
-            s += s_tw[w][threadIdx.x];
-        out[threadIdx.x] = s;
+        for (int w = 1; w < WARPS; ++w)
+            two_sum_add(hi, lo, s_tw[w][threadIdx.x][0], s_tw[w][threadIdx.x][1]);
+        out[threadIdx.x] = (double)hi + (double)lo;
     }
 }
 
@@ -570,7 +574,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     __shared__ uint32_t s_rec[kBwd2Chunk];
     __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
     __shared__ int s_maxl[kBwd2Warps];
-    __shared__ double s_tw[kBwd2Warps][6];
+    __shared__ float s_tw[kBwd2Warps][6][2];
     const uint32_t t = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
     const int vp = (int)a.tile_vp[t];
     const VpDesc &d = a.vps[vp];
