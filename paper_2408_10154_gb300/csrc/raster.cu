@@ -317,22 +317,32 @@ __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int lane)
     return s;
 }
 
-// Six running FP32 sums with Kahan compensation (the lost low-order part is
-// carried in c); the true sum is s - c.
+constexpr int kBwd2Threads = 128;
+constexpr int kBwd2Warps = kBwd2Threads / 32;
+constexpr int kBwd2Chunk = 128;
+constexpr int kBwd2MinBlocks = 8;
+
+// Six running FP32 sums of one thread with Kahan compensation (the lost
+// low-order part is carried in c; the true sum is s - c), kept in shared
+// memory as [2 k + (0: s, 1: c)][thread]: they are touched once per record
+// at the end of a chunk, and in registers they would stay live across the
+// whole pixel walk.
 struct Twist6 {
-    float s[6], c[6];
-    __device__ __forceinline__ void zero()
+    float *base;  // the thread's column of the block's [12][kBwd2Threads] array
+    __device__ __forceinline__ float &s(int k) const { return base[(2 * k) * kBwd2Threads]; }
+    __device__ __forceinline__ float &c(int k) const { return base[(2 * k + 1) * kBwd2Threads]; }
+    __device__ __forceinline__ void zero() const
     {
 #pragma unroll
         for (int k = 0; k < 6; ++k)
-            s[k] = c[k] = 0.0f;
+            s(k) = c(k) = 0.0f;
     }
-    __device__ __forceinline__ void add(int k, float v)
+    __device__ __forceinline__ void add(int k, float v) const
     {
-        const float y = v - c[k];
-        const float t = s[k] + y;
-        c[k] = (t - s[k]) - y;
-        s[k] = t;
+        const float sk = s(k), y = v - c(k);
+        const float t = sk + y;
+        c(k) = (t - sk) - y;
+        s(k) = t;
     }
 };
 
@@ -359,7 +369,7 @@ __device__ __forceinline__ void store_tile_twist(const Twist6 &tw, float (*s_tw)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        float hi = tw.s[k], lo = -tw.c[k];
+        float hi = tw.s(k), lo = -tw.c(k);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
@@ -396,7 +406,7 @@ __device__ __forceinline__ void load_pivot(const double *c_cam, int vp, float *s
 // 2 dL/dSigma2D_00, 2 dL/dSigma2D_01, 2 dL/dSigma2D_11, dL/dz, ...} (the 2D
 // covariance is the dilated one; dilation is constant).
 __device__ __forceinline__ void chain_twist(const float *G, const float4 &q1, const float4 &x0, const float4 &x1,
-                                            float fx, float fy, const float *cc, Twist6 &tw)
+                                            float fx, float fy, const float *cc, const Twist6 &tw)
 {
     using S = float;
     const S mx = x0.x, my = x0.y, mz = q1.z;
@@ -559,10 +569,6 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     return true;
 }
 
-constexpr int kBwd2Threads = 128;
-constexpr int kBwd2Warps = kBwd2Threads / 32;
-constexpr int kBwd2Chunk = 128;
-constexpr int kBwd2MinBlocks = 7;
 static_assert(kBwd2Chunk <= kBwd2Threads, "one thread stages one record");
 
 template <bool REG, bool FULL>
@@ -607,7 +613,8 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     __shared__ float s_cc[3];
     float cc[3];
     load_pivot(a.c_cam, vp, s_cc, cc);
-    Twist6 tw;
+    __shared__ float s_acc[12][kBwd2Threads];
+    const Twist6 tw{&s_acc[0][threadIdx.x]};
     tw.zero();
     for (int hi = maxl; hi > 0; hi -= kBwd2Chunk) {
         const int lo = max(hi - kBwd2Chunk, 0), cnt = hi - lo;
