@@ -319,7 +319,7 @@ __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int lane)
 
 constexpr int kBwd2Threads = 128;
 constexpr int kBwd2Warps = kBwd2Threads / 32;
-constexpr int kBwd2Chunk = 128;
+constexpr int kBwd2Chunk = 64;
 constexpr int kBwd2MinBlocks = 8;
 
 // Six running FP32 sums of one thread with Kahan compensation (the lost
