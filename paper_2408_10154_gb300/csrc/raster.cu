@@ -454,8 +454,16 @@ __device__ __forceinline__ void chain_twist(const float *G, const float4 &q1, co
 // and their gradients are added before the warp reduction, which therefore
 // covers 64 pixels.
 // ---------------------------------------------------------------------------
+// Per-pixel state of the back-to-front walk.  g = (gr, gg, gb, gd) is the
+// loss gradient w.r.t. the pixel's colour and depth, constant along the
+// walk, so the colour behind the current Gaussian enters dL/dalpha only
+// through Q = g . S, S = sum over the Gaussians behind (and the background)
+// of colour x alpha x transmittance: dL/dalpha_i = T_i (g . c_i) -
+// Q / (1 - alpha_i), then Q += (g . c_i) alpha_i T_i.  (One scalar instead
+// of the four normalised colours behind, and seven operations per pair
+// instead of seventeen.)
 struct PixAdj {
-    float pxf, pyf, T, Tf, Rr, Rg, Rb, Rd, gr, gg, gb, gd, ga_tf;
+    float pxf, pyf, T, Tf, Q, gr, gg, gb, gd, ga_tf;
     int last;
 };
 
@@ -505,10 +513,7 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
         }
     }
     P.T = P.Tf;
-    P.Rr = bg[0];
-    P.Rg = bg[1];
-    P.Rb = bg[2];
-    P.Rd = 0.0f;
+    P.Q = (P.gr * bg[0] + P.gg * bg[1] + P.gb * bg[2]) * P.Tf;  // the background behind everything (depth 0)
     P.ga_tf = ga * P.Tf;
 }
 
@@ -534,16 +539,15 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     if (alpha < a.alpha_min)
         return false;
     const float om = 1.0f - alpha;
-    const float Ti = __fdividef(P.T, om);
+    const float rom = __fdividef(1.0f, om);
+    const float Ti = P.T * rom;
     const float4 q2 = *q2p;
-    float dal = Ti * (P.gr * (q2.x - P.Rr) + P.gg * (q2.y - P.Rg) + P.gb * (q2.z - P.Rb) + P.gd * (q1.z - P.Rd));
+    const float gcc = fmaf(P.gd, q1.z, fmaf(P.gb, q2.z, fmaf(P.gg, q2.y, P.gr * q2.x)));
+    float dal = fmaf(Ti, gcc, -(P.Q * rom));
     if (ALPHA)
-        dal += __fdividef(P.ga_tf, om);
-    P.Rr = fmaf(alpha, q2.x, om * P.Rr);
-    P.Rg = fmaf(alpha, q2.y, om * P.Rg);
-    P.Rb = fmaf(alpha, q2.z, om * P.Rb);
-    P.Rd = fmaf(alpha, q1.z, om * P.Rd);
+        dal = fmaf(P.ga_tf, rom, dal);
     const float wgt = alpha * Ti;
+    P.Q = fmaf(gcc, wgt, P.Q);
     g[5] = fmaf(P.gd, wgt, g[5]);
     if (FULL) {
         g[7] = fmaf(P.gr, wgt, g[7]);
