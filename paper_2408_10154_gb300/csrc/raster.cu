@@ -43,14 +43,22 @@ __device__ __forceinline__ PixelCoord pixel_of(const VpDesc &d, uint32_t t)
     return p;
 }
 
-// exponent of record (q0 = u, v, ca, cb; cc) at the pixel sample (FP32 contract)
-__device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float pxf, float pyf, float &dx, float &dy)
+// exponent of record (q0 = u, v, ca, cb; cc) at the pixel sample (FP32
+// contract); h = ca dx + cb dy and ky = cc dy are its intermediates
+__device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float pxf, float pyf, float &dx, float &dy,
+                                             float &h, float &ky)
 {
     dx = sub_rn(q0.x, pxf);
     dy = sub_rn(q0.y, pyf);
-    const float h = fma_rn(q0.z, dx, mul_rn(q0.w, dy));
-    const float k = mul_rn(mul_rn(cc, dy), dy);
-    return fma_rn(h, dx, k);
+    h = fma_rn(q0.z, dx, mul_rn(q0.w, dy));
+    ky = mul_rn(cc, dy);
+    return fma_rn(h, dx, mul_rn(ky, dy));
+}
+
+__device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float pxf, float pyf, float &dx, float &dy)
+{
+    float h, ky;
+    return exponent_at(q0, cc, pxf, pyf, dx, dy, h, ky);
 }
 
 // Warp-level cull of a staged record against the warp's pixel patch.  The
@@ -528,8 +536,8 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
 {
     if (jj >= P.last)
         return false;
-    float dx, dy;
-    const float power = exponent_at(q0, q1.x, P.pxf, P.pyf, dx, dy);
+    float dx, dy, h, ky;
+    const float power = exponent_at(q0, q1.x, P.pxf, P.pyf, dx, dy, h, ky);
     if (power > 0.0f || power < q1.w)
         return false;
     const float e = exp_ct(power);
@@ -557,9 +565,10 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     if (!clamped) {
         // d(exponent)/d(u, v) = (gu, gv) = -Q d; the exponent's gradient
         // w.r.t. the 2D covariance is (Q d)(Q d)^T / 2, accumulated as twice that
+        // (2 ca dx + cb dy, cb dx + 2 cc dy) from the exponent's intermediates
         const float dp = dal * alpha;
-        const float gu = fmaf(2.0f * q0.z, dx, q0.w * dy);
-        const float gv = fmaf(q0.w, dx, 2.0f * q1.x * dy);
+        const float gu = fmaf(q0.z, dx, h);
+        const float gv = fmaf(q0.w, dx, ky + ky);
         const float g0 = dp * gu, g1 = dp * gv;
         g[0] += g0;
         g[1] += g1;
