@@ -71,9 +71,13 @@ __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fm
 // e^x: Cody-Waite reduction k = round(x log2 e), r = x - k ln2 (two-part
 // ln2), degree-6 Taylor polynomial of e^r, exact scaling by 2^k; argument
 // clamped to [-80, 80].
-__device__ __forceinline__ float exp_ct(float x)
+__device__ __forceinline__ float exp_ct_core(float x);
+__device__ __forceinline__ float exp_ct(float x) { return exp_ct_core(fminf(fmaxf(x, -80.0f), 80.0f)); }
+// the same function for x <= 0 (or NaN, which the lower clamp maps to -80
+// either way): the upper clamp is a no-op there and is left out
+__device__ __forceinline__ float exp_ct_nonpos(float x) { return exp_ct_core(fmaxf(x, -80.0f)); }
+__device__ __forceinline__ float exp_ct_core(float x)
 {
-    x = fminf(fmaxf(x, -80.0f), 80.0f);
     const float magic = 12582912.0f;  // 1.5 * 2^23
     const float t = __fmaf_rn(x, 1.4426950408889634f, magic);
     const float kf = __fsub_rn(t, magic);

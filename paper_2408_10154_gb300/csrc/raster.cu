@@ -136,7 +136,6 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
     const PixelCoord p = pixel_of(d, t);
     const float pxf = (float)p.px + 0.5f, pyf = (float)p.py + 0.5f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float xa = pxf - (float)(lane & 7), xb = xa + 7.0f, ya = pyf - (float)(lane >> 3), yb = ya + 3.0f;
     const bool cull = a.alpha_min > 0.0f;
     const uint2 rg = a.ranges[t];
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
@@ -156,9 +155,13 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
         const int cnt = (int)min(256u, rg.y - b);
         int nsel = 0;
         if (!__all_sync(0xffffffffu, done)) {
+            // the warp's 8x4 patch of pixel samples (derived here: registers
+            // held across the pixel walk limit the CTAs per SM)
+            const float xa = pxf - (float)(lane & 7), ya = pyf - (float)(lane >> 3);
             for (int j0 = 0; j0 < cnt; j0 += 32) {
                 const int j = j0 + lane;
-                const bool keep = j < cnt && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].w, xa, xb, ya, yb));
+                const bool keep =
+                    j < cnt && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].w, xa, xa + 7.0f, ya, ya + 3.0f));
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (keep)
                     s_sel[warp][nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
                 const float power = exponent_at(q0, q1.x, pxf, pyf, dx, dy);
                 if (power > 0.0f || power < q1.w)
                     continue;
-                const float x = mul_rn(q1.y, exp_ct(power));
+                const float x = mul_rn(q1.y, exp_ct_nonpos(power));
                 const float alpha = x > a.alpha_max ? a.alpha_max : x;
                 if (alpha < a.alpha_min)
                     continue;
@@ -540,7 +543,7 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     const float power = exponent_at(q0, q1.x, P.pxf, P.pyf, dx, dy, h, ky);
     if (power > 0.0f || power < q1.w)
         return false;
-    const float e = exp_ct(power);
+    const float e = exp_ct_nonpos(power);
     const float x = mul_rn(q1.y, e);
     const bool clamped = x > a.alpha_max;
     const float alpha = clamped ? a.alpha_max : x;
