@@ -1372,7 +1372,8 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
     GS_TRY(alloc_pipe(ctx, P, true, p));
     float *pose32 = nullptr, *tloss = nullptr, *tf = nullptr;
     double *pose64 = nullptr, *adam = nullptr, *pivot = nullptr, *ccam = nullptr, *cent = nullptr, *lossd = nullptr,
-           *ttw = nullptr, *Tdev = nullptr, *confd = nullptr, *est = nullptr;
+           *Tdev = nullptr, *confd = nullptr, *est = nullptr;
+    float2 *ttw = nullptr;
     int32_t *last = nullptr, *rev = nullptr, *pf = nullptr, *pc = nullptr;
     uint8_t *code = nullptr;
     const size_t npix = (size_t)std::max<int64_t>(P.n_pix, 1), ntl = (size_t)std::max<uint64_t>(P.n_tiles, 1);
@@ -1875,7 +1876,8 @@ struct gs_server {
     int n_vps = 0, n_problems = 0;
     float *pose32 = nullptr, *tloss = nullptr, *tf = nullptr;
     double *pose64 = nullptr, *adam = nullptr, *pivot = nullptr, *ccam = nullptr, *cent = nullptr,
-           *lossd = nullptr, *ttw = nullptr, *Tdev = nullptr, *confd = nullptr;
+           *lossd = nullptr, *Tdev = nullptr, *confd = nullptr;
+    float2 *ttw = nullptr;
     int32_t *last = nullptr, *rev = nullptr, *pf = nullptr, *pc = nullptr;
     uint8_t *code = nullptr;
     gsl::PoseArgs pa{};

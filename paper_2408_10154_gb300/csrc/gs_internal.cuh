@@ -97,6 +97,18 @@ __device__ __forceinline__ float exp_ct_core(float x)
     return __fmul_rn(p, __int_as_float((k + 127) << 23));
 }
 
+// hi + lo += bhi + blo without losing the rounding error of the high parts
+// (Knuth's TwoSum: e is exactly the error of hi + bhi); FP32 only -- the
+// FP64 pipe of this part is a small fraction of its FP32 rate.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float bhi, float blo)
+{
+    const float s = hi + bhi;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (bhi - bp);
+    hi = s;
+    lo = lo + blo + e;
+}
+
 // M = V o T (3x4 row-major) in FP32
 __device__ __forceinline__ void compose_ct(const float *V, const float *T, float *M)
 {
@@ -299,7 +311,7 @@ struct RasterArgs {
     const uint32_t *tile_order;      // CTA -> tile schedule (longest lists first), or null = natural
     int exposure;                    // some keyframe compensates exposure (forward variant)
     int count_contrib;               // count the pairs that pass the alpha test (forward variant)
-    double *tile_twist;       // [tiles][6], camera frame
+    float2 *tile_twist;       // [tiles][6] camera-frame twist as FP32 (hi, lo) pairs (value hi + lo)
     const double *c_cam;      // [vp][3] pivot in camera frame
     float *dup_grads;         // [dups][10] screen-space partials (full mode)
     // tracking-loss keyframes (loss_kind 1): the forward writes the FP32
@@ -398,7 +410,7 @@ void overlap_count(const OverlapArgs &a, cudaStream_t s);
 struct PoseArgs {
     const gsk::VpDesc *vps;
     int n_vps;
-    const double *tile_twist;  // [tiles][6]
+    const float2 *tile_twist;  // [tiles][6] (hi, lo)
     const float *tile_loss;    // [tiles]
     double *pose64;            // [vp][12]
     float *pose32;             // [vp][12]

@@ -1,5 +1,6 @@
 // pose.cu -- per-keyframe reductions and the on-device registration step:
-// tile twists -> 6-vector per keyframe (FP64 block tree, fixed order),
+// tile twists -> 6-vector per keyframe (FP32 TwoSum pairs in a fixed
+// order, one FP64 value per component),
 // Adam on the twist with a cosine-decayed learning rate, exponential-map
 // pose update about the moving submap's centroid (Sec. 3.2; learning rates
 // Supp. B), the standalone L1 loss, the Eq. 7 fusion and the Eq. 8/9 rigid
@@ -19,8 +20,10 @@ __device__ void so3_exp(const double *w, double R[3][3])
         a = 1.0 - th2 / 6.0;
         b = 0.5 - th2 / 24.0;
     } else {
-        a = sin(th) / th;
-        b = (1.0 - cos(th)) / th2;
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        a = sn / th;
+        b = (1.0 - cs) / th2;
     }
     const double K[3][3] = {{0, -w[2], w[1]}, {w[2], 0, -w[0]}, {-w[1], w[0], 0}};
     for (int i = 0; i < 3; ++i)
@@ -28,6 +31,21 @@ __device__ void so3_exp(const double *w, double R[3][3])
             double k2 = K[i][0] * K[0][j] + K[i][1] * K[1][j] + K[i][2] * K[2][j];
             R[i][j] = (i == j ? 1.0 : 0.0) + a * K[i][j] + b * k2;
         }
+}
+
+// b^n for a step count n >= 1 (binary powering: a few multiplies instead of
+// a general pow, whose FP64 log/exp chain is long on this part)
+__device__ __forceinline__ double pow_count(double b, double n)
+{
+    unsigned long long m = (unsigned long long)n;
+    double r = 1.0, x = b;
+    while (m) {
+        if (m & 1ull)
+            r *= x;
+        x *= x;
+        m >>= 1;
+    }
+    return r;
 }
 
 // Adam step of twist component i (0..2 rotation, 3..5 translation) with
@@ -42,8 +60,8 @@ __device__ double adam_component(double *st, int i, double gi, double t, int k, 
     const double sched = f + (1.0 - f) * 0.5 * (1.0 + cos(kPi * (double)k / (double)iters));
     st[i] = b1 * st[i] + (1.0 - b1) * gi;
     st[6 + i] = b2 * st[6 + i] + (1.0 - b2) * gi * gi;
-    const double mh = st[i] / (1.0 - pow(b1, t));
-    const double vh = st[6 + i] / (1.0 - pow(b2, t));
+    const double mh = st[i] / (1.0 - pow_count(b1, t));
+    const double vh = st[6 + i] / (1.0 - pow_count(b2, t));
     const double lr = (i < 3 ? (double)lr_rot : (double)lr_trans) * sched;
     return -lr * mh / (sqrt(vh) + eps);
 }
@@ -165,39 +183,58 @@ __device__ void exposure_step(double *e, const double *g, int k, int iters, floa
 // exponential-map update, the exposure step and the pivots on lane 0.
 __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
 {
-    __shared__ double s[8][9];
-    __shared__ double s_g[6], s_xi[6];
+    __shared__ float s[8][9][2];
+    __shared__ double s_tot[9], s_g[6], s_xi[6];
     const int vp = blockIdx.x;
     const VpDesc &d = a.vps[vp];
     const uint32_t nt = (uint32_t)d.TX * d.TY;
     const bool expo = d.exposure && a.tile_expo && a.expo;
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // (hi, lo) FP32 pairs summed by TwoSum in a fixed order (per thread,
+    // then butterflies, then the warps); one FP64 value per component
+    float hs[9], ls[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        hs[i] = ls[i] = 0.0f;
     for (uint32_t k = threadIdx.x; k < nt; k += blockDim.x) {
         const size_t t = d.tile_base + k;
         if (a.tile_twist)
-            for (int i = 0; i < 6; ++i)
-                acc[i] += a.tile_twist[t * 6 + i];
-        acc[6] += (double)a.tile_loss[t];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const float2 v = a.tile_twist[t * 6 + i];
+                two_sum_add(hs[i], ls[i], v.x, v.y);
+            }
+        two_sum_add(hs[6], ls[6], a.tile_loss[t], 0.0f);
         if (expo) {
-            acc[7] += (double)a.tile_expo[2 * t];
-            acc[8] += (double)a.tile_expo[2 * t + 1];
+            two_sum_add(hs[7], ls[7], a.tile_expo[2 * t], 0.0f);
+            two_sum_add(hs[8], ls[8], a.tile_expo[2 * t + 1], 0.0f);
         }
     }
+#pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const double v = warp_sum(acc[i]);
-        if ((threadIdx.x & 31) == 0)
-            s[threadIdx.x >> 5][i] = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, hs[i], o), bl = __shfl_xor_sync(0xffffffffu, ls[i], o);
+            two_sum_add(hs[i], ls[i], bh, bl);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s[threadIdx.x >> 5][i][0] = hs[i];
+            s[threadIdx.x >> 5][i][1] = ls[i];
+        }
     }
     __syncthreads();
     if (threadIdx.x >= 32)
         return;
     const int lane = threadIdx.x;
-    double tot[9];
-    for (int i = 0; i < 9; ++i) {
-        tot[i] = 0;
-        for (int w = 0; w < 8; ++w)
-            tot[i] += s[w][i];
+    if (lane < 9) {
+        float h = s[0][lane][0], l = s[0][lane][1];
+        for (int w = 1; w < 8; ++w)
+            two_sum_add(h, l, s[w][lane][0], s[w][lane][1]);
+        s_tot[lane] = (double)h + (double)l;
     }
+    __syncwarp();
+    double tot[9];
+    for (int i = 0; i < 9; ++i)
+        tot[i] = s_tot[i];
     if (lane == 0)
         a.loss[vp] = tot[6];
     if (!a.tile_twist)

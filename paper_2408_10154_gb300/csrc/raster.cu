@@ -357,25 +357,13 @@ struct Twist6 {
     }
 };
 
-// hi + lo += bhi + blo without losing the rounding error of the high parts
-// (Knuth's TwoSum: e is exactly the error of hi + bhi); FP32 only -- the
-// FP64 pipe of this part is a small fraction of its FP32 rate.
-__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float bhi, float blo)
-{
-    const float s = hi + bhi;
-    const float bp = s - hi;
-    const float e = (hi - (s - bp)) + (bhi - bp);
-    hi = s;
-    lo = lo + blo + e;
-}
-
 // The tile's twist: each warp reduces its lanes' compensated sums with
-// TwoSum butterflies, threads 0..5 join the warps' (hi, lo) pairs the same
-// way in a fixed order, and each leaves hi + lo in FP64 (one conversion per
-// component and tile: the FP64 pipe is a small fraction of the FP32 one,
-// and FP64 work in every warp kept it busy and lengthened every CTA's tail).
+// TwoSum butterflies, and threads 0..5 join the warps' (hi, lo) pairs the
+// same way in a fixed order and store them (no FP64 here: the FP64 pipe is a
+// small fraction of the FP32 one, and FP64 work in every warp kept it busy
+// and lengthened every CTA's tail).
 template <int WARPS>
-__device__ __forceinline__ void store_tile_twist(const Twist6 &tw, float (*s_tw)[6][2], double *out)
+__device__ __forceinline__ void store_tile_twist(const Twist6 &tw, float (*s_tw)[6][2], float2 *out)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -397,7 +385,7 @@ __device__ __forceinline__ void store_tile_twist(const Twist6 &tw, float (*s_tw)
 #pragma unroll
         for (int w = 1; w < WARPS; ++w)
             two_sum_add(hi, lo, s_tw[w][threadIdx.x][0], s_tw[w][threadIdx.x][1]);
-        out[threadIdx.x] = (double)hi + (double)lo;
+        out[threadIdx.x] = make_float2(hi, lo);
     }
 }
 
