@@ -49,7 +49,7 @@ BWD_FLOPS_CONTRIB = 82.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
 # the current kernel (profiles/k_backward2_room_150k.md); None while the
 # kernel has changed since the capture
-BWD_TRAFFIC_BYTES = None
+BWD_TRAFFIC_BYTES = 185.384192e6
 SMS = 152
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
