@@ -819,15 +819,16 @@ __device__ __forceinline__ unsigned long long warp_bitonic32(unsigned long long 
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
         {
+            // the lower position keeps the smaller key, the upper the larger
             const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, k - 1);
             const bool lower = (lane & (k >> 1)) == 0;
-            x = lower ? (y < x ? y : x) : (y > x ? y : x);
+            x = (y < x) == lower ? y : x;
         }
 #pragma unroll
         for (int j = k >> 2; j >= 1; j >>= 1) {
             const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
             const bool lower = (lane & j) == 0;
-            x = lower ? (y < x ? y : x) : (y > x ? y : x);
+            x = (y < x) == lower ? y : x;
         }
     }
     return x;
@@ -839,9 +840,8 @@ __device__ __forceinline__ unsigned long long warp_bitonic32(unsigned long long 
 template <int K>
 __device__ __forceinline__ void warp_bitonic_reg(unsigned long long (&x)[K], int lane)
 {
-    auto pick = [](unsigned long long u, unsigned long long v, bool lower) {
-        return lower ? (v < u ? v : u) : (v > u ? v : u);
-    };
+    // the lower position keeps the smaller key, the upper the larger
+    auto pick = [](unsigned long long u, unsigned long long v, bool lower) { return (v < u) == lower ? v : u; };
 #pragma unroll
     for (int size = 2; size <= 32 * K; size <<= 1) {
         if (size <= 32) {
@@ -866,8 +866,9 @@ __device__ __forceinline__ void warp_bitonic_reg(unsigned long long (&x)[K], int
                 for (int k = 0; k < K; ++k)
                     if ((k & (j / 32)) == 0) {
                         const unsigned long long u = x[k], v = x[k | (j / 32)];
-                        x[k] = v < u ? v : u;
-                        x[k | (j / 32)] = v < u ? u : v;
+                        const bool sw = v < u;
+                        x[k] = sw ? v : u;
+                        x[k | (j / 32)] = sw ? u : v;
                     }
             } else {
                 const bool lower = (lane & j) == 0;

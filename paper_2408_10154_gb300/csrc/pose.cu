@@ -109,28 +109,37 @@ __device__ void pivots_of(const VpDesc &d, const double *pose, const double *mba
                   (double)d.w2c[4 * i + 3];
 }
 
+// mean of each Gaussian set's means: FP32 TwoSum pairs per thread, TwoSum
+// butterflies and a fixed-order TwoSum of the warps, one FP64 division
+// (FP64 sums over 10^5 means were latency-bound on the slow FP64 pipe)
 __global__ void k_centroid(const VpDesc *vps, const int *set_vp, double *centroid)
 {
-    __shared__ double s[8][3];
+    __shared__ float s[8][3][2];
     const VpDesc &d = vps[set_vp[blockIdx.x]];
-    double acc[3] = {0, 0, 0};
+    float hs[3] = {0.0f, 0.0f, 0.0f}, ls[3] = {0.0f, 0.0f, 0.0f};
     for (int i = threadIdx.x; i < d.n; i += blockDim.x) {
         const float4 m = d.means[i];
-        acc[0] += m.x;
-        acc[1] += m.y;
-        acc[2] += m.z;
+        two_sum_add(hs[0], ls[0], m.x, 0.0f);
+        two_sum_add(hs[1], ls[1], m.y, 0.0f);
+        two_sum_add(hs[2], ls[2], m.z, 0.0f);
     }
     for (int k = 0; k < 3; ++k) {
-        const double v = warp_sum(acc[k]);
-        if ((threadIdx.x & 31) == 0)
-            s[threadIdx.x >> 5][k] = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, hs[k], o), bl = __shfl_xor_sync(0xffffffffu, ls[k], o);
+            two_sum_add(hs[k], ls[k], bh, bl);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s[threadIdx.x >> 5][k][0] = hs[k];
+            s[threadIdx.x >> 5][k][1] = ls[k];
+        }
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        double v = 0;
-        for (int w = 0; w < 8; ++w)
-            v += s[w][threadIdx.x];
-        centroid[3 * blockIdx.x + threadIdx.x] = d.n > 0 ? v / d.n : 0.0;
+        float h = s[0][threadIdx.x][0], l = s[0][threadIdx.x][1];
+        for (int w = 1; w < 8; ++w)
+            two_sum_add(h, l, s[w][threadIdx.x][0], s[w][threadIdx.x][1]);
+        centroid[3 * blockIdx.x + threadIdx.x] = d.n > 0 ? ((double)h + (double)l) / d.n : 0.0;
     }
 }
 
