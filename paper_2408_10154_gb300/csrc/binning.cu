@@ -737,7 +737,8 @@ __global__ void __launch_bounds__(kSegTileThreads) k_seg_ranges(const gsl::BinAr
     }
 }
 
-constexpr uint32_t kSegSmall = 8;  // records with more tiles are placed by the whole warp
+constexpr uint32_t kSegSmall = 4;  // tiles of a record placed by its own thread; more: by the whole warp
+constexpr int kSegPerThread = 2;    // records per thread (more cursor atomics in flight per warp)
 
 __device__ __forceinline__ void seg_put(const gsl::BinArgs &a, uint32_t t, uint32_t zb, uint32_t r)
 {
@@ -748,60 +749,80 @@ __device__ __forceinline__ void seg_put(const gsl::BinArgs &a, uint32_t t, uint3
     }
 }
 
-// One thread per record: a visible one writes (depth bits, record) into the
-// lists of the tiles of its rectangle (from its seg_list entry) at positions
-// taken from the tiles' cursors, all cursor atomics in flight before the
-// stores.
-// Entries with more than kSegSmall tiles are spread over the lanes of their
-// warp, one entry at a time, so a splat covering thousands of tiles does not
-// serialise one thread.  Positions at or past the capacity are dropped (the
-// capacity flag is already set).
+// kSegPerThread records per thread (kSegThreads apart, so each load is
+// coalesced): a visible one writes (depth bits, record) into the lists of
+// the tiles of its rectangle (from its seg_list entry) at positions taken
+// from the tiles' cursors, all cursor atomics of the thread in flight
+// before its stores.  Records with more than kSegSmall tiles are spread over
+// the lanes of their warp, one record at a time, so a splat covering
+// thousands of tiles does not serialise one thread.  Positions at or past
+// the capacity are dropped (the capacity flag is already set).
 __global__ void __launch_bounds__(kSegThreads) k_seg_place(const gsl::BinArgs a)
 {
-    const uint32_t r = blockIdx.x * kSegThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    uint32_t cnt = 0, t0 = 0, w = 1, tx = 0, zb = 0;
-    if (r < a.n_records) {
-        const uint4 e = a.seg_list[r];
-        if (e.z) {
-            zb = e.x;
-            t0 = e.y;
-            w = e.z & 0xffffu;
-            cnt = w * (e.z >> 16);
-            tx = e.w;
+    uint32_t cnt[kSegPerThread], t0[kSegPerThread], w[kSegPerThread], tx[kSegPerThread], zb[kSegPerThread],
+        rr[kSegPerThread];
+#pragma unroll
+    for (int q = 0; q < kSegPerThread; ++q) {
+        const uint32_t r = (blockIdx.x * kSegPerThread + q) * kSegThreads + threadIdx.x;
+        rr[q] = r;
+        cnt[q] = 0;
+        t0[q] = 0;
+        w[q] = 1;
+        tx[q] = 0;
+        zb[q] = 0;
+        if (r < a.n_records) {
+            const uint4 e = a.seg_list[r];
+            if (e.z) {
+                zb[q] = e.x;
+                t0[q] = e.y;
+                w[q] = e.z & 0xffffu;
+                cnt[q] = w[q] * (e.z >> 16);
+                tx[q] = e.w;
+            }
         }
     }
-    const bool big = cnt > kSegSmall;
-    if (!big) {
-        uint32_t pos[kSegSmall];
-        uint32_t col = 0, row = t0;
+    uint32_t pos[kSegPerThread][kSegSmall];
+#pragma unroll
+    for (int q = 0; q < kSegPerThread; ++q) {
+        if (cnt[q] > kSegSmall)
+            continue;
+        uint32_t col = 0, row = t0[q];
 #pragma unroll
         for (uint32_t k = 0; k < kSegSmall; ++k) {
-            if (k < cnt) {
-                pos[k] = atomicAdd(a.seg_cursor + row + col, 1u);
-                if (++col == w) {
+            if (k < cnt[q]) {
+                pos[q][k] = atomicAdd(a.seg_cursor + row + col, 1u);
+                if (++col == w[q]) {
                     col = 0;
-                    row += tx;
+                    row += tx[q];
                 }
             }
         }
+    }
+#pragma unroll
+    for (int q = 0; q < kSegPerThread; ++q) {
+        if (cnt[q] > kSegSmall)
+            continue;
 #pragma unroll
         for (uint32_t k = 0; k < kSegSmall; ++k) {
-            if (k < cnt && pos[k] < a.capacity) {
-                a.tkeys[0][pos[k]] = zb;
-                a.vals[0][pos[k]] = r;
+            if (k < cnt[q] && pos[q][k] < a.capacity) {
+                a.tkeys[0][pos[q][k]] = zb[q];
+                a.vals[0][pos[q][k]] = rr[q];
             }
         }
     }
-    unsigned m = __ballot_sync(0xffffffffu, big);
-    while (m) {
-        const int src = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t c = __shfl_sync(0xffffffffu, cnt, src), b = __shfl_sync(0xffffffffu, t0, src);
-        const uint32_t ww = __shfl_sync(0xffffffffu, w, src), tt = __shfl_sync(0xffffffffu, tx, src);
-        const uint32_t z = __shfl_sync(0xffffffffu, zb, src), rr = __shfl_sync(0xffffffffu, r, src);
-        for (uint32_t k = lane; k < c; k += 32)
-            seg_put(a, b + (k / ww) * tt + k % ww, z, rr);
+#pragma unroll
+    for (int q = 0; q < kSegPerThread; ++q) {
+        unsigned m = __ballot_sync(0xffffffffu, cnt[q] > kSegSmall);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t c = __shfl_sync(0xffffffffu, cnt[q], src), b = __shfl_sync(0xffffffffu, t0[q], src);
+            const uint32_t ww = __shfl_sync(0xffffffffu, w[q], src), tt = __shfl_sync(0xffffffffu, tx[q], src);
+            const uint32_t z = __shfl_sync(0xffffffffu, zb[q], src), r = __shfl_sync(0xffffffffu, rr[q], src);
+            for (uint32_t k = lane; k < c; k += 32)
+                seg_put(a, b + (k / ww) * tt + k % ww, z, r);
+        }
     }
 }
 
@@ -1162,7 +1183,7 @@ int bin_seg(const BinArgs &a, cudaStream_t s)
     k_seg_ranges<<<a.n_vps, kSegTileThreads, 0, s>>>(a);
     g_launches += 2;
     if (a.n_records) {
-        k_seg_place<<<div_up(a.n_records, kSegThreads), kSegThreads, 0, s>>>(a);
+        k_seg_place<<<div_up(a.n_records, kSegThreads * kSegPerThread), kSegThreads, 0, s>>>(a);
         ++g_launches;
     }
     if (a.n_tiles) {
