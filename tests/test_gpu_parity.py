@@ -184,6 +184,16 @@ def test_binning_long_tile_lists(gs, ctx, n):
     check_render(gs, ctx, gd, cams, poses)
 
 
+def test_binning_and_render_large_image(gs, ctx):
+    # 2560 x 1920 (160 x 120 = 19,200 tiles): the per-keyframe tile counts
+    # are summed in global memory instead of shared memory
+    c = synth.small_case(2500, 2560, 1920, 1400.0, n_views=1, seed=41, ls_mean=-3.5)
+    gd, cams = c["gaussians"], c["cams"]
+    poses = rand_poses(np.random.default_rng(6), len(cams), 1.0, 0.01)
+    assert check_binning(gs, ctx, gd, cams, poses) > 10_000
+    check_render(gs, ctx, gd, cams, poses)
+
+
 def test_binning_empty(gs, ctx):
     gd, cams = plain_case()
     poses = np.stack([np.eye(3, 4)] * 4)
