@@ -37,18 +37,19 @@ ITERS = 100
 WORKLOAD = ("room_150k: 150,000-Gaussian room submap pair (10 deg / 15 cm), 8+8 keyframes 1200x680, "
             "100 iterations fwd+bwd+update in both directions, residual + Eq. 7 fusion")
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-# FP32 operations of the dominant kernels per unit of work
-# (FMA = 2) per (pixel, Gaussian) pair that passes the alpha test -- the
-# work any implementation must do: the forward 43 (exponent 9, exp32 22,
-# alpha, transmittance, 4 blends), the adjoint 82 (exponent, exp32, alpha,
-# T by division, dL/dalpha, colour-behind recursion, screen and
-# 2D-covariance gradients).  Pairs walked and skipped are overhead (how
-# many depends on how tight the tile lists and culls are), not counted.
-FWD_FLOPS_CONTRIB = 43.0
-BWD_FLOPS_CONTRIB = 82.0
+# FP32 operations of the dominant kernels per unit of work (FMA = 2) per
+# (pixel, Gaussian) pair that passes the alpha test -- the work the method's
+# arithmetic needs as implemented: the forward 41 (exponent 9, exp32 20,
+# opacity x e^x 1, 1 - alpha 1, transmittance 1, weight 1, 4 blends 8), the
+# adjoint 64 (exponent 9, exp32 20, opacity x e^x 1, transmittance by
+# division 3, g . c 7, dL/dalpha 3, weight 1, the colour-behind scalar 2,
+# depth 2, screen and 2D-covariance gradients 16).  Pairs walked and
+# skipped are overhead (how many depends on how tight the tile lists and
+# culls are), not counted.
+FWD_FLOPS_CONTRIB = 41.0
+BWD_FLOPS_CONTRIB = 64.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
-# the current kernel (profiles/k_backward2_room_150k.md); None while the
-# kernel has changed since the capture
+# the current kernel; None while the kernel has changed since the capture
 BWD_TRAFFIC_BYTES = 185.384192e6
 SMS = 152
 FP32_LANES = 128
