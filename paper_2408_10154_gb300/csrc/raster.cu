@@ -12,12 +12,13 @@
 // transmittance and the last-contributor index.  Nothing else per pixel is
 // saved; the adjoint recomputes alpha and recovers transmittance by division.
 //
-// Adjoint: 128 threads per tile, two pixels per thread.  Per (pixel,
-// Gaussian) screen-space gradients are summed over each warp with shuffles,
-// over the tile's warps in shared memory (fixed order), chained through the
-// projection into a camera-frame twist per Gaussian, accumulated per thread
-// in FP32 with Kahan compensation and reduced per tile by TwoSum butterflies
-// and an FP64 sum of the warp totals -- no global atomics, bit-reproducible.
+// Adjoint: 128 threads per tile, two pixels per thread (8x8 warp patches).
+// Per (pixel, Gaussian) screen-space gradients are summed over each warp
+// with shuffles, over the tile's warps in shared memory (fixed order),
+// chained through the projection into a camera-frame twist per Gaussian,
+// accumulated per thread in FP32 with Kahan compensation and reduced per
+// tile by TwoSum butterflies to FP32 (hi, lo) pairs -- no global atomics,
+// bit-reproducible.
 #include <float.h>
 
 #include "gs_internal.cuh"
