@@ -276,10 +276,8 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const K *kin, const
 }
 
 // ---------------------------------------------------------------- ranges
-// tile of a key: the high word of a 64-bit (tile << 32 | depth) key, or a
-// 32-bit tile key itself
+// tile of a 64-bit (tile << 32 | depth) key
 __device__ __forceinline__ uint32_t tile_of(uint64_t k) { return (uint32_t)(k >> 32); }
-__device__ __forceinline__ uint32_t tile_of(uint32_t k) { return k; }
 
 template <typename K>
 __global__ void k_ranges(const K *keys, const uint32_t *n_dups, uint32_t cap, uint2 *ranges)
@@ -294,14 +292,6 @@ __global__ void k_ranges(const K *keys, const uint32_t *n_dups, uint32_t cap, ui
     if (i == n - 1 || tile_of(keys[i + 1]) != t)
         ranges[t].y = i + 1;
 }
-
-// ---------------------------------------------------------------- two-stage binning
-// Stage 1 sorts the visible records by depth (stable, ties by record
-// index); stage 2 emits their duplicates in that order with 32-bit tile
-// keys and sorts them stably by tile.  The per-tile order is (depth bits,
-// record index), the same as a stable sort of (tile << 32 | depth) keys
-// emitted in record order, with 4-byte keys and 2 tile passes instead of 6
-// passes over 8-byte keys.
 
 inline uint32_t div_up(size_t a, size_t b) { return (uint32_t)((a + b - 1) / b); }
 
