@@ -51,6 +51,10 @@ BWD_FLOPS_CONTRIB = 64.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
 # the current kernel; None while the kernel has changed since the capture
 BWD_TRAFFIC_BYTES = 185.384192e6
+# the same capture's smsp__issue_active (fraction of cycles issuing an
+# instruction): the adjoint is bound by instruction issue, of which the
+# counted flops are a part
+BWD_ISSUE_ACTIVE = 0.825
 SMS = 152
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -282,6 +286,7 @@ def run_ours(args):
         roof = {"kernel": "k_backward2" if names[dom] == "backward" else "k_forward", "bound": "alu",
                 "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
                 "traffic": BWD_TRAFFIC_BYTES if names[dom] == "backward" else None,
+                "issue_active": BWD_ISSUE_ACTIVE if names[dom] == "backward" else None,
                 "flops_per_launch": flops,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock (derived; no measured FP32 peak)"}
     else:

@@ -109,35 +109,50 @@ __device__ void pivots_of(const VpDesc &d, const double *pose, const double *mba
                   (double)d.w2c[4 * i + 3];
 }
 
-// mean of each Gaussian set's means: FP32 TwoSum pairs per thread, TwoSum
-// butterflies and a fixed-order TwoSum of the warps, one FP64 division
-// (FP64 sums over 10^5 means were latency-bound on the slow FP64 pipe)
-__global__ void k_centroid(const VpDesc *vps, const int *set_vp, double *centroid)
+// mean of each Gaussian set's means (one 1024-thread block per set): FP32
+// TwoSum pairs per thread (two interleaved chains), TwoSum butterflies and a
+// fixed-order TwoSum of the warps, one FP64 division (FP64 sums over 10^5
+// means were latency-bound on the slow FP64 pipe)
+constexpr int kCentroidThreads = 1024;
+
+__global__ void __launch_bounds__(kCentroidThreads) k_centroid(const VpDesc *vps, const int *set_vp, double *centroid)
 {
-    __shared__ float s[8][3][2];
+    __shared__ float s[kCentroidThreads / 32][3][2];
     const VpDesc &d = vps[set_vp[blockIdx.x]];
-    float hs[3] = {0.0f, 0.0f, 0.0f}, ls[3] = {0.0f, 0.0f, 0.0f};
-    for (int i = threadIdx.x; i < d.n; i += blockDim.x) {
-        const float4 m = d.means[i];
-        two_sum_add(hs[0], ls[0], m.x, 0.0f);
-        two_sum_add(hs[1], ls[1], m.y, 0.0f);
-        two_sum_add(hs[2], ls[2], m.z, 0.0f);
+    float hs[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}}, ls[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+    int i = threadIdx.x;
+    for (; i + kCentroidThreads < d.n; i += 2 * kCentroidThreads) {
+        const float4 m0 = d.means[i], m1 = d.means[i + kCentroidThreads];
+        two_sum_add(hs[0][0], ls[0][0], m0.x, 0.0f);
+        two_sum_add(hs[0][1], ls[0][1], m0.y, 0.0f);
+        two_sum_add(hs[0][2], ls[0][2], m0.z, 0.0f);
+        two_sum_add(hs[1][0], ls[1][0], m1.x, 0.0f);
+        two_sum_add(hs[1][1], ls[1][1], m1.y, 0.0f);
+        two_sum_add(hs[1][2], ls[1][2], m1.z, 0.0f);
+    }
+    if (i < d.n) {
+        const float4 m0 = d.means[i];
+        two_sum_add(hs[0][0], ls[0][0], m0.x, 0.0f);
+        two_sum_add(hs[0][1], ls[0][1], m0.y, 0.0f);
+        two_sum_add(hs[0][2], ls[0][2], m0.z, 0.0f);
     }
     for (int k = 0; k < 3; ++k) {
+        float h = hs[0][k], l = ls[0][k];
+        two_sum_add(h, l, hs[1][k], ls[1][k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float bh = __shfl_xor_sync(0xffffffffu, hs[k], o), bl = __shfl_xor_sync(0xffffffffu, ls[k], o);
-            two_sum_add(hs[k], ls[k], bh, bl);
+            const float bh = __shfl_xor_sync(0xffffffffu, h, o), bl = __shfl_xor_sync(0xffffffffu, l, o);
+            two_sum_add(h, l, bh, bl);
         }
         if ((threadIdx.x & 31) == 0) {
-            s[threadIdx.x >> 5][k][0] = hs[k];
-            s[threadIdx.x >> 5][k][1] = ls[k];
+            s[threadIdx.x >> 5][k][0] = h;
+            s[threadIdx.x >> 5][k][1] = l;
         }
     }
     __syncthreads();
     if (threadIdx.x < 3) {
         float h = s[0][threadIdx.x][0], l = s[0][threadIdx.x][1];
-        for (int w = 1; w < 8; ++w)
+        for (int w = 1; w < kCentroidThreads / 32; ++w)
             two_sum_add(h, l, s[w][threadIdx.x][0], s[w][threadIdx.x][1]);
         centroid[3 * blockIdx.x + threadIdx.x] = d.n > 0 ? ((double)h + (double)l) / d.n : 0.0;
     }
@@ -520,7 +535,7 @@ namespace gsl {
 void centroids(const VpDesc *vps, const int *set_vp, int n_sets, double *centroid, cudaStream_t s)
 {
     if (n_sets > 0) {
-        k_centroid<<<n_sets, 256, 0, s>>>(vps, set_vp, centroid);
+        k_centroid<<<n_sets, kCentroidThreads, 0, s>>>(vps, set_vp, centroid);
         ++g_launches;
     }
 }
