@@ -143,8 +143,8 @@ typedef struct {
     int32_t iterations;      /* optimisation iterations run */
     int32_t reserved;
     /* profile != 0: summed CUDA-event time (ms) of each phase over the
-     * iterations: project, bin (scan+emit+sort+ranges), forward+loss,
-     * backward, pose update */
+     * iterations: project, bin (tile counts and ranges, placement, per-tile
+     * sort), forward+loss, backward, pose update */
     double phase_ms[5];
     int64_t contributing;    /* profile = 2 only (else 0): sum over iterations of the (pixel,
                                 Gaussian) pairs that pass the alpha test before the early stop */
@@ -399,9 +399,8 @@ gs_status_t gs_overlap_ratio(gs_ctx_t *ctx, const gs_gaussians_t *p, const gs_ga
 /* --------------------------------------------------------------- utility */
 
 /* Stable sort of n (key, value) pairs by the low `bits` bits of the keys
- * (device arrays, sorted in place): the one-sweep LSD radix sort of the
- * tile lists (8-bit digits; one histogram pass, one look-back scatter per
- * digit).  GS_ERR_TIMEOUT if a pass's bounded wait gave up (the device
+ * (device arrays, sorted in place): a one-sweep LSD radix sort (8-bit
+ * digits; one histogram pass, one look-back scatter per digit).  GS_ERR_TIMEOUT if a pass's bounded wait gave up (the device
  * keeps answering; the arrays' contents are then unspecified).
  * Synchronises `stream`. */
 gs_status_t gs_sort_u32(gs_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int bits, gs_stream_t stream);
