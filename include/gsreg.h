@@ -132,6 +132,13 @@ typedef struct {
      * alpha_min (its alpha-threshold ellipse's box, with margins; about a
      * third fewer duplicates), 0 = the 3-sigma rectangles of gs_bin */
     int32_t tight_lists;
+    /* capacity of the tile lists of gs_register* as a multiple of the
+     * duplicates at the initial poses (1.5; 64 Ki entries more when >= 1):
+     * the lists move with the poses, and when an iteration outgrows them
+     * the edge is redone from its initial poses with max(2 x, 1.5) (the
+     * results are those of a run that did not outgrow them).  Finite and
+     * in (0, 64]; below 1 the first attempt always outgrows its lists. */
+    float list_headroom;
 } gs_options_t;
 
 /* Statistics of the last gs_register / gs_render call on a context. */

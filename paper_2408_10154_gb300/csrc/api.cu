@@ -194,6 +194,8 @@ gs_status_t check_options(gs_ctx *ctx, const gs_options_t *o)
         return fail(ctx, GS_ERR_INVALID_ARG, "tile_schedule must be 0 (autotune), 1 or 2");
     if (o->tight_lists != 0 && o->tight_lists != 1)
         return fail(ctx, GS_ERR_INVALID_ARG, "tight_lists must be 0 or 1");
+    if (!(o->list_headroom > 0.0f) || !(o->list_headroom <= 64.0f))
+        return fail(ctx, GS_ERR_INVALID_ARG, "list_headroom must be in (0, 64]");
     if ((o->exposure != 0 && o->exposure != 1) || !(o->lr_exposure >= 0) || !std::isfinite(o->lr_exposure) ||
         (o->exposure && o->tracking_loss))
         return fail(ctx, GS_ERR_INVALID_ARG,
@@ -681,6 +683,7 @@ void gs_default_options(gs_options_t *o)
     o->lr_exposure = 0.1f;
     o->tile_schedule = 0;
     o->tight_lists = 1;
+    o->list_headroom = 1.5f;
     o->lr_final = 0.001f;
 }
 
@@ -1440,7 +1443,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
 
     gsl::RasterArgs expo_r{};
     GS_TRY(alloc_exposure(ctx, P, pa, expo_r));
-    double headroom = 1.5;
+    double headroom = opt->list_headroom;
     for (int attempt = 0; attempt < 3; ++attempt) {
         const long long l0 = gsl::g_launches;
         long long captured = 0, graph_kernels = 0, trial_kernels = 0;
@@ -1452,10 +1455,12 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         int cur = 0;
         uint32_t nd = 0;
         GS_TRY(project_and_bin(ctx, P, D, p, pose32, opt, s, &cur, &nd, opt->tight_lists != 0));
-        const uint64_t want = (uint64_t)(headroom * nd) + 65536;
+        const uint64_t want = (uint64_t)(headroom * nd) + (headroom >= 1.0 ? 65536 : 0);
         if (p.cap < want)
             GS_TRY(alloc_sort(ctx, want, p));
         gsl::BinArgs b = bin_args(P, D, p);
+        // the sizing rule's capacity, whatever earlier calls left allocated
+        b.capacity = (uint32_t)std::max<uint64_t>(std::min<uint64_t>(want, p.cap), 1);
         gsl::RasterArgs r = raster_args(P, D, p, 0, opt);
         r.t_final = tf;
         r.last = last;
@@ -1645,7 +1650,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         if (flags & gsk::kFlagTimeout)
             return fail(ctx, GS_ERR_TIMEOUT, "a sort pass gave up waiting for an earlier tile");
         if (flags & gsk::kFlagCapacity) {
-            headroom *= 2.0;  // the lists outgrew the headroom: redo with more
+            headroom = std::max(2.0 * headroom, 1.5);  // the lists outgrew the headroom: redo with more
             continue;
         }
         std::vector<double> epsh(nv);

@@ -54,6 +54,7 @@ def test_default_options_match_the_oracle(lib):
                                rtol=1e-6)
     assert o.tracking_loss == 0 and np.float32(o.lambda_c) == np.float32(O.TRACK_LAMBDA_C)
     assert o.exposure == 0 and np.float32(o.lr_exposure) == np.float32(0.1) and o.tile_schedule == 0 and o.tight_lists == 1
+    assert np.float32(o.list_headroom) == np.float32(1.5)
 
 
 def test_structs_match_the_library(lib):
@@ -63,7 +64,7 @@ def test_structs_match_the_library(lib):
     assert lib.gs_abi_sizes(sizes, len(structs)) == len(structs)
     for st, sz in zip(structs, sizes):
         assert ctypes.sizeof(st) == sz, st.__name__
-    assert ctypes.sizeof(gsreg.gs_camera_t) == 72 and ctypes.sizeof(gsreg.gs_options_t) == 4 * 23
+    assert ctypes.sizeof(gsreg.gs_camera_t) == 72 and ctypes.sizeof(gsreg.gs_options_t) == 4 * 24
 
 
 def test_context_without_device_is_rejected(lib):

@@ -522,6 +522,26 @@ def test_registration_room_full_size_converged_keyframes(gs, ctx):
     assert ang < 0.5 and dt < 0.01, (ang, dt)
 
 
+def test_outgrown_tile_lists_are_redone(gs, ctx):
+    # a list capacity of half the initial duplicates makes the first attempt
+    # outgrow its lists at its first iteration; the edge is redone with
+    # room to spare, and the result is that of a run that never outgrew
+    # them (the overflowing attempt wrote only inside its lists)
+    c = synth.room_150k()
+    og = O.Gaussians.from_dict(c["gaussians"])
+    g = gs.Gaussians.from_numpy(c["gaussians"])
+    views = []
+    for cam in c["src_cams"][:2]:
+        tr = O.render(og, c["T_gt"], cam)
+        views.append((cam, dev(tr["rgb"].astype(np.float32)), dev(tr["depth"].astype(np.float32))))
+    ref = gs.gs_register(ctx, g, g, [], views, 10, gs.default_options(tile_schedule=1))
+    small = gs.gs_register(ctx, g, g, [], views, 10, gs.default_options(tile_schedule=1, list_headroom=0.5))
+    np.testing.assert_array_equal(small[0], ref[0])
+    np.testing.assert_array_equal(small[2], ref[2])
+    with pytest.raises(RuntimeError):
+        gs.gs_register(ctx, g, g, [], views, 10, gs.default_options(list_headroom=0.0))
+
+
 def test_transform_batch_equals_single_transforms(gs, ctx):
     # map adjustment: three submaps (one empty) corrected in one launch,
     # bit-equal to one gs_transform each and within 2e-6 of the oracle
