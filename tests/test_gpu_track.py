@@ -66,13 +66,20 @@ def targets(og, cams, rng):
     return out
 
 
-@pytest.mark.parametrize("case", ["ragged", "needles"])
+@pytest.mark.parametrize("case", ["ragged", "needles", "room_640x480"])
 def test_track_loss_parity(gs, ctx, case):
     if case == "ragged":
         c = synth.small_case(700, 100, 70, 70.0, n_views=3, seed=9, ls_mean=-3.5)
-    else:
+        gd, cams = c["gaussians"], c["cams"]
+    elif case == "needles":
         c = synth.small_case(1500, 300, 200, 200.0, n_views=2, seed=21, ls_mean=-3.2, ls_std=0.3)
-    gd, cams = c["gaussians"], c["cams"]
+        gd, cams = c["gaussians"], c["cams"]
+    else:
+        # a served tracking frame: 640 x 480 (f = 320) from a room keyframe's
+        # pose against the 150k-Gaussian room submap
+        c = synth.room_150k()
+        w2c = np.asarray(c["src_cams"][0][6:], np.float64).reshape(3, 4)
+        gd, cams = c["gaussians"], np.stack([synth.camera(320.0, 320.0, 320.0, 240.0, 640, 480, w2c)])
     og = O.Gaussians.from_dict(gd)
     g = gs.Gaussians.from_numpy(gd)
     rng = np.random.default_rng(11)
