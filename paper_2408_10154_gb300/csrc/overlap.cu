@@ -161,6 +161,9 @@ __global__ void k_bbox(const float4 *a, int na, const float4 *b, int nb, uint32_
             hi[k] = max(hi[k], c[k]);
         }
     }
+    // warp, then block (shared memory), then one atomic per block and bound
+    // (an atomic per warp serialised ~10^4 of them on six addresses)
+    __shared__ uint32_t s_mm[6][8];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
@@ -168,9 +171,20 @@ __global__ void k_bbox(const float4 *a, int na, const float4 *b, int nb, uint32_
     }
     if ((threadIdx.x & 31) == 0)
         for (int k = 0; k < 3; ++k) {
-            atomicMin(&mm[k], lo[k]);
-            atomicMax(&mm[3 + k], hi[k]);
+            s_mm[k][threadIdx.x >> 5] = lo[k];
+            s_mm[3 + k][threadIdx.x >> 5] = hi[k];
         }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        uint32_t m = s_mm[k][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            m = k < 3 ? min(m, s_mm[k][w]) : max(m, s_mm[k][w]);
+        if (k < 3)
+            atomicMin(&mm[k], m);
+        else
+            atomicMax(&mm[k], m);
+    }
 }
 
 __device__ __forceinline__ int cell_axis(float x, float o, float inv_s, int n)
@@ -313,7 +327,7 @@ void overlap_moved_bbox(const OverlapArgs &a, uint32_t *bbox, cudaStream_t s)
         ++g_launches;
     }
     if (a.np + a.nq > 0) {
-        k_bbox<<<std::min<unsigned>(div_up(a.np + a.nq, 256), 1216), 256, 0, s>>>(a.pt, a.np, a.q, a.nq, bbox);
+        k_bbox<<<std::min<unsigned>(div_up(a.np + a.nq, 256), 2 * 152), 256, 0, s>>>(a.pt, a.np, a.q, a.nq, bbox);
         ++g_launches;
     }
 }
