@@ -24,7 +24,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_SEGZ, S_SEGCUR, S_SEGBIG, S_SEGLIST, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_GCELL2, S_GSTART2, S_GCUR2, S_GPART2, S_GPTS2, S_GIDX2, S_GLIST2, S_GNL2, S_SEGZ, S_SEGCUR, S_SEGBIG, S_SEGLIST, S_COUNT
 };
 
 struct Buf {
@@ -1139,17 +1139,28 @@ gs_status_t gs_overlap_ratio(gs_ctx_t *ctx, const gs_gaussians_t *p, const gs_ga
             amax = std::max(amax, std::max(std::fabs(lo[k]), std::fabs(lo[k] + ext[k])));
         g.margin = (float)(4e-6 * (emax + amax) + 1e-7);
         const size_t cells = (size_t)dims[0] * dims[1] * dims[2], nmax = std::max(np, nq);
-        gsl::NNScratch sc{};
-        GS_TRY(wsT(ctx, S_GCELL, nmax, &sc.cell));
-        GS_TRY(wsT(ctx, S_GSTART, cells + 1, &sc.start));
-        GS_TRY(wsT(ctx, S_GCUR, cells, &sc.cursor));
-        GS_TRY(wsT(ctx, S_GPART, gsl::scan_partials(cells + 1), &sc.partials));
-        GS_TRY(wsT(ctx, S_GPTS, nmax, &sc.spts));
-        GS_TRY(wsT(ctx, S_GIDX, nmax, &sc.sidx));
-        GS_TRY(wsT(ctx, S_GLIST, nmax, &sc.list));
-        GS_TRY(wsT(ctx, S_GNL, 1, &sc.n_list));
-        gsl::nn_grid(a.pt, (int)np, a.q, (int)nq, g, sc, a.nn_pq, a.d2, s);
-        gsl::nn_grid(a.q, (int)nq, a.pt, (int)np, g, sc, a.nn_qp, nullptr, s);
+        // one grid per set; each set's points in cell order are then the
+        // query order of its search in the other set's grid (neighbouring
+        // threads search the same cells)
+        gsl::NNScratch sq{}, sp{};
+        const int sl[2][8] = {{S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL},
+                              {S_GCELL2, S_GSTART2, S_GCUR2, S_GPART2, S_GPTS2, S_GIDX2, S_GLIST2, S_GNL2}};
+        gsl::NNScratch *scs[2] = {&sq, &sp};
+        for (int k = 0; k < 2; ++k) {
+            gsl::NNScratch &sc = *scs[k];
+            GS_TRY(wsT(ctx, sl[k][0], nmax, &sc.cell));
+            GS_TRY(wsT(ctx, sl[k][1], cells + 1, &sc.start));
+            GS_TRY(wsT(ctx, sl[k][2], cells, &sc.cursor));
+            GS_TRY(wsT(ctx, sl[k][3], gsl::scan_partials(cells + 1), &sc.partials));
+            GS_TRY(wsT(ctx, sl[k][4], nmax, &sc.spts));
+            GS_TRY(wsT(ctx, sl[k][5], nmax, &sc.sidx));
+            GS_TRY(wsT(ctx, sl[k][6], nmax, &sc.list));
+            GS_TRY(wsT(ctx, sl[k][7], 1, &sc.n_list));
+        }
+        gsl::nn_grid_build(a.q, (int)nq, g, sq, s);
+        gsl::nn_grid_build(a.pt, (int)np, g, sp, s);
+        gsl::nn_grid_search(a.pt, (int)np, sp.sidx, a.q, (int)nq, g, sq, a.nn_pq, a.d2, s);
+        gsl::nn_grid_search(a.q, (int)nq, sq.sidx, a.pt, (int)np, g, sp, a.nn_qp, nullptr, s);
         gsl::overlap_count(a, s);
     }
     unsigned long long c[2] = {0, 0};

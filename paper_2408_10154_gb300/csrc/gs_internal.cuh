@@ -402,8 +402,13 @@ void overlap_moved_bbox(const OverlapArgs &a, uint32_t *bbox, cudaStream_t s);
 // distance, ties to the smaller index): a grid search that stops once no
 // unsearched cell can hold a nearer target, and the brute-force sweep for
 // the queries whose search would run past kNNMaxRing rings
-void nn_grid(const float4 *A, int na, const float4 *B, int nb, const NNGrid &g, const NNScratch &sc, int32_t *nn,
-             float *d2, cudaStream_t s);
+// the grid of the targets B: their cells, per-cell starts, and the targets
+// (sidx: their indices) in cell order
+void nn_grid_build(const float4 *B, int nb, const NNGrid &g, const NNScratch &sc, cudaStream_t s);
+// the search of every query of A in the grid of B built into sc; thread t
+// takes query order[t] when order is given (a permutation of 0..na-1)
+void nn_grid_search(const float4 *A, int na, const int32_t *order, const float4 *B, int nb, const NNGrid &g,
+                    const NNScratch &sc, int32_t *nn, float *d2, cudaStream_t s);
 // |K| and the pairs within tau from the nearest neighbours both ways
 void overlap_count(const OverlapArgs &a, cudaStream_t s);
 

@@ -218,13 +218,16 @@ __global__ void k_cell_scatter(const float4 *pts, int n, const uint32_t *cell, u
     sidx[pos] = i;
 }
 
-__global__ void __launch_bounds__(256) k_nn_grid(const float4 *A, int na, const gsl::NNGrid g, const uint32_t *start,
-                                                 const float4 *spts, const int32_t *sidx, int32_t *nn, float *d2,
-                                                 int32_t *list, uint32_t *n_list)
+__global__ void __launch_bounds__(256) k_nn_grid(const float4 *A, int na, const int32_t *order, const gsl::NNGrid g,
+                                                 const uint32_t *start, const float4 *spts, const int32_t *sidx,
+                                                 int32_t *nn, float *d2, int32_t *list, uint32_t *n_list)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= na)
+    // thread t takes query order[t] (the queries in cell order: neighbouring
+    // lanes search the same cells) or query t
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= na)
         return;
+    const int i = order ? order[t] : t;
     const float4 a = A[i];
     const int cx = cell_axis(a.x, g.ox, g.inv_s, g.nx), cy = cell_axis(a.y, g.oy, g.inv_s, g.ny),
               cz = cell_axis(a.z, g.oz, g.inv_s, g.nz);
@@ -332,14 +335,10 @@ void overlap_moved_bbox(const OverlapArgs &a, uint32_t *bbox, cudaStream_t s)
     }
 }
 
-void nn_grid(const float4 *A, int na, const float4 *B, int nb, const NNGrid &g, const NNScratch &sc, int32_t *nn,
-             float *d2, cudaStream_t s)
+void nn_grid_build(const float4 *B, int nb, const NNGrid &g, const NNScratch &sc, cudaStream_t s)
 {
-    if (na <= 0)
-        return;
     const size_t cells = (size_t)g.nx * g.ny * g.nz;
     cudaMemsetAsync(sc.start, 0, sizeof(uint32_t) * (cells + 1), s);
-    cudaMemsetAsync(sc.n_list, 0, sizeof(uint32_t), s);
     if (nb > 0) {
         k_cell_count<<<div_up(nb, 256), 256, 0, s>>>(B, nb, g, sc.cell, sc.start);
         ++g_launches;
@@ -350,7 +349,16 @@ void nn_grid(const float4 *A, int na, const float4 *B, int nb, const NNGrid &g, 
         k_cell_scatter<<<div_up(nb, 256), 256, 0, s>>>(B, nb, sc.cell, sc.cursor, sc.spts, sc.sidx);
         ++g_launches;
     }
-    k_nn_grid<<<div_up(na, 256), 256, 0, s>>>(A, na, g, sc.start, sc.spts, sc.sidx, nn, d2, sc.list, sc.n_list);
+}
+
+void nn_grid_search(const float4 *A, int na, const int32_t *order, const float4 *B, int nb, const NNGrid &g,
+                    const NNScratch &sc, int32_t *nn, float *d2, cudaStream_t s)
+{
+    if (na <= 0)
+        return;
+    cudaMemsetAsync(sc.n_list, 0, sizeof(uint32_t), s);
+    k_nn_grid<<<div_up(na, 256), 256, 0, s>>>(A, na, order, g, sc.start, sc.spts, sc.sidx, nn, d2, sc.list,
+                                             sc.n_list);
     k_nn_list<<<div_up(na, kNNThreads * kNNQ), kNNThreads, 0, s>>>(A, sc.list, sc.n_list, B, nb, nn, d2);
     g_launches += 2;
 }
