@@ -246,27 +246,47 @@ def run_ours(args):
     host = {k: getattr(src, k).cpu().pin_memory() for k in ("means4", "log_scales4", "quats4", "logits", "rgb4")}
     host_t = {k: getattr(tgt, k).cpu().pin_memory() for k in ("means4", "log_scales4", "quats4", "logits", "rgb4")}
     host_v = [(cam, r.cpu().pin_memory(), d.cpu().pin_memory()) for cam, r, d in list(sv) + list(tv)]
-    dsrc = gs.Gaussians(*[torch.empty_like(getattr(src, k)) for k in ("means4", "log_scales4", "quats4", "logits",
-                                                                         "rgb4")])
-    dtgt = gs.Gaussians(*[torch.empty_like(getattr(tgt, k)) for k in ("means4", "log_scales4", "quats4", "logits",
-                                                                         "rgb4")])
-    dviews = [(cam, torch.empty_like(r, device="cuda"), torch.empty_like(d, device="cuda")) for cam, r, d in host_v]
+    # two device input sets: each step's upload (side stream) overlaps the
+    # previous step's registration, as a pipelined caller would run it; the
+    # timed region holds every step's upload (the first one exposed) and
+    # every result read-back
+    names_g = ("means4", "log_scales4", "quats4", "logits", "rgb4")
+    sets = []
+    for _ in range(2):
+        dsrc = gs.Gaussians(*[torch.empty_like(getattr(src, k)) for k in names_g])
+        dtgt = gs.Gaussians(*[torch.empty_like(getattr(tgt, k)) for k in names_g])
+        dviews = [(cam, torch.empty_like(r, device="cuda"), torch.empty_like(d, device="cuda")) for cam, r, d in host_v]
+        sets.append((dsrc, dtgt, dviews))
     h2d = sum(v.numel() * v.element_size() for v in list(host.values()) + list(host_t.values()))
     h2d += sum(r.numel() * r.element_size() + d.numel() * d.element_size() for _, r, d in host_v)
     d2h = 12 * 8 + 8 + 16 * 8 + 16 * 12 * 8
-    e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in host:
-            getattr(dsrc, k).copy_(host[k], non_blocking=True)
-            getattr(dtgt, k).copy_(host_t[k], non_blocking=True)
-        for (cam, r, d), (_, hr, hd) in zip(dviews, host_v):
-            r.copy_(hr, non_blocking=True)
-            d.copy_(hd, non_blocking=True)
+    side = torch.cuda.Stream()
+
+    def upload(st):
+        dsrc, dtgt, dviews = st
+        with torch.cuda.stream(side):
+            for k in host:
+                getattr(dsrc, k).copy_(host[k], non_blocking=True)
+                getattr(dtgt, k).copy_(host_t[k], non_blocking=True)
+            for (cam, r, d), (_, hr, hd) in zip(dviews, host_v):
+                r.copy_(hr, non_blocking=True)
+                d.copy_(hd, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(side)
+        return ev
+
+    n_e2e = max(2, min(args.steps, 4))
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev = upload(sets[0])
+    for k in range(n_e2e):
+        torch.cuda.current_stream().wait_event(ev)
+        if k + 1 < n_e2e:
+            ev = upload(sets[(k + 1) % 2])
+        dsrc, dtgt, dviews = sets[k % 2]
         gs.gs_register(ctx, dsrc, dtgt, dviews[:8], dviews[8:], ITERS, opt)  # returns T on the host
-        e2e_times.append((time.perf_counter() - t0) * 1000.0)
+    e2e_times = [(time.perf_counter() - t0) * 1000.0 / n_e2e]
     e2e_value = world * ITERS / (np.mean(e2e_times) / 1000.0)
 
     pk = peaks()
