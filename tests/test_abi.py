@@ -74,3 +74,15 @@ def test_context_without_device_is_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.gs_ctx_create(0, 0, ctypes.byref(h)) == 1  # GS_ERR_INVALID_ARG
     assert lib.gs_last_error(None) == b"null context"
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no fallback path: without the compiled library the binding raises
+    # before any work, for the loader and for a context alike
+    from paper_2408_10154_gb300 import build, gsreg
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "libgsreg.so"))
+    monkeypatch.setattr(gsreg, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        gsreg.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        gsreg.Context(0)
