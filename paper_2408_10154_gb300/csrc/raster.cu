@@ -358,34 +358,43 @@ struct Twist6 {
     }
 };
 
-// The tile's twist: each warp reduces its lanes' compensated sums with
-// TwoSum butterflies, and threads 0..5 join the warps' (hi, lo) pairs the
-// same way in a fixed order and store them (no FP64 here: the FP64 pipe is a
-// small fraction of the FP32 one, and FP64 work in every warp kept it busy
-// and lengthened every CTA's tail).
+// The tile's twist: each of the first nw warps (the ones whose threads
+// accumulated anything) reduces its lanes' compensated sums with TwoSum
+// butterflies, and threads 0..5 join those warps' (hi, lo) pairs the same
+// way in a fixed order and store them.  Leaving out the warps that hold
+// only zeros changes no bit: a TwoSum of (0, 0) leaves a pair as it is.
+// (No FP64 here: the FP64 pipe is a small fraction of the FP32 one, and
+// FP64 work in every warp kept it busy and lengthened every CTA's tail.)
 template <int WARPS>
-__device__ __forceinline__ void store_tile_twist(const Twist6 &tw, float (*s_tw)[6][2], float2 *out)
+__device__ __forceinline__ void store_tile_twist(const Twist6 &tw, int nw, float (*s_tw)[6][2], float2 *out)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < nw) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        float hi = tw.s(k), lo = -tw.c(k);
+        for (int k = 0; k < 6; ++k) {
+            float hi = tw.s(k), lo = -tw.c(k);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
-            two_sum_add(hi, lo, bh, bl);
-        }
-        if (lane == 0) {
-            s_tw[warp][k][0] = hi;
-            s_tw[warp][k][1] = lo;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
+                two_sum_add(hi, lo, bh, bl);
+            }
+            if (lane == 0) {
+                s_tw[warp][k][0] = hi;
+                s_tw[warp][k][1] = lo;
+            }
         }
     }
     __syncthreads();
     if (threadIdx.x < 6) {
-        float hi = s_tw[0][threadIdx.x][0], lo = s_tw[0][threadIdx.x][1];
+        float hi = 0.0f, lo = 0.0f;
+        if (nw > 0) {
+            hi = s_tw[0][threadIdx.x][0];
+            lo = s_tw[0][threadIdx.x][1];
+        }
 #pragma unroll
         for (int w = 1; w < WARPS; ++w)
-            two_sum_add(hi, lo, s_tw[w][threadIdx.x][0], s_tw[w][threadIdx.x][1]);
+            if (w < nw)
+                two_sum_add(hi, lo, s_tw[w][threadIdx.x][0], s_tw[w][threadIdx.x][1]);
         out[threadIdx.x] = make_float2(hi, lo);
     }
 }
@@ -574,7 +583,7 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     return true;
 }
 
-static_assert(kBwd2Chunk <= kBwd2Threads, "one thread stages one record");
+static_assert(kBwd2Chunk <= kBwd2Threads && kBwd2Chunk % 32 == 0, "one thread stages one record");
 
 template <bool REG, bool FULL>
 __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(const gsl::RasterArgs a)
@@ -618,9 +627,13 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     __shared__ float s_cc[3];
     float cc[3];
     load_pivot(a.c_cam, vp, s_cc, cc);
+    // one thread per record of a chunk runs chain_twist, so only threads
+    // below the largest chunk (min(maxl, chunk)) ever hold twist sums
     __shared__ float s_acc[12][kBwd2Threads];
     const Twist6 tw{&s_acc[0][threadIdx.x]};
-    tw.zero();
+    if ((int)threadIdx.x < kBwd2Chunk)
+        tw.zero();
+    const int twist_warps = (min(maxl, kBwd2Chunk) + 31) / 32;
     for (int hi = maxl; hi > 0; hi -= kBwd2Chunk) {
         const int lo = max(hi - kBwd2Chunk, 0), cnt = hi - lo;
         __syncthreads();
@@ -696,7 +709,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     }
     if (!a.tile_twist)
         return;
-    store_tile_twist<kBwd2Warps>(tw, s_tw, a.tile_twist + (size_t)t * 6);
+    store_tile_twist<kBwd2Warps>(tw, twist_warps, s_tw, a.tile_twist + (size_t)t * 6);
 }
 
 template <bool REG, bool FULL>
