@@ -399,17 +399,6 @@ __device__ __forceinline__ void store_tile_twist(const Twist6 &tw, int nw, float
     }
 }
 
-// camera-frame pivot of keyframe vp as floats, converted once per CTA
-__device__ __forceinline__ void load_pivot(const double *c_cam, int vp, float *s_cc, float *cc)
-{
-    if (threadIdx.x < 3)
-        s_cc[threadIdx.x] = c_cam ? (float)c_cam[3 * vp + threadIdx.x] : 0.0f;
-    __syncthreads();
-    cc[0] = s_cc[0];
-    cc[1] = s_cc[1];
-    cc[2] = s_cc[2];
-}
-
 // d(screen params) of one (tile, Gaussian) -> camera-frame twist (w, v)
 // about cc (camera frame), added to tw.  G = {dL/du, dL/dv,
 // 2 dL/dSigma2D_00, 2 dL/dSigma2D_01, 2 dL/dSigma2D_11, dL/dz, ...} (the 2D
@@ -608,6 +597,12 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     const float ya = (float)(ty * kTile + (warp >> 1) * 8) + 0.5f, yb = ya + 7.0f;
     const bool cull = a.alpha_min > 0.0f;
     const uint2 rg = a.ranges[t];
+    // the keyframe's camera-frame pivot as floats, read with the pixel state
+    // so that the two loads overlap, and shared behind the same barrier
+    __shared__ float s_cc[3];
+    float pivot = 0.0f;
+    if (threadIdx.x < 3 && a.c_cam)
+        pivot = (float)a.c_cam[3 * vp + threadIdx.x];
     PixAdj P0, P1;
     const float gain = (REG && d.exposure) ? a.expo32[2 * vp] : 1.0f;
     pix_adj_init<REG>(P0, d, a, px, py0, a.bg, gain);
@@ -618,15 +613,14 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
         ml = max(ml, __shfl_xor_sync(0xffffffffu, ml, o));
     if (lane == 0)
         s_maxl[warp] = ml;
+    if (threadIdx.x < 3)
+        s_cc[threadIdx.x] = pivot;
     __syncthreads();
     int maxl = 0;
 #pragma unroll
     for (int w = 0; w < kBwd2Warps; ++w)
         maxl = max(maxl, s_maxl[w]);
-
-    __shared__ float s_cc[3];
-    float cc[3];
-    load_pivot(a.c_cam, vp, s_cc, cc);
+    const float cc[3] = {s_cc[0], s_cc[1], s_cc[2]};
     // one thread per record of a chunk runs chain_twist, so only threads
     // below the largest chunk (min(maxl, chunk)) ever hold twist sums
     __shared__ float s_acc[12][kBwd2Threads];
