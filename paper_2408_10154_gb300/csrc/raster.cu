@@ -578,9 +578,10 @@ template <bool REG, bool FULL>
 __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(const gsl::RasterArgs a)
 {
     constexpr int NG = FULL ? 10 : 6;
-    extern __shared__ float s_slots[];  // [NG][warps][chunk]
+    extern __shared__ float4 s_dyn[];  // declared float4: 16-byte aligned for the float4 zeroing
+    float *const s_slots = reinterpret_cast<float *>(s_dyn);  // [NG][warps][chunk]
     __shared__ float4 s0[kBwd2Chunk], s1[kBwd2Chunk], s2[kBwd2Chunk];
-    __shared__ uint32_t s_rec[kBwd2Chunk];
+    __shared__ float4 s_x0[kBwd2Chunk], s_x1[kBwd2Chunk];  // the records' camera-frame mean and covariance
     __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
     __shared__ int s_maxl[kBwd2Warps];
     __shared__ float s_tw[kBwd2Warps][6][2];
@@ -633,14 +634,20 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
             const uint32_t r = a.vals[rg.x + lo + threadIdx.x];
-            s_rec[threadIdx.x] = r;
             const float4 *R = a.rec + 3 * (size_t)r;
             s0[threadIdx.x] = R[0];
             s1[threadIdx.x] = stage_cutoff(R[1], a);
             s2[threadIdx.x] = R[2];
+            if (a.tile_twist) {
+                // staged with the record (not read after the walk) so that
+                // these loads overlap the ones above
+                s_x0[threadIdx.x] = a.aux[2 * (size_t)r];
+                s_x1[threadIdx.x] = a.aux[2 * (size_t)r + 1];
+            }
         }
-        for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwd2Chunk; k += kBwd2Threads)
-            s_slots[k] = 0.0f;
+        static_assert(NG * kBwd2Warps * kBwd2Chunk % 4 == 0, "slots zeroed as float4");
+        for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwd2Chunk / 4; k += kBwd2Threads)
+            s_dyn[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         __syncthreads();
         // this warp's pixels never reach past wl: skip the list tail
         const int wl = min(s_maxl[warp] - lo, cnt);
@@ -690,7 +697,6 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
                 G[k] = s;
                 any |= s != 0.0f;
             }
-            const uint32_t r = s_rec[threadIdx.x];
             if (FULL) {
                 float *dst = a.dup_grads + (size_t)(rg.x + lo + threadIdx.x) * 10;
 #pragma unroll
@@ -698,7 +704,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
                     dst[k] = G[k];
             }
             if (any && a.tile_twist)
-                chain_twist(G, s1[threadIdx.x], a.aux[2 * (size_t)r], a.aux[2 * (size_t)r + 1], d.fx, d.fy, cc, tw);
+                chain_twist(G, s1[threadIdx.x], s_x0[threadIdx.x], s_x1[threadIdx.x], d.fx, d.fy, cc, tw);
         }
     }
     if (!a.tile_twist)
