@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
             float g[NG];
 #pragma unroll
             for (int k = 0; k < NG; ++k)
-                g[k] = 0.0f;
+                g[k] = -0.0f;  // -0 + x == x for every x (not so +0): the first additions fold away
             const float4 q0 = s0[j];
             const float4 q1 = s1[j];
             const bool c0 = pix_adj_pair<FULL, !REG>(P0, lo + j, q0, q1, &s2[j], a, g);
@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
             bool any = false;
 #pragma unroll
             for (int k = 0; k < NG; ++k) {
-                float s = 0.0f;
+                float s = -0.0f;
 #pragma unroll
                 for (int w = 0; w < kBwd2Warps; ++w)
                     s += s_slots[(k * kBwd2Warps + w) * kBwd2Chunk + threadIdx.x];
