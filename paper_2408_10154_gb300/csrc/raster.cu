@@ -295,9 +295,11 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
             a.tile_expo[2 * (size_t)t + 1] = sb;
         }
         if (a.tile_pairs) {
-            a.tile_pairs[t] += np;
+            // reductions without a return (no load to wait for as the CTA
+            // ends); one writer per tile, integer sums: deterministic
+            atomicAdd(&a.tile_pairs[t], np);
             if (X & kFwdCount)
-                a.tile_pairs[a.n_tiles + t] += nc;
+                atomicAdd(&a.tile_pairs[a.n_tiles + t], nc);
         }
     }
 }
