@@ -133,24 +133,37 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
     __shared__ uint8_t s_sel[8][256];  // per warp: batch positions that may hit its patch
     __shared__ float s_red[8];
     const uint32_t t = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
-    const VpDesc &d = a.vps[a.tile_vp[t]];
+    // The first batch is staged before any barrier (nothing has read the
+    // staging arrays yet) and its list entry is read before the tile's
+    // descriptor is used, so that the two chains of dependent loads (range,
+    // entry, record; keyframe index, descriptor) overlap.
+    const uint32_t vp = a.tile_vp[t];
+    const uint2 rg = a.ranges[t];
+    const bool staged0 = rg.x + threadIdx.x < rg.y;
+    const uint32_t v0 = staged0 ? a.vals[rg.x + threadIdx.x] : 0u;
+    const VpDesc &d = a.vps[vp];
     const PixelCoord p = pixel_of(d, t);
+    auto stage = [&](uint32_t v) {
+        const float4 *R = a.rec + 3 * (size_t)v;
+        s0[threadIdx.x] = R[0];
+        s1[threadIdx.x] = stage_cutoff(R[1], a);
+        s2[threadIdx.x] = R[2];
+    };
+    if (staged0)
+        stage(v0);
     const float pxf = (float)p.px + 0.5f, pyf = (float)p.py + 0.5f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool cull = a.alpha_min > 0.0f;
-    const uint2 rg = a.ranges[t];
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     int last = 0, n_contrib = 0;
     bool done = !p.inside;
     for (uint32_t b = rg.x; b < rg.y; b += 256) {
-        if (__syncthreads_count(done) == 256)
-            break;
-        const uint32_t idx = b + threadIdx.x;
-        if (idx < rg.y) {
-            const float4 *R = a.rec + 3 * (size_t)a.vals[idx];
-            s0[threadIdx.x] = R[0];
-            s1[threadIdx.x] = stage_cutoff(R[1], a);
-            s2[threadIdx.x] = R[2];
+        if (b != rg.x) {
+            if (__syncthreads_count(done) == 256)
+                break;
+            const uint32_t idx = b + threadIdx.x;
+            if (idx < rg.y)
+                stage(a.vals[idx]);
         }
         __syncthreads();
         const int cnt = (int)min(256u, rg.y - b);
@@ -600,6 +613,27 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     const float ya = (float)(ty * kTile + (warp >> 1) * 8) + 0.5f, yb = ya + 7.0f;
     const bool cull = a.alpha_min > 0.0f;
     const uint2 rg = a.ranges[t];
+    // staging of one record of a chunk (thread i, chunk position i)
+    auto stage = [&](uint32_t r) {
+        const float4 *R = a.rec + 3 * (size_t)r;
+        s0[threadIdx.x] = R[0];
+        s1[threadIdx.x] = stage_cutoff(R[1], a);
+        s2[threadIdx.x] = R[2];
+        if (a.tile_twist) {
+            // the camera-frame mean and covariance, staged with the record
+            // (not read after the walk) so that these loads overlap
+            s_x0[threadIdx.x] = a.aux[2 * (size_t)r];
+            s_x1[threadIdx.x] = a.aux[2 * (size_t)r + 1];
+        }
+    };
+    // The walk's first chunk ends at the tile's last contributor, known only
+    // after the barrier below.  It is staged before it on the guess that the
+    // list's last entry contributes (checked after the barrier; a wrong guess
+    // stages the chunk again), so that its loads overlap the pixel state's.
+    const int n_list = (int)(rg.y - rg.x);
+    const int lo_guess = max(n_list - kBwd2Chunk, 0);
+    const bool guess_row = (int)threadIdx.x < n_list - lo_guess;
+    const uint32_t r_guess = guess_row ? a.vals[rg.x + lo_guess + threadIdx.x] : 0u;
     // the keyframe's camera-frame pivot as floats, read with the pixel state
     // so that the two loads overlap, and shared behind the same barrier
     __shared__ float s_cc[3];
@@ -610,6 +644,8 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     const float gain = (REG && d.exposure) ? a.expo32[2 * vp] : 1.0f;
     pix_adj_init<REG>(P0, d, a, px, py0, a.bg, gain);
     pix_adj_init<REG>(P1, d, a, px, py0 + 4, a.bg, gain);
+    if (guess_row)
+        stage(r_guess);
     int ml = max(P0.last, P1.last);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -634,19 +670,9 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     for (int hi = maxl; hi > 0; hi -= kBwd2Chunk) {
         const int lo = max(hi - kBwd2Chunk, 0), cnt = hi - lo;
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t r = a.vals[rg.x + lo + threadIdx.x];
-            const float4 *R = a.rec + 3 * (size_t)r;
-            s0[threadIdx.x] = R[0];
-            s1[threadIdx.x] = stage_cutoff(R[1], a);
-            s2[threadIdx.x] = R[2];
-            if (a.tile_twist) {
-                // staged with the record (not read after the walk) so that
-                // these loads overlap the ones above
-                s_x0[threadIdx.x] = a.aux[2 * (size_t)r];
-                s_x1[threadIdx.x] = a.aux[2 * (size_t)r + 1];
-            }
-        }
+        // hi == n_list only for a first chunk the guess staged already
+        if (hi != n_list && (int)threadIdx.x < cnt)
+            stage(a.vals[rg.x + lo + threadIdx.x]);
         static_assert(NG * kBwd2Warps * kBwd2Chunk % 4 == 0, "slots zeroed as float4");
         for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwd2Chunk / 4; k += kBwd2Threads)
             s_dyn[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
