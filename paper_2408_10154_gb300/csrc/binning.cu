@@ -729,15 +729,7 @@ __global__ void __launch_bounds__(kSegTileThreads) k_seg_ranges(const gsl::BinAr
 
 constexpr uint32_t kSegSmall = 4;  // tiles of a record placed by its own thread; more: by the whole warp
 constexpr int kSegPerThread = 2;    // records per thread (more cursor atomics in flight per warp)
-
-__device__ __forceinline__ void seg_put(const gsl::BinArgs &a, uint32_t t, uint32_t zb, uint32_t r)
-{
-    const uint32_t pos = atomicAdd(a.seg_cursor + t, 1u);
-    if (pos < a.capacity) {
-        a.tkeys[0][pos] = zb;
-        a.vals[0][pos] = r;
-    }
-}
+constexpr int kSegRounds = 8;       // a large record: rounds of 32 tiles whose atomics are in flight together
 
 // kSegPerThread records per thread (kSegThreads apart, so each load is
 // coalesced): a visible one writes (depth bits, record) into the lists of
@@ -745,8 +737,11 @@ __device__ __forceinline__ void seg_put(const gsl::BinArgs &a, uint32_t t, uint3
 // from the tiles' cursors, all cursor atomics of the thread in flight
 // before its stores.  Records with more than kSegSmall tiles are spread over
 // the lanes of their warp, one record at a time, so a splat covering
-// thousands of tiles does not serialise one thread.  Positions at or past
-// the capacity are dropped (the capacity flag is already set).
+// thousands of tiles does not serialise one thread, kSegRounds rounds of 32
+// tiles with all their atomics in flight before the stores (a record over a
+// whole 1200x680 frame is 101 rounds: one atomic round trip each made it
+// the kernel's critical path).  Positions at or past the capacity are
+// dropped (the capacity flag is already set).
 __global__ void __launch_bounds__(kSegThreads) k_seg_place(const gsl::BinArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -810,8 +805,23 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_place(const gsl::BinArgs a)
             const uint32_t c = __shfl_sync(0xffffffffu, cnt[q], src), b = __shfl_sync(0xffffffffu, t0[q], src);
             const uint32_t ww = __shfl_sync(0xffffffffu, w[q], src), tt = __shfl_sync(0xffffffffu, tx[q], src);
             const uint32_t z = __shfl_sync(0xffffffffu, zb[q], src), r = __shfl_sync(0xffffffffu, rr[q], src);
-            for (uint32_t k = lane; k < c; k += 32)
-                seg_put(a, b + (k / ww) * tt + k % ww, z, r);
+            for (uint32_t k0 = 0; k0 < c; k0 += 32 * kSegRounds) {
+                uint32_t pos[kSegRounds];
+#pragma unroll
+                for (int u = 0; u < kSegRounds; ++u) {
+                    const uint32_t k = k0 + 32 * u + lane;
+                    if (k < c)
+                        pos[u] = atomicAdd(a.seg_cursor + b + (k / ww) * tt + k % ww, 1u);
+                }
+#pragma unroll
+                for (int u = 0; u < kSegRounds; ++u) {
+                    const uint32_t k = k0 + 32 * u + lane;
+                    if (k < c && pos[u] < a.capacity) {
+                        a.tkeys[0][pos[u]] = z;
+                        a.vals[0][pos[u]] = r;
+                    }
+                }
+            }
         }
     }
 }
