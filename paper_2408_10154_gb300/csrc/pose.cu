@@ -199,15 +199,19 @@ __device__ void exposure_step(double *e, const double *g, int k, int iters, floa
     }
 }
 
+// 1024 threads per block: a keyframe's 3,225 tile pairs (1200x680) are
+// about three loads deep per thread (256 threads waited on thirteen).
+constexpr int kPoseThreads = 1024, kPoseWarps = kPoseThreads / 32;
+
 // one block per keyframe: reduce the tile twists and losses in a fixed
 // order, rotate the twist to the world frame, then (update) take the step.
 // The step's FP64 work runs on warp 0: Adam on the six twist components in
 // parallel (one lane each -- serially, their pow/sqrt chains dominated the
 // update, the FP64 pipe being a small fraction of the FP32 one), then the
 // exponential-map update, the exposure step and the pivots on lane 0.
-__global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
+__global__ void __launch_bounds__(kPoseThreads) k_pose_update(const gsl::PoseArgs a)
 {
-    __shared__ float s[8][9][2];
+    __shared__ float s[kPoseWarps][9][2];
     __shared__ double s_tot[9], s_g[6], s_xi[6];
     const int vp = blockIdx.x;
     const VpDesc &d = a.vps[vp];
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(256) k_pose_update(const gsl::PoseArgs a)
     const int lane = threadIdx.x;
     if (lane < 9) {
         float h = s[0][lane][0], l = s[0][lane][1];
-        for (int w = 1; w < 8; ++w)
+        for (int w = 1; w < kPoseWarps; ++w)
             two_sum_add(h, l, s[w][lane][0], s[w][lane][1]);
         s_tot[lane] = (double)h + (double)l;
     }
@@ -551,7 +555,7 @@ void pose_init(const PoseArgs &a, cudaStream_t s)
 void pose_update(const PoseArgs &a, cudaStream_t s)
 {
     if (a.n_vps > 0) {
-        k_pose_update<<<a.n_vps, 256, 0, s>>>(a);
+        k_pose_update<<<a.n_vps, kPoseThreads, 0, s>>>(a);
         ++g_launches;
     }
 }
@@ -585,7 +589,7 @@ void loss(const VpDesc *vps, int n_vps, uint32_t n_tiles, const uint32_t *tile_v
     a.n_vps = n_vps;
     a.tile_loss = tile_loss;
     a.loss = loss_out;
-    k_pose_update<<<n_vps, 256, 0, s>>>(a);
+    k_pose_update<<<n_vps, kPoseThreads, 0, s>>>(a);
     g_launches += 2;
 }
 
@@ -606,7 +610,7 @@ void loss_reduce(const VpDesc *vps, int n_vps, const float *tile_loss, double *l
     a.n_vps = n_vps;
     a.tile_loss = tile_loss;
     a.loss = loss_out;
-    k_pose_update<<<n_vps, 256, 0, s>>>(a);
+    k_pose_update<<<n_vps, kPoseThreads, 0, s>>>(a);
     ++g_launches;
 }
 
