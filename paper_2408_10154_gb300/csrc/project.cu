@@ -26,6 +26,11 @@ using namespace gsk;
 // half-sizes sqrt(-2 tau Sigma00), sqrt(-2 tau Sigma11) about (u, v); tile t
 // meets it when its centres [16 t + 0.5, 16 t + 15.5] meet the box.  An
 // opacity below alpha_min e^-0.06 empties the rectangle.
+// the reciprocal of the tile size, a power of two: x * kInvTile is x / 16
+// correctly rounded
+constexpr float kInvTile = 1.0f / (float)kTile;
+static_assert(kTile == 16, "kInvTile is exact for a power-of-two tile");
+
 __device__ __forceinline__ void tighten(float ca, float cb, float cc, float o, float u, float v, float skip_below,
                                         int TX, int TY, int &x0, int &x1, int &y0, int &y1)
 {
@@ -43,11 +48,11 @@ __device__ __forceinline__ void tighten(float ca, float cb, float cc, float o, f
     const float ex = fmaf(sqrtf(s * C), 1.001f, 0.01f), ey = fmaf(sqrtf(s * A), 1.001f, 0.01f);
     if (!(ex >= 0.0f) || !(ey >= 0.0f))
         return;
-    const float B16 = (float)kTile;
-    const float tx0 = fminf(fmaxf(ceilf((u - ex - 15.5f) / B16), 0.0f), (float)TX);
-    const float tx1 = fminf(fmaxf(floorf((u + ex - 0.5f) / B16) + 1.0f, 0.0f), (float)TX);
-    const float ty0 = fminf(fmaxf(ceilf((v - ey - 15.5f) / B16), 0.0f), (float)TY);
-    const float ty1 = fminf(fmaxf(floorf((v + ey - 0.5f) / B16) + 1.0f, 0.0f), (float)TY);
+    const float iB = kInvTile;
+    const float tx0 = fminf(fmaxf(ceilf((u - ex - 15.5f) * iB), 0.0f), (float)TX);
+    const float tx1 = fminf(fmaxf(floorf((u + ex - 0.5f) * iB) + 1.0f, 0.0f), (float)TX);
+    const float ty0 = fminf(fmaxf(ceilf((v - ey - 15.5f) * iB), 0.0f), (float)TY);
+    const float ty1 = fminf(fmaxf(floorf((v + ey - 0.5f) * iB) + 1.0f, 0.0f), (float)TY);
     x0 = max(x0, (int)tx0);
     x1 = min(x1, (int)tx1);
     y0 = max(y0, (int)ty0);
@@ -202,11 +207,13 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
                     if (a.smooth) {
                         x0 = 0; x1 = TX; y0 = 0; y1 = TY;
                     } else {
-                        const float B = (float)kTile;
-                        const float fx0 = floorf(__fdiv_rn(sub_rn(u, rf), B));
-                        const float fx1 = add_rn(floorf(__fdiv_rn(add_rn(u, rf), B)), 1.0f);
-                        const float fy0 = floorf(__fdiv_rn(sub_rn(vv, rf), B));
-                        const float fy1 = add_rn(floorf(__fdiv_rn(add_rn(vv, rf), B)), 1.0f);
+                        // x / 16 as x * (1/16): the same correctly rounded
+                        // value (a power of two), without a division
+                        const float iB = kInvTile;
+                        const float fx0 = floorf(mul_rn(sub_rn(u, rf), iB));
+                        const float fx1 = add_rn(floorf(mul_rn(add_rn(u, rf), iB)), 1.0f);
+                        const float fy0 = floorf(mul_rn(sub_rn(vv, rf), iB));
+                        const float fy1 = add_rn(floorf(mul_rn(add_rn(vv, rf), iB)), 1.0f);
                         x0 = (int)fminf(fmaxf(fx0, 0.0f), (float)TX);
                         x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)TX);
                         y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)TY);
