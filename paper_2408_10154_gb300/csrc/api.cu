@@ -237,6 +237,10 @@ void add_vp(Plan &P, const gs_gaussians_t *g, const gs_camera_t &c, int set, int
     d.tile_base = (uint32_t)P.n_tiles;
     d.diff_base = (uint32_t)P.n_diff;
     d.pix_base = P.n_pix;
+    // the loss means' FP32 factors, rounded as the kernels would round them
+    const int64_t HW = (int64_t)c.width * c.height;
+    d.inv3hw = 1.0f / (3.0f * (float)HW);
+    d.invhw = 1.0f / (float)HW;
     d.t_rgb = trgb;
     d.t_depth = tdepth;
     d.set = set;

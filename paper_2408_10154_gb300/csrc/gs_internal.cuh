@@ -47,6 +47,7 @@ struct VpDesc {
     float lambda_c;        // tracking loss colour weight
     int exposure;          // 1: the registration loss compares e^a I^ + b (Supp. B) and fits (a, b)
     float lr_exposure;
+    float inv3hw, invhw;   // 1 / (3 W H) and 1 / (W H) in FP32 (the L1 means), set on the host
 };
 
 // A projection group: vps that share one Gaussian set and are projected by

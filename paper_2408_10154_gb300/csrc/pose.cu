@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256) k_loss_tiles(const VpDesc *vps, const uin
     float l = 0.0f;
     if (px < d.W && py < d.H) {
         const int64_t HW = (int64_t)d.W * d.H, off = (int64_t)py * d.W + px;
-        const float inv3 = 1.0f / (3.0f * (float)HW), inv1 = 1.0f / (float)HW;
+        const float inv3 = d.inv3hw, inv1 = d.invhw;
         auto sg = [](float e) -> float { return e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f); };
         for (int ch = 0; ch < 3; ++ch) {
             const float e = rgb[3 * d.pix_base + ch * HW + off] - d.t_rgb[ch * HW + off];

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
         }
         const float e0 = o0 - d.t_rgb[off], e1 = o1 - d.t_rgb[HW + off], e2 = o2 - d.t_rgb[2 * HW + off];
         const float ed = D - d.t_depth[off];
-        const float inv3 = 1.0f / (3.0f * (float)HW), inv1 = 1.0f / (float)HW;
+        const float inv3 = d.inv3hw, inv1 = d.invhw;
         lsum = (fabsf(e0) + fabsf(e1) + fabsf(e2)) * inv3 + fabsf(ed) * inv1;
         auto sg = [](float e) -> uint32_t { return e > 0.0f ? 1u : (e < 0.0f ? 2u : 0u); };
         a.code[pix] = (uint8_t)(sg(e0) | (sg(e1) << 2) | (sg(e2) << 4) | (sg(ed) << 6));
@@ -500,7 +500,7 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
             const uint32_t c = a.code[pix];
             auto dec = [](uint32_t v) -> float { return v == 1u ? 1.0f : (v == 2u ? -1.0f : 0.0f); };
             // registration: means over 3HW and HW; tracking: mask weight x lambda_c, x (1 - lambda_c)
-            float inv3 = 1.0f / (3.0f * (float)HW), inv1 = 1.0f / (float)HW;
+            float inv3 = d.inv3hw, inv1 = d.invhw;
             if (d.loss_kind == 1) {
                 const float w = a.trk_w[pix];
                 inv3 = w * d.lambda_c;
