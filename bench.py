@@ -50,11 +50,11 @@ FWD_FLOPS_CONTRIB = 41.0
 BWD_FLOPS_CONTRIB = 64.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
 # the current kernel; None while the kernel has changed since the capture
-BWD_TRAFFIC_BYTES = 185.618944e6
+BWD_TRAFFIC_BYTES = 185.855232e6
 # the same capture's smsp__issue_active (fraction of cycles issuing an
 # instruction): the adjoint is bound by instruction issue, of which the
 # counted flops are a part
-BWD_ISSUE_ACTIVE = 0.835
+BWD_ISSUE_ACTIVE = 0.827
 SMS = 152
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
