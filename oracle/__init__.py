@@ -15,8 +15,8 @@ Every function takes numpy arrays in the layout of the C-ABI inputs:
 Gaussians as float32 ``means4 [n,4]``, ``log_scales4 [n,4]``, ``quats4 [n,4]``
 (w, x, y, z), ``logits [n]``, ``rgb4 [n,4]``; a camera as float32
 ``cam18 = [fx, fy, cx, cy, W, H, world_to_cam (3x4 row-major)]``; options
-as float32 ``opt10 = [tile, z_near, dilation, alpha_min, alpha_max, t_min,
-bg_r, bg_g, bg_b, smooth]``; poses as float64 ``[3,4]`` (object -> world).
+as float32 ``opt11 = [tile, z_near, dilation, alpha_min, alpha_max, t_min,
+bg_r, bg_g, bg_b, smooth, tight]``; poses as float64 ``[3,4]`` (object -> world).
 """
 from __future__ import annotations
 
@@ -35,10 +35,14 @@ _lock = threading.Lock()
 _lib = None
 
 # default options: 16-pixel tiles, near plane 0.2 m, dilation 0.3 px^2,
-# alpha in [1/255, 0.99], early stop below transmittance 1e-4, black background
-DEFAULT_OPT = np.array([16, 0.2, 0.3, 1.0 / 255.0, 0.99, 1e-4, 0, 0, 0, 0], dtype=np.float32)
+# alpha in [1/255, 0.99], early stop below transmittance 1e-4, black
+# background, tight tile rectangles (the alpha-threshold box of each record)
+DEFAULT_OPT = np.array([16, 0.2, 0.3, 1.0 / 255.0, 0.99, 1e-4, 0, 0, 0, 0, 1], dtype=np.float32)
+# the same with the plain 3-sigma tile rectangles
+LOOSE_OPT = np.array([16, 0.2, 0.3, 1.0 / 255.0, 0.99, 1e-4, 0, 0, 0, 0, 0], dtype=np.float32)
 # smooth options (finite-difference checks): no thresholds, no radius cull
-SMOOTH_OPT = np.array([16, 0.2, 0.3, 0.0, 1.0, 0.0, 0, 0, 0, 1], dtype=np.float32)
+SMOOTH_OPT = np.array([16, 0.2, 0.3, 0.0, 1.0, 0.0, 0, 0, 0, 1, 0], dtype=np.float32)
+N_OPT = 11
 # registration hyper-parameters {lr_rot, lr_trans, beta1, beta2, eps, final lr fraction}:
 # learning rates of the paper's real-data column (Supp. B, loop-closure table);
 # Adam constants and the cosine decay to 0.1 % are this implementation's reading
@@ -48,13 +52,14 @@ DEFAULT_HYPER = np.array([0.015, 0.005, 0.8, 0.99, 1e-8, 0.001], dtype=np.float6
 def build(force: bool = False) -> str:
     """Compile gs_oracle.c into oracle/_build/liboracle.so (gcc, C11,
     -ffp-contract=off so that the FP32 mirror is evaluated exactly as
-    written)."""
+    written; OpenMP for the optional multi-threaded loops, one thread unless
+    set_threads asks for more)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
            "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -72,6 +77,8 @@ def _load():
         L = ctypes.c_long
         lib.or_exp32.argtypes = [ctypes.c_float]
         lib.or_exp32.restype = ctypes.c_float
+        lib.or_log32.argtypes = [ctypes.c_float]
+        lib.or_log32.restype = ctypes.c_float
         lib.or_project32.argtypes = [I, P, P, P, P, P, P, P, P, P]
         lib.or_project64.argtypes = [I, P, P, P, P, P, P, P, P]
         lib.or_bin.argtypes = [I, P, P, P, P, I, P, P, P, P, P, L, P, P]
@@ -95,8 +102,19 @@ def _load():
         for f in ("or_project32", "or_project64", "or_bin", "or_render", "or_backward",
                   "or_pose_step", "or_register_view", "or_transform"):
             getattr(lib, f).restype = ctypes.c_int
+        lib.or_contrib_sig.argtypes = [I, P, P, P, P, P, P, P, P, P]
+        lib.or_contrib_sig.restype = I
+        lib.or_set_threads.argtypes = [I]
+        lib.or_set_threads.restype = I
+        lib.or_set_threads(1)
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (compositing rows, adjoint
+    bands); results do not depend on it.  Returns the number in effect."""
+    return int(_load().or_set_threads(int(n)))
 
 
 def _f32(a, shape=None):
@@ -115,6 +133,13 @@ def _f64(a, shape=None):
 
 def _p(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _opt(opt):
+    o = _f32(opt)
+    if o.shape != (N_OPT,):
+        raise ValueError(f"oracle options must be {N_OPT} floats, got shape {o.shape}")
+    return o
 
 
 def _check(st, what):
@@ -146,13 +171,18 @@ def exp32(x: float) -> float:
     return float(_load().or_exp32(float(x)))
 
 
+def log32(x: float) -> float:
+    """The FP32 mirror's logarithm of the tight tile rectangles."""
+    return float(_load().or_log32(float(x)))
+
+
 def project32(g: Gaussians, pose, cam, opt=DEFAULT_OPT):
     """FP32 mirror projection.  Returns (f [n,8] = u, v, z, ca, cb, cc, o, 0;
     i [n,6] = visible, radius, x0, x1, y0, y1)."""
     lib = _load()
     f = np.zeros((g.n, 8), np.float32)
     i = np.zeros((g.n, 6), np.int32)
-    _check(lib.or_project32(*g.args(), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_f32(opt)), _p(f), _p(i)),
+    _check(lib.or_project32(*g.args(), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_opt(opt)), _p(f), _p(i)),
            "project32")
     return f, i
 
@@ -161,7 +191,7 @@ def project64(g: Gaussians, pose, cam, opt=DEFAULT_OPT):
     """FP64 projection: [n,16] = U, V, z, A, B, C, o, x, y, Sc(6), 0."""
     lib = _load()
     out = np.zeros((g.n, 16), np.float64)
-    _check(lib.or_project64(*g.args(), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_f32(opt)), _p(out)),
+    _check(lib.or_project64(*g.args(), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_opt(opt)), _p(out)),
            "project64")
     return out
 
@@ -182,11 +212,11 @@ def bin_tiles(g: Gaussians, poses, cams, opt=DEFAULT_OPT):
     ranges = np.zeros((tiles, 2), np.int64)
     nd = ctypes.c_long(0)
     # first pass: count
-    _check(lib.or_bin(*g.args(), len(cams), _p(poses), _p(cams), _p(_f32(opt)), None, None, 0, _p(ranges),
+    _check(lib.or_bin(*g.args(), len(cams), _p(poses), _p(cams), _p(_opt(opt)), None, None, 0, _p(ranges),
                       ctypes.byref(nd)), "bin")
     keys = np.zeros(max(nd.value, 1), np.uint64)
     vals = np.zeros(max(nd.value, 1), np.uint32)
-    _check(lib.or_bin(*g.args(), len(cams), _p(poses), _p(cams), _p(_f32(opt)), _p(keys), _p(vals), nd.value,
+    _check(lib.or_bin(*g.args(), len(cams), _p(poses), _p(cams), _p(_opt(opt)), _p(keys), _p(vals), nd.value,
                       _p(ranges), ctypes.byref(nd)), "bin")
     return keys[: nd.value], vals[: nd.value], ranges
 
@@ -203,9 +233,21 @@ def render(g: Gaussians, pose, cam, opt=DEFAULT_OPT):
     tf32 = np.zeros((H, W), np.float32)
     last = np.zeros((H, W), np.int32)
     d32 = np.zeros((H, W), np.float32)
-    _check(lib.or_render(*g.args(), _p(g.rgb4), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_f32(opt)), _p(rgb),
+    _check(lib.or_render(*g.args(), _p(g.rgb4), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_opt(opt)), _p(rgb),
                          _p(depth), _p(alpha), _p(tf), _p(tf32), _p(last), _p(d32)), "render")
     return dict(rgb=rgb, depth=depth, alpha=alpha, t_final=tf, t_final32=tf32, last=last, depth32=d32)
+
+
+def contrib_sig(g: Gaussians, pose, cam, opt=DEFAULT_OPT):
+    """Per-pixel signature [H, W] (uint64) of the contributor sequence of
+    ``render``: equal signatures mean the same alpha-test, clamp and
+    early-stop decisions at that pixel."""
+    lib = _load()
+    W, H = int(cam[4]), int(cam[5])
+    sig = np.zeros((H, W), np.uint64)
+    _check(lib.or_contrib_sig(*g.args(), _p(g.rgb4), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_opt(opt)), _p(sig)),
+           "contrib_sig")
+    return sig
 
 
 # lambda_c of the tracking loss (Supp. A, per-dataset hyperparameters: 0.6 on
@@ -260,7 +302,7 @@ def backward(g: Gaussians, pose, cam, cot_rgb=None, cot_depth=None, cot_alpha=No
     cd = None if cot_depth is None else _f64(cot_depth)
     ca = None if cot_alpha is None else _f64(cot_alpha)
     pv = None if pivot is None else _f64(pivot, (3,))
-    _check(lib.or_backward(*g.args(), _p(g.rgb4), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_f32(opt)), _p(cr),
+    _check(lib.or_backward(*g.args(), _p(g.rgb4), _p(_f64(pose, (12,))), _p(_f32(cam)), _p(_opt(opt)), _p(cr),
                            _p(cd), _p(ca), _p(pv), _p(tw), _p(out.get("means")), _p(out.get("log_scales")),
                            _p(out.get("quats")), _p(out.get("logits")), _p(out.get("rgb"))), "backward")
     return out
@@ -294,7 +336,7 @@ def register_view(g: Gaussians, cam, t_rgb, t_depth, iters, pose0=None, opt=DEFA
     trk = None if track_lambda_c is None else np.array([track_lambda_c], np.float64)
     ex = None if lr_exposure is None else np.array([lr_exposure], np.float64)
     ab = np.zeros(2, np.float64)
-    _check(lib.or_register_view(*g.args(), _p(g.rgb4), _p(_f32(cam)), _p(_f32(opt)), _p(_f32(t_rgb)),
+    _check(lib.or_register_view(*g.args(), _p(g.rgb4), _p(_f32(cam)), _p(_opt(opt)), _p(_f32(t_rgb)),
                                 _p(_f32(t_depth)), _p(_f64(hyper, (6,))), int(iters), _p(pose),
                                 ctypes.byref(eps), _p(hist), _p(trk), _p(ex), _p(ab)), "register_view")
     out = (pose.reshape(3, 4), eps.value, (hist[:iters] if history else None))

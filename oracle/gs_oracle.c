@@ -38,6 +38,10 @@
  * reduction (k = round(x log2 e), r = x - k ln2 with a two-part ln2) followed
  * by the degree-6 Taylor polynomial of e^r and an exact scaling by 2^k.
  */
+#include <float.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -52,15 +56,17 @@
 #define OR_ERR_OOM 2
 
 /* ------------------------------------------------------------------------ */
-/* options: float opt[10] = {tile, z_near, dilation, alpha_min, alpha_max,    */
-/*                            t_min, bg_r, bg_g, bg_b, smooth}                */
+/* options: float opt[11] = {tile, z_near, dilation, alpha_min, alpha_max,    */
+/*                            t_min, bg_r, bg_g, bg_b, smooth, tight}         */
 /* smooth != 0: every visible Gaussian covers every tile (no radius cull).    */
+/* tight != 0: tile rectangles shrunk to the alpha-threshold box (m_tighten). */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int tile;
     float z_near, dilation, alpha_min, alpha_max, t_min;
     float bg[3];
     int smooth;
+    int tight;
 } opts_t;
 
 static void read_opts(const float *o, opts_t *p)
@@ -75,6 +81,7 @@ static void read_opts(const float *o, opts_t *p)
     p->bg[1] = o[7];
     p->bg[2] = o[8];
     p->smooth = o[9] != 0.0f;
+    p->tight = o[10] != 0.0f;
 }
 
 /* camera: float cam[18] = {fx, fy, cx, cy, width, height, w2c[12] row-major} */
@@ -107,6 +114,33 @@ float or_exp32(float x)
     return p * scale;
 }
 
+/* ln x in FP32 for a positive normal x, as the tight tile rectangles take
+ * it: x = m 2^e with the mantissa m moved into [sqrt(1/2), sqrt(2)) (halved,
+ * e raised, when above sqrt(2)); ln m = 2 artanh(s), s = (m - 1)/(m + 1),
+ * summed as 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9) by Horner in s^2 (|s| is
+ * at most 0.1716, so the next term is below 2e-10); result e ln2 + that. */
+float or_log32(float x)
+{
+    uint32_t b;
+    memcpy(&b, &x, sizeof b);
+    int e = (int)(b >> 23) - 127;
+    uint32_t mb = (b & 0x007fffffu) | 0x3f800000u;
+    float m;
+    memcpy(&m, &mb, sizeof m);
+    if (m > 1.41421354f) {
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float p = 0.222222222f;
+    p = fmaf(p, s2, 0.285714286f);
+    p = fmaf(p, s2, 0.4f);
+    p = fmaf(p, s2, 0.666666667f);
+    p = fmaf(p, s2, 2.0f);
+    return fmaf((float)e, 0.693147181f, s * p);
+}
+
 /* camera-from-object transform M = V o T in FP32 (3x4 row-major each). */
 static void m_compose(const float V[12], const float T[12], float M[12])
 {
@@ -126,6 +160,47 @@ typedef struct {
     float ca, cb, cc;   /* exponent = ca dx^2 + cb dx dy + cc dy^2 */
     float o;            /* opacity */
 } m32_t;
+
+/* The tight tile rectangle: the tiles of the 3-sigma rectangle whose pixel
+ * centres can reach the alpha threshold.  A pixel passes the alpha test only
+ * where o e^power >= alpha_min, i.e. power >= ln(alpha_min / o); with a
+ * margin of 0.06 for the FP32 evaluation, tau = ln alpha_min - ln o - 0.06,
+ * and power >= tau is the ellipse d^T Q d <= -2 tau about (u, v), with
+ * Q = [[A, B], [B, C]] = -[[2 ca, cb], [cb, 2 cc]].  Its axis-aligned box has
+ * half-widths sqrt(-2 tau C / det) and sqrt(-2 tau A / det), det = AC - B^2,
+ * taken 0.1 % + 0.01 px wider; tile t of side B (pixel centres B t + 0.5 ..
+ * B t + B - 0.5) meets it when ceil((u - ex - (B - 0.5)) / B) <= t <=
+ * floor((u + ex - 0.5) / B).
+ * tau >= 0 (opacity below alpha_min e^-0.06) empties the rectangle; a nearly
+ * singular conic (B^2 > 0.998 AC) keeps the 3-sigma one. */
+static void m_tighten(const m32_t *g, float alpha_min, int tile, int TX, int TY, int *x0, int *x1, int *y0,
+                      int *y1)
+{
+    float tau = (or_log32(alpha_min) - or_log32(g->o)) - 0.06f;
+    if (!(tau < 0.0f)) {
+        *x1 = *x0;
+        return;
+    }
+    float A = -2.0f * g->ca, B = -g->cb, C = -2.0f * g->cc;
+    float AC = A * C, BB = B * B;
+    float det = AC - BB;
+    if (!(det > 0.0f) || !(BB <= 0.998f * AC))
+        return;
+    float s = (-2.0f * tau) / det;
+    float ex = fmaf(sqrtf(s * C), 1.001f, 0.01f);
+    float ey = fmaf(sqrtf(s * A), 1.001f, 0.01f);
+    if (!(ex >= 0.0f) || !(ey >= 0.0f))
+        return;
+    const float Bt = (float)tile, hi = Bt - 0.5f;
+    float tx0 = fminf(fmaxf(ceilf(((g->u - ex) - hi) / Bt), 0.0f), (float)TX);
+    float tx1 = fminf(fmaxf(floorf(((g->u + ex) - 0.5f) / Bt) + 1.0f, 0.0f), (float)TX);
+    float ty0 = fminf(fmaxf(ceilf(((g->v - ey) - hi) / Bt), 0.0f), (float)TY);
+    float ty1 = fminf(fmaxf(floorf(((g->v + ey) - 0.5f) / Bt) + 1.0f, 0.0f), (float)TY);
+    if ((int)tx0 > *x0) *x0 = (int)tx0;
+    if ((int)tx1 < *x1) *x1 = (int)tx1;
+    if ((int)ty0 > *y0) *y0 = (int)ty0;
+    if ((int)ty1 < *y1) *y1 = (int)ty1;
+}
 
 static void m_project(const float *mu, const float *s, const float *q, float logit,
                       const float M[12], const float *cam, const opts_t *op, m32_t *g)
@@ -218,15 +293,17 @@ static void m_project(const float *mu, const float *s, const float *q, float log
         y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)TY);
         y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)TY);
     }
+    g->u = u;
+    g->v = v;
+    g->z = z;
+    g->o = 1.0f / (1.0f + or_exp32(-logit));
+    if (op->tight && !op->smooth && op->alpha_min >= FLT_MIN)
+        m_tighten(g, op->alpha_min, op->tile, TX, TY, &x0, &x1, &y0, &y1);
     if (x0 >= x1 || y0 >= y1)
         return;
     g->vis = 1;
     g->r = r;
     g->x0 = x0; g->x1 = x1; g->y0 = y0; g->y1 = y1;
-    g->u = u;
-    g->v = v;
-    g->z = z;
-    g->o = 1.0f / (1.0f + or_exp32(-logit));
     (void)H;
 }
 
@@ -555,6 +632,8 @@ static void composite(const prep_t *p, const opts_t *op, const float *rgb4, doub
                       int32_t *out_last, float *out_depth32)
 {
     const long HW = (long)p->W * p->H;
+    /* pixels are independent: rows may run on several threads */
+#pragma omp parallel for schedule(dynamic, 4)
     for (int py = 0; py < p->H; ++py)
         for (int px = 0; px < p->W; ++px) {
             double c[3], d, Tf;
@@ -582,9 +661,15 @@ static void composite(const prep_t *p, const opts_t *op, const float *rgb4, doub
 enum { G_U, G_V, G_A, G_B, G_C, G_Z, G_O, G_R, G_G, G_BL, G_N };
 
 /* Accumulates dL/d(screen parameters) of every Gaussian, given per-pixel
- * cotangents of the rendered colour (3 planes), depth and alpha. */
-static int adjoint_screen(const prep_t *p, const opts_t *op, const float *rgb4, const double *g_rgb,
-                          const double *g_depth, const double *g_alpha, double *acc /* n x G_N */)
+ * cotangents of the rendered colour (3 planes), depth and alpha.  The image
+ * is cut into OR_CHUNKS bands of tile rows; each band sums its pixels'
+ * contributions (row-major) into its own accumulator, and the bands are
+ * added in band order, so the result does not depend on how many threads
+ * run the bands. */
+#define OR_CHUNKS 16
+
+static int adjoint_band(const prep_t *p, const opts_t *op, const float *rgb4, const double *g_rgb,
+                        const double *g_depth, const double *g_alpha, int py0, int py1, double *acc)
 {
     const long HW = (long)p->W * p->H;
     long ml = max_list(p);
@@ -595,7 +680,7 @@ static int adjoint_screen(const prep_t *p, const opts_t *op, const float *rgb4, 
         free(Sc);
         return OR_ERR_OOM;
     }
-    for (int py = 0; py < p->H; ++py)
+    for (int py = py0; py < py1; ++py)
         for (int px = 0; px < p->W; ++px) {
             long pix = (long)py * p->W + px;
             double gc[3], gd, ga;
@@ -649,6 +734,46 @@ static int adjoint_screen(const prep_t *p, const opts_t *op, const float *rgb4, 
     free(cl);
     free(Sc);
     return OR_OK;
+}
+
+static int adjoint_screen(const prep_t *p, const opts_t *op, const float *rgb4, const double *g_rgb,
+                          const double *g_depth, const double *g_alpha, double *acc /* n x G_N */)
+{
+    const size_t na = (size_t)(p->n > 0 ? p->n : 1) * G_N;
+    double *band = calloc(na * OR_CHUNKS, sizeof(double));
+    if (!band)
+        return OR_ERR_OOM;
+    int st = OR_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < OR_CHUNKS; ++c) {
+        /* band c: tile rows [c TY / K, (c + 1) TY / K) */
+        const int ty0 = (int)((long)c * p->TY / OR_CHUNKS), ty1 = (int)((long)(c + 1) * p->TY / OR_CHUNKS);
+        const int py0 = ty0 * op->tile, py1 = ty1 * op->tile < p->H ? ty1 * op->tile : p->H;
+        if (py0 < py1 && adjoint_band(p, op, rgb4, g_rgb, g_depth, g_alpha, py0, py1, band + na * c) != OR_OK) {
+#pragma omp critical
+            st = OR_ERR_OOM;
+        }
+    }
+    if (st == OR_OK)
+        for (int c = 0; c < OR_CHUNKS; ++c)
+            for (size_t k = 0; k < na; ++k)
+                acc[k] += band[na * c + k];
+    free(band);
+    return st;
+}
+
+/* Threads used by the parallel loops (1 unless the library was built with
+ * OpenMP); returns the number in effect. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 static void cross3(const double a[3], const double b[3], double c[3])
@@ -907,6 +1032,40 @@ int or_render(int n, const float *means4, const float *scales4, const float *qua
     int st = prep_camera(n, means4, scales4, quats4, logits, pose, cam, &op, &p);
     if (st == OR_OK)
         composite(&p, &op, rgb4, out_rgb, out_depth, out_alpha, out_tf, out_tf32, out_last, out_depth32);
+    prep_free(&p);
+    return st;
+}
+
+/* Per-pixel signature of the contributor sequence of or_render (FNV-1a over
+ * (Gaussian index, clamped) of each contributor in list order, then the
+ * count): two renders whose signatures agree at every pixel take the same
+ * discrete choices (alpha test, clamp, early stop) everywhere, so a finite
+ * difference between them crosses no threshold.  sig[H][W]. */
+int or_contrib_sig(int n, const float *means4, const float *scales4, const float *quats4, const float *logits,
+                   const float *rgb4, const double *pose, const float *cam, const float *opt, uint64_t *sig)
+{
+    opts_t op;
+    read_opts(opt, &op);
+    if (n < 0 || !check_cam(cam, &op))
+        return OR_ERR_ARG;
+    prep_t p;
+    int st = prep_camera(n, means4, scales4, quats4, logits, pose, cam, &op, &p);
+    long ml = st == OR_OK ? max_list(&p) : 0;
+    contrib_t *cl = st == OR_OK ? malloc((size_t)(ml > 0 ? ml : 1) * sizeof(contrib_t)) : NULL;
+    if (st == OR_OK && !cl)
+        st = OR_ERR_OOM;
+    for (int py = 0; st == OR_OK && py < p.H; ++py)
+        for (int px = 0; px < p.W; ++px) {
+            double c[3], d, Tf;
+            float Tf32;
+            long last;
+            int K = walk_pixel(&p, &op, px, py, cl, c, &d, rgb4, &Tf, &Tf32, NULL, &last);
+            uint64_t h = 1469598103934665603ull;
+            for (int i = 0; i < K; ++i)
+                h = (h ^ (uint64_t)(2 * (uint64_t)cl[i].gid + (uint64_t)cl[i].clamped)) * 1099511628211ull;
+            sig[(long)py * p.W + px] = (h ^ (uint64_t)K) * 1099511628211ull;
+        }
+    free(cl);
     prep_free(&p);
     return st;
 }

@@ -265,6 +265,126 @@ def test_binning_matches_bruteforce():
     np.testing.assert_array_equal(order, np.arange(len(bk)))
 
 
+@pytest.mark.parametrize("opt", ["tight", "loose"])
+def test_binning_matches_bruteforce_both_rectangles(opt):
+    # the brute force above reads the rectangles of project32; here the two
+    # rectangle rules side by side: the tight lists are the 3-sigma lists
+    # with the dropped (tile, record) pairs removed, order kept
+    c = synth.small_case(300, 80, 56, 60.0, n_views=2, seed=22)
+    g = O.Gaussians.from_dict(c["gaussians"])
+    rng = np.random.default_rng(3)
+    poses = np.stack([synth.random_rigid(rng, 3.0, 0.02) for _ in range(2)])
+    o = O.DEFAULT_OPT if opt == "tight" else O.LOOSE_OPT
+    keys, vals, ranges = O.bin_tiles(g, poses, c["cams"], o)
+    lk, lv, _ = O.bin_tiles(g, poses, c["cams"], O.LOOSE_OPT)
+    loose = list(zip(lk.tolist(), lv.tolist()))
+    tight = list(zip(keys.tolist(), vals.tolist()))
+    keep = set(tight)
+    assert [kv for kv in loose if kv in keep] == tight  # a subsequence of the 3-sigma lists
+    if opt == "tight":
+        assert len(tight) < len(loose)
+
+
+# --------------------------------------------------------------------------
+# tight tile rectangles: the FP32 logarithm, and what the rectangles drop
+# --------------------------------------------------------------------------
+
+def test_log32_against_libm():
+    xs = np.concatenate([np.logspace(-37, 0, 4001), np.linspace(0.5, 2.0, 3001), [1.0 / 255.0, 1.0]])
+    worst = 0.0
+    for x in xs:
+        x32 = float(np.float32(x))
+        ref = math.log(x32)
+        worst = max(worst, abs(O.log32(x32) - ref) / max(1.0, abs(ref)))
+    assert worst < 3e-7, worst
+    assert O.log32(1.0) == 0.0
+
+
+def _needle_scene(n, W, H, f, seed):
+    # needle-shaped splats (one axis x4.5, one x0.08) in all orientations,
+    # half of them with opacities near alpha_min: where a threshold box is
+    # closest to the pixels it must keep
+    c = synth.small_case(n, W, H, f, n_views=2, seed=seed, ls_mean=-3.2, ls_std=0.3)
+    g = {k: np.array(v, copy=True) for k, v in c["gaussians"].items()}
+    rng = np.random.default_rng(seed)
+    g["log_scales4"][:, 0] += 1.5
+    g["log_scales4"][:, 1] -= 2.5
+    near = rng.random(n) < 0.5
+    g["logits"][near] = rng.normal(-5.55, 0.15, int(near.sum()))
+    return O.Gaussians.from_dict(g), c["cams"]
+
+
+def _scenes():
+    yield _needle_scene(1200, 240, 160, 160.0, 21)
+    c = synth.small_case(900, 120, 90, 100.0, n_views=2, seed=23, ls_mean=-3.0)
+    yield O.Gaussians.from_dict(c["gaussians"]), c["cams"]
+
+
+def test_tight_rectangles_drop_only_tiles_below_alpha_min():
+    # FP64 check of every dropped (record, tile) pair: at each pixel centre
+    # of the tile the exact alpha o e^power of the FP64 projection stays
+    # below alpha_min e^-0.05 (the rectangle's margin is 0.06 in the
+    # exponent); the tight rectangle lies inside the 3-sigma one
+    amin = float(O.DEFAULT_OPT[3])
+    dropped = 0
+    for g, cams in _scenes():
+        rng = np.random.default_rng(7)
+        for cam in cams:
+            pose = synth.random_rigid(rng, 3.0, 0.03)
+            _, it = O.project32(g, pose, cam, O.DEFAULT_OPT)
+            _, il = O.project32(g, pose, cam, O.LOOSE_OPT)
+            p64 = O.project64(g, pose, cam)
+            W, H = int(cam[4]), int(cam[5])
+            assert np.all(il[it[:, 0] == 1, 0] == 1)
+            for k in np.nonzero(il[:, 0] == 1)[0]:
+                x0, x1, y0, y1 = il[k, 2:6]
+                if it[k, 0]:
+                    a0, a1, b0, b1 = it[k, 2:6]
+                    assert x0 <= a0 < a1 <= x1 and y0 <= b0 < b1 <= y1
+                else:
+                    a0 = a1 = b0 = b1 = 0
+                px = np.arange(16 * x0, min(16 * x1, W))
+                py = np.arange(16 * y0, min(16 * y1, H))
+                X, Y = np.meshgrid(px, py)
+                tx, ty = X // 16, Y // 16
+                out = ~((tx >= a0) & (tx < a1) & (ty >= b0) & (ty < b1))
+                if not out.any():
+                    continue
+                U, V, _, A, B, C, o = p64[k, :7]
+                dx, dy = U - (X + 0.5), V - (Y + 0.5)
+                alpha = o * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy)
+                assert alpha[out].max() < amin * math.exp(-0.05), (k, alpha[out].max())
+                dropped += int(len(set(zip(tx[out].ravel(), ty[out].ravel()))))
+    assert dropped > 500, dropped
+
+
+def test_tight_lists_render_identically_to_3sigma_lists():
+    # every pair the tight lists drop fails the FP32 alpha test at every
+    # pixel: the same contributors in the same order, so the FP32 final
+    # transmittance and the FP64 colour and depth are bit-equal; only list
+    # positions (last) move forward
+    for g, cams in _scenes():
+        rng = np.random.default_rng(8)
+        for cam in cams:
+            pose = synth.random_rigid(rng, 3.0, 0.03)
+            rt = O.render(g, pose, cam, O.DEFAULT_OPT)
+            rl = O.render(g, pose, cam, O.LOOSE_OPT)
+            np.testing.assert_array_equal(rt["t_final32"].view(np.uint32), rl["t_final32"].view(np.uint32))
+            np.testing.assert_array_equal(rt["rgb"], rl["rgb"])
+            np.testing.assert_array_equal(rt["depth"], rl["depth"])
+            assert np.all(rt["last"] <= rl["last"]) and np.any(rt["last"] < rl["last"])
+
+
+def test_tight_lists_shrink_the_room_lists():
+    c = synth.room_150k()
+    g = O.Gaussians.from_dict(c["gaussians"])
+    cams = c["src_cams"][:2]
+    poses = np.stack([np.eye(3, 4)] * 2)
+    kt, _, _ = O.bin_tiles(g, poses, cams, O.DEFAULT_OPT)
+    kl, _, _ = O.bin_tiles(g, poses, cams, O.LOOSE_OPT)
+    assert len(kt) < 0.8 * len(kl), (len(kt), len(kl))
+
+
 # --------------------------------------------------------------------------
 # loss
 # --------------------------------------------------------------------------
@@ -363,6 +483,69 @@ def test_adjoint_matches_finite_differences_500_subset():
                 if abs(fd - an[i, k]) > 2e-3 * max(abs(an[i, k]), 0.02 * scale):
                     bad.append((name, i, k, fd, an[i, k]))
     assert not bad, bad
+
+
+def _threshold_scene():
+    # 40 Gaussians of ~2.5 px in front of a 40 x 30 image (2 x 3 tiles,
+    # ragged): a third nearly opaque (o ~ 0.996: clamped at alpha_max near
+    # their centres, and stacks of them stop early on t_min), a third with
+    # opacities near alpha_min, a third ordinary; grey background
+    c = synth.small_case(40, 40, 30, 60.0, seed=44, ls_mean=-2.5, ls_std=0.2, half=0.25)
+    d = {k: np.array(v, copy=True) for k, v in c["gaussians"].items()}
+    rng = np.random.default_rng(44)
+    kind = np.arange(40) % 3
+    d["logits"][kind == 0] = rng.normal(5.5, 0.3, int((kind == 0).sum()))
+    d["logits"][kind == 1] = rng.normal(-5.4, 0.2, int((kind == 1).sum()))
+    opt = O.DEFAULT_OPT.copy()
+    opt[6:9] = (0.3, 0.5, 0.7)
+    cam = c["cams"][0]
+    H, W = int(cam[5]), int(cam[4])
+    cot = (rng.standard_normal((3, H, W)), rng.standard_normal((H, W)), rng.standard_normal((H, W)))
+    return O.Gaussians.from_dict(d), cam, cot, np.eye(3, 4), opt
+
+
+def test_adjoint_matches_finite_differences_with_thresholds_on():
+    # alpha_min, alpha_max and t_min active, a non-zero background: central
+    # differences on every parameter whose +h and -h renders keep the same
+    # contributor sequence (alpha test, clamp and early stop) at every pixel
+    g, cam, cot, pose, opt = _threshold_scene()
+    # the scene exercises what the thresholds change: early stops (the
+    # final transmittance differs without t_min), clamps (it differs with
+    # alpha_max = 1) and the alpha test (with alpha_min = 0)
+    base = O.render(g, pose, cam, opt)
+    for k, v in ((5, 0.0), (4, 1.0), (3, 0.0)):
+        o2 = opt.copy()
+        o2[k] = v
+        if k == 3:
+            o2[10] = 0.0  # no alpha threshold: 3-sigma rectangles
+        assert np.any(O.render(g, pose, cam, o2)["t_final32"] != base["t_final32"]), k
+    sig0 = O.contrib_sig(g, pose, cam, opt)
+    b = O.backward(g, pose, cam, *cot, pivot=O.centroid(g), opt=opt)
+    arrs = {a: getattr(g, a) for _, a, _ in FIELDS}
+    tested, bad = 0, []
+    for name, field, K in FIELDS:
+        an = b[name].reshape(g.n, -1)
+        scale = np.abs(an).max()
+        h = 2e-4 if name == "means" else 1e-3
+        for i in range(g.n):
+            for k in range(K):
+                same = True
+                for sgn in (1, -1):
+                    d = {a: v.copy() for a, v in arrs.items()}
+                    if field == "logits":
+                        d[field][i] = np.float32(float(d[field][i]) + sgn * h)
+                    else:
+                        d[field][i, k] = np.float32(float(d[field][i, k]) + sgn * h)
+                    gp = O.Gaussians(d["means4"], d["log_scales4"], d["quats4"], d["logits"], d["rgb4"])
+                    same = same and np.array_equal(O.contrib_sig(gp, pose, cam, opt), sig0)
+                if not same:
+                    continue
+                fd = _fd_param(g, pose, cam, cot, opt, field, i, k, h)
+                tested += 1
+                if abs(fd - an[i, k]) > 2e-3 * max(abs(an[i, k]), 0.02 * scale):
+                    bad.append((name, i, k, fd, an[i, k]))
+    assert not bad, bad
+    assert tested >= 300, tested
 
 
 def _twist_pose(pose, xi, pivot):
