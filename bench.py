@@ -50,12 +50,7 @@ FWD_FLOPS_CONTRIB = 41.0
 BWD_FLOPS_CONTRIB = 64.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
 # the current kernel; None while the kernel has changed since the capture
-BWD_TRAFFIC_BYTES = 185.855232e6
-# the same capture's smsp__issue_active (fraction of cycles issuing an
-# instruction): the adjoint is bound by instruction issue, of which the
-# counted flops are a part
-BWD_ISSUE_ACTIVE = 0.827
-SMS = 152
+BWD_TRAFFIC_BYTES = None
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -142,42 +137,51 @@ def rot_err(P, T):
 
 
 def run_reference(args):
+    """The oracle as it stands (FP64, OpenMP over pixel rows and adjoint
+    bands on every host core) on the room workload.  One timed step = one
+    keyframe iteration at full size (1200x680 render + L1 loss + adjoint +
+    pose step, alternating the two directions); the value is scaled to the
+    metric's unit (a registration step covers 16 keyframe iterations)."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
     import oracle as O
     from paper_2408_10154_gb300 import synth
     O.build()
+    cores = O.set_threads(os.cpu_count() or 1)
     c = synth.room_150k()
     g_src = O.Gaussians.from_dict(c["gaussians"])
     g_tgt = O.transform(g_src, c["T_gt"])
-    cam = c["src_cams"][0]
-    tr = O.render(g_src, np.eye(3, 4), cam)
-    t_rgb, t_dep = tr["rgb"].astype(np.float32), tr["depth"].astype(np.float32)
-    piv = O.centroid(g_tgt)
+    jobs = []
+    for moving, fixed, cam in ((g_tgt, g_src, c["src_cams"][0]), (g_src, g_tgt, c["tgt_cams"][0])):
+        tr = O.render(fixed, np.eye(3, 4), cam)
+        jobs.append((moving, cam, tr["rgb"].astype(np.float32), tr["depth"].astype(np.float32), O.centroid(moving)))
 
-    def one_keyframe_iteration():
+    def one_keyframe_iteration(k):
+        moving, cam, t_rgb, t_dep, piv = jobs[k % 2]
         pose = np.eye(3, 4)
-        r = O.render(g_tgt, pose, cam)
+        r = O.render(moving, pose, cam)
         L, gr, gd = O.loss(r["rgb"], r["depth"], t_rgb, t_dep)
-        b = O.backward(g_tgt, pose, cam, gr, gd, pivot=piv, params=False)
+        b = O.backward(moving, pose, cam, gr, gd, pivot=piv, params=False)
         O.pose_step(pose, np.zeros(13), b["twist"], piv, 0, ITERS)
 
-    for _ in range(args.warmup):
-        one_keyframe_iteration()
+    for k in range(args.warmup):
+        one_keyframe_iteration(k)
     times = []
-    for _ in range(args.steps):
+    for k in range(args.steps):
         t = time.perf_counter()
-        one_keyframe_iteration()
+        one_keyframe_iteration(k)
         times.append(time.perf_counter() - t)
     per_kf = float(np.mean(times))
-    value = 1.0 / (16.0 * per_kf)  # a registration step covers 16 keyframes
-    sample = "one keyframe iteration (1200x680 render + L1 loss + adjoint + pose step) of the room workload per step"
+    value = 1.0 / (16.0 * per_kf)  # a registration step covers 16 keyframe iterations
+    sample = ("one keyframe iteration per bench step (1200x680 render + L1 loss + adjoint + pose step of the room "
+              "workload, the two directions alternating), scaled to registration steps (16 keyframe iterations)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_kf * 16 * 1000.0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_kf * 1000.0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "iters_per_edge": ITERS},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "iters_per_edge": ITERS,
+                       "bench_step": "one keyframe iteration = 1/16 of a registration step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -298,7 +302,11 @@ def run_ours(args):
     dom = int(np.argmax(per_launch_ms))
     pairs_per_launch = pairs / (calls * ITERS)
     contrib_per_launch = contrib / (calls * ITERS)
-    peak_fp32 = SMS * FP32_LANES * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+    # FP32 peak: measured by an FMA-loop probe on this device (the SM count
+    # read from it), beside the figure derived from unit counts and clocks
+    probe_tflops, sms = gs.gs_probe_fp32(ctx)
+    derived_fp32 = sms * FP32_LANES * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+    peak_fp32 = probe_tflops
     if names[dom] in ("backward", "forward"):
         fc = BWD_FLOPS_CONTRIB if names[dom] == "backward" else FWD_FLOPS_CONTRIB
         flops = fc * contrib_per_launch
@@ -306,13 +314,33 @@ def run_ours(args):
         roof = {"kernel": "k_backward2" if names[dom] == "backward" else "k_forward", "bound": "alu",
                 "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
                 "traffic": BWD_TRAFFIC_BYTES if names[dom] == "backward" else None,
-                "issue_active": BWD_ISSUE_ACTIVE if names[dom] == "backward" else None,
                 "flops_per_launch": flops,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock (derived; no measured FP32 peak)"}
+                "peak_source": "measured: FMA-loop probe (gs_probe_fp32) on this GPU, %d SMs" % sms,
+                "peak_derived": derived_fp32,
+                "frac_of_derived": achieved / derived_fp32}
     else:
         hbm = pk.get("hbm_gbs", 6800.0)
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None}
+    # HBM-bound steps: algorithmic bytes per launch / CUDA-event time.
+    # Projection: 56 B per Gaussian of each moving submap + 52 B (48 B
+    # record + 4 B count) per visible (keyframe, Gaussian).  Tile lists:
+    # 16 B entry read per visible record, 8 B written at placement and 8 B
+    # read + 8 B written by the per-tile sort per duplicate, 8 B range per tile.
+    I8 = torch.tensor(np.stack([np.eye(3, 4)] * 8).reshape(8, 12), dtype=torch.float32, device="cuda")
+    vis = sum(int((gs.gs_project(ctx, g, I8, cams, with_aux=False)[2] > 0).sum())
+              for g, cams in ((tgt, c["src_cams"]), (src, c["tgt_cams"])))
+    tiles = 16 * ((1200 + 15) // 16) * ((680 + 15) // 16)
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    hbm = {}
+    for name, nbytes in (("project", 56.0 * (src.n + tgt.n) + 52.0 * vis),
+                         ("bin", 16.0 * vis + 24.0 * dups + 8.0 * tiles)):
+        ms = per_launch_ms[names.index(name)]
+        gbs = nbytes / (ms / 1000.0) / 1e9
+        hbm[name] = {"bytes_per_launch": nbytes, "ms_per_launch": float(ms), "achieved_gbs": gbs,
+                     "peak_gbs": hbm_peak, "frac": gbs / hbm_peak}
+    hbm["visible_records_at_start"] = vis
+    hbm["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback 6800 GB/s"
     lat = sorted(times)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -327,7 +355,9 @@ def run_ours(args):
         "pairs_per_iteration": pairs_per_launch, "contributing_pairs_per_iteration": contrib_per_launch,
         "dups": int(dups),
         "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "hbm": hbm,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "bench_step": "one loop edge (100 registration steps): the bytes are per edge"},
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
@@ -335,42 +365,63 @@ def run_ours(args):
     ang, dt = rot_err(T, c["T_gt"])
     out["accuracy"] = {"rot_err_deg": ang, "trans_err_mm": dt * 1000.0,
                        "keyframes_converged": int(np.sum(np.asarray(results[-1][2]) < 0.01))}
+    ctx.close()
+    if world == 1 and not args.room_only:
+        # the rest of the metric: batched vs plain, and serving p50/p99
+        bctx = gs.Context(device, 96 << 30)
+        out["batched_32"], _ = measure_batched(gs, bctx, torch, reps=1, warmup=1)
+        bctx.close()
+        torch.cuda.empty_cache()
+        out["serving"] = measure_serve(args.serve_rate, args.serve_seconds, 64, args.max_kf, args.round_iters)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(c)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
 def cpu_baseline(c):
-    """Times the FP64 oracle, as it stands, on host cores: four keyframe
-    iterations (render + loss + adjoint + pose step) at full size from each
-    direction (about 10 s of CPU work), scaled to registration steps/s (16
-    keyframes per step)."""
+    """Times the FP64 oracle, as it stands, on the host cores: keyframe
+    iterations (render + loss + adjoint + pose step) of the room workload at
+    full size, alternating the two directions -- 8 on all cores (OpenMP over
+    pixel rows and adjoint bands) and 4 on one core -- scaled to
+    registration steps/s (16 keyframe iterations per step)."""
     import oracle as O
     O.build()
     g_src = O.Gaussians.from_dict(c["gaussians"])
     g_tgt = O.transform(g_src, c["T_gt"])
-    jobs = [(g_tgt, g_src, c["src_cams"][k]) for k in range(4)] + [(g_src, g_tgt, c["tgt_cams"][k]) for k in range(4)]
-    per = []
-    for moving, fixed, cam in jobs:
-        tr = O.render(fixed, np.eye(3, 4), cam)
-        t_rgb, t_dep = tr["rgb"].astype(np.float32), tr["depth"].astype(np.float32)
-        piv = O.centroid(moving)
-        t = time.perf_counter()
-        pose = np.eye(3, 4)
-        r = O.render(moving, pose, cam)
-        L, gr, gd = O.loss(r["rgb"], r["depth"], t_rgb, t_dep)
-        b = O.backward(moving, pose, cam, gr, gd, pivot=piv, params=False)
-        O.pose_step(pose, np.zeros(13), b["twist"], piv, 0, ITERS)
-        per.append(time.perf_counter() - t)
-    per_kf = float(np.mean(per))
-    return {"value": 1.0 / (16.0 * per_kf), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "8 keyframe iterations at full size (4 per direction), scaled x2 to a 16-keyframe step",
-            "seconds": float(sum(per))}
+    jobs = []
+    for k in range(4):
+        for moving, fixed, cam in ((g_tgt, g_src, c["src_cams"][k]), (g_src, g_tgt, c["tgt_cams"][k])):
+            tr = O.render(fixed, np.eye(3, 4), cam)
+            jobs.append((moving, cam, tr["rgb"].astype(np.float32), tr["depth"].astype(np.float32),
+                         O.centroid(moving)))
+
+    def timed(js):
+        per = []
+        for moving, cam, t_rgb, t_dep, piv in js:
+            t = time.perf_counter()
+            pose = np.eye(3, 4)
+            r = O.render(moving, pose, cam)
+            L, gr, gd = O.loss(r["rgb"], r["depth"], t_rgb, t_dep)
+            b = O.backward(moving, pose, cam, gr, gd, pivot=piv, params=False)
+            O.pose_step(pose, np.zeros(13), b["twist"], piv, 0, ITERS)
+            per.append(time.perf_counter() - t)
+        return float(np.mean(per)), float(sum(per))
+
+    cores = O.set_threads(os.cpu_count() or 1)
+    per_all, sec_all = timed(jobs)
+    O.set_threads(1)
+    per_one, sec_one = timed(jobs[:4])
+    return {"value": 1.0 / (16.0 * per_all), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "8 keyframe iterations of the room workload at full size (4 per direction) on %d cores, "
+                      "scaled to a 16-keyframe registration step" % cores,
+            "seconds": sec_all,
+            "single_core": {"value": 1.0 / (16.0 * per_one), "unit": UNIT, "cores": 1, "seconds": sec_one,
+                            "sample": "4 of the same keyframe iterations on one core"},
+            "host_cpus": os.cpu_count()}
 
 
 def edge_problems(gs, ctx, torch, pairs):
@@ -394,20 +445,19 @@ def edge_problems(gs, ctx, torch, pairs):
     return problems, px
 
 
-def run_serve(args):
+def measure_serve(rate, seconds, pool, max_kf, round_iters):
     """Serving stream (Poisson arrivals, 70 % frame-to-model tracking of a
     resident submap, 30 % loop edges; 40 / 100 iterations) through the
     continuous-batching server in real time, and the plain form: the same
     stream served one request at a time in arrival order (each request's
     gs_register time measured, FIFO queueing computed from the arrivals).
-    Prints one JSON line with p50/p99 latencies and throughput of both."""
+    Returns a dict with p50/p99 latencies and throughput of both."""
     import time
     import torch
-    torch.cuda.set_device(0)
     import paper_2408_10154_gb300 as gs
     from paper_2408_10154_gb300 import synth
-    ctx = gs.Context(0, 64 << 30)
-    st = synth.serving_stream(rate=args.rate, seconds=args.seconds, n_submaps=args.pool)
+    ctx = gs.Context(torch.cuda.current_device(), 64 << 30)
+    st = synth.serving_stream(rate=rate, seconds=seconds, n_submaps=pool)
     edges, _ = edge_problems(gs, ctx, torch, synth.batched_pairs()["pairs"])
     tracks = []
     for sm in st["submaps"]:
@@ -436,14 +486,15 @@ def run_serve(args):
     for a in (next(x for x in arrivals if x[1] == "track"), next(x for x in arrivals if x[1] == "edge")):
         prob, iters, _ = request(a)
         gs.gs_register(ctx, *prob[:4], iters, *prob[4:])
-        w = gs.Server(0, max_keyframes=args.max_kf, max_round_iters=args.round_iters)
+        w = gs.Server(torch.cuda.current_device(), max_keyframes=max_kf, max_round_iters=round_iters)
         w.submit(*prob[:4], iters, *prob[4:])
         while w.counts()[1] or w.counts()[0]:
             w.step()
         w.close()
     torch.cuda.synchronize()
     # served: submit each request at its arrival time, one round per step
-    srv = gs.Server(0, budget_bytes=160 << 30, max_keyframes=args.max_kf, max_round_iters=args.round_iters)
+    srv = gs.Server(torch.cuda.current_device(), budget_bytes=160 << 30, max_keyframes=max_kf,
+                    max_round_iters=round_iters)
     done_at, rid_of, i = {}, {}, 0
     t0 = time.perf_counter()
     while len(done_at) < n:
@@ -488,17 +539,26 @@ def run_serve(args):
     served = summary(done_at)
     plain = summary({k: finish[k] for k in range(n)})
     same = sum(int(np.array_equal(served_T[k], plain_T[k])) for k in range(n))
-    out = {"metric": "serving requests/s", "value": served["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
-           "steps": n, "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": "synthetic",
-           "config": {"workload": "serving: Poisson %.0f/s for %.0f s (%d requests; 70 %% tracking 640x480 with the Eq. 2 loss, 40 it, "
-                                  "%d resident submaps of 50k-300k; 30 %% loop edges of the batched pool, 100 it)"
-                                  % (args.rate, args.seconds, n, args.pool),
-                      "max_keyframes": args.max_kf, "round_iters": args.round_iters},
-           "served": served, "plain": plain, "served_rounds": rounds, "served_replans": replans,
-           "results_identical": same, "n_requests": n}
-    print(json.dumps(out), flush=True)
     ctx.close()
+    return {"workload": "serving: Poisson %.0f/s for %.0f s (%d requests; 70 %% tracking 640x480 with the Eq. 2 "
+                        "loss, 40 it, %d resident submaps of 50k-300k; 30 %% loop edges of the batched pool, 100 it)"
+                        % (rate, seconds, n, pool),
+            "rate_per_s": rate, "n_requests": n, "max_keyframes": max_kf, "round_iters": round_iters,
+            "served": served, "plain": plain, "served_rounds": rounds, "served_replans": replans,
+            "results_identical": same,
+            "mean_plain_service_ms": 1000.0 * float(np.mean(service))}
+
+
+def run_serve(args):
+    """--workload serve: the serving record alone, as its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    rec = measure_serve(args.rate, args.seconds, args.pool, args.max_kf, args.round_iters)
+    out = {"metric": "serving requests/s", "value": rec["served"]["requests_per_s"], "unit": "requests/s",
+           "n_gpus": 1, "steps": rec["n_requests"], "warmup": 2, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": {"workload": rec["workload"]},
+           **{k: v for k, v in rec.items() if k != "workload"}}
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -537,29 +597,16 @@ def run_overlap(args):
     return 0
 
 
-def run_batched(args):
-    """Batched uneven registration: the 32 submap pairs of the batched
-    workload (20k-400k Gaussians, 4-12 keyframes per submap at 640x480 or
-    1200x680, offsets up to 15 deg / 25 cm), each pair in both directions,
-    registered (a) one pair per call ("plain", gs_register) and (b) all
-    pairs in one batch (gs_register_batch).  Prints one JSON line."""
-    import torch
-    rank, world, local = env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    import paper_2408_10154_gb300 as gs
-    from paper_2408_10154_gb300 import shard, synth
-    ctx = gs.Context(torch.cuda.current_device(), 96 << 30)
-    wl = synth.batched_pairs()
-    # whole edges per rank (LPT on rendering work); each rank fuses its own
-    costs = [shard.edge_cost(len(pr["gaussians"]["means4"]), len(pr["gaussians"]["means4"]), pr["src_cams"],
-                             pr["tgt_cams"]) for pr in wl["pairs"]]
-    mine = shard.lpt_partition(costs, world)[rank]
-    problems, px = edge_problems(gs, ctx, torch, [wl["pairs"][i] for i in mine])
+def measure_batched(gs, ctx, torch, reps=1, warmup=1, problems=None, px=None, n_edges=None, T_gts=None):
+    """Batched uneven registration: the pairs of the batched workload, each
+    in both directions, registered (a) one pair per call ("plain",
+    gs_register) and (b) all pairs in one batch (gs_register_batch).
+    Returns (record dict, fused T and confidence of the last batch)."""
+    from paper_2408_10154_gb300 import synth
+    if problems is None:
+        wl = synth.batched_pairs()
+        problems, px = edge_problems(gs, ctx, torch, wl["pairs"])
+        T_gts = [pr["T_gt"] for pr in wl["pairs"]]
     iters = ITERS
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -581,18 +628,62 @@ def run_batched(args):
     def batched():
         return gs.gs_register_batch(ctx, problems, iters)
 
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         batched()
         plain()
-    plain_runs, batch_runs = [], []
-    for _ in range(args.steps):
-        lat = plain()
-        plain_runs.append(lat)
+    plain_runs, batch_runs, res = [], [], None
+    for _ in range(max(reps, 1)):
+        plain_runs.append(plain())
         t, res = timed(batched)
         batch_runs.append(t)
     plain_ms = float(np.mean([sum(l) for l in plain_runs]))
     batch_ms = float(np.mean(batch_runs))
-    lat_all = [x for l in plain_runs for x in l]
+    lat_all = sorted(x for l in plain_runs for x in l)
+    n = len(problems)
+    rec = {"workload": "batched_32: %d uneven submap pairs (20k-400k Gaussians, 4-12 keyframes per submap at "
+                       "640x480 / 1200x680), both directions, %d iterations" % (n, iters),
+           "pixels_per_iteration": int(px),
+           "batched": {"ms_per_batch": batch_ms, "steps_per_s": n * iters / (batch_ms / 1000.0),
+                       "edges_per_s": n / (batch_ms / 1000.0),
+                       "mpx_per_s": px * iters / (batch_ms / 1000.0) / 1e6},
+           "plain": {"ms_per_batch": plain_ms, "steps_per_s": n * iters / (plain_ms / 1000.0),
+                     "edges_per_s": n / (plain_ms / 1000.0),
+                     "mpx_per_s": px * iters / (plain_ms / 1000.0) / 1e6,
+                     "edge_latency_ms": {"p50": float(np.percentile(lat_all, 50)),
+                                         "p99": float(np.percentile(lat_all, 99))}},
+           "batched_over_plain": plain_ms / batch_ms,
+           "step": "steps_per_s counts registration steps of single loop edges (one iteration of all the keyframe "
+                   "problems of one edge, as in the headline), summed over the %d edges" % n}
+    if T_gts is not None and res is not None:
+        rec["batched"]["edges_within_1deg_2cm"] = int(sum(
+            rot_err(res[0][k], T_gts[k])[0] < 1.0 and rot_err(res[0][k], T_gts[k])[1] < 0.02 for k in range(n)))
+    return rec, res
+
+
+def run_batched(args):
+    """--workload batched_32: batched vs one-pair-per-call as its own JSON
+    line; under torchrun the pairs are sharded (whole edges per rank, LPT on
+    rendering work) and one result all-reduce gathers the fused transforms."""
+    import torch
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2408_10154_gb300 as gs
+    from paper_2408_10154_gb300 import shard, synth
+    ctx = gs.Context(torch.cuda.current_device(), 96 << 30)
+    wl = synth.batched_pairs()
+    if args.pairs:
+        wl["pairs"] = wl["pairs"][:args.pairs]  # a smaller batch (profiling captures only)
+    costs = [shard.edge_cost(len(pr["gaussians"]["means4"]), len(pr["gaussians"]["means4"]), pr["src_cams"],
+                             pr["tgt_cams"]) for pr in wl["pairs"]]
+    mine = shard.lpt_partition(costs, world)[rank]
+    problems, px = edge_problems(gs, ctx, torch, [wl["pairs"][i] for i in mine])
+    rec, res = measure_batched(gs, ctx, torch, args.steps, args.warmup, problems, px)
+    plain_ms, batch_ms = rec["plain"]["ms_per_batch"], rec["batched"]["ms_per_batch"]
     n_edges = len(wl["pairs"])
     rows = {i: np.concatenate([np.asarray(res[0][k], np.float64).reshape(12), [res[1][k]]])
             for k, i in enumerate(mine)}
@@ -604,27 +695,15 @@ def run_batched(args):
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         dist.all_reduce(t)
         plain_ms, batch_ms, px = float(tmax[0]), float(tmax[1]), int(t[2])
-        lat_obj = [None] * world
-        dist.all_gather_object(lat_obj, lat_all)
-        lat_all = [x for l in lat_obj for x in l]
-    lat_all = sorted(lat_all)
-    out = {"metric": METRIC, "value": n_edges * iters / (batch_ms / 1000.0), "unit": UNIT, "n_gpus": world,
+    out = {"metric": METRIC, "value": n_edges * ITERS / (batch_ms / 1000.0), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True,
            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "batched_32: 32 uneven submap pairs (20k-400k Gaussians, 4-12 keyframes per "
-                                  "submap at 640x480 / 1200x680), both directions, %d iterations" % iters,
-                      "pixels_per_iteration": px, "step": "all 32 loop edges, one registration iteration"},
-           "batched": {"ms_per_batch": batch_ms, "edges_per_s": n_edges / (batch_ms / 1000.0),
-                       "mpx_per_s": px * iters / (batch_ms / 1000.0) / 1e6,
-                       "edges_within_1deg_2cm": int(sum(
-                           rot_err(fused[i, :12].reshape(3, 4), pr["T_gt"])[0] < 1.0 and
-                           rot_err(fused[i, :12].reshape(3, 4), pr["T_gt"])[1] < 0.02
-                           for i, pr in enumerate(wl["pairs"])))},
-           "plain": {"ms_per_batch": plain_ms, "edges_per_s": n_edges / (plain_ms / 1000.0),
-                     "mpx_per_s": px * iters / (plain_ms / 1000.0) / 1e6,
-                     "edge_latency_ms": {"p50": float(np.percentile(lat_all, 50)),
-                                         "p99": float(np.percentile(lat_all, 99))}},
-           "batched_over_plain": plain_ms / batch_ms}
+           "config": {"workload": rec["workload"], "pixels_per_iteration": px,
+                      "step": "all %d loop edges, %d registration iterations" % (n_edges, ITERS)},
+           "batched": rec["batched"], "plain": rec["plain"], "batched_over_plain": plain_ms / batch_ms,
+           "edges_within_1deg_2cm": int(sum(
+               rot_err(fused[i, :12].reshape(3, 4), pr["T_gt"])[0] < 1.0 and
+               rot_err(fused[i, :12].reshape(3, 4), pr["T_gt"])[1] < 0.02 for i, pr in enumerate(wl["pairs"])))}
     if world > 1:
         out["config"]["sharding"] = "whole edges per rank by LPT on rendering work; one result all-reduce"
     if rank == 0:
@@ -642,6 +721,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--room-only", action="store_true",
+                    help="the room line only (no batched and serving records)")
+    ap.add_argument("--serve-rate", type=float, default=12.0,
+                    help="arrivals per second of the serving record in the default line")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--workload", default="room_150k", choices=["room_150k", "batched_32", "serve", "overlap"],
                     help="room_150k: the benchmark line; batched_32: batched vs one-pair-per-call; "
                          "serve: continuous-batching server vs one request at a time")
@@ -650,6 +734,8 @@ def main():
     ap.add_argument("--pool", type=int, default=64, help="serve: resident tracking submaps")
     ap.add_argument("--max-kf", type=int, default=128, help="serve: keyframe problems in flight")
     ap.add_argument("--round-iters", type=int, default=10, help="serve: iterations per round")
+    ap.add_argument("--pairs", type=int, default=0,
+                    help="batched_32: register only the first N pairs (profiling captures; 0 = all 32)")
     ap.add_argument("--iters", type=int, default=ITERS,
                     help="iterations per loop edge (100 for the benchmark; fewer only for profiling captures)")
     args = ap.parse_args()

@@ -56,7 +56,9 @@ typedef enum {
     GS_ERR_NONFINITE = 4,   /* an input Gaussian parameter or pose is NaN / Inf */
     GS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
     GS_ERR_DIVERGED = 6,    /* a registration ended with a non-finite residual */
-    GS_ERR_CAPACITY = 7     /* a duplicate list outgrew its capacity twice */
+    GS_ERR_CAPACITY = 7     /* the tile lists outgrew their capacity (gs_register* after its redos,
+                               gs_bin's caller capacity), or the work exceeds the fixed scratch of
+                               gs_render_noalloc */
 } gs_status_t;
 
 typedef struct gs_ctx gs_ctx_t;
@@ -121,16 +123,26 @@ typedef struct {
      * pose; not combinable with tracking_loss */
     int32_t exposure;
     float lr_exposure; /* 0.1 (Supp. B) */
-    /* CTA schedule of the compositing kernels in gs_register* (results are
-     * identical either way): 0 = picked by the autotuner (the first
-     * registration of a plan shape on a context times both on trial
-     * iterations from the initial poses and keeps the faster), 1 = natural
-     * tile order, 2 = longest tile lists first */
+    /* CTA schedule of the compositing kernels in gs_register* and the
+     * server (results are identical either way): 0 = picked by the
+     * autotuner (the first registration of a plan shape on a context times
+     * the four below on trial iterations from the initial poses, keeps the
+     * fastest per shape and starts over); one CTA per tile in 1 = natural
+     * tile order, 2 = longest tile lists first; persistent CTAs (as many as
+     * fit on the GPU) pulling tiles of every keyframe problem from one work
+     * queue in 3 = natural order, 4 = longest lists first */
     int32_t tile_schedule;
-    /* tile lists of gs_register* (results are identical either way): 1 =
-     * each Gaussian listed only on the tiles where some pixel can reach
-     * alpha_min (its alpha-threshold ellipse's box, with margins; about a
-     * third fewer duplicates), 0 = the 3-sigma rectangles of gs_bin */
+    /* tile rectangles of every call that projects or bins (gs_project and
+     * so gs_bin, gs_render, gs_render_backward, gs_render_noalloc,
+     * gs_register*, the server): 1 = each Gaussian listed only on the tiles
+     * of its 3-sigma rectangle whose pixel centres can reach alpha_min (the
+     * box of its alpha-threshold ellipse, with margins, by a fixed FP32
+     * operation sequence; about a third fewer duplicates on room-sized
+     * scenes), 0 = the 3-sigma rectangles.  Colour, depth, alpha and final
+     * transmittance are identical either way (the dropped pairs fail the
+     * alpha test); list positions (`last`) differ, so gs_render and
+     * gs_render_backward must use the same value.  Needs alpha_min >=
+     * FLT_MIN and smooth = 0, else the 3-sigma rectangles are used. */
     int32_t tight_lists;
     /* capacity of the tile lists of gs_register* as a multiple of the
      * duplicates at the initial poses (1.5; 64 Ki entries more when >= 1):
@@ -148,7 +160,7 @@ typedef struct {
     int64_t n_pixels;        /* pixels of one render pass over all keyframes */
     int64_t pairs;           /* sum over iterations and pixels of the list prefix the adjoint re-walks */
     int32_t iterations;      /* optimisation iterations run */
-    int32_t reserved;
+    int32_t schedule;        /* CTA schedule the registration ran (1..4, see tile_schedule) */
     /* profile != 0: summed CUDA-event time (ms) of each phase over the
      * iterations: project, bin (tile counts and ranges, placement, per-tile
      * sort), forward+loss, backward, pose update */
@@ -208,7 +220,8 @@ gs_status_t gs_project(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *pose
                        float *records, float *aux, int32_t *counts, gs_stream_t stream);
 
 /* Tile binning of the records of gs_project: duplicates every visible record
- * into each tile it touches with key (global tile << 32) | float bits of z,
+ * into each tile of its rectangle (the tight or the 3-sigma one, as
+ * gs_project's options chose) with key (global tile << 32) | float bits of z,
  * value = record index, sorted stably by key (ties keep record order), and
  * per-tile [start, end) ranges (0,0 when empty).  Camera c's tiles follow
  * those of cameras 0..c-1 (row-major within a camera).
@@ -348,12 +361,16 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
  * counting them).  The call synchronises `stream` (to count duplicates) and
  * returns GS_ERR_NONFINITE for non-finite Gaussian parameters.
  *
- * The first call on a device looks up the scratch's device address (once
- * per device, with that device current); make that first call before any
- * stream capture.  Every call on a device reuses the same scratch and leaves
- * its contents behind; the call clears what must start at zero.  Two calls
- * that overlap on the GPU (different streams or threads at the same time)
- * race on the scratch and produce undefined results: serialise them. */
+ * The scratch's device address belongs to the CUDA context the call runs
+ * in (a device's primary context, a context made current with the driver
+ * API, or a primary context re-created after cudaDeviceReset each have
+ * their own copy of the array): the first call in each context looks it up
+ * with that context current and caches it under the context's id; make
+ * that first call before any stream capture.  Every call in a context
+ * reuses the same scratch and leaves its contents behind; the call clears
+ * what must start at zero.  Two calls that overlap on the GPU (different
+ * streams or threads at the same time) race on the scratch and produce
+ * undefined results: serialise them. */
 gs_status_t gs_render_noalloc(const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams, int n_cams,
                               const gs_options_t *opt, float *rgb, float *depth, float *alpha, float *t_final,
                               int32_t *last, gs_stream_t stream);
@@ -385,6 +402,35 @@ typedef struct {
 gs_status_t gs_register_batch(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt, int iters,
                               double *T_out, double *conf_out, double *eps_out, gs_stream_t stream);
 
+/* Stream-ordered forms of gs_register and gs_register_batch (Sec. 3.2, the
+ * same problem statement: P, Q, their keyframes -> T_{P->Q} and the
+ * residuals eps): every output is a DEVICE buffer written on `stream`, and
+ * the call returns once the work is enqueued, so a caller can chain edges
+ * (or feed T to its own kernels) without a host round trip.  Results equal
+ * the synchronous calls' bit for bit.
+ *   T_dev [problems][12] double, conf_dev [problems] double,
+ *   eps_dev [keyframes] double or NULL (V^P first, problem-major),
+ *   est_dev [keyframes][12] double or NULL (gs_register_async only),
+ *   status_dev [1] int32: written on the stream when the work completes --
+ *     GS_OK, GS_ERR_NONFINITE, GS_ERR_TIMEOUT, GS_ERR_DIVERGED, or
+ *     GS_ERR_CAPACITY when the tile lists outgrew their capacity (the
+ *     outputs are then invalid: redo with gs_register, which grows them).
+ * The lists are sized from the largest duplicate count an earlier call on
+ * this context saw for the same plan shape (tiles, keyframe problems,
+ * records) times list_headroom; for a shape it has not seen, the call
+ * counts them first, which synchronises `stream` once.  Growing the
+ * context's scratch (a larger plan than before) frees and allocates device
+ * memory, which synchronises the device.  The CTA schedule is the one the
+ * autotuner chose earlier for the shape, else natural order (no trial
+ * runs); profile is ignored.  Calls on one context must use one stream. */
+gs_status_t gs_register_async(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gaussians_t *tgt,
+                              const gs_view_t *src_views, int n_src_views, const gs_view_t *tgt_views,
+                              int n_tgt_views, const gs_options_t *opt, int iters, double *T_dev, double *conf_dev,
+                              double *eps_dev, double *est_dev, int32_t *status_dev, gs_stream_t stream);
+gs_status_t gs_register_batch_async(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt,
+                                    int iters, double *T_dev, double *conf_dev, double *eps_dev, int32_t *status_dev,
+                                    gs_stream_t stream);
+
 /* ----------------------------------------------------------- loop filter */
 
 /* Overlap ratio of submaps P and Q under T = T_{P->Q} (the loop filter of
@@ -412,6 +458,14 @@ gs_status_t gs_overlap_ratio(gs_ctx_t *ctx, const gs_gaussians_t *p, const gs_ga
  * Synchronises `stream`. */
 gs_status_t gs_sort_u32(gs_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int bits, gs_stream_t stream);
 
+/* FP32 peak probe (no counterpart in the paper; the denominator of the
+ * compositing kernels' roofline): 8 independent FMA chains per thread,
+ * 8 CTAs of 256 threads per SM, 4096 rounds, timed with CUDA events on
+ * `stream`; *tflops = the best of five timed launches (2 flops per FMA),
+ * *sm_count (may be NULL) = the device's multiprocessor count.
+ * Synchronises `stream`. */
+gs_status_t gs_probe_fp32(gs_ctx_t *ctx, double *tflops, int *sm_count, gs_stream_t stream);
+
 /* Self-test of the bounded device waits (no counterpart in the paper): one
  * sort pass over (keys, vals) whose first tile of 2048 keys is withheld, so
  * that every later tile's look-back runs out of its spin limit (well under
@@ -431,9 +485,12 @@ gs_status_t gs_selftest_bounded_wait(gs_ctx_t *ctx, uint32_t *keys, uint32_t *va
  *
  * gs_server_step runs one round on `stream`:
  *   1. admits waiting requests in submission order while the in-flight
- *      keyframe problems stay <= max_keyframes and the estimated scratch of
+ *      keyframe problems stay <= max_keyframes and the scratch footprint of
  *      the in-flight requests stays <= hbm_budget_bytes (the first waiting
- *      request is always admitted into an empty server);
+ *      request is always admitted into an empty server).  A request's
+ *      footprint comes from its tile lists counted at submission (its
+ *      Gaussians projected and binned at its starting poses on a separate
+ *      measuring context and stream; see gs_server_footprint);
  *   2. when the in-flight set changed, re-plans it: one projection pass per
  *      moving submap, one sort and one compositing launch over every tile of
  *      every in-flight keyframe per iteration, captured into a CUDA graph,
@@ -455,9 +512,11 @@ const char *gs_server_last_error(const gs_server_t *srv);
 
 /* Queues a request; the problem's arrays must stay valid until it is done.
  * iters >= 0.  *id_out = the request id (ids start at 0 and increase).
- * GS_ERR_OOM if the request's estimated scratch alone exceeds the budget
- * (hbm_budget_bytes, 0 = 16 GiB; the scratch arena may exceed it by a
- * quarter, at least 256 MiB, to absorb the estimate's error). */
+ * Counts the request's tile lists first (synchronises the measuring
+ * context's own stream, not the serving stream).  GS_ERR_OOM if the
+ * request's footprint alone exceeds the budget (hbm_budget_bytes, 0 =
+ * 16 GiB; the scratch arena may exceed it by a quarter, at least 256 MiB,
+ * for the lists' growth as the poses move). */
 gs_status_t gs_server_submit(gs_server_t *srv, const gs_problem_t *problem, int iters, int64_t *id_out);
 
 /* One round (see above).  done_ids [max_done] host out (may be NULL): ids of
@@ -474,6 +533,18 @@ gs_status_t gs_server_poll(gs_server_t *srv, int64_t id, int *state, double *T_o
 
 /* Counts: requests waiting, in flight, done; rounds and re-plans run. */
 gs_status_t gs_server_counts(const gs_server_t *srv, int64_t out[5]);
+
+/* Admission by measured footprint: out[0] = requests whose tile lists were
+ * counted at submission, out[1] = requests the memory budget kept waiting
+ * at least once, out[2] = scratch bytes of the requests in flight now. */
+gs_status_t gs_server_admission(const gs_server_t *srv, int64_t out[3]);
+
+/* The footprint admission used for request `id`: *dups = its tile
+ * duplicates at its starting poses, *bytes = its scratch in a plan (per
+ * record 100 B, per list entry 12.5 B at the server's list headroom, per
+ * pixel 9 B (+12 B for tracking), per tile 92 B, per keyframe problem its
+ * optimiser state).  Either pointer may be NULL. */
+gs_status_t gs_server_footprint(const gs_server_t *srv, int64_t id, int64_t *dups, int64_t *bytes);
 
 /* Rigid transform of a submap by T (Eq. 8/9): mu <- R mu + t,
  * q <- q_R (x) q (so Sigma <- R Sigma R^T); scales, opacities, colours

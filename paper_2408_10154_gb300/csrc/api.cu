@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -24,7 +25,7 @@ enum Slot {
     S_HIST, S_HISTP, S_RANGES, S_FLAGS, S_TF, S_LAST, S_CODE, S_TLOSS, S_TTWIST, S_POSE64, S_ADAM, S_PIVOT,
     S_CCAM, S_CENT, S_LOSS, S_SETVP, S_REV, S_PFIRST, S_PCOUNT, S_TOUT, S_CONF, S_EST, S_GRAD, S_DUPG,
     S_PAIRS, S_RK0, S_RK1, S_RP0, S_RP1, S_RRANGES, S_TERR, S_TCOL, S_TW,
-    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_GCELL2, S_GSTART2, S_GCUR2, S_GPART2, S_GPTS2, S_GIDX2, S_GLIST2, S_GNL2, S_SEGZ, S_SEGCUR, S_SEGBIG, S_SEGLIST, S_COUNT
+    S_TMED, S_TNV, S_TVPS, S_EXPO, S_EXPO32, S_TEXPO, S_OPT, S_ONN1, S_ONN2, S_OD2, S_OT, S_OCNT, S_MAPS, S_OS, S_ORDER, S_ORDC, S_SK, S_SV, S_SN, S_OBOX, S_GCELL, S_GSTART, S_GCUR, S_GPART, S_GPTS, S_GIDX, S_GLIST, S_GNL, S_GCELL2, S_GSTART2, S_GCUR2, S_GPART2, S_GPTS2, S_GIDX2, S_GLIST2, S_GNL2, S_SEGZ, S_SEGCUR, S_SEGBIG, S_SEGLIST, S_PROBE, S_QUEUE, S_COUNT
 };
 
 struct Buf {
@@ -53,6 +54,9 @@ struct gs_ctx {
     // autotuner: tile schedule chosen per plan shape (tiles, keyframes, records)
     std::map<std::tuple<uint64_t, size_t, uint64_t>, int> schedule;
     int64_t tuned = 0;  // trial runs made
+    // largest tile-duplicate count seen at the initial poses per plan shape
+    // (sizes the lists of the asynchronous registration calls)
+    std::map<std::tuple<uint64_t, size_t, uint64_t>, uint32_t> dups_seen;
 };
 
 namespace {
@@ -190,8 +194,8 @@ gs_status_t check_options(gs_ctx *ctx, const gs_options_t *o)
         return fail(ctx, GS_ERR_INVALID_ARG, "options out of range");
     if ((o->tracking_loss != 0 && o->tracking_loss != 1) || !(o->lambda_c >= 0 && o->lambda_c <= 1))
         return fail(ctx, GS_ERR_INVALID_ARG, "tracking_loss must be 0 or 1 and lambda_c in [0, 1]");
-    if (o->tile_schedule < 0 || o->tile_schedule > 2)
-        return fail(ctx, GS_ERR_INVALID_ARG, "tile_schedule must be 0 (autotune), 1 or 2");
+    if (o->tile_schedule < 0 || o->tile_schedule > 4)
+        return fail(ctx, GS_ERR_INVALID_ARG, "tile_schedule must be 0 (autotune) or 1..4");
     if (o->tight_lists != 0 && o->tight_lists != 1)
         return fail(ctx, GS_ERR_INVALID_ARG, "tight_lists must be 0 or 1");
     if (!(o->list_headroom > 0.0f) || !(o->list_headroom <= 64.0f))
@@ -394,7 +398,7 @@ gs_status_t alloc_sort(gs_ctx *ctx, uint64_t want, Pipe &p)
 int run_bin(const gsl::BinArgs &b, cudaStream_t s) { return gsl::bin_seg(b, s); }
 
 gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, const float *pose32,
-                              const gs_options_t *o, bool tight = false)
+                              const gs_options_t *o)
 {
     gsl::ProjectArgs a{};
     a.vps = D.vps;
@@ -409,8 +413,9 @@ gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, co
     a.aux = p.aux;
     a.counts = p.counts;
     a.flags = p.flags;
-    a.tight = tight && o->alpha_min > 0 && !o->smooth;
-    a.skip_below = skip_threshold(o);
+    // tight lists need a normal alpha_min (the contract's logarithm)
+    a.tight = o->tight_lists != 0 && o->alpha_min >= FLT_MIN && !o->smooth;
+    a.alpha_min = o->alpha_min;
     // the projection counts and lists for the segmented build (run_bin follows every projection here)
     a.seg_hdr = p.seg_hdr;
     a.seg_diff = p.seg_diff;
@@ -475,10 +480,10 @@ gsl::RasterArgs raster_args(const Plan &P, const DevPlan &D, const Pipe &p, int 
 
 // project + count duplicates (synchronises) + size the sort + emit/sort/range
 gs_status_t project_and_bin(gs_ctx *ctx, const Plan &P, const DevPlan &D, Pipe &p, const float *pose32,
-                            const gs_options_t *o, cudaStream_t s, int *cur, uint32_t *n_dups_out, bool tight = false)
+                            const gs_options_t *o, cudaStream_t s, int *cur, uint32_t *n_dups_out)
 {
     GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
-    gsl::project(project_args(P, D, p, pose32, o, tight), s);
+    gsl::project(project_args(P, D, p, pose32, o), s);
     gsl::BinArgs b = bin_args(P, D, p);
     gsl::bin_count(b, s);
     uint32_t nd = 0;
@@ -543,6 +548,29 @@ __global__ void k_to_float(const double *in, float *out, int n)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n)
         out[i] = (float)in[i];
+}
+
+// FP32 peak probe: each thread runs 8 independent FMA chains for `iters`
+// rounds (enough independent work per warp to hide the FMA latency), and
+// writes one value so the chains are not removed.
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(256) k_fma_probe(float *sink, int iters, float a, float b)
+{
+    float x[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k)
+        x[k] = (float)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k)
+            x[k] = fmaf(x[k], a, b);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k)
+        s += x[k];
+    if (s == 1.2345f)  // never true for the arguments used: keeps the store conditional
+        sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 // The keyframe problems of one registration problem (Sec. 3.2): keyframes
@@ -654,8 +682,15 @@ gs_status_t check_problem(gs_ctx *ctx, const gs_problem_t &q)
     return GS_OK;
 }
 
+// device outputs of the asynchronous registration calls
+struct AsyncOut {
+    double *T = nullptr, *conf = nullptr, *eps = nullptr, *est = nullptr;
+    int32_t *status = nullptr;
+};
+
 gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_options_t *opt, int iters,
-                             cudaStream_t s, double *T_out, double *conf_out, double *eps_out, double *est_out);
+                             cudaStream_t s, double *T_out, double *conf_out, double *eps_out, double *est_out,
+                             const AsyncOut *ao = nullptr);
 
 }  // namespace
 
@@ -1317,6 +1352,48 @@ gs_status_t gs_transform_batch(gs_ctx_t *ctx, const gs_gaussians_t *maps, int n_
     return GS_OK;
 }
 
+gs_status_t gs_probe_fp32(gs_ctx_t *ctx, double *tflops, int *sm_count, gs_stream_t stream)
+{
+    if (!ctx || !tflops)
+        return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int sms = 0;
+    GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (sm_count)
+        *sm_count = sms;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    float *sink = nullptr;
+    GS_TRY(wsT(ctx, S_PROBE, (size_t)blocks * threads, &sink));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GS_CUDA(cudaEventCreate(&e0));
+    GS_CUDA(cudaEventCreate(&e1));
+    float best = 0.0f;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 6 && err == cudaSuccess; ++rep) {
+        err = cudaEventRecord(e0, s);
+        k_fma_probe<<<blocks, threads, 0, s>>>(sink, iters, 0.9999999f, 1e-7f);
+        ++gsl::g_launches;
+        if (err == cudaSuccess)
+            err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess)
+            err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess)
+            err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && rep > 0 && ms > 0.0f) {  // the first launch warms up
+            const float tf = (float)((double)blocks * threads * iters * kProbeChains * 2.0 / (ms * 1e-3) / 1e12);
+            best = std::max(best, tf);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess)
+        return fail(ctx, GS_ERR_CUDA, std::string("fp32 probe: ") + cudaGetErrorString(err));
+    *tflops = best;
+    return GS_OK;
+}
+
 gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gaussians_t *tgt,
                         const gs_view_t *src_views, int n_src_views, const gs_view_t *tgt_views, int n_tgt_views,
                         const gs_options_t *opt, int iters, double *T_out, double *confidence, double *eps_out,
@@ -1345,6 +1422,68 @@ gs_status_t gs_register(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gauss
     int sets = 0;
     add_problem(P, src, tgt, src_views, n_src_views, tgt_views, n_tgt_views, 0, sets, opt);
     return run_registration(ctx, P, 1, opt, iters, (cudaStream_t)stream, T_out, confidence, eps_out, est_out);
+}
+
+gs_status_t gs_register_async(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gaussians_t *tgt,
+                              const gs_view_t *src_views, int n_src_views, const gs_view_t *tgt_views,
+                              int n_tgt_views, const gs_options_t *opt, int iters, double *T_dev, double *conf_dev,
+                              double *eps_dev, double *est_dev, int32_t *status_dev, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_options(ctx, opt));
+    if (!src || !tgt || !T_dev || !conf_dev || !status_dev || iters < 0 || n_src_views < 0 || n_tgt_views < 0 ||
+        n_src_views + n_tgt_views == 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_register_async: bad arguments");
+    gs_problem_t q{};
+    q.src = *src;
+    q.tgt = *tgt;
+    q.src_views = src_views;
+    q.n_src_views = n_src_views;
+    q.tgt_views = tgt_views;
+    q.n_tgt_views = n_tgt_views;
+    GS_TRY(check_problem(ctx, q));
+    DeviceGuard dg(ctx->device);
+    Plan P;
+    int sets = 0;
+    add_problem(P, src, tgt, src_views, n_src_views, tgt_views, n_tgt_views, 0, sets, opt);
+    AsyncOut ao;
+    ao.T = T_dev;
+    ao.conf = conf_dev;
+    ao.eps = eps_dev;
+    ao.est = est_dev;
+    ao.status = status_dev;
+    return run_registration(ctx, P, 1, opt, iters, (cudaStream_t)stream, nullptr, nullptr, nullptr, nullptr, &ao);
+}
+
+gs_status_t gs_register_batch_async(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt,
+                                    int iters, double *T_dev, double *conf_dev, double *eps_dev, int32_t *status_dev,
+                                    gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_options(ctx, opt));
+    if (n <= 0 || !problems || iters < 0 || !T_dev || !conf_dev || !status_dev)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_register_batch_async: bad arguments");
+    for (int i = 0; i < n; ++i) {
+        GS_TRY(check_problem(ctx, problems[i]));
+        if (problems[i].opt)
+            GS_TRY(check_options(ctx, problems[i].opt));
+    }
+    DeviceGuard dg(ctx->device);
+    Plan P;
+    int sets = 0;
+    for (int i = 0; i < n; ++i) {
+        const gs_problem_t &q = problems[i];
+        add_problem(P, &q.src, &q.tgt, q.src_views, q.n_src_views, q.tgt_views, q.n_tgt_views, i, sets,
+                    q.opt ? q.opt : opt);
+    }
+    AsyncOut ao;
+    ao.T = T_dev;
+    ao.conf = conf_dev;
+    ao.eps = eps_dev;
+    ao.status = status_dev;
+    return run_registration(ctx, P, n, opt, iters, (cudaStream_t)stream, nullptr, nullptr, nullptr, nullptr, &ao);
 }
 
 gs_status_t gs_register_batch(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt, int iters,
@@ -1378,8 +1517,30 @@ namespace {
 // The registration engine behind gs_register and gs_register_batch: every
 // keyframe problem of the plan (any mix of submaps, keyframe counts and
 // image sizes) advances together, one CUDA graph per iteration.
+// The status word of an asynchronous registration: the device flags and the
+// residuals' finiteness as a gs_status_t.
+__global__ void k_async_status(const int *flags, const double *eps, int nv, int32_t *status)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    const int f = *flags;
+    int32_t st = GS_OK;
+    if (f & gsk::kFlagNonFinite)
+        st = GS_ERR_NONFINITE;
+    else if (f & gsk::kFlagTimeout)
+        st = GS_ERR_TIMEOUT;
+    else if (f & gsk::kFlagCapacity)
+        st = GS_ERR_CAPACITY;
+    else
+        for (int v = 0; v < nv; ++v)
+            if (!isfinite(eps[v]))
+                st = GS_ERR_DIVERGED;
+    *status = st;
+}
+
 gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_options_t *opt, int iters,
-                             cudaStream_t s, double *T_out, double *conf_out, double *eps_out, double *est_out)
+                             cudaStream_t s, double *T_out, double *conf_out, double *eps_out, double *est_out,
+                             const AsyncOut *ao)
 {
     GS_TRY(finalize(ctx, P));
     DevPlan D;
@@ -1444,7 +1605,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
 
     unsigned long long *pairs = nullptr;
     GS_TRY(wsT(ctx, S_PAIRS, 2 * ntl, &pairs));  // per tile: walked, contributing
-    const bool prof = opt->profile != 0 && iters > 0;
+    const bool prof = opt->profile != 0 && iters > 0 && !ao;
     if (prof) {
         for (cudaEvent_t &e : ctx->tev)
             if (!e)
@@ -1459,6 +1620,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
     gsl::RasterArgs expo_r{};
     GS_TRY(alloc_exposure(ctx, P, pa, expo_r));
     double headroom = opt->list_headroom;
+    const auto key = std::make_tuple((uint64_t)P.n_tiles, P.vps.size(), (uint64_t)P.n_records);
     for (int attempt = 0; attempt < 3; ++attempt) {
         const long long l0 = gsl::g_launches;
         long long captured = 0, graph_kernels = 0, trial_kernels = 0;
@@ -1466,10 +1628,19 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         gsl::centroids(D.vps, D.set_vp, n_sets, cent, s);
         gsl::pose_init(pa, s);
         // size the duplicate lists at the initial poses (with headroom: the
-        // count drifts as the poses move)
+        // count drifts as the poses move).  The asynchronous form takes the
+        // largest count an earlier call saw for this plan shape, and counts
+        // (synchronising once) only for a shape it has not seen.
         int cur = 0;
         uint32_t nd = 0;
-        GS_TRY(project_and_bin(ctx, P, D, p, pose32, opt, s, &cur, &nd, opt->tight_lists != 0));
+        const auto seen = ctx->dups_seen.find(key);
+        if (ao && seen != ctx->dups_seen.end()) {
+            nd = seen->second;
+        } else {
+            GS_TRY(project_and_bin(ctx, P, D, p, pose32, opt, s, &cur, &nd));
+            uint32_t &m = ctx->dups_seen[key];
+            m = std::max(m, nd);
+        }
         const uint64_t want = (uint64_t)(headroom * nd) + (headroom >= 1.0 ? 65536 : 0);
         if (p.cap < want)
             GS_TRY(alloc_sort(ctx, want, p));
@@ -1490,10 +1661,11 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         r.count_contrib = opt->profile >= 2;
         gsl::TrackArgs ta;
         GS_TRY(alloc_track(ctx, P, D, r, ta, tloss, s));
-        uint32_t *order = nullptr, *order_cnt = nullptr;
+        uint32_t *order = nullptr, *order_cnt = nullptr, *queue = nullptr;
         GS_TRY(wsT(ctx, S_ORDER, ntl, &order));
         GS_TRY(wsT(ctx, S_ORDC, 128, &order_cnt));
-        bool ordered = false, marking = prof;
+        GS_TRY(wsT(ctx, S_QUEUE, 4, &queue));
+        bool ordered = false, persistent = false, marking = prof;
         cudaError_t mark_err = cudaSuccess;
         auto mark = [&](int k, cudaStream_t st) {
             // an event record node of the captured graph (re-targeted per replay)
@@ -1502,7 +1674,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         };
         auto iteration = [&](cudaStream_t st) {
             mark(0, st);
-            gsl::project(project_args(P, D, p, pose32, opt, opt->tight_lists != 0), st);
+            gsl::project(project_args(P, D, p, pose32, opt), st);
             mark(1, st);
             const int c = run_bin(b, st);
             if (ordered)
@@ -1510,6 +1682,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             mark(2, st);
             r.vals = p.vals[c];
             r.tile_order = ordered ? order : nullptr;
+            r.queue = persistent ? queue : nullptr;
             gsl::forward(r, true, st);
             gsl::track_loss(ta, st);
             mark(3, st);
@@ -1537,48 +1710,57 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
                 cudaGraphDestroy(graph);
             return GS_OK;
         };
-        // Autotuner: the CTA schedule of the compositing kernels (natural
-        // tile order or longest lists first) for this plan shape, timed on
-        // trial iterations A B B A from the initial poses, then the poses
-        // start over.  Either schedule gives the same results.
+        // Autotuner: the CTA schedule of the compositing kernels for this
+        // plan shape -- tile order (natural, or longest lists first) x launch
+        // (one CTA per tile, or persistent CTAs pulling tiles from one work
+        // queue over every keyframe problem) -- timed on trial iterations
+        // 1 2 3 4 4 3 2 1 from the initial poses, then the poses start over.
+        // Every schedule gives the same results.
         int sched = opt->tile_schedule;
-        const auto key = std::make_tuple((uint64_t)P.n_tiles, P.vps.size(), (uint64_t)P.n_records);
         if (sched == 0) {
             const auto it = ctx->schedule.find(key);
             if (it != ctx->schedule.end()) {
                 sched = it->second;
-            } else if (iters >= 8 && P.n_tiles >= 2048) {
+            } else if (iters >= 8 && P.n_tiles >= 2048 && !ao) {
                 marking = false;
-                cudaGraphExec_t ga = nullptr, gb = nullptr;
+                cudaGraphExec_t g[4] = {};
                 const long long t0 = gsl::g_launches;
-                ordered = false;
-                GS_TRY(capture(&ga, nullptr));
-                ordered = true;
-                gs_status_t st = capture(&gb, nullptr);
+                gs_status_t st = GS_OK;
+                for (int k = 0; k < 4 && st == GS_OK; ++k) {
+                    ordered = (k & 1) != 0;
+                    persistent = (k & 2) != 0;
+                    st = capture(&g[k], nullptr);
+                }
                 trial_kernels = gsl::g_launches - t0;  // each graph runs twice: count them once more
-                cudaEvent_t e[5] = {};
+                cudaEvent_t e[9] = {};
                 for (cudaEvent_t &x : e)
                     if (st == GS_OK && cudaEventCreate(&x) != cudaSuccess)
                         st = fail(ctx, GS_ERR_CUDA, "autotuner events");
-                const cudaGraphExec_t seq[4] = {ga, gb, gb, ga};
+                const int seq[8] = {0, 1, 2, 3, 3, 2, 1, 0};
                 if (st == GS_OK && cudaEventRecord(e[0], s) != cudaSuccess)
                     st = fail(ctx, GS_ERR_CUDA, "autotuner events");
-                for (int k = 0; k < 4 && st == GS_OK; ++k)
-                    if (cudaGraphLaunch(seq[k], s) != cudaSuccess || cudaEventRecord(e[k + 1], s) != cudaSuccess)
+                for (int k = 0; k < 8 && st == GS_OK; ++k)
+                    if (cudaGraphLaunch(g[seq[k]], s) != cudaSuccess || cudaEventRecord(e[k + 1], s) != cudaSuccess)
                         st = fail(ctx, GS_ERR_CUDA, "autotuner trial launch");
                 float ms[4] = {0, 0, 0, 0};
-                if (st == GS_OK && cudaEventSynchronize(e[4]) == cudaSuccess)
-                    for (int k = 0; k < 4; ++k)
-                        cudaEventElapsedTime(&ms[k], e[k], e[k + 1]);
+                if (st == GS_OK && cudaEventSynchronize(e[8]) == cudaSuccess)
+                    for (int k = 0; k < 8; ++k) {
+                        float x = 0.0f;
+                        cudaEventElapsedTime(&x, e[k], e[k + 1]);
+                        ms[seq[k]] += x;
+                    }
                 for (cudaEvent_t x : e)
                     if (x)
                         cudaEventDestroy(x);
-                if (ga)
-                    cudaGraphExecDestroy(ga);
-                if (gb)
-                    cudaGraphExecDestroy(gb);
+                for (cudaGraphExec_t x : g)
+                    if (x)
+                        cudaGraphExecDestroy(x);
                 GS_TRY(st);
-                sched = (ms[1] + ms[2] < ms[0] + ms[3]) ? 2 : 1;
+                int best = 0;
+                for (int k = 1; k < 4; ++k)
+                    if (ms[k] < ms[best])
+                        best = k;
+                sched = best + 1;
                 ctx->schedule[key] = sched;
                 ++ctx->tuned;
                 gsl::pose_init(pa, s);  // back to the initial poses
@@ -1587,7 +1769,9 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
                 sched = 1;
             }
         }
-        ordered = sched == 2;
+        ordered = sched == 2 || sched == 4;
+        persistent = sched >= 3;
+        const int sched_run = sched;
         GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
         GS_CUDA(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * 2 * ntl, s));
         if (iters > 0) {
@@ -1638,7 +1822,8 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         // residual eps at the final poses, then Eq. 7
         r.tile_pairs = nullptr;
         r.tile_order = nullptr;
-        gsl::project(project_args(P, D, p, pose32, opt, opt->tight_lists != 0), s);
+        r.queue = nullptr;
+        gsl::project(project_args(P, D, p, pose32, opt), s);
         r.vals = p.vals[run_bin(b, s)];
         gsl::forward(r, true, s);
         gsl::track_loss(ta, s);
@@ -1658,6 +1843,26 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         f.est_out = est;
         gsl::fuse(f, s);
         GS_CUDA(cudaGetLastError());
+        if (ao) {
+            // stream-ordered results in the caller's device buffers and a
+            // device status word; nothing is read back, nothing is redone
+            k_async_status<<<1, 32, 0, s>>>(p.flags, lossd, nv, ao->status);
+            ++gsl::g_launches;
+            GS_CUDA(cudaMemcpyAsync(ao->T, Tdev, 12 * sizeof(double) * n_problems, cudaMemcpyDeviceToDevice, s));
+            GS_CUDA(cudaMemcpyAsync(ao->conf, confd, sizeof(double) * n_problems, cudaMemcpyDeviceToDevice, s));
+            if (ao->eps)
+                GS_CUDA(cudaMemcpyAsync(ao->eps, lossd, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+            if (ao->est)
+                GS_CUDA(cudaMemcpyAsync(ao->est, est, 12 * sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+            GS_CUDA(cudaGetLastError());
+            gs_stats_t &st = ctx->stats;
+            st.kernel_launches = (gsl::g_launches - l0) - captured + graph_kernels * iters;
+            st.n_dups = nd;
+            st.n_pixels = P.n_pix;
+            st.iterations = iters;
+            st.schedule = sched_run;
+            return GS_OK;
+        }
         int flags = 0;
         GS_TRY(read_flags(ctx, p, s, &flags));
         if (flags & gsk::kFlagNonFinite)
@@ -1683,6 +1888,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         st.n_dups = nd;
         st.n_pixels = P.n_pix;
         st.iterations = iters;
+        st.schedule = sched_run;
         for (size_t k = 0; k < ntl; ++k) {
             st.pairs += (int64_t)pairs_h[k];
             st.contributing += (int64_t)pairs_h[ntl + k];
@@ -1716,31 +1922,70 @@ namespace {
 // the fixed scratch; every GPU that loads the library holds it until exit
 __device__ __align__(256) unsigned char g_noalloc_scratch[GS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kNoallocMaxDevices = 64;
+// The scratch's device address belongs to the module as loaded in one CUDA
+// context: the primary context of a device, a context the caller created
+// with the driver API, or the primary context re-created after
+// cudaDeviceReset each have their own.  The address is therefore looked up
+// once per context (keyed by the driver's context id, which is never
+// reused within a process) with that context current, and cached.
 std::mutex g_noalloc_mutex;
-void *g_noalloc_addr[kNoallocMaxDevices] = {};
+std::map<unsigned long long, void *> g_noalloc_addr;
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
 
-// Device address of the scratch on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// id of the calling thread's current context, or false if it cannot be had
+bool current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = (CtxGetCurrentFn)f1;
+            get_id = (CtxGetIdFn)f2;
+        }
+        cudaGetLastError();
+        looked_up = true;
+    }
+    void *c = nullptr;
+    return get_current && get_id && get_current(&c) == 0 && c && get_id(c, id) == 0;
+}
+
+// Device address of the scratch in the current context.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress (once per context; on every call if the context id
+// cannot be read).  The first call in a context does this set-up.
 gs_status_t noalloc_scratch(void **out)
 {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
         cudaGetLastError();
         return GS_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return GS_ERR_CUDA;
+    unsigned long long id = 0;
+    const bool keyed = current_context_id(&id);
+    if (keyed) {
+        const auto it = g_noalloc_addr.find(id);
+        if (it != g_noalloc_addr.end()) {
+            *out = it->second;
+            return GS_OK;
         }
-        g_noalloc_addr[dev] = p;
     }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
+    if (keyed)
+        g_noalloc_addr[id] = p;
+    *out = p;
     return GS_OK;
 }
 
@@ -1854,8 +2099,6 @@ namespace {
 // per keyframe problem: pose64 [12], Adam state [13], pivot [3], camera-frame
 // pivot [3], exposure state [7]
 constexpr int kVpState = 38;
-// tile duplicates per record assumed by admission (the room workload has ~1.2)
-constexpr double kAdmitDupsPerRecord = 3.0;
 
 struct ServerReq {
     gs_gaussians_t src{}, tgt{};
@@ -1870,7 +2113,9 @@ struct ServerReq {
     double T[12] = {}, conf = 0;
     std::vector<double> eps;
     double t_submit = 0, t_done = 0;
-    size_t est_bytes = 0;
+    size_t est_bytes = 0;  // scratch footprint from its measured tile duplicates
+    int64_t dups = 0;      // tile duplicates at its starting poses, counted at submission
+    bool held = false;     // once kept waiting by the memory budget
     int n_vps() const { return (int)(sv.size() + tv.size()); }
 };
 
@@ -1878,6 +2123,8 @@ struct ServerReq {
 
 struct gs_server {
     gs_ctx *ctx = nullptr;
+    gs_ctx *mctx = nullptr;  // footprint measurement (own scratch and stream: never the in-flight plan's)
+    int64_t measured = 0, held_back = 0;
     gs_options_t opt{};
     int max_kf = 0, max_round = 0;
     size_t budget = 0;
@@ -1911,21 +2158,69 @@ double srv_now(const gs_server *srv)
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - srv->t0).count();
 }
 
-size_t estimate_bytes(const ServerReq &r)
+// Scratch of a request in a plan, from its measured tile duplicates nd:
+// per record 100 B (record 48, auxiliary 32, count 4, list entry 16); per
+// list entry of capacity (headroom x nd; a plan's 64 Ki spare entries come
+// out of the arena's slack) 12.5 B (depth bits, two value buffers,
+// histogram share); per pixel 9 B (final transmittance,
+// last contributor, loss sign code), 12 B more for tracking masks; per tile
+// 92 B (range, keyframe, loss, twist, counters, cursors, order); per
+// keyframe problem its FP64 optimiser state.
+size_t footprint_bytes(const ServerReq &r, int64_t nd, double headroom)
 {
-    double b = 0;
+    double rec = 0, px = 0, tiles = 0;
     auto add = [&](const gs_gaussians_t &g, const gs_view_t &v) {
-        const double n = (double)g.n, px = (double)v.cam.width * v.cam.height;
-        const double tiles = (double)((v.cam.width + GS_TILE - 1) / GS_TILE) * ((v.cam.height + GS_TILE - 1) / GS_TILE);
-        // records + aux + counts + depth keys; duplicates (keys + values, double-buffered, headroom);
-        // per pixel T_final, last, code; per tile ranges, loss, twist, counters
-        b += n * (48 + 32 + 4 + 16) + kAdmitDupsPerRecord * n * 16 * 1.5 + px * 9 + tiles * (8 + 4 + 48 + 16);
+        rec += (double)g.n;
+        px += (double)v.cam.width * v.cam.height;
+        tiles += (double)((v.cam.width + GS_TILE - 1) / GS_TILE) * ((v.cam.height + GS_TILE - 1) / GS_TILE);
     };
     for (const gs_view_t &v : r.sv)
         add(r.tgt, v);
     for (const gs_view_t &v : r.tv)
         add(r.src, v);
+    const double per_px = 9.0 + (r.opt.tracking_loss ? 12.0 : 0.0);
+    const double b = rec * 100.0 + headroom * (double)nd * 12.5 + px * per_px + tiles * 92.0 +
+                     (double)r.n_vps() * kVpState * 8.0;
     return (size_t)b + 4096;
+}
+
+// Counts the request's tile duplicates at its starting poses (the identity)
+// on the measuring context: projection and list counting only, on that
+// context's own stream (synchronised), so nothing of the plan in flight is
+// touched.
+gs_status_t srv_measure(gs_server *srv, ServerReq &r)
+{
+    if (!srv->mctx)
+        GS_TRY(gs_ctx_create(srv->ctx->device, 0, &srv->mctx));
+    gs_ctx *ctx = srv->mctx;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = ctx->cap;
+    Plan P;
+    int sets = 0;
+    add_problem(P, &r.src, &r.tgt, r.sv.data(), (int)r.sv.size(), r.tv.data(), (int)r.tv.size(), 0, sets, &r.opt);
+    GS_TRY(finalize(ctx, P));
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    Pipe p;
+    GS_TRY(alloc_pipe(ctx, P, false, p));
+    const int nv = (int)P.vps.size();
+    std::vector<float> ident((size_t)12 * nv, 0.0f);
+    for (int v = 0; v < nv; ++v)
+        ident[12 * v] = ident[12 * v + 5] = ident[12 * v + 10] = 1.0f;
+    float *pose32 = nullptr;
+    GS_TRY(upload(ctx, S_POSE32, ident, &pose32, s));
+    GS_CUDA(cudaMemsetAsync(p.flags, 0, sizeof(int), s));
+    gsl::project(project_args(P, D, p, pose32, &r.opt), s);
+    gsl::BinArgs b = bin_args(P, D, p);
+    gsl::bin_count(b, s);
+    uint32_t nd = 0;
+    GS_CUDA(cudaMemcpyAsync(&nd, p.ndups, sizeof nd, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    if (nd == 0xffffffffu)
+        return fail(srv->ctx, GS_ERR_CAPACITY, "more than 2^32 tile duplicates");
+    r.dups = nd;
+    ++srv->measured;
+    return GS_OK;
 }
 
 // admits waiting requests (FIFO) within the keyframe and memory limits
@@ -1940,8 +2235,13 @@ void srv_admit(gs_server *srv)
     while (srv->wait_head < srv->waiting.size()) {
         ServerReq &r = srv->reqs[srv->waiting[srv->wait_head]];
         const bool empty = srv->active.empty();
-        if (!empty && (kf + r.n_vps() > srv->max_kf || bytes + r.est_bytes > srv->budget))
+        if (!empty && (kf + r.n_vps() > srv->max_kf || bytes + r.est_bytes > srv->budget)) {
+            if (!r.held && kf + r.n_vps() <= srv->max_kf) {
+                r.held = true;  // kept waiting by the memory budget
+                ++srv->held_back;
+            }
             break;
+        }
         kf += r.n_vps();
         bytes += r.est_bytes;
         r.state = 1;
@@ -2056,7 +2356,7 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     // size the duplicate lists at the current poses
     int cur = 0;
     uint32_t nd = 0;
-    GS_TRY(project_and_bin(ctx, P, D, p, srv->pose32, &srv->opt, s, &cur, &nd, srv->opt.tight_lists != 0));
+    GS_TRY(project_and_bin(ctx, P, D, p, srv->pose32, &srv->opt, s, &cur, &nd));
     const uint64_t want = (uint64_t)(srv->headroom * nd) + 65536;
     if (p.cap < want)
         GS_TRY(alloc_sort(ctx, want, p));
@@ -2075,7 +2375,7 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     gsl::TrackArgs ta;
     GS_TRY(alloc_track(ctx, P, D, r, ta, srv->tloss, s));
     GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    gsl::project(project_args(P, D, p, srv->pose32, &srv->opt, srv->opt.tight_lists != 0), ctx->cap);
+    gsl::project(project_args(P, D, p, srv->pose32, &srv->opt), ctx->cap);
     r.vals = p.vals[run_bin(b, ctx->cap)];
     gsl::forward(r, true, ctx->cap);
     gsl::track_loss(ta, ctx->cap);
@@ -2244,6 +2544,8 @@ gs_status_t gs_server_destroy(gs_server_t *srv)
             cudaGraphExecDestroy(srv->exec);
     }
     gs_ctx_destroy(srv->ctx);
+    if (srv->mctx)
+        gs_ctx_destroy(srv->mctx);
     delete srv;
     return GS_OK;
 }
@@ -2269,10 +2571,13 @@ gs_status_t gs_server_submit(gs_server_t *srv, const gs_problem_t *q, int iters,
     r.sv.assign(q->src_views, q->src_views + q->n_src_views);
     r.tv.assign(q->tgt_views, q->tgt_views + q->n_tgt_views);
     r.iters = iters;
-    r.est_bytes = estimate_bytes(r);
+    const gs_status_t ms = srv_measure(srv, r);
+    if (ms != GS_OK)
+        return fail(ctx, ms, "counting the request's tile lists: " + (srv->mctx ? srv->mctx->err : std::string()));
+    r.est_bytes = footprint_bytes(r, r.dups, srv->headroom);
     if (r.est_bytes > srv->budget)
         return fail(ctx, GS_ERR_OOM, "the request's scratch (" + std::to_string(r.est_bytes) +
-                                         " bytes estimated) exceeds the server's budget");
+                                         " bytes for its measured tile lists) exceeds the server's budget");
     r.t_submit = srv_now(srv);
     *id_out = (int64_t)srv->reqs.size();
     srv->waiting.push_back(*id_out);
@@ -2311,6 +2616,30 @@ gs_status_t gs_server_poll(gs_server_t *srv, int64_t id, int *state, double *T_o
         std::memcpy(eps_out, r.eps.data(), r.eps.size() * sizeof(double));
     if (t_done)
         *t_done = r.t_done;
+    return GS_OK;
+}
+
+gs_status_t gs_server_admission(const gs_server_t *srv, int64_t out[3])
+{
+    if (!srv || !out)
+        return GS_ERR_INVALID_ARG;
+    size_t bytes = 0;
+    for (int64_t id : srv->active)
+        bytes += srv->reqs[id].est_bytes;
+    out[0] = srv->measured;
+    out[1] = srv->held_back;
+    out[2] = (int64_t)bytes;
+    return GS_OK;
+}
+
+gs_status_t gs_server_footprint(const gs_server_t *srv, int64_t id, int64_t *dups, int64_t *bytes)
+{
+    if (!srv || id < 0 || id >= (int64_t)srv->reqs.size())
+        return GS_ERR_INVALID_ARG;
+    if (dups)
+        *dups = srv->reqs[id].dups;
+    if (bytes)
+        *bytes = (int64_t)srv->reqs[id].est_bytes;
     return GS_OK;
 }
 

@@ -91,11 +91,36 @@ __device__ __forceinline__ float exp_ct_core(float x)
     p = __fmaf_rn(p, r, 0.5f);
     p = __fmaf_rn(p, r, 1.0f);
     p = __fmaf_rn(p, r, 1.0f);
-    // k = kf exactly: t = 1.5 * 2^23 + k holds k in its low mantissa bits
-    // (|k| <= 116 here), so an integer difference of the bit patterns gives
-    // it without a float-to-int conversion
-    const int k = __float_as_int(t) - 0x4B400000;
-    return __fmul_rn(p, __int_as_float((k + 127) << 23));
+    // p * 2^k with k = kf: t = 1.5 * 2^23 + k holds k in its low mantissa
+    // bits (|k| <= 116 here), and the bit pattern of 1.5 * 2^23 (0x4B400000)
+    // is 0 in its low 9 bits, so bits(t) << 23 = k << 23 (mod 2^32).  p lies
+    // in [0.7, 1.5) and p 2^k stays a normal number, so adding k to p's
+    // exponent field is the exact product __fmul_rn(p, 2^k), bit for bit.
+    return __int_as_float(__float_as_int(p) + (int)((uint32_t)__float_as_int(t) << 23));
+}
+
+// ln x for a positive normal x (the tight tile lists' threshold): x = m 2^e
+// with m in [sqrt(1/2), sqrt(2)), ln m = 2 artanh(s) with s = (m - 1) /
+// (m + 1), |s| <= 0.1716, by the odd series 2 (s + s^3/3 + ... + s^9/9)
+// (first omitted term below 2e-10), plus e ln 2.  A fixed FP32 operation
+// sequence (no library logarithm), so the oracle takes the same value.
+__device__ __forceinline__ float log_ct(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)(b >> 23) - 127;
+    float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+    if (m > 1.41421354f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(s, s);
+    float p = 0.222222222f;              // 2/9
+    p = __fmaf_rn(p, s2, 0.285714286f);  // 2/7
+    p = __fmaf_rn(p, s2, 0.4f);          // 2/5
+    p = __fmaf_rn(p, s2, 0.666666667f);  // 2/3
+    p = __fmaf_rn(p, s2, 2.0f);
+    return __fmaf_rn((float)e, 0.693147181f, __fmul_rn(s, p));
 }
 
 // hi + lo += bhi + blo without losing the rounding error of the high parts
@@ -201,14 +226,15 @@ struct ProjectArgs {
     float4 *aux;               // [records][2] auxiliary (may be null)
     int32_t *counts;
     int *flags;
-    // registration lists: shrink each rectangle to the tiles that meet the
+    // tight lists: shrink each rectangle to the tiles that meet the
     // axis-aligned box of the record's alpha-threshold ellipse (exponent >=
     // ln(alpha_min / o) - 0.06, box widened by 0.1 % + 0.01 px; nearly
-    // singular conics keep the 3-sigma rectangle).  The dropped (tile,
-    // record) pairs fail the alpha test at every pixel of the tile, so the
-    // compositing is unchanged; the lists are no longer those of gs_bin.
+    // singular conics keep the 3-sigma rectangle; see tighten in
+    // project.cu).  The dropped (tile, record) pairs fail the alpha test at
+    // every pixel of the tile, so the compositing is unchanged; the lists
+    // (and list positions such as `last`) are shorter.
     int tight;
-    float skip_below;         // ln(alpha_min) - 0.05
+    float alpha_min;          // the threshold of the tight rectangles
     // segmented tile lists (null: not built here): clears seg_hdr/seg_diff
     // (seg_zero_bytes), then every visible record adds its rectangle to its
     // keyframe's difference grid, and every record writes its seg_list
@@ -310,6 +336,8 @@ struct RasterArgs {
     unsigned long long *tile_pairs;  // [2][tiles] += sum of `last`, pairs passing the alpha test
                                      // (count_contrib only); statistics, may be null
     const uint32_t *tile_order;      // CTA -> tile schedule (longest lists first), or null = natural
+    uint32_t *queue;                 // registration: work-queue word of the persistent kernels (zeroed
+                                     // before each launch), or null = one CTA per tile
     int exposure;                    // some keyframe compensates exposure (forward variant)
     int count_contrib;               // count the pairs that pass the alpha test (forward variant)
     float2 *tile_twist;       // [tiles][6] camera-frame twist as FP32 (hi, lo) pairs (value hi + lo)

@@ -20,39 +20,46 @@ namespace {
 
 using namespace gsk;
 
-// The tiles of [x0, x1) x [y0, y1) whose pixel centres can reach the
-// record's alpha threshold (see ProjectArgs::tight): the ellipse
-// d^T Q d <= -2 tau, tau = ln(alpha_min / o) - 0.06, lies in the box of
-// half-sizes sqrt(-2 tau Sigma00), sqrt(-2 tau Sigma11) about (u, v); tile t
+// Tight tile rectangle (contract step 7b, see ProjectArgs::tight): the
+// tiles of the 3-sigma rectangle [x0, x1) x [y0, y1) whose pixel centres can
+// reach the record's alpha threshold.  Such a pixel lies in the ellipse
+// d^T Q d <= -2 tau (Q = [[A, B], [B, C]], A = -2 ca, B = -cb, C = -2 cc;
+// tau = ln(alpha_min) - ln(o) - 0.06 with the contract's log_ct), whose
+// axis-aligned box about (u, v) has half-sizes sqrt(-2 tau C / det),
+// sqrt(-2 tau A / det) (det = AC - B^2), widened by 0.1 % + 0.01 px; tile t
 // meets it when its centres [16 t + 0.5, 16 t + 15.5] meet the box.  An
-// opacity below alpha_min e^-0.06 empties the rectangle.
+// opacity below alpha_min e^-0.06 empties the rectangle; nearly singular
+// conics (B^2 > 0.998 AC), whose FP32 exponent is less accurate than the
+// margins, keep the 3-sigma rectangle.  Every step is a fixed FP32
+// operation, mirrored by the oracle, so both sides build the same lists.
 // the reciprocal of the tile size, a power of two: x * kInvTile is x / 16
 // correctly rounded
 constexpr float kInvTile = 1.0f / (float)kTile;
 static_assert(kTile == 16, "kInvTile is exact for a power-of-two tile");
 
-__device__ __forceinline__ void tighten(float ca, float cb, float cc, float o, float u, float v, float skip_below,
+__device__ __forceinline__ void tighten(float ca, float cb, float cc, float o, float u, float v, float alpha_min,
                                         int TX, int TY, int &x0, int &x1, int &y0, int &y1)
 {
-    const float A = -2.0f * ca, B = -cb, C = -2.0f * cc;
-    const float AC = A * C, BB = B * B;
-    const float tau = skip_below - 0.01f - __logf(o);
-    if (tau >= 0.0f) {
+    const float tau = sub_rn(sub_rn(log_ct(alpha_min), log_ct(o)), 0.06f);
+    if (!(tau < 0.0f)) {
         x1 = x0;
         return;
     }
-    const float det = AC - BB;
-    if (!(det > 0.0f) || !(BB <= 0.998f * AC))
+    const float A = mul_rn(-2.0f, ca), B = -cb, C = mul_rn(-2.0f, cc);
+    const float AC = mul_rn(A, C), BB = mul_rn(B, B);
+    const float det = sub_rn(AC, BB);
+    if (!(det > 0.0f) || !(BB <= mul_rn(0.998f, AC)))
         return;
-    const float s = (-2.0f * tau) / det;
-    const float ex = fmaf(sqrtf(s * C), 1.001f, 0.01f), ey = fmaf(sqrtf(s * A), 1.001f, 0.01f);
+    const float s = __fdiv_rn(mul_rn(-2.0f, tau), det);
+    const float ex = fma_rn(__fsqrt_rn(mul_rn(s, C)), 1.001f, 0.01f);
+    const float ey = fma_rn(__fsqrt_rn(mul_rn(s, A)), 1.001f, 0.01f);
     if (!(ex >= 0.0f) || !(ey >= 0.0f))
         return;
     const float iB = kInvTile;
-    const float tx0 = fminf(fmaxf(ceilf((u - ex - 15.5f) * iB), 0.0f), (float)TX);
-    const float tx1 = fminf(fmaxf(floorf((u + ex - 0.5f) * iB) + 1.0f, 0.0f), (float)TX);
-    const float ty0 = fminf(fmaxf(ceilf((v - ey - 15.5f) * iB), 0.0f), (float)TY);
-    const float ty1 = fminf(fmaxf(floorf((v + ey - 0.5f) * iB) + 1.0f, 0.0f), (float)TY);
+    const float tx0 = fminf(fmaxf(ceilf(mul_rn(sub_rn(sub_rn(u, ex), 15.5f), iB)), 0.0f), (float)TX);
+    const float tx1 = fminf(fmaxf(add_rn(floorf(mul_rn(sub_rn(add_rn(u, ex), 0.5f), iB)), 1.0f), 0.0f), (float)TX);
+    const float ty0 = fminf(fmaxf(ceilf(mul_rn(sub_rn(sub_rn(v, ey), 15.5f), iB)), 0.0f), (float)TY);
+    const float ty1 = fminf(fmaxf(add_rn(floorf(mul_rn(sub_rn(add_rn(v, ey), 0.5f), iB)), 1.0f), 0.0f), (float)TY);
     x0 = max(x0, (int)tx0);
     x1 = min(x1, (int)tx1);
     y0 = max(y0, (int)ty0);
@@ -219,7 +226,7 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
                         y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)TY);
                         y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)TY);
                         if (a.tight)
-                            tighten(ca, cb, cc, opa, u, vv, a.skip_below, TX, TY, x0, x1, y0, y1);
+                            tighten(ca, cb, cc, opa, u, vv, a.alpha_min, TX, TY, x0, x1, y0, y1);
                     }
                     if (x0 < x1 && y0 < y1) {
                         count = (x1 - x0) * (y1 - y0);

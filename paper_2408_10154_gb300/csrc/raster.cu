@@ -21,6 +21,8 @@
 // bit-reproducible.
 #include <float.h>
 
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace {
@@ -126,13 +128,13 @@ __device__ __forceinline__ float4 stage_cutoff(float4 q1, const gsl::RasterArgs 
 // costs the common variant a register)
 constexpr int kFwdExposure = 1, kFwdCount = 2;
 
+// One tile of the forward (all 256 threads of the CTA take part).
 template <bool REG, int X>
-__global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
+__device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_t t)
 {
     __shared__ float4 s0[256], s1[256], s2[256];
     __shared__ uint8_t s_sel[8][256];  // per warp: batch positions that may hit its patch
     __shared__ float s_red[8];
-    const uint32_t t = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
     // The first batch is staged before any barrier (nothing has read the
     // staging arrays yet) and its list entry is read before the tile's
     // descriptor is used, so that the two chains of dependent loads (range,
@@ -315,6 +317,48 @@ __global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
                 atomicAdd(&a.tile_pairs[a.n_tiles + t], nc);
         }
     }
+}
+
+// One CTA per tile (the grid covers every tile; tile_order, when given,
+// maps CTA -> tile).
+template <bool REG, int X>
+__global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
+{
+    fwd_tile<REG, X>(a, a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x);
+}
+
+// Persistent form: a grid of a few CTAs per SM, each CTA pulling the next
+// tile (in tile_order, or natural order) from the work queue a.queue (one
+// atomic per tile, zeroed before the launch) until every tile is taken.
+// Tiles of every keyframe problem of a batch share one queue.  Thread 0
+// claims the next queue position as a tile starts and publishes it only
+// when the tile ends, so the atomic's round trip overlaps the tile's work;
+// the barrier before publishing also ends every thread's use of the
+// previous tile's shared memory (the tile's own barriers order the read of
+// s_next before its next write).
+template <typename Tile>
+__device__ __forceinline__ void run_queue(const gsl::RasterArgs &a, Tile &&tile)
+{
+    __shared__ uint32_t s_next;
+    uint32_t claimed = threadIdx.x == 0 ? atomicAdd(a.queue, 1u) : 0u;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_next = claimed;
+        __syncthreads();
+        const uint32_t i = s_next;
+        if (i >= a.n_tiles)
+            return;
+        if (threadIdx.x == 0)
+            claimed = atomicAdd(a.queue, 1u);
+        tile(a.tile_order ? a.tile_order[i] : i);
+    }
+}
+
+template <bool REG, int X>
+__global__ void __launch_bounds__(256, 6) k_forward_q(const gsl::RasterArgs a)
+{
+    run_queue(a, [&](uint32_t t) { fwd_tile<REG, X>(a, t); });
 }
 
 // Warp sums of N (8 or 16) values per lane.  Each exchange over a lane bit
@@ -589,8 +633,9 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
 
 static_assert(kBwd2Chunk <= kBwd2Threads && kBwd2Chunk % 32 == 0, "one thread stages one record");
 
+// One tile of the adjoint (all kBwd2Threads threads of the CTA take part).
 template <bool REG, bool FULL>
-__global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(const gsl::RasterArgs a)
+__device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_t t)
 {
     constexpr int NG = FULL ? 10 : 6;
     extern __shared__ float4 s_dyn[];  // declared float4: 16-byte aligned for the float4 zeroing
@@ -600,7 +645,6 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
     __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
     __shared__ int s_maxl[kBwd2Warps];
     __shared__ float s_tw[kBwd2Warps][6][2];
-    const uint32_t t = a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x;
     const int vp = (int)a.tile_vp[t];
     const VpDesc &d = a.vps[vp];
     const uint32_t lt = t - d.tile_base;
@@ -741,18 +785,55 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(cons
 }
 
 template <bool REG, bool FULL>
+__global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2(const gsl::RasterArgs a)
+{
+    bwd_tile<REG, FULL>(a, a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x);
+}
+
+// persistent form of the adjoint (see k_forward_q)
+template <bool REG, bool FULL>
+__global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2_q(const gsl::RasterArgs a)
+{
+    run_queue(a, [&](uint32_t t) { bwd_tile<REG, FULL>(a, t); });
+}
+
+template <bool REG, bool FULL>
 constexpr size_t bwd2_smem()
 {
     return (size_t)(FULL ? 10 : 6) * kBwd2Warps * kBwd2Chunk * sizeof(float);
 }
+
+// CTAs of the persistent kernels: as many as can be resident at once
+// (occupancy x SMs), found once by raster_init
+int g_fwd_q_ctas = 0, g_bwd_q_ctas = 0;
 
 // (a one-pixel-per-thread adjoint with 256-thread CTAs measured 2.00 ms
 // against 1.43 ms for this one on the room workload)
 template <bool REG, bool FULL>
 void launch_backward(const gsl::RasterArgs &a, cudaStream_t s)
 {
+    if constexpr (REG && !FULL) {
+        if (a.queue && g_bwd_q_ctas > 0) {
+            cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
+            k_backward2_q<REG, FULL><<<(unsigned)std::min<uint32_t>(a.n_tiles, g_bwd_q_ctas), kBwd2Threads,
+                                       bwd2_smem<REG, FULL>(), s>>>(a);
+            ++gsl::g_launches;
+            return;
+        }
+    }
     k_backward2<REG, FULL><<<a.n_tiles, kBwd2Threads, bwd2_smem<REG, FULL>(), s>>>(a);
     ++gsl::g_launches;
+}
+
+template <int X>
+void launch_forward_reg(const gsl::RasterArgs &a, cudaStream_t s)
+{
+    if (a.queue && g_fwd_q_ctas > 0) {
+        cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
+        k_forward_q<true, X><<<(unsigned)std::min<uint32_t>(a.n_tiles, g_fwd_q_ctas), 256, 0, s>>>(a);
+    } else {
+        k_forward<true, X><<<a.n_tiles, 256, 0, s>>>(a);
+    }
 }
 
 }  // namespace
@@ -767,6 +848,18 @@ void raster_init()
                          (int)bwd2_smem<false, false>());
     cudaFuncSetAttribute(k_backward2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)bwd2_smem<false, true>());
+    cudaFuncSetAttribute(k_backward2_q<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd2_smem<true, false>());
+    int dev = 0, sms = 0, f = 0, b = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_forward_q<true, 0>, 256, 0) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward2_q<true, false>, kBwd2Threads,
+                                                      bwd2_smem<true, false>()) == cudaSuccess) {
+        g_fwd_q_ctas = std::max(f, 1) * sms;
+        g_bwd_q_ctas = std::max(b, 1) * sms;
+    }
+    cudaGetLastError();
 }
 
 void forward(const RasterArgs &a, bool registration, cudaStream_t s)
@@ -778,13 +871,13 @@ void forward(const RasterArgs &a, bool registration, cudaStream_t s)
     if (!registration)
         k_forward<false, 0><<<a.n_tiles, 256, 0, s>>>(a);
     else if (a.exposure && a.count_contrib)
-        k_forward<true, kFwdExposure | kFwdCount><<<a.n_tiles, 256, 0, s>>>(a);
+        launch_forward_reg<kFwdExposure | kFwdCount>(a, s);
     else if (a.exposure)
-        k_forward<true, kFwdExposure><<<a.n_tiles, 256, 0, s>>>(a);
+        launch_forward_reg<kFwdExposure>(a, s);
     else if (a.count_contrib)
-        k_forward<true, kFwdCount><<<a.n_tiles, 256, 0, s>>>(a);
+        launch_forward_reg<kFwdCount>(a, s);
     else
-        k_forward<true, 0><<<a.n_tiles, 256, 0, s>>>(a);
+        launch_forward_reg<0>(a, s);
     ++g_launches;
 }
 

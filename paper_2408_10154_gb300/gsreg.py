@@ -60,7 +60,7 @@ class gs_options_t(ctypes.Structure):
 
 class gs_stats_t(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("n_dups", ctypes.c_int64), ("n_pixels", ctypes.c_int64),
-                ("pairs", ctypes.c_int64), ("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pairs", ctypes.c_int64), ("iterations", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("phase_ms", ctypes.c_double * 5), ("contributing", ctypes.c_int64)]
 
 
@@ -71,11 +71,11 @@ class gs_gaussian_grads_t(ctypes.Structure):
 
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
-           "gs_fuse", "gs_register", "gs_register_batch", "gs_transform", "gs_render_noalloc", "gs_track_loss",
-           "gs_overlap_ratio", "gs_transform_batch", "gs_sort_u32", "gs_selftest_bounded_wait",
+           "gs_fuse", "gs_register", "gs_register_batch", "gs_register_async", "gs_register_batch_async", "gs_transform", "gs_render_noalloc", "gs_track_loss",
+           "gs_overlap_ratio", "gs_transform_batch", "gs_sort_u32", "gs_selftest_bounded_wait", "gs_probe_fp32",
            "gs_server_create",
            "gs_server_destroy", "gs_server_last_error", "gs_server_submit", "gs_server_step", "gs_server_poll",
-           "gs_server_counts"]
+           "gs_server_counts", "gs_server_admission", "gs_server_footprint"]
 
 _lock = threading.Lock()
 _lib = None
@@ -116,12 +116,15 @@ def load(build_if_missing: bool = False):
             "gs_transform_batch": ([P, P, I, P, P, P, P], I),
             "gs_sort_u32": ([P, P, P, I64, I, P], I),
             "gs_selftest_bounded_wait": ([P, P, P, I64, P], I),
+            "gs_probe_fp32": ([P, P, P, P], I),
             "gs_pose_step": ([P, I, P, P, P, P, I, I, P, P], I),
             "gs_fuse": ([P, I, P, P, P, P, P, P], I),
             "gs_register": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P], I),
             "gs_transform": ([P, P, P, P, P, P], I),
             "gs_render_noalloc": ([P, P, P, I, P, P, P, P, P, P, P], I),
             "gs_register_batch": ([P, P, I, P, I, P, P, P, P], I),
+            "gs_register_async": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P, P], I),
+            "gs_register_batch_async": ([P, P, I, P, I, P, P, P, P, P], I),
             "gs_server_create": ([I, ctypes.c_size_t, I, I, P, P], I),
             "gs_server_destroy": ([P], I),
             "gs_server_last_error": ([P], ctypes.c_char_p),
@@ -129,6 +132,8 @@ def load(build_if_missing: bool = False):
             "gs_server_step": ([P, P, P, I, P], I),
             "gs_server_poll": ([P, I64, P, P, P, P, P, P], I),
             "gs_server_counts": ([P, P], I),
+            "gs_server_admission": ([P, P], I),
+            "gs_server_footprint": ([P, I64, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -434,6 +439,13 @@ def gs_sort_u32(ctx: Context, keys, vals, bits=32):
     return keys, vals
 
 
+def gs_probe_fp32(ctx: Context):
+    """Measured FP32 FMA throughput of the device: (TFLOP/s, SM count)."""
+    tf, sms = ctypes.c_double(), ctypes.c_int()
+    ctx.check(ctx._lib.gs_probe_fp32(ctx.handle, ctypes.byref(tf), ctypes.byref(sms), _stream()))
+    return tf.value, sms.value
+
+
 def gs_transform_batch(ctx: Context, maps, Ts):
     """Map adjustment: every submap of ``maps`` moved by its own T (Eq. 8/9)
     in one launch.  Returns new Gaussians per map."""
@@ -458,16 +470,20 @@ def gs_render_noalloc(g: Gaussians, poses: torch.Tensor, cams, opt=None, out=Non
     opt = opt or default_options()
     npx = _npix(cams)
     dev = g.means4.device
-    out = dict(out or {})
-    out.setdefault("rgb", torch.empty(3 * npx, device=dev))
-    out.setdefault("depth", torch.empty(npx, device=dev))
-    out.setdefault("alpha", torch.empty(npx, device=dev))
-    out.setdefault("t_final", torch.empty(npx, device=dev))
-    out.setdefault("last", torch.empty(npx, dtype=torch.int32, device=dev))
-    gst = g.c_struct()
-    st = load().gs_render_noalloc(ctypes.byref(gst), _ptr(poses.contiguous()), cam_arr, nc, ctypes.byref(opt),
-                                  _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]), _ptr(out["t_final"]),
-                                  _ptr(out["last"]), _stream())
+    if poses.dtype != torch.float32 or tuple(poses.shape) != (nc, 12) or poses.device != dev:
+        raise ValueError(f"poses must be float32 [{nc}, 12] on {dev}")
+    # the C call runs on the current device: make it the submap's
+    with torch.cuda.device(dev):
+        out = dict(out or {})
+        out.setdefault("rgb", torch.empty(3 * npx, device=dev))
+        out.setdefault("depth", torch.empty(npx, device=dev))
+        out.setdefault("alpha", torch.empty(npx, device=dev))
+        out.setdefault("t_final", torch.empty(npx, device=dev))
+        out.setdefault("last", torch.empty(npx, dtype=torch.int32, device=dev))
+        gst = g.c_struct()
+        st = load().gs_render_noalloc(ctypes.byref(gst), _ptr(poses.contiguous()), cam_arr, nc, ctypes.byref(opt),
+                                      _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]),
+                                      _ptr(out["t_final"]), _ptr(out["last"]), _stream())
     return st, out
 
 
@@ -509,6 +525,53 @@ def gs_register_batch(ctx: Context, problems, iters, opt=None):
     ctx.check(ctx._lib.gs_register_batch(ctx.handle, arr, n, ctypes.byref(opt), int(iters), d(T), d(conf), d(eps),
                                          _stream()))
     return T.reshape(n, 3, 4), conf, eps[:total]
+
+
+def gs_register_async(ctx: Context, src: Gaussians, tgt: Gaussians, src_views, tgt_views, iters, opt=None,
+                      out=None):
+    """gs_register enqueued on the current stream with device outputs (no
+    host synchronisation once the plan shape's list size is known).  Returns
+    dict(T [3,4], conf [1], eps [n], est [n,3,4] float64, status [1] int32),
+    all CUDA tensors, valid once the stream reaches them; ``out`` may supply
+    them.  The returned dict also keeps the keyframe arrays the call reads."""
+    opt = opt or default_options()
+    n = len(src_views) + len(tgt_views)
+    dev = src.means4.device
+    o = dict(out or {})
+    o.setdefault("T", torch.empty((3, 4), dtype=torch.float64, device=dev))
+    o.setdefault("conf", torch.empty(1, dtype=torch.float64, device=dev))
+    o.setdefault("eps", torch.empty(max(n, 1), dtype=torch.float64, device=dev))
+    o.setdefault("est", torch.empty((max(n, 1), 3, 4), dtype=torch.float64, device=dev))
+    o.setdefault("status", torch.full((1,), -1, dtype=torch.int32, device=dev))
+    sv, tv = _views(src_views), _views(tgt_views)
+    s, t = src.c_struct(), tgt.c_struct()
+    ctx.check(ctx._lib.gs_register_async(ctx.handle, ctypes.byref(s), ctypes.byref(t), sv, len(src_views), tv,
+                                         len(tgt_views), ctypes.byref(opt), int(iters), _ptr(o["T"]), _ptr(o["conf"]),
+                                         _ptr(o["eps"]), _ptr(o["est"]), _ptr(o["status"]), _stream()))
+    o["_keep"] = (src, tgt, src_views, tgt_views)
+    return o
+
+
+def gs_register_batch_async(ctx: Context, problems, iters, opt=None):
+    """gs_register_batch enqueued on the current stream with device outputs:
+    dict(T [n,3,4], conf [n], eps [keyframes] float64, status [1] int32)."""
+    opt = opt or default_options()
+    n = len(problems)
+    arr = (gs_problem_t * n)()
+    keep = []
+    total = 0
+    for i, p in enumerate(problems):
+        arr[i] = _problem(p, keep)
+        total += len(p[2]) + len(p[3])
+    dev = problems[0][0].means4.device
+    o = dict(T=torch.empty((n, 3, 4), dtype=torch.float64, device=dev),
+             conf=torch.empty(n, dtype=torch.float64, device=dev),
+             eps=torch.empty(max(total, 1), dtype=torch.float64, device=dev),
+             status=torch.full((1,), -1, dtype=torch.int32, device=dev))
+    ctx.check(ctx._lib.gs_register_batch_async(ctx.handle, arr, n, ctypes.byref(opt), int(iters), _ptr(o["T"]),
+                                               _ptr(o["conf"]), _ptr(o["eps"]), _ptr(o["status"]), _stream()))
+    o["_keep"] = (problems, keep)
+    return o
 
 
 class Server:
@@ -574,6 +637,19 @@ class Server:
         out = (ctypes.c_int64 * 5)()
         self.check(self._lib.gs_server_counts(self.handle, out))
         return tuple(out)
+
+    def admission(self):
+        """(requests measured, requests held back by the memory budget,
+        bytes in flight)."""
+        out = (ctypes.c_int64 * 3)()
+        self.check(self._lib.gs_server_admission(self.handle, out))
+        return tuple(out)
+
+    def footprint(self, rid: int):
+        """(tile duplicates at the starting poses, scratch bytes) of a request."""
+        d, b = ctypes.c_int64(), ctypes.c_int64()
+        self.check(self._lib.gs_server_footprint(self.handle, int(rid), ctypes.byref(d), ctypes.byref(b)))
+        return d.value, b.value
 
     def close(self):
         if self.handle:

@@ -96,14 +96,20 @@ CASES = {"plain_2k": plain_case, "ragged_100x70": ragged_case, "needles_300x200"
 
 
 # ----------------------------------------------------------------- projection
-def check_projection(gs, ctx, gd, cams, poses):
+def opts(gs, tight):
+    """(library options, oracle options) with tight or 3-sigma tile rectangles."""
+    return gs.default_options(tight_lists=int(tight)), (O.DEFAULT_OPT if tight else O.LOOSE_OPT)
+
+
+def check_projection(gs, ctx, gd, cams, poses, tight=True):
     og = O.Gaussians.from_dict(gd)
     g = gs.Gaussians.from_numpy(gd)
-    recs, aux, counts = gs.gs_project(ctx, g, dev(poses.reshape(-1, 12)), cams)
+    opt_g, opt_o = opts(gs, tight)
+    recs, aux, counts = gs.gs_project(ctx, g, dev(poses.reshape(-1, 12)), cams, opt_g)
     recs, aux, counts = recs.cpu().numpy(), aux.cpu().numpy(), counts.cpu().numpy()
     n = og.n
     for c, cam in enumerate(cams):
-        f, i = O.project32(og, f32pose(poses[c]), cam)
+        f, i = O.project32(og, f32pose(poses[c]), cam, opt_o)
         sl = slice(c * n, (c + 1) * n)
         vis = i[:, 0] == 1
         np.testing.assert_array_equal(counts[sl] > 0, vis)
@@ -126,43 +132,48 @@ def check_projection(gs, ctx, gd, cams, poses):
     return int(counts.sum())
 
 
+@pytest.mark.parametrize("tight", [1, 0])
 @pytest.mark.parametrize("case", list(CASES))
-def test_projection_bit_exact(gs, ctx, case):
+def test_projection_bit_exact(gs, ctx, case, tight):
     gd, cams = CASES[case]()
     poses = rand_poses(np.random.default_rng(1), len(cams))
-    assert check_projection(gs, ctx, gd, cams, poses) > 0
+    assert check_projection(gs, ctx, gd, cams, poses, tight) > 0
 
 
-def test_projection_bit_exact_room_full_size(gs, ctx):
+@pytest.mark.parametrize("tight", [1, 0])
+def test_projection_bit_exact_room_full_size(gs, ctx, tight):
     c = synth.room_150k()
     poses = rand_poses(np.random.default_rng(2), 8, 10.0, 0.15)
-    assert check_projection(gs, ctx, c["gaussians"], c["src_cams"], poses) > 0
+    assert check_projection(gs, ctx, c["gaussians"], c["src_cams"], poses, tight) > 0
 
 
 # ----------------------------------------------------------------- binning
-def check_binning(gs, ctx, gd, cams, poses):
+def check_binning(gs, ctx, gd, cams, poses, tight=True):
     og = O.Gaussians.from_dict(gd)
     g = gs.Gaussians.from_numpy(gd)
-    recs, _, counts = gs.gs_project(ctx, g, dev(poses.reshape(-1, 12)), cams, with_aux=False)
+    opt_g, opt_o = opts(gs, tight)
+    recs, _, counts = gs.gs_project(ctx, g, dev(poses.reshape(-1, 12)), cams, opt_g, with_aux=False)
     keys, vals, ranges = gs.gs_bin(ctx, recs, counts, cams, g.n)
-    ok, ov, orng = O.bin_tiles(og, np.stack([f32pose(p) for p in poses]), cams)
+    ok, ov, orng = O.bin_tiles(og, np.stack([f32pose(p) for p in poses]), cams, opt_o)
     np.testing.assert_array_equal(keys.cpu().numpy().view(np.uint64), ok)
     np.testing.assert_array_equal(vals.cpu().numpy().view(np.uint32), ov)
     np.testing.assert_array_equal(ranges.cpu().numpy().astype(np.int64), orng)
     return len(ok)
 
 
+@pytest.mark.parametrize("tight", [1, 0])
 @pytest.mark.parametrize("case", list(CASES))
-def test_binning_bit_exact(gs, ctx, case):
+def test_binning_bit_exact(gs, ctx, case, tight):
     gd, cams = CASES[case]()
     poses = rand_poses(np.random.default_rng(3), len(cams))
-    assert check_binning(gs, ctx, gd, cams, poses) > 0
+    assert check_binning(gs, ctx, gd, cams, poses, tight) > 0
 
 
-def test_binning_bit_exact_room_full_size(gs, ctx):
+@pytest.mark.parametrize("tight", [1, 0])
+def test_binning_bit_exact_room_full_size(gs, ctx, tight):
     gd, cams = room_case(2)
     poses = rand_poses(np.random.default_rng(4), 2, 10.0, 0.15)
-    assert check_binning(gs, ctx, gd, cams, poses) > 100_000
+    assert check_binning(gs, ctx, gd, cams, poses, tight) > 100_000
 
 
 def dense_case(n):
@@ -173,15 +184,17 @@ def dense_case(n):
     return c["gaussians"], c["cams"]
 
 
+@pytest.mark.parametrize("tight", [1, 0])
 @pytest.mark.parametrize("n", [400, 3000])
-def test_binning_long_tile_lists(gs, ctx, n):
+def test_binning_long_tile_lists(gs, ctx, n, tight):
     gd, cams = dense_case(n)
     poses = rand_poses(np.random.default_rng(5), len(cams), 1.0, 0.005)
-    assert check_binning(gs, ctx, gd, cams, poses) > 0
-    _, _, ranges = O.bin_tiles(O.Gaussians.from_dict(gd), np.stack([f32pose(p) for p in poses]), cams)
+    assert check_binning(gs, ctx, gd, cams, poses, tight) > 0
+    _, opt_o = opts(gs, tight)
+    _, _, ranges = O.bin_tiles(O.Gaussians.from_dict(gd), np.stack([f32pose(p) for p in poses]), cams, opt_o)
     longest = int((ranges[:, 1] - ranges[:, 0]).max())
     assert longest > (256 if n == 400 else 512), longest
-    check_render(gs, ctx, gd, cams, poses)
+    check_render(gs, ctx, gd, cams, poses, *reversed(opts(gs, tight)))
 
 
 def test_binning_and_render_large_image(gs, ctx):
@@ -207,6 +220,7 @@ def test_binning_empty(gs, ctx):
 
 # ----------------------------------------------------------------- render
 def check_render(gs, ctx, gd, cams, poses, opt_o=O.DEFAULT_OPT, opt_g=None):
+    # opt_g None: the library defaults, whose tight rectangles DEFAULT_OPT mirrors
     og = O.Gaussians.from_dict(gd)
     g = gs.Gaussians.from_numpy(gd)
     out = gs.gs_render(ctx, g, dev(poses.reshape(-1, 12)), cams, opt_g)
@@ -226,10 +240,12 @@ def check_render(gs, ctx, gd, cams, poses, opt_o=O.DEFAULT_OPT, opt_g=None):
     return out
 
 
+@pytest.mark.parametrize("tight", [1, 0])
 @pytest.mark.parametrize("case", list(CASES))
-def test_render_parity(gs, ctx, case):
+def test_render_parity(gs, ctx, case, tight):
     gd, cams = CASES[case]()
-    check_render(gs, ctx, gd, cams, rand_poses(np.random.default_rng(5), len(cams)))
+    opt_g, opt_o = opts(gs, tight)
+    check_render(gs, ctx, gd, cams, rand_poses(np.random.default_rng(5), len(cams)), opt_o, opt_g)
 
 
 def test_render_parity_smooth_mode(gs, ctx):
@@ -238,9 +254,11 @@ def test_render_parity_smooth_mode(gs, ctx):
                  gs.default_options(alpha_min=0.0, alpha_max=1.0, t_min=0.0, smooth=1))
 
 
-def test_render_parity_room_full_size(gs, ctx):
+@pytest.mark.parametrize("tight", [1, 0])
+def test_render_parity_room_full_size(gs, ctx, tight):
     gd, cams = room_case(2)
-    check_render(gs, ctx, gd, cams, rand_poses(np.random.default_rng(7), 2, 10.0, 0.15))
+    opt_g, opt_o = opts(gs, tight)
+    check_render(gs, ctx, gd, cams, rand_poses(np.random.default_rng(7), 2, 10.0, 0.15), opt_o, opt_g)
 
 
 def test_render_empty_and_single(gs, ctx):
@@ -429,12 +447,15 @@ def _problem(gs, n, W, H, f, n_src, n_tgt, seed):
     return src, tgt, sv, tv
 
 
-def test_batched_registration_equals_separate_calls(gs, ctx):
+@pytest.mark.parametrize("sched", [1, 4])
+def test_batched_registration_equals_separate_calls(gs, ctx, sched):
     # uneven problems: submap sizes, keyframe counts per direction, image
-    # sizes (ragged tiles) all differ; one batch vs one call per problem
+    # sizes (ragged tiles) all differ; one batch (one CTA per tile, or the
+    # persistent kernels' queue over every problem's tiles, longest first)
+    # vs one call per problem
     probs = [_problem(gs, 900, 96, 64, 80.0, 1, 2, 31), _problem(gs, 300, 64, 40, 50.0, 2, 0, 32),
              _problem(gs, 1500, 120, 90, 100.0, 2, 1, 33)]
-    T, conf, eps = gs.gs_register_batch(ctx, probs, 15)
+    T, conf, eps = gs.gs_register_batch(ctx, probs, 15, gs.default_options(tile_schedule=sched))
     off = 0
     for i, (src, tgt, sv, tv) in enumerate(probs):
         Ti, ci, ei, _ = gs.gs_register(ctx, src, tgt, sv, tv, 15)
@@ -492,34 +513,83 @@ def test_registration_room_full_size_trajectory_matches_oracle(gs, ctx):
     np.testing.assert_allclose(eps, [ep, eq], rtol=1e-3)
 
 
-def test_registration_room_full_size_converged_keyframes(gs, ctx):
-    # the room workload as benchmarked (8+8 keyframes, 100 iterations, both
-    # directions; keyframes rendered on the device).  With a 10 deg / 15 cm
-    # offset only some keyframes lie inside the photometric basin (the oracle
-    # shows the same); every keyframe whose residual fell to 1 % of its
-    # start must carry the ground truth, and they dominate the Eq. 7 fusion.
-    # Near the basin floor a keyframe's pose error follows its residual
-    # (about 2.5 deg per unit: 1.5e-3 -> 0.0014 deg, 4.9e-3 -> 0.012 deg), so
-    # at the 1 % cut the bound is 0.02 deg / 1 mm (0.27 px at 600 px focal)
+@pytest.fixture(scope="module")
+def room_edge(gs, ctx):
+    """The benchmarked edge (room, 8 + 8 keyframes of 1200x680, 100
+    iterations, both directions) registered on the GPU with keyframe images
+    rendered by the oracle (FP32-rounded), so both sides start from the same
+    inputs.  Returns the case, the oracle submaps and images, and the GPU
+    result (T, confidence, residuals, per-keyframe estimates)."""
+    import os
+    O.set_threads(os.cpu_count() or 1)
     c = synth.room_150k()
+    og = O.Gaussians.from_dict(c["gaussians"])
+    oq = O.transform(og, c["T_gt"])
     src = gs.Gaussians.from_numpy(c["gaussians"])
-    tgt = gs.gs_transform(ctx, src, c["T_gt"])
-    I = dev(np.stack([np.eye(3, 4)] * 8).reshape(8, 12))
-    rs = gs.gs_render(ctx, src, I, c["src_cams"])
-    rt = gs.gs_render(ctx, tgt, I, c["tgt_cams"])
-    sv = list(zip(c["src_cams"], [x.contiguous() for x in gs.split_views(rs["rgb"], c["src_cams"], 3)],
-                  [x.contiguous() for x in gs.split_views(rs["depth"], c["src_cams"], 1)]))
-    tv = list(zip(c["tgt_cams"], [x.contiguous() for x in gs.split_views(rt["rgb"], c["tgt_cams"], 3)],
-                  [x.contiguous() for x in gs.split_views(rt["depth"], c["tgt_cams"], 1)]))
-    T, conf, eps, est = gs.gs_register(ctx, src, tgt, sv, tv, 100)
+    tgt = gs.Gaussians(*[dev(a) for a in (oq.means4, oq.log_scales4, oq.quats4, oq.logits, oq.rgb4)])
+    ims_p = [O.render(og, np.eye(3, 4), cam) for cam in c["src_cams"]]
+    ims_q = [O.render(oq, np.eye(3, 4), cam) for cam in c["tgt_cams"]]
+    f32 = lambda r: (r["rgb"].astype(np.float32), r["depth"].astype(np.float32))
+    ims_p, ims_q = [f32(r) for r in ims_p], [f32(r) for r in ims_q]
+    sv = [(cam, dev(i[0]), dev(i[1])) for cam, i in zip(c["src_cams"], ims_p)]
+    tv = [(cam, dev(i[0]), dev(i[1])) for cam, i in zip(c["tgt_cams"], ims_q)]
+    res = gs.gs_register(ctx, src, tgt, sv, tv, 100)
+    return dict(c=c, og=og, oq=oq, ims_p=ims_p, ims_q=ims_q, res=res)
+
+
+def test_registration_room_full_size_100_iterations_matches_oracle(gs, ctx, room_edge):
+    # The north-star bar on the benchmarked configuration: for the keyframe
+    # of each direction whose GPU residual fell the most (a converging
+    # problem), the oracle runs the same 100 iterations on the same inputs;
+    # the recovered transforms agree within 0.5 mm / 0.01 deg, and the GPU
+    # lands on the ground truth within the same bar plus the oracle's own
+    # distance to it.  The GPU's residual is the oracle's loss at the GPU's
+    # final pose (1e-3 relative; near the optimum the L1 residual is steep in
+    # the remaining pose error, so the two runs' residuals are not compared
+    # with each other).
+    c, res = room_edge["c"], room_edge["res"]
+    T, conf, eps, est = res
     assert np.all(np.isfinite(eps)) and conf > 0
-    conv = np.nonzero(eps < 5e-3)[0]
+    for side in (0, 1):
+        ks = np.arange(8) + 8 * side
+        k = int(ks[np.argmin(eps[ks])])
+        j = k - 8 * side
+        if side == 0:  # keyframe of P localised in Q (estimate X^-1)
+            moving, cam, ims = room_edge["oq"], c["src_cams"][j], room_edge["ims_p"][j]
+            X, e_o, _ = O.register_view(moving, cam, *ims, 100)
+            want, pose_g = O.invert(X), O.invert(est[k])
+        else:          # keyframe of Q localised in P
+            moving, cam, ims = room_edge["og"], c["tgt_cams"][j], room_edge["ims_q"][j]
+            want, e_o, _ = O.register_view(moving, cam, *ims, 100)
+            pose_g = est[k]
+        ang, dt = rot_err(est[k], want)
+        assert ang < 0.01 and dt < 5e-4, (k, ang, dt, eps[k], e_o)
+        r = O.render(moving, f32pose(pose_g), cam)
+        L, _, _ = O.loss(r["rgb"], r["depth"], *ims)
+        assert eps[k] == pytest.approx(L, rel=1e-3, abs=1e-6), (k, eps[k], L, e_o)
+        a_o, d_o = rot_err(want, c["T_gt"])
+        a_g, d_g = rot_err(est[k], c["T_gt"])
+        assert a_g < a_o + 0.01 and d_g < d_o + 5e-4, (k, a_g, a_o, d_g, d_o)
+
+
+def test_registration_room_full_size_converged_keyframes(gs, ctx, room_edge):
+    # With a 10 deg / 15 cm offset only some keyframes lie inside the
+    # photometric basin (the oracle shows the same).  A keyframe counts as
+    # converged when its residual (the per-pixel L1 mean) fell below 2e-3,
+    # half a grey level of 8-bit colour; each such keyframe carries the
+    # ground truth within the bar, and the Eq. 7 fusion of the GPU's
+    # estimates with its residuals is the oracle's fusion of the same
+    # numbers (1e-9).
+    c, (T, conf, eps, est) = room_edge["c"], room_edge["res"]
+    conv = np.nonzero(eps < 2e-3)[0]
     assert len(conv) >= 2, eps
     for k in conv:
         ang, dt = rot_err(est[k], c["T_gt"])
-        assert ang < 0.02 and dt < 1e-3, (k, ang, dt, eps[k])
-    ang, dt = rot_err(T, c["T_gt"])
-    assert ang < 0.5 and dt < 0.01, (ang, dt)
+        assert ang < 0.01 and dt < 5e-4, (k, ang, dt, eps[k])
+    rev = [True] * 8 + [False] * 8
+    Tf, cf = O.fuse(np.stack([O.invert(E) if r else E for E, r in zip(est, rev)]), eps, rev)
+    np.testing.assert_allclose(T, Tf, atol=1e-9)
+    assert conf == pytest.approx(cf, rel=1e-9)
 
 
 def test_outgrown_tile_lists_are_redone(gs, ctx):
@@ -561,8 +631,9 @@ def test_transform_batch_equals_single_transforms(gs, ctx):
 
 def test_tile_schedules_give_identical_registrations(gs, ctx):
     # two full-size room keyframes (3225 tiles each): natural tile order,
-    # longest lists first, the autotuner's pick, tight or 3-sigma tile lists
-    # give the same result
+    # longest lists first, either of them through the persistent kernels'
+    # work queue, the autotuner's pick, tight or 3-sigma tile lists give the
+    # same result
     c = synth.room_150k()
     og = O.Gaussians.from_dict(c["gaussians"])
     g = gs.Gaussians.from_numpy(c["gaussians"])
@@ -570,7 +641,7 @@ def test_tile_schedules_give_identical_registrations(gs, ctx):
     for cam in c["src_cams"][:2]:
         tr = O.render(og, c["T_gt"], cam)
         views.append((cam, dev(tr["rgb"].astype(np.float32)), dev(tr["depth"].astype(np.float32))))
-    out = [gs.gs_register(ctx, g, g, [], views, 10, gs.default_options(tile_schedule=k)) for k in (1, 2, 0, 0)]
+    out = [gs.gs_register(ctx, g, g, [], views, 10, gs.default_options(tile_schedule=k)) for k in (1, 2, 3, 4, 0, 0)]
     for o in out[1:]:
         np.testing.assert_array_equal(o[0], out[0][0])
         np.testing.assert_array_equal(o[2], out[0][2])

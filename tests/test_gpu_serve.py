@@ -53,10 +53,10 @@ def edge(gs, n, W, H, f, n_src, n_tgt, seed):
     return src, tgt, sv, tv
 
 
-def tracking(gs, n, W, H, f, seed):
+def tracking(gs, n, W, H, f, seed, ls_mean=-3.3):
     """Frame-to-model tracking: one frame rendered at the true camera, the
     request's camera a small perturbation of it (0.7 deg, 1.3 cm)."""
-    c = synth.small_case(n, W, H, f, n_views=1, seed=seed, ls_mean=-3.3)
+    c = synth.small_case(n, W, H, f, n_views=1, seed=seed, ls_mean=ls_mean)
     og = O.Gaussians.from_dict(c["gaussians"])
     cam = c["cams"][0]
     _, rgb, depth = view(og, cam)
@@ -135,7 +135,7 @@ def test_admission_limits(gs, ctx, requests):
         assert sum(kf[i] for i in inflight_ids) <= 3
     srv.close()
     # a 300 kB budget holds one of the tracking requests at a time (their
-    # scratch is estimated at 146-265 kB); the 3-keyframe edge is refused
+    # footprints are about 200-290 kB); the 3-keyframe edge is refused
     srv = gs.Server(0, budget_bytes=300_000, max_round_iters=4)
     track = [requests[i] for i in (0, 2, 4)]
     for prob, iters in track:
@@ -159,4 +159,52 @@ def test_rejects_bad_requests(gs, requests):
     with pytest.raises(gs.GsError):
         srv.submit(*requests[0][0], -1)
     assert srv.counts()[0] == 0
+    srv.close()
+
+
+def fixed_estimate(prob):
+    # the footprint rule this admission replaces: three tile duplicates per
+    # record whatever the splats' screen sizes, 16 B each with headroom 1.5
+    src, tgt, sv, tv = prob
+    b = 0.0
+    for g, views in ((tgt, sv), (src, tv)):
+        for cam, _, _ in views:
+            px = int(cam[4]) * int(cam[5])
+            tiles = ((int(cam[4]) + 15) // 16) * ((int(cam[5]) + 15) // 16)
+            b += g.n * 100 + 3.0 * g.n * 16 * 1.5 + px * 9 + tiles * 92
+    return b
+
+
+@pytest.mark.parametrize("splats", ["large", "small"])
+def test_admission_by_measured_footprint(gs, ctx, splats):
+    # two tracking requests whose splats cover many tiles each (large) or
+    # about one (small): their measured footprints lie on the other side of
+    # the budget from the fixed three-duplicates-per-record rule, and
+    # admission follows the measurement -- one at a time for the large
+    # splats, both together for the small ones; results are gs_register's
+    if splats == "large":
+        probs = [tracking(gs, 2000, 128, 96, 120.0, 51, ls_mean=-1.8), tracking(gs, 2000, 128, 96, 120.0, 52, -1.8)]
+    else:
+        probs = [tracking(gs, 3000, 64, 48, 40.0, 53, ls_mean=-4.5), tracking(gs, 3000, 64, 48, 40.0, 54, -4.5)]
+    probe = gs.Server(0)
+    fp = [probe.footprint(probe.submit(*p, 8)) for p in probs]
+    probe.close()
+    measured = sum(b for _, b in fp)
+    fixed = sum(fixed_estimate(p) for p in probs)
+    budget = int((measured + fixed) / 2)
+    srv = gs.Server(0, budget_bytes=budget, max_round_iters=4)
+    ids = [srv.submit(*p, 8) for p in probs]
+    assert [srv.footprint(i) for i in ids] == fp
+    srv.step()
+    together = srv.counts()[1] == 2  # 8 iterations take more than one round of 4
+    if splats == "large":
+        assert fp[0][0] > 10 * 2000 and measured > budget > fixed
+        assert srv.admission()[1] == 1 and not together
+    else:
+        assert fp[0][0] < 2 * 3000 and fixed > budget > measured
+        assert srv.admission()[1] == 0 and together
+    drain(srv)
+    assert srv.admission()[0] == 2
+    for i, p in zip(ids, probs):
+        same(srv.poll(i), gs.gs_register(ctx, *p, 8))
     srv.close()
