@@ -50,7 +50,7 @@ FWD_FLOPS_CONTRIB = 41.0
 BWD_FLOPS_CONTRIB = 64.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
 # the current kernel; None while the kernel has changed since the capture
-BWD_TRAFFIC_BYTES = None
+BWD_TRAFFIC_BYTES = 185.76128e6
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -723,7 +723,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--room-only", action="store_true",
                     help="the room line only (no batched and serving records)")
-    ap.add_argument("--serve-rate", type=float, default=12.0,
+    ap.add_argument("--serve-rate", type=float, default=17.0,
                     help="arrivals per second of the serving record in the default line")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--workload", default="room_150k", choices=["room_150k", "batched_32", "serve", "overlap"],

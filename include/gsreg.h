@@ -268,6 +268,37 @@ gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const flo
                                const float *d_depth, const float *d_alpha, const float *pivots,
                                float *pose_grad, const gs_gaussian_grads_t *grads, gs_stream_t stream);
 
+/* A forward pass kept for its adjoint (the saved state of the 3DGS
+ * rasteriser the paper renders with, Sec. 3.2): gs_render_saved renders like
+ * gs_render and keeps the projected records, their camera-frame means and
+ * covariances, the sorted tile lists and the per-pixel final transmittance
+ * and last contributor; gs_render_backward_saved then runs the adjoint from
+ * them -- no second projection or binning, and no host synchronisation.
+ * The saved state lives in two device blocks allocated stream-ordered
+ * (cudaMallocAsync on `stream`, outside the context's scratch budget) and
+ * freed by gs_saved_destroy (cudaFreeAsync on its stream).  The submap's
+ * arrays and the options are read again by the adjoint: keep the arrays
+ * unchanged until then.  gs_render_saved synchronises `stream` like
+ * gs_render; rgb, depth, alpha may be NULL. */
+typedef struct gs_saved gs_saved_t;
+
+gs_status_t gs_render_saved(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams,
+                            int n_cams, const gs_options_t *opt, float *rgb, float *depth, float *alpha,
+                            gs_saved_t **saved, gs_stream_t stream);
+
+/* Device pointers of the saved per-pixel state ([sum HW] each, owned by
+ * the saved forward): final transmittance and last contributor. */
+gs_status_t gs_saved_outputs(const gs_saved_t *saved, float **t_final, int32_t **last);
+
+/* gs_render_backward from a saved forward (same cotangents, pivots and
+ * outputs); stream-ordered, returns once the work is enqueued. */
+gs_status_t gs_render_backward_saved(gs_ctx_t *ctx, const gs_saved_t *saved, const float *d_rgb,
+                                     const float *d_depth, const float *d_alpha, const float *pivots,
+                                     float *pose_grad, const gs_gaussian_grads_t *grads, gs_stream_t stream);
+
+/* Frees a saved forward (stream-ordered after the work already on `stream`). */
+gs_status_t gs_saved_destroy(gs_saved_t *saved, gs_stream_t stream);
+
 /* L1 colour + L1 depth loss per view (Sec. 3.2: L = L_col + L_depth):
  * L_v = mean over 3HW of |I^ - I| + mean over HW of |D^ - D|, and its
  * gradients sign(.)/(3HW), sign(.)/(HW) (sign(0) = 0).  Images are

@@ -14,27 +14,26 @@ class Rasterize(torch.autograd.Function):
     """(means4, log_scales4, quats4, logits, rgb4, twist) -> (rgb, depth,
     alpha), concatenated per camera as gs_render returns them.  ``twist``
     [n_cams, 6] is the left perturbation (w, v) of each pose about its
-    pivot, evaluated at zero: it must be zero, and its gradient is the pose
-    gradient of the registration."""
+    pivot, evaluated at zero: its value is not read (the render is taken at
+    the given poses), and its gradient is the pose gradient of the
+    registration.  The forward keeps its projection and tile lists
+    (gs_render_saved), so the backward neither projects nor bins again."""
 
     @staticmethod
     def forward(fctx, gsctx, cams, poses, pivots, means4, log_scales4, quats4, logits, rgb4, twist):
-        if torch.any(twist != 0):
-            raise ValueError("the twist input is evaluated at zero")
         g = gsreg.Gaussians(means4.contiguous(), log_scales4.contiguous(), quats4.contiguous(), logits.contiguous(),
                             rgb4.contiguous())
-        out = gsreg.gs_render(gsctx, g, poses, cams)
-        fctx.gsctx, fctx.cams = gsctx, cams
-        fctx.save_for_backward(g.means4, g.log_scales4, g.quats4, g.logits, g.rgb4, poses, pivots, out["t_final"],
-                               out["last"])
+        out, saved = gsreg.gs_render_saved(gsctx, g, poses, cams)
+        fctx.gsctx, fctx.saved = gsctx, saved
+        fctx.save_for_backward(pivots)
         return out["rgb"], out["depth"], out["alpha"]
 
     @staticmethod
     def backward(fctx, d_rgb, d_depth, d_alpha):
-        m, s, q, lg, c, poses, pivots, tf, last = fctx.saved_tensors
-        g = gsreg.Gaussians(m, s, q, lg, c)
-        pg, gr = gsreg.gs_render_backward(fctx.gsctx, g, poses, fctx.cams, tf, last, d_rgb.contiguous(),
-                                          d_depth.contiguous(), d_alpha.contiguous(), pivots, params=True)
+        (pivots,) = fctx.saved_tensors
+        pg, gr = gsreg.gs_render_backward_saved(fctx.gsctx, fctx.saved, d_rgb.contiguous(), d_depth.contiguous(),
+                                                d_alpha.contiguous(), pivots, params=True)
+        fctx.saved.close()
         return (None, None, None, None, gr["means4"], gr["log_scales4"], gr["quats4"], gr["logits"], gr["rgb4"], pg)
 
 

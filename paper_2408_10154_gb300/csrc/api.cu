@@ -397,8 +397,11 @@ gs_status_t alloc_sort(gs_ctx *ctx, uint64_t want, Pipe &p)
 
 int run_bin(const gsl::BinArgs &b, cudaStream_t s) { return gsl::bin_seg(b, s); }
 
+// counts = false: the per-record tile counts are not written (the
+// segmented lists read the records' seg_list entries; only the scan for the
+// duplicate total at the initial poses reads the counts)
 gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, const float *pose32,
-                              const gs_options_t *o)
+                              const gs_options_t *o, bool counts = true)
 {
     gsl::ProjectArgs a{};
     a.vps = D.vps;
@@ -411,7 +414,7 @@ gsl::ProjectArgs project_args(const Plan &P, const DevPlan &D, const Pipe &p, co
     a.smooth = o->smooth;
     a.rec = p.rec;
     a.aux = p.aux;
-    a.counts = p.counts;
+    a.counts = counts ? p.counts : nullptr;
     a.flags = p.flags;
     // tight lists need a normal alpha_min (the contract's logarithm)
     a.tight = o->tight_lists != 0 && o->alpha_min >= FLT_MIN && !o->smooth;
@@ -909,30 +912,19 @@ gs_status_t gs_render(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses
     return GS_OK;
 }
 
-gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses,
-                               const gs_camera_t *cams, int n_cams, const gs_options_t *opt,
-                               const float *t_final, const int32_t *last, const float *d_rgb,
-                               const float *d_depth, const float *d_alpha, const float *pivots, float *pose_grad,
-                               const gs_gaussian_grads_t *grads, gs_stream_t stream)
+}  // extern "C"
+
+namespace {
+
+// The adjoint of one forward pass whose projection (p.rec, p.aux), tile
+// lists (p.vals[cur], p.ranges, p.ndups, capacity p.cap) and per-pixel state
+// (t_final, last) are in place: screen-space adjoint per tile, the pose
+// twist per camera, and optionally every Gaussian parameter.
+gs_status_t backward_core(gs_ctx *ctx, const Plan &P, const DevPlan &D, Pipe &p, int cur, const gs_gaussians_t *g,
+                          const float *poses, const gs_options_t *opt, const float *t_final, const int32_t *last,
+                          const float *d_rgb, const float *d_depth, const float *d_alpha, const float *pivots,
+                          float *pose_grad, const gs_gaussian_grads_t *grads, bool full, cudaStream_t s)
 {
-    GS_TRY(check_common(ctx, g, cams, n_cams, opt));
-    if (!poses || !t_final || !last)
-        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward: null poses or forward state");
-    const bool full = grads && (grads->means || grads->log_scales || grads->quats || grads->opacity_logits ||
-                                grads->rgb);
-    if (full && ((grads->means && !aligned16(grads->means)) || (grads->log_scales && !aligned16(grads->log_scales)) ||
-                 (grads->quats && !aligned16(grads->quats)) || (grads->rgb && !aligned16(grads->rgb))))
-        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward: gradient float4 arrays must be 16-byte aligned");
-    DeviceGuard dg(ctx->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    Plan P = plan_for(g, cams, n_cams);
-    GS_TRY(finalize(ctx, P));
-    DevPlan D;
-    GS_TRY(upload_plan(ctx, P, D, s));
-    Pipe p;
-    GS_TRY(alloc_pipe(ctx, P, true, p));
-    int cur = 0;
-    GS_TRY(project_and_bin(ctx, P, D, p, poses, opt, s, &cur, nullptr));
     gsl::RasterArgs r = raster_args(P, D, p, cur, opt);
     r.t_final = (float *)t_final;
     r.last = (int32_t *)last;
@@ -964,7 +956,7 @@ gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const flo
         GS_TRY(wsT(ctx, S_RK1, p.cap, &rk[1]));
         GS_TRY(wsT(ctx, S_RP0, p.cap, &rp[0]));
         GS_TRY(wsT(ctx, S_RP1, p.cap, &rp[1]));
-        GS_TRY(wsT(ctx, S_RRANGES, (size_t)p.n_records, &rr));
+        GS_TRY(wsT(ctx, S_RRANGES, (size_t)std::max<uint64_t>(P.n_records, 1), &rr));
         gsl::ParamArgs pa{};
         pa.vps = D.vps;
         pa.n_vps = nv;
@@ -998,10 +990,270 @@ gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const flo
         ++gsl::g_launches;
     }
     GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+bool wants_params(const gs_gaussian_grads_t *grads)
+{
+    return grads && (grads->means || grads->log_scales || grads->quats || grads->opacity_logits || grads->rgb);
+}
+
+gs_status_t check_grads(gs_ctx *ctx, const gs_gaussian_grads_t *grads)
+{
+    if (wants_params(grads) &&
+        ((grads->means && !aligned16(grads->means)) || (grads->log_scales && !aligned16(grads->log_scales)) ||
+         (grads->quats && !aligned16(grads->quats)) || (grads->rgb && !aligned16(grads->rgb))))
+        return fail(ctx, GS_ERR_INVALID_ARG, "gradient float4 arrays must be 16-byte aligned");
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status_t gs_render_backward(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses,
+                               const gs_camera_t *cams, int n_cams, const gs_options_t *opt,
+                               const float *t_final, const int32_t *last, const float *d_rgb,
+                               const float *d_depth, const float *d_alpha, const float *pivots, float *pose_grad,
+                               const gs_gaussian_grads_t *grads, gs_stream_t stream)
+{
+    GS_TRY(check_common(ctx, g, cams, n_cams, opt));
+    if (!poses || !t_final || !last)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward: null poses or forward state");
+    GS_TRY(check_grads(ctx, grads));
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan P = plan_for(g, cams, n_cams);
+    GS_TRY(finalize(ctx, P));
+    DevPlan D;
+    GS_TRY(upload_plan(ctx, P, D, s));
+    Pipe p;
+    GS_TRY(alloc_pipe(ctx, P, true, p));
+    int cur = 0;
+    GS_TRY(project_and_bin(ctx, P, D, p, poses, opt, s, &cur, nullptr));
+    GS_TRY(backward_core(ctx, P, D, p, cur, g, poses, opt, t_final, last, d_rgb, d_depth, d_alpha, pivots, pose_grad,
+                         grads, wants_params(grads), s));
     int flags = 0;
     GS_TRY(read_flags(ctx, p, s, &flags));
     if (flags & gsk::kFlagTimeout)
         return fail(ctx, GS_ERR_TIMEOUT, "a sort pass gave up waiting for an earlier tile");
+    return GS_OK;
+}
+
+}  // extern "C"
+
+// A forward pass kept for its adjoint: the plan (host), and in two
+// stream-ordered device blocks the plan tables, the pose copy, the records
+// and their auxiliary camera-frame mean and covariance, the counts, tile
+// ranges, the duplicate count, per-pixel final transmittance and last
+// contributor (block 1, sized from the plan), and the sorted tile lists
+// (block 2, sized after counting).
+struct gs_saved {
+    int device = 0;
+    Plan P;
+    DevPlan D;
+    gs_gaussians_t g{};
+    gs_options_t opt{};
+    void *blk[2] = {nullptr, nullptr};
+    float *pose32 = nullptr, *t_final = nullptr;
+    float4 *rec = nullptr, *aux = nullptr;
+    int32_t *counts = nullptr, *last = nullptr;
+    uint2 *ranges = nullptr;
+    uint32_t *vals = nullptr, *ndups = nullptr;
+    uint32_t cap = 0;
+};
+
+namespace {
+
+// byte offsets of 256-aligned pieces in one block
+struct Layout {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t o = off;
+        off += ((bytes ? bytes : 1) + 255) & ~(size_t)255;
+        return o;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+gs_status_t gs_render_saved(gs_ctx_t *ctx, const gs_gaussians_t *g, const float *poses, const gs_camera_t *cams,
+                            int n_cams, const gs_options_t *opt, float *rgb, float *depth, float *alpha,
+                            gs_saved_t **saved, gs_stream_t stream)
+{
+    GS_TRY(check_common(ctx, g, cams, n_cams, opt));
+    if (!poses || !saved)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_saved: null poses or saved");
+    *saved = nullptr;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gs_saved *sv = new gs_saved();
+    sv->device = ctx->device;
+    sv->g = *g;
+    sv->opt = *opt;
+    sv->P = plan_for(g, cams, n_cams);
+    Plan &P = sv->P;
+    const gs_status_t fs = finalize(ctx, P);
+    if (fs != GS_OK) {
+        delete sv;
+        return fs;
+    }
+    const size_t nv = P.vps.size(), R = std::max<uint64_t>(P.n_records, 1), T = std::max<uint64_t>(P.n_tiles, 1),
+                 px = (size_t)std::max<int64_t>(P.n_pix, 1);
+    Layout L;
+    const size_t o_vps = L.take(sizeof(VpDesc) * nv), o_grp = L.take(sizeof(GroupDesc) * P.groups.size()),
+                 o_tvp = L.take(sizeof(uint32_t) * P.tile_vp.size()), o_pose = L.take(sizeof(float) * 12 * nv),
+                 o_rec = L.take(sizeof(float4) * 3 * R), o_aux = L.take(sizeof(float4) * 2 * R),
+                 o_cnt = L.take(sizeof(int32_t) * R), o_rng = L.take(sizeof(uint2) * T),
+                 o_nd = L.take(sizeof(uint32_t) * 4), o_tf = L.take(sizeof(float) * px),
+                 o_last = L.take(sizeof(int32_t) * px);
+    auto cleanup = [&](gs_status_t st) {
+        for (void *b : sv->blk)
+            if (b)
+                cudaFreeAsync(b, s);
+        delete sv;
+        return st;
+    };
+    if (cudaMallocAsync(&sv->blk[0], L.off, s) != cudaSuccess) {
+        cudaGetLastError();
+        sv->blk[0] = nullptr;
+        return cleanup(fail(ctx, GS_ERR_OOM, "gs_render_saved: cudaMallocAsync failed"));
+    }
+    char *b0 = (char *)sv->blk[0];
+    sv->D.vps = (VpDesc *)(b0 + o_vps);
+    sv->D.groups = (GroupDesc *)(b0 + o_grp);
+    sv->D.tile_vp = (uint32_t *)(b0 + o_tvp);
+    sv->pose32 = (float *)(b0 + o_pose);
+    sv->rec = (float4 *)(b0 + o_rec);
+    sv->aux = (float4 *)(b0 + o_aux);
+    sv->counts = (int32_t *)(b0 + o_cnt);
+    sv->ranges = (uint2 *)(b0 + o_rng);
+    sv->ndups = (uint32_t *)(b0 + o_nd);
+    sv->t_final = (float *)(b0 + o_tf);
+    sv->last = (int32_t *)(b0 + o_last);
+    auto copy = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind k) {
+        return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, k, s) == cudaSuccess;
+    };
+    if (!copy(sv->D.vps, P.vps.data(), sizeof(VpDesc) * nv, cudaMemcpyHostToDevice) ||
+        !copy(sv->D.groups, P.groups.data(), sizeof(GroupDesc) * P.groups.size(), cudaMemcpyHostToDevice) ||
+        !copy(sv->D.tile_vp, P.tile_vp.data(), sizeof(uint32_t) * P.tile_vp.size(), cudaMemcpyHostToDevice) ||
+        !copy(sv->pose32, poses, sizeof(float) * 12 * nv, cudaMemcpyDeviceToDevice))
+        return cleanup(fail(ctx, GS_ERR_CUDA, "gs_render_saved: copy of the plan"));
+    // projection into the saved block, list building scratch in the arena
+    Pipe p;
+    p.rec = sv->rec;
+    p.aux = sv->aux;
+    p.counts = sv->counts;
+    p.ranges = sv->ranges;
+    p.ndups = sv->ndups;
+    p.n_records = R;
+    gs_status_t st = wsT(ctx, S_PARTIALS, gsl::scan_partials(R), &p.partials);
+    if (st == GS_OK)
+        st = wsT(ctx, S_FLAGS, 4, &p.flags);
+    if (st == GS_OK)
+        st = alloc_seg(ctx, P, p);
+    if (st != GS_OK)
+        return cleanup(st);
+    if (cudaMemsetAsync(p.flags, 0, sizeof(int), s) != cudaSuccess)
+        return cleanup(fail(ctx, GS_ERR_CUDA, "gs_render_saved: memset"));
+    gsl::project(project_args(P, sv->D, p, sv->pose32, opt), s);
+    gsl::BinArgs b = bin_args(P, sv->D, p);
+    gsl::bin_count(b, s);
+    uint32_t nd = 0;
+    if (cudaMemcpyAsync(&nd, p.ndups, sizeof nd, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cleanup(fail(ctx, GS_ERR_CUDA, "gs_render_saved: duplicate count"));
+    if (nd == 0xffffffffu)
+        return cleanup(fail(ctx, GS_ERR_CAPACITY, "more than 2^32 tile duplicates"));
+    st = alloc_sort(ctx, nd, p);
+    if (st != GS_OK)
+        return cleanup(st);
+    if (cudaMallocAsync(&sv->blk[1], sizeof(uint32_t) * (size_t)p.cap, s) != cudaSuccess) {
+        cudaGetLastError();
+        sv->blk[1] = nullptr;
+        return cleanup(fail(ctx, GS_ERR_OOM, "gs_render_saved: cudaMallocAsync failed"));
+    }
+    sv->vals = (uint32_t *)sv->blk[1];
+    sv->cap = p.cap;
+    p.vals[0] = sv->vals;  // the sorted lists land in the saved block
+    b = bin_args(P, sv->D, p);
+    const int cur = run_bin(b, s);
+    gsl::RasterArgs r = raster_args(P, sv->D, p, cur, opt);
+    r.out_rgb = rgb;
+    r.out_depth = depth;
+    r.out_alpha = alpha;
+    r.t_final = sv->t_final;
+    r.last = sv->last;
+    gsl::forward(r, false, s);
+    if (cudaGetLastError() != cudaSuccess)
+        return cleanup(fail(ctx, GS_ERR_CUDA, "gs_render_saved: launch"));
+    int flags = 0;
+    st = read_flags(ctx, p, s, &flags);
+    if (st != GS_OK)
+        return cleanup(st);
+    if (flags & gsk::kFlagNonFinite)
+        return cleanup(fail(ctx, GS_ERR_NONFINITE, "non-finite Gaussian parameter"));
+    ctx->stats = gs_stats_t{};
+    ctx->stats.n_dups = nd;
+    ctx->stats.n_pixels = P.n_pix;
+    *saved = sv;
+    return GS_OK;
+}
+
+gs_status_t gs_saved_outputs(const gs_saved_t *saved, float **t_final, int32_t **last)
+{
+    if (!saved)
+        return GS_ERR_INVALID_ARG;
+    if (t_final)
+        *t_final = saved->t_final;
+    if (last)
+        *last = saved->last;
+    return GS_OK;
+}
+
+gs_status_t gs_render_backward_saved(gs_ctx_t *ctx, const gs_saved_t *saved, const float *d_rgb,
+                                     const float *d_depth, const float *d_alpha, const float *pivots,
+                                     float *pose_grad, const gs_gaussian_grads_t *grads, gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    if (!saved || saved->device != ctx->device)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward_saved: no saved forward of this context's device");
+    GS_TRY(check_grads(ctx, grads));
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Plan &P = saved->P;
+    Pipe p;
+    p.rec = saved->rec;
+    p.aux = saved->aux;
+    p.counts = saved->counts;
+    p.ranges = saved->ranges;
+    p.vals[0] = saved->vals;
+    p.ndups = saved->ndups;
+    p.cap = saved->cap;
+    p.n_records = std::max<uint64_t>(P.n_records, 1);
+    const bool full = wants_params(grads);
+    if (full) {
+        const size_t hn = gsl::sort_hist_entries((uint32_t)std::max<uint64_t>(p.cap, p.n_records));
+        GS_TRY(wsT(ctx, S_HIST, hn, &p.hist));
+        GS_TRY(wsT(ctx, S_HISTP, gsl::scan_partials(hn), &p.histp));
+    }
+    return backward_core(ctx, P, saved->D, p, 0, &saved->g, saved->pose32, &saved->opt, saved->t_final,
+                         saved->last, d_rgb, d_depth, d_alpha, pivots, pose_grad, grads, full, s);
+}
+
+gs_status_t gs_saved_destroy(gs_saved_t *saved, gs_stream_t stream)
+{
+    if (!saved)
+        return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(saved->device);
+    for (void *b : saved->blk)
+        if (b)
+            cudaFreeAsync(b, (cudaStream_t)stream);
+    delete saved;
     return GS_OK;
 }
 
@@ -1674,7 +1926,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         };
         auto iteration = [&](cudaStream_t st) {
             mark(0, st);
-            gsl::project(project_args(P, D, p, pose32, opt), st);
+            gsl::project(project_args(P, D, p, pose32, opt, false), st);
             mark(1, st);
             const int c = run_bin(b, st);
             if (ordered)
@@ -1823,7 +2075,7 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
         r.tile_pairs = nullptr;
         r.tile_order = nullptr;
         r.queue = nullptr;
-        gsl::project(project_args(P, D, p, pose32, opt), s);
+        gsl::project(project_args(P, D, p, pose32, opt, false), s);
         r.vals = p.vals[run_bin(b, s)];
         gsl::forward(r, true, s);
         gsl::track_loss(ta, s);
@@ -2375,7 +2627,7 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     gsl::TrackArgs ta;
     GS_TRY(alloc_track(ctx, P, D, r, ta, srv->tloss, s));
     GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    gsl::project(project_args(P, D, p, srv->pose32, &srv->opt), ctx->cap);
+    gsl::project(project_args(P, D, p, srv->pose32, &srv->opt, false), ctx->cap);
     r.vals = p.vals[run_bin(b, ctx->cap)];
     gsl::forward(r, true, ctx->cap);
     gsl::track_loss(ta, ctx->cap);

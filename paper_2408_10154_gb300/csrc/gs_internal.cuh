@@ -224,7 +224,8 @@ struct ProjectArgs {
     int smooth;
     float4 *rec;               // [records][3] main record (AoS, 48 B)
     float4 *aux;               // [records][2] auxiliary (may be null)
-    int32_t *counts;
+    int32_t *counts;          // tiles touched per record (null: not written; the segmented
+                              // lists read the seg_list entries instead)
     int *flags;
     // tight lists: shrink each rectangle to the tiles that meet the
     // axis-aligned box of the record's alpha-threshold ellipse (exponent >=

@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(256) k_project(const gsl::ProjectArgs a)
                 }
             }
         }
-        a.counts[rec] = count;
+        if (a.counts)
+            a.counts[rec] = count;
         if (a.seg_hdr)
             seg_note(a, sGeo[v], rec, z, count, x0, x1, y0, y1);
     }

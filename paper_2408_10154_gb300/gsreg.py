@@ -70,7 +70,8 @@ class gs_gaussian_grads_t(ctypes.Structure):
 
 
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
-           "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_loss", "gs_pose_step",
+           "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_render_saved",
+           "gs_saved_outputs", "gs_render_backward_saved", "gs_saved_destroy", "gs_loss", "gs_pose_step",
            "gs_fuse", "gs_register", "gs_register_batch", "gs_register_async", "gs_register_batch_async", "gs_transform", "gs_render_noalloc", "gs_track_loss",
            "gs_overlap_ratio", "gs_transform_batch", "gs_sort_u32", "gs_selftest_bounded_wait", "gs_probe_fp32",
            "gs_server_create",
@@ -110,6 +111,10 @@ def load(build_if_missing: bool = False):
             "gs_bin": ([P, P, P, P, I, I64, P, P, I64, P, P, P], I),
             "gs_render": ([P, P, P, P, I, P, P, P, P, P, P, P], I),
             "gs_render_backward": ([P, P, P, P, I, P, P, P, P, P, P, P, P, P, P], I),
+            "gs_render_saved": ([P, P, P, P, I, P, P, P, P, P, P], I),
+            "gs_saved_outputs": ([P, P, P], I),
+            "gs_render_backward_saved": ([P, P, P, P, P, P, P, P, P], I),
+            "gs_saved_destroy": ([P, P], I),
             "gs_loss": ([P, P, I, P, P, P, P, P, P, P, P], I),
             "gs_track_loss": ([P, P, I, P, P, P, P, P, ctypes.c_float, P, P, P, P, P, P], I),
             "gs_overlap_ratio": ([P, P, P, P, ctypes.c_float, P, P, P, P, P], I),
@@ -329,6 +334,68 @@ def gs_render_backward(ctx: Context, g: Gaussians, poses, cams, t_final, last, d
                                           ctypes.byref(opt), _ptr(t_final), _ptr(last), _ptr(d_rgb),
                                           _ptr(d_depth), _ptr(d_alpha), _ptr(pivots), _ptr(pose_grad), grads,
                                           _stream()))
+    return (pose_grad, out) if params else pose_grad
+
+
+class Saved:
+    """A forward pass kept for its adjoint (gs_render_saved); freed on
+    close() or when collected.  Keeps the submap, poses and options alive."""
+
+    def __init__(self, ctx: Context, handle, g: Gaussians, poses, cams, npx):
+        self.ctx, self.handle, self.g, self.poses, self.cams = ctx, handle, g, poses, cams
+        tf, last = ctypes.c_void_p(), ctypes.c_void_p()
+        ctx.check(ctx._lib.gs_saved_outputs(handle, ctypes.byref(tf), ctypes.byref(last)))
+        self._tf, self._last, self.npx = tf.value, last.value, npx
+
+    def close(self, stream=None):
+        if self.handle:
+            self.ctx._lib.gs_saved_destroy(self.handle, stream if stream is not None else _stream())
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gs_render_saved(ctx: Context, g: Gaussians, poses: torch.Tensor, cams, opt=None):
+    """gs_render that keeps its projection, tile lists and per-pixel state
+    for gs_render_backward_saved.  Returns (dict(rgb, depth, alpha), Saved)."""
+    cam_arr, nc = cameras(cams)
+    opt = opt or default_options()
+    npx = _npix(cams)
+    dev = g.means4.device
+    out = dict(rgb=torch.empty(3 * npx, device=dev), depth=torch.empty(npx, device=dev),
+               alpha=torch.empty(npx, device=dev))
+    gst = g.c_struct()
+    h = ctypes.c_void_p()
+    poses = poses.contiguous()
+    ctx.check(ctx._lib.gs_render_saved(ctx.handle, ctypes.byref(gst), _ptr(poses), cam_arr, nc, ctypes.byref(opt),
+                                       _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["alpha"]), ctypes.byref(h),
+                                       _stream()))
+    sv = Saved(ctx, h, g, poses, cams, npx)
+    sv.opt = opt
+    return out, sv
+
+
+def gs_render_backward_saved(ctx: Context, saved: Saved, d_rgb=None, d_depth=None, d_alpha=None, pivots=None,
+                             params=False):
+    """gs_render_backward from a saved forward: pose twist gradient
+    [n_cams, 6], and with ``params`` the per-Gaussian gradients."""
+    nc = len(np.asarray(saved.cams).reshape(-1, 18))
+    g = saved.g
+    dev = g.means4.device
+    pose_grad = torch.empty((nc, 6), dtype=torch.float32, device=dev)
+    out, grads = None, None
+    if params:
+        out = dict(means4=torch.empty_like(g.means4), log_scales4=torch.empty_like(g.log_scales4),
+                   quats4=torch.empty_like(g.quats4), logits=torch.empty_like(g.logits), rgb4=torch.empty_like(g.rgb4))
+        grads = ctypes.byref(gs_gaussian_grads_t(out["means4"].data_ptr(), out["log_scales4"].data_ptr(),
+                                                 out["quats4"].data_ptr(), out["logits"].data_ptr(),
+                                                 out["rgb4"].data_ptr()))
+    ctx.check(ctx._lib.gs_render_backward_saved(ctx.handle, saved.handle, _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha),
+                                                _ptr(pivots), _ptr(pose_grad), grads, _stream()))
     return (pose_grad, out) if params else pose_grad
 
 

@@ -96,3 +96,30 @@ def test_autograd_function_matches_render_backward(env):
                                   torch.zeros_like(alpha), params=True)
     for leaf, key in zip(leaves, ("means4", "log_scales4", "quats4", "logits", "rgb4")):
         assert torch.equal(leaf.grad, gr[key])
+
+
+@pytest.mark.parametrize("n,W,H,f,views", [(500, 64, 48, 56.0, 2), (3000, 160, 120, 140.0, 3)])
+def test_saved_forward_equals_render_and_backward(env, n, W, H, f, views):
+    # gs_render_saved + gs_render_backward_saved (the adjoint from the kept
+    # projection and tile lists, no second binning) against gs_render +
+    # gs_render_backward: the same renders and gradients, bit for bit
+    gs, autograd, ctx = env
+    c = synth.small_case(n, W, H, f, n_views=views, seed=n, ls_mean=-3.0)
+    g = gs.Gaussians.from_numpy(c["gaussians"])
+    rng = np.random.default_rng(n)
+    poses = np.stack([synth.random_rigid(rng, 3.0, 0.03) for _ in range(views)])
+    P = dev(poses.reshape(-1, 12))
+    out = gs.gs_render(ctx, g, P, c["cams"])
+    o2, sv = gs.gs_render_saved(ctx, g, P, c["cams"])
+    for k in ("rgb", "depth", "alpha"):
+        assert torch.equal(out[k], o2[k]), k
+    npx = sum(int(cam[4]) * int(cam[5]) for cam in c["cams"])
+    cr, cd, ca = (dev(rng.standard_normal(3 * npx)), dev(rng.standard_normal(npx)), dev(rng.standard_normal(npx)))
+    piv = dev(np.stack([O.centroid(O.Gaussians.from_dict(c["gaussians"]))] * views))
+    pg1, gr1 = gs.gs_render_backward(ctx, g, P, c["cams"], out["t_final"], out["last"], cr, cd, ca, piv, params=True)
+    for _ in range(2):  # the saved state serves more than one adjoint
+        pg2, gr2 = gs.gs_render_backward_saved(ctx, sv, cr, cd, ca, piv, params=True)
+        assert torch.equal(pg1, pg2)
+        for k in gr1:
+            assert torch.equal(gr1[k], gr2[k]), k
+    sv.close()
