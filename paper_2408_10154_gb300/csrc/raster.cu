@@ -388,10 +388,17 @@ __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int lane)
     return s;
 }
 
-constexpr int kBwd2Threads = 128;
+// Adjoint layout: kBwdPPT pixels per thread, each warp on a kBwdPatchW x 8
+// patch of its tile (lane -> column lane % kBwdPatchW, rows lane /
+// kBwdPatchW + k * kBwdRowStep for k < kBwdPPT).
+constexpr int kBwdPPT = 2;
+constexpr int kBwd2Threads = kTilePix / kBwdPPT;
 constexpr int kBwd2Warps = kBwd2Threads / 32;
+constexpr int kBwdPatchW = kBwdPPT == 2 ? 8 : 16;
+constexpr int kBwdRowStep = 32 / kBwdPatchW;
 constexpr int kBwd2Chunk = 64;
-constexpr int kBwd2MinBlocks = 8;
+constexpr int kBwd2MinBlocks = kBwdPPT == 2 ? 8 : 12;
+static_assert(kBwdPPT * kBwdRowStep == 8 && kTile % kBwdPatchW == 0, "warp patches of 8 rows tile the 16x16 tile");
 
 // Six running FP32 sums of one thread with Kahan compensation (the lost
 // low-order part is carried in c; the true sum is s - c), kept in shared
@@ -650,11 +657,13 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     const uint32_t lt = t - d.tile_base;
     const int tx = (int)(lt % (uint32_t)d.TX), ty = (int)(lt / (uint32_t)d.TX);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
-    const int py0 = ty * kTile + (warp >> 1) * 8 + (lane >> 3);
-    // the warp's pixel samples: an 8x8 patch
-    const float xa = (float)(tx * kTile + (warp & 1) * 8) + 0.5f, xb = xa + 7.0f;
-    const float ya = (float)(ty * kTile + (warp >> 1) * 8) + 0.5f, yb = ya + 7.0f;
+    constexpr int kPatchesX = kTile / kBwdPatchW;
+    const int wx = tx * kTile + (warp % kPatchesX) * kBwdPatchW, wy = ty * kTile + (warp / kPatchesX) * 8;
+    const int px = wx + lane % kBwdPatchW;
+    const int py0 = wy + lane / kBwdPatchW;
+    // the warp's pixel samples: a kBwdPatchW x 8 patch
+    const float xa = (float)wx + 0.5f, xb = xa + (float)(kBwdPatchW - 1);
+    const float ya = (float)wy + 0.5f, yb = ya + 7.0f;
     const bool cull = a.alpha_min > 0.0f;
     const uint2 rg = a.ranges[t];
     // staging of one record of a chunk (thread i, chunk position i)
@@ -684,13 +693,17 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     float pivot = 0.0f;
     if (threadIdx.x < 3 && a.c_cam)
         pivot = (float)a.c_cam[3 * vp + threadIdx.x];
-    PixAdj P0, P1;
+    PixAdj P[kBwdPPT];
     const float gain = (REG && d.exposure) ? a.expo32[2 * vp] : 1.0f;
-    pix_adj_init<REG>(P0, d, a, px, py0, a.bg, gain);
-    pix_adj_init<REG>(P1, d, a, px, py0 + 4, a.bg, gain);
+#pragma unroll
+    for (int k = 0; k < kBwdPPT; ++k)
+        pix_adj_init<REG>(P[k], d, a, px, py0 + k * kBwdRowStep, a.bg, gain);
     if (guess_row)
         stage(r_guess);
-    int ml = max(P0.last, P1.last);
+    int ml = P[0].last;
+#pragma unroll
+    for (int k = 1; k < kBwdPPT; ++k)
+        ml = max(ml, P[k].last);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         ml = max(ml, __shfl_xor_sync(0xffffffffu, ml, o));
@@ -741,9 +754,11 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
                 g[k] = -0.0f;  // -0 + x == x for every x (not so +0): the first additions fold away
             const float4 q0 = s0[j];
             const float4 q1 = s1[j];
-            const bool c0 = pix_adj_pair<FULL, !REG>(P0, lo + j, q0, q1, &s2[j], a, g);
-            const bool c1 = pix_adj_pair<FULL, !REG>(P1, lo + j, q0, q1, &s2[j], a, g);
-            if (__any_sync(0xffffffffu, c0 || c1)) {
+            bool contrib = false;
+#pragma unroll
+            for (int k = 0; k < kBwdPPT; ++k)
+                contrib |= pix_adj_pair<FULL, !REG>(P[k], lo + j, q0, q1, &s2[j], a, g);
+            if (__any_sync(0xffffffffu, contrib)) {
                 constexpr int NP = NG <= 8 ? 8 : 16;
                 float v[NP];
 #pragma unroll
