@@ -664,3 +664,31 @@ def test_tile_schedules_give_identical_registrations(gs, ctx):
     assert tight_dups < 0.9 * st.n_dups
     np.testing.assert_allclose(loose[0], out[0][0], atol=1e-4)
     np.testing.assert_allclose(loose[2], out[0][2], rtol=1e-4)
+
+
+def test_batched_full_size_pairs_equal_separate_calls(gs, ctx):
+    # the first 4 pairs of the batched workload at full size (62k / 25k /
+    # 192k / 22k Gaussians, 7-12 keyframes per submap at 640x480 or
+    # 1200x680, both directions), keyframes rendered by the oracle: one
+    # batch equals one gs_register call per pair, bit for bit
+    import os
+    O.set_threads(os.cpu_count() or 1)
+    pairs = synth.batched_pairs()["pairs"][:4]
+    probs = []
+    for pr in pairs:
+        og = O.Gaussians.from_dict(pr["gaussians"])
+        oq = O.transform(og, pr["T_gt"])
+        f32 = lambda r: (dev(r["rgb"].astype(np.float32)), dev(r["depth"].astype(np.float32)))
+        sv = [(cam, *f32(O.render(og, np.eye(3, 4), cam))) for cam in pr["src_cams"][:3]]
+        tv = [(cam, *f32(O.render(oq, np.eye(3, 4), cam))) for cam in pr["tgt_cams"][:3]]
+        src = gs.Gaussians.from_numpy(pr["gaussians"])
+        tgt = gs.Gaussians(*[dev(a) for a in (oq.means4, oq.log_scales4, oq.quats4, oq.logits, oq.rgb4)])
+        probs.append((src, tgt, sv, tv))
+    T, conf, eps = gs.gs_register_batch(ctx, probs, 10)
+    off = 0
+    for i, p in enumerate(probs):
+        Ti, ci, ei, _ = gs.gs_register(ctx, *p, 10)
+        np.testing.assert_array_equal(T[i], Ti)
+        assert conf[i] == ci
+        np.testing.assert_array_equal(eps[off:off + len(ei)], ei)
+        off += len(ei)
