@@ -397,6 +397,10 @@ constexpr int kBwd2Warps = kBwd2Threads / 32;
 constexpr int kBwdPatchW = kBwdPPT == 2 ? 8 : 16;
 constexpr int kBwdRowStep = 32 / kBwdPatchW;
 constexpr int kBwd2Chunk = 64;
+// a row of per-record warp sums in shared memory: one float more than the
+// chunk, so that the lanes storing one record's sums of different values
+// (rows k * warps + warp, 65 floats apart) hit different banks
+constexpr int kBwdSlotRow = kBwd2Chunk + 1;
 constexpr int kBwd2MinBlocks = kBwdPPT == 2 ? 8 : 12;
 static_assert(kBwdPPT * kBwdRowStep == 8 && kTile % kBwdPatchW == 0, "warp patches of 8 rows tile the 16x16 tile");
 
@@ -646,7 +650,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
 {
     constexpr int NG = FULL ? 10 : 6;
     extern __shared__ float4 s_dyn[];  // declared float4: 16-byte aligned for the float4 zeroing
-    float *const s_slots = reinterpret_cast<float *>(s_dyn);  // [NG][warps][chunk]
+    float *const s_slots = reinterpret_cast<float *>(s_dyn);  // [NG][warps][kBwdSlotRow]
     __shared__ float4 s0[kBwd2Chunk], s1[kBwd2Chunk], s2[kBwd2Chunk];
     __shared__ float4 s_x0[kBwd2Chunk], s_x1[kBwd2Chunk];  // the records' camera-frame mean and covariance
     __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
@@ -730,8 +734,8 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
         // hi == n_list only for a first chunk the guess staged already
         if (hi != n_list && (int)threadIdx.x < cnt)
             stage(a.vals[rg.x + lo + threadIdx.x]);
-        static_assert(NG * kBwd2Warps * kBwd2Chunk % 4 == 0, "slots zeroed as float4");
-        for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwd2Chunk / 4; k += kBwd2Threads)
+        static_assert(NG * kBwd2Warps * kBwdSlotRow % 4 == 0, "slots zeroed as float4");
+        for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwdSlotRow / 4; k += kBwd2Threads)
             s_dyn[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         __syncthreads();
         // this warp's pixels never reach past wl: skip the list tail
@@ -768,7 +772,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
                 constexpr int L = 32 / NP;
                 const int k = lane / L;
                 if ((lane % L) == 0 && k < NG)
-                    s_slots[(k * kBwd2Warps + warp) * kBwd2Chunk + j] = sum;
+                    s_slots[(k * kBwd2Warps + warp) * kBwdSlotRow + j] = sum;
             }
         }
         __syncthreads();
@@ -780,7 +784,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
                 float s = -0.0f;
 #pragma unroll
                 for (int w = 0; w < kBwd2Warps; ++w)
-                    s += s_slots[(k * kBwd2Warps + w) * kBwd2Chunk + threadIdx.x];
+                    s += s_slots[(k * kBwd2Warps + w) * kBwdSlotRow + threadIdx.x];
                 G[k] = s;
                 any |= s != 0.0f;
             }
@@ -815,7 +819,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2_q(co
 template <bool REG, bool FULL>
 constexpr size_t bwd2_smem()
 {
-    return (size_t)(FULL ? 10 : 6) * kBwd2Warps * kBwd2Chunk * sizeof(float);
+    return (size_t)(FULL ? 10 : 6) * kBwd2Warps * kBwdSlotRow * sizeof(float);
 }
 
 // CTAs of the persistent kernels: as many as can be resident at once
