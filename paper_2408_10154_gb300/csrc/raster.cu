@@ -592,7 +592,7 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
 // loss has none).
 template <bool FULL, bool ALPHA>
 __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0, const float4 &q1,
-                                             const float4 *q2p, const gsl::RasterArgs &a, float *g)
+                                             const float4 &q2, const gsl::RasterArgs &a, float *g)
 {
     if (jj >= P.last)
         return false;
@@ -609,7 +609,6 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     const float om = 1.0f - alpha;
     const float rom = __fdividef(1.0f, om);
     const float Ti = P.T * rom;
-    const float4 q2 = *q2p;
     const float gcc = fmaf(P.gd, q1.z, fmaf(P.gb, q2.z, fmaf(P.gg, q2.y, P.gr * q2.x)));
     float dal = fmaf(Ti, gcc, -(P.Q * rom));
     if (ALPHA)
@@ -743,7 +742,11 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
         int nsel = 0;
         for (int j0 = 0; j0 < wl; j0 += 32) {
             const int j = j0 + lane;
-            const bool keep = j < wl && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].w, xa, xb, ya, yb));
+            bool keep = false;
+            if (j < wl) {
+                const float4 t1 = s1[j];  // one 16-byte load for cc and the cutoff
+                keep = !cull || patch_may_hit(s0[j], t1.x, t1.w, xa, xb, ya, yb);
+            }
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (keep)
                 s_sel[warp][nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
@@ -758,10 +761,11 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
                 g[k] = -0.0f;  // -0 + x == x for every x (not so +0): the first additions fold away
             const float4 q0 = s0[j];
             const float4 q1 = s1[j];
+            const float4 q2 = s2[j];  // the record's colour, loaded once for every pixel of the lane
             bool contrib = false;
 #pragma unroll
             for (int k = 0; k < kBwdPPT; ++k)
-                contrib |= pix_adj_pair<FULL, !REG>(P[k], lo + j, q0, q1, &s2[j], a, g);
+                contrib |= pix_adj_pair<FULL, !REG>(P[k], lo + j, q0, q1, q2, a, g);
             if (__any_sync(0xffffffffu, contrib)) {
                 constexpr int NP = NG <= 8 ? 8 : 16;
                 float v[NP];

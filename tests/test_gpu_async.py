@@ -119,3 +119,33 @@ def test_async_registration_reports_outgrown_lists_in_its_status(gs, ctx):
     ok = gs.gs_register_async(ctx, src, tgt, sv, tv, 5)
     torch.cuda.synchronize()
     assert int(ok["status"].item()) == 0
+
+
+def test_async_rejects_bad_arguments(gs, ctx):
+    # the host checks run before anything is enqueued: a missing status word
+    # or output, and a problem without keyframes, are refused
+    import ctypes
+    src, tgt, sv, tv = _problem(gs, 300, 64, 40, 50.0, 1, 1, 35)
+    T = torch.empty(12, dtype=torch.float64, device="cuda")
+    conf = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    s, t = src.c_struct(), tgt.c_struct()
+    views = gs.gsreg._views(sv)
+    lib, h = ctx._lib, ctx.handle
+    opt = gs.default_options()
+    P = ctypes.c_void_p
+    args = lambda Tp, cp, stp, nsv: (h, ctypes.byref(s), ctypes.byref(t), views, nsv, None, 0, ctypes.byref(opt), 5,
+                                     Tp, cp, None, None, stp, gs.gsreg._stream())
+    assert lib.gs_register_async(*args(P(T.data_ptr()), P(conf.data_ptr()), None, 1)) == 1
+    assert lib.gs_register_async(*args(None, P(conf.data_ptr()), P(st.data_ptr()), 1)) == 1
+    assert lib.gs_register_async(*args(P(T.data_ptr()), P(conf.data_ptr()), P(st.data_ptr()), 0)) == 1
+
+
+def test_fp32_probe_measures_the_device(gs, ctx):
+    tflops, sms = gs.gs_probe_fp32(ctx)
+    props = torch.cuda.get_device_properties(0)
+    assert sms == props.multi_processor_count
+    # 128 FP32 lanes x 2 flops per FMA per SM per cycle: the probe lands
+    # below that bound at the highest clock and well above a tenth of it
+    bound = sms * 128 * 2 * 2.2e9 / 1e12
+    assert 0.1 * bound < tflops < bound, (tflops, bound)
