@@ -729,7 +729,12 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     const int twist_warps = (min(maxl, kBwd2Chunk) + 31) / 32;
     for (int hi = maxl; hi > 0; hi -= kBwd2Chunk) {
         const int lo = max(hi - kBwd2Chunk, 0), cnt = hi - lo;
-        __syncthreads();
+        // a later chunk restages what the previous chunk's epilogue read; the
+        // first one follows the pixel-state barrier, and until the barrier
+        // below each thread writes only its own staging slots and zeroes
+        // slots nobody reads yet (hi is the same for the whole block)
+        if (hi != maxl)
+            __syncthreads();
         // hi == n_list only for a first chunk the guess staged already
         if (hi != n_list && (int)threadIdx.x < cnt)
             stage(a.vals[rg.x + lo + threadIdx.x]);
