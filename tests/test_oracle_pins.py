@@ -635,6 +635,31 @@ def test_registration_recovers_known_transform():
         assert eps < 0.01 * hist[0]
 
 
+def test_fused_registration_meets_the_convergence_precheck():
+    # the plain 2k workload with its four keyframes, 50 iterations each,
+    # fused by Eq. 7: the fused estimate recovers the known transform within
+    # 0.1 mm / 0.002 deg, the pre-check the registration parity bar rests on
+    # (each keyframe alone is within 0.005 deg / 0.2 mm, three of the four
+    # within the pre-check too)
+    O.set_threads(os.cpu_count() or 1)  # results do not depend on the thread count
+    c = synth.plain_2k()
+    g = O.Gaussians.from_dict(c["gaussians"])
+    T = c["T_gt"]
+    ests, epss, tight = [], [], 0
+    for cam in c["cams"]:
+        tr = O.render(g, T, cam)
+        P, eps, _ = O.register_view(g, cam, tr["rgb"], tr["depth"], 50)
+        ang, dt = _rot_err(P, T)
+        assert ang < 0.005 and dt < 2e-4, (ang, dt)
+        tight += ang < 0.002 and dt < 1e-4
+        ests.append(P)
+        epss.append(eps)
+    assert tight >= 3
+    Tf, _ = O.fuse(np.stack(ests), epss, [False] * 4)
+    ang, dt = _rot_err(Tf, T)
+    assert ang < 0.002 and dt < 1e-4, (ang, dt)
+
+
 def test_fuse_closed_forms():
     rng = np.random.default_rng(7)
     T = synth.random_rigid(rng, 20.0, 0.3)
