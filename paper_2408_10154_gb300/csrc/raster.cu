@@ -641,6 +641,137 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Packed form of the registration adjoint's pair arithmetic.  A thread's two
+// pixels (same column, rows r and r + 4) go through one f32x2 operation per
+// step: add/sub/mul/fma.rn.f32x2 round each of the two lanes exactly as the
+// scalar .rn operation does, and issue once for both.  The pair's early
+// exits become masks (a pair that fails a test enters every sum with weight
+// 0, so every value is the scalar walk's, up to the sign of zero sums), and
+// the walk carries -Q and produces the negated screen-space gradient, so
+// that no operand needs a negation: -RN(a b) = RN(-a b) and -RN(a b + c) =
+// RN(-a b - c) exactly.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;  // {lo, hi} = {pixel 0, pixel 1}
+__device__ __forceinline__ f32x2 x2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void x2_split(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32x2 bc2(float v) { return x2(v, v); }
+
+// the two pixels' walk state: T, -Q and the loss gradient per pixel
+struct PixAdj2 {
+    f32x2 pxf, pyf, T, nQ, gr, gg, gb, gd;
+    int last0, last1;
+};
+
+// A staged record, each value twice ({v, v} pairs): {u, v}, {ca, cb},
+// {cc, -o}, {z, r}, {g, b}
+struct RecX2 {
+    ulonglong2 uv, ab, cn, zr, gb;
+};
+
+// Both pixels of one (thread, Gaussian) pair of the registration adjoint:
+// the contract's decisions (the alpha test decides alone: the exponent
+// cutoff only ever skips pairs that fail it), the transmittance recovery,
+// the colour-behind update and the negated screen-space gradient, summed
+// over the two pixels in the scalar walk's order, into ng.  Returns
+// whether either pixel contributed.
+__device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, float amax, float namax,
+                                           float namin, float (&ng)[6])
+{
+    const f32x2 dx = sub2(R.uv.x, P.pxf), dy = sub2(R.uv.y, P.pyf);
+    const f32x2 h = fma2(R.ab.x, dx, mul2(R.ab.y, dy));
+    const f32x2 ky = mul2(R.cn.x, dy);
+    const f32x2 power = fma2(h, dx, mul2(ky, dy));
+    float p0, p1;
+    x2_split(power, p0, p1);
+    // the contract exponential (exp_ct_nonpos) of both exponents
+    const f32x2 xc = x2(fmaxf(p0, -80.0f), fmaxf(p1, -80.0f));
+    const f32x2 magic = bc2(12582912.0f);
+    const f32x2 t = fma2(xc, bc2(1.4426950408889634f), magic);
+    const f32x2 kf = sub2(t, magic);
+    f32x2 r = fma2(kf, bc2(-0.693145751953125f), xc);
+    r = fma2(kf, bc2(-1.428606820309417e-06f), r);
+    f32x2 p = fma2(bc2(1.3888888888888889e-03f), r, bc2(8.3333333333333333e-03f));
+    p = fma2(p, r, bc2(4.1666666666666667e-02f));
+    p = fma2(p, r, bc2(1.6666666666666667e-01f));
+    p = fma2(p, r, bc2(0.5f));
+    p = fma2(p, r, bc2(1.0f));
+    p = fma2(p, r, bc2(1.0f));
+    float pl, ph, tl, th;
+    x2_split(p, pl, ph);
+    x2_split(t, tl, th);
+    const float e0 = __int_as_float(__float_as_int(pl) + (int)((uint32_t)__float_as_int(tl) << 23));
+    const float e1 = __int_as_float(__float_as_int(ph) + (int)((uint32_t)__float_as_int(th) << 23));
+    // -x = (-o) e; clamped: x > alpha_max; -alpha; the alpha test
+    float nx0, nx1;
+    x2_split(mul2(R.cn.y, x2(e0, e1)), nx0, nx1);
+    const bool cl0 = nx0 < namax, cl1 = nx1 < namax;
+    const float na0 = cl0 ? namax : nx0, na1 = cl1 ? namax : nx1;
+    const bool live0 = jj < P.last0 && !(p0 > 0.0f) && !(na0 > namin);
+    const bool live1 = jj < P.last1 && !(p1 > 0.0f) && !(na1 > namin);
+    const f32x2 nal = x2(live0 ? na0 : 0.0f, live1 ? na1 : 0.0f);
+    const f32x2 nag = x2(live0 && !cl0 ? na0 : 0.0f, live1 && !cl1 ? na1 : 0.0f);
+    // 1 - alpha, its reciprocal, T_i = T / (1 - alpha)
+    float om0, om1;
+    x2_split(add2(bc2(1.0f), nal), om0, om1);
+    const f32x2 rom = x2(__fdividef(1.0f, om0), __fdividef(1.0f, om1));
+    const f32x2 Ti = mul2(P.T, rom);
+    const f32x2 gcc = fma2(P.gd, R.zr.x, fma2(P.gb, R.gb.y, fma2(P.gg, R.gb.x, mul2(P.gr, R.zr.y))));
+    const f32x2 dal = fma2(Ti, gcc, mul2(P.nQ, rom));
+    const f32x2 nwgt = mul2(nal, Ti);
+    P.nQ = fma2(gcc, nwgt, P.nQ);
+    const f32x2 ndp = mul2(dal, nag);
+    const f32x2 gu = fma2(R.ab.x, dx, h);
+    const f32x2 gv = fma2(R.ab.y, dx, add2(ky, ky));
+    float a0, a1, b0, b1, u0, u1, v0, v1, d0, d1, w0, w1;
+    x2_split(mul2(ndp, gu), a0, a1);
+    x2_split(mul2(ndp, gv), b0, b1);
+    x2_split(gu, u0, u1);
+    x2_split(gv, v0, v1);
+    x2_split(P.gd, d0, d1);
+    x2_split(nwgt, w0, w1);
+    ng[0] = a0 + a1;
+    ng[1] = b0 + b1;
+    ng[2] = fmaf(a1, u1, a0 * u0);
+    ng[3] = fmaf(a1, v1, a0 * v0);
+    ng[4] = fmaf(b1, v1, b0 * v0);
+    ng[5] = fmaf(d1, w1, d0 * w0);
+    P.T = Ti;
+    return live0 || live1;
+}
+
 static_assert(kBwd2Chunk <= kBwd2Threads && kBwd2Chunk % 32 == 0, "one thread stages one record");
 
 // One tile of the adjoint (all kBwd2Threads threads of the CTA take part).
@@ -652,6 +783,10 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     float *const s_slots = reinterpret_cast<float *>(s_dyn);  // [NG][warps][kBwdSlotRow]
     __shared__ float4 s0[kBwd2Chunk], s1[kBwd2Chunk], s2[kBwd2Chunk];
     __shared__ float4 s_x0[kBwd2Chunk], s_x1[kBwd2Chunk];  // the records' camera-frame mean and covariance
+    // the registration adjoint walks both pixels of a thread with packed
+    // operations, on records staged with each value twice (RecX2)
+    constexpr bool PK = REG && !FULL && kBwdPPT == 2;
+    __shared__ RecX2 s_x2[PK ? kBwd2Chunk : 1];
     __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
     __shared__ int s_maxl[kBwd2Warps];
     __shared__ float s_tw[kBwd2Warps][6][2];
@@ -672,9 +807,21 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     // staging of one record of a chunk (thread i, chunk position i)
     auto stage = [&](uint32_t r) {
         const float4 *R = a.rec + 3 * (size_t)r;
-        s0[threadIdx.x] = R[0];
-        s1[threadIdx.x] = stage_cutoff(R[1], a);
-        s2[threadIdx.x] = R[2];
+        if constexpr (PK) {
+            const float4 q0 = R[0], q1 = R[1], q2 = R[2];
+            s0[threadIdx.x] = q0;
+            s1[threadIdx.x] = stage_cutoff(q1, a);
+            float4 *X = reinterpret_cast<float4 *>(&s_x2[threadIdx.x]);
+            X[0] = make_float4(q0.x, q0.x, q0.y, q0.y);
+            X[1] = make_float4(q0.z, q0.z, q0.w, q0.w);
+            X[2] = make_float4(q1.x, q1.x, -q1.y, -q1.y);
+            X[3] = make_float4(q1.z, q1.z, q2.x, q2.x);
+            X[4] = make_float4(q2.y, q2.y, q2.z, q2.z);
+        } else {
+            s0[threadIdx.x] = R[0];
+            s1[threadIdx.x] = stage_cutoff(R[1], a);
+            s2[threadIdx.x] = R[2];
+        }
         if (a.tile_twist) {
             // the camera-frame mean and covariance, staged with the record
             // (not read after the walk) so that these loads overlap
@@ -701,6 +848,19 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
 #pragma unroll
     for (int k = 0; k < kBwdPPT; ++k)
         pix_adj_init<REG>(P[k], d, a, px, py0 + k * kBwdRowStep, a.bg, gain);
+    PixAdj2 P2;
+    if constexpr (PK) {
+        P2.pxf = bc2(P[0].pxf);
+        P2.pyf = x2(P[0].pyf, P[1].pyf);
+        P2.T = x2(P[0].T, P[1].T);
+        P2.nQ = x2(-P[0].Q, -P[1].Q);
+        P2.gr = x2(P[0].gr, P[1].gr);
+        P2.gg = x2(P[0].gg, P[1].gg);
+        P2.gb = x2(P[0].gb, P[1].gb);
+        P2.gd = x2(P[0].gd, P[1].gd);
+        P2.last0 = P[0].last;
+        P2.last1 = P[1].last;
+    }
     if (guess_row)
         stage(r_guess);
     int ml = P[0].last;
@@ -764,13 +924,17 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
 #pragma unroll
             for (int k = 0; k < NG; ++k)
                 g[k] = -0.0f;  // -0 + x == x for every x (not so +0): the first additions fold away
-            const float4 q0 = s0[j];
-            const float4 q1 = s1[j];
-            const float4 q2 = s2[j];  // the record's colour, loaded once for every pixel of the lane
             bool contrib = false;
+            if constexpr (PK) {
+                contrib = pix_adj_x2(P2, lo + j, s_x2[j], a.alpha_max, -a.alpha_max, -a.alpha_min, g);
+            } else {
+                const float4 q0 = s0[j];
+                const float4 q1 = s1[j];
+                const float4 q2 = s2[j];  // the record's colour, loaded once for every pixel of the lane
 #pragma unroll
-            for (int k = 0; k < kBwdPPT; ++k)
-                contrib |= pix_adj_pair<FULL, !REG>(P[k], lo + j, q0, q1, q2, a, g);
+                for (int k = 0; k < kBwdPPT; ++k)
+                    contrib |= pix_adj_pair<FULL, !REG>(P[k], lo + j, q0, q1, q2, a, g);
+            }
             if (__any_sync(0xffffffffu, contrib)) {
                 constexpr int NP = NG <= 8 ? 8 : 16;
                 float v[NP];
@@ -794,7 +958,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
 #pragma unroll
                 for (int w = 0; w < kBwd2Warps; ++w)
                     s += s_slots[(k * kBwd2Warps + w) * kBwdSlotRow + threadIdx.x];
-                G[k] = s;
+                G[k] = PK ? -s : s;  // the packed walk sums the negated gradient
                 any |= s != 0.0f;
             }
             if (FULL) {
