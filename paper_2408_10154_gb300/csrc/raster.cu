@@ -123,6 +123,97 @@ __device__ __forceinline__ float4 stage_cutoff(float4 q1, const gsl::RasterArgs 
     return q1;
 }
 
+// ---------------------------------------------------------------------------
+// Packed pixel pairs.  In the registration forward and adjoint a thread
+// walks two pixels (same column, rows r and r + 4) with one f32x2 operation
+// per step: add/sub/mul/fma.rn.f32x2 round each of the two lanes exactly as
+// the scalar .rn operation does, and issue once for both.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;  // {lo, hi} = {pixel 0, pixel 1}
+__device__ __forceinline__ f32x2 x2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void x2_split(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32x2 bc2(float v) { return x2(v, v); }
+
+// A staged record with each value twice ({v, v} pairs) for the packed
+// walks: {u, v}, {ca, cb}, {cc, o} (the adjoint stages -o), {z, r}, {g, b}
+struct RecX2 {
+    ulonglong2 uv, ab, co, zr, gb;
+};
+__device__ __forceinline__ void stage_x2(RecX2 &dst, const float4 &q0, const float4 &q1, const float4 &q2, float o)
+{
+    float4 *X = reinterpret_cast<float4 *>(&dst);
+    X[0] = make_float4(q0.x, q0.x, q0.y, q0.y);
+    X[1] = make_float4(q0.z, q0.z, q0.w, q0.w);
+    X[2] = make_float4(q1.x, q1.x, o, o);
+    X[3] = make_float4(q1.z, q1.z, q2.x, q2.x);
+    X[4] = make_float4(q2.y, q2.y, q2.z, q2.z);
+}
+
+// the contract exponential (exp_ct_nonpos) of both lanes of x
+__device__ __forceinline__ void exp_ct_nonpos_x2(float x0, float x1, float &e0, float &e1)
+{
+    const f32x2 xc = x2(fmaxf(x0, -80.0f), fmaxf(x1, -80.0f));
+    const f32x2 magic = bc2(12582912.0f);
+    const f32x2 t = fma2(xc, bc2(1.4426950408889634f), magic);
+    const f32x2 kf = sub2(t, magic);
+    f32x2 r = fma2(kf, bc2(-0.693145751953125f), xc);
+    r = fma2(kf, bc2(-1.428606820309417e-06f), r);
+    f32x2 p = fma2(bc2(1.3888888888888889e-03f), r, bc2(8.3333333333333333e-03f));
+    p = fma2(p, r, bc2(4.1666666666666667e-02f));
+    p = fma2(p, r, bc2(1.6666666666666667e-01f));
+    p = fma2(p, r, bc2(0.5f));
+    p = fma2(p, r, bc2(1.0f));
+    p = fma2(p, r, bc2(1.0f));
+    float pl, ph, tl, th;
+    x2_split(p, pl, ph);
+    x2_split(t, tl, th);
+    e0 = __int_as_float(__float_as_int(pl) + (int)((uint32_t)__float_as_int(tl) << 23));
+    e1 = __int_as_float(__float_as_int(ph) + (int)((uint32_t)__float_as_int(th) << 23));
+}
+
+// exponent of a staged record at both pixel samples (the contract's
+// operation sequence, as exponent_at)
+__device__ __forceinline__ f32x2 exponent_x2(const RecX2 &R, f32x2 pxf, f32x2 pyf, f32x2 &dx, f32x2 &h, f32x2 &ky)
+{
+    dx = sub2(R.uv.x, pxf);
+    const f32x2 dy = sub2(R.uv.y, pyf);
+    h = fma2(R.ab.x, dx, mul2(R.ab.y, dy));
+    ky = mul2(R.co.x, dy);
+    return fma2(h, dx, mul2(ky, dy));
+}
+
 // forward variants (registration mode): exposure compensation, and the
 // count of pairs that pass the alpha test (statistics runs only: the counter
 // costs the common variant a register)
@@ -319,6 +410,224 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Registration forward with two pixels per thread: 128 threads per 16x16
+// tile, warp w on the 8x8 quadrant (w & 1, w >> 1), lane -> column lane & 7,
+// rows lane >> 3 and + 4 (the adjoint's layout), both pixels of a thread
+// walked with packed operations.  A pixel's early exits and its stop become
+// masks: a pair that fails the alpha test, or that would take T below t_min
+// (the pixel is then done), enters the sums with weight 0 and leaves T and
+// `last` as they are, so every output is the one-pixel walk's.  Records are
+// staged 256 at a time (two per thread) as RecX2 plus the exponent cutoff,
+// which only the warp cull uses: a pair below it fails the alpha test.
+// ---------------------------------------------------------------------------
+constexpr int kFwd2Threads = 128, kFwd2Batch = 256;
+
+template <int X>
+__device__ __forceinline__ void fwd_tile2(const gsl::RasterArgs &a, const uint32_t t)
+{
+    __shared__ RecX2 s_r[kFwd2Batch];
+    __shared__ float s_cut[kFwd2Batch];
+    __shared__ uint8_t s_sel[4][kFwd2Batch];
+    __shared__ float s_red[4], s_ea[4], s_eb[4];
+    __shared__ int s_pairs[4], s_contrib[4];
+    const uint32_t vp = a.tile_vp[t];
+    const uint2 rg = a.ranges[t];
+    uint32_t v0[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+        v0[r] = rg.x + threadIdx.x + r * kFwd2Threads < rg.y ? a.vals[rg.x + threadIdx.x + r * kFwd2Threads] : 0u;
+    const VpDesc &d = a.vps[vp];
+    auto stage = [&](int slot, uint32_t v) {
+        const float4 *R = a.rec + 3 * (size_t)v;
+        const float4 q0 = R[0], q1 = R[1], q2 = R[2];
+        stage_x2(s_r[slot], q0, q1, q2, q1.y);
+        s_cut[slot] = stage_cutoff(q1, a).w;
+    };
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+        if (rg.x + threadIdx.x + r * kFwd2Threads < rg.y)
+            stage(threadIdx.x + r * kFwd2Threads, v0[r]);
+    const uint32_t lt = t - d.tile_base;
+    const int tx = (int)(lt % (uint32_t)d.TX), ty = (int)(lt / (uint32_t)d.TX);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wx = tx * kTile + (warp & 1) * 8, wy = ty * kTile + (warp >> 1) * 8;
+    const int px = wx + (lane & 7), py0 = wy + (lane >> 3), py1 = py0 + 4;
+    const bool in0 = px < d.W && py0 < d.H, in1 = px < d.W && py1 < d.H;
+    const f32x2 pxf = bc2((float)px + 0.5f), pyf = x2((float)py0 + 0.5f, (float)py1 + 0.5f);
+    const float xa = (float)wx + 0.5f, ya = (float)wy + 0.5f;
+    const bool cull = a.alpha_min > 0.0f;
+    f32x2 T = bc2(1.0f), C0 = bc2(0.0f), C1 = bc2(0.0f), C2 = bc2(0.0f), D = bc2(0.0f);
+    int last0 = 0, last1 = 0, nc = 0;
+    bool done0 = !in0, done1 = !in1;
+    for (uint32_t b = rg.x; b < rg.y; b += kFwd2Batch) {
+        if (b != rg.x) {
+            if (__syncthreads_count(done0 && done1) == kFwd2Threads)
+                break;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const uint32_t idx = b + threadIdx.x + r * kFwd2Threads;
+                if (idx < rg.y)
+                    stage(threadIdx.x + r * kFwd2Threads, a.vals[idx]);
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)kFwd2Batch, rg.y - b);
+        int nsel = 0;
+        if (!__all_sync(0xffffffffu, done0 && done1)) {
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                const int j = j0 + lane;
+                bool keep = false;
+                if (j < cnt) {
+                    const float4 *Xj = reinterpret_cast<const float4 *>(&s_r[j]);
+                    const float4 uv = Xj[0], ab = Xj[1];
+                    keep = !cull || patch_may_hit(make_float4(uv.x, uv.z, ab.x, ab.z), Xj[2].x, s_cut[j], xa,
+                                                  xa + 7.0f, ya, ya + 7.0f);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep)
+                    s_sel[warp][nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
+                nsel += __popc(m);
+            }
+            __syncwarp();
+        }
+        if (!(done0 && done1)) {
+            const int base = (int)(b - rg.x) + 1;
+            for (int k = 0; k < nsel; ++k) {
+                const int j = s_sel[warp][k];
+                const RecX2 &R = s_r[j];
+                f32x2 dx, h, ky;
+                float p0, p1, e0, e1;
+                x2_split(exponent_x2(R, pxf, pyf, dx, h, ky), p0, p1);
+                exp_ct_nonpos_x2(p0, p1, e0, e1);
+                float x0, x1;
+                x2_split(mul2(R.co.y, x2(e0, e1)), x0, x1);
+                const float al0 = x0 > a.alpha_max ? a.alpha_max : x0;
+                const float al1 = x1 > a.alpha_max ? a.alpha_max : x1;
+                const bool ok0 = !done0 && !(p0 > 0.0f) && !(al0 < a.alpha_min);
+                const bool ok1 = !done1 && !(p1 > 0.0f) && !(al1 < a.alpha_min);
+                float tn0, tn1;
+                x2_split(mul2(T, sub2(bc2(1.0f), x2(ok0 ? al0 : 0.0f, ok1 ? al1 : 0.0f))), tn0, tn1);
+                const bool st0 = ok0 && tn0 < a.t_min, st1 = ok1 && tn1 < a.t_min;
+                const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
+                done0 |= st0;
+                done1 |= st1;
+                const f32x2 w = mul2(x2(c0 ? al0 : 0.0f, c1 ? al1 : 0.0f), T);
+                C0 = fma2(R.zr.y, w, C0);
+                C1 = fma2(R.gb.x, w, C1);
+                C2 = fma2(R.gb.y, w, C2);
+                D = fma2(R.zr.x, w, D);
+                float T0, T1;
+                x2_split(T, T0, T1);
+                T = x2(c0 ? tn0 : T0, c1 ? tn1 : T1);
+                last0 = c0 ? base + j : last0;
+                last1 = c1 ? base + j : last1;
+                if (X & kFwdCount)
+                    nc += (int)c0 + (int)c1;
+                if (done0 && done1)
+                    break;
+            }
+        }
+    }
+    // registration: fused L1 colour + L1 depth loss and its sign code, per pixel
+    constexpr bool EXPO = (X & kFwdExposure) != 0;
+    const bool expo = EXPO && d.exposure;
+    const float gain = expo ? a.expo32[2 * vp] : 1.0f;
+    const float off_b = expo ? a.expo32[2 * vp + 1] : 0.0f;
+    float lsum = 0.0f, ga = 0.0f, gb = 0.0f;
+    float Tk[2], C0k[2], C1k[2], C2k[2], Dk[2];
+    x2_split(T, Tk[0], Tk[1]);
+    x2_split(C0, C0k[0], C0k[1]);
+    x2_split(C1, C1k[0], C1k[1]);
+    x2_split(C2, C2k[0], C2k[1]);
+    x2_split(D, Dk[0], Dk[1]);
+    const int lastk[2] = {last0, last1};
+    const bool ink[2] = {in0, in1};
+    const int pyk[2] = {py0, py1};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (!ink[k])
+            continue;
+        const int64_t HW = (int64_t)d.W * d.H;
+        const int64_t off = (int64_t)pyk[k] * d.W + px;
+        const int64_t pix = d.pix_base + off;
+        const float r0 = fmaf(Tk[k], a.bg[0], C0k[k]), r1 = fmaf(Tk[k], a.bg[1], C1k[k]),
+                    r2 = fmaf(Tk[k], a.bg[2], C2k[k]);
+        float o0 = r0, o1 = r1, o2 = r2;
+        if (expo) {
+            // exposure-compensated colour e^a I^ + b (Supp. B)
+            o0 = fmaf(gain, r0, off_b);
+            o1 = fmaf(gain, r1, off_b);
+            o2 = fmaf(gain, r2, off_b);
+        }
+        const float e0 = o0 - d.t_rgb[off], e1 = o1 - d.t_rgb[HW + off], e2 = o2 - d.t_rgb[2 * HW + off];
+        const float ed = Dk[k] - d.t_depth[off];
+        const float inv3 = d.inv3hw, inv1 = d.invhw;
+        lsum += (fabsf(e0) + fabsf(e1) + fabsf(e2)) * inv3 + fabsf(ed) * inv1;
+        auto sg = [](float e) -> uint32_t { return e > 0.0f ? 1u : (e < 0.0f ? 2u : 0u); };
+        a.code[pix] = (uint8_t)(sg(e0) | (sg(e1) << 2) | (sg(e2) << 4) | (sg(ed) << 6));
+        if (expo) {
+            // dL/da = sum_c dL/dI'_c e^a I^_c, dL/db = sum_c dL/dI'_c
+            auto sf = [](float e) -> float { return e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f); };
+            const float s0 = sf(e0), s1 = sf(e1), s2 = sf(e2);
+            ga += inv3 * gain * (s0 * r0 + s1 * r1 + s2 * r2);
+            gb += inv3 * (s0 + s1 + s2);
+        }
+        a.t_final[pix] = Tk[k];
+        a.last[pix] = lastk[k];
+        if (d.loss_kind == 1) {
+            // tracking loss: depth error (+inf without input depth) and colour L1 for its masks
+            a.trk_err[pix] = d.t_depth[off] > 0.0f ? fabsf(ed) : __uint_as_float(0x7f800000u);
+            a.trk_col[pix] = fabsf(e0) + fabsf(e1) + fabsf(e2);
+        }
+    }
+    lsum = warp_sum(lsum);
+    const int wl = warp_sum(last0 + last1);
+    if (expo) {
+        ga = warp_sum(ga);
+        gb = warp_sum(gb);
+    }
+    int wc = 0;
+    if (X & kFwdCount)
+        wc = warp_sum(nc);
+    if (lane == 0) {
+        s_red[warp] = lsum;
+        s_pairs[warp] = wl;
+        s_contrib[warp] = wc;
+        s_ea[warp] = ga;
+        s_eb[warp] = gb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float sl = 0.0f, sa = 0.0f, sb = 0.0f;
+        unsigned long long np = 0, ncs = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            sl += s_red[w];
+            np += (unsigned long long)s_pairs[w];
+            ncs += (unsigned long long)s_contrib[w];
+            sa += s_ea[w];
+            sb += s_eb[w];
+        }
+        a.tile_loss[t] = sl;
+        if (expo) {
+            a.tile_expo[2 * (size_t)t] = sa;
+            a.tile_expo[2 * (size_t)t + 1] = sb;
+        }
+        if (a.tile_pairs) {
+            atomicAdd(&a.tile_pairs[t], np);
+            if (X & kFwdCount)
+                atomicAdd(&a.tile_pairs[a.n_tiles + t], ncs);
+        }
+    }
+}
+
+template <int X>
+__global__ void __launch_bounds__(kFwd2Threads, 8) k_forward2(const gsl::RasterArgs a)
+{
+    fwd_tile2<X>(a, a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x);
+}
+
 // One CTA per tile (the grid covers every tile; tile_order, when given,
 // maps CTA -> tile).
 template <bool REG, int X>
@@ -355,18 +664,22 @@ __device__ __forceinline__ void run_queue(const gsl::RasterArgs &a, Tile &&tile)
     }
 }
 
-template <bool REG, int X>
-__global__ void __launch_bounds__(256, 6) k_forward_q(const gsl::RasterArgs a)
+template <int X>
+__global__ void __launch_bounds__(kFwd2Threads, 8) k_forward2_q(const gsl::RasterArgs a)
 {
-    run_queue(a, [&](uint32_t t) { fwd_tile<REG, X>(a, t); });
+    run_queue(a, [&](uint32_t t) { fwd_tile2<X>(a, t); });
 }
 
 // Warp sums of N (8 or 16) values per lane.  Each exchange over a lane bit
 // halves the values a lane carries (it keeps the half its partner sends
 // away), so log2(N) halving steps plus log2(32/N) plain butterflies need
 // N - 1 + log2(32/N) shuffles instead of 5 N.  On return lane l holds the
-// full sum of value index l / (32 / N).
-template <int N>
+// full sum of value index l / (32 / N).  Values NV..N-1 are zero padding:
+// in the first exchange the lanes that keep such an index would add two
+// zeros, so that step adds v[i] of both partners instead (no selects); the
+// lanes keeping index i + h >= NV then carry a sum that only ever meets
+// other padding indices, and their results are not used.
+template <int N, int NV = N>
 __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int lane)
 {
     int bit = 16;
@@ -375,6 +688,10 @@ __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int lane)
         const bool up = (lane & bit) != 0;
 #pragma unroll
         for (int i = 0; i < h; ++i) {
+            if (h == N / 2 && i + h >= NV) {
+                v[i] = v[i] + __shfl_xor_sync(0xffffffffu, v[i], bit);
+                continue;
+            }
             const float send = up ? v[i] : v[i + h];
             const float keep = up ? v[i + h] : v[i];
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
@@ -641,64 +958,10 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     return true;
 }
 
-// ---------------------------------------------------------------------------
-// Packed form of the registration adjoint's pair arithmetic.  A thread's two
-// pixels (same column, rows r and r + 4) go through one f32x2 operation per
-// step: add/sub/mul/fma.rn.f32x2 round each of the two lanes exactly as the
-// scalar .rn operation does, and issue once for both.  The pair's early
-// exits become masks (a pair that fails a test enters every sum with weight
-// 0, so every value is the scalar walk's, up to the sign of zero sums), and
-// the walk carries -Q and produces the negated screen-space gradient, so
-// that no operand needs a negation: -RN(a b) = RN(-a b) and -RN(a b + c) =
-// RN(-a b - c) exactly.
-// ---------------------------------------------------------------------------
-typedef unsigned long long f32x2;  // {lo, hi} = {pixel 0, pixel 1}
-__device__ __forceinline__ f32x2 x2(float lo, float hi)
-{
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void x2_split(f32x2 v, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
-{
-    f32x2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
-{
-    f32x2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
-{
-    f32x2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
-{
-    f32x2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f32x2 bc2(float v) { return x2(v, v); }
-
 // the two pixels' walk state: T, -Q and the loss gradient per pixel
 struct PixAdj2 {
     f32x2 pxf, pyf, T, nQ, gr, gg, gb, gd;
     int last0, last1;
-};
-
-// A staged record, each value twice ({v, v} pairs): {u, v}, {ca, cb},
-// {cc, -o}, {z, r}, {g, b}
-struct RecX2 {
-    ulonglong2 uv, ab, cn, zr, gb;
 };
 
 // Both pixels of one (thread, Gaussian) pair of the registration adjoint:
@@ -710,33 +973,14 @@ struct RecX2 {
 __device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, float amax, float namax,
                                            float namin, float (&ng)[6])
 {
-    const f32x2 dx = sub2(R.uv.x, P.pxf), dy = sub2(R.uv.y, P.pyf);
-    const f32x2 h = fma2(R.ab.x, dx, mul2(R.ab.y, dy));
-    const f32x2 ky = mul2(R.cn.x, dy);
-    const f32x2 power = fma2(h, dx, mul2(ky, dy));
-    float p0, p1;
+    f32x2 dx, h, ky;
+    const f32x2 power = exponent_x2(R, P.pxf, P.pyf, dx, h, ky);
+    float p0, p1, e0, e1;
     x2_split(power, p0, p1);
-    // the contract exponential (exp_ct_nonpos) of both exponents
-    const f32x2 xc = x2(fmaxf(p0, -80.0f), fmaxf(p1, -80.0f));
-    const f32x2 magic = bc2(12582912.0f);
-    const f32x2 t = fma2(xc, bc2(1.4426950408889634f), magic);
-    const f32x2 kf = sub2(t, magic);
-    f32x2 r = fma2(kf, bc2(-0.693145751953125f), xc);
-    r = fma2(kf, bc2(-1.428606820309417e-06f), r);
-    f32x2 p = fma2(bc2(1.3888888888888889e-03f), r, bc2(8.3333333333333333e-03f));
-    p = fma2(p, r, bc2(4.1666666666666667e-02f));
-    p = fma2(p, r, bc2(1.6666666666666667e-01f));
-    p = fma2(p, r, bc2(0.5f));
-    p = fma2(p, r, bc2(1.0f));
-    p = fma2(p, r, bc2(1.0f));
-    float pl, ph, tl, th;
-    x2_split(p, pl, ph);
-    x2_split(t, tl, th);
-    const float e0 = __int_as_float(__float_as_int(pl) + (int)((uint32_t)__float_as_int(tl) << 23));
-    const float e1 = __int_as_float(__float_as_int(ph) + (int)((uint32_t)__float_as_int(th) << 23));
+    exp_ct_nonpos_x2(p0, p1, e0, e1);
     // -x = (-o) e; clamped: x > alpha_max; -alpha; the alpha test
     float nx0, nx1;
-    x2_split(mul2(R.cn.y, x2(e0, e1)), nx0, nx1);
+    x2_split(mul2(R.co.y, x2(e0, e1)), nx0, nx1);
     const bool cl0 = nx0 < namax, cl1 = nx1 < namax;
     const float na0 = cl0 ? namax : nx0, na1 = cl1 ? namax : nx1;
     const bool live0 = jj < P.last0 && !(p0 > 0.0f) && !(na0 > namin);
@@ -811,12 +1055,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
             const float4 q0 = R[0], q1 = R[1], q2 = R[2];
             s0[threadIdx.x] = q0;
             s1[threadIdx.x] = stage_cutoff(q1, a);
-            float4 *X = reinterpret_cast<float4 *>(&s_x2[threadIdx.x]);
-            X[0] = make_float4(q0.x, q0.x, q0.y, q0.y);
-            X[1] = make_float4(q0.z, q0.z, q0.w, q0.w);
-            X[2] = make_float4(q1.x, q1.x, -q1.y, -q1.y);
-            X[3] = make_float4(q1.z, q1.z, q2.x, q2.x);
-            X[4] = make_float4(q2.y, q2.y, q2.z, q2.z);
+            stage_x2(s_x2[threadIdx.x], q0, q1, q2, -q1.y);
         } else {
             s0[threadIdx.x] = R[0];
             s1[threadIdx.x] = stage_cutoff(R[1], a);
@@ -941,7 +1180,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
 #pragma unroll
                 for (int k = 0; k < NP; ++k)
                     v[k] = k < NG ? g[k] : 0.0f;
-                const float sum = warp_sum_transpose<NP>(v, lane);
+                const float sum = warp_sum_transpose<NP, NG>(v, lane);
                 constexpr int L = 32 / NP;
                 const int k = lane / L;
                 if ((lane % L) == 0 && k < NG)
@@ -1022,9 +1261,9 @@ void launch_forward_reg(const gsl::RasterArgs &a, cudaStream_t s)
 {
     if (a.queue && g_fwd_q_ctas > 0) {
         cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
-        k_forward_q<true, X><<<(unsigned)std::min<uint32_t>(a.n_tiles, g_fwd_q_ctas), 256, 0, s>>>(a);
+        k_forward2_q<X><<<(unsigned)std::min<uint32_t>(a.n_tiles, g_fwd_q_ctas), kFwd2Threads, 0, s>>>(a);
     } else {
-        k_forward<true, X><<<a.n_tiles, 256, 0, s>>>(a);
+        k_forward2<X><<<a.n_tiles, kFwd2Threads, 0, s>>>(a);
     }
 }
 
@@ -1045,7 +1284,7 @@ void raster_init()
     int dev = 0, sms = 0, f = 0, b = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_forward_q<true, 0>, 256, 0) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_forward2_q<0>, kFwd2Threads, 0) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward2_q<true, false>, kBwd2Threads,
                                                       bwd2_smem<true, false>()) == cudaSuccess) {
         g_fwd_q_ctas = std::max(f, 1) * sms;

@@ -490,6 +490,34 @@ def test_registration_profile_and_stats(gs, ctx):
     assert all(v > 0 for v in st.phase_ms)
 
 
+@pytest.mark.parametrize("case", list(CASES) + ["room_full_size"])
+def test_registration_forward_matches_oracle(gs, ctx, case):
+    # the registration forward (tight lists, fused L1 loss) at the starting
+    # pose against the oracle: each keyframe's loss (the residual of a
+    # 0-iteration call) within the FP32 render's rounding, and the sum over
+    # every pixel of `last` (the list prefix each pixel walks, which the
+    # 1-iteration profile counts) exactly
+    import ctypes
+    gd, cams = room_case(2) if case == "room_full_size" else CASES[case]()
+    og = O.Gaussians.from_dict(gd)
+    g = gs.Gaussians.from_numpy(gd)
+    T = synth.about_point(synth.random_rigid(np.random.default_rng(17), 1.5, 0.02), O.centroid(og))
+    views, refs = [], []
+    for cam in cams:
+        tr = O.render(og, T, cam)
+        t_rgb, t_dep = tr["rgb"].astype(np.float32), tr["depth"].astype(np.float32)
+        views.append((cam, dev(t_rgb), dev(t_dep)))
+        refs.append((O.render(og, np.eye(3, 4), cam), t_rgb, t_dep))
+    _, _, eps, _ = gs.gs_register(ctx, g, g, [], views, 0)
+    for k, (r, t_rgb, t_dep) in enumerate(refs):
+        L, _, _ = O.loss(r["rgb"], r["depth"], t_rgb, t_dep)
+        assert eps[k] == pytest.approx(L, rel=1e-4), (k, eps[k], L)
+    gs.gs_register(ctx, g, g, [], views, 1, gs.default_options(profile=1))
+    st = gs.gsreg.gs_stats_t()
+    ctx.check(ctx._lib.gs_ctx_stats(ctx.handle, ctypes.byref(st)))
+    assert st.pairs == sum(int(r["last"].astype(np.int64).sum()) for r, _, _ in refs)
+
+
 def test_registration_room_full_size_trajectory_matches_oracle(gs, ctx):
     # room workload at full size (150k Gaussians, 1200x680), one keyframe per
     # direction, the first 3 iterations: same inputs (oracle-rendered
