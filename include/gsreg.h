@@ -492,9 +492,10 @@ gs_status_t gs_sort_u32(gs_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n
 /* FP32 peak probe (no counterpart in the paper; the denominator of the
  * compositing kernels' roofline): 8 independent FMA chains per thread,
  * 8 CTAs of 256 threads per SM, 4096 rounds, timed with CUDA events on
- * `stream`; *tflops = the best of five timed launches (2 flops per FMA),
- * *sm_count (may be NULL) = the device's multiprocessor count.
- * Synchronises `stream`. */
+ * `stream`, once with scalar FMAs and once with packed ones (fma.rn.f32x2,
+ * the compositing kernels' form); *tflops = the best of the ten timed
+ * launches (five per form, 2 flops per FMA), *sm_count (may be NULL) = the
+ * device's multiprocessor count.  Synchronises `stream`. */
 gs_status_t gs_probe_fp32(gs_ctx_t *ctx, double *tflops, int *sm_count, gs_stream_t stream);
 
 /* Self-test of the bounded device waits (no counterpart in the paper): one

@@ -555,23 +555,46 @@ __global__ void k_to_float(const double *in, float *out, int n)
 
 // FP32 peak probe: each thread runs 8 independent FMA chains for `iters`
 // rounds (enough independent work per warp to hide the FMA latency), and
-// writes one value so the chains are not removed.
+// writes one value so the chains are not removed.  PACKED: the chains are
+// pairs (fma.rn.f32x2, two FMAs per instruction), as the compositing
+// kernels issue them.
 constexpr int kProbeChains = 8;
+template <bool PACKED>
 __global__ void __launch_bounds__(256) k_fma_probe(float *sink, int iters, float a, float b)
 {
-    float x[kProbeChains];
+    float s = 0.0f;
+    if constexpr (PACKED) {
+        unsigned long long x[kProbeChains / 2], ab, bb;
+        asm("mov.b64 %0, {%1, %1};" : "=l"(ab) : "f"(a));
+        asm("mov.b64 %0, {%1, %1};" : "=l"(bb) : "f"(b));
 #pragma unroll
-    for (int k = 0; k < kProbeChains; ++k)
-        x[k] = (float)(threadIdx.x + k);
-    for (int i = 0; i < iters; ++i) {
+        for (int k = 0; k < kProbeChains / 2; ++k)
+            asm("mov.b64 %0, {%1, %2};" : "=l"(x[k]) : "f"((float)(threadIdx.x + 2 * k)), "f"((float)(threadIdx.x + 2 * k + 1)));
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int k = 0; k < kProbeChains / 2; ++k)
+                asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[k]) : "l"(ab), "l"(bb));
+        }
+#pragma unroll
+        for (int k = 0; k < kProbeChains / 2; ++k) {
+            float lo, hi;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[k]));
+            s += lo + hi;
+        }
+    } else {
+        float x[kProbeChains];
 #pragma unroll
         for (int k = 0; k < kProbeChains; ++k)
-            x[k] = fmaf(x[k], a, b);
-    }
-    float s = 0.0f;
+            x[k] = (float)(threadIdx.x + k);
+        for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < kProbeChains; ++k)
-        s += x[k];
+            for (int k = 0; k < kProbeChains; ++k)
+                x[k] = fmaf(x[k], a, b);
+        }
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k)
+            s += x[k];
+    }
     if (s == 1.2345f)  // never true for the arguments used: keeps the store conditional
         sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
@@ -1622,9 +1645,13 @@ gs_status_t gs_probe_fp32(gs_ctx_t *ctx, double *tflops, int *sm_count, gs_strea
     GS_CUDA(cudaEventCreate(&e1));
     float best = 0.0f;
     cudaError_t err = cudaSuccess;
-    for (int rep = 0; rep < 6 && err == cudaSuccess; ++rep) {
+    for (int rep = 0; rep < 12 && err == cudaSuccess; ++rep) {
         err = cudaEventRecord(e0, s);
-        k_fma_probe<<<blocks, threads, 0, s>>>(sink, iters, 0.9999999f, 1e-7f);
+        // scalar and packed launches alternate; each form's first launch warms up
+        if (rep % 2 == 0)
+            k_fma_probe<false><<<blocks, threads, 0, s>>>(sink, iters, 0.9999999f, 1e-7f);
+        else
+            k_fma_probe<true><<<blocks, threads, 0, s>>>(sink, iters, 0.9999999f, 1e-7f);
         ++gsl::g_launches;
         if (err == cudaSuccess)
             err = cudaEventRecord(e1, s);
@@ -1633,7 +1660,7 @@ gs_status_t gs_probe_fp32(gs_ctx_t *ctx, double *tflops, int *sm_count, gs_strea
         float ms = 0.0f;
         if (err == cudaSuccess)
             err = cudaEventElapsedTime(&ms, e0, e1);
-        if (err == cudaSuccess && rep > 0 && ms > 0.0f) {  // the first launch warms up
+        if (err == cudaSuccess && rep > 1 && ms > 0.0f) {
             const float tf = (float)((double)blocks * threads * iters * kProbeChains * 2.0 / (ms * 1e-3) / 1e12);
             best = std::max(best, tf);
         }

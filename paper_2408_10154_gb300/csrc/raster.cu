@@ -1,24 +1,25 @@
 // raster.cu -- front-to-back compositing (forward) and back-to-front adjoint
 // (backward) of the tiled 3D Gaussian splatting renderer.
 //
-// Forward: one CTA of 256 threads per 16x16 tile, one pixel per thread, each
-// warp on an 8x4 patch.  The tile's depth-sorted list is staged through
-// shared memory 256 records (48 B each) at a time, each warp iterates only
-// the records that can reach alpha_min in its patch, and the CTA stops once
-// every pixel is opaque (transmittance would drop below t_min).  In
-// registration mode it fuses the loss: it reads the keyframe's colour and
-// depth (exposure-compensated colour if asked), accumulates the tile's L1
-// loss and stores a 1-byte sign code of dL/dpixel next to the final
-// transmittance and the last-contributor index.  Nothing else per pixel is
-// saved; the adjoint recomputes alpha and recovers transmittance by division.
+// Forward: one CTA of 128 threads per 16x16 tile, two pixels per thread
+// (same column, 4 rows apart; each warp on an 8x8 patch), both walked with
+// packed f32x2 operations.  The tile's depth-sorted list is staged through
+// shared memory 256 records at a time, each warp iterates only the records
+// that can reach alpha_min in its patch, and the CTA stops once every pixel
+// is opaque (transmittance would drop below t_min).  In registration mode
+// it fuses the loss: it reads the keyframe's colour and depth
+// (exposure-compensated colour if asked), accumulates the tile's L1 loss and
+// stores a 1-byte sign code of dL/dpixel next to the final transmittance and
+// the last-contributor index.  Nothing else per pixel is saved; the adjoint
+// recomputes alpha and recovers transmittance by division.
 //
-// Adjoint: 128 threads per tile, two pixels per thread (8x8 warp patches).
-// Per (pixel, Gaussian) screen-space gradients are summed over each warp
-// with shuffles, over the tile's warps in shared memory (fixed order),
-// chained through the projection into a camera-frame twist per Gaussian,
-// accumulated per thread in FP32 with Kahan compensation and reduced per
-// tile by TwoSum butterflies to FP32 (hi, lo) pairs -- no global atomics,
-// bit-reproducible.
+// Adjoint: 128 threads per tile, two pixels per thread (8x8 warp patches;
+// packed operations in registration mode).  Per (pixel, Gaussian)
+// screen-space gradients are summed over each warp with shuffles, over the
+// tile's warps in shared memory (fixed order), chained through the
+// projection into a camera-frame twist per Gaussian, accumulated per thread
+// in FP32 with Kahan compensation and reduced per tile by TwoSum butterflies
+// to FP32 (hi, lo) pairs -- no global atomics, bit-reproducible.
 #include <float.h>
 
 #include <algorithm>
@@ -28,23 +29,6 @@
 namespace {
 
 using namespace gsk;
-
-struct PixelCoord {
-    int px, py;
-    bool inside;
-};
-
-__device__ __forceinline__ PixelCoord pixel_of(const VpDesc &d, uint32_t t)
-{
-    const uint32_t lt = t - d.tile_base;
-    const int tx = (int)(lt % (uint32_t)d.TX), ty = (int)(lt / (uint32_t)d.TX);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    PixelCoord p;
-    p.px = tx * kTile + (warp & 1) * 8 + (lane & 7);
-    p.py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
-    p.inside = p.px < d.W && p.py < d.H;
-    return p;
-}
 
 // exponent of record (q0 = u, v, ca, cb; cc) at the pixel sample (FP32
 // contract); h = ca dx + cb dy and ky = cc dy are its intermediates
@@ -56,12 +40,6 @@ __device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float p
     h = fma_rn(q0.z, dx, mul_rn(q0.w, dy));
     ky = mul_rn(cc, dy);
     return fma_rn(h, dx, mul_rn(ky, dy));
-}
-
-__device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float pxf, float pyf, float &dx, float &dy)
-{
-    float h, ky;
-    return exponent_at(q0, cc, pxf, pyf, dx, dy, h, ky);
 }
 
 // Warp-level cull of a staged record against the warp's pixel patch.  The
@@ -219,216 +197,25 @@ __device__ __forceinline__ f32x2 exponent_x2(const RecX2 &R, f32x2 pxf, f32x2 py
 // costs the common variant a register)
 constexpr int kFwdExposure = 1, kFwdCount = 2;
 
-// One tile of the forward (all 256 threads of the CTA take part).
+// ---------------------------------------------------------------------------
+// Forward, two pixels per thread: 128 threads per 16x16 tile, warp w on the
+// 8x8 quadrant (w & 1, w >> 1), lane -> column lane & 7, rows lane >> 3 and
+// + 4 (the adjoint's layout), both pixels of a thread walked with packed
+// operations.  A pixel's early exits and its stop are masks: a pair that
+// fails the alpha test, or that would take T below t_min (the pixel is then
+// done), enters the sums with weight 0 and leaves T and `last` as they are,
+// so every output is the one-pixel walk's.  Records are staged 256 at a
+// time (two per thread) as RecX2 plus the exponent cutoff, which only the
+// warp cull uses: a pair below it fails the alpha test.
+// ---------------------------------------------------------------------------
+constexpr int kFwdThreads = 128, kFwdBatch = 256;
+
 template <bool REG, int X>
 __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_t t)
 {
-    __shared__ float4 s0[256], s1[256], s2[256];
-    __shared__ uint8_t s_sel[8][256];  // per warp: batch positions that may hit its patch
-    __shared__ float s_red[8];
-    // The first batch is staged before any barrier (nothing has read the
-    // staging arrays yet) and its list entry is read before the tile's
-    // descriptor is used, so that the two chains of dependent loads (range,
-    // entry, record; keyframe index, descriptor) overlap.
-    const uint32_t vp = a.tile_vp[t];
-    const uint2 rg = a.ranges[t];
-    const bool staged0 = rg.x + threadIdx.x < rg.y;
-    const uint32_t v0 = staged0 ? a.vals[rg.x + threadIdx.x] : 0u;
-    const VpDesc &d = a.vps[vp];
-    const PixelCoord p = pixel_of(d, t);
-    auto stage = [&](uint32_t v) {
-        const float4 *R = a.rec + 3 * (size_t)v;
-        s0[threadIdx.x] = R[0];
-        s1[threadIdx.x] = stage_cutoff(R[1], a);
-        s2[threadIdx.x] = R[2];
-    };
-    if (staged0)
-        stage(v0);
-    const float pxf = (float)p.px + 0.5f, pyf = (float)p.py + 0.5f;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool cull = a.alpha_min > 0.0f;
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    int last = 0, n_contrib = 0;
-    bool done = !p.inside;
-    for (uint32_t b = rg.x; b < rg.y; b += 256) {
-        if (b != rg.x) {
-            if (__syncthreads_count(done) == 256)
-                break;
-            const uint32_t idx = b + threadIdx.x;
-            if (idx < rg.y)
-                stage(a.vals[idx]);
-        }
-        __syncthreads();
-        const int cnt = (int)min(256u, rg.y - b);
-        int nsel = 0;
-        if (!__all_sync(0xffffffffu, done)) {
-            // the warp's 8x4 patch of pixel samples (derived here: registers
-            // held across the pixel walk limit the CTAs per SM)
-            const float xa = pxf - (float)(lane & 7), ya = pyf - (float)(lane >> 3);
-            for (int j0 = 0; j0 < cnt; j0 += 32) {
-                const int j = j0 + lane;
-                const bool keep =
-                    j < cnt && (!cull || patch_may_hit(s0[j], s1[j].x, s1[j].w, xa, xa + 7.0f, ya, ya + 3.0f));
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
-                if (keep)
-                    s_sel[warp][nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
-                nsel += __popc(m);
-            }
-            __syncwarp();
-        }
-        if (!done) {
-            for (int k = 0; k < nsel; ++k) {
-                const int j = s_sel[warp][k];
-                const float4 q0 = s0[j];
-                const float4 q1 = s1[j];
-                float dx, dy;
-                const float power = exponent_at(q0, q1.x, pxf, pyf, dx, dy);
-                if (power > 0.0f || power < q1.w)
-                    continue;
-                const float x = mul_rn(q1.y, exp_ct_nonpos(power));
-                const float alpha = x > a.alpha_max ? a.alpha_max : x;
-                if (alpha < a.alpha_min)
-                    continue;
-                const float Tn = mul_rn(T, sub_rn(1.0f, alpha));
-                if (Tn < a.t_min) {
-                    done = true;
-                    break;
-                }
-                const float w = alpha * T;
-                const float4 q2 = s2[j];
-                C0 = fmaf(q2.x, w, C0);
-                C1 = fmaf(q2.y, w, C1);
-                C2 = fmaf(q2.z, w, C2);
-                D = fmaf(q1.z, w, D);
-                T = Tn;
-                last = (int)(b - rg.x) + j + 1;
-                if (X & kFwdCount)
-                    ++n_contrib;
-            }
-        }
-    }
-    const int64_t HW = (int64_t)d.W * d.H;
-    const int64_t off = (int64_t)p.py * d.W + p.px;
-    const int64_t pix = d.pix_base + off;
-    float o0 = fmaf(T, a.bg[0], C0), o1 = fmaf(T, a.bg[1], C1), o2 = fmaf(T, a.bg[2], C2);
-    if (!REG) {
-        if (p.inside) {
-            if (a.out_rgb) {
-                float *rgb = a.out_rgb + 3 * d.pix_base;
-                rgb[off] = o0;
-                rgb[HW + off] = o1;
-                rgb[2 * HW + off] = o2;
-            }
-            if (a.out_depth)
-                a.out_depth[pix] = D;
-            if (a.out_alpha)
-                a.out_alpha[pix] = 1.0f - T;
-            if (a.t_final)
-                a.t_final[pix] = T;
-            if (a.last)
-                a.last[pix] = last;
-        }
-        return;
-    }
-    // registration: fused L1 colour + L1 depth loss and its sign code
-    __shared__ int s_pairs[8], s_contrib[8];
-    __shared__ float s_ea[8], s_eb[8];
-    constexpr bool EXPO = (X & kFwdExposure) != 0;
-    float lsum = 0.0f, ga = 0.0f, gb = 0.0f;
-    const bool expo = EXPO && d.exposure;
-    const float gain = expo ? a.expo32[2 * a.tile_vp[t]] : 1.0f;
-    if (p.inside) {
-        const float r0 = o0, r1 = o1, r2 = o2;
-        if (expo) {
-            // exposure-compensated colour e^a I^ + b (Supp. B)
-            const float off_b = a.expo32[2 * a.tile_vp[t] + 1];
-            o0 = fmaf(gain, r0, off_b);
-            o1 = fmaf(gain, r1, off_b);
-            o2 = fmaf(gain, r2, off_b);
-        }
-        const float e0 = o0 - d.t_rgb[off], e1 = o1 - d.t_rgb[HW + off], e2 = o2 - d.t_rgb[2 * HW + off];
-        const float ed = D - d.t_depth[off];
-        const float inv3 = d.inv3hw, inv1 = d.invhw;
-        lsum = (fabsf(e0) + fabsf(e1) + fabsf(e2)) * inv3 + fabsf(ed) * inv1;
-        auto sg = [](float e) -> uint32_t { return e > 0.0f ? 1u : (e < 0.0f ? 2u : 0u); };
-        a.code[pix] = (uint8_t)(sg(e0) | (sg(e1) << 2) | (sg(e2) << 4) | (sg(ed) << 6));
-        if (expo) {
-            // dL/da = sum_c dL/dI'_c e^a I^_c, dL/db = sum_c dL/dI'_c
-            auto sf = [](float e) -> float { return e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f); };
-            const float s0 = sf(e0), s1 = sf(e1), s2 = sf(e2);
-            ga = inv3 * gain * (s0 * r0 + s1 * r1 + s2 * r2);
-            gb = inv3 * (s0 + s1 + s2);
-        }
-        a.t_final[pix] = T;
-        a.last[pix] = last;
-        if (d.loss_kind == 1) {
-            // tracking loss: depth error (+inf without input depth) and colour L1 for its masks
-            a.trk_err[pix] = d.t_depth[off] > 0.0f ? fabsf(ed) : __uint_as_float(0x7f800000u);
-            a.trk_col[pix] = fabsf(e0) + fabsf(e1) + fabsf(e2);
-        }
-    }
-    lsum = warp_sum(lsum);
-    const int wl = warp_sum(last);
-    if (expo) {
-        ga = warp_sum(ga);
-        gb = warp_sum(gb);
-    }
-    int wc = 0;
-    if (X & kFwdCount)
-        wc = warp_sum(n_contrib);
-    if ((threadIdx.x & 31) == 0) {
-        s_red[threadIdx.x >> 5] = lsum;
-        s_pairs[threadIdx.x >> 5] = wl;
-        s_contrib[threadIdx.x >> 5] = wc;
-        s_ea[threadIdx.x >> 5] = ga;
-        s_eb[threadIdx.x >> 5] = gb;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.0f, sa = 0.0f, sb = 0.0f;
-        unsigned long long np = 0, nc = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            s += s_red[w];
-            np += (unsigned long long)s_pairs[w];
-            nc += (unsigned long long)s_contrib[w];
-            sa += s_ea[w];
-            sb += s_eb[w];
-        }
-        a.tile_loss[t] = s;
-        if (expo) {
-            a.tile_expo[2 * (size_t)t] = sa;
-            a.tile_expo[2 * (size_t)t + 1] = sb;
-        }
-        if (a.tile_pairs) {
-            // reductions without a return (no load to wait for as the CTA
-            // ends); one writer per tile, integer sums: deterministic
-            atomicAdd(&a.tile_pairs[t], np);
-            if (X & kFwdCount)
-                atomicAdd(&a.tile_pairs[a.n_tiles + t], nc);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Registration forward with two pixels per thread: 128 threads per 16x16
-// tile, warp w on the 8x8 quadrant (w & 1, w >> 1), lane -> column lane & 7,
-// rows lane >> 3 and + 4 (the adjoint's layout), both pixels of a thread
-// walked with packed operations.  A pixel's early exits and its stop become
-// masks: a pair that fails the alpha test, or that would take T below t_min
-// (the pixel is then done), enters the sums with weight 0 and leaves T and
-// `last` as they are, so every output is the one-pixel walk's.  Records are
-// staged 256 at a time (two per thread) as RecX2 plus the exponent cutoff,
-// which only the warp cull uses: a pair below it fails the alpha test.
-// ---------------------------------------------------------------------------
-constexpr int kFwd2Threads = 128, kFwd2Batch = 256;
-
-template <int X>
-__device__ __forceinline__ void fwd_tile2(const gsl::RasterArgs &a, const uint32_t t)
-{
-    __shared__ RecX2 s_r[kFwd2Batch];
-    __shared__ float s_cut[kFwd2Batch];
-    __shared__ uint8_t s_sel[4][kFwd2Batch];
+    __shared__ RecX2 s_r[kFwdBatch];
+    __shared__ float s_cut[kFwdBatch];
+    __shared__ uint8_t s_sel[4][kFwdBatch];
     __shared__ float s_red[4], s_ea[4], s_eb[4];
     __shared__ int s_pairs[4], s_contrib[4];
     const uint32_t vp = a.tile_vp[t];
@@ -436,7 +223,7 @@ __device__ __forceinline__ void fwd_tile2(const gsl::RasterArgs &a, const uint32
     uint32_t v0[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-        v0[r] = rg.x + threadIdx.x + r * kFwd2Threads < rg.y ? a.vals[rg.x + threadIdx.x + r * kFwd2Threads] : 0u;
+        v0[r] = rg.x + threadIdx.x + r * kFwdThreads < rg.y ? a.vals[rg.x + threadIdx.x + r * kFwdThreads] : 0u;
     const VpDesc &d = a.vps[vp];
     auto stage = [&](int slot, uint32_t v) {
         const float4 *R = a.rec + 3 * (size_t)v;
@@ -446,8 +233,8 @@ __device__ __forceinline__ void fwd_tile2(const gsl::RasterArgs &a, const uint32
     };
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-        if (rg.x + threadIdx.x + r * kFwd2Threads < rg.y)
-            stage(threadIdx.x + r * kFwd2Threads, v0[r]);
+        if (rg.x + threadIdx.x + r * kFwdThreads < rg.y)
+            stage(threadIdx.x + r * kFwdThreads, v0[r]);
     const uint32_t lt = t - d.tile_base;
     const int tx = (int)(lt % (uint32_t)d.TX), ty = (int)(lt / (uint32_t)d.TX);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -460,19 +247,19 @@ __device__ __forceinline__ void fwd_tile2(const gsl::RasterArgs &a, const uint32
     f32x2 T = bc2(1.0f), C0 = bc2(0.0f), C1 = bc2(0.0f), C2 = bc2(0.0f), D = bc2(0.0f);
     int last0 = 0, last1 = 0, nc = 0;
     bool done0 = !in0, done1 = !in1;
-    for (uint32_t b = rg.x; b < rg.y; b += kFwd2Batch) {
+    for (uint32_t b = rg.x; b < rg.y; b += kFwdBatch) {
         if (b != rg.x) {
-            if (__syncthreads_count(done0 && done1) == kFwd2Threads)
+            if (__syncthreads_count(done0 && done1) == kFwdThreads)
                 break;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const uint32_t idx = b + threadIdx.x + r * kFwd2Threads;
+                const uint32_t idx = b + threadIdx.x + r * kFwdThreads;
                 if (idx < rg.y)
-                    stage(threadIdx.x + r * kFwd2Threads, a.vals[idx]);
+                    stage(threadIdx.x + r * kFwdThreads, a.vals[idx]);
             }
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)kFwd2Batch, rg.y - b);
+        const int cnt = (int)min((uint32_t)kFwdBatch, rg.y - b);
         int nsel = 0;
         if (!__all_sync(0xffffffffu, done0 && done1)) {
             for (int j0 = 0; j0 < cnt; j0 += 32) {
@@ -529,12 +316,6 @@ __device__ __forceinline__ void fwd_tile2(const gsl::RasterArgs &a, const uint32
             }
         }
     }
-    // registration: fused L1 colour + L1 depth loss and its sign code, per pixel
-    constexpr bool EXPO = (X & kFwdExposure) != 0;
-    const bool expo = EXPO && d.exposure;
-    const float gain = expo ? a.expo32[2 * vp] : 1.0f;
-    const float off_b = expo ? a.expo32[2 * vp + 1] : 0.0f;
-    float lsum = 0.0f, ga = 0.0f, gb = 0.0f;
     float Tk[2], C0k[2], C1k[2], C2k[2], Dk[2];
     x2_split(T, Tk[0], Tk[1]);
     x2_split(C0, C0k[0], C0k[1]);
@@ -544,11 +325,41 @@ __device__ __forceinline__ void fwd_tile2(const gsl::RasterArgs &a, const uint32
     const int lastk[2] = {last0, last1};
     const bool ink[2] = {in0, in1};
     const int pyk[2] = {py0, py1};
+    const int64_t HW = (int64_t)d.W * d.H;
+    if (!REG) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!ink[k])
+                continue;
+            const int64_t off = (int64_t)pyk[k] * d.W + px;
+            const int64_t pix = d.pix_base + off;
+            if (a.out_rgb) {
+                float *rgb = a.out_rgb + 3 * d.pix_base;
+                rgb[off] = fmaf(Tk[k], a.bg[0], C0k[k]);
+                rgb[HW + off] = fmaf(Tk[k], a.bg[1], C1k[k]);
+                rgb[2 * HW + off] = fmaf(Tk[k], a.bg[2], C2k[k]);
+            }
+            if (a.out_depth)
+                a.out_depth[pix] = Dk[k];
+            if (a.out_alpha)
+                a.out_alpha[pix] = 1.0f - Tk[k];
+            if (a.t_final)
+                a.t_final[pix] = Tk[k];
+            if (a.last)
+                a.last[pix] = lastk[k];
+        }
+        return;
+    }
+    // registration: fused L1 colour + L1 depth loss and its sign code, per pixel
+    constexpr bool EXPO = (X & kFwdExposure) != 0;
+    const bool expo = EXPO && d.exposure;
+    const float gain = expo ? a.expo32[2 * vp] : 1.0f;
+    const float off_b = expo ? a.expo32[2 * vp + 1] : 0.0f;
+    float lsum = 0.0f, ga = 0.0f, gb = 0.0f;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (!ink[k])
             continue;
-        const int64_t HW = (int64_t)d.W * d.H;
         const int64_t off = (int64_t)pyk[k] * d.W + px;
         const int64_t pix = d.pix_base + off;
         const float r0 = fmaf(Tk[k], a.bg[0], C0k[k]), r1 = fmaf(Tk[k], a.bg[1], C1k[k]),
@@ -622,19 +433,14 @@ __device__ __forceinline__ void fwd_tile2(const gsl::RasterArgs &a, const uint32
     }
 }
 
-template <int X>
-__global__ void __launch_bounds__(kFwd2Threads, 8) k_forward2(const gsl::RasterArgs a)
-{
-    fwd_tile2<X>(a, a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x);
-}
-
 // One CTA per tile (the grid covers every tile; tile_order, when given,
 // maps CTA -> tile).
 template <bool REG, int X>
-__global__ void __launch_bounds__(256, 6) k_forward(const gsl::RasterArgs a)
+__global__ void __launch_bounds__(kFwdThreads, 8) k_forward(const gsl::RasterArgs a)
 {
     fwd_tile<REG, X>(a, a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x);
 }
+
 
 // Persistent form: a grid of a few CTAs per SM, each CTA pulling the next
 // tile (in tile_order, or natural order) from the work queue a.queue (one
@@ -665,9 +471,9 @@ __device__ __forceinline__ void run_queue(const gsl::RasterArgs &a, Tile &&tile)
 }
 
 template <int X>
-__global__ void __launch_bounds__(kFwd2Threads, 8) k_forward2_q(const gsl::RasterArgs a)
+__global__ void __launch_bounds__(kFwdThreads, 8) k_forward_q(const gsl::RasterArgs a)
 {
-    run_queue(a, [&](uint32_t t) { fwd_tile2<X>(a, t); });
+    run_queue(a, [&](uint32_t t) { fwd_tile<true, X>(a, t); });
 }
 
 // Warp sums of N (8 or 16) values per lane.  Each exchange over a lane bit
@@ -1261,9 +1067,9 @@ void launch_forward_reg(const gsl::RasterArgs &a, cudaStream_t s)
 {
     if (a.queue && g_fwd_q_ctas > 0) {
         cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
-        k_forward2_q<X><<<(unsigned)std::min<uint32_t>(a.n_tiles, g_fwd_q_ctas), kFwd2Threads, 0, s>>>(a);
+        k_forward_q<X><<<(unsigned)std::min<uint32_t>(a.n_tiles, g_fwd_q_ctas), kFwdThreads, 0, s>>>(a);
     } else {
-        k_forward2<X><<<a.n_tiles, kFwd2Threads, 0, s>>>(a);
+        k_forward<true, X><<<a.n_tiles, kFwdThreads, 0, s>>>(a);
     }
 }
 
@@ -1284,7 +1090,7 @@ void raster_init()
     int dev = 0, sms = 0, f = 0, b = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_forward2_q<0>, kFwd2Threads, 0) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_forward_q<0>, kFwdThreads, 0) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward2_q<true, false>, kBwd2Threads,
                                                       bwd2_smem<true, false>()) == cudaSuccess) {
         g_fwd_q_ctas = std::max(f, 1) * sms;
@@ -1297,10 +1103,12 @@ void forward(const RasterArgs &a, bool registration, cudaStream_t s)
 {
     if (a.n_tiles == 0)
         return;
-    // (a two-pixels-per-thread forward measured slower: 0.82 vs 0.76 ms on
-    // the room workload; the early stop favours one pixel per thread)
+    // (one pixel per thread with scalar operations, 256-thread CTAs on 8x4
+    // warp patches: 0.551 against 0.447 ms on the room workload; without
+    // packed operations two pixels per thread had measured slower, 0.82
+    // against 0.76 ms, as the early stop favours one pixel per thread)
     if (!registration)
-        k_forward<false, 0><<<a.n_tiles, 256, 0, s>>>(a);
+        k_forward<false, 0><<<a.n_tiles, kFwdThreads, 0, s>>>(a);
     else if (a.exposure && a.count_contrib)
         launch_forward_reg<kFwdExposure | kFwdCount>(a, s);
     else if (a.exposure)
