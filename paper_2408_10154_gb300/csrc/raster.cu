@@ -144,20 +144,13 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
 }
 __device__ __forceinline__ f32x2 bc2(float v) { return x2(v, v); }
 
-// A staged record with each value twice ({v, v} pairs) for the packed
-// walks: {u, v}, {ca, cb}, {cc, o} (the adjoint stages -o), {z, r}, {g, b}
+// A record's values, each broadcast to both lanes ({v, v} pairs), for the
+// packed walks: {u, v}, {ca, cb}, {cc, o} (-o in the adjoint), {z, r}, {g, b}.
+// Built from the staged float4s as they are loaded (staging the pairs
+// themselves, 80 B a record, measured slower: more shared-memory loads).
 struct RecX2 {
     ulonglong2 uv, ab, co, zr, gb;
 };
-__device__ __forceinline__ void stage_x2(RecX2 &dst, const float4 &q0, const float4 &q1, const float4 &q2, float o)
-{
-    float4 *X = reinterpret_cast<float4 *>(&dst);
-    X[0] = make_float4(q0.x, q0.x, q0.y, q0.y);
-    X[1] = make_float4(q0.z, q0.z, q0.w, q0.w);
-    X[2] = make_float4(q1.x, q1.x, o, o);
-    X[3] = make_float4(q1.z, q1.z, q2.x, q2.x);
-    X[4] = make_float4(q2.y, q2.y, q2.z, q2.z);
-}
 
 // the contract exponential (exp_ct_nonpos) of both lanes of x
 __device__ __forceinline__ void exp_ct_nonpos_x2(float x0, float x1, float &e0, float &e1)
@@ -205,16 +198,16 @@ constexpr int kFwdExposure = 1, kFwdCount = 2;
 // fails the alpha test, or that would take T below t_min (the pixel is then
 // done), enters the sums with weight 0 and leaves T and `last` as they are,
 // so every output is the one-pixel walk's.  Records are staged 256 at a
-// time (two per thread) as RecX2 plus the exponent cutoff, which only the
-// warp cull uses: a pair below it fails the alpha test.
+// time (two per thread) with the exponent cutoff in the tile rectangle's
+// slot (stage_cutoff); only the warp cull uses it: a pair below it fails the
+// alpha test.
 // ---------------------------------------------------------------------------
 constexpr int kFwdThreads = 128, kFwdBatch = 256;
 
 template <bool REG, int X>
 __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_t t)
 {
-    __shared__ RecX2 s_r[kFwdBatch];
-    __shared__ float s_cut[kFwdBatch];
+    __shared__ float4 s0[kFwdBatch], s1[kFwdBatch], s2[kFwdBatch];
     __shared__ uint8_t s_sel[4][kFwdBatch];
     __shared__ float s_red[4], s_ea[4], s_eb[4];
     __shared__ int s_pairs[4], s_contrib[4];
@@ -227,9 +220,9 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
     const VpDesc &d = a.vps[vp];
     auto stage = [&](int slot, uint32_t v) {
         const float4 *R = a.rec + 3 * (size_t)v;
-        const float4 q0 = R[0], q1 = R[1], q2 = R[2];
-        stage_x2(s_r[slot], q0, q1, q2, q1.y);
-        s_cut[slot] = stage_cutoff(q1, a).w;
+        s0[slot] = R[0];
+        s1[slot] = stage_cutoff(R[1], a);
+        s2[slot] = R[2];
     };
 #pragma unroll
     for (int r = 0; r < 2; ++r)
@@ -266,10 +259,8 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                 const int j = j0 + lane;
                 bool keep = false;
                 if (j < cnt) {
-                    const float4 *Xj = reinterpret_cast<const float4 *>(&s_r[j]);
-                    const float4 uv = Xj[0], ab = Xj[1];
-                    keep = !cull || patch_may_hit(make_float4(uv.x, uv.z, ab.x, ab.z), Xj[2].x, s_cut[j], xa,
-                                                  xa + 7.0f, ya, ya + 7.0f);
+                    const float4 t1 = s1[j];
+                    keep = !cull || patch_may_hit(s0[j], t1.x, t1.w, xa, xa + 7.0f, ya, ya + 7.0f);
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (keep)
@@ -282,7 +273,13 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
             const int base = (int)(b - rg.x) + 1;
             for (int k = 0; k < nsel; ++k) {
                 const int j = s_sel[warp][k];
-                const RecX2 &R = s_r[j];
+                const float4 q0 = s0[j], q1 = s1[j], q2 = s2[j];
+                RecX2 R;
+                R.uv = make_ulonglong2(bc2(q0.x), bc2(q0.y));
+                R.ab = make_ulonglong2(bc2(q0.z), bc2(q0.w));
+                R.co = make_ulonglong2(bc2(q1.x), bc2(q1.y));
+                R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
+                R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
                 f32x2 dx, h, ky;
                 float p0, p1, e0, e1;
                 x2_split(exponent_x2(R, pxf, pyf, dx, h, ky), p0, p1);
@@ -834,9 +831,9 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     __shared__ float4 s0[kBwd2Chunk], s1[kBwd2Chunk], s2[kBwd2Chunk];
     __shared__ float4 s_x0[kBwd2Chunk], s_x1[kBwd2Chunk];  // the records' camera-frame mean and covariance
     // the registration adjoint walks both pixels of a thread with packed
-    // operations, on records staged with each value twice (RecX2)
+    // operations (the record's values broadcast to both lanes as loaded; o
+    // staged negated)
     constexpr bool PK = REG && !FULL && kBwdPPT == 2;
-    __shared__ RecX2 s_x2[PK ? kBwd2Chunk : 1];
     __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
     __shared__ int s_maxl[kBwd2Warps];
     __shared__ float s_tw[kBwd2Warps][6][2];
@@ -857,16 +854,12 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     // staging of one record of a chunk (thread i, chunk position i)
     auto stage = [&](uint32_t r) {
         const float4 *R = a.rec + 3 * (size_t)r;
-        if constexpr (PK) {
-            const float4 q0 = R[0], q1 = R[1], q2 = R[2];
-            s0[threadIdx.x] = q0;
-            s1[threadIdx.x] = stage_cutoff(q1, a);
-            stage_x2(s_x2[threadIdx.x], q0, q1, q2, -q1.y);
-        } else {
-            s0[threadIdx.x] = R[0];
-            s1[threadIdx.x] = stage_cutoff(R[1], a);
-            s2[threadIdx.x] = R[2];
-        }
+        s0[threadIdx.x] = R[0];
+        float4 q1 = stage_cutoff(R[1], a);
+        if (PK)
+            q1.y = -q1.y;
+        s1[threadIdx.x] = q1;
+        s2[threadIdx.x] = R[2];
         if (a.tile_twist) {
             // the camera-frame mean and covariance, staged with the record
             // (not read after the walk) so that these loads overlap
@@ -932,20 +925,21 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     if ((int)threadIdx.x < kBwd2Chunk)
         tw.zero();
     const int twist_warps = (min(maxl, kBwd2Chunk) + 31) / 32;
+    // the warp sums' slots start zeroed; the epilogue thread of chunk
+    // position i zeroes column i again after reading it, and no other column
+    // is ever written
+    static_assert(NG * kBwd2Warps * kBwdSlotRow % 4 == 0, "slots zeroed as float4");
+    for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwdSlotRow / 4; k += kBwd2Threads)
+        s_dyn[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int hi = maxl; hi > 0; hi -= kBwd2Chunk) {
         const int lo = max(hi - kBwd2Chunk, 0), cnt = hi - lo;
-        // a later chunk restages what the previous chunk's epilogue read; the
-        // first one follows the pixel-state barrier, and until the barrier
-        // below each thread writes only its own staging slots and zeroes
-        // slots nobody reads yet (hi is the same for the whole block)
-        if (hi != maxl)
-            __syncthreads();
-        // hi == n_list only for a first chunk the guess staged already
+        // Thread i stages chunk position i, which only its own epilogue of the
+        // previous chunk read, and every warp's walk of that chunk ended at
+        // its closing barrier: one barrier per chunk fewer than restaging
+        // behind a barrier of its own.  hi == n_list only for a first chunk
+        // the guess staged already.
         if (hi != n_list && (int)threadIdx.x < cnt)
             stage(a.vals[rg.x + lo + threadIdx.x]);
-        static_assert(NG * kBwd2Warps * kBwdSlotRow % 4 == 0, "slots zeroed as float4");
-        for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwdSlotRow / 4; k += kBwd2Threads)
-            s_dyn[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         __syncthreads();
         // this warp's pixels never reach past wl: skip the list tail
         const int wl = min(s_maxl[warp] - lo, cnt);
@@ -971,7 +965,14 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
                 g[k] = -0.0f;  // -0 + x == x for every x (not so +0): the first additions fold away
             bool contrib = false;
             if constexpr (PK) {
-                contrib = pix_adj_x2(P2, lo + j, s_x2[j], a.alpha_max, -a.alpha_max, -a.alpha_min, g);
+                const float4 q0 = s0[j], q1 = s1[j], q2 = s2[j];
+                RecX2 R;
+                R.uv = make_ulonglong2(bc2(q0.x), bc2(q0.y));
+                R.ab = make_ulonglong2(bc2(q0.z), bc2(q0.w));
+                R.co = make_ulonglong2(bc2(q1.x), bc2(q1.y));
+                R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
+                R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
+                contrib = pix_adj_x2(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
             } else {
                 const float4 q0 = s0[j];
                 const float4 q1 = s1[j];
@@ -1001,8 +1002,11 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
             for (int k = 0; k < NG; ++k) {
                 float s = -0.0f;
 #pragma unroll
-                for (int w = 0; w < kBwd2Warps; ++w)
-                    s += s_slots[(k * kBwd2Warps + w) * kBwdSlotRow + threadIdx.x];
+                for (int w = 0; w < kBwd2Warps; ++w) {
+                    float &slot = s_slots[(k * kBwd2Warps + w) * kBwdSlotRow + threadIdx.x];
+                    s += slot;
+                    slot = 0.0f;
+                }
                 G[k] = PK ? -s : s;  // the packed walk sums the negated gradient
                 any |= s != 0.0f;
             }
