@@ -269,7 +269,10 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
             }
             __syncwarp();
         }
-        if (!(done0 && done1)) {
+        // The walk is warp-uniform: every lane iterates until all of the
+        // warp's pixels are done (a done pixel's pairs are masked), so that
+        // the votes below see all 32 lanes.
+        if (!__all_sync(0xffffffffu, done0 && done1)) {
             const int base = (int)(b - rg.x) + 1;
             for (int k = 0; k < nsel; ++k) {
                 const int j = s_sel[warp][k];
@@ -290,9 +293,26 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                 const float al1 = x1 > a.alpha_max ? a.alpha_max : x1;
                 const bool ok0 = !done0 && !(p0 > 0.0f) && !(al0 < a.alpha_min);
                 const bool ok1 = !done1 && !(p1 > 0.0f) && !(al1 < a.alpha_min);
+                const f32x2 al = x2(ok0 ? al0 : 0.0f, ok1 ? al1 : 0.0f);
+                const f32x2 tn = mul2(T, sub2(bc2(1.0f), al));  // T itself where al = 0
                 float tn0, tn1;
-                x2_split(mul2(T, sub2(bc2(1.0f), x2(ok0 ? al0 : 0.0f, ok1 ? al1 : 0.0f))), tn0, tn1);
+                x2_split(tn, tn0, tn1);
                 const bool st0 = ok0 && tn0 < a.t_min, st1 = ok1 && tn1 < a.t_min;
+                if (!__any_sync(0xffffffffu, st0 || st1)) {
+                    // no pixel of the warp stops here (the common case)
+                    const f32x2 w = mul2(al, T);
+                    C0 = fma2(R.zr.y, w, C0);
+                    C1 = fma2(R.gb.x, w, C1);
+                    C2 = fma2(R.gb.y, w, C2);
+                    D = fma2(R.zr.x, w, D);
+                    T = tn;
+                    last0 = ok0 ? base + j : last0;
+                    last1 = ok1 ? base + j : last1;
+                    if (X & kFwdCount)
+                        nc += (int)ok0 + (int)ok1;
+                    continue;
+                }
+                // a stopping pixel is done: its pair adds nothing, T stays
                 const bool c0 = ok0 && !st0, c1 = ok1 && !st1;
                 done0 |= st0;
                 done1 |= st1;
@@ -308,7 +328,7 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                 last1 = c1 ? base + j : last1;
                 if (X & kFwdCount)
                     nc += (int)c0 + (int)c1;
-                if (done0 && done1)
+                if (__all_sync(0xffffffffu, done0 && done1))
                     break;
             }
         }
