@@ -50,7 +50,7 @@ FWD_FLOPS_CONTRIB = 41.0
 BWD_FLOPS_CONTRIB = 64.0
 # DRAM bytes per adjoint launch of the room workload from one ncu capture of
 # the current kernel; None while the kernel has changed since the capture
-BWD_TRAFFIC_BYTES = 185.572096e6
+BWD_TRAFFIC_BYTES = None
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -315,7 +315,8 @@ def run_ours(args):
                 "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
                 "traffic": BWD_TRAFFIC_BYTES if names[dom] == "backward" else None,
                 "flops_per_launch": flops,
-                "peak_source": "measured: FMA-loop probe (gs_probe_fp32) on this GPU, %d SMs" % sms,
+                "peak_source": "measured: FMA-loop probe (gs_probe_fp32, scalar and packed f32x2 FMAs) on this GPU, "
+                               "%d SMs" % sms,
                 "peak_derived": derived_fp32,
                 "frac_of_derived": achieved / derived_fp32}
     else:
