@@ -48,8 +48,10 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # culls are), not counted.
 FWD_FLOPS_CONTRIB = 41.0
 BWD_FLOPS_CONTRIB = 64.0
-# DRAM bytes per adjoint launch of the room workload from one ncu capture of
-# the current kernel; None while the kernel has changed since the capture
+# DRAM bytes per launch of the room workload from one ncu capture of the
+# current kernel (the fused forward + adjoint that the timed calls run, and
+# the two-kernel adjoint); None while the kernel has changed since the capture
+FB_TRAFFIC_BYTES = None
 BWD_TRAFFIC_BYTES = None
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -307,18 +309,27 @@ def run_ours(args):
     probe_tflops, sms = gs.gs_probe_fp32(ctx)
     derived_fp32 = sms * FP32_LANES * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
     peak_fp32 = probe_tflops
-    if names[dom] in ("backward", "forward"):
-        fc = BWD_FLOPS_CONTRIB if names[dom] == "backward" else FWD_FLOPS_CONTRIB
+    # with fused compositing (the default for the registration loss) the
+    # forward phase is the one kernel k_fwdbwd and the backward phase is empty
+    fused = bool(opt.fuse_compositing)
+    peak_source = ("measured: FMA-loop probe (gs_probe_fp32, scalar and packed f32x2 FMAs) on this GPU, "
+                   "%d SMs" % sms)
+
+    def alu_roof(kernel, fc, ms, traffic):
         flops = fc * contrib_per_launch
-        achieved = flops / (per_launch_ms[dom] / 1000.0) / 1e12
-        roof = {"kernel": "k_backward2" if names[dom] == "backward" else "k_forward", "bound": "alu",
-                "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
-                "traffic": BWD_TRAFFIC_BYTES if names[dom] == "backward" else None,
-                "flops_per_launch": flops,
-                "peak_source": "measured: FMA-loop probe (gs_probe_fp32, scalar and packed f32x2 FMAs) on this GPU, "
-                               "%d SMs" % sms,
-                "peak_derived": derived_fp32,
+        achieved = flops / (ms / 1000.0) / 1e12
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                "frac": achieved / peak_fp32, "traffic": traffic, "flops_per_launch": flops,
+                "ms_per_launch": float(ms), "peak_source": peak_source, "peak_derived": derived_fp32,
                 "frac_of_derived": achieved / derived_fp32}
+
+    if names[dom] in ("backward", "forward"):
+        if fused and names[dom] == "forward":
+            roof = alu_roof("k_fwdbwd", FWD_FLOPS_CONTRIB + BWD_FLOPS_CONTRIB, per_launch_ms[dom], FB_TRAFFIC_BYTES)
+        elif names[dom] == "backward":
+            roof = alu_roof("k_backward2", BWD_FLOPS_CONTRIB, per_launch_ms[dom], BWD_TRAFFIC_BYTES)
+        else:
+            roof = alu_roof("k_forward", FWD_FLOPS_CONTRIB, per_launch_ms[dom], None)
     else:
         hbm = pk.get("hbm_gbs", 6800.0)
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
@@ -341,6 +352,16 @@ def run_ours(args):
         hbm[name] = {"bytes_per_launch": nbytes, "ms_per_launch": float(ms), "achieved_gbs": gbs,
                      "peak_gbs": hbm_peak, "frac": gbs / hbm_peak}
     hbm["visible_records_at_start"] = vis
+    # the same edge with the forward and the adjoint as two kernels (one
+    # untimed profiled call; bit-identical results): their own times and
+    # the adjoint's roofline
+    two = None
+    if fused:
+        gs.gs_register(ctx, src, tgt, sv, tv, ITERS, gs.default_options(profile=1, fuse_compositing=0))
+        ph = np.array(list(stats().phase_ms)) / ITERS
+        two = {"phase_ms_per_iteration": {n: float(v) for n, v in zip(names, ph)},
+               "adjoint_roofline": alu_roof("k_backward2", BWD_FLOPS_CONTRIB, ph[3], BWD_TRAFFIC_BYTES),
+               "forward_roofline": alu_roof("k_forward", FWD_FLOPS_CONTRIB, ph[2], None)}
     hbm["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback 6800 GB/s"
     lat = sorted(times)
     out = {
@@ -356,6 +377,7 @@ def run_ours(args):
         "pairs_per_iteration": pairs_per_launch, "contributing_pairs_per_iteration": contrib_per_launch,
         "dups": int(dups),
         "roofline": roof,
+        "two_kernels": two,
         "hbm": hbm,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "bench_step": "one loop edge (100 registration steps): the bytes are per edge"},

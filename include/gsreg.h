@@ -151,6 +151,15 @@ typedef struct {
      * results are those of a run that did not outgrow them).  Finite and
      * in (0, 64]; below 1 the first attempt always outgrows its lists. */
     float list_headroom;
+    /* compositing of the registration iterations of gs_register* and the
+     * server: 1 = the forward and the adjoint of a tile in one CTA (one
+     * launch; the pixel state stays in registers), for problems whose
+     * keyframes all use the registration loss (the tracking loss needs every
+     * tile's forward before any adjoint and always runs them as two
+     * kernels); 0 = two kernels.  Results are bit-identical either way; with
+     * 1, the profile's forward phase holds the fused kernel and its backward
+     * phase is empty.  Default 1. */
+    int32_t fuse_compositing;
 } gs_options_t;
 
 /* Statistics of the last gs_register / gs_render call on a context. */

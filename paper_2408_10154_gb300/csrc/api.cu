@@ -200,6 +200,8 @@ gs_status_t check_options(gs_ctx *ctx, const gs_options_t *o)
         return fail(ctx, GS_ERR_INVALID_ARG, "tight_lists must be 0 or 1");
     if (!(o->list_headroom > 0.0f) || !(o->list_headroom <= 64.0f))
         return fail(ctx, GS_ERR_INVALID_ARG, "list_headroom must be in (0, 64]");
+    if (o->fuse_compositing != 0 && o->fuse_compositing != 1)
+        return fail(ctx, GS_ERR_INVALID_ARG, "fuse_compositing must be 0 or 1");
     if ((o->exposure != 0 && o->exposure != 1) || !(o->lr_exposure >= 0) || !std::isfinite(o->lr_exposure) ||
         (o->exposure && o->tracking_loss))
         return fail(ctx, GS_ERR_INVALID_ARG,
@@ -749,6 +751,7 @@ void gs_default_options(gs_options_t *o)
     o->tile_schedule = 0;
     o->tight_lists = 1;
     o->list_headroom = 1.5f;
+    o->fuse_compositing = 1;
     o->lr_final = 0.001f;
 }
 
@@ -1962,10 +1965,15 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
             r.vals = p.vals[c];
             r.tile_order = ordered ? order : nullptr;
             r.queue = persistent ? queue : nullptr;
-            gsl::forward(r, true, st);
-            gsl::track_loss(ta, st);
-            mark(3, st);
-            gsl::backward(r, true, false, st);
+            if (opt->fuse_compositing && ta.n_track == 0) {
+                gsl::forward_backward(r, st);
+                mark(3, st);
+            } else {
+                gsl::forward(r, true, st);
+                gsl::track_loss(ta, st);
+                mark(3, st);
+                gsl::backward(r, true, false, st);
+            }
             mark(4, st);
             gsl::pose_update(pa, st);
             mark(5, st);
@@ -2656,9 +2664,13 @@ gs_status_t srv_replan(gs_server *srv, cudaStream_t s)
     GS_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     gsl::project(project_args(P, D, p, srv->pose32, &srv->opt, false), ctx->cap);
     r.vals = p.vals[run_bin(b, ctx->cap)];
-    gsl::forward(r, true, ctx->cap);
-    gsl::track_loss(ta, ctx->cap);
-    gsl::backward(r, true, false, ctx->cap);
+    if (srv->opt.fuse_compositing && ta.n_track == 0) {
+        gsl::forward_backward(r, ctx->cap);
+    } else {
+        gsl::forward(r, true, ctx->cap);
+        gsl::track_loss(ta, ctx->cap);
+        gsl::backward(r, true, false, ctx->cap);
+    }
     gsl::pose_update(pa, ctx->cap);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);

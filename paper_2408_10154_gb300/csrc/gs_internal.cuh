@@ -357,6 +357,11 @@ struct RasterArgs {
 void forward(const RasterArgs &a, bool registration, cudaStream_t s);
 void raster_init();  // one-time kernel attributes (before any graph capture)
 void backward(const RasterArgs &a, bool registration, bool full, cudaStream_t s);
+// Registration forward and adjoint fused per tile (the registration loss
+// only: no keyframe may use the tracking loss); the same values as
+// forward(a, true) followed by backward(a, true, false), without the
+// per-pixel T_final, last and code stores.
+void forward_backward(const RasterArgs &a, cudaStream_t s);
 
 // Tracking loss (Eq. 2, masks of Supp. A) of the tracking keyframes of a
 // plan: per keyframe the lower median of the valid depth errors (radix

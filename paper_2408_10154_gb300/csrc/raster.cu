@@ -152,6 +152,19 @@ struct RecX2 {
     ulonglong2 uv, ab, co, zr, gb;
 };
 
+// the two pixels' adjoint walk state: T, -Q and the loss gradient per pixel
+struct PixAdj2 {
+    f32x2 pxf, pyf, T, nQ, gr, gg, gb, gd;
+    int last0, last1;
+};
+
+// g . S of the background behind every Gaussian of a pixel (the colour
+// behind starts at T_final bg): the adjoint walk's first Q
+__device__ __forceinline__ float q_background(float gr, float gg, float gb, const float bg[3], float Tf)
+{
+    return (gr * bg[0] + gg * bg[1] + gb * bg[2]) * Tf;
+}
+
 // the contract exponential (exp_ct_nonpos) of both lanes of x
 __device__ __forceinline__ void exp_ct_nonpos_x2(float x0, float x1, float &e0, float &e1)
 {
@@ -204,10 +217,18 @@ constexpr int kFwdExposure = 1, kFwdCount = 2;
 // ---------------------------------------------------------------------------
 constexpr int kFwdThreads = 128, kFwdBatch = 256;
 
-template <bool REG, int X>
+// the adjoint half of the fused registration tile (defined with the adjoint)
+__device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t t, const VpDesc &d, uint2 rg,
+                                              float4 *s0, float4 *s1, float4 *s2, const uint32_t *s_v,
+                                              uint8_t *s_selw, float xa, float ya, PixAdj2 &P2, int maxl,
+                                              int wmaxl, const float *cc);
+
+template <bool REG, int X, bool FUSED = false>
 __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_t t)
 {
+    static_assert(REG || !FUSED, "only the registration forward is fused with the adjoint");
     __shared__ float4 s0[kFwdBatch], s1[kFwdBatch], s2[kFwdBatch];
+    __shared__ uint32_t s_v[FUSED ? kFwdBatch : 1];  // fused: the staged records' indices
     __shared__ uint8_t s_sel[4][kFwdBatch];
     __shared__ float s_red[4], s_ea[4], s_eb[4];
     __shared__ int s_pairs[4], s_contrib[4];
@@ -221,8 +242,16 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
     auto stage = [&](int slot, uint32_t v) {
         const float4 *R = a.rec + 3 * (size_t)v;
         s0[slot] = R[0];
-        s1[slot] = stage_cutoff(R[1], a);
-        s2[slot] = R[2];
+        const float4 q1 = R[1];
+        s1[slot] = stage_cutoff(q1, a);
+        float4 q2 = R[2];
+        if (FUSED) {
+            // the adjoint's -o in the slot of the tile rows, which compositing
+            // does not read
+            q2.w = -q1.y;
+            s_v[slot] = v;
+        }
+        s2[slot] = q2;
     };
 #pragma unroll
     for (int r = 0; r < 2; ++r)
@@ -237,6 +266,10 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
     const f32x2 pxf = bc2((float)px + 0.5f), pyf = x2((float)py0 + 0.5f, (float)py1 + 0.5f);
     const float xa = (float)wx + 0.5f, ya = (float)wy + 0.5f;
     const bool cull = a.alpha_min > 0.0f;
+    // fused: the keyframe's camera-frame pivot as floats, read early
+    float pivot = 0.0f;
+    if (FUSED && threadIdx.x < 3 && a.c_cam)
+        pivot = (float)a.c_cam[3 * vp + threadIdx.x];
     f32x2 T = bc2(1.0f), C0 = bc2(0.0f), C1 = bc2(0.0f), C2 = bc2(0.0f), D = bc2(0.0f);
     int last0 = 0, last1 = 0, nc = 0;
     bool done0 = !in0, done1 = !in1;
@@ -373,6 +406,8 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
     const float gain = expo ? a.expo32[2 * vp] : 1.0f;
     const float off_b = expo ? a.expo32[2 * vp + 1] : 0.0f;
     float lsum = 0.0f, ga = 0.0f, gb = 0.0f;
+    // fused: the loss gradient's signs per pixel (the sign code's values)
+    float sgk[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (!ink[k])
@@ -393,7 +428,15 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
         const float inv3 = d.inv3hw, inv1 = d.invhw;
         lsum += (fabsf(e0) + fabsf(e1) + fabsf(e2)) * inv3 + fabsf(ed) * inv1;
         auto sg = [](float e) -> uint32_t { return e > 0.0f ? 1u : (e < 0.0f ? 2u : 0u); };
-        a.code[pix] = (uint8_t)(sg(e0) | (sg(e1) << 2) | (sg(e2) << 4) | (sg(ed) << 6));
+        if (FUSED) {
+            auto sf = [](float e) -> float { return e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f); };
+            sgk[k][0] = sf(e0);
+            sgk[k][1] = sf(e1);
+            sgk[k][2] = sf(e2);
+            sgk[k][3] = sf(ed);
+        } else {
+            a.code[pix] = (uint8_t)(sg(e0) | (sg(e1) << 2) | (sg(e2) << 4) | (sg(ed) << 6));
+        }
         if (expo) {
             // dL/da = sum_c dL/dI'_c e^a I^_c, dL/db = sum_c dL/dI'_c
             auto sf = [](float e) -> float { return e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f); };
@@ -401,6 +444,8 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
             ga += inv3 * gain * (s0 * r0 + s1 * r1 + s2 * r2);
             gb += inv3 * (s0 + s1 + s2);
         }
+        if (FUSED)
+            continue;
         a.t_final[pix] = Tk[k];
         a.last[pix] = lastk[k];
         if (d.loss_kind == 1) {
@@ -418,6 +463,20 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
     int wc = 0;
     if (X & kFwdCount)
         wc = warp_sum(nc);
+    // fused: the warps' last contributors and the pivot behind the same barrier
+    __shared__ int s_maxl[FUSED ? 4 : 1];
+    __shared__ float s_cc[3];
+    int wmaxl = 0;
+    if (FUSED) {
+        wmaxl = max(last0, last1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            wmaxl = max(wmaxl, __shfl_xor_sync(0xffffffffu, wmaxl, o));
+        if (lane == 0)
+            s_maxl[warp] = wmaxl;
+        if (threadIdx.x < 3)
+            s_cc[threadIdx.x] = pivot;
+    }
     if (lane == 0) {
         s_red[warp] = lsum;
         s_pairs[warp] = wl;
@@ -447,6 +506,37 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
             if (X & kFwdCount)
                 atomicAdd(&a.tile_pairs[a.n_tiles + t], ncs);
         }
+    }
+    if constexpr (FUSED) {
+        // the adjoint's state from this thread's own two pixels, as
+        // pix_adj_init derives it from the stored T_final, last and code
+        int maxl = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            maxl = max(maxl, s_maxl[w]);
+        const float cc[3] = {s_cc[0], s_cc[1], s_cc[2]};
+        const float inv3 = expo ? d.inv3hw * gain : d.inv3hw, inv1 = d.invhw;
+        float g[2][4], q[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            g[k][0] = sgk[k][0] * inv3;
+            g[k][1] = sgk[k][1] * inv3;
+            g[k][2] = sgk[k][2] * inv3;
+            g[k][3] = sgk[k][3] * inv1;
+            q[k] = q_background(g[k][0], g[k][1], g[k][2], a.bg, Tk[k]);
+        }
+        PixAdj2 P2;
+        P2.pxf = pxf;
+        P2.pyf = pyf;
+        P2.T = T;
+        P2.nQ = x2(-q[0], -q[1]);
+        P2.gr = x2(g[0][0], g[1][0]);
+        P2.gg = x2(g[0][1], g[1][1]);
+        P2.gb = x2(g[0][2], g[1][2]);
+        P2.gd = x2(g[0][3], g[1][3]);
+        P2.last0 = last0;
+        P2.last1 = last1;
+        fused_adjoint(a, t, d, rg, s0, s1, s2, s_v, s_sel[warp], xa, ya, P2, maxl, wmaxl, cc);
     }
 }
 
@@ -548,11 +638,12 @@ static_assert(kBwdPPT * kBwdRowStep == 8 && kTile % kBwdPatchW == 0, "warp patch
 // low-order part is carried in c; the true sum is s - c), kept in shared
 // memory as [2 k + (0: s, 1: c)][thread]: they are touched once per record
 // at the end of a chunk, and in registers they would stay live across the
-// whole pixel walk.
-struct Twist6 {
-    float *base;  // the thread's column of the block's [12][kBwd2Threads] array
-    __device__ __forceinline__ float &s(int k) const { return base[(2 * k) * kBwd2Threads]; }
-    __device__ __forceinline__ float &c(int k) const { return base[(2 * k + 1) * kBwd2Threads]; }
+// whole pixel walk.  STRIDE: the columns of the block's [12][STRIDE] array.
+template <int STRIDE>
+struct Twist6T {
+    float *base;  // the thread's column
+    __device__ __forceinline__ float &s(int k) const { return base[(2 * k) * STRIDE]; }
+    __device__ __forceinline__ float &c(int k) const { return base[(2 * k + 1) * STRIDE]; }
     __device__ __forceinline__ void zero() const
     {
 #pragma unroll
@@ -567,6 +658,7 @@ struct Twist6 {
         s(k) = t;
     }
 };
+using Twist6 = Twist6T<kBwd2Threads>;
 
 // The tile's twist: each of the first nw warps (the ones whose threads
 // accumulated anything) reduces its lanes' compensated sums with TwoSum
@@ -575,8 +667,8 @@ struct Twist6 {
 // only zeros changes no bit: a TwoSum of (0, 0) leaves a pair as it is.
 // (No FP64 here: the FP64 pipe is a small fraction of the FP32 one, and
 // FP64 work in every warp kept it busy and lengthened every CTA's tail.)
-template <int WARPS>
-__device__ __forceinline__ void store_tile_twist(const Twist6 &tw, int nw, float (*s_tw)[6][2], float2 *out)
+template <int WARPS, typename Tw>
+__device__ __forceinline__ void store_tile_twist(const Tw &tw, int nw, float (*s_tw)[6][2], float2 *out)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < nw) {
@@ -613,8 +705,9 @@ __device__ __forceinline__ void store_tile_twist(const Twist6 &tw, int nw, float
 // about cc (camera frame), added to tw.  G = {dL/du, dL/dv,
 // 2 dL/dSigma2D_00, 2 dL/dSigma2D_01, 2 dL/dSigma2D_11, dL/dz, ...} (the 2D
 // covariance is the dilated one; dilation is constant).
+template <typename Tw>
 __device__ __forceinline__ void chain_twist(const float *G, const float4 &q1, const float4 &x0, const float4 &x1,
-                                            float fx, float fy, const float *cc, const Twist6 &tw)
+                                            float fx, float fy, const float *cc, const Tw &tw)
 {
     using S = float;
     const S mx = x0.x, my = x0.y, mz = q1.z;
@@ -721,7 +814,7 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
         }
     }
     P.T = P.Tf;
-    P.Q = (P.gr * bg[0] + P.gg * bg[1] + P.gb * bg[2]) * P.Tf;  // the background behind everything (depth 0)
+    P.Q = q_background(P.gr, P.gg, P.gb, bg, P.Tf);  // the background behind everything (depth 0)
     P.ga_tf = ga * P.Tf;
 }
 
@@ -780,12 +873,6 @@ __device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0
     P.T = Ti;
     return true;
 }
-
-// the two pixels' walk state: T, -Q and the loss gradient per pixel
-struct PixAdj2 {
-    f32x2 pxf, pyf, T, nQ, gr, gg, gb, gd;
-    int last0, last1;
-};
 
 // Both pixels of one (thread, Gaussian) pair of the registration adjoint:
 // the contract's decisions (the alpha test decides alone: the exponent
@@ -1058,6 +1145,141 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2_q(co
     run_queue(a, [&](uint32_t t) { bwd_tile<REG, FULL>(a, t); });
 }
 
+// The adjoint half of the fused registration tile (k_fwdbwd): the walk of
+// bwd_tile's packed registration path on the forward's pixels and staging.
+// A list the forward staged whole (n_list <= kFwdBatch) is walked from
+// there, chunk position j at list position lo + j; a longer one is
+// restaged chunk by chunk into the first kBwd2Chunk slots.  Only the
+// records' camera-frame mean and covariance are loaded per chunk.
+__device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t t, const VpDesc &d, uint2 rg,
+                                              float4 *s0, float4 *s1, float4 *s2, const uint32_t *s_v,
+                                              uint8_t *s_selw, float xa, float ya, PixAdj2 &P2, int maxl,
+                                              int wmaxl, const float *cc)
+{
+    constexpr int NG = 6;
+    extern __shared__ float4 s_dyn[];
+    float *const s_slots = reinterpret_cast<float *>(s_dyn);  // [NG][warps][kBwdSlotRow]
+    __shared__ float4 s_x0[kBwd2Chunk], s_x1[kBwd2Chunk];
+    __shared__ float s_acc[12][kBwd2Chunk];
+    __shared__ float s_tw[kBwd2Warps][6][2];
+    static_assert(kFwdThreads == kBwd2Threads && kBwd2Chunk <= kFwdBatch, "the fused tile shares the layout");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Twist6T<kBwd2Chunk> tw{&s_acc[0][threadIdx.x % kBwd2Chunk]};  // used by threads < kBwd2Chunk only
+    if ((int)threadIdx.x < kBwd2Chunk)
+        tw.zero();
+    static_assert(NG * kBwd2Warps * kBwdSlotRow % 4 == 0, "slots zeroed as float4");
+    for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwdSlotRow / 4; k += kBwd2Threads)
+        s_dyn[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const int n_list = (int)(rg.y - rg.x);
+    const bool whole = n_list <= kFwdBatch;
+    const bool cull = a.alpha_min > 0.0f;
+    const int twist_warps = (min(maxl, kBwd2Chunk) + 31) / 32;
+    for (int hi = maxl; hi > 0; hi -= kBwd2Chunk) {
+        const int lo = max(hi - kBwd2Chunk, 0), cnt = hi - lo;
+        const int sb = whole ? lo : 0;  // staging slot of chunk position 0
+        // thread i stages chunk position i (as in bwd_tile: only its own
+        // epilogue of the previous chunk read that slot)
+        if ((int)threadIdx.x < cnt) {
+            uint32_t r;
+            if (whole) {
+                r = s_v[lo + threadIdx.x];
+            } else {
+                r = a.vals[rg.x + lo + threadIdx.x];
+                const float4 *R = a.rec + 3 * (size_t)r;
+                s0[threadIdx.x] = R[0];
+                const float4 q1 = R[1];
+                s1[threadIdx.x] = stage_cutoff(q1, a);
+                float4 q2 = R[2];
+                q2.w = -q1.y;
+                s2[threadIdx.x] = q2;
+            }
+            if (a.tile_twist) {
+                s_x0[threadIdx.x] = a.aux[2 * (size_t)r];
+                s_x1[threadIdx.x] = a.aux[2 * (size_t)r + 1];
+            }
+        }
+        __syncthreads();
+        const int wl = min(wmaxl - lo, cnt);
+        int nsel = 0;
+        for (int j0 = 0; j0 < wl; j0 += 32) {
+            const int j = j0 + lane;
+            bool keep = false;
+            if (j < wl) {
+                const float4 t1 = s1[sb + j];
+                keep = !cull || patch_may_hit(s0[sb + j], t1.x, t1.w, xa, xa + 7.0f, ya, ya + 7.0f);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep)
+                s_selw[nsel + __popc(m & lanemask_lt())] = (uint8_t)j;
+            nsel += __popc(m);
+        }
+        __syncwarp();
+        for (int k = nsel - 1; k >= 0; --k) {
+            const int j = s_selw[k];
+            float g[NG];
+            const float4 q0 = s0[sb + j], q1 = s1[sb + j], q2 = s2[sb + j];
+            RecX2 R;
+            R.uv = make_ulonglong2(bc2(q0.x), bc2(q0.y));
+            R.ab = make_ulonglong2(bc2(q0.z), bc2(q0.w));
+            R.co = make_ulonglong2(bc2(q1.x), bc2(q2.w));
+            R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
+            R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
+            const bool contrib = pix_adj_x2(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
+            if (__any_sync(0xffffffffu, contrib)) {
+                float v[8];
+#pragma unroll
+                for (int k2 = 0; k2 < 8; ++k2)
+                    v[k2] = k2 < NG ? g[k2] : 0.0f;
+                const float sum = warp_sum_transpose<8, NG>(v, lane);
+                const int kk = lane / 4;
+                if ((lane % 4) == 0 && kk < NG)
+                    s_slots[(kk * kBwd2Warps + warp) * kBwdSlotRow + j] = sum;
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            float G[NG];
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+                float s = -0.0f;
+#pragma unroll
+                for (int w = 0; w < kBwd2Warps; ++w) {
+                    float &slot = s_slots[(k * kBwd2Warps + w) * kBwdSlotRow + threadIdx.x];
+                    s += slot;
+                    slot = 0.0f;
+                }
+                G[k] = -s;  // the packed walk sums the negated gradient
+                any |= s != 0.0f;
+            }
+            if (any && a.tile_twist)
+                chain_twist(G, s1[sb + threadIdx.x], s_x0[threadIdx.x], s_x1[threadIdx.x], d.fx, d.fy, cc, tw);
+        }
+    }
+    if (a.tile_twist)
+        store_tile_twist<kBwd2Warps>(tw, twist_warps, s_tw, a.tile_twist + (size_t)t * 6);
+}
+
+// The registration forward and adjoint of one tile in one CTA (the
+// registration loss of Sec. 3.2; not the tracking loss, whose per-keyframe
+// median needs every tile's forward first).  A thread holds the same two
+// pixels in both halves, so T_final, `last` and the loss signs stay in
+// registers instead of a round trip through HBM, and the adjoint needs no
+// set-up of its own (descriptor, pixel state, pivot, first chunk): one
+// launch in place of the forward and the adjoint, with the same values
+// bit for bit (the same operations in the same order).
+template <int X>
+__global__ void __launch_bounds__(kFwdThreads, 8) k_fwdbwd(const gsl::RasterArgs a)
+{
+    fwd_tile<true, X, true>(a, a.tile_order ? a.tile_order[blockIdx.x] : blockIdx.x);
+}
+
+template <int X>
+__global__ void __launch_bounds__(kFwdThreads, 8) k_fwdbwd_q(const gsl::RasterArgs a)
+{
+    run_queue(a, [&](uint32_t t) { fwd_tile<true, X, true>(a, t); });
+}
+
 template <bool REG, bool FULL>
 constexpr size_t bwd2_smem()
 {
@@ -1066,7 +1288,7 @@ constexpr size_t bwd2_smem()
 
 // CTAs of the persistent kernels: as many as can be resident at once
 // (occupancy x SMs), found once by raster_init
-int g_fwd_q_ctas = 0, g_bwd_q_ctas = 0;
+int g_fwd_q_ctas = 0, g_bwd_q_ctas = 0, g_fb_q_ctas = 0;
 
 // (a one-pixel-per-thread adjoint with 256-thread CTAs measured 2.00 ms
 // against 1.43 ms for this one on the room workload)
@@ -1084,6 +1306,18 @@ void launch_backward(const gsl::RasterArgs &a, cudaStream_t s)
     }
     k_backward2<REG, FULL><<<a.n_tiles, kBwd2Threads, bwd2_smem<REG, FULL>(), s>>>(a);
     ++gsl::g_launches;
+}
+
+template <int X>
+void launch_fwdbwd(const gsl::RasterArgs &a, cudaStream_t s)
+{
+    constexpr size_t smem = bwd2_smem<true, false>();
+    if (a.queue && g_fb_q_ctas > 0) {
+        cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
+        k_fwdbwd_q<X><<<(unsigned)std::min<uint32_t>(a.n_tiles, g_fb_q_ctas), kFwdThreads, smem, s>>>(a);
+    } else {
+        k_fwdbwd<X><<<a.n_tiles, kFwdThreads, smem, s>>>(a);
+    }
 }
 
 template <int X>
@@ -1111,14 +1345,17 @@ void raster_init()
                          (int)bwd2_smem<false, true>());
     cudaFuncSetAttribute(k_backward2_q<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)bwd2_smem<true, false>());
-    int dev = 0, sms = 0, f = 0, b = 0;
+    int dev = 0, sms = 0, f = 0, b = 0, fb = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_forward_q<0>, kFwdThreads, 0) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward2_q<true, false>, kBwd2Threads,
-                                                      bwd2_smem<true, false>()) == cudaSuccess) {
+                                                      bwd2_smem<true, false>()) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fb, k_fwdbwd_q<0>, kFwdThreads, bwd2_smem<true, false>()) ==
+            cudaSuccess) {
         g_fwd_q_ctas = std::max(f, 1) * sms;
         g_bwd_q_ctas = std::max(b, 1) * sms;
+        g_fb_q_ctas = std::max(fb, 1) * sms;
     }
     cudaGetLastError();
 }
@@ -1154,6 +1391,21 @@ void backward(const RasterArgs &a, bool registration, bool full, cudaStream_t s)
         launch_backward<false, true>(a, s);
     else
         launch_backward<false, false>(a, s);
+}
+
+void forward_backward(const RasterArgs &a, cudaStream_t s)
+{
+    if (a.n_tiles == 0)
+        return;
+    if (a.exposure && a.count_contrib)
+        launch_fwdbwd<kFwdExposure | kFwdCount>(a, s);
+    else if (a.exposure)
+        launch_fwdbwd<kFwdExposure>(a, s);
+    else if (a.count_contrib)
+        launch_fwdbwd<kFwdCount>(a, s);
+    else
+        launch_fwdbwd<0>(a, s);
+    ++g_launches;
 }
 
 }  // namespace gsl

@@ -55,7 +55,8 @@ class gs_options_t(ctypes.Structure):
                 ("adam_eps", ctypes.c_float), ("lr_final", ctypes.c_float), ("profile", ctypes.c_int32),
                 ("tracking_loss", ctypes.c_int32), ("lambda_c", ctypes.c_float), ("exposure", ctypes.c_int32),
                 ("lr_exposure", ctypes.c_float), ("tile_schedule", ctypes.c_int32),
-                ("tight_lists", ctypes.c_int32), ("list_headroom", ctypes.c_float)]
+                ("tight_lists", ctypes.c_int32), ("list_headroom", ctypes.c_float),
+                ("fuse_compositing", ctypes.c_int32)]
 
 
 class gs_stats_t(ctypes.Structure):

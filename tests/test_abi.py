@@ -64,7 +64,7 @@ def test_structs_match_the_library(lib):
     assert lib.gs_abi_sizes(sizes, len(structs)) == len(structs)
     for st, sz in zip(structs, sizes):
         assert ctypes.sizeof(st) == sz, st.__name__
-    assert ctypes.sizeof(gsreg.gs_camera_t) == 72 and ctypes.sizeof(gsreg.gs_options_t) == 4 * 24
+    assert ctypes.sizeof(gsreg.gs_camera_t) == 72 and ctypes.sizeof(gsreg.gs_options_t) == 4 * 25
 
 
 def test_context_without_device_is_rejected(lib):
