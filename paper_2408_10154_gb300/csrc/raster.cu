@@ -217,6 +217,22 @@ constexpr int kFwdExposure = 1, kFwdCount = 2;
 // ---------------------------------------------------------------------------
 constexpr int kFwdThreads = 128, kFwdBatch = 256;
 
+// Adjoint layout: kBwdPPT pixels per thread, each warp on a kBwdPatchW x 8
+// patch of its tile (lane -> column lane % kBwdPatchW, rows lane /
+// kBwdPatchW + k * kBwdRowStep for k < kBwdPPT).
+constexpr int kBwdPPT = 2;
+constexpr int kBwd2Threads = kTilePix / kBwdPPT;
+constexpr int kBwd2Warps = kBwd2Threads / 32;
+constexpr int kBwdPatchW = kBwdPPT == 2 ? 8 : 16;
+constexpr int kBwdRowStep = 32 / kBwdPatchW;
+constexpr int kBwd2Chunk = 64;
+// a row of per-record warp sums in shared memory: one float more than the
+// chunk, so that the lanes storing one record's sums of different values
+// (rows k * warps + warp, 65 floats apart) hit different banks
+constexpr int kBwdSlotRow = kBwd2Chunk + 1;
+constexpr int kBwd2MinBlocks = kBwdPPT == 2 ? 8 : 12;
+static_assert(kBwdPPT * kBwdRowStep == 8 && kTile % kBwdPatchW == 0, "warp patches of 8 rows tile the 16x16 tile");
+
 // the adjoint half of the fused registration tile (defined with the adjoint)
 __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t t, const VpDesc &d, uint2 rg,
                                               float4 *s0, float4 *s1, float4 *s2, const uint32_t *s_v,
@@ -476,6 +492,11 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
             s_maxl[warp] = wmaxl;
         if (threadIdx.x < 3)
             s_cc[threadIdx.x] = pivot;
+        // the adjoint's warp-sum slots, zeroed behind the same barrier
+        extern __shared__ float4 s_dyn[];
+        static_assert(6 * kBwd2Warps * kBwdSlotRow % 4 == 0, "slots zeroed as float4");
+        for (int k = threadIdx.x; k < 6 * kBwd2Warps * kBwdSlotRow / 4; k += kBwd2Threads)
+            s_dyn[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     if (lane == 0) {
         s_red[warp] = lsum;
@@ -618,21 +639,6 @@ __device__ __forceinline__ float warp_sum_transpose(float (&v)[N], int lane)
     return s;
 }
 
-// Adjoint layout: kBwdPPT pixels per thread, each warp on a kBwdPatchW x 8
-// patch of its tile (lane -> column lane % kBwdPatchW, rows lane /
-// kBwdPatchW + k * kBwdRowStep for k < kBwdPPT).
-constexpr int kBwdPPT = 2;
-constexpr int kBwd2Threads = kTilePix / kBwdPPT;
-constexpr int kBwd2Warps = kBwd2Threads / 32;
-constexpr int kBwdPatchW = kBwdPPT == 2 ? 8 : 16;
-constexpr int kBwdRowStep = 32 / kBwdPatchW;
-constexpr int kBwd2Chunk = 64;
-// a row of per-record warp sums in shared memory: one float more than the
-// chunk, so that the lanes storing one record's sums of different values
-// (rows k * warps + warp, 65 floats apart) hit different banks
-constexpr int kBwdSlotRow = kBwd2Chunk + 1;
-constexpr int kBwd2MinBlocks = kBwdPPT == 2 ? 8 : 12;
-static_assert(kBwdPPT * kBwdRowStep == 8 && kTile % kBwdPatchW == 0, "warp patches of 8 rows tile the 16x16 tile");
 
 // Six running FP32 sums of one thread with Kahan compensation (the lost
 // low-order part is carried in c; the true sum is s - c), kept in shared
@@ -1166,10 +1172,8 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Twist6T<kBwd2Chunk> tw{&s_acc[0][threadIdx.x % kBwd2Chunk]};  // used by threads < kBwd2Chunk only
     if ((int)threadIdx.x < kBwd2Chunk)
-        tw.zero();
-    static_assert(NG * kBwd2Warps * kBwdSlotRow % 4 == 0, "slots zeroed as float4");
-    for (int k = threadIdx.x; k < NG * kBwd2Warps * kBwdSlotRow / 4; k += kBwd2Threads)
-        s_dyn[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        tw.zero();  // each thread's own column: no barrier needed
+    // (the slots were zeroed before the forward's last barrier)
     const int n_list = (int)(rg.y - rg.x);
     const bool whole = n_list <= kFwdBatch;
     const bool cull = a.alpha_min > 0.0f;
@@ -1198,7 +1202,15 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
                 s_x1[threadIdx.x] = a.aux[2 * (size_t)r + 1];
             }
         }
-        __syncthreads();
+        // The first chunk of a list walked from the forward's staging needs
+        // no barrier: the walk reads that staging and the zeroed slots, both
+        // ordered by the forward's last barrier, and the means and
+        // covariances staged here are read only by the thread that staged
+        // them (in the epilogue).  Any later chunk follows an epilogue that
+        // re-zeroed slot columns the walk writes, and restaged records are
+        // read by every warp.
+        if (!(whole && hi == maxl))
+            __syncthreads();
         const int wl = min(wmaxl - lo, cnt);
         int nsel = 0;
         for (int j0 = 0; j0 < wl; j0 += 32) {
