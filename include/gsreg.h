@@ -442,6 +442,23 @@ typedef struct {
 gs_status_t gs_register_batch(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt, int iters,
                               double *T_out, double *conf_out, double *eps_out, gs_stream_t stream);
 
+/* The registration loss of Sec. 3.2 and its pose gradient at the starting
+ * poses: the keyframe problems gs_register would set up (the same submaps,
+ * keyframes and options; every keyframe starts from the identity), run for
+ * one iteration's forward and adjoint with nothing updated -- the kernels
+ * of the registration hot path (fused or not, per fuse_compositing).
+ *   loss_out [keyframes] double, host, or NULL: each keyframe's loss (the
+ *     residual a 0-iteration gs_register returns), V^P first;
+ *   grad_out [keyframes][6] double, host: each keyframe's gradient of its
+ *     loss with respect to the pose of the submap that moves for it (Q for
+ *     the keyframes of P, P for those of Q), as a world-frame twist
+ *     (rotation w, then translation v) about that submap's centroid.
+ * Synchronises `stream`; errors as gs_register. */
+gs_status_t gs_register_gradient(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gaussians_t *tgt,
+                                 const gs_view_t *src_views, int n_src_views, const gs_view_t *tgt_views,
+                                 int n_tgt_views, const gs_options_t *opt, double *loss_out, double *grad_out,
+                                 gs_stream_t stream);
+
 /* Stream-ordered forms of gs_register and gs_register_batch (Sec. 3.2, the
  * same problem statement: P, Q, their keyframes -> T_{P->Q} and the
  * residuals eps): every output is a DEVICE buffer written on `stream`, and

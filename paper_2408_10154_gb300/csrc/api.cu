@@ -718,7 +718,7 @@ struct AsyncOut {
 
 gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_options_t *opt, int iters,
                              cudaStream_t s, double *T_out, double *conf_out, double *eps_out, double *est_out,
-                             const AsyncOut *ao = nullptr);
+                             const AsyncOut *ao = nullptr, double *grad_out = nullptr);
 
 }  // namespace
 
@@ -1738,6 +1738,33 @@ gs_status_t gs_register_async(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs
     return run_registration(ctx, P, 1, opt, iters, (cudaStream_t)stream, nullptr, nullptr, nullptr, nullptr, &ao);
 }
 
+gs_status_t gs_register_gradient(gs_ctx_t *ctx, const gs_gaussians_t *src, const gs_gaussians_t *tgt,
+                                 const gs_view_t *src_views, int n_src_views, const gs_view_t *tgt_views,
+                                 int n_tgt_views, const gs_options_t *opt, double *loss_out, double *grad_out,
+                                 gs_stream_t stream)
+{
+    if (!ctx)
+        return GS_ERR_INVALID_ARG;
+    GS_TRY(check_options(ctx, opt));
+    if (!src || !tgt || !grad_out || n_src_views < 0 || n_tgt_views < 0 || n_src_views + n_tgt_views == 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_register_gradient: bad arguments");
+    gs_problem_t q{};
+    q.src = *src;
+    q.tgt = *tgt;
+    q.src_views = src_views;
+    q.n_src_views = n_src_views;
+    q.tgt_views = tgt_views;
+    q.n_tgt_views = n_tgt_views;
+    GS_TRY(check_problem(ctx, q));
+    DeviceGuard dg(ctx->device);
+    Plan P;
+    int sets = 0;
+    add_problem(P, src, tgt, src_views, n_src_views, tgt_views, n_tgt_views, 0, sets, opt);
+    double T[12], conf = 0.0;
+    return run_registration(ctx, P, 1, opt, 1, (cudaStream_t)stream, T, &conf, loss_out, nullptr, nullptr,
+                            grad_out);
+}
+
 gs_status_t gs_register_batch_async(gs_ctx_t *ctx, const gs_problem_t *problems, int n, const gs_options_t *opt,
                                     int iters, double *T_dev, double *conf_dev, double *eps_dev, int32_t *status_dev,
                                     gs_stream_t stream)
@@ -1822,7 +1849,7 @@ __global__ void k_async_status(const int *flags, const double *eps, int nv, int3
 
 gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_options_t *opt, int iters,
                              cudaStream_t s, double *T_out, double *conf_out, double *eps_out, double *est_out,
-                             const AsyncOut *ao)
+                             const AsyncOut *ao, double *grad_out)
 {
     GS_TRY(finalize(ctx, P));
     DevPlan D;
@@ -1884,6 +1911,14 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
     pa.lr_final = opt->lr_final;
     pa.iters = std::max(iters, 1);
     pa.update = 1;
+    double *gradd = nullptr;
+    if (grad_out) {
+        // gradient mode (gs_register_gradient): one iteration that reduces
+        // each keyframe's twist and updates nothing
+        GS_TRY(wsT(ctx, S_GRAD, 6 * (size_t)std::max(nv, 1), &gradd));
+        pa.grad = gradd;
+        pa.update = 0;
+    }
 
     unsigned long long *pairs = nullptr;
     GS_TRY(wsT(ctx, S_PAIRS, 2 * ntl, &pairs));  // per tile: walked, contributing
@@ -2169,6 +2204,8 @@ gs_status_t run_registration(gs_ctx *ctx, Plan &P, int n_problems, const gs_opti
                                 s));
         if (est_out)
             GS_CUDA(cudaMemcpyAsync(est_out, est, 12 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (grad_out)
+            GS_CUDA(cudaMemcpyAsync(grad_out, gradd, 6 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
         GS_CUDA(cudaStreamSynchronize(s));
         gs_stats_t &st = ctx->stats;
         st.kernel_launches = (gsl::g_launches - l0) - captured + graph_kernels * iters + trial_kernels;

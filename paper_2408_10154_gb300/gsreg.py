@@ -73,7 +73,7 @@ class gs_gaussian_grads_t(ctypes.Structure):
 EXPORTS = ["gs_default_options", "gs_ctx_create", "gs_ctx_destroy", "gs_last_error", "gs_ctx_bytes", "gs_ctx_stats",
            "gs_abi_sizes", "gs_project", "gs_bin", "gs_render", "gs_render_backward", "gs_render_saved",
            "gs_saved_outputs", "gs_render_backward_saved", "gs_saved_destroy", "gs_loss", "gs_pose_step",
-           "gs_fuse", "gs_register", "gs_register_batch", "gs_register_async", "gs_register_batch_async", "gs_transform", "gs_render_noalloc", "gs_track_loss",
+           "gs_fuse", "gs_register", "gs_register_batch", "gs_register_async", "gs_register_batch_async", "gs_register_gradient", "gs_transform", "gs_render_noalloc", "gs_track_loss",
            "gs_overlap_ratio", "gs_transform_batch", "gs_sort_u32", "gs_selftest_bounded_wait", "gs_probe_fp32",
            "gs_server_create",
            "gs_server_destroy", "gs_server_last_error", "gs_server_submit", "gs_server_step", "gs_server_poll",
@@ -131,6 +131,7 @@ def load(build_if_missing: bool = False):
             "gs_register_batch": ([P, P, I, P, I, P, P, P, P], I),
             "gs_register_async": ([P, P, P, P, I, P, I, P, I, P, P, P, P, P, P], I),
             "gs_register_batch_async": ([P, P, I, P, I, P, P, P, P, P], I),
+            "gs_register_gradient": ([P, P, P, P, I, P, I, P, P, P, P], I),
             "gs_server_create": ([I, ctypes.c_size_t, I, I, P, P], I),
             "gs_server_destroy": ([P], I),
             "gs_server_last_error": ([P], ctypes.c_char_p),
@@ -487,6 +488,25 @@ def gs_register(ctx: Context, src: Gaussians, tgt: Gaussians, src_views, tgt_vie
                                    len(tgt_views), ctypes.byref(opt), int(iters), d(T), ctypes.byref(conf), d(eps),
                                    d(est), _stream()))
     return T.reshape(3, 4), conf.value, eps[:n], est[:n].reshape(n, 3, 4)
+
+
+def gs_register_gradient(ctx: Context, src: Gaussians, tgt: Gaussians, src_views, tgt_views, opt=None):
+    """The registration loss and its pose gradient at the starting poses of
+    the keyframe problems gs_register would set up.  Returns (loss [n],
+    grad [n,6] world-frame twists about the moving submap's centroid)."""
+    opt = opt or default_options()
+    for _, rgb, depth in list(src_views) + list(tgt_views):
+        if not (rgb.is_cuda and depth.is_cuda and rgb.is_contiguous() and depth.is_contiguous()):
+            raise ValueError("keyframe images must be contiguous CUDA tensors")
+    sv, tv = _views(src_views), _views(tgt_views)
+    n = len(src_views) + len(tgt_views)
+    loss = np.zeros(max(n, 1), np.float64)
+    grad = np.zeros((max(n, 1), 6), np.float64)
+    s, t = src.c_struct(), tgt.c_struct()
+    d = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    ctx.check(ctx._lib.gs_register_gradient(ctx.handle, ctypes.byref(s), ctypes.byref(t), sv, len(src_views), tv,
+                                            len(tgt_views), ctypes.byref(opt), d(loss), d(grad), _stream()))
+    return loss[:n], grad[:n]
 
 
 def gs_transform(ctx: Context, g: Gaussians, T) -> Gaussians:
