@@ -30,18 +30,6 @@ namespace {
 
 using namespace gsk;
 
-// exponent of record (q0 = u, v, ca, cb; cc) at the pixel sample (FP32
-// contract); h = ca dx + cb dy and ky = cc dy are its intermediates
-__device__ __forceinline__ float exponent_at(const float4 &q0, float cc, float pxf, float pyf, float &dx, float &dy,
-                                             float &h, float &ky)
-{
-    dx = sub_rn(q0.x, pxf);
-    dy = sub_rn(q0.y, pyf);
-    h = fma_rn(q0.z, dx, mul_rn(q0.w, dy));
-    ky = mul_rn(cc, dy);
-    return fma_rn(h, dx, mul_rn(ky, dy));
-}
-
 // Warp-level cull of a staged record against the warp's pixel patch.  The
 // record can only pass the alpha test (alpha >= alpha_min) where its exact
 // exponent is at least tau = ln(alpha_min / o), i.e. inside the ellipse
@@ -155,6 +143,7 @@ struct RecX2 {
 // the two pixels' adjoint walk state: T, -Q and the loss gradient per pixel
 struct PixAdj2 {
     f32x2 pxf, pyf, T, nQ, gr, gg, gb, gd;
+    f32x2 ga_tf;  // render mode: the alpha cotangent times T_final
     int last0, last1;
 };
 
@@ -187,8 +176,10 @@ __device__ __forceinline__ void exp_ct_nonpos_x2(float x0, float x1, float &e0, 
     e1 = __int_as_float(__float_as_int(ph) + (int)((uint32_t)__float_as_int(th) << 23));
 }
 
-// exponent of a staged record at both pixel samples (the contract's
-// operation sequence, as exponent_at)
+// exponent of a staged record (u, v, ca, cb, cc) at both pixel samples, the
+// contract's FP32 sequence per lane: dx = u - px, dy = v - py, h = ca dx +
+// (cb dy), ky = cc dy, power = h dx + (ky dy); h and ky are the gradient's
+// intermediates
 __device__ __forceinline__ f32x2 exponent_x2(const RecX2 &R, f32x2 pxf, f32x2 pyf, f32x2 &dx, f32x2 &h, f32x2 &ky)
 {
     dx = sub2(R.uv.x, pxf);
@@ -757,11 +748,12 @@ __device__ __forceinline__ void chain_twist(const float *G, const float4 &q1, co
 // owns the 8x8 quadrant (w & 1, w >> 1) (lane -> column lane & 7, rows
 // lane >> 3 and +4): the squarest patch of 64 pixels, which the fewest
 // records reach.
-// Each staged record is evaluated for both pixels (two independent chains)
-// and their gradients are added before the warp reduction, which therefore
-// covers 64 pixels.
+// Each staged record is evaluated for both pixels in one chain of packed
+// operations (pix_adj_x2) and their gradients are added before the warp
+// reduction, which therefore covers 64 pixels.
 // ---------------------------------------------------------------------------
-// Per-pixel state of the back-to-front walk.  g = (gr, gg, gb, gd) is the
+// Per-pixel state of the back-to-front walk (as read from the forward's
+// outputs; the walk carries it packed, PixAdj2).  g = (gr, gg, gb, gd) is the
 // loss gradient w.r.t. the pixel's colour and depth, constant along the
 // walk, so the colour behind the current Gaussian enters dL/dalpha only
 // through Q = g . S, S = sum over the Gaussians behind (and the background)
@@ -824,70 +816,20 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
     P.ga_tf = ga * P.Tf;
 }
 
-// One (pixel, Gaussian) pair of the back-to-front walk: the contract's
-// decisions, the transmittance recovery, the colour-behind update and the
-// screen-space gradient added to g.  Returns whether the pair contributed.
-// ALPHA: the alpha image has a cotangent (render mode; the registration
-// loss has none).
-template <bool FULL, bool ALPHA>
-__device__ __forceinline__ bool pix_adj_pair(PixAdj &P, int jj, const float4 &q0, const float4 &q1,
-                                             const float4 &q2, const gsl::RasterArgs &a, float *g)
-{
-    if (jj >= P.last)
-        return false;
-    float dx, dy, h, ky;
-    const float power = exponent_at(q0, q1.x, P.pxf, P.pyf, dx, dy, h, ky);
-    if (power > 0.0f || power < q1.w)
-        return false;
-    const float e = exp_ct_nonpos(power);
-    const float x = mul_rn(q1.y, e);
-    const bool clamped = x > a.alpha_max;
-    const float alpha = clamped ? a.alpha_max : x;
-    if (alpha < a.alpha_min)
-        return false;
-    const float om = 1.0f - alpha;
-    const float rom = __fdividef(1.0f, om);
-    const float Ti = P.T * rom;
-    const float gcc = fmaf(P.gd, q1.z, fmaf(P.gb, q2.z, fmaf(P.gg, q2.y, P.gr * q2.x)));
-    float dal = fmaf(Ti, gcc, -(P.Q * rom));
-    if (ALPHA)
-        dal = fmaf(P.ga_tf, rom, dal);
-    const float wgt = alpha * Ti;
-    P.Q = fmaf(gcc, wgt, P.Q);
-    g[5] = fmaf(P.gd, wgt, g[5]);
-    if (FULL) {
-        g[7] = fmaf(P.gr, wgt, g[7]);
-        g[8] = fmaf(P.gg, wgt, g[8]);
-        g[9] = fmaf(P.gb, wgt, g[9]);
-    }
-    if (!clamped) {
-        // d(exponent)/d(u, v) = (gu, gv) = -Q d; the exponent's gradient
-        // w.r.t. the 2D covariance is (Q d)(Q d)^T / 2, accumulated as twice that
-        // (2 ca dx + cb dy, cb dx + 2 cc dy) from the exponent's intermediates
-        const float dp = dal * alpha;
-        const float gu = fmaf(q0.z, dx, h);
-        const float gv = fmaf(q0.w, dx, ky + ky);
-        const float g0 = dp * gu, g1 = dp * gv;
-        g[0] += g0;
-        g[1] += g1;
-        g[2] = fmaf(g0, gu, g[2]);
-        g[3] = fmaf(g0, gv, g[3]);
-        g[4] = fmaf(g1, gv, g[4]);
-        if (FULL)
-            g[6] = fmaf(dal, e, g[6]);
-    }
-    P.T = Ti;
-    return true;
-}
 
-// Both pixels of one (thread, Gaussian) pair of the registration adjoint:
-// the contract's decisions (the alpha test decides alone: the exponent
-// cutoff only ever skips pairs that fail it), the transmittance recovery,
-// the colour-behind update and the negated screen-space gradient, summed
-// over the two pixels in the scalar walk's order, into ng.  Returns
-// whether either pixel contributed.
+// Both pixels of one (thread, Gaussian) pair of the adjoint: the
+// contract's decisions (the alpha test decides alone: the exponent cutoff
+// only ever skips pairs that fail it), the transmittance recovery, the
+// colour-behind update and the negated screen-space gradient, summed over
+// the two pixels in a one-pixel walk's order (pixel 0's term first), into
+// ng.  The pair's early exits are masks: a pair that fails a test enters
+// every sum with weight 0 (so every value is the one-pixel walk's, up to the
+// sign of zero sums).  ALPHA: the alpha image has a cotangent (render mode).
+// FULL: also the opacity and colour gradients (ng[6..9]).  Returns whether
+// either pixel contributed.
+template <bool ALPHA, bool FULL>
 __device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, float amax, float namax,
-                                           float namin, float (&ng)[6])
+                                           float namin, float (&ng)[FULL ? 10 : 6])
 {
     f32x2 dx, h, ky;
     const f32x2 power = exponent_x2(R, P.pxf, P.pyf, dx, h, ky);
@@ -909,7 +851,9 @@ __device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, f
     const f32x2 rom = x2(__fdividef(1.0f, om0), __fdividef(1.0f, om1));
     const f32x2 Ti = mul2(P.T, rom);
     const f32x2 gcc = fma2(P.gd, R.zr.x, fma2(P.gb, R.gb.y, fma2(P.gg, R.gb.x, mul2(P.gr, R.zr.y))));
-    const f32x2 dal = fma2(Ti, gcc, mul2(P.nQ, rom));
+    f32x2 dal = fma2(Ti, gcc, mul2(P.nQ, rom));
+    if (ALPHA)
+        dal = fma2(P.ga_tf, rom, dal);
     const f32x2 nwgt = mul2(nal, Ti);
     P.nQ = fma2(gcc, nwgt, P.nQ);
     const f32x2 ndp = mul2(dal, nag);
@@ -928,6 +872,19 @@ __device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, f
     ng[3] = fmaf(a1, v1, a0 * v0);
     ng[4] = fmaf(b1, v1, b0 * v0);
     ng[5] = fmaf(d1, w1, d0 * w0);
+    if constexpr (FULL) {
+        // -(dal e) over the live, unclamped pixels; -(g_c wgt) over the live ones
+        const float ne0 = live0 && !cl0 ? -e0 : 0.0f, ne1 = live1 && !cl1 ? -e1 : 0.0f;
+        float l0, l1, r0, r1, g0, g1, c0, c1;
+        x2_split(dal, l0, l1);
+        x2_split(P.gr, r0, r1);
+        x2_split(P.gg, g0, g1);
+        x2_split(P.gb, c0, c1);
+        ng[6] = fmaf(l1, ne1, l0 * ne0);
+        ng[7] = fmaf(r1, w1, r0 * w0);
+        ng[8] = fmaf(g1, w1, g0 * w0);
+        ng[9] = fmaf(c1, w1, c0 * w0);
+    }
     P.T = Ti;
     return live0 || live1;
 }
@@ -943,10 +900,10 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
     float *const s_slots = reinterpret_cast<float *>(s_dyn);  // [NG][warps][kBwdSlotRow]
     __shared__ float4 s0[kBwd2Chunk], s1[kBwd2Chunk], s2[kBwd2Chunk];
     __shared__ float4 s_x0[kBwd2Chunk], s_x1[kBwd2Chunk];  // the records' camera-frame mean and covariance
-    // the registration adjoint walks both pixels of a thread with packed
-    // operations (the record's values broadcast to both lanes as loaded; o
-    // staged negated)
-    constexpr bool PK = REG && !FULL && kBwdPPT == 2;
+    // both pixels of a thread are walked with packed operations (the
+    // record's values broadcast to both lanes as loaded; o staged negated)
+    constexpr bool PK = kBwdPPT == 2;
+    static_assert(PK, "the adjoint walks two pixels per thread");
     __shared__ uint8_t s_sel[kBwd2Warps][kBwd2Chunk];  // per warp: chunk positions that may hit its rows
     __shared__ int s_maxl[kBwd2Warps];
     __shared__ float s_tw[kBwd2Warps][6][2];
@@ -1009,6 +966,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
         P2.gg = x2(P[0].gg, P[1].gg);
         P2.gb = x2(P[0].gb, P[1].gb);
         P2.gd = x2(P[0].gd, P[1].gd);
+        P2.ga_tf = x2(P[0].ga_tf, P[1].ga_tf);
         P2.last0 = P[0].last;
         P2.last1 = P[1].last;
     }
@@ -1073,27 +1031,14 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
         for (int k = nsel - 1; k >= 0; --k) {
             const int j = s_sel[warp][k];
             float g[NG];
-#pragma unroll
-            for (int k = 0; k < NG; ++k)
-                g[k] = -0.0f;  // -0 + x == x for every x (not so +0): the first additions fold away
-            bool contrib = false;
-            if constexpr (PK) {
-                const float4 q0 = s0[j], q1 = s1[j], q2 = s2[j];
-                RecX2 R;
-                R.uv = make_ulonglong2(bc2(q0.x), bc2(q0.y));
-                R.ab = make_ulonglong2(bc2(q0.z), bc2(q0.w));
-                R.co = make_ulonglong2(bc2(q1.x), bc2(q1.y));
-                R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
-                R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
-                contrib = pix_adj_x2(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
-            } else {
-                const float4 q0 = s0[j];
-                const float4 q1 = s1[j];
-                const float4 q2 = s2[j];  // the record's colour, loaded once for every pixel of the lane
-#pragma unroll
-                for (int k = 0; k < kBwdPPT; ++k)
-                    contrib |= pix_adj_pair<FULL, !REG>(P[k], lo + j, q0, q1, q2, a, g);
-            }
+            const float4 q0 = s0[j], q1 = s1[j], q2 = s2[j];
+            RecX2 R;
+            R.uv = make_ulonglong2(bc2(q0.x), bc2(q0.y));
+            R.ab = make_ulonglong2(bc2(q0.z), bc2(q0.w));
+            R.co = make_ulonglong2(bc2(q1.x), bc2(q1.y));
+            R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
+            R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
+            const bool contrib = pix_adj_x2<!REG, FULL>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
             if (__any_sync(0xffffffffu, contrib)) {
                 constexpr int NP = NG <= 8 ? 8 : 16;
                 float v[NP];
@@ -1120,7 +1065,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
                     s += slot;
                     slot = 0.0f;
                 }
-                G[k] = PK ? -s : s;  // the packed walk sums the negated gradient
+                G[k] = -s;  // the packed walk sums the negated gradient
                 any |= s != 0.0f;
             }
             if (FULL) {
@@ -1236,7 +1181,7 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
             R.co = make_ulonglong2(bc2(q1.x), bc2(q2.w));
             R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
             R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
-            const bool contrib = pix_adj_x2(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
+            const bool contrib = pix_adj_x2<false, false>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
             if (__any_sync(0xffffffffu, contrib)) {
                 float v[8];
 #pragma unroll
