@@ -13,13 +13,17 @@
 // the last-contributor index.  Nothing else per pixel is saved; the adjoint
 // recomputes alpha and recovers transmittance by division.
 //
-// Adjoint: 128 threads per tile, two pixels per thread (8x8 warp patches;
-// packed operations in registration mode).  Per (pixel, Gaussian)
+// Adjoint: 128 threads per tile, two pixels per thread (8x8 warp patches),
+// both walked with packed operations.  Per (pixel, Gaussian)
 // screen-space gradients are summed over each warp with shuffles, over the
 // tile's warps in shared memory (fixed order), chained through the
 // projection into a camera-frame twist per Gaussian, accumulated per thread
 // in FP32 with Kahan compensation and reduced per tile by TwoSum butterflies
 // to FP32 (hi, lo) pairs -- no global atomics, bit-reproducible.
+//
+// Registration iterations (the registration loss) run both in one CTA per
+// tile (k_fwdbwd): the adjoint walks the forward's pixels from registers
+// and, for lists of at most 256 entries, the forward's staging.
 #include <float.h>
 
 #include <algorithm>
