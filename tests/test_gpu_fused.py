@@ -151,3 +151,30 @@ def test_fused_option_is_checked(gs, ctx):
     views = views_of(gd, cams, 43)
     with pytest.raises(Exception):
         gs.gs_register(ctx, g, g, [], views, 2, gs.default_options(fuse_compositing=2))
+
+
+def one_tile(n, seed):
+    # n faint, wide splats in front of a 16x16 camera: every one lands on the
+    # frame's only tile, and pixels stay far from opaque, so the walks run
+    # the whole list -- list lengths at the fused kernel's chunk (64) and
+    # staging (256) boundaries
+    c = synth.small_case(n, 16, 16, 20.0, n_views=1, seed=seed, ls_mean=-1.6, ls_std=0.1, half=0.2)
+    g = {k: np.array(v, copy=True) for k, v in c["gaussians"].items()}
+    g["logits"][:] = np.random.default_rng(seed).normal(-4.0, 0.2, len(g["logits"]))
+    return g, c["cams"]
+
+
+@pytest.mark.parametrize("n", [63, 64, 65, 128, 255, 256, 257, 300])
+def test_fused_at_list_length_boundaries(gs, ctx, n):
+    gd, cams = one_tile(n, 70 + n)
+    og = O.Gaussians.from_dict(gd)
+    _, _, ranges = O.bin_tiles(og, np.eye(3, 4)[None], cams, O.DEFAULT_OPT)
+    assert int((ranges[:, 1] - ranges[:, 0]).max()) == n
+    g = gs.Gaussians.from_numpy(gd)
+    views = views_of(gd, cams, 80 + n, angle=1.0, trans=0.01)
+    a, b = both(gs, ctx, lambda o: gs.gs_register(ctx, g, g, [], views, 6, o))
+    assert_same(a, b)
+    la, ga = gs.gs_register_gradient(ctx, g, g, [], views)
+    lb, gb = gs.gs_register_gradient(ctx, g, g, [], views, gs.default_options(fuse_compositing=0))
+    np.testing.assert_array_equal(ga, gb)
+    np.testing.assert_array_equal(la, lb)

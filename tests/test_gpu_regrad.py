@@ -55,7 +55,19 @@ def small(*a, **k):
     return c["gaussians"], c["cams"]
 
 
+def one_tile(n, seed):
+    # n faint, wide splats on a 16x16 frame's only tile: lists of exactly n
+    # entries walked to the end (n = 65: two adjoint chunks; n = 257: more
+    # than one forward batch, restaged chunk by chunk)
+    c = synth.small_case(n, 16, 16, 20.0, n_views=1, seed=seed, ls_mean=-1.6, ls_std=0.1, half=0.2)
+    g = {k: np.array(v, copy=True) for k, v in c["gaussians"].items()}
+    g["logits"][:] = np.random.default_rng(seed).normal(-4.0, 0.2, len(g["logits"]))
+    return g, c["cams"]
+
+
 CASES = {
+    "one_tile_65": lambda: one_tile(65, 135),
+    "one_tile_257": lambda: one_tile(257, 327),
     "plain_2k": lambda: (lambda c: (c["gaussians"], c["cams"]))(synth.plain_2k()),
     "ragged_100x70": lambda: small(700, 100, 70, 70.0, n_views=3, seed=9, ls_mean=-3.5),
     "needles_300x200": needles,
