@@ -126,3 +126,43 @@ def test_registration_gradient_is_the_first_step_of_gs_register(gs, ctx):
     loss, _ = gs.gs_register_gradient(ctx, g, g, views[:1], views[1:])
     _, _, eps, _ = gs.gs_register(ctx, g, g, views[:1], views[1:], 0)
     np.testing.assert_array_equal(loss, eps)
+
+
+def test_registration_gradient_of_reverse_keyframes_matches_oracle(gs, ctx):
+    # keyframes of P localised in Q: the submap that moves is Q (= T P), its
+    # render at P's keyframe cameras is compared with P's images, and the
+    # gradient is Q's twist about Q's centroid
+    gd, cams = CASES["ragged_100x70"]()
+    og = O.Gaussians.from_dict(gd)
+    T = synth.about_point(synth.random_rigid(np.random.default_rng(63), 2.0, 0.03), O.centroid(og))
+    oq = O.transform(og, T)
+    src = gs.Gaussians.from_numpy(gd)
+    tgt = gs.Gaussians(*[dev(a) for a in (oq.means4, oq.log_scales4, oq.quats4, oq.logits, oq.rgb4)])
+    ims = []
+    for cam in cams:
+        r = O.render(og, np.eye(3, 4), cam)
+        ims.append((cam, r["rgb"].astype(np.float32), r["depth"].astype(np.float32)))
+    views = [(cam, dev(rgb), dev(dep)) for cam, rgb, dep in ims]
+    loss, grad = gs.gs_register_gradient(ctx, src, tgt, views, [])
+    piv = O.centroid(oq)
+    for k, (cam, rgb, dep) in enumerate(ims):
+        r = O.render(oq, np.eye(3, 4), cam)
+        L, gr, gdp = O.loss(r["rgb"], r["depth"], rgb, dep)
+        ref = O.backward(oq, np.eye(3, 4), cam, gr, gdp, pivot=piv, params=False)["twist"]
+        err = np.linalg.norm(grad[k] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-3, (k, err, grad[k], ref)
+        assert loss[k] == pytest.approx(L, rel=1e-4), (k, loss[k], L)
+
+
+def test_registration_gradient_with_exposure_and_counting(gs, ctx):
+    # the exposure variant (gain 1, offset 0 at the start) and the counting
+    # variant of the fused kernel give the plain gradient
+    gd, cams = CASES["ragged_100x70"]()
+    g = gs.Gaussians.from_numpy(gd)
+    og = O.Gaussians.from_dict(gd)
+    views = [(cam, dev(rgb), dev(dep)) for cam, rgb, dep in targets(og, cams, 64)]
+    base = gs.gs_register_gradient(ctx, g, g, [], views)
+    for kw in (dict(exposure=1), dict(profile=2), dict(exposure=1, profile=2)):
+        got = gs.gs_register_gradient(ctx, g, g, [], views, gs.default_options(**kw))
+        np.testing.assert_array_equal(got[0], base[0])
+        np.testing.assert_array_equal(got[1], base[1])
