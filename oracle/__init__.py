@@ -76,6 +76,8 @@ def _load():
         I = ctypes.c_int
         L = ctypes.c_long
         lib.or_exp32.argtypes = [ctypes.c_float]
+        lib.or_exp32_count_above_one.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        lib.or_exp32_count_above_one.restype = ctypes.c_int64
         lib.or_exp32.restype = ctypes.c_float
         lib.or_log32.argtypes = [ctypes.c_float]
         lib.or_log32.restype = ctypes.c_float
@@ -169,6 +171,12 @@ class Gaussians:
 def exp32(x: float) -> float:
     """The FP32 mirror's exponential (Cody-Waite + degree-6 Taylor)."""
     return float(_load().or_exp32(float(x)))
+
+
+def exp32_count_above_one(lo_bits: int, hi_bits: int) -> int:
+    """How many floats with bit patterns in [lo_bits, hi_bits] the mirror's
+    exponential maps above 1."""
+    return int(_load().or_exp32_count_above_one(lo_bits, hi_bits))
 
 
 def log32(x: float) -> float:

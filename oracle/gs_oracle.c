@@ -114,6 +114,25 @@ float or_exp32(float x)
     return p * scale;
 }
 
+/* How many floats x with bit patterns in [lo, hi] have or_exp32(x) > 1
+ * (a property check for the tests: for every exponent x <= 0 the mirror's
+ * e^x is at most 1, so x o can exceed alpha_max only when the opacity o
+ * does).  Multi-threaded under or_set_threads. */
+int64_t or_exp32_count_above_one(uint32_t lo, uint32_t hi)
+{
+    int64_t bad = 0;
+    const int64_t n = (int64_t)hi - (int64_t)lo + 1;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t u = lo + (uint32_t)i;
+        float x;
+        memcpy(&x, &u, sizeof x);
+        if (!(or_exp32(x) <= 1.0f))
+            ++bad;
+    }
+    return bad;
+}
+
 /* ln x in FP32 for a positive normal x, as the tight tile rectangles take
  * it: x = m 2^e with the mantissa m moved into [sqrt(1/2), sqrt(2)) (halved,
  * e raised, when above sqrt(2)); ln m = 2 artanh(s), s = (m - 1)/(m + 1),

@@ -27,6 +27,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "gs_internal.cuh"
 
@@ -232,7 +233,7 @@ static_assert(kBwdPPT * kBwdRowStep == 8 && kTile % kBwdPatchW == 0, "warp patch
 __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t t, const VpDesc &d, uint2 rg,
                                               float4 *s0, float4 *s1, float4 *s2, const uint32_t *s_v,
                                               uint8_t *s_selw, float xa, float ya, PixAdj2 &P2, int maxl,
-                                              int wmaxl, const float *cc);
+                                              int wmaxl, const float *cc, bool fclamp);
 
 template <bool REG, int X, bool FUSED = false>
 __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_t t)
@@ -284,6 +285,9 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
     f32x2 T = bc2(1.0f), C0 = bc2(0.0f), C1 = bc2(0.0f), C2 = bc2(0.0f), D = bc2(0.0f);
     int last0 = 0, last1 = 0, nc = 0;
     bool done0 = !in0, done1 = !in1;
+    // whether the batch holds a record whose opacity exceeds alpha_max (only
+    // those can reach the clamp: x = o e with e <= 1 for every exponent <= 0)
+    bool clamp = false;
     for (uint32_t b = rg.x; b < rg.y; b += kFwdBatch) {
         if (b != rg.x) {
             if (__syncthreads_count(done0 && done1) == kFwdThreads)
@@ -295,7 +299,13 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                     stage(threadIdx.x + r * kFwdThreads, a.vals[idx]);
             }
         }
-        __syncthreads();
+        {
+            bool hot = false;
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                hot |= b + threadIdx.x + r * kFwdThreads < rg.y && s1[threadIdx.x + r * kFwdThreads].y > a.alpha_max;
+            clamp = __syncthreads_or(hot) != 0;
+        }
         const int cnt = (int)min((uint32_t)kFwdBatch, rg.y - b);
         int nsel = 0;
         if (!__all_sync(0xffffffffu, done0 && done1)) {
@@ -318,6 +328,10 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
         // the votes below see all 32 lanes.
         if (!__all_sync(0xffffffffu, done0 && done1)) {
             const int base = (int)(b - rg.x) + 1;
+            // two copies of the walk: with the clamp, and for a batch that
+            // cannot reach it without (no compare, no min)
+            auto walk = [&](auto clamp_tag) {
+            constexpr bool CLAMP = decltype(clamp_tag)::value;
             for (int k = 0; k < nsel; ++k) {
                 const int j = s_sel[warp][k];
                 const float4 q0 = s0[j], q1 = s1[j], q2 = s2[j];
@@ -333,8 +347,7 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                 exp_ct_nonpos_x2(p0, p1, e0, e1);
                 float x0, x1;
                 x2_split(mul2(R.co.y, x2(e0, e1)), x0, x1);
-                const float al0 = x0 > a.alpha_max ? a.alpha_max : x0;
-                const float al1 = x1 > a.alpha_max ? a.alpha_max : x1;
+                const float al0 = CLAMP ? fminf(x0, a.alpha_max) : x0, al1 = CLAMP ? fminf(x1, a.alpha_max) : x1;
                 const bool ok0 = !done0 && !(p0 > 0.0f) && !(al0 < a.alpha_min);
                 const bool ok1 = !done1 && !(p1 > 0.0f) && !(al1 < a.alpha_min);
                 const f32x2 al = x2(ok0 ? al0 : 0.0f, ok1 ? al1 : 0.0f);
@@ -375,6 +388,11 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                 if (__all_sync(0xffffffffu, done0 && done1))
                     break;
             }
+            };
+            if (clamp)
+                walk(std::true_type{});
+            else
+                walk(std::false_type{});
         }
     }
     float Tk[2], C0k[2], C1k[2], C2k[2], Dk[2];
@@ -552,7 +570,7 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
         P2.gd = x2(g[0][3], g[1][3]);
         P2.last0 = last0;
         P2.last1 = last1;
-        fused_adjoint(a, t, d, rg, s0, s1, s2, s_v, s_sel[warp], xa, ya, P2, maxl, wmaxl, cc);
+        fused_adjoint(a, t, d, rg, s0, s1, s2, s_v, s_sel[warp], xa, ya, P2, maxl, wmaxl, cc, clamp);
     }
 }
 
@@ -831,7 +849,7 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
 // sign of zero sums).  ALPHA: the alpha image has a cotangent (render mode).
 // FULL: also the opacity and colour gradients (ng[6..9]).  Returns whether
 // either pixel contributed.
-template <bool ALPHA, bool FULL>
+template <bool ALPHA, bool FULL, bool CLAMP = true>
 __device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, float amax, float namax,
                                            float namin, float (&ng)[FULL ? 10 : 6])
 {
@@ -843,12 +861,12 @@ __device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, f
     // -x = (-o) e; clamped: x > alpha_max; -alpha; the alpha test
     float nx0, nx1;
     x2_split(mul2(R.co.y, x2(e0, e1)), nx0, nx1);
-    const bool cl0 = nx0 < namax, cl1 = nx1 < namax;
-    const float na0 = cl0 ? namax : nx0, na1 = cl1 ? namax : nx1;
+    const bool cl0 = CLAMP && nx0 < namax, cl1 = CLAMP && nx1 < namax;
+    const float na0 = CLAMP ? fmaxf(nx0, namax) : nx0, na1 = CLAMP ? fmaxf(nx1, namax) : nx1;
     const bool live0 = jj < P.last0 && !(p0 > 0.0f) && !(na0 > namin);
     const bool live1 = jj < P.last1 && !(p1 > 0.0f) && !(na1 > namin);
     const f32x2 nal = x2(live0 ? na0 : 0.0f, live1 ? na1 : 0.0f);
-    const f32x2 nag = x2(live0 && !cl0 ? na0 : 0.0f, live1 && !cl1 ? na1 : 0.0f);
+    const f32x2 nag = CLAMP ? x2(live0 && !cl0 ? na0 : 0.0f, live1 && !cl1 ? na1 : 0.0f) : nal;
     // 1 - alpha, its reciprocal, T_i = T / (1 - alpha)
     float om0, om1;
     x2_split(add2(bc2(1.0f), nal), om0, om1);
@@ -1109,7 +1127,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2_q(co
 __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t t, const VpDesc &d, uint2 rg,
                                               float4 *s0, float4 *s1, float4 *s2, const uint32_t *s_v,
                                               uint8_t *s_selw, float xa, float ya, PixAdj2 &P2, int maxl,
-                                              int wmaxl, const float *cc)
+                                              int wmaxl, const float *cc, bool fclamp)
 {
     constexpr int NG = 6;
     extern __shared__ float4 s_dyn[];
@@ -1158,8 +1176,15 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
         // them (in the epilogue).  Any later chunk follows an epilogue that
         // re-zeroed slot columns the walk writes, and restaged records are
         // read by every warp.
-        if (!(whole && hi == maxl))
-            __syncthreads();
+        // whether the chunk holds a record whose opacity exceeds alpha_max
+        // (a list walked from the forward's staging: the forward's flag)
+        bool clamp = fclamp;
+        if (!(whole && hi == maxl)) {
+            const bool hot = !whole && (int)threadIdx.x < cnt && s1[threadIdx.x].y > a.alpha_max;
+            const bool any_hot = __syncthreads_or(hot) != 0;
+            if (!whole)
+                clamp = any_hot;
+        }
         const int wl = min(wmaxl - lo, cnt);
         int nsel = 0;
         for (int j0 = 0; j0 < wl; j0 += 32) {
@@ -1175,6 +1200,8 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
             nsel += __popc(m);
         }
         __syncwarp();
+        auto walk = [&](auto clamp_tag) {
+        constexpr bool CLAMP = decltype(clamp_tag)::value;
         for (int k = nsel - 1; k >= 0; --k) {
             const int j = s_selw[k];
             float g[NG];
@@ -1185,7 +1212,8 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
             R.co = make_ulonglong2(bc2(q1.x), bc2(q2.w));
             R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
             R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
-            const bool contrib = pix_adj_x2<false, false>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
+            const bool contrib =
+                pix_adj_x2<false, false, CLAMP>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
             if (__any_sync(0xffffffffu, contrib)) {
                 float v[8];
 #pragma unroll
@@ -1197,6 +1225,11 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
                     s_slots[(kk * kBwd2Warps + warp) * kBwdSlotRow + j] = sum;
             }
         }
+        };
+        if (clamp)
+            walk(std::true_type{});
+        else
+            walk(std::false_type{});
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
             float G[NG];

@@ -290,3 +290,18 @@ def small_case(n, W, H, f, n_views=1, seed=0, ls_mean=-3.0, ls_std=0.4, half=0.8
         cams = circle_cameras(n_views, 0.25, (0.0, 0.0, depth), W, H, f)
     T = about_point(random_rigid(rng, angle_deg, trans_m), centroid(g))
     return dict(name=f"small_{n}_{W}x{H}", gaussians=g, cams=cams, T_gt=T)
+
+
+def saturated_case(seed=41):
+    """A small scene whose left half holds near-opaque Gaussians (opacity
+    logits N(6, 1): most opacities above the 0.99 alpha clamp) and whose
+    right half the usual N(0, 1) logits, so that some screen tiles see
+    clamped alphas and others none, 2 views of 160x120."""
+    c = small_case(1500, 160, 120, 150.0, n_views=2, seed=seed, ls_mean=-3.2, ls_std=0.3)
+    g = {k: np.array(v, copy=True) for k, v in c["gaussians"].items()}
+    rng = np.random.default_rng(seed + 1)
+    left = g["means4"][:, 0] < 0.0
+    g["logits"][left] = rng.normal(6.0, 1.0, int(left.sum()))
+    c["gaussians"] = g
+    return c
+

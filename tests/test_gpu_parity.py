@@ -92,7 +92,15 @@ def needle_case():
     return g, c["cams"]
 
 
-CASES = {"plain_2k": plain_case, "ragged_100x70": ragged_case, "needles_300x200": needle_case}
+def saturated_case():
+    # near-opaque Gaussians on the scene's left half (alphas at the 0.99
+    # clamp), plain ones on the right: tiles with and without clamped pairs
+    c = synth.saturated_case()
+    return c["gaussians"], c["cams"]
+
+
+CASES = {"plain_2k": plain_case, "ragged_100x70": ragged_case, "needles_300x200": needle_case,
+         "saturated_160x120": saturated_case}
 
 
 # ----------------------------------------------------------------- projection

@@ -72,6 +72,7 @@ CASES = {
     "ragged_100x70": lambda: small(700, 100, 70, 70.0, n_views=3, seed=9, ls_mean=-3.5),
     "needles_300x200": needles,
     "dense_3000": lambda: small(3000, 64, 48, 200.0, n_views=2, seed=31, ls_mean=-3.0, ls_std=0.2, half=0.05),
+    "saturated_160x120": lambda: (lambda c: (c["gaussians"], c["cams"]))(synth.saturated_case()),
     "room_full_size": lambda: (lambda c: (c["gaussians"], c["src_cams"][:2]))(synth.room_150k()),
 }
 

@@ -48,6 +48,21 @@ def test_exp32_against_libm():
     assert O.exp32(0.0) == 1.0
 
 
+def test_exp32_at_most_one_for_every_nonpositive_float():
+    # exhaustive over the 1.1e9 floats from -0 (0x80000000) to -80
+    # (0xC2A00000), plus +0: e^x <= 1 for x <= 0, so x o <= o and a Gaussian
+    # whose opacity is at most alpha_max never reaches the alpha clamp
+    # (below -80 the argument is clamped to -80)
+    prev = O.set_threads(os.cpu_count() or 1)
+    try:
+        assert O.exp32_count_above_one(0x80000000, 0xC2A00000) == 0
+    finally:
+        O.set_threads(prev)
+    assert O.exp32(0.0) == 1.0
+    assert O.exp32_count_above_one(0x00000000, 0x00000000) == 0
+    assert O.exp32_count_above_one(0x3F000000, 0x3F000001) == 2  # the scan sees e^0.5 > 1
+
+
 def test_exp32_monotone_on_alpha_range():
     xs = np.float32(-6.0) + np.arange(60000, dtype=np.float32) * np.float32(1e-4)
     vals = [O.exp32(float(x)) for x in xs]
