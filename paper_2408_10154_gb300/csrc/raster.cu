@@ -354,7 +354,8 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                 const f32x2 tn = mul2(T, sub2(bc2(1.0f), al));  // T itself where al = 0
                 float tn0, tn1;
                 x2_split(tn, tn0, tn1);
-                const bool st0 = ok0 && tn0 < a.t_min, st1 = ok1 && tn1 < a.t_min;
+                // (a pair that fails leaves tn = T >= t_min: no ok test needed)
+                const bool st0 = tn0 < a.t_min, st1 = tn1 < a.t_min;
                 if (!__any_sync(0xffffffffu, st0 || st1)) {
                     // no pixel of the warp stops here (the common case)
                     const f32x2 w = mul2(al, T);
@@ -1033,7 +1034,9 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
         // the guess staged already.
         if (hi != n_list && (int)threadIdx.x < cnt)
             stage(a.vals[rg.x + lo + threadIdx.x]);
-        __syncthreads();
+        // whether the chunk holds a record whose opacity exceeds alpha_max
+        // (each thread reads back the slot it staged; o is staged negated)
+        const bool clamp = __syncthreads_or((int)threadIdx.x < cnt && s1[threadIdx.x].y < -a.alpha_max) != 0;
         // this warp's pixels never reach past wl: skip the list tail
         const int wl = min(s_maxl[warp] - lo, cnt);
         int nsel = 0;
@@ -1050,6 +1053,8 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
             nsel += __popc(m);
         }
         __syncwarp();
+        auto walk = [&](auto clamp_tag) {
+        constexpr bool CLAMP = decltype(clamp_tag)::value;
         for (int k = nsel - 1; k >= 0; --k) {
             const int j = s_sel[warp][k];
             float g[NG];
@@ -1060,7 +1065,8 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
             R.co = make_ulonglong2(bc2(q1.x), bc2(q1.y));
             R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
             R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
-            const bool contrib = pix_adj_x2<!REG, FULL>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
+            const bool contrib =
+                pix_adj_x2<!REG, FULL, CLAMP>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
             if (__any_sync(0xffffffffu, contrib)) {
                 constexpr int NP = NG <= 8 ? 8 : 16;
                 float v[NP];
@@ -1074,6 +1080,11 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
                     s_slots[(k * kBwd2Warps + warp) * kBwdSlotRow + j] = sum;
             }
         }
+        };
+        if (clamp)
+            walk(std::true_type{});
+        else
+            walk(std::false_type{});
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
             float G[NG];
