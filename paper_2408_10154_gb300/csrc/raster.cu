@@ -94,6 +94,23 @@ __device__ __forceinline__ float4 stage_cutoff(float4 q1, const gsl::RasterArgs 
     return q1;
 }
 
+// Whether the exponent ca dx^2 + cb dx dy + cc dy^2 of a record, as the
+// walks evaluate it in FP32 (h = ca dx + (cb dy), ky = cc dy, h dx + (ky dy),
+// each product and sum rounded once), is <= 0 at every pixel, so that its
+// pairs need no positive-exponent test.  The form is negative definite with
+// smallest eigenvalue magnitude mu >= det / tr >= det / S (det = ca cc -
+// cb^2 / 4, S = |ca| + |cb| + |cc|), and the rounding moves the computed
+// value by at most 2.01 u S (dx^2 + dy^2) (u = 2^-24) plus subnormal
+// terms far below mu (dx^2 + dy^2): a nonzero offset is at least 2^-26 px.
+// det >= 1e-6 S^2 (after det's own rounding, <= 3u S^2) and |ca|, |cc| >
+// 1e-12 leave a wide margin.  NaN or infinite coefficients fail the test.
+__device__ __forceinline__ bool conic_safe(float ca, float cb, float cc)
+{
+    const float S = fabsf(ca) + fabsf(cb) + fabsf(cc);
+    const float det = ca * cc - 0.25f * cb * cb;
+    return ca < -1e-12f && cc < -1e-12f && det >= 1e-6f * (S * S);
+}
+
 // ---------------------------------------------------------------------------
 // Packed pixel pairs.  In the registration forward and adjoint a thread
 // walks two pixels (same column, rows r and r + 4) with one f32x2 operation
@@ -233,7 +250,7 @@ static_assert(kBwdPPT * kBwdRowStep == 8 && kTile % kBwdPatchW == 0, "warp patch
 __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t t, const VpDesc &d, uint2 rg,
                                               float4 *s0, float4 *s1, float4 *s2, const uint32_t *s_v,
                                               uint8_t *s_selw, float xa, float ya, PixAdj2 &P2, int maxl,
-                                              int wmaxl, const float *cc, bool fclamp);
+                                              int wmaxl, const float *cc, bool fgen);
 
 template <bool REG, int X, bool FUSED = false>
 __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_t t)
@@ -285,9 +302,10 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
     f32x2 T = bc2(1.0f), C0 = bc2(0.0f), C1 = bc2(0.0f), C2 = bc2(0.0f), D = bc2(0.0f);
     int last0 = 0, last1 = 0, nc = 0;
     bool done0 = !in0, done1 = !in1;
-    // whether the batch holds a record whose opacity exceeds alpha_max (only
-    // those can reach the clamp: x = o e with e <= 1 for every exponent <= 0)
-    bool clamp = false;
+    // whether the batch needs the general walk: it holds a record whose
+    // opacity exceeds alpha_max (only those can reach the clamp: x = o e with
+    // e <= 1 for every exponent <= 0) or whose exponent could round above 0
+    bool gen = false;
     for (uint32_t b = rg.x; b < rg.y; b += kFwdBatch) {
         if (b != rg.x) {
             if (__syncthreads_count(done0 && done1) == kFwdThreads)
@@ -302,9 +320,14 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
         {
             bool hot = false;
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
-                hot |= b + threadIdx.x + r * kFwdThreads < rg.y && s1[threadIdx.x + r * kFwdThreads].y > a.alpha_max;
-            clamp = __syncthreads_or(hot) != 0;
+            for (int r = 0; r < 2; ++r) {
+                const int sl = threadIdx.x + r * kFwdThreads;
+                if (b + sl < rg.y) {
+                    const float4 t0 = s0[sl], t1 = s1[sl];
+                    hot |= t1.y > a.alpha_max || !conic_safe(t0.z, t0.w, t1.x);
+                }
+            }
+            gen = __syncthreads_or(hot) != 0;
         }
         const int cnt = (int)min((uint32_t)kFwdBatch, rg.y - b);
         int nsel = 0;
@@ -328,10 +351,11 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
         // the votes below see all 32 lanes.
         if (!__all_sync(0xffffffffu, done0 && done1)) {
             const int base = (int)(b - rg.x) + 1;
-            // two copies of the walk: with the clamp, and for a batch that
-            // cannot reach it without (no compare, no min)
-            auto walk = [&](auto clamp_tag) {
-            constexpr bool CLAMP = decltype(clamp_tag)::value;
+            // two copies of the walk: the general one, and for a batch that
+            // can reach neither the clamp nor a positive exponent one without
+            // those tests
+            auto walk = [&](auto gen_tag) {
+            constexpr bool GEN = decltype(gen_tag)::value;
             for (int k = 0; k < nsel; ++k) {
                 const int j = s_sel[warp][k];
                 const float4 q0 = s0[j], q1 = s1[j], q2 = s2[j];
@@ -347,9 +371,9 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                 exp_ct_nonpos_x2(p0, p1, e0, e1);
                 float x0, x1;
                 x2_split(mul2(R.co.y, x2(e0, e1)), x0, x1);
-                const float al0 = CLAMP ? fminf(x0, a.alpha_max) : x0, al1 = CLAMP ? fminf(x1, a.alpha_max) : x1;
-                const bool ok0 = !done0 && !(p0 > 0.0f) && !(al0 < a.alpha_min);
-                const bool ok1 = !done1 && !(p1 > 0.0f) && !(al1 < a.alpha_min);
+                const float al0 = GEN ? fminf(x0, a.alpha_max) : x0, al1 = GEN ? fminf(x1, a.alpha_max) : x1;
+                const bool ok0 = !done0 && (!GEN || !(p0 > 0.0f)) && !(al0 < a.alpha_min);
+                const bool ok1 = !done1 && (!GEN || !(p1 > 0.0f)) && !(al1 < a.alpha_min);
                 const f32x2 al = x2(ok0 ? al0 : 0.0f, ok1 ? al1 : 0.0f);
                 const f32x2 tn = mul2(T, sub2(bc2(1.0f), al));  // T itself where al = 0
                 float tn0, tn1;
@@ -390,7 +414,7 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
                     break;
             }
             };
-            if (clamp)
+            if (gen)
                 walk(std::true_type{});
             else
                 walk(std::false_type{});
@@ -571,7 +595,7 @@ __device__ __forceinline__ void fwd_tile(const gsl::RasterArgs &a, const uint32_
         P2.gd = x2(g[0][3], g[1][3]);
         P2.last0 = last0;
         P2.last1 = last1;
-        fused_adjoint(a, t, d, rg, s0, s1, s2, s_v, s_sel[warp], xa, ya, P2, maxl, wmaxl, cc, clamp);
+        fused_adjoint(a, t, d, rg, s0, s1, s2, s_v, s_sel[warp], xa, ya, P2, maxl, wmaxl, cc, gen);
     }
 }
 
@@ -850,7 +874,7 @@ __device__ __forceinline__ void pix_adj_init(PixAdj &P, const VpDesc &d, const g
 // sign of zero sums).  ALPHA: the alpha image has a cotangent (render mode).
 // FULL: also the opacity and colour gradients (ng[6..9]).  Returns whether
 // either pixel contributed.
-template <bool ALPHA, bool FULL, bool CLAMP = true>
+template <bool ALPHA, bool FULL, bool GEN = true>
 __device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, float amax, float namax,
                                            float namin, float (&ng)[FULL ? 10 : 6])
 {
@@ -862,12 +886,12 @@ __device__ __forceinline__ bool pix_adj_x2(PixAdj2 &P, int jj, const RecX2 &R, f
     // -x = (-o) e; clamped: x > alpha_max; -alpha; the alpha test
     float nx0, nx1;
     x2_split(mul2(R.co.y, x2(e0, e1)), nx0, nx1);
-    const bool cl0 = CLAMP && nx0 < namax, cl1 = CLAMP && nx1 < namax;
-    const float na0 = CLAMP ? fmaxf(nx0, namax) : nx0, na1 = CLAMP ? fmaxf(nx1, namax) : nx1;
-    const bool live0 = jj < P.last0 && !(p0 > 0.0f) && !(na0 > namin);
-    const bool live1 = jj < P.last1 && !(p1 > 0.0f) && !(na1 > namin);
+    const bool cl0 = GEN && nx0 < namax, cl1 = GEN && nx1 < namax;
+    const float na0 = GEN ? fmaxf(nx0, namax) : nx0, na1 = GEN ? fmaxf(nx1, namax) : nx1;
+    const bool live0 = jj < P.last0 && (!GEN || !(p0 > 0.0f)) && !(na0 > namin);
+    const bool live1 = jj < P.last1 && (!GEN || !(p1 > 0.0f)) && !(na1 > namin);
     const f32x2 nal = x2(live0 ? na0 : 0.0f, live1 ? na1 : 0.0f);
-    const f32x2 nag = CLAMP ? x2(live0 && !cl0 ? na0 : 0.0f, live1 && !cl1 ? na1 : 0.0f) : nal;
+    const f32x2 nag = GEN ? x2(live0 && !cl0 ? na0 : 0.0f, live1 && !cl1 ? na1 : 0.0f) : nal;
     // 1 - alpha, its reciprocal, T_i = T / (1 - alpha)
     float om0, om1;
     x2_split(add2(bc2(1.0f), nal), om0, om1);
@@ -1034,9 +1058,15 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
         // the guess staged already.
         if (hi != n_list && (int)threadIdx.x < cnt)
             stage(a.vals[rg.x + lo + threadIdx.x]);
-        // whether the chunk holds a record whose opacity exceeds alpha_max
-        // (each thread reads back the slot it staged; o is staged negated)
-        const bool clamp = __syncthreads_or((int)threadIdx.x < cnt && s1[threadIdx.x].y < -a.alpha_max) != 0;
+        // whether the chunk needs the general walk (a record whose opacity
+        // exceeds alpha_max or whose exponent could round above 0; each
+        // thread reads back the slot it staged, o staged negated)
+        bool hot = false;
+        if ((int)threadIdx.x < cnt) {
+            const float4 t0 = s0[threadIdx.x], t1 = s1[threadIdx.x];
+            hot = t1.y < -a.alpha_max || !conic_safe(t0.z, t0.w, t1.x);
+        }
+        const bool gen = __syncthreads_or(hot) != 0;
         // this warp's pixels never reach past wl: skip the list tail
         const int wl = min(s_maxl[warp] - lo, cnt);
         int nsel = 0;
@@ -1053,8 +1083,8 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
             nsel += __popc(m);
         }
         __syncwarp();
-        auto walk = [&](auto clamp_tag) {
-        constexpr bool CLAMP = decltype(clamp_tag)::value;
+        auto walk = [&](auto gen_tag) {
+        constexpr bool GEN = decltype(gen_tag)::value;
         for (int k = nsel - 1; k >= 0; --k) {
             const int j = s_sel[warp][k];
             float g[NG];
@@ -1066,7 +1096,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
             R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
             R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
             const bool contrib =
-                pix_adj_x2<!REG, FULL, CLAMP>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
+                pix_adj_x2<!REG, FULL, GEN>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
             if (__any_sync(0xffffffffu, contrib)) {
                 constexpr int NP = NG <= 8 ? 8 : 16;
                 float v[NP];
@@ -1081,7 +1111,7 @@ __device__ __forceinline__ void bwd_tile(const gsl::RasterArgs &a, const uint32_
             }
         }
         };
-        if (clamp)
+        if (gen)
             walk(std::true_type{});
         else
             walk(std::false_type{});
@@ -1138,7 +1168,7 @@ __global__ void __launch_bounds__(kBwd2Threads, kBwd2MinBlocks) k_backward2_q(co
 __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t t, const VpDesc &d, uint2 rg,
                                               float4 *s0, float4 *s1, float4 *s2, const uint32_t *s_v,
                                               uint8_t *s_selw, float xa, float ya, PixAdj2 &P2, int maxl,
-                                              int wmaxl, const float *cc, bool fclamp)
+                                              int wmaxl, const float *cc, bool fgen)
 {
     constexpr int NG = 6;
     extern __shared__ float4 s_dyn[];
@@ -1187,14 +1217,18 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
         // them (in the epilogue).  Any later chunk follows an epilogue that
         // re-zeroed slot columns the walk writes, and restaged records are
         // read by every warp.
-        // whether the chunk holds a record whose opacity exceeds alpha_max
-        // (a list walked from the forward's staging: the forward's flag)
-        bool clamp = fclamp;
+        // whether the chunk needs the general walk (as in the forward; a
+        // list walked from the forward's staging takes the forward's flag)
+        bool gen = fgen;
         if (!(whole && hi == maxl)) {
-            const bool hot = !whole && (int)threadIdx.x < cnt && s1[threadIdx.x].y > a.alpha_max;
+            bool hot = false;
+            if (!whole && (int)threadIdx.x < cnt) {
+                const float4 t0 = s0[threadIdx.x], t1 = s1[threadIdx.x];
+                hot = t1.y > a.alpha_max || !conic_safe(t0.z, t0.w, t1.x);
+            }
             const bool any_hot = __syncthreads_or(hot) != 0;
             if (!whole)
-                clamp = any_hot;
+                gen = any_hot;
         }
         const int wl = min(wmaxl - lo, cnt);
         int nsel = 0;
@@ -1211,8 +1245,8 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
             nsel += __popc(m);
         }
         __syncwarp();
-        auto walk = [&](auto clamp_tag) {
-        constexpr bool CLAMP = decltype(clamp_tag)::value;
+        auto walk = [&](auto gen_tag) {
+        constexpr bool GEN = decltype(gen_tag)::value;
         for (int k = nsel - 1; k >= 0; --k) {
             const int j = s_selw[k];
             float g[NG];
@@ -1224,7 +1258,7 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
             R.zr = make_ulonglong2(bc2(q1.z), bc2(q2.x));
             R.gb = make_ulonglong2(bc2(q2.y), bc2(q2.z));
             const bool contrib =
-                pix_adj_x2<false, false, CLAMP>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
+                pix_adj_x2<false, false, GEN>(P2, lo + j, R, a.alpha_max, -a.alpha_max, -a.alpha_min, g);
             if (__any_sync(0xffffffffu, contrib)) {
                 float v[8];
 #pragma unroll
@@ -1237,7 +1271,7 @@ __device__ __forceinline__ void fused_adjoint(const gsl::RasterArgs &a, uint32_t
             }
         }
         };
-        if (clamp)
+        if (gen)
             walk(std::true_type{});
         else
             walk(std::false_type{});
