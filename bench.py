@@ -51,8 +51,8 @@ BWD_FLOPS_CONTRIB = 64.0
 # DRAM bytes per launch of the room workload from one ncu capture of the
 # current kernel (the fused forward + adjoint that the timed calls run, and
 # the two-kernel adjoint); None while the kernel has changed since the capture
-FB_TRAFFIC_BYTES = 278.108672e6
-BWD_TRAFFIC_BYTES = 185.745408e6
+FB_TRAFFIC_BYTES = 278.152448e6
+BWD_TRAFFIC_BYTES = 185.502976e6
 FP32_LANES = 128
 PEAK_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
