@@ -78,6 +78,8 @@ def _load():
         lib.or_exp32.argtypes = [ctypes.c_float]
         lib.or_exp32_count_above_one.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
         lib.or_exp32_count_above_one.restype = ctypes.c_int64
+        lib.or_count_positive_power.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 7
+        lib.or_count_positive_power.restype = ctypes.c_int64
         lib.or_exp32.restype = ctypes.c_float
         lib.or_log32.argtypes = [ctypes.c_float]
         lib.or_log32.restype = ctypes.c_float
@@ -177,6 +179,15 @@ def exp32_count_above_one(lo_bits: int, hi_bits: int) -> int:
     """How many floats with bit patterns in [lo_bits, hi_bits] the mirror's
     exponential maps above 1."""
     return int(_load().or_exp32_count_above_one(lo_bits, hi_bits))
+
+
+def count_positive_power(ca, cb, cc, u, v, pxf, pyf) -> int:
+    """How many of the given (conic, mean, pixel sample) cases the mirror's
+    FP32 exponent puts above 0 (float32 arrays of one length)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (ca, cb, cc, u, v, pxf, pyf)]
+    n = len(arrs[0])
+    assert all(len(a) == n for a in arrs)
+    return int(_load().or_count_positive_power(n, *[a.ctypes.data for a in arrs]))
 
 
 def log32(x: float) -> float:

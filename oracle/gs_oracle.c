@@ -328,13 +328,20 @@ static void m_project(const float *mu, const float *s, const float *q, float log
 
 /* Contribution decision of Gaussian g at pixel (px,py).  Returns 1 and the
  * FP32 alpha if it contributes (before the transmittance test). */
+/* the exponent of the Gaussian density at pixel sample (pxf, pyf) in the
+ * mirror's FP32 sequence: dx, dy, h = ca dx + (cb dy), (cc dy) dy, h dx + that */
+static float m_power(float u, float v, float ca, float cb, float cc, float pxf, float pyf)
+{
+    float dx = u - pxf, dy = v - pyf;
+    float h = fmaf(ca, dx, cb * dy);
+    float k = (cc * dy) * dy;
+    return fmaf(h, dx, k);
+}
+
 static int m_alpha(const m32_t *g, int px, int py, const opts_t *op, float *alpha, int *clamped)
 {
     float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    float dx = g->u - pxf, dy = g->v - pyf;
-    float h = fmaf(g->ca, dx, g->cb * dy);
-    float k = (g->cc * dy) * dy;
-    float power = fmaf(h, dx, k);
+    float power = m_power(g->u, g->v, g->ca, g->cb, g->cc, pxf, pyf);
     if (power > 0.0f)
         return 0;
     float x = g->o * or_exp32(power);
@@ -345,6 +352,20 @@ static int m_alpha(const m32_t *g, int px, int py, const opts_t *op, float *alph
     *alpha = a;
     *clamped = cl;
     return 1;
+}
+
+/* How many of n (conic, mean, pixel sample) cases have a positive mirror
+ * exponent (a property check for the tests: a well-conditioned conic's
+ * exponent never rounds above 0).  Multi-threaded under or_set_threads. */
+int64_t or_count_positive_power(int64_t n, const float *ca, const float *cb, const float *cc, const float *u,
+                                const float *v, const float *pxf, const float *pyf)
+{
+    int64_t pos = 0;
+#pragma omp parallel for schedule(static) reduction(+ : pos)
+    for (int64_t i = 0; i < n; ++i)
+        if (m_power(u[i], v[i], ca[i], cb[i], cc[i], pxf[i], pyf[i]) > 0.0f)
+            ++pos;
+    return pos;
 }
 
 /* ======================================================================== */

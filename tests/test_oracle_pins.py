@@ -63,6 +63,52 @@ def test_exp32_at_most_one_for_every_nonpositive_float():
     assert O.exp32_count_above_one(0x3F000000, 0x3F000001) == 2  # the scan sees e^0.5 > 1
 
 
+def test_well_conditioned_conic_exponent_is_never_positive():
+    # The compositing walks drop the positive-exponent test for batches whose
+    # conics all satisfy ca, cc < -1e-12 and ca cc - cb^2 / 4 >= 1e-6 S^2
+    # (S = |ca| + |cb| + |cc|): a negative-definite quadratic form whose FP32
+    # evaluation cannot round above 0.  Adversarial sample: conics of every
+    # scale and axis ratio, down to and past the criterion's edge, with pixel
+    # samples along an eigen-axis (mostly the weak one) from 2^-26 px to
+    # 8000 px away.  No conic that passes may give a positive mirror
+    # exponent; near-singular and indefinite ones that fail must give some,
+    # which shows that the sample reaches the regime.
+    rng = np.random.default_rng(7)
+    n = 8_000_000
+    l1 = np.exp(rng.uniform(-30.0, 5.0, n))
+    ratio = np.exp(rng.uniform(-30.0, 0.0, n))
+    indef = rng.random(n) < 0.3
+    ratio[indef] *= -1e-3
+    l2 = l1 * ratio
+    th = rng.uniform(0.0, 2.0 * np.pi, n)
+    c, s_ = np.cos(th), np.sin(th)
+    ca = (-(l1 * c * c + l2 * s_ * s_)).astype(np.float32)
+    cc = (-(l1 * s_ * s_ + l2 * c * c)).astype(np.float32)
+    cb = (-2.0 * (l1 - l2) * c * s_).astype(np.float32)
+    mag = np.exp(rng.uniform(-18.0, 9.0, n))
+    d = th + np.where(rng.random(n) < 0.8, 0.5 * np.pi, 0.0) + (rng.random(n) - 0.5) * 1e-3 * rng.random(n)
+    ox, oy = mag * np.cos(d), mag * np.sin(d)
+    u = 1000.0 * rng.random(n)
+    v = 1000.0 * rng.random(n)
+    pxf = np.floor(u - ox) + 0.5
+    pyf = np.floor(v - oy) + 0.5
+    near = rng.random(n) < 0.5  # the mean placed at the exact offset from a pixel centre
+    u = np.where(near, pxf + ox, u)
+    v = np.where(near, pyf + oy, v)
+    f32 = np.float32
+    S = np.abs(ca) + np.abs(cb) + np.abs(cc)
+    det = ca * cc - f32(0.25) * cb * cb
+    ok = (ca < f32(-1e-12)) & (cc < f32(-1e-12)) & (det >= f32(1e-6) * (S * S))
+    args = [a.astype(np.float32) for a in (ca, cb, cc, u, v, pxf, pyf)]
+    assert ok.sum() > n // 4 and (~ok).sum() > n // 4
+    prev = O.set_threads(os.cpu_count() or 1)
+    try:
+        assert O.count_positive_power(*[a[ok] for a in args]) == 0
+        assert O.count_positive_power(*[a[~ok] for a in args]) > 1000
+    finally:
+        O.set_threads(prev)
+
+
 def test_exp32_monotone_on_alpha_range():
     xs = np.float32(-6.0) + np.arange(60000, dtype=np.float32) * np.float32(1e-4)
     vals = [O.exp32(float(x)) for x in xs]
