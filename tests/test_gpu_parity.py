@@ -574,7 +574,7 @@ def room_edge(gs, ctx):
 
 
 def test_registration_room_full_size_100_iterations_matches_oracle(gs, ctx, room_edge):
-    # The spec bar on the benchmarked configuration: for the keyframe
+    # The accuracy bar on the full-size room edge: for the keyframe
     # of each direction whose GPU residual fell the most (a converging
     # problem), the oracle runs the same 100 iterations on the same inputs;
     # the recovered transforms agree within 0.5 mm / 0.01 deg, and the GPU
