@@ -305,3 +305,19 @@ def saturated_case(seed=41):
     c["gaussians"] = g
     return c
 
+
+def giant_needles_case(seed=51):
+    """A small scene with a few giant needles (3 % of the Gaussians: one
+    axis e^1.8 = 6 m, the others e^-6 = 2.5 mm) among ordinary splats: their
+    projections cross the whole 120x90 image with 2D covariances so
+    elongated that their conics' condition numbers pass 10^6, 2 views."""
+    c = small_case(600, 120, 90, 100.0, n_views=2, seed=seed, ls_mean=-3.0, ls_std=0.3)
+    g = {k: np.array(v, copy=True) for k, v in c["gaussians"].items()}
+    rng = np.random.default_rng(seed + 1)
+    giant = rng.random(len(g["logits"])) < 0.03
+    g["log_scales4"][giant, 0] = 1.8
+    g["log_scales4"][giant, 1] = -6.0
+    g["log_scales4"][giant, 2] = -6.0
+    c["gaussians"] = g
+    return c
+

@@ -61,6 +61,9 @@ CASES = {
         synth.small_case(3000, 64, 48, 200.0, n_views=2, seed=31, ls_mean=-3.0, ls_std=0.2, half=0.05)),
     # alphas at the 0.99 clamp on the left half only
     "saturated_160x120": lambda: (lambda c: (c["gaussians"], c["cams"]))(synth.saturated_case()),
+    # needles across the whole image whose conics are too ill-conditioned
+    # for the fast walk
+    "giant_needles_120x90": lambda: (lambda c: (c["gaussians"], c["cams"]))(synth.giant_needles_case()),
 }
 
 

@@ -99,8 +99,20 @@ def saturated_case():
     return c["gaussians"], c["cams"]
 
 
+def giant_needles_case():
+    # a few needles across the whole image with ill-conditioned conics
+    c = synth.giant_needles_case()
+    return c["gaussians"], c["cams"]
+
+
 CASES = {"plain_2k": plain_case, "ragged_100x70": ragged_case, "needles_300x200": needle_case,
          "saturated_160x120": saturated_case}
+# Conics with condition numbers near 10^6: every FP32 decision still matches
+# the oracle bit for bit, but the FP32 exponent's rounding error grows with
+# the condition number (about u kappa of the form's terms), so rendered
+# values are compared only through the decisions there.
+ILL_CASES = {"giant_needles_120x90": giant_needles_case}
+EXACT_CASES = {**CASES, **ILL_CASES}
 
 
 # ----------------------------------------------------------------- projection
@@ -141,9 +153,9 @@ def check_projection(gs, ctx, gd, cams, poses, tight=True):
 
 
 @pytest.mark.parametrize("tight", [1, 0])
-@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("case", list(EXACT_CASES))
 def test_projection_bit_exact(gs, ctx, case, tight):
-    gd, cams = CASES[case]()
+    gd, cams = EXACT_CASES[case]()
     poses = rand_poses(np.random.default_rng(1), len(cams))
     assert check_projection(gs, ctx, gd, cams, poses, tight) > 0
 
@@ -170,9 +182,9 @@ def check_binning(gs, ctx, gd, cams, poses, tight=True):
 
 
 @pytest.mark.parametrize("tight", [1, 0])
-@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("case", list(EXACT_CASES))
 def test_binning_bit_exact(gs, ctx, case, tight):
-    gd, cams = CASES[case]()
+    gd, cams = EXACT_CASES[case]()
     poses = rand_poses(np.random.default_rng(3), len(cams))
     assert check_binning(gs, ctx, gd, cams, poses, tight) > 0
 
@@ -227,8 +239,9 @@ def test_binning_empty(gs, ctx):
 
 
 # ----------------------------------------------------------------- render
-def check_render(gs, ctx, gd, cams, poses, opt_o=O.DEFAULT_OPT, opt_g=None):
-    # opt_g None: the library defaults, whose tight rectangles DEFAULT_OPT mirrors
+def check_render(gs, ctx, gd, cams, poses, opt_o=O.DEFAULT_OPT, opt_g=None, values=True):
+    # opt_g None: the library defaults, whose tight rectangles DEFAULT_OPT mirrors;
+    # values False: the decisions (T_final bits, `last`) only
     og = O.Gaussians.from_dict(gd)
     g = gs.Gaussians.from_numpy(gd)
     out = gs.gs_render(ctx, g, dev(poses.reshape(-1, 12)), cams, opt_g)
@@ -244,7 +257,8 @@ def check_render(gs, ctx, gd, cams, poses, opt_o=O.DEFAULT_OPT, opt_g=None):
                     np.abs(alp[c] - ref["alpha"]).max())
         np.testing.assert_array_equal(tf[c].view(np.uint32), ref["t_final32"].view(np.uint32))
         np.testing.assert_array_equal(last[c], ref["last"])
-    assert worst <= 1e-4, worst
+    if values:
+        assert worst <= 1e-4, worst
     return out
 
 
@@ -254,6 +268,16 @@ def test_render_parity(gs, ctx, case, tight):
     gd, cams = CASES[case]()
     opt_g, opt_o = opts(gs, tight)
     check_render(gs, ctx, gd, cams, rand_poses(np.random.default_rng(5), len(cams)), opt_o, opt_g)
+
+
+@pytest.mark.parametrize("tight", [1, 0])
+@pytest.mark.parametrize("case", list(ILL_CASES))
+def test_render_decisions_ill_conditioned(gs, ctx, case, tight):
+    # batches holding these conics take the general compositing walk (with
+    # the positive-exponent test); T_final and `last` bit-exact
+    gd, cams = ILL_CASES[case]()
+    opt_g, opt_o = opts(gs, tight)
+    check_render(gs, ctx, gd, cams, rand_poses(np.random.default_rng(5), len(cams)), opt_o, opt_g, values=False)
 
 
 def test_render_parity_smooth_mode(gs, ctx):
