@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_pose_update(const gsl::PoseArg
 #pragma unroll
     for (int i = 0; i < 9; ++i)
         hs[i] = ls[i] = 0.0f;
+#pragma unroll 4
     for (uint32_t k = threadIdx.x; k < nt; k += blockDim.x) {
         const size_t t = d.tile_base + k;
         if (a.tile_twist)
